@@ -1,0 +1,198 @@
+"""ctypes wrapper around the C oracle (test infrastructure only).
+
+The oracle runs the plain method single-threaded: for every parent it builds
+the Liouvillian column term by term [Eq. (1), Eq. (2)], draws one Philox word
+per walker [End Matter, spawn step], and annihilates with a sorted merge
+[End Matter, annihilation step].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .build import build
+
+_lib = None
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_DT_TOO_LARGE = -4
+ERR_POP_OVERFLOW = -5
+ERR_STATE = -8
+ERR_COEF_RANGE = -9
+
+EULER = 0
+AB2 = 1
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        L.orc_problem_new.restype = C.c_void_p
+        L.orc_problem_new.argtypes = [C.c_int] + [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                   C.c_void_p, C.c_void_p] + \
+            [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p] + \
+            [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p] + \
+            [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p] + \
+            [C.c_int, C.c_void_p, C.c_void_p]
+        L.orc_problem_free.argtypes = [C.c_void_p]
+        L.orc_column.restype = C.c_int
+        L.orc_column.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
+                                 C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_state_new.restype = C.c_void_p
+        L.orc_state_new.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
+                                    C.c_int64]
+        L.orc_state_free.argtypes = [C.c_void_p]
+        L.orc_init.restype = C.c_int
+        L.orc_init.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p]
+        L.orc_set_population.restype = C.c_int
+        L.orc_set_population.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
+        L.orc_set_clock.restype = C.c_int
+        L.orc_set_clock.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_double, C.c_double,
+                                    C.c_int]
+        L.orc_get_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_step.restype = C.c_int
+        L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.orc_count.restype = C.c_int64
+        L.orc_count.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_export.restype = C.c_int
+        L.orc_export.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]
+        L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+class OracleProblem:
+    """The oracle's own copy of a :class:`problems.Problem`."""
+
+    def __init__(self, prob):
+        self.prob = prob
+        self.n = prob.n
+        a = prob.arrays()
+        self._keep = a
+        L = lib()
+        d = lambda k: a[k].ctypes.data if a[k].size else None  # noqa: E731
+        self.handle = L.orc_problem_new(
+            prob.n,
+            len(a["h"]), d("h"), d("hx"), d("hz"), d("hrate"), d("hwin"),
+            len(a["lstart"]), d("lstart"), d("lcount"), d("lrate"), d("lwin"),
+            len(a["lre"]), d("lre"), d("lim"), d("lx"), d("lz"),
+            len(a["rkind"]), d("rkind"), d("ra"), d("rb"), d("rc"),
+            len(a["wt0"]), d("wt0"), d("wt1"))
+        if not self.handle:
+            raise ValueError("oracle rejected the problem")
+
+    def column(self, x: int, y: int, t: float, dt_eff: float):
+        """Quantised column of dt_eff * L(t) at |x><y|: (mask, qre, qim) sorted by mask,
+        in units of 2^-52."""
+        cap = 4096
+        mask = np.zeros(cap, dtype=np.uint64)
+        qre = np.zeros(cap, dtype=np.int64)
+        qim = np.zeros(cap, dtype=np.int64)
+        n = lib().orc_column(self.handle, x, y, t, dt_eff, cap, mask.ctypes.data,
+                             qre.ctypes.data, qim.ctypes.data)
+        if n < 0:
+            raise RuntimeError(f"orc_column failed: {n}")
+        return mask[:n].copy(), qre[:n].copy(), qim[:n].copy()
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().orc_problem_free(self.handle)
+            self.handle = None
+
+
+class OracleSim:
+    """Populations of ``nseg`` independent vectors evolved by the plain method."""
+
+    def __init__(self, prob, nseg: int, seed: int, integrator: int = AB2,
+                 init_min: int = 0, n_diag: int = 10000):
+        self.problem = prob if isinstance(prob, OracleProblem) else OracleProblem(prob)
+        self.n = self.problem.n
+        self.nseg = nseg
+        self.n_diag = n_diag
+        self.handle = lib().orc_state_new(self.problem.handle, nseg, seed, integrator,
+                                          init_min, n_diag)
+        if not self.handle:
+            raise ValueError("oracle rejected the state")
+
+    def init(self, rho0):
+        x = np.array([e[0] for e in rho0], dtype=np.uint64)
+        y = np.array([e[1] for e in rho0], dtype=np.uint64)
+        re = np.array([e[2] for e in rho0], dtype=np.float64)
+        im = np.array([e[3] for e in rho0], dtype=np.float64)
+        rc = lib().orc_init(self.handle, len(x), x.ctypes.data, y.ctypes.data, re.ctypes.data,
+                            im.ctypes.data)
+        if rc != OK:
+            raise RuntimeError(f"orc_init failed: {rc}")
+
+    def set_population(self, seg: int, keys, re, im, which: int = 0):
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        re = np.ascontiguousarray(re, dtype=np.int32)
+        im = np.ascontiguousarray(im, dtype=np.int32)
+        rc = lib().orc_set_population(self.handle, seg, which, len(keys), keys.ctypes.data,
+                                      re.ctypes.data, im.ctypes.data)
+        if rc != OK:
+            raise RuntimeError(f"orc_set_population failed: {rc}")
+
+    def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
+                  prev_valid: bool = False):
+        lib().orc_set_clock(self.handle, step, t, t_prev, dt_last, int(prev_valid))
+
+    def clock(self):
+        step = np.zeros(1, dtype=np.uint64)
+        tt = np.zeros(4, dtype=np.float64)
+        lib().orc_get_clock(self.handle, step.ctypes.data, tt.ctypes.data)
+        return int(step[0]), float(tt[0]), float(tt[1]), float(tt[2]), bool(tt[3])
+
+    def step(self, dt: float, nsteps: int = 1) -> int:
+        return lib().orc_step(self.handle, dt, nsteps)
+
+    def population(self, seg: int, which: int = 0):
+        cnt = lib().orc_count(self.handle, seg, which)
+        keys = np.zeros(cnt, dtype=np.uint64)
+        re = np.zeros(cnt, dtype=np.int32)
+        im = np.zeros(cnt, dtype=np.int32)
+        if cnt:
+            lib().orc_export(self.handle, seg, which, keys.ctypes.data, re.ctypes.data,
+                             im.ctypes.data)
+        return keys, re, im
+
+    def stats(self, seg: int):
+        out = np.zeros(4, dtype=np.int64)
+        lib().orc_stats(self.handle, seg, out.ctypes.data)
+        return out
+
+    def density(self, seg: int) -> np.ndarray:
+        """Dense N(t) of one vector as a D x D complex matrix (tiny n only)."""
+        D = 1 << self.n
+        rho = np.zeros((D, D), dtype=np.complex128)
+        keys, re, im = self.population(seg)
+        x = (keys >> np.uint64(self.n)).astype(np.int64)
+        y = (keys & np.uint64(D - 1)).astype(np.int64)
+        rho[x, y] = re + 1j * im
+        return rho
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().orc_state_free(self.handle)
+            self.handle = None

@@ -1,0 +1,721 @@
+/*
+ * qmc_oracle.c -- CPU oracle for one step of real-time population-dynamics QMC
+ * (Shen & Lidar, "Real-time sign-problem-suppressed QMC for noisy quantum
+ * circuit simulations", arXiv:2502.18929).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this file.  It shares no
+ * code with the CUDA library: its Philox, Pauli algebra, Liouvillian column,
+ * sampling and annihilation are written out here, plainly and slowly, one
+ * parent and one walker at a time.  Build with -ffp-contract=off.
+ *
+ * What it computes (paper passages in brackets):
+ *   - The Liouvillian column of an occupied state |x><y| [Eq. (1), Eq. (2)],
+ *     evaluated term by term by applying Pauli strings to the ket and bra.
+ *     Each expanded term's coefficient c * rate(t) * dt_eff is rounded to the
+ *     grid 2^-52 ("quantised"), then the column's elements are exact integer
+ *     sums of those (reading R1: exact integer weights, so the sum order does
+ *     not matter).
+ *   - Spawning [End Matter, spawn step]: N^sp ~ B(m, p) with
+ *     p = dt * sum_kl (|Re L| + |Im L|), spread over (kl, channel) by a
+ *     multinomial with probabilities |c(L)| / sum.  Written as m independent
+ *     walkers, each drawing one 64-bit Philox word R: T = R >> 12; the walker
+ *     spawns iff T < P (P = p * 2^52) and then goes to the entry whose
+ *     cumulative-weight interval holds T (reading R2).  The sign rule is the
+ *     paper's: Re channel s * sgn(Re L), Im channel i * s * sgn(Im L).
+ *   - Annihilation [End Matter, annihilation step]: spawned walkers are added
+ *     to the current population key by key; opposite signs cancel; zeros go.
+ *   - Initiator rule [End Matter, simulation methodology]: a spawn from a
+ *     parent with fewer than xi N^diag walkers onto a state unoccupied in N(t)
+ *     is discarded.  The threshold arrives as an integer walker count.
+ *   - Euler and AB2 [End Matter, simulation methodology]: AB2 spawns from N(t)
+ *     with dt_eff = 1.5 dt at L(t) and from N(t - dt) with dt_eff = 0.5 dt at
+ *     L(t - dt), the latter with the opposite sign.  The first step (and the
+ *     first after a change of dt) is Euler.
+ *   - Initialisation N(0) = N^diag rho(0) [walker averaging, Eq. (3)]:
+ *     stochastic rounding of each component.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_INVALID_ARG (-1)
+#define ORC_ERR_OOM (-2)
+#define ORC_ERR_DT_TOO_LARGE (-4)
+#define ORC_ERR_POP_OVERFLOW (-5)
+#define ORC_ERR_STATE (-8)
+#define ORC_ERR_COEF_RANGE (-9)
+
+#define ONE_52 4503599627370496.0 /* 2^52 */
+#define P_LIMIT (((int64_t)1) << 52)
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11): 10 rounds of the 4x32 round function with the   */
+/* published multipliers and Weyl key increments.                           */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Stream layout (reading R3; the paper names no generator). */
+#define TAG_STEP 0x53544550u /* per (step, segment) key derivation */
+#define TAG_INIT 0x494E4954u /* per segment key for initial rounding */
+#define KIND_SPAWN 0u
+#define KIND_INIT 1u
+
+static void derive_key(uint64_t seed, uint64_t step, uint32_t seg, uint32_t tag, uint32_t kd[2])
+{
+    uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), seg, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox(ctr, key, out);
+    kd[0] = out[0];
+    kd[1] = out[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct { double h; uint64_t xm, zm; int rate, win; } ham_term;
+typedef struct { double re, im; uint64_t xm, zm; } pauli_coef;
+typedef struct { int start, count, rate, win; } lind_op;
+typedef struct { int kind; double a, b, c; } rate_fn;
+typedef struct { double t0, t1; } window_fn;
+
+typedef struct {
+    int n;
+    int nh, nl, nr, nw;
+    ham_term* ham;
+    lind_op* lind;
+    pauli_coef* lp;
+    rate_fn* rates;
+    window_fn* wins;
+} problem;
+
+void* orc_problem_new(int n,
+                      int nh, const double* h, const uint64_t* hx, const uint64_t* hz,
+                      const int32_t* hrate, const int32_t* hwin,
+                      int nl, const int32_t* lstart, const int32_t* lcount,
+                      const int32_t* lrate, const int32_t* lwin,
+                      int nlp, const double* lre, const double* lim,
+                      const uint64_t* lx, const uint64_t* lz,
+                      int nr, const int32_t* rkind, const double* ra, const double* rb,
+                      const double* rc,
+                      int nw, const double* wt0, const double* wt1)
+{
+    if (n < 1 || n > 32) return NULL;
+    problem* p = (problem*)calloc(1, sizeof(problem));
+    if (!p) return NULL;
+    p->n = n; p->nh = nh; p->nl = nl; p->nr = nr; p->nw = nw;
+    p->ham = (ham_term*)calloc((size_t)(nh > 0 ? nh : 1), sizeof(ham_term));
+    p->lind = (lind_op*)calloc((size_t)(nl > 0 ? nl : 1), sizeof(lind_op));
+    p->lp = (pauli_coef*)calloc((size_t)(nlp > 0 ? nlp : 1), sizeof(pauli_coef));
+    p->rates = (rate_fn*)calloc((size_t)(nr > 0 ? nr : 1), sizeof(rate_fn));
+    p->wins = (window_fn*)calloc((size_t)(nw > 0 ? nw : 1), sizeof(window_fn));
+    for (int i = 0; i < nh; ++i) {
+        p->ham[i].h = h[i]; p->ham[i].xm = hx[i]; p->ham[i].zm = hz[i];
+        p->ham[i].rate = hrate[i]; p->ham[i].win = hwin[i];
+    }
+    for (int i = 0; i < nl; ++i) {
+        p->lind[i].start = lstart[i]; p->lind[i].count = lcount[i];
+        p->lind[i].rate = lrate[i]; p->lind[i].win = lwin[i];
+    }
+    for (int i = 0; i < nlp; ++i) {
+        p->lp[i].re = lre[i]; p->lp[i].im = lim[i]; p->lp[i].xm = lx[i]; p->lp[i].zm = lz[i];
+    }
+    for (int i = 0; i < nr; ++i) {
+        p->rates[i].kind = rkind[i]; p->rates[i].a = ra[i];
+        p->rates[i].b = rb[i]; p->rates[i].c = rc[i];
+    }
+    for (int i = 0; i < nw; ++i) { p->wins[i].t0 = wt0[i]; p->wins[i].t1 = wt1[i]; }
+    return p;
+}
+
+void orc_problem_free(void* pp)
+{
+    problem* p = (problem*)pp;
+    if (!p) return;
+    free(p->ham); free(p->lind); free(p->lp); free(p->rates); free(p->wins);
+    free(p);
+}
+
+static double rate_value(const problem* p, int id, double t)
+{
+    const rate_fn* r = &p->rates[id];
+    if (r->kind == 1) return r->a * cos(r->b * t + r->c);
+    return r->a;
+}
+
+static int window_on(const problem* p, int id, double t)
+{
+    if (id < 0) return 1;
+    return p->wins[id].t0 <= t && t < p->wins[id].t1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pauli strings on computational basis states.                            */
+/* X|b> = |1-b>, Y|b> = i (-1)^b |1-b>, Z|b> = (-1)^b |b>.  A phase is i^k,  */
+/* k in {0,1,2,3}.                                                          */
+/* ------------------------------------------------------------------------ */
+static void pauli_on_ket(int n, uint64_t xm, uint64_t zm, uint64_t x, uint64_t* x_out, int* k_out)
+{
+    int k = 0;
+    for (int q = 0; q < n; ++q) {
+        int xb = (int)((xm >> q) & 1u), zb = (int)((zm >> q) & 1u);
+        int b = (int)((x >> q) & 1u);
+        if (xb && zb) {              /* Y */
+            k += 1 + (b ? 2 : 0);
+            x ^= ((uint64_t)1) << q;
+        } else if (xb) {             /* X */
+            x ^= ((uint64_t)1) << q;
+        } else if (zb) {             /* Z */
+            k += b ? 2 : 0;
+        }
+    }
+    *x_out = x;
+    *k_out = k & 3;
+}
+
+typedef struct { int64_t re, im; } cint;
+
+/* (a + ib) * i^k, exact */
+static cint times_ik(cint z, int k)
+{
+    cint r;
+    switch (k & 3) {
+    case 0: r = z; break;
+    case 1: r.re = -z.im; r.im = z.re; break;
+    case 2: r.re = -z.re; r.im = -z.im; break;
+    default: r.re = z.im; r.im = -z.re; break;
+    }
+    return r;
+}
+
+/* Round a coefficient to the grid 2^-52 (nearest, ties to even). */
+static int quantise(double re, double im, cint* out)
+{
+    double a = re * ONE_52, b = im * ONE_52;
+    if (!(fabs(a) < 4611686018427387904.0) || !(fabs(b) < 4611686018427387904.0))
+        return ORC_ERR_COEF_RANGE; /* |c| >= 2^10: no such step can have p < 1 */
+    out->re = (int64_t)nearbyint(a);
+    out->im = (int64_t)nearbyint(b);
+    return ORC_OK;
+}
+
+/* Column entries of dt_eff * L(t) for the source |x><y|: a small list of     */
+/* destinations keyed by mask = (dx << n) | dy, kept sorted by that key.      */
+typedef struct { uint64_t mask; cint v; } col_entry;
+typedef struct { col_entry* e; int len, cap; } column;
+
+static int column_add(column* c, uint64_t mask, cint v)
+{
+    int lo = 0, hi = c->len;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (c->e[mid].mask < mask) lo = mid + 1; else hi = mid;
+    }
+    if (lo < c->len && c->e[lo].mask == mask) {
+        c->e[lo].v.re += v.re;
+        c->e[lo].v.im += v.im;
+        return ORC_OK;
+    }
+    if (c->len == c->cap) {
+        int ncap = c->cap ? 2 * c->cap : 64;
+        col_entry* ne = (col_entry*)realloc(c->e, (size_t)ncap * sizeof(col_entry));
+        if (!ne) return ORC_ERR_OOM;
+        c->e = ne;
+        c->cap = ncap;
+    }
+    memmove(&c->e[lo + 1], &c->e[lo], (size_t)(c->len - lo) * sizeof(col_entry));
+    c->e[lo].mask = mask;
+    c->e[lo].v = v;
+    c->len++;
+    return ORC_OK;
+}
+
+/*
+ * Column of dt_eff * L(t) at source |x><y| [Eq. (1), Eq. (2)].
+ * Expanded terms (each quantised on its own, reading R1):
+ *   -i[H, rho]:  for h P with s = rate(t) * dt_eff and v = h * s:
+ *                (-i v) P rho      and   (+i v) rho P
+ *   gamma(t) (L rho L^dag - 1/2 L^dag L rho - 1/2 rho L^dag L), L = sum_a l_a P_a,
+ *                with s = gamma(t) * dt_eff, for every ordered pair (a, b):
+ *                z = l_a conj(l_b) = (la.re lb.re + la.im lb.im, la.im lb.re - la.re lb.im)
+ *                (s z) P_a rho P_b
+ *                (-s/2) conj(z) P_a P_b rho    and   (-s/2) conj(z) rho P_a P_b
+ * A bra-side string acts as <y|P = conj(phase of P|y>) <y'| (P Hermitian);
+ * <y| P_a P_b is the conjugate of P_b P_a |y>.
+ */
+static int build_column(const problem* p, uint64_t x, uint64_t y, double t, double dt_eff,
+                        column* col)
+{
+    const int n = p->n;
+    col->len = 0;
+    int rc;
+    for (int i = 0; i < p->nh; ++i) {
+        const ham_term* ht = &p->ham[i];
+        if (!window_on(p, ht->win, t)) continue;
+        double s = rate_value(p, ht->rate, t) * dt_eff;
+        double v = ht->h * s;
+        cint qk, qb;
+        if ((rc = quantise(0.0, -v, &qk)) != ORC_OK) return rc;
+        if ((rc = quantise(0.0, v, &qb)) != ORC_OK) return rc;
+        uint64_t x2, y2;
+        int kx, ky;
+        pauli_on_ket(n, ht->xm, ht->zm, x, &x2, &kx);
+        if ((rc = column_add(col, ((x ^ x2) << n), times_ik(qk, kx))) != ORC_OK) return rc;
+        pauli_on_ket(n, ht->xm, ht->zm, y, &y2, &ky);
+        if ((rc = column_add(col, (y ^ y2), times_ik(qb, 4 - ky))) != ORC_OK) return rc;
+    }
+    for (int i = 0; i < p->nl; ++i) {
+        const lind_op* lo = &p->lind[i];
+        if (!window_on(p, lo->win, t)) continue;
+        double s = rate_value(p, lo->rate, t) * dt_eff;
+        double hs = -0.5 * s;
+        for (int a = 0; a < lo->count; ++a) {
+            const pauli_coef* la = &p->lp[lo->start + a];
+            for (int b = 0; b < lo->count; ++b) {
+                const pauli_coef* lb = &p->lp[lo->start + b];
+                double zre = la->re * lb->re + la->im * lb->im;
+                double zim = la->im * lb->re - la->re * lb->im;
+                cint qj, qa;
+                if ((rc = quantise(s * zre, s * zim, &qj)) != ORC_OK) return rc;
+                if ((rc = quantise(hs * zre, -(hs * zim), &qa)) != ORC_OK) return rc;
+                uint64_t xa, yb, u1, u2, v1, v2;
+                int ka, kb, k1, k2, j1, j2;
+                /* jump: P_a |x><y| P_b */
+                pauli_on_ket(n, la->xm, la->zm, x, &xa, &ka);
+                pauli_on_ket(n, lb->xm, lb->zm, y, &yb, &kb);
+                if ((rc = column_add(col, ((x ^ xa) << n) | (y ^ yb),
+                                     times_ik(qj, ka + 4 - kb))) != ORC_OK) return rc;
+                /* ket side: P_a P_b |x> */
+                pauli_on_ket(n, lb->xm, lb->zm, x, &u1, &k1);
+                pauli_on_ket(n, la->xm, la->zm, u1, &u2, &k2);
+                if ((rc = column_add(col, ((x ^ u2) << n), times_ik(qa, k1 + k2))) != ORC_OK)
+                    return rc;
+                /* bra side: <y| P_a P_b = conj(P_b P_a |y>) */
+                pauli_on_ket(n, la->xm, la->zm, y, &v1, &j1);
+                pauli_on_ket(n, lb->xm, lb->zm, v1, &v2, &j2);
+                if ((rc = column_add(col, (y ^ v2), times_ik(qa, 8 - j1 - j2))) != ORC_OK)
+                    return rc;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Exported for tests: the quantised column, sorted by mask.  Returns the
+ * number of entries (which may exceed cap; only cap are written) or < 0. */
+int orc_column(const void* pp, uint64_t x, uint64_t y, double t, double dt_eff, int cap,
+               uint64_t* mask, int64_t* qre, int64_t* qim)
+{
+    const problem* p = (const problem*)pp;
+    column col = {0, 0, 0};
+    int rc = build_column(p, x, y, t, dt_eff, &col);
+    if (rc != ORC_OK) { free(col.e); return rc; }
+    for (int i = 0; i < col.len && i < cap; ++i) {
+        mask[i] = col.e[i].mask;
+        qre[i] = col.e[i].v.re;
+        qim[i] = col.e[i].v.im;
+    }
+    int len = col.len;
+    free(col.e);
+    return len;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Populations                                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint64_t key; int32_t re, im; } rec;
+typedef struct { rec* r; int64_t len, cap; } pop;
+
+typedef struct { uint64_t key; int64_t re, im; int noninit; } spawn_rec;
+typedef struct { spawn_rec* s; int64_t len, cap; } spawn_list;
+
+typedef struct {
+    const problem* prob;
+    int nseg;
+    uint64_t seed;
+    int integrator;       /* 0 = Euler, 1 = AB2 */
+    int64_t init_min;     /* initiator threshold in walkers (ceil(xi N^diag)); 0 = off */
+    int64_t n_diag;
+    pop* cur;
+    pop* prev;
+    uint64_t step;        /* global step index */
+    double t, t_prev, dt_last;
+    int prev_valid;
+} state;
+
+static int pop_reserve(pop* p, int64_t cap)
+{
+    if (p->cap >= cap) return ORC_OK;
+    int64_t nc = p->cap ? p->cap : 16;
+    while (nc < cap) nc *= 2;
+    rec* nr = (rec*)realloc(p->r, (size_t)nc * sizeof(rec));
+    if (!nr) return ORC_ERR_OOM;
+    p->r = nr;
+    p->cap = nc;
+    return ORC_OK;
+}
+
+static int spawn_push(spawn_list* l, uint64_t key, int64_t re, int64_t im, int noninit)
+{
+    if (l->len == l->cap) {
+        int64_t nc = l->cap ? 2 * l->cap : 256;
+        spawn_rec* ns = (spawn_rec*)realloc(l->s, (size_t)nc * sizeof(spawn_rec));
+        if (!ns) return ORC_ERR_OOM;
+        l->s = ns;
+        l->cap = nc;
+    }
+    l->s[l->len].key = key;
+    l->s[l->len].re = re;
+    l->s[l->len].im = im;
+    l->s[l->len].noninit = noninit;
+    l->len++;
+    return ORC_OK;
+}
+
+void* orc_state_new(const void* prob, int nseg, uint64_t seed, int integrator, int64_t init_min,
+                    int64_t n_diag)
+{
+    if (!prob || nseg < 1) return NULL;
+    state* s = (state*)calloc(1, sizeof(state));
+    if (!s) return NULL;
+    s->prob = (const problem*)prob;
+    s->nseg = nseg;
+    s->seed = seed;
+    s->integrator = integrator;
+    s->init_min = init_min;
+    s->n_diag = n_diag;
+    s->cur = (pop*)calloc((size_t)nseg, sizeof(pop));
+    s->prev = (pop*)calloc((size_t)nseg, sizeof(pop));
+    return s;
+}
+
+void orc_state_free(void* sp)
+{
+    state* s = (state*)sp;
+    if (!s) return;
+    for (int i = 0; i < s->nseg; ++i) { free(s->cur[i].r); free(s->prev[i].r); }
+    free(s->cur); free(s->prev);
+    free(s);
+}
+
+static int cmp_u64(uint64_t a, uint64_t b) { return a < b ? -1 : (a > b ? 1 : 0); }
+
+static int rec_cmp(const void* a, const void* b)
+{
+    return cmp_u64(((const rec*)a)->key, ((const rec*)b)->key);
+}
+
+static int spawn_cmp(const void* a, const void* b)
+{
+    return cmp_u64(((const spawn_rec*)a)->key, ((const spawn_rec*)b)->key);
+}
+
+/* N(0) := N^diag rho(0), each component stochastically rounded (reading R4). */
+int orc_init(void* sp, int ne, const uint64_t* x, const uint64_t* y, const double* re,
+             const double* im)
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    for (int seg = 0; seg < s->nseg; ++seg) {
+        uint32_t kd[2];
+        derive_key(s->seed, 0, (uint32_t)seg, TAG_INIT, kd);
+        pop* c = &s->cur[seg];
+        c->len = 0;
+        s->prev[seg].len = 0;
+        if (pop_reserve(c, ne > 0 ? ne : 1) != ORC_OK) return ORC_ERR_OOM;
+        for (int i = 0; i < ne; ++i) {
+            uint64_t key = (x[i] << n) | y[i];
+            int64_t v[2];
+            for (int comp = 0; comp < 2; ++comp) {
+                double val = (double)s->n_diag * (comp == 0 ? re[i] : im[i]);
+                double fl = floor(val);
+                double fr = val - fl;
+                uint32_t ctr[4] = {(uint32_t)key, (uint32_t)(key >> 32),
+                                   ((uint32_t)comp << 1) | (KIND_INIT << 2), 0u};
+                uint32_t w[4];
+                orc_philox(ctr, kd, w);
+                uint64_t r = ((uint64_t)w[1] << 32) | w[0];
+                double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+                v[comp] = (int64_t)fl + (u < fr ? 1 : 0);
+                if (v[comp] > INT32_MAX || v[comp] < -INT32_MAX) return ORC_ERR_POP_OVERFLOW;
+            }
+            if (v[0] == 0 && v[1] == 0) continue;
+            c->r[c->len].key = key;
+            c->r[c->len].re = (int32_t)v[0];
+            c->r[c->len].im = (int32_t)v[1];
+            c->len++;
+        }
+        qsort(c->r, (size_t)c->len, sizeof(rec), rec_cmp);
+        for (int64_t i = 1; i < c->len; ++i)
+            if (c->r[i].key == c->r[i - 1].key) return ORC_ERR_INVALID_ARG;
+    }
+    s->step = 0;
+    s->t = 0.0;
+    s->t_prev = 0.0;
+    s->dt_last = 0.0;
+    s->prev_valid = 0;
+    return ORC_OK;
+}
+
+int orc_set_population(void* sp, int seg, int which, int64_t cnt, const uint64_t* keys,
+                       const int32_t* re, const int32_t* im)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    pop* p = which ? &s->prev[seg] : &s->cur[seg];
+    if (pop_reserve(p, cnt > 0 ? cnt : 1) != ORC_OK) return ORC_ERR_OOM;
+    p->len = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+        if (re[i] == 0 && im[i] == 0) continue;
+        p->r[p->len].key = keys[i];
+        p->r[p->len].re = re[i];
+        p->r[p->len].im = im[i];
+        p->len++;
+    }
+    qsort(p->r, (size_t)p->len, sizeof(rec), rec_cmp);
+    for (int64_t i = 1; i < p->len; ++i)
+        if (p->r[i].key == p->r[i - 1].key) return ORC_ERR_INVALID_ARG;
+    return ORC_OK;
+}
+
+int orc_set_clock(void* sp, uint64_t step, double t, double t_prev, double dt_last, int prev_valid)
+{
+    state* s = (state*)sp;
+    s->step = step;
+    s->t = t;
+    s->t_prev = t_prev;
+    s->dt_last = dt_last;
+    s->prev_valid = prev_valid;
+    return ORC_OK;
+}
+
+void orc_get_clock(void* sp, uint64_t* step, double* tt)
+{
+    state* s = (state*)sp;
+    *step = s->step;
+    tt[0] = s->t;
+    tt[1] = s->t_prev;
+    tt[2] = s->dt_last;
+    tt[3] = (double)s->prev_valid;
+}
+
+/*
+ * Spawns of one parent [End Matter, spawn step].  phase 0: the population
+ * N(t) (sign +1); phase 1: N(t - dt) in AB2 (sign -1).  Every spawned walker,
+ * including one landing on the parent itself (the diagonal, "death/cloning"
+ * element, which is one of the kl in the paper's sum), becomes one record.
+ */
+static int spawn_parent(const state* s, const rec* par, int phase, double t, double dt_eff,
+                        int sigma, const uint32_t kd[2], column* col, spawn_list* out)
+{
+    const problem* p = s->prob;
+    const int n = p->n;
+    uint64_t x = par->key >> n;
+    uint64_t y = par->key & ((((uint64_t)1) << n) - 1);
+    int rc = build_column(p, x, y, t, dt_eff, col);
+    if (rc != ORC_OK) return rc;
+
+    /* P = 2^52 * dt_eff * sum_kl (|Re L_kl| + |Im L_kl|) */
+    int64_t P = 0;
+    for (int e = 0; e < col->len; ++e) {
+        P += llabs(col->e[e].v.re) + llabs(col->e[e].v.im);
+        if (P >= P_LIMIT) return ORC_ERR_DT_TOO_LARGE;
+    }
+    int64_t walkers = llabs((int64_t)par->re) + llabs((int64_t)par->im);
+    int noninit = (s->init_min > 0 && walkers < s->init_min) ? 1 : 0;
+
+    for (int comp = 0; comp < 2; ++comp) {
+        int64_t val = comp == 0 ? par->re : par->im;
+        int64_t m = llabs(val);
+        int64_t sg = val > 0 ? 1 : -1;
+        uint32_t w[4] = {0, 0, 0, 0};
+        for (int64_t j = 0; j < m; ++j) {
+            if ((j & 1) == 0) {
+                uint32_t ctr[4] = {(uint32_t)par->key, (uint32_t)(par->key >> 32),
+                                   (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_SPAWN << 2),
+                                   (uint32_t)(j >> 1)};
+                orc_philox(ctr, kd, w);
+            }
+            uint64_t R = (j & 1) ? (((uint64_t)w[3] << 32) | w[2])
+                                 : (((uint64_t)w[1] << 32) | w[0]);
+            int64_t T = (int64_t)(R >> 12);
+            if (T >= P) continue; /* this walker does not spawn */
+            /* multinomial over (destination, channel) in ascending mask order,
+             * Re channel before Im channel */
+            for (int e = 0; e < col->len; ++e) {
+                int64_t wr = llabs(col->e[e].v.re);
+                int64_t wi = llabs(col->e[e].v.im);
+                int chan = -1;
+                if (T < wr) chan = 0;
+                else {
+                    T -= wr;
+                    if (T < wi) chan = 1;
+                    else T -= wi;
+                }
+                if (chan < 0) continue;
+                int64_t dre = 0, dim = 0;
+                if (chan == 0) {
+                    /* Re channel: sign s * sgn(Re L) */
+                    int64_t sv = sigma * sg * (col->e[e].v.re > 0 ? 1 : -1);
+                    if (comp == 0) dre = sv; else dim = sv;
+                } else {
+                    /* Im channel: sign i * s * sgn(Im L) */
+                    int64_t sv = sigma * sg * (col->e[e].v.im > 0 ? 1 : -1);
+                    if (comp == 0) dim = sv; else dre = -sv;
+                }
+                rc = spawn_push(out, par->key ^ col->e[e].mask, dre, dim, noninit);
+                if (rc != ORC_OK) return rc;
+                break;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Annihilation [End Matter, annihilation step] with the initiator rule. */
+static int annihilate(const pop* cur, spawn_list* sp, pop* next)
+{
+    qsort(sp->s, (size_t)sp->len, sizeof(spawn_rec), spawn_cmp);
+    int rc = pop_reserve(next, cur->len + sp->len + 1);
+    if (rc != ORC_OK) return rc;
+    next->len = 0;
+    int64_t i = 0, j = 0;
+    while (i < cur->len || j < sp->len) {
+        uint64_t key;
+        if (j >= sp->len || (i < cur->len && cur->r[i].key <= sp->s[j].key)) key = cur->r[i].key;
+        else key = sp->s[j].key;
+        int occupied = (i < cur->len && cur->r[i].key == key);
+        int64_t re = 0, im = 0;
+        if (occupied) { re = cur->r[i].re; im = cur->r[i].im; ++i; }
+        while (j < sp->len && sp->s[j].key == key) {
+            if (occupied || !sp->s[j].noninit) { re += sp->s[j].re; im += sp->s[j].im; }
+            ++j;
+        }
+        if (re == 0 && im == 0) continue;
+        if (re > INT32_MAX || re < -INT32_MAX || im > INT32_MAX || im < -INT32_MAX)
+            return ORC_ERR_POP_OVERFLOW;
+        next->r[next->len].key = key;
+        next->r[next->len].re = (int32_t)re;
+        next->r[next->len].im = (int32_t)im;
+        next->len++;
+    }
+    return ORC_OK;
+}
+
+/*
+ * nsteps steps of size dt.  Step i of this call uses L at t_i = t0 + i*dt,
+ * where t0 is the clock at entry; an AB2 step's second pass uses L at the
+ * time the previous step used.
+ */
+int orc_step(void* sp, double dt, int nsteps)
+{
+    state* s = (state*)sp;
+    if (!(dt > 0.0) || nsteps < 0) return ORC_ERR_INVALID_ARG;
+    column col = {0, 0, 0};
+    spawn_list spl = {0, 0, 0};
+    pop next = {0, 0, 0};
+    int rc = ORC_OK;
+    const double t0 = s->t;
+    for (int it = 0; it < nsteps && rc == ORC_OK; ++it) {
+        double t = t0 + (double)it * dt;
+        int ab2 = (s->integrator == 1 && s->prev_valid && s->dt_last == dt);
+        double dt_cur = ab2 ? dt * 1.5 : dt;
+        double dt_prev = dt * 0.5;
+        for (int seg = 0; seg < s->nseg && rc == ORC_OK; ++seg) {
+            uint32_t kd[2];
+            derive_key(s->seed, s->step, (uint32_t)seg, TAG_STEP, kd);
+            spl.len = 0;
+            const pop* cur = &s->cur[seg];
+            for (int64_t i = 0; i < cur->len && rc == ORC_OK; ++i)
+                rc = spawn_parent(s, &cur->r[i], 0, t, dt_cur, 1, kd, &col, &spl);
+            if (ab2) {
+                const pop* prv = &s->prev[seg];
+                for (int64_t i = 0; i < prv->len && rc == ORC_OK; ++i)
+                    rc = spawn_parent(s, &prv->r[i], 1, s->t_prev, dt_prev, -1, kd, &col, &spl);
+            }
+            if (rc != ORC_OK) break;
+            /* spawns from N(t - dt) that land on states unoccupied in N(t) are
+             * treated like every other spawn: the initiator rule uses N(t). */
+            rc = annihilate(cur, &spl, &next);
+            if (rc != ORC_OK) break;
+            /* rotate: prev <- cur, cur <- next */
+            pop old_prev = s->prev[seg];
+            s->prev[seg] = s->cur[seg];
+            s->cur[seg] = next;
+            next = old_prev;
+        }
+        if (rc != ORC_OK) break;
+        s->t_prev = t;
+        s->dt_last = dt;
+        s->prev_valid = 1;
+        s->step += 1;
+        s->t = t0 + (double)(it + 1) * dt;
+    }
+    free(col.e);
+    free(spl.s);
+    free(next.r);
+    return rc;
+}
+
+int64_t orc_count(void* sp, int seg, int which)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg) return -1;
+    return which ? s->prev[seg].len : s->cur[seg].len;
+}
+
+int orc_export(void* sp, int seg, int which, uint64_t* keys, int32_t* re, int32_t* im)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    const pop* p = which ? &s->prev[seg] : &s->cur[seg];
+    for (int64_t i = 0; i < p->len; ++i) {
+        keys[i] = p->r[i].key;
+        re[i] = p->r[i].re;
+        im[i] = p->r[i].im;
+    }
+    return ORC_OK;
+}
+
+/* K, N_tot = sum |re| + |im|, and N^diag = sum over x == y (re, im). */
+void orc_stats(void* sp, int seg, int64_t out[4])
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    const pop* p = &s->cur[seg];
+    int64_t ntot = 0, dre = 0, dim = 0;
+    uint64_t ymask = (((uint64_t)1) << n) - 1;
+    for (int64_t i = 0; i < p->len; ++i) {
+        ntot += llabs((int64_t)p->r[i].re) + llabs((int64_t)p->r[i].im);
+        if ((p->r[i].key >> n) == (p->r[i].key & ymask)) {
+            dre += p->r[i].re;
+            dim += p->r[i].im;
+        }
+    }
+    out[0] = p->len;
+    out[1] = ntot;
+    out[2] = dre;
+    out[3] = dim;
+}

@@ -1,0 +1,283 @@
+"""Problem descriptions and seeded synthetic inputs.
+
+This module only *describes* master equations and initial populations; it holds
+none of the method's arithmetic (no Liouvillian expansion, no sampling).  Both
+the CUDA path and the CPU oracle consume the same description.
+
+Conventions
+-----------
+* Qubit ``q`` is bit ``q`` of a basis index ``x`` (``x = sum_q x_q 2**q``).
+* A Pauli string is a pair of bit masks ``(xm, zm)``: qubit ``q`` carries
+  ``I`` (0,0), ``X`` (1,0), ``Z`` (0,1) or the Hermitian ``Y`` (1,1).
+* The master equation is Eq. (1):
+  ``drho/dt = -i[H(t), rho] + 1/2 sum_k gamma_k(t) D[L_k] rho`` with
+  ``D[L] rho = 2 L rho L^dag - {L^dag L, rho}``.
+  ``H(t) = sum_j h_j r_j(t) w_j(t) P_j`` and each ``L_k = sum_a l_a P_a``.
+* Rates: kind 0 = constant ``a``; kind 1 = ``a * cos(b * t + c)``.
+* Windows: ``[t0, t1)``; window id -1 means "always on".
+* A density-matrix element ``rho_xy`` lives at the packed key ``(x << n) | y``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+RATE_CONST = 0
+RATE_COS = 1
+ALWAYS = -1
+
+
+def pauli(spec: dict[int, str]) -> tuple[int, int]:
+    """Return ``(xm, zm)`` for a Pauli string given as ``{qubit: 'X'|'Y'|'Z'}``."""
+    xm = zm = 0
+    for q, letter in spec.items():
+        letter = letter.upper()
+        if letter in ("X", "Y"):
+            xm |= 1 << q
+        if letter in ("Z", "Y"):
+            zm |= 1 << q
+        if letter not in ("I", "X", "Y", "Z"):
+            raise ValueError(f"bad Pauli letter {letter!r}")
+    return xm, zm
+
+
+@dataclass
+class Problem:
+    """A time-local master equation over ``n`` qubits (Eq. (1))."""
+
+    n: int
+    ham: list = field(default_factory=list)      # (h, xm, zm, rate_id, window_id)
+    lind: list = field(default_factory=list)     # ([(coef complex, xm, zm)], rate_id, window_id)
+    rates: list = field(default_factory=list)    # (kind, a, b, c)
+    windows: list = field(default_factory=list)  # (t0, t1)
+    name: str = ""
+    t_end: float = 0.0
+
+    # -- construction helpers -------------------------------------------------
+    def rate(self, kind: int, a: float, b: float = 0.0, c: float = 0.0) -> int:
+        self.rates.append((int(kind), float(a), float(b), float(c)))
+        return len(self.rates) - 1
+
+    def window(self, t0: float, t1: float) -> int:
+        self.windows.append((float(t0), float(t1)))
+        return len(self.windows) - 1
+
+    def add_h(self, h: float, spec: dict[int, str], rate: int, window: int = ALWAYS):
+        xm, zm = pauli(spec)
+        self.ham.append((float(h), xm, zm, int(rate), int(window)))
+
+    def add_lindblad(self, ops: list, rate: int, window: int = ALWAYS):
+        """``ops`` is a list of ``(complex coefficient, {qubit: letter})``."""
+        terms = []
+        for coef, spec in ops:
+            xm, zm = pauli(spec)
+            terms.append((complex(coef), xm, zm))
+        self.lind.append((terms, int(rate), int(window)))
+
+    # -- flat arrays for the C interfaces ------------------------------------
+    def arrays(self) -> dict:
+        h = np.array([t[0] for t in self.ham], dtype=np.float64)
+        hx = np.array([t[1] for t in self.ham], dtype=np.uint64)
+        hz = np.array([t[2] for t in self.ham], dtype=np.uint64)
+        hr = np.array([t[3] for t in self.ham], dtype=np.int32)
+        hw = np.array([t[4] for t in self.ham], dtype=np.int32)
+        lstart, lcount, lrate, lwin = [], [], [], []
+        lre, lim, lx, lz = [], [], [], []
+        for ops, r, w in self.lind:
+            lstart.append(len(lre))
+            lcount.append(len(ops))
+            lrate.append(r)
+            lwin.append(w)
+            for coef, xm, zm in ops:
+                lre.append(coef.real)
+                lim.append(coef.imag)
+                lx.append(xm)
+                lz.append(zm)
+        return dict(
+            h=h, hx=hx, hz=hz, hrate=hr, hwin=hw,
+            lstart=np.array(lstart, dtype=np.int32), lcount=np.array(lcount, dtype=np.int32),
+            lrate=np.array(lrate, dtype=np.int32), lwin=np.array(lwin, dtype=np.int32),
+            lre=np.array(lre, dtype=np.float64), lim=np.array(lim, dtype=np.float64),
+            lx=np.array(lx, dtype=np.uint64), lz=np.array(lz, dtype=np.uint64),
+            rkind=np.array([r[0] for r in self.rates], dtype=np.int32),
+            ra=np.array([r[1] for r in self.rates], dtype=np.float64),
+            rb=np.array([r[2] for r in self.rates], dtype=np.float64),
+            rc=np.array([r[3] for r in self.rates], dtype=np.float64),
+            wt0=np.array([w[0] for w in self.windows], dtype=np.float64),
+            wt1=np.array([w[1] for w in self.windows], dtype=np.float64),
+        )
+
+    def boundaries(self, t_end: float | None = None) -> list[float]:
+        """Sorted window edges inside ``[0, t_end]`` (segment edges for a run)."""
+        t_end = self.t_end if t_end is None else t_end
+        edges = {0.0, float(t_end)}
+        for t0, t1 in self.windows:
+            for e in (t0, t1):
+                if 0.0 < e < t_end:
+                    edges.add(float(e))
+        return sorted(edges)
+
+
+# ---------------------------------------------------------------------------
+# Noise channels used throughout the paper's circuits (transmon model):
+# amplitude damping L = sigma^- = |0><1| = (X + iY)/2 and dephasing L = Z.
+# ---------------------------------------------------------------------------
+
+def add_local_noise(p: Problem, gamma1: float, gamma_phi: float, x_basis: bool = False,
+                    rate_kind: int = RATE_CONST, omega1: float = 0.0, omega_phi: float = 0.0):
+    """Per-qubit amplitude damping (rate gamma1) and dephasing (rate gamma_phi).
+
+    With ``x_basis`` every operator is conjugated by Hadamards (X <-> Z, Y -> -Y),
+    which is how a ``|+>``-type initial state is kept sparse.
+    With ``rate_kind == RATE_COS`` the rates are ``gamma * cos(omega t)`` (negative
+    half-periods are non-Markovian).
+    """
+    r1 = p.rate(rate_kind, gamma1, omega1 if rate_kind == RATE_COS else 0.0)
+    rp = p.rate(rate_kind, gamma_phi, omega_phi if rate_kind == RATE_COS else 0.0)
+    for q in range(p.n):
+        if gamma1 != 0.0:
+            if x_basis:
+                # H sigma^- H = (Z - iY)/2
+                p.add_lindblad([(0.5, {q: "Z"}), (-0.5j, {q: "Y"})], r1)
+            else:
+                p.add_lindblad([(0.5, {q: "X"}), (0.5j, {q: "Y"})], r1)
+        if gamma_phi != 0.0:
+            p.add_lindblad([(1.0, {q: "X" if x_basis else "Z"})], rp)
+
+
+def add_hadamard_pulse(p: Problem, q: int, t0: float, t1: float):
+    """Square pulse whose propagator over ``[t0, t1)`` is the Hadamard gate.
+
+    Generator (pi/2)(I - (X+Z)/sqrt 2) / (t1 - t0); the identity part drops out of
+    the commutator, so only the X and Z parts are kept.
+    """
+    dur = t1 - t0
+    w = p.window(t0, t1)
+    one = p.rate(RATE_CONST, 1.0)
+    amp = -(math.pi / 2.0) / math.sqrt(2.0) / dur
+    p.add_h(amp, {q: "X"}, one, w)
+    p.add_h(amp, {q: "Z"}, one, w)
+
+
+def add_cnot_pulse(p: Problem, c: int, t: int, t0: float, t1: float):
+    """Square pulse with generator (pi/4)(1 - Z_c)(1 - X_t) / (t1 - t0).
+
+    exp(-i pi Proj) with Proj = |1><1|_c (x) |-><-|_t is exactly CNOT.  The
+    identity part is dropped (it commutes with everything).
+    """
+    dur = t1 - t0
+    w = p.window(t0, t1)
+    one = p.rate(RATE_CONST, 1.0)
+    a = (math.pi / 4.0) / dur
+    p.add_h(-a, {c: "Z"}, one, w)
+    p.add_h(-a, {t: "X"}, one, w)
+    p.add_h(a, {c: "Z", t: "X"}, one, w)
+
+
+def ghz_circuit(n: int, gamma1: float = 0.01, gamma_phi: float = 0.02, pulse: float = 1.0,
+                rate_kind: int = RATE_CONST, omega1: float = 0.0, omega_phi: float = 0.0) -> Problem:
+    """GHZ preparation: Hadamard on q0, then CNOT(q_i -> q_{i+1}); each gate is a
+    square pulse of duration ``pulse`` (Fig. 1(d)), under local noise."""
+    p = Problem(n=n, name=f"ghz{n}")
+    add_hadamard_pulse(p, 0, 0.0, pulse)
+    for i in range(n - 1):
+        add_cnot_pulse(p, i, i + 1, (i + 1) * pulse, (i + 2) * pulse)
+    add_local_noise(p, gamma1, gamma_phi, rate_kind=rate_kind, omega1=omega1, omega_phi=omega_phi)
+    p.t_end = n * pulse
+    return p
+
+
+def dd_ring(n: int = 12, seed: int = 0, gamma_phi: float = 5e-3, gamma1: float = 2e-3,
+            width: float = 0.02, tau: float = 1.0, t_end: float = 20.0,
+            x_basis: bool = True) -> Problem:
+    """Staggered XX dynamical decoupling on a ring with ZZ crosstalk (Fig. 1(c)).
+
+    ``H = sum_i J_i Z_i Z_{i+1}`` (ring), ``J_i ~ U[0.5, 1.5] * 2 pi * 1e-3`` from
+    ``seed``.  Even qubits get X pulses at tau/2 + k tau, odd qubits at tau + k tau
+    (each a square pi pulse of duration ``width``).  In the X basis (the sparse
+    frame for ``|+>^n``) ZZ -> XX and the X pulses become Z pulses.
+    """
+    rng = np.random.default_rng(seed)
+    J = rng.uniform(0.5, 1.5, size=n) * 2.0 * math.pi * 1e-3
+    p = Problem(n=n, name=f"dd{n}")
+    one = p.rate(RATE_CONST, 1.0)
+    zz = "X" if x_basis else "Z"
+    for i in range(n):
+        p.add_h(float(J[i]), {i: zz, (i + 1) % n: zz}, one)
+    amp = math.pi / (2.0 * width)
+    letter = "Z" if x_basis else "X"
+    k = 0
+    while True:
+        placed = False
+        for q in range(n):
+            start = (tau / 2.0 if q % 2 == 0 else tau) + k * tau
+            if start + width <= t_end:
+                w = p.window(start, start + width)
+                p.add_h(amp, {q: letter}, one, w)
+                placed = True
+        if not placed:
+            break
+        k += 1
+    add_local_noise(p, gamma1, gamma_phi, x_basis=x_basis)
+    p.t_end = t_end
+    return p
+
+
+def pure_noise(n: int, gamma1: float, gamma_phi: float, rate_kind: int = RATE_CONST,
+               omega1: float = 0.0, omega_phi: float = 0.0) -> Problem:
+    p = Problem(n=n, name=f"noise{n}")
+    add_local_noise(p, gamma1, gamma_phi, rate_kind=rate_kind, omega1=omega1, omega_phi=omega_phi)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# Initial density matrices (sparse) and observable targets
+# ---------------------------------------------------------------------------
+
+def rho_basis(x: int = 0) -> list:
+    """``|x><x|`` as sparse entries ``(x, y, re, im)``."""
+    return [(x, x, 1.0, 0.0)]
+
+
+def rho_pure(amplitudes: dict[int, complex]) -> list:
+    """``|psi><psi|`` for a sparse ``psi`` (normalised here)."""
+    norm = math.sqrt(sum(abs(a) ** 2 for a in amplitudes.values()))
+    out = []
+    for x, ax in sorted(amplitudes.items()):
+        for y, ay in sorted(amplitudes.items()):
+            v = (ax / norm) * (ay / norm).conjugate()
+            if v != 0:
+                out.append((x, y, v.real, v.imag))
+    return out
+
+
+def ghz_target(n: int) -> dict[int, complex]:
+    return {0: 1.0, (1 << n) - 1: 1.0}
+
+
+def w_state(n: int) -> dict[int, complex]:
+    return {1 << q: 1.0 for q in range(n)}
+
+
+def spread_population(n: int, count: int, seed: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """``count`` distinct uniformly random keys over 2n bits, each holding one
+    walker of sign +1, -1, +i or -i.  Returns sorted keys and int32 (re, im)."""
+    rng = np.random.default_rng(seed)
+    bits = 2 * n
+    keys = np.empty(0, dtype=np.uint64)
+    while keys.size < count:
+        need = int((count - keys.size) * 1.05) + 16
+        if bits >= 64:
+            cand = rng.integers(0, 2**63, size=need, dtype=np.uint64) * np.uint64(2) + \
+                rng.integers(0, 2, size=need, dtype=np.uint64)
+        else:
+            cand = rng.integers(0, 1 << bits, size=need, dtype=np.uint64)
+        keys = np.unique(np.concatenate([keys, cand]))
+    keys = rng.permutation(keys)[:count]
+    keys.sort()
+    sel = rng.integers(0, 4, size=count)
+    re = np.where(sel == 0, 1, np.where(sel == 1, -1, 0)).astype(np.int32)
+    im = np.where(sel == 2, 1, np.where(sel == 3, -1, 0)).astype(np.int32)
+    return keys, re, im
