@@ -1,0 +1,394 @@
+"""Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--workload dd12|ghz4|spread32|ghzN]
+
+One "step" is one dt step of every population vector through the whole hot
+path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
+of the spawns, annihilation + initiator rule + compaction, per-vector
+observables.  value = sum over the timed steps of N_tot (walkers of N(t + dt),
+all vectors, all ranks) / max-over-ranks device time.
+
+Default workload ``dd12``: staggered-XX dynamical decoupling on a 12-qubit ring
+with ZZ crosstalk, 64 vectors x 1e6 walkers, dt = 0.005 (pulse windows
+sub-stepped so p < 1/2), t in [0, 20).  By default the timed region is the
+whole trajectory after the warm-up steps.
+
+Multi-GPU: vectors are independent, so each rank runs its own 64 vectors
+(seed offset by rank) with no collective on the data path ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_18929_gb300 import planner  # noqa: E402
+from paper_2502_18929_gb300 import problems as P  # noqa: E402
+
+METRIC = "walker-steps/s (spawn+annihilate)"
+UNIT = "walker-steps/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def workload(name: str):
+    if name == "dd12":
+        prob = P.dd_ring(12, seed=0, t_end=20.0)
+        return dict(name="dd12", desc="staggered-XX DD, 12-qubit ring, ZZ crosstalk, X basis",
+                    prob=prob, nseg=64, n_diag=10**6, dt=0.005, t_end=20.0, rho0=P.rho_basis(0))
+    if name == "ghz4":
+        prob = P.ghz_circuit(4)
+        return dict(name="ghz4", desc="GHZ-4 preparation", prob=prob, nseg=16, n_diag=10**4, dt=0.01,
+                    t_end=4.0, rho0=P.rho_basis(0))
+    if name.startswith("ghz") and name[3:].isdigit():
+        n = int(name[3:])
+        prob = P.ghz_circuit(n)
+        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8}.get(n, 10**7)
+        return dict(name=name, desc=f"GHZ-{n} preparation", prob=prob, nseg=16, n_diag=total // 16, dt=0.01,
+                    t_end=float(n), rho0=P.rho_basis(0))
+    if name == "spread32":
+        prob = P.ghz_circuit(32)
+        return dict(name="spread32", desc="1e8 random states x 1 walker, GHZ-32 Liouvillian in a CNOT window",
+                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
+                    spread=10**8 // 64)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def step_list(wl):
+    pl = planner.plan(wl["prob"], wl["t_end"], wl["dt"], t_start=wl.get("t_start", 0.0))
+    return pl
+
+
+def run_range(sim, pl, begin: int, count: int):
+    """Steps [begin, begin + count) of plan pl (pieces keep their own dt)."""
+    idx = 0
+    done = 0
+    for t0, d, n in pl:
+        lo, hi = idx, idx + n
+        idx = hi
+        a, b = max(lo, begin), min(hi, begin + count)
+        if a >= b:
+            continue
+        if a == lo:
+            step, _, tp, dl, pv = sim.clock()
+            sim.set_clock(step, t0, tp, dl, pv)
+        sim.step(d, b - a)
+        done += b - a
+    return done
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def kernel_bytes(name: str, c: dict) -> float:
+    """Algorithmic bytes of a kernel over the counted steps (16-byte records)."""
+    r = 16.0
+    if name == "k_spawn_light":
+        return r * (c["k_cur"] + c["k_prev"] + c["spawns"])
+    if name == "k_merge":
+        return r * (c["k_cur"] + c["spawns"] + c["k_next"])
+    if name == "k_sort_scatter":
+        return r * 2.0 * c["spawns"] * c.get("passes", 1)
+    if name == "k_sort_hist":
+        return r * c["spawns"]
+    return 0.0
+
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_2502_18929_gb300 import qmc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    wl = workload(args.workload)
+    prob = wl["prob"]
+    stream = torch.cuda.current_stream()
+    seed = 1000 + rank
+    sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
+                  capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
+    sim.load_schedule(prob)
+    pl = step_list(wl)
+    total = planner.total_steps(pl)
+    W = args.warmup
+    K = args.steps if args.steps > 0 else total - W
+    if W + K > total:
+        raise SystemExit(f"workload has {total} steps; warmup + steps = {W + K}")
+
+    # host inputs (e2e leg starts here)
+    t_e2e0 = time.perf_counter()
+    if "spread" in wl:
+        pops = [P.spread_population(prob.n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
+        h2d_init = sum(k.nbytes + r.nbytes + i.nbytes for k, r, i in pops)
+        sim.set_populations(pops)
+        sim.set_clock(0, wl["t_start"])
+    else:
+        h2d_init = len(wl["rho0"]) * 32
+        sim.init_populations(wl["rho0"])
+    run_range(sim, pl, 0, W)
+    torch.cuda.synchronize()
+    sim.counters(reset=True)
+    nkeys_start = int(sim.observables()[:, 0].sum())
+
+    ck_path = None
+    if not args.no_profile:
+        ck_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                               f".bench_ck_{rank}.bin")
+        sim.checkpoint(ck_path)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.perf_counter()
+    ev0.record(stream)
+    run_range(sim, pl, W, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    c = sim.counters(reset=True)
+    # D2H read of the per-vector observables of the final state (the result)
+    obs = sim.observables()
+    t_e2e1 = time.perf_counter()
+    walkers = c["walker_steps"]
+    if dist is not None:
+        tt = torch.tensor([ms, float(walkers), t_e2e1 - t_e2e0], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm_ = tt.clone()
+        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+        ms_all, walkers_all, e2e_s = mx[0].item(), sm_[1].item(), mx[2].item()
+    else:
+        ms_all, walkers_all, e2e_s = ms, float(walkers), t_e2e1 - t_e2e0
+
+    # per-kernel times over the same timed steps (replayed from the checkpoint)
+    roof = None
+    kernel_ms = {}
+    if ck_path is not None:
+        sim.restore(ck_path)
+        sim.counters(reset=True)
+        idx = 0
+        for t0, d, n in pl:
+            lo, hi = idx, idx + n
+            idx = hi
+            a, b = max(lo, W), min(hi, W + K)
+            if a >= b:
+                continue
+            if a == lo:
+                step, _, tp, dl, pv = sim.clock()
+                sim.set_clock(step, t0, tp, dl, pv)
+            for name, v in sim.step_profile(d, b - a).items():
+                kernel_ms[name] = kernel_ms.get(name, 0.0) + v
+        cp = sim.counters(reset=True)
+        cp["passes"] = (2 * prob.n + 7) // 8 + (math.ceil(math.log2(wl["nseg"])) + 7) // 8
+        try:
+            os.remove(ck_path)
+        except OSError:
+            pass
+        peak, peak_kind = load_peaks()
+        top = max(kernel_ms, key=kernel_ms.get)
+        launches = cp["steps"] * (cp["passes"] if top == "k_sort_scatter" else 1)
+        avg_ms = kernel_ms[top] / max(1, launches)
+        bytes_per_launch = kernel_bytes(top, cp) / max(1, launches)
+        achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+        roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "avg_launch_ms": round(avg_ms, 5),
+                "algorithmic_bytes_per_launch": round(bytes_per_launch),
+                "kernel_share": {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, pl, W, budget_s=args.cpu_budget)
+
+    if rank != 0:
+        return
+    value = walkers_all / (ms_all * 1e-3)
+    npasses = (2 * prob.n + 7) // 8 + (math.ceil(math.log2(wl["nseg"])) + 7) // 8
+    ws = 3 * c["k_next"] / max(1, c["steps"]) * 16 * (world if world > 1 else 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_all / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl["name"], "description": wl["desc"], "n_qubits": prob.n,
+                   "vectors_per_gpu": wl["nseg"], "n_diag": wl["n_diag"], "dt": wl["dt"],
+                   "integrator": "AB2", "timed_steps_of_job": f"{W}..{W + K} of {total}",
+                   "records_per_step_avg": c["k_next"] / max(1, c["steps"]),
+                   "spawns_per_step_avg": c["spawns"] / max(1, c["steps"]),
+                   "key_steps_per_s": c["k_next"] * world / (ms_all * 1e-3),
+                   "l2": ("inputs larger than L2" if ws > L2_BYTES else
+                          "working set below L2 (no flush between steps)"),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": walkers_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_init / max(1, W + K),
+                "d2h_bytes_per_step": obs.nbytes / max(1, K)},
+        "gpu_launches": int(c["steps"] * (9 + npasses)),
+        "clocks": clocks,
+    }
+    if roof is not None:
+        line["roofline"] = roof
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def cpu_baseline(wl, pl, start_step: int, budget_s: float = 15.0):
+    """The oracle as it stands, single-threaded, on one vector of the same
+    workload: the first steps from the initial state until the budget is used."""
+    from oracle import oracle as O
+    prob = wl["prob"]
+    sim = O.OracleSim(prob, 1, 1000, integrator=O.AB2, n_diag=wl["n_diag"])
+    if "spread" in wl:
+        k, r, i = P.spread_population(prob.n, min(wl["spread"], 200000), 0)
+        sim.set_population(0, k, r, i)
+        sim.set_clock(0, wl["t_start"])
+    else:
+        sim.init(wl["rho0"])
+    t0 = time.perf_counter()
+    walkers = 0
+    steps = 0
+    idx = 0
+    for tp0, d, n in pl:
+        for j in range(n):
+            if j == 0:
+                stp, _, tpp, dl, pv = sim.clock()
+                sim.set_clock(stp, tp0, tpp, dl, pv)
+            rc = sim.step(d, 1)
+            if rc != 0:
+                raise RuntimeError(f"oracle step failed {rc}")
+            walkers += int(sim.stats(0)[1])
+            steps += 1
+            idx += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    sample = f"1 vector of {wl['name']}"
+    if "spread" in wl:
+        sample += f" ({min(wl['spread'], 200000)} states)"
+    return {"value": walkers / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, first {steps} steps, {el:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    pl = step_list(wl)
+    total = planner.total_steps(pl)
+    W = args.warmup
+    K = args.steps if args.steps > 0 else total - W
+    per_step_budget = max(0.5, min(20.0, 120.0 / max(1, K + W)))
+    res = cpu_baseline(wl, pl, 0, budget_s=per_step_budget * (K + W))
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": wl["name"], "description": wl["desc"]},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0 = rest of the job)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dd12")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * qmc.h -- C ABI of the GB300 (sm_103a) library for one step of real-time
+ * population-dynamics quantum Monte Carlo for noisy circuits
+ * (Shen & Lidar, arXiv:2502.18929).
+ *
+ * The library evolves many independent, signed-integer, sparse population
+ * vectors N(t) over the vectorised density matrix |rho>> [walker averaging,
+ * Eq. (3)] under the Liouvillian L(t) of the time-local master equation
+ * [Eq. (1), Eq. (2)].  One step = spawning over L's Hamiltonian and Lindblad
+ * terms (diagonal "death" included) [End Matter, spawn step], annihilation of
+ * opposite signs on equal states [End Matter, annihilation step], the
+ * initiator rule [End Matter, simulation methodology] and the per-vector
+ * observables N^diag, N_tot, K [End Matter, sign-problem suppression].
+ *
+ * Conventions (all entry points):
+ *   - Every call returns QMC_OK (0) or a negative QMC_ERR_* code;
+ *     qmc_last_error() gives a one-line reason.  Calls are not thread-safe on
+ *     one context.
+ *   - Pointers marked "host" are caller-owned host memory, borrowed for the
+ *     duration of the call only.  Pointers marked "device" are device memory
+ *     on the context's GPU.  The library owns all memory it allocates.
+ *   - Keys: qubit q is bit q of a basis index; rho_xy lives at the packed key
+ *     (x << n) | y, n = number of qubits (1 <= n <= 32).
+ *   - Pauli strings are bit-mask pairs (xm, zm): I (0,0), X (1,0), Z (0,1),
+ *     Hermitian Y (1,1) per qubit.
+ *   - Work is issued on the stream given in qmc_config.cuda_stream (0 = the
+ *     legacy default stream).  Entry points that return data to the host
+ *     synchronise that stream.
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define QMC_OK 0
+#define QMC_ERR_INVALID_ARG (-1)    /* bad argument or inconsistent sizes       */
+#define QMC_ERR_OOM (-2)            /* device or host allocation failed        */
+#define QMC_ERR_CAPACITY (-3)       /* buffers full; grown and retried inside  */
+                                    /* qmc_step, surfaced only past max_records */
+#define QMC_ERR_DT_TOO_LARGE (-4)   /* a spawn probability p >= 1               */
+#define QMC_ERR_POP_OVERFLOW (-5)   /* |re| or |im| of a state exceeds 2^31-1   */
+#define QMC_ERR_DEVICE_TIMEOUT (-6) /* a bounded device wait expired            */
+#define QMC_ERR_CUDA (-7)           /* a CUDA runtime call failed               */
+#define QMC_ERR_STATE (-8)          /* call out of order (e.g. step before init)*/
+#define QMC_ERR_COEF_RANGE (-9)     /* |coefficient * rate * dt| >= 2^10        */
+#define QMC_ERR_IO (-10)            /* checkpoint file could not be read/written*/
+#define QMC_ERR_CHECKPOINT (-11)    /* checkpoint corrupt or from another setup */
+
+#define QMC_EULER 0
+#define QMC_AB2 1
+
+#define QMC_RATE_CONST 0 /* rate(t) = a                      */
+#define QMC_RATE_COS 1   /* rate(t) = a * cos(b * t + c)     */
+
+typedef struct qmc_ctx qmc_ctx;
+
+/* Run configuration.  n_segments independent population vectors ("samples",
+ * Eq. (3)) share one problem; each draws its own counter-based random stream
+ * keyed by (seed, step, segment, key, walker). */
+typedef struct {
+    int32_t n_qubits;      /* 1..32                                              */
+    int32_t n_segments;    /* number of independent vectors, >= 1                */
+    int32_t integrator;    /* QMC_EULER or QMC_AB2 (AB2 starts with one Euler)   */
+    int32_t reserved0;
+    uint64_t seed;
+    int64_t n_diag;        /* N^diag: walkers on the diagonal of N(0) = N^diag rho(0) */
+    int64_t initiator_min; /* initiator threshold ceil(xi N^diag) in walkers; 0 = off */
+    int64_t capacity_hint; /* initial records per population buffer (0 = auto)   */
+    int64_t max_records;   /* hard cap for automatic growth (0 = no cap)         */
+    void* cuda_stream;     /* cudaStream_t to issue work on                     */
+} qmc_config;
+
+/* One term h * rate(t) * window(t) * P of H(t) [Eq. (1)]. */
+typedef struct {
+    double h;
+    uint64_t xm, zm;
+    int32_t rate_id;   /* index into the rate table                           */
+    int32_t window_id; /* index into the window table, -1 = always on         */
+} qmc_ham_term;
+
+/* One Pauli component l_a * P_a of a Lindblad operator L_k = sum_a l_a P_a. */
+typedef struct {
+    double re, im;
+    uint64_t xm, zm;
+} qmc_pauli_coef;
+
+/* A Lindblad operator with rate gamma_k(t) [Eq. (1)]; gamma may be negative
+ * (non-Markovian).  Its components are coefs[first .. first + count). */
+typedef struct {
+    int32_t first, count;
+    int32_t rate_id, window_id;
+} qmc_lindblad;
+
+typedef struct { int32_t kind; int32_t pad; double a, b, c; } qmc_rate;
+typedef struct { double t0, t1; } qmc_window; /* active on [t0, t1) */
+
+/* Per-vector observables, exact integer sums over N(t).
+ * N^diag = n_diag_re + i n_diag_im; theta = atan2(im, re) [sign-problem
+ * suppression]; Tr rho_j = n_diag_re / N^diag [replica aggregation]. */
+typedef struct {
+    int64_t n_records; /* K: occupied states, dim(H_QMC) of this vector        */
+    int64_t n_walkers; /* N_tot = sum |re| + |im|                               */
+    int64_t n_diag_re;
+    int64_t n_diag_im;
+} qmc_obs;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  *out is set only on success.
+ * Errors: INVALID_ARG (n_qubits outside 1..32, n_segments < 1, n_diag < 1),
+ * OOM, CUDA. */
+int qmc_create(qmc_ctx** out, const qmc_config* cfg);
+
+/* Free all device and host memory of the context (NULL is a no-op). */
+void qmc_destroy(qmc_ctx* ctx);
+
+/* One-line description of the last error on this context (never NULL). */
+const char* qmc_last_error(const qmc_ctx* ctx);
+
+/* ---- problem ------------------------------------------------------------ */
+
+/* Load H(t) and the Lindblad operators [Eq. (1)].  The library expands
+ * -i[H, rho] and gamma (L rho L^dag - 1/2 {L^dag L, rho}) into Pauli
+ * superoperator terms and, per step, into the column tables of Eq. (2).
+ * All arrays are host, copied.  Errors: INVALID_ARG (ids out of range, masks
+ * beyond n qubits). */
+int qmc_load_schedule(qmc_ctx* ctx,
+                      const qmc_ham_term* ham, int32_t n_ham,
+                      const qmc_lindblad* lind, int32_t n_lind,
+                      const qmc_pauli_coef* coefs, int32_t n_coefs,
+                      const qmc_rate* rates, int32_t n_rates,
+                      const qmc_window* windows, int32_t n_windows);
+
+/* N(0) := N^diag rho(0) for every vector [walker averaging, Eq. (3)]: each
+ * entry rho_xy = re + i im (host arrays of length nnz, (x, y) distinct) is
+ * scaled by N^diag and each component stochastically rounded (exact in the
+ * mean).  Resets the clock to t = 0, step 0, no previous population.
+ * Errors: INVALID_ARG (duplicate keys, x or y >= 2^n), POP_OVERFLOW, STATE
+ * (no schedule loaded). */
+int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y,
+                         const double* re, const double* im, int64_t nnz);
+
+/* Replace the population of every vector (which = 0: N(t), 1: N(t - dt)) with
+ * host records (keys ascending within each vector; values nonzero).
+ * counts[s] records for vector s, laid out back to back.  Used to start from
+ * a given state.  Errors: INVALID_ARG (unsorted/duplicate keys), CAPACITY. */
+int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts,
+                        const uint64_t* keys, const int32_t* re, const int32_t* im);
+
+/* Set the clock: global step index (keys the random stream), t of N(t), and,
+ * for AB2, the time and step size of the previous step.  prev_valid = 0 makes
+ * the next step Euler. */
+int qmc_set_clock(qmc_ctx* ctx, uint64_t step, double t, double t_prev, double dt_last,
+                  int32_t prev_valid);
+int qmc_get_clock(const qmc_ctx* ctx, uint64_t* step, double* t, double* t_prev,
+                  double* dt_last, int32_t* prev_valid);
+
+/* ---- the hot path --------------------------------------------------------- */
+
+/* Advance every vector by nsteps steps of size dt.  Step i of the call uses
+ * L(t0 + i dt), t0 = the clock at entry; AB2 steps also spawn from N(t - dt)
+ * with L at the previous step's time [End Matter, simulation methodology].
+ * Issued asynchronously on the context stream (captured once in a CUDA graph
+ * and replayed); returns after checking the device status word.  On
+ * CAPACITY the buffers grow and the failed step is redone (the result is
+ * bit-identical: every draw is keyed by step, vector, key and walker).
+ * Errors: STATE, DT_TOO_LARGE, POP_OVERFLOW, CAPACITY (past max_records),
+ * DEVICE_TIMEOUT, CUDA.  After an error the state is that of the last
+ * completed step. */
+int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps);
+
+/* Take nsteps steps like qmc_step (dt, nsteps >= 1), and time each kernel of
+ * every step with CUDA events on the context's stream: each step is taken
+ * once, then replayed kernel by kernel with events between the launches (the
+ * replay reproduces the step exactly; a mismatch returns STATE).  Adds the
+ * per-kernel milliseconds, summed over the steps, to host kernel_ms[0 .. cap)
+ * (zeroed first) and sets *n_kernels; qmc_kernel_name(i) names kernel i.
+ * For measurement; slower than qmc_step (one synchronisation per step). */
+int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap,
+                     int32_t* n_kernels);
+const char* qmc_kernel_name(int32_t i);
+
+/* Upper bound of the spawn probability p over all states for a step of size
+ * dt at time t (AB2 factor 3/2 included): sum over the expanded terms of
+ * |Re c| + |Im c| times |rate| times dt.  Host-only; used to choose dt. */
+int qmc_spawn_prob_bound(const qmc_ctx* ctx, double t, double dt, double* p_bound);
+
+/* ---- results --------------------------------------------------------------- */
+
+/* Per-vector observables of N(t) into obs[0 .. n_segments) (host).
+ * Synchronises the stream. */
+int qmc_observables(qmc_ctx* ctx, qmc_obs* obs);
+
+/* Per-step observables of the last qmc_step call: host array of
+ * nsteps * n_segments entries, step-major.  *count receives the number of
+ * steps recorded (<= cap_steps). */
+int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* count);
+
+/* Cumulative totals since the last reset, all vectors (host out[8]):
+ * out[0] steps, [1] walker-steps (sum over steps of N_tot of N(t + dt)),
+ * [2] records read from N(t), [3] records read from N(t - dt) (AB2 steps),
+ * [4] spawn records, [5] records written to N(t + dt), [6] heavy work items,
+ * [7] reserved (0).  reset != 0 zeroes them after reading.  Synchronises. */
+int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out);
+
+/* Copy the records of vector seg (which = 0: N(t), 1: N(t - dt)) to host
+ * arrays of capacity cap; *count receives the number of records (if it
+ * exceeds cap nothing is copied and INVALID_ARG is returned). */
+int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t* re,
+               int32_t* im, int64_t cap, int64_t* count);
+
+/* Sum over the target support of conj(psi_x) psi_y N_xy for vector seg, as
+ * exact integers accumulated in FP64 on the host (fidelity F = |value| /
+ * N^diag for a normalised psi) [Markovian circuit dynamics].  psi given as
+ * host arrays idx[len], (re, im)[len]. */
+int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* psi_re,
+                const double* psi_im, int32_t len, double* out_re, double* out_im);
+
+/* ---- checkpoint / resume ------------------------------------------------- */
+
+/* Write (clock, seed, configuration hash, N(t), N(t - dt)) to path; restore
+ * reads it back into a context created with the same configuration and
+ * schedule.  A resumed run is bit-identical to an uninterrupted one.
+ * Errors: IO, CHECKPOINT (bad magic, checksum or configuration hash). */
+int qmc_checkpoint(qmc_ctx* ctx, const char* path);
+int qmc_restore(qmc_ctx* ctx, const char* path);
+
+/* ---- host-only utility -------------------------------------------------- */
+
+/* Compile the column of dt_eff * L(t) [Eq. (2)] exactly as qmc_step does and
+ * evaluate it at the source state |x><y| on the host (no GPU needed): writes up
+ * to cap destinations in the canonical (ascending mask) order -- mask =
+ * (dx << n) | dy, value (vre + i vim) in units of 2^-52 -- and the spawn
+ * weight P = 2^52 dt_eff sum (|Re L| + |Im L|) to *p_out [End Matter, spawn
+ * step].  Schedule arrays as in qmc_load_schedule (host, borrowed).  Returns
+ * the number of destinations, or INVALID_ARG / COEF_RANGE. */
+int qmc_column_eval(int32_t n_qubits, const qmc_ham_term* ham, int32_t n_ham, const qmc_lindblad* lind,
+                    int32_t n_lind, const qmc_pauli_coef* coefs, int32_t n_coefs, const qmc_rate* rates,
+                    int32_t n_rates, const qmc_window* windows, int32_t n_windows, double t, double dt_eff,
+                    uint64_t x, uint64_t y, int32_t cap, uint64_t* mask, int64_t* vre, int64_t* vim,
+                    int64_t* p_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMC_H */

@@ -61,6 +61,8 @@ def lib():
         L.orc_set_clock.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_double, C.c_double,
                                     C.c_int]
         L.orc_get_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_set_active.restype = C.c_int
+        L.orc_set_active.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
         L.orc_count.restype = C.c_int64
@@ -157,6 +159,12 @@ class OracleSim:
     def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
                   prev_valid: bool = False):
         lib().orc_set_clock(self.handle, step, t, t_prev, dt_last, int(prev_valid))
+
+    def set_active(self, segs):
+        """Step only the listed vectors (the others keep their populations)."""
+        segs = set(segs)
+        for s in range(self.nseg):
+            lib().orc_set_active(self.handle, s, 1 if s in segs else 0)
 
     def clock(self):
         step = np.zeros(1, dtype=np.uint64)

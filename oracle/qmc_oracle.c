@@ -358,6 +358,7 @@ typedef struct {
     int integrator;       /* 0 = Euler, 1 = AB2 */
     int64_t init_min;     /* initiator threshold in walkers (ceil(xi N^diag)); 0 = off */
     int64_t n_diag;
+    unsigned char* active; /* segments stepped by orc_step (all by default) */
     pop* cur;
     pop* prev;
     uint64_t step;        /* global step index */
@@ -408,6 +409,8 @@ void* orc_state_new(const void* prob, int nseg, uint64_t seed, int integrator, i
     s->n_diag = n_diag;
     s->cur = (pop*)calloc((size_t)nseg, sizeof(pop));
     s->prev = (pop*)calloc((size_t)nseg, sizeof(pop));
+    s->active = (unsigned char*)malloc((size_t)nseg);
+    memset(s->active, 1, (size_t)nseg);
     return s;
 }
 
@@ -416,7 +419,7 @@ void orc_state_free(void* sp)
     state* s = (state*)sp;
     if (!s) return;
     for (int i = 0; i < s->nseg; ++i) { free(s->cur[i].r); free(s->prev[i].r); }
-    free(s->cur); free(s->prev);
+    free(s->cur); free(s->prev); free(s->active);
     free(s);
 }
 
@@ -497,6 +500,16 @@ int orc_set_population(void* sp, int seg, int which, int64_t cnt, const uint64_t
     qsort(p->r, (size_t)p->len, sizeof(rec), rec_cmp);
     for (int64_t i = 1; i < p->len; ++i)
         if (p->r[i].key == p->r[i - 1].key) return ORC_ERR_INVALID_ARG;
+    return ORC_OK;
+}
+
+/* Restrict orc_step to a subset of the vectors (each vector is independent,
+ * so a subset evolves exactly as in the full run). */
+int orc_set_active(void* sp, int seg, int on)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    s->active[seg] = on ? 1 : 0;
     return ORC_OK;
 }
 
@@ -644,6 +657,7 @@ int orc_step(void* sp, double dt, int nsteps)
         double dt_cur = ab2 ? dt * 1.5 : dt;
         double dt_prev = dt * 0.5;
         for (int seg = 0; seg < s->nseg && rc == ORC_OK; ++seg) {
+            if (!s->active[seg]) continue;
             uint32_t kd[2];
             derive_key(s->seed, s->step, (uint32_t)seg, TAG_STEP, kd);
             spl.len = 0;

@@ -1,0 +1,41 @@
+// Host evaluation of the compiled column program: the same program and the
+// same evaluator (column_eval.h) the kernels use, callable without a GPU.
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "column_eval.h"
+#include "term_compiler.h"
+
+using namespace qmc;
+
+extern "C" int qmc_column_eval(int32_t n_qubits, const qmc_ham_term* ham, int32_t n_ham, const qmc_lindblad* lind,
+                               int32_t n_lind, const qmc_pauli_coef* coefs, int32_t n_coefs, const qmc_rate* rates,
+                               int32_t n_rates, const qmc_window* windows, int32_t n_windows, double t, double dt_eff,
+                               uint64_t x, uint64_t y, int32_t cap, uint64_t* mask, int64_t* vre, int64_t* vim,
+                               int64_t* p_out)
+{
+    if (n_qubits < 1 || n_qubits > 32 || !p_out) return QMC_ERR_INVALID_ARG;
+    Schedule s;
+    s.n = n_qubits;
+    if (n_ham > 0) s.ham.assign(ham, ham + n_ham);
+    if (n_lind > 0) s.lind.assign(lind, lind + n_lind);
+    if (n_coefs > 0) s.coefs.assign(coefs, coefs + n_coefs);
+    if (n_rates > 0) s.rates.assign(rates, rates + n_rates);
+    if (n_windows > 0) s.windows.assign(windows, windows + n_windows);
+    if (validate_schedule(s, nullptr) != QMC_OK) return QMC_ERR_INVALID_ARG;
+    std::vector<uint8_t> blob;
+    int rc = build_program(s, t, dt_eff, &blob);
+    if (rc != QMC_OK) return rc;
+    const Prog p = prog_at(blob.data());
+    int64_t sre, sim;
+    *p_out = column_weight(p, (uint32_t)x, (uint32_t)y, &sre, &sim);
+    const int ne = p.h->n_entry;
+    for (int e = 0; e < ne && e < cap; ++e) {
+        int64_t a, b;
+        entry_value(p, p.ent[e], (uint32_t)x, (uint32_t)y, sre, sim, &a, &b);
+        mask[e] = p.ent[e].mask_key;
+        vre[e] = a;
+        vim[e] = b;
+    }
+    return ne;
+}

@@ -1,0 +1,125 @@
+// Evaluation of a compiled column program (qmc_types.h) at a source state
+// |x><y|: the diagonal element and the weight P = 2^52 dt_eff sum over
+// destinations of (|Re L| + |Im L|) [End Matter, spawn step], and the value of
+// any destination.  Shared by the kernels and the host-side program check.
+#pragma once
+#include <stdint.h>
+
+#include "qmc_types.h"
+
+#ifdef __CUDACC__
+#define QMC_HD __host__ __device__
+#else
+#define QMC_HD
+#endif
+
+namespace qmc {
+
+QMC_HD inline int qmc_popc(uint32_t v)
+{
+#ifdef __CUDA_ARCH__
+    return __popc(v);
+#else
+    return __builtin_popcount(v);
+#endif
+}
+
+QMC_HD inline int64_t qmc_iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+// ---------------------------------------------------------------------------
+// Column program access
+// ---------------------------------------------------------------------------
+struct Prog {
+    const ProgHeader* h;
+    const SelfFam* sf;
+    const SelfGen* sg;
+    const Fam* fam;
+    const Gen* gen;
+    const GTerm* gt;
+    const Entry* ent;
+};
+
+QMC_HD inline Prog prog_at(const uint8_t* base)
+{
+    Prog p;
+    p.h = (const ProgHeader*)base;
+    p.sf = (const SelfFam*)(base + p.h->off_selffam);
+    p.sg = (const SelfGen*)(base + p.h->off_selfgen);
+    p.fam = (const Fam*)(base + p.h->off_fam);
+    p.gen = (const Gen*)(base + p.h->off_gen);
+    p.gt = (const GTerm*)(base + p.h->off_gterm);
+    p.ent = (const Entry*)(base + p.h->off_entry);
+    return p;
+}
+
+QMC_HD inline void gen_value(const Prog& p, int g, uint32_t x, uint32_t y,
+                                          int64_t* vr, int64_t* vi)
+{
+    const Gen& G = p.gen[g];
+    if (G.is_const) { *vr = G.cre; *vi = G.cim; return; }
+    int64_t er = 0, ei = 0;
+    for (int j = 0; j < G.count; ++j) {
+        const GTerm& t = p.gt[G.first + j];
+        const int par = (qmc_popc(x & t.zl) + qmc_popc(y & t.zr)) & 1;
+        er += par ? -t.qre : t.qre;
+        ei += par ? -t.qim : t.qim;
+    }
+    *vr = er;
+    *vi = ei;
+}
+
+// Diagonal element (sre, sim) and P = 2^52 dt_eff sum_kl (|Re L| + |Im L|).
+QMC_HD inline int64_t column_weight(const Prog& p, uint32_t x, uint32_t y,
+                                                 int64_t* sre_out, int64_t* sim_out)
+{
+    const ProgHeader& h = *p.h;
+    int64_t sre = h.self_const_re, sim = h.self_const_im;
+    for (int i = 0; i < h.n_selffam; ++i) {
+        const SelfFam f = p.sf[i];
+        const uint32_t pat = f.type == 0 ? x : (f.type == 1 ? y : (x ^ y));
+        const int c = qmc_popc(f.members) - 2 * qmc_popc(pat & f.members);
+        sre += f.qre * c;
+        sim += f.qim * c;
+    }
+    for (int i = 0; i < h.n_selfgen; ++i) {
+        const SelfGen g = p.sg[i];
+        const int par = (qmc_popc(x & g.zl) + qmc_popc(y & g.zr)) & 1;
+        sre += par ? -g.qre : g.qre;
+        sim += par ? -g.qim : g.qim;
+    }
+    int64_t P = qmc_iabs64(sre) + qmc_iabs64(sim) + h.p_const;
+    for (int i = 0; i < h.n_fam; ++i) {
+        const Fam& f = p.fam[i];
+        const uint32_t M = f.members;
+        const int c3 = qmc_popc(M & x & y), c2 = qmc_popc(M & x & ~y), c1 = qmc_popc(M & ~x & y);
+        const int c0 = qmc_popc(M) - c1 - c2 - c3;
+        P += f.a[0] * c0 + f.a[1] * c1 + f.a[2] * c2 + f.a[3] * c3;
+    }
+    for (int g = 0; g < h.n_nonconst_gen; ++g) {
+        int64_t vr, vi;
+        gen_value(p, g, x, y, &vr, &vi);
+        P += qmc_iabs64(vr) + qmc_iabs64(vi);
+    }
+    *sre_out = sre;
+    *sim_out = sim;
+    return P;
+}
+
+QMC_HD inline void entry_value(const Prog& p, const Entry& e, uint32_t x, uint32_t y,
+                                            int64_t sre, int64_t sim, int64_t* vr, int64_t* vi)
+{
+    if (e.kind == 0) {
+        *vr = sre;
+        *vi = sim;
+    } else if (e.kind == 1) {
+        const Fam& f = p.fam[e.idx & 0xFFFFu];
+        const int q = (int)(e.idx >> 16);
+        const int pi = (int)((((x >> q) & 1u) << 1) | ((y >> q) & 1u));
+        *vr = f.tre[pi];
+        *vi = f.tim[pi];
+    } else {
+        gen_value(p, (int)e.idx, x, y, vr, vi);
+    }
+}
+
+} // namespace qmc

@@ -1,0 +1,71 @@
+// Library-internal definition of the opaque qmc_ctx (include/qmc.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/qmc.h"
+#include "kernels.h"
+#include "qmc_types.h"
+#include "term_compiler.h"
+
+using qmc::DevState;
+using qmc::HeavyItem;
+using qmc::Rec;
+using qmc::Schedule;
+using qmc::SegStats;
+using qmc::SRec;
+using qmc::StepInfo;
+
+struct qmc_ctx {
+    qmc_config cfg{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    int grid = 0;
+
+    Schedule sched;
+    bool has_sched = false;
+    bool has_pop = false;
+
+    DevState* d_state = nullptr;
+    Rec* d_pop[3] = {nullptr, nullptr, nullptr};
+    int64_t* d_segoff[3] = {nullptr, nullptr, nullptr};
+    int64_t pop_cap = 0;
+    SRec* d_spawn = nullptr;
+    SRec* d_spawn_alt = nullptr;
+    int64_t spawn_cap = 0;
+    HeavyItem* d_heavy = nullptr;
+    int64_t heavy_cap = 0;
+    uint2* d_kd = nullptr;
+    unsigned int* d_sort_hist = nullptr;
+    unsigned long long* d_sort_status = nullptr;
+    int64_t sort_tiles_cap = 0;
+    int64_t* d_bseg = nullptr;
+    int64_t* d_tile_start = nullptr;
+    int64_t* d_part = nullptr;
+    unsigned long long* d_merge_status = nullptr;
+    int64_t merge_tiles_cap = 0;
+    SegStats* d_segacc = nullptr;
+    SegStats* d_history = nullptr;
+    int64_t history_cap = 0;
+    StepInfo* d_info = nullptr;
+    int64_t info_cap = 0;
+    uint8_t* d_progs = nullptr;
+    int64_t progs_cap = 0;
+    SegStats* d_obs = nullptr;
+
+    // host mirror of the clock
+    uint64_t step = 0;
+    double t = 0.0, t_prev = 0.0, dt_last = 0.0;
+    bool prev_valid = false;
+    int64_t last_call_steps = 0;
+
+    cudaGraphExec_t graph = nullptr;
+    bool graph_dirty = true;
+
+    std::string err;
+};

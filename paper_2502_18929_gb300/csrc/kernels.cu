@@ -1,0 +1,1161 @@
+// One step of real-time population-dynamics QMC on sm_103a (arXiv:2502.18929).
+//
+//   k_prologue      per-step Philox keys, counter resets
+//   k_spawn_light   spawning [End Matter, spawn step] for parents with few walkers
+//   k_spawn_heavy   the same for heavy parents, one CTA per walker chunk,
+//                   aggregated per destination in shared memory
+//   k_sort_hist     digit histograms of all LSD radix passes
+//   k_sort_scatter  one stable LSD pass, decoupled look-back, smem exchange
+//   k_spawn_segoff  segment boundaries of the sorted spawns
+//   k_merge_plan    merge tiles per segment
+//   k_merge_part    merge-path partition of every tile
+//   k_merge         annihilation [End Matter, annihilation step] + initiator
+//                   rule + compaction + per-vector observables
+//   k_finalize      segment offsets of N(t + dt), history, rotate the slots
+//
+// Integer-only: weights are exact 2^-52 fixed point, so spawning, annihilation
+// and the observables are bit-identical to any other exact evaluation.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "column_eval.h"
+#include "kernels.h"
+
+namespace qmc {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
+constexpr int kStage = 128; // spawn records staged per warp
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+__device__ __forceinline__ void set_error(DevState* st, uint32_t code)
+{
+    atomicCAS(&st->error, 0u, code);
+}
+
+__device__ __forceinline__ uint32_t read_error(const DevState* st)
+{
+    return *(volatile const uint32_t*)&st->error;
+}
+
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p)
+{
+    return *(volatile const unsigned long long*)p;
+}
+
+__device__ __forceinline__ void st_vol(unsigned long long* p, unsigned long long v)
+{
+    *(volatile unsigned long long*)p = v;
+}
+
+__device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, uint32_t flag, uint32_t v)
+{
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (v & 0x3FFFFFFFu);
+}
+
+// Wait (bounded) until *addr carries this epoch and a flag; returns false on
+// timeout after raising DERR_TIMEOUT.
+__device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned long long* out,
+                        DevState* st)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        unsigned long long v = ld_vol(addr);
+        if ((uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u) {
+            *out = v;
+            return true;
+        }
+        if (read_error(st) == DERR_TIMEOUT) break;
+        if (it > 32) __nanosleep(64);
+    }
+    set_error(st, DERR_TIMEOUT);
+    return false;
+}
+
+// Segment of record i in a population slot: upper_bound(off[1..nseg], i).
+__device__ __forceinline__ int seg_of(const int64_t* off, int nseg, int64_t i)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&off[mid]) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The record of one spawned walker.  sign rule [End Matter, spawn step]:
+// Re channel s sgn(Re L), Im channel i s sgn(Im L); s = sgn(re) for a real
+// walker, i sgn(im) for an imaginary one; sigma = -1 for the N(t - dt) pass.
+__device__ __forceinline__ SRec make_spawn(uint64_t dest, int seg, int comp, int chan, int64_t v,
+                                           int sg, int sigma, int noninit, int32_t count)
+{
+    const int s = sigma * sg * (v > 0 ? 1 : -1);
+    int target, val;
+    if (chan == 0) { target = comp; val = s; }
+    else if (comp == 0) { target = 1; val = s; }
+    else { target = 0; val = -s; }
+    SRec r;
+    r.key = dest;
+    r.meta = ((uint32_t)seg << 2) | ((uint32_t)target << 1) | (uint32_t)noninit;
+    r.val = val * count;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Prologue: keys of this step, counter resets.
+// ---------------------------------------------------------------------------
+__global__ void k_prologue(StepParams P)
+{
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const uint64_t step = st->step;
+    for (int s = threadIdx.x; s < P.nseg; s += blockDim.x) {
+        uint4 o = philox10(make_uint4((uint32_t)step, (uint32_t)(step >> 32), (uint32_t)s, kTagStep),
+                           make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+        P.kd[s] = make_uint2(o.x, o.y);
+        P.segacc[s] = SegStats{0ull, 0ll, 0ll, 0ll};
+    }
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) P.sort_hist[i] = 0u;
+    for (int i = threadIdx.x; i < kMaxTileCounters; i += blockDim.x) st->tile_ctr[i] = 0u;
+    if (threadIdx.x == 0) {
+        st->spawn_total = 0;
+        st->heavy_total = 0;
+        st->next_total = 0;
+        st->merge_tiles = 0;
+        st->seq += 16u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spawning, light parents: one lane per parent, one Philox call per two
+// walkers.  T = R >> 12 (52 bits); the walker spawns iff T < P and then goes
+// to the (destination, channel) whose cumulative-weight interval holds T.
+// ---------------------------------------------------------------------------
+struct SpawnCtx {
+    Prog prog[2];
+    const Rec* src[2];
+    const int64_t* off[2];
+    int64_t k0, total;
+};
+
+__device__ __forceinline__ void warp_flush(SRec* stage, int n, const StepParams& P, int lane)
+{
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long*)&P.st->spawn_total, (unsigned long long)n);
+    base = __shfl_sync(kFull, base, 0);
+    if ((int64_t)base + n > P.spawn_cap) {
+        if (lane == 0) set_error(P.st, DERR_SPAWN_CAPACITY);
+    }
+    for (int j = lane; j < n; j += 32) {
+        const int64_t pos = (int64_t)base + j;
+        if (pos < P.spawn_cap) P.spawn[pos] = stage[j];
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kThreads) k_spawn_light(StepParams P)
+{
+    __shared__ SRec stage_all[kThreads / 32][kStage];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int ci = st->call_index;
+    const StepInfo inf = P.info[ci];
+    const int cur = st->cur, prv = (cur + 2) % 3;
+    const int64_t K0 = st->count[cur];
+    const int64_t K1 = inf.ab2 ? st->count[prv] : 0;
+    const int64_t total = K0 + K1;
+    const Prog prog0 = prog_at(P.progs + inf.prog_off[0]);
+    const Prog prog1 = prog_at(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]));
+    const Rec* src0 = P.pop[cur];
+    const Rec* src1 = P.pop[prv];
+    const int64_t* off0 = P.segoff[cur];
+    const int64_t* off1 = P.segoff[prv];
+    const int n = P.n;
+    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    SRec* stage = stage_all[warp];
+    int staged = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+
+    for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * 32; base < total;
+         base += nwarps * 32) {
+        const int64_t i = base + lane;
+        int phase = 0, seg = 0, my_pairs = 0, pairs_re = 0;
+        int64_t m_re = 0, m_im = 0, P_w = 0, sre = 0, sim = 0;
+        Rec par{0ull, 0, 0};
+        uint32_t x = 0, y = 0;
+        int noninit = 0;
+        uint2 kd = make_uint2(0u, 0u);
+        if (i < total) {
+            phase = i >= K0 ? 1 : 0;
+            const int64_t j = phase ? i - K0 : i;
+            par = phase ? src1[j] : src0[j];
+            seg = seg_of(phase ? off1 : off0, P.nseg, j);
+            x = (uint32_t)(par.key >> n);
+            y = (uint32_t)(par.key & ymask);
+            P_w = column_weight(phase ? prog1 : prog0, x, y, &sre, &sim);
+            if (P_w >= (1ll << 52)) {
+                set_error(st, DERR_DT_TOO_LARGE);
+                P_w = 0;
+            }
+            m_re = iabs64(par.re);
+            m_im = iabs64(par.im);
+            noninit = (P.init_min > 0 && (m_re + m_im) < P.init_min) ? 1 : 0;
+            kd = P.kd[seg];
+            if (P_w > 0) {
+                if (m_re + m_im > kHeavyWalkers) {
+                    // hand over to the heavy path in chunks of kHeavyChunk walkers
+                    for (int comp = 0; comp < 2; ++comp) {
+                        const int64_t m = comp ? m_im : m_re;
+                        const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
+                        if (chunks == 0) continue;
+                        const unsigned long long hb =
+                            atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
+                        for (int64_t c = 0; c < chunks; ++c) {
+                            const int64_t pos = (int64_t)hb + c;
+                            if (pos < P.heavy_cap) {
+                                HeavyItem it;
+                                it.parent = j;
+                                it.phase = phase;
+                                it.comp = comp;
+                                it.chunk = (int32_t)c;
+                                it.seg = seg;
+                                P.heavy[pos] = it;
+                            } else {
+                                set_error(st, DERR_HEAVY_CAPACITY);
+                            }
+                        }
+                    }
+                } else {
+                    pairs_re = (int)((m_re + 1) / 2);
+                    my_pairs = pairs_re + (int)((m_im + 1) / 2);
+                }
+            }
+        }
+        const Prog& prog = phase ? prog1 : prog0;
+        const int sigma = phase ? -1 : 1;
+        const int max_pairs = __reduce_max_sync(kFull, my_pairs);
+        for (int jp = 0; jp < max_pairs; ++jp) {
+            SRec r[2];
+            bool v[2] = {false, false};
+            if (jp < my_pairs) {
+                const int comp = jp < pairs_re ? 0 : 1;
+                const int j2 = comp ? jp - pairs_re : jp;
+                const int64_t m = comp ? m_im : m_re;
+                const int sg = (comp ? par.im : par.re) > 0 ? 1 : -1;
+                const uint4 w = philox10(
+                    make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
+                               (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
+                    kd);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (2 * (int64_t)j2 + h >= m) break;
+                    const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
+                    int64_t T = (int64_t)(R >> 12);
+                    if (T >= P_w) continue;
+                    for (int e = 0; e < prog.h->n_entry; ++e) {
+                        const Entry E = prog.ent[e];
+                        int64_t vr, vi;
+                        entry_value(prog, E, x, y, sre, sim, &vr, &vi);
+                        const int64_t wr = iabs64(vr);
+                        if (T < wr) {
+                            r[h] = make_spawn(par.key ^ E.mask_key, seg, comp, 0, vr, sg, sigma, noninit, 1);
+                            v[h] = true;
+                            break;
+                        }
+                        T -= wr;
+                        const int64_t wi = iabs64(vi);
+                        if (T < wi) {
+                            r[h] = make_spawn(par.key ^ E.mask_key, seg, comp, 1, vi, sg, sigma, noninit, 1);
+                            v[h] = true;
+                            break;
+                        }
+                        T -= wi;
+                    }
+                }
+            }
+            const uint32_t b0 = __ballot_sync(kFull, v[0]);
+            const uint32_t b1 = __ballot_sync(kFull, v[1]);
+            const int cnt = __popc(b0) + __popc(b1);
+            if (cnt == 0) continue;
+            if (staged + cnt > kStage) {
+                warp_flush(stage, staged, P, lane);
+                staged = 0;
+            }
+            if (v[0]) stage[staged + __popc(b0 & lt)] = r[0];
+            if (v[1]) stage[staged + __popc(b0) + __popc(b1 & lt)] = r[1];
+            staged += cnt;
+            __syncwarp();
+        }
+    }
+    if (staged) warp_flush(stage, staged, P, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Spawning, heavy parents: one CTA per chunk of kHeavyChunk walkers of one
+// parent component.  The column is evaluated once into shared memory as a
+// cumulative weight table; each spawned walker finds its interval by binary
+// search; counts are aggregated per (destination, channel) and emitted as one
+// record each.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
+{
+    __shared__ int64_t cum[2 * kMaxEntries];
+    __shared__ int64_t vals[2 * kMaxEntries];
+    __shared__ int hist[2 * kMaxEntries];
+    __shared__ int64_t warp_tot[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ int s_nout;
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int64_t nitems = min(st->heavy_total, P.heavy_cap);
+    if (nitems == 0) return;
+    const int ci = st->call_index;
+    const StepInfo inf = P.info[ci];
+    const int cur = st->cur, prv = (cur + 2) % 3;
+    const int n = P.n;
+    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const HeavyItem it = P.heavy[item];
+        const Prog prog = prog_at(P.progs + inf.prog_off[it.phase]);
+        const Rec par = (it.phase ? P.pop[prv] : P.pop[cur])[it.parent];
+        const uint32_t x = (uint32_t)(par.key >> n), y = (uint32_t)(par.key & ymask);
+        int64_t sre, sim;
+        const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+        const int ne = prog.h->n_entry;
+        if (ne > kMaxEntries) {
+            if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
+            return;
+        }
+        // entry values and weights
+        for (int e = tid; e < ne; e += kThreads) {
+            int64_t vr, vi;
+            entry_value(prog, prog.ent[e], x, y, sre, sim, &vr, &vi);
+            vals[2 * e] = vr;
+            vals[2 * e + 1] = vi;
+        }
+        for (int b = tid; b < 2 * ne; b += kThreads) hist[b] = 0;
+        __syncthreads();
+        // inclusive prefix of |vals| (blocked per thread, then across threads)
+        const int nb = 2 * ne;
+        const int per = (nb + kThreads - 1) / kThreads;
+        const int b0 = tid * per, b1 = min(nb, b0 + per);
+        int64_t acc = 0;
+        for (int b = b0; b < b1; ++b) acc += iabs64(vals[b]);
+        int64_t incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int64_t woff = 0;
+        for (int w = 0; w < warp; ++w) woff += warp_tot[w];
+        int64_t run = woff + incl - acc;
+        for (int b = b0; b < b1; ++b) {
+            run += iabs64(vals[b]);
+            cum[b] = run;
+        }
+        __syncthreads();
+
+        const int comp = it.comp;
+        const int64_t m = iabs64(comp ? par.im : par.re);
+        const int64_t w_lo = (int64_t)it.chunk * kHeavyChunk;
+        const int64_t w_hi = min(m, w_lo + kHeavyChunk);
+        const uint2 kd = P.kd[it.seg];
+        for (int64_t j2 = w_lo / 2 + tid; 2 * j2 < w_hi; j2 += kThreads) {
+            const uint4 w = philox10(
+                make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
+                           (uint32_t)it.phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
+                kd);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (2 * j2 + h >= w_hi) break;
+                const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
+                const int64_t T = (int64_t)(R >> 12);
+                if (T >= Pw) continue;
+                int lo = 0, hi = nb - 1; // first b with cum[b] > T
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cum[mid] > T) hi = mid; else lo = mid + 1;
+                }
+                atomicAdd(&hist[lo], 1);
+            }
+        }
+        if (tid == 0) s_nout = 0;
+        __syncthreads();
+        // emit one record per nonzero (destination, channel)
+        const int sg = (comp ? par.im : par.re) > 0 ? 1 : -1;
+        const int sigma = it.phase ? -1 : 1;
+        const int noninit = (P.init_min > 0 && (iabs64(par.re) + iabs64(par.im)) < P.init_min) ? 1 : 0;
+        int my_n = 0;
+        for (int b = tid; b < nb; b += kThreads) my_n += hist[b] ? 1 : 0;
+        int my_off = 0;
+        if (my_n) my_off = atomicAdd(&s_nout, my_n);
+        __syncthreads();
+        if (tid == 0) {
+            s_base = s_nout ? atomicAdd((unsigned long long*)&st->spawn_total, (unsigned long long)s_nout) : 0ull;
+            if ((int64_t)s_base + s_nout > P.spawn_cap) set_error(st, DERR_SPAWN_CAPACITY);
+        }
+        __syncthreads();
+        int k = 0;
+        for (int b = tid; b < nb; b += kThreads) {
+            if (!hist[b]) continue;
+            const int e = b >> 1, chan = b & 1;
+            const SRec r = make_spawn(par.key ^ prog.ent[e].mask_key, it.seg, comp, chan, vals[b], sg,
+                                      sigma, noninit, hist[b]);
+            const int64_t pos = (int64_t)s_base + my_off + k;
+            if (pos < P.spawn_cap) P.spawn[pos] = r;
+            ++k;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of spawn records by (segment, key).
+// Digits: key bits [8p, 8p + 8) for p < key_passes, then segment bits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t digit_of(const SRec& r, int pass, int key_passes)
+{
+    if (pass < key_passes) return (uint32_t)(r.key >> (8 * pass)) & 0xFFu;
+    return ((r.meta >> 2) >> (8 * (pass - key_passes))) & 0xFFu;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_hist(StepParams P)
+{
+    __shared__ unsigned int h[kMaxPasses * 256];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int64_t S = min(st->spawn_total, P.spawn_cap);
+    const int np = P.key_passes + P.seg_passes;
+    for (int i = threadIdx.x; i < np * 256; i += kThreads) h[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < S; i += (int64_t)gridDim.x * kThreads) {
+        const SRec r = P.spawn[i];
+        for (int p = 0; p < np; ++p) atomicAdd(&h[p * 256 + digit_of(r, p, P.key_passes)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * 256; i += kThreads)
+        if (h[i]) atomicAdd(&P.sort_hist[i], h[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_scatter(StepParams P, int pass, const SRec* __restrict__ src,
+                                                          SRec* __restrict__ dst)
+{
+    __shared__ SRec buf[kSortTile];
+    __shared__ unsigned int whist[kThreads / 32][256];
+    __shared__ unsigned int dbase[256];
+    __shared__ unsigned int gpre[256];
+    __shared__ unsigned int lstart[256];
+    __shared__ unsigned int s_tile;
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int64_t S = min(st->spawn_total, P.spawn_cap);
+    const int64_t ntiles = (S + kSortTile - 1) / kSortTile;
+    if (ntiles > P.sort_tiles_cap) {
+        if (threadIdx.x == 0) set_error(st, DERR_TILE_CAPACITY);
+        return;
+    }
+    const uint32_t epoch = st->seq + (uint32_t)pass;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    // exclusive scan of the global digit histogram (once per CTA)
+    {
+        const unsigned int c = P.sort_hist[pass * 256 + tid];
+        unsigned int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) whist[0][warp] = incl;
+        __syncthreads();
+        unsigned int off = 0;
+        for (int w = 0; w < warp; ++w) off += whist[0][w];
+        dbase[tid] = off + incl - c;
+        __syncthreads();
+    }
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[pass], 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        for (int d = tid; d < (kThreads / 32) * 256; d += kThreads) (&whist[0][0])[d] = 0u;
+        __syncthreads();
+        SRec rec[kSortItems];
+        uint32_t dig[kSortItems];
+        uint32_t rank[kSortItems];
+        const int64_t t0 = tile * kSortTile;
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const int64_t idx = t0 + warp * (32 * kSortItems) + it * 32 + lane;
+            if (idx < S) {
+                rec[it] = src[idx];
+                dig[it] = digit_of(rec[it], pass, P.key_passes);
+            } else {
+                dig[it] = 256u;
+            }
+        }
+        // stable warp-level ranking (warp-blocked, item-striped order = input order)
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const uint32_t d = dig[it];
+            const uint32_t peers = __match_any_sync(kFull, d);
+            uint32_t before = 0;
+            if (d < 256u) before = whist[warp][d];
+            __syncwarp();
+            if (d < 256u) {
+                rank[it] = before + __popc(peers & lt);
+                if ((peers & lt) == 0u) whist[warp][d] = before + __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: warp prefixes, tile count
+        unsigned int tot = 0;
+        {
+            const int d = tid;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const unsigned int c = whist[w][d];
+                whist[w][d] = tot;
+                tot += c;
+            }
+        }
+        // decoupled look-back for this digit across tiles
+        {
+            const int d = tid;
+            unsigned long long* my = P.sort_status + tile * 256 + d;
+            unsigned int excl = 0;
+            if (tile == 0) {
+                st_vol(my, lb_word(epoch, kFlagIncl, tot));
+            } else {
+                st_vol(my, lb_word(epoch, kFlagAgg, tot));
+                for (int64_t j = tile - 1; j >= 0; --j) {
+                    unsigned long long v;
+                    if (!lb_wait(P.sort_status + j * 256 + d, epoch, &v, st)) break;
+                    excl += (unsigned int)(v & 0x3FFFFFFFu);
+                    if (((v >> 30) & 3u) == kFlagIncl) break;
+                }
+                st_vol(my, lb_word(epoch, kFlagIncl, excl + tot));
+            }
+            gpre[d] = excl;
+        }
+        // local digit starts inside the tile
+        {
+            unsigned int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            __shared__ unsigned int wsum[kThreads / 32];
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            unsigned int off = 0;
+            for (int w = 0; w < warp; ++w) off += wsum[w];
+            lstart[tid] = off + incl - tot;
+        }
+        __syncthreads();
+        int nvalid = 0;
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            if (dig[it] < 256u) {
+                const uint32_t lpos = lstart[dig[it]] + whist[warp][dig[it]] + rank[it];
+                buf[lpos] = rec[it];
+            }
+        }
+        {
+            const int64_t rem = S - t0;
+            nvalid = (int)(rem < kSortTile ? rem : kSortTile);
+        }
+        __syncthreads();
+        for (int j = tid; j < nvalid; j += kThreads) {
+            const SRec r = buf[j];
+            const uint32_t d = digit_of(r, pass, P.key_passes);
+            const int64_t g = (int64_t)dbase[d] + gpre[d] + (j - (int)lstart[d]);
+            if (g >= 0 && g < S) dst[g] = r;   // always true unless a look-back timed out
+        }
+        __syncthreads();
+    }
+}
+
+// Offsets of each segment inside the sorted spawns (lower bounds).
+__global__ void k_spawn_segoff(StepParams P, const SRec* __restrict__ sorted)
+{
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int64_t S = min(st->spawn_total, P.spawn_cap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.nseg; s += gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = S;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int)(sorted[mid].meta >> 2) < s) lo = mid + 1; else hi = mid;
+        }
+        P.bseg[s] = lo;
+    }
+}
+
+// Merge tiles per segment (single CTA).
+__global__ void k_merge_plan(StepParams P)
+{
+    __shared__ int64_t wsum[32];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int cur = st->cur;
+    const int64_t* aoff = P.segoff[cur];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t carry = 0;
+    for (int base = 0; base < P.nseg; base += blockDim.x) {
+        const int s = base + tid;
+        int64_t t = 0;
+        if (s < P.nseg) {
+            const int64_t na = aoff[s + 1] - aoff[s];
+            const int64_t nb = P.bseg[s + 1] - P.bseg[s];
+            t = (na + nb + kMergeTile - 1) / kMergeTile;
+        }
+        int64_t incl = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        int64_t off = 0;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (s < P.nseg) P.tile_start[s] = carry + off + incl - t;
+        __syncthreads();
+        int64_t blk = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) blk += wsum[w];
+        carry += blk;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        P.tile_start[P.nseg] = carry;
+        st->merge_tiles = carry;
+        if (carry > st->max_tiles) st->max_tiles = carry;
+        if (carry > P.merge_tiles_cap) set_error(st, DERR_TILE_CAPACITY);
+    }
+}
+
+__device__ __forceinline__ int tile_seg(const int64_t* tile_start, int nseg, int64_t t)
+{
+    int lo = 0, hi = nseg - 1; // last s with tile_start[s] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Merge-path partition: for every tile, how many of its segment's N(t)
+// records precede it (ties: N(t) before spawns).
+__global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
+{
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int cur = st->cur;
+    const int64_t T = st->merge_tiles;
+    const Rec* A = P.pop[cur];
+    const int64_t* aoff = P.segoff[cur];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+        const int s = tile_seg(P.tile_start, P.nseg, t);
+        const int64_t a0 = aoff[s], na = aoff[s + 1] - a0;
+        const int64_t b0 = P.bseg[s], nb = P.bseg[s + 1] - b0;
+        const int64_t d = (t - P.tile_start[s]) * kMergeTile;
+        int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (A[a0 + mid].key <= sorted[b0 + d - mid - 1].key) lo = mid + 1; else hi = mid;
+        }
+        P.part[2 * t] = lo;
+        P.part[2 * t + 1] = d - lo;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Annihilation.  A run is all items (at most one N(t) record and any number of
+// spawn records) with one key.  Value = N(t) + initiator spawns +
+// (occupied ? non-initiator spawns : 0); zero runs are dropped.  A tile emits
+// the runs whose first item lies in it, reading past its end if its last run
+// continues (only spawn records can follow, since N(t) sorts first on ties).
+// ---------------------------------------------------------------------------
+struct MItem {
+    uint64_t key;
+    int32_t v0, v1;
+};
+
+__global__ void __launch_bounds__(kThreads) k_merge(StepParams P, const SRec* __restrict__ sorted)
+{
+    __shared__ MItem items[kMergeTile];
+    __shared__ uint8_t cls[kMergeTile];    // bit0: from N(t); bit1: target im; bit2: non-initiator
+    __shared__ int64_t s_tile;
+    __shared__ int s_wcount[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ long long s_red[3][kThreads / 32];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int cur = st->cur, nxt = (cur + 1) % 3;
+    const int64_t T = st->merge_tiles;
+    const Rec* A = P.pop[cur];
+    Rec* out = P.pop[nxt];
+    const int64_t* aoff = P.segoff[cur];
+    const uint32_t epoch = st->seq + 15u;
+    const int n = P.n;
+    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) s_tile = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
+        __syncthreads();
+        const int64_t t = s_tile;
+        if (t >= T) break;
+        const int s = tile_seg(P.tile_start, P.nseg, t);
+        const int64_t a_base = aoff[s], na_seg = aoff[s + 1] - a_base;
+        const int64_t b_base = P.bseg[s], nb_seg = P.bseg[s + 1] - b_base;
+        const int64_t ia0 = P.part[2 * t], ib0 = P.part[2 * t + 1];
+        int64_t ia1 = na_seg, ib1 = nb_seg;
+        if (t + 1 < P.tile_start[s + 1]) {
+            ia1 = P.part[2 * t + 2];
+            ib1 = P.part[2 * t + 3];
+        }
+        const int na = (int)(ia1 - ia0), nb = (int)(ib1 - ib0), nt = na + nb;
+        // stage A part then B part
+        for (int j = tid; j < na; j += kThreads) {
+            const Rec r = A[a_base + ia0 + j];
+            items[j] = MItem{r.key, r.re, r.im};
+            cls[j] = 1u;
+        }
+        for (int j = tid; j < nb; j += kThreads) {
+            const SRec r = sorted[b_base + ib0 + j];
+            items[na + j] = MItem{r.key, r.val, 0};
+            cls[na + j] = (uint8_t)(((r.meta >> 1) & 1u) << 1 | (r.meta & 1u) << 2);
+        }
+        // key of the merged item just before this tile (same segment)
+        bool has_prev = false;
+        uint64_t prev_key = 0;
+        if (ia0 > 0 || ib0 > 0) {
+            has_prev = true;
+            if (ia0 > 0 && ib0 > 0) {
+                const uint64_t ka = A[a_base + ia0 - 1].key, kb = sorted[b_base + ib0 - 1].key;
+                prev_key = ka > kb ? ka : kb;
+            } else if (ia0 > 0) {
+                prev_key = A[a_base + ia0 - 1].key;
+            } else {
+                prev_key = sorted[b_base + ib0 - 1].key;
+            }
+        }
+        __syncthreads();
+        // per-thread merge of kMergeItems items (merge path in shared memory)
+        MItem mi[kMergeItems];
+        uint8_t mc[kMergeItems];
+        const int d0 = tid * kMergeItems;
+        int cnt = 0;
+        if (d0 < nt) {
+            int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (items[mid].key <= items[na + d0 - mid - 1].key) lo = mid + 1; else hi = mid;
+            }
+            int ia = lo, ib = d0 - lo;
+            cnt = min(kMergeItems, nt - d0);
+            for (int k = 0; k < kMergeItems; ++k) {
+                if (k >= cnt) break;
+                bool takeA;
+                if (ia >= na) takeA = false;
+                else if (ib >= nb) takeA = true;
+                else takeA = items[ia].key <= items[na + ib].key;
+                const int src = takeA ? ia++ : na + ib++;
+                mi[k] = items[src];
+                mc[k] = cls[src];
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            items[d0 + k] = mi[k];
+            cls[d0 + k] = mc[k];
+        }
+        __syncthreads();
+        // runs whose head lies in this tile; each handled by the head's thread
+        Rec outrec[kMergeItems];
+        int nout = 0;
+        long long my_ntot = 0, my_dre = 0, my_dim = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const int pos = d0 + k;
+            const uint64_t key = items[pos].key;
+            const bool head = pos == 0 ? !(has_prev && prev_key == key) : items[pos - 1].key != key;
+            if (!head) continue;
+            long long sre = 0, sim = 0, nre = 0, nim = 0;
+            bool occupied = false;
+            int q = pos;
+            for (; q < nt && items[q].key == key; ++q) {
+                const uint8_t c = cls[q];
+                if (c & 1u) {
+                    occupied = true;
+                    sre += items[q].v0;
+                    sim += items[q].v1;
+                } else {
+                    long long* dst_re = (c & 4u) ? &nre : &sre;
+                    long long* dst_im = (c & 4u) ? &nim : &sim;
+                    if (c & 2u) *dst_im += items[q].v0; else *dst_re += items[q].v0;
+                }
+            }
+            if (q == nt) {
+                // the run may continue in later tiles: only spawn records follow
+                for (int64_t jb = ib1; jb < nb_seg; ++jb) {
+                    const SRec r = sorted[b_base + jb];
+                    if (r.key != key) break;
+                    long long* dst_re = (r.meta & 1u) ? &nre : &sre;
+                    long long* dst_im = (r.meta & 1u) ? &nim : &sim;
+                    if ((r.meta >> 1) & 1u) *dst_im += r.val; else *dst_re += r.val;
+                }
+            }
+            if (occupied) { sre += nre; sim += nim; }
+            if (sre == 0 && sim == 0) continue;
+            if (sre > 2147483647ll || sre < -2147483647ll || sim > 2147483647ll || sim < -2147483647ll) {
+                set_error(st, DERR_POP_OVERFLOW);
+                continue;
+            }
+            outrec[nout++] = Rec{key, (int32_t)sre, (int32_t)sim};
+            my_ntot += (sre < 0 ? -sre : sre) + (sim < 0 ? -sim : sim);
+            if ((uint32_t)(key >> n) == (uint32_t)(key & ymask)) {
+                my_dre += sre;
+                my_dim += sim;
+            }
+        }
+        // block scan of output counts
+        int incl = nout;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_wcount[warp] = incl;
+        long long r0 = my_ntot, r1 = my_dre, r2 = my_dim;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            r0 += __shfl_down_sync(kFull, r0, o);
+            r1 += __shfl_down_sync(kFull, r1, o);
+            r2 += __shfl_down_sync(kFull, r2, o);
+        }
+        if (lane == 0) {
+            s_red[0][warp] = r0;
+            s_red[1][warp] = r1;
+            s_red[2][warp] = r2;
+        }
+        __syncthreads();
+        int woff = 0, tile_count = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < warp) woff += s_wcount[w];
+            tile_count += s_wcount[w];
+        }
+        if (tid == 0) {
+            // decoupled look-back over merge tiles (global output order)
+            unsigned long long* my = P.merge_status + t;
+            unsigned long long excl = 0;
+            if (t == 0) {
+                st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)tile_count));
+            } else {
+                st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)tile_count));
+                for (int64_t j = t - 1; j >= 0; --j) {
+                    unsigned long long v;
+                    if (!lb_wait(P.merge_status + j, epoch, &v, st)) break;
+                    excl += v & 0x3FFFFFFFull;
+                    if (((v >> 30) & 3u) == kFlagIncl) break;
+                }
+                st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tile_count)));
+            }
+            s_base = excl;
+            if (t == T - 1) {
+                st->next_total = (int64_t)(excl + tile_count);
+                if ((int64_t)(excl + tile_count) > st->max_next) st->max_next = (int64_t)(excl + tile_count);
+            }
+            if (tile_count) {
+                long long a = 0, b = 0, c = 0;
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    a += s_red[0][w];
+                    b += s_red[1][w];
+                    c += s_red[2][w];
+                }
+                atomicAdd(&P.segacc[s].count, (unsigned long long)tile_count);
+                atomicAdd((unsigned long long*)&P.segacc[s].ntot, (unsigned long long)a);
+                atomicAdd((unsigned long long*)&P.segacc[s].dre, (unsigned long long)b);
+                atomicAdd((unsigned long long*)&P.segacc[s].dim, (unsigned long long)c);
+            }
+        }
+        __syncthreads();
+        const int64_t obase = (int64_t)s_base + woff + incl - nout;
+        for (int k = 0; k < nout; ++k) {
+            const int64_t pos = obase + k;
+            if (pos < P.pop_cap) out[pos] = outrec[k];
+            else set_error(st, DERR_POP_CAPACITY);
+        }
+        __syncthreads();
+    }
+}
+
+// Segment offsets of N(t + dt), history, rotation (single CTA).
+__global__ void k_finalize(StepParams P)
+{
+    __shared__ long long wsum[32];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int cur = st->cur, nxt = (cur + 1) % 3;
+    int64_t* off = P.segoff[nxt];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ci = st->call_index;
+    long long carry = 0;
+    for (int base = 0; base < P.nseg; base += blockDim.x) {
+        const int s = base + tid;
+        long long c = 0;
+        if (s < P.nseg) {
+            c = (long long)P.segacc[s].count;
+            if (ci < P.history_cap) {
+                SegStats h = P.segacc[s];
+                P.history[(int64_t)ci * P.nseg + s] = h;
+            }
+        }
+        long long incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        long long wo = 0;
+        for (int w = 0; w < warp; ++w) wo += wsum[w];
+        if (s < P.nseg) off[s] = carry + wo + incl - c;
+        __syncthreads();
+        long long blk = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) blk += wsum[w];
+        carry += blk;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        long long walkers = 0;
+        for (int s = 0; s < P.nseg; ++s) walkers += P.segacc[s].ntot;
+        const StepInfo inf = P.info[ci];
+        st->acc_steps += 1;
+        st->acc_walkers += walkers;
+        st->acc_kcur += st->count[cur];
+        st->acc_kprev += inf.ab2 ? st->count[(cur + 2) % 3] : 0;
+        st->acc_spawn += st->spawn_total;
+        st->acc_knext += carry;
+        st->acc_heavy += st->heavy_total;
+        off[P.nseg] = carry;
+        if (st->spawn_total > st->max_spawn) st->max_spawn = st->spawn_total;
+        if (st->heavy_total > st->max_heavy) st->max_heavy = st->heavy_total;
+        st->count[nxt] = carry;
+        st->cur = nxt;
+        st->step += 1;
+        st->call_index += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial populations: N(0) = N^diag rho(0), stochastic rounding per
+// component with the kind-1 stream of each segment.
+// ---------------------------------------------------------------------------
+__global__ void k_init_values(StepParams P, const uint64_t* __restrict__ keys, const double* __restrict__ re,
+                              const double* __restrict__ im, int64_t nnz, int64_t n_diag,
+                              int64_t* __restrict__ vals)
+{
+    const int64_t total = nnz * P.nseg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i / nnz);
+        const int64_t e = i - (int64_t)s * nnz;
+        const uint4 kk = philox10(make_uint4(0u, 0u, (uint32_t)s, kTagInit),
+                                  make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+        const uint2 kd = make_uint2(kk.x, kk.y);
+        const uint64_t key = keys[e];
+        for (int comp = 0; comp < 2; ++comp) {
+            const double v = __dmul_rn((double)n_diag, comp ? im[e] : re[e]);
+            const double fl = floor(v);
+            const double fr = __dsub_rn(v, fl);
+            const uint4 w = philox10(make_uint4((uint32_t)key, (uint32_t)(key >> 32),
+                                                ((uint32_t)comp << 1) | (kKindInit << 2), 0u), kd);
+            const uint64_t r = ((uint64_t)w.y << 32) | w.x;
+            const double u = __dmul_rn((double)(r >> 11), 1.0 / 9007199254740992.0);
+            int64_t val = (int64_t)fl + (u < fr ? 1 : 0);
+            if (val > 2147483647ll || val < -2147483647ll) {
+                set_error(P.st, DERR_POP_OVERFLOW);
+                val = 0;
+            }
+            vals[2 * i + comp] = val;
+        }
+    }
+}
+
+// Compact nonzero values per segment into slot 'cur' (single CTA, in order).
+__global__ void k_init_compact(StepParams P, const uint64_t* __restrict__ keys, int64_t nnz,
+                               const int64_t* __restrict__ vals)
+{
+    __shared__ int s_cnt[kThreads];
+    DevState* st = P.st;
+    const int slot = st->cur;
+    Rec* dst = P.pop[slot];
+    int64_t* off = P.segoff[slot];
+    int64_t pos = 0;
+    const int tid = threadIdx.x;
+    for (int s = 0; s < P.nseg; ++s) {
+        if (tid == 0) off[s] = pos;
+        for (int64_t base = 0; base < nnz; base += kThreads) {
+            const int64_t e = base + tid;
+            const int64_t i = (int64_t)s * nnz + e;
+            const bool keep = e < nnz && (vals[2 * i] != 0 || vals[2 * i + 1] != 0);
+            s_cnt[tid] = keep ? 1 : 0;
+            __syncthreads();
+            for (int o = 1; o < kThreads; o <<= 1) {
+                const int v = tid >= o ? s_cnt[tid - o] : 0;
+                __syncthreads();
+                s_cnt[tid] += v;
+                __syncthreads();
+            }
+            const int excl = s_cnt[tid] - (keep ? 1 : 0);
+            const int blk = s_cnt[kThreads - 1];
+            if (keep && pos + excl < P.pop_cap)
+                dst[pos + excl] = Rec{keys[e], (int32_t)vals[2 * i], (int32_t)vals[2 * i + 1]};
+            pos += blk;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        off[P.nseg] = pos;
+        st->count[slot] = pos;
+        if (pos > P.pop_cap) set_error(st, DERR_POP_CAPACITY);
+    }
+}
+
+// Per-segment K, N_tot, N^diag of one population slot.
+__global__ void k_obs(StepParams P, int which, SegStats* __restrict__ out)
+{
+    const DevState* st = P.st;
+    const int slot = which == 0 ? st->cur : (st->cur + 2) % 3;
+    const Rec* pop = P.pop[slot];
+    const int64_t* off = P.segoff[slot];
+    const int64_t K = off[P.nseg];
+    const int n = P.n;
+    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const Rec r = pop[i];
+        const int s = seg_of(off, P.nseg, i);
+        const long long a = (r.re < 0 ? -(long long)r.re : r.re) + (r.im < 0 ? -(long long)r.im : r.im);
+        atomicAdd(&out[s].count, 1ull);
+        atomicAdd((unsigned long long*)&out[s].ntot, (unsigned long long)a);
+        if ((uint32_t)(r.key >> n) == (uint32_t)(r.key & ymask)) {
+            atomicAdd((unsigned long long*)&out[s].dre, (unsigned long long)(long long)r.re);
+            atomicAdd((unsigned long long*)&out[s].dim, (unsigned long long)(long long)r.im);
+        }
+    }
+}
+
+// Values of query keys in one segment of N(t) (0 when absent).
+__global__ void k_lookup(StepParams P, int seg, const uint64_t* __restrict__ q, int nq, int64_t* __restrict__ out)
+{
+    const DevState* st = P.st;
+    const int slot = st->cur;
+    const Rec* pop = P.pop[slot];
+    const int64_t lo0 = P.segoff[slot][seg], hi0 = P.segoff[slot][seg + 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+        int64_t lo = lo0, hi = hi0;
+        const uint64_t key = q[i];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (pop[mid].key < key) lo = mid + 1; else hi = mid;
+        }
+        int64_t re = 0, im = 0;
+        if (lo < hi0 && pop[lo].key == key) { re = pop[lo].re; im = pop[lo].im; }
+        out[2 * i] = re;
+        out[2 * i + 1] = im;
+    }
+}
+
+} // namespace
+
+void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream)
+{
+    cudaMemsetAsync(out, 0, sizeof(SegStats) * P.nseg, stream);
+    k_obs<<<grid, kThreads, 0, stream>>>(P, which, out);
+}
+
+void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int64_t* out, cudaStream_t stream)
+{
+    k_lookup<<<(nq + kThreads - 1) / kThreads, kThreads, 0, stream>>>(P, seg, q, nq, out);
+}
+
+const char* const kKernelNames[kNumTimedKernels] = {
+    "k_prologue", "k_spawn_light", "k_spawn_heavy", "k_sort_hist", "k_sort_scatter",
+    "k_spawn_segoff", "k_merge_plan", "k_merge_part", "k_merge", "k_finalize"};
+
+void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev)
+{
+    // ev (optional): kNumTimedKernels + 1 events; kernel i runs between ev[i] and ev[i + 1]
+    auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], stream); };
+    mark(0);
+    k_prologue<<<1, kThreads, 0, stream>>>(P);
+    mark(1);
+    k_spawn_light<<<grid, kThreads, 0, stream>>>(P);
+    mark(2);
+    k_spawn_heavy<<<grid, kThreads, 0, stream>>>(P);
+    mark(3);
+    const int np = P.key_passes + P.seg_passes;
+    k_sort_hist<<<grid, kThreads, 0, stream>>>(P);
+    mark(4);
+    SRec* a = P.spawn;
+    SRec* b = P.spawn_alt;
+    for (int p = 0; p < np; ++p) {
+        k_sort_scatter<<<grid, kThreads, 0, stream>>>(P, p, a, b);
+        SRec* t = a;
+        a = b;
+        b = t;
+    }
+    mark(5);
+    const SRec* sorted = a;
+    k_spawn_segoff<<<(P.nseg + 1 + kThreads - 1) / kThreads, kThreads, 0, stream>>>(P, sorted);
+    mark(6);
+    k_merge_plan<<<1, 1024, 0, stream>>>(P);
+    mark(7);
+    k_merge_part<<<grid, kThreads, 0, stream>>>(P, sorted);
+    mark(8);
+    k_merge<<<grid, kThreads, 0, stream>>>(P, sorted);
+    mark(9);
+    k_finalize<<<1, 1024, 0, stream>>>(P);
+    mark(10);
+}
+
+void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,
+                 int64_t nnz, int64_t n_diag, int64_t* tmp_vals, cudaStream_t stream)
+{
+    const int64_t total = nnz * P.nseg;
+    const int blocks = (int)((total + kThreads - 1) / kThreads < 4096 ? (total + kThreads - 1) / kThreads : 4096);
+    k_init_values<<<blocks > 0 ? blocks : 1, kThreads, 0, stream>>>(P, keys, re, im, nnz, n_diag, tmp_vals);
+    k_init_compact<<<1, kThreads, 0, stream>>>(P, keys, nnz, tmp_vals);
+}
+
+} // namespace qmc

@@ -1,0 +1,83 @@
+// Kernel launch interface (library-internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qmc_types.h"
+
+namespace qmc {
+
+constexpr int kThreads = 256;
+constexpr int kSortItems = 8;                        // records per thread per sort tile
+constexpr int kSortTile = kThreads * kSortItems;     // 2048 records
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = kThreads * kMergeItems;   // 2048 merged items
+constexpr int kHeavyWalkers = 256;                   // parents above this go to the heavy path
+constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
+constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
+constexpr int kMaxPasses = 12;
+constexpr int kCtrMerge = kMaxPasses;                // tile counter index of the merge
+constexpr uint32_t kTagStep = 0x53544550u;
+constexpr uint32_t kTagInit = 0x494E4954u;
+constexpr uint32_t kKindSpawn = 0u;
+constexpr uint32_t kKindInit = 1u;
+
+struct HeavyItem {
+    int64_t parent;  // index inside its population slot
+    int32_t phase;   // 0: N(t), 1: N(t - dt)
+    int32_t comp;    // 0: real walkers, 1: imaginary walkers
+    int32_t chunk;   // walker chunk index
+    int32_t seg;
+};
+
+struct SegStats {
+    unsigned long long count;
+    long long ntot, dre, dim;
+};
+
+// Everything a step's kernels need.  Pointers are device pointers.
+struct StepParams {
+    DevState* st;
+    const StepInfo* info;
+    const uint8_t* progs;
+    Rec* pop[3];
+    int64_t* segoff[3];   // nseg + 1 offsets per slot
+    int64_t pop_cap;
+    SRec* spawn;          // spawn records (sort ping-pong A)
+    SRec* spawn_alt;      // sort ping-pong B
+    int64_t spawn_cap;
+    HeavyItem* heavy;
+    int64_t heavy_cap;
+    uint2* kd;            // per-segment Philox key of the current step
+    unsigned int* sort_hist;   // [kMaxPasses][256]
+    unsigned long long* sort_status; // [tiles][256] look-back words
+    int64_t sort_tiles_cap;
+    int64_t* bseg;        // nseg + 1: offsets of each segment in the sorted spawns
+    int64_t* tile_start;  // nseg + 1: first merge tile of each segment
+    int64_t* part;        // 2 per merge tile: local (a, b) start of the tile
+    unsigned long long* merge_status; // per merge tile look-back word
+    int64_t merge_tiles_cap;
+    SegStats* segacc;     // per-segment accumulators of the merge
+    SegStats* history;    // [steps of call][nseg]
+    int64_t history_cap;  // steps
+    int n;
+    int nseg;
+    int seg_bits;
+    int key_passes;
+    int seg_passes;
+    int pad;
+    uint64_t seed;
+    int64_t init_min;
+};
+
+// Launchers (kernels.cu).  All take their sizes from DevState, so the same
+// launch sequence can be captured once in a CUDA graph and replayed.
+constexpr int kNumTimedKernels = 10;
+extern const char* const kKernelNames[kNumTimedKernels];
+void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);
+void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int64_t* out, cudaStream_t stream);
+void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,
+                 int64_t nnz, int64_t n_diag, int64_t* tmp_vals, cudaStream_t stream);
+
+} // namespace qmc

@@ -1,0 +1,924 @@
+// C ABI of the library (include/qmc.h): context, memory, step orchestration,
+// results, checkpoints.  Kernels live in kernels.cu, the term compiler in
+// term_compiler.cpp.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "kernels.h"
+#include "qmc_types.h"
+#include "term_compiler.h"
+#include "context.h"
+
+using namespace qmc;
+
+
+namespace {
+
+constexpr int64_t kLookbackValueLimit = (1ll << 30) - 1;
+
+int fail(qmc_ctx* c, int code, const std::string& why)
+{
+    if (c) c->err = why;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, QMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int dalloc(qmc_ctx* ctx, T** p, int64_t count)
+{
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, QMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return QMC_OK;
+}
+
+int seg_bits_of(int nseg)
+{
+    int b = 0;
+    while ((1ll << b) < nseg) ++b;
+    return b;
+}
+
+StepParams params(qmc_ctx* c)
+{
+    StepParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.st = c->d_state;
+    P.info = c->d_info;
+    P.progs = c->d_progs;
+    for (int i = 0; i < 3; ++i) {
+        P.pop[i] = c->d_pop[i];
+        P.segoff[i] = c->d_segoff[i];
+    }
+    P.pop_cap = c->pop_cap;
+    P.spawn = c->d_spawn;
+    P.spawn_alt = c->d_spawn_alt;
+    P.spawn_cap = c->spawn_cap;
+    P.heavy = c->d_heavy;
+    P.heavy_cap = c->heavy_cap;
+    P.kd = c->d_kd;
+    P.sort_hist = c->d_sort_hist;
+    P.sort_status = c->d_sort_status;
+    P.sort_tiles_cap = c->sort_tiles_cap;
+    P.bseg = c->d_bseg;
+    P.tile_start = c->d_tile_start;
+    P.part = c->d_part;
+    P.merge_status = c->d_merge_status;
+    P.merge_tiles_cap = c->merge_tiles_cap;
+    P.segacc = c->d_segacc;
+    P.history = c->d_history;
+    P.history_cap = c->history_cap;
+    P.n = c->cfg.n_qubits;
+    P.nseg = c->cfg.n_segments;
+    P.seg_bits = seg_bits_of(c->cfg.n_segments);
+    P.key_passes = (2 * c->cfg.n_qubits + 7) / 8;
+    P.seg_passes = (P.seg_bits + 7) / 8;
+    P.seed = c->cfg.seed;
+    P.init_min = c->cfg.initiator_min;
+    return P;
+}
+
+// Make the work stream wait for the caller's stream (and vice versa at exit).
+int enter(qmc_ctx* ctx)
+{
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaEventRecord(ctx->ev, ctx->user_stream));
+    CK(cudaStreamWaitEvent(ctx->work, ctx->ev, 0));
+    return QMC_OK;
+}
+
+int leave(qmc_ctx* ctx)
+{
+    CK(cudaEventRecord(ctx->ev, ctx->work));
+    CK(cudaStreamWaitEvent(ctx->user_stream, ctx->ev, 0));
+    return QMC_OK;
+}
+
+int grow_spawn(qmc_ctx* ctx, int64_t need)
+{
+    int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
+    if (cap > kLookbackValueLimit) cap = kLookbackValueLimit;
+    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "spawn records exceed 2^30 - 1 per step");
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->d_spawn, cap)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_spawn_alt, cap)) != QMC_OK) return rc;
+    ctx->spawn_cap = cap;
+    ctx->sort_tiles_cap = (cap + kSortTile - 1) / kSortTile + 1;
+    if ((rc = dalloc(ctx, &ctx->d_sort_status, ctx->sort_tiles_cap * 256)) != QMC_OK) return rc;
+    CK(cudaMemsetAsync(ctx->d_sort_status, 0, (size_t)ctx->sort_tiles_cap * 256 * 8, ctx->work));
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
+int grow_merge_tiles(qmc_ctx* ctx)
+{
+    const int64_t cap = (ctx->pop_cap + ctx->spawn_cap) / kMergeTile + ctx->cfg.n_segments + 2;
+    if (cap <= ctx->merge_tiles_cap) return QMC_OK;
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->d_part, 2 * cap)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_merge_status, cap)) != QMC_OK) return rc;
+    CK(cudaMemsetAsync(ctx->d_merge_status, 0, (size_t)cap * 8, ctx->work));
+    ctx->merge_tiles_cap = cap;
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
+// Grow the three population slots to hold need records, keeping contents.
+int grow_pop(qmc_ctx* ctx, int64_t need)
+{
+    int64_t cap = std::max<int64_t>(need + need / 2, 1 << 12);
+    if (cap > kLookbackValueLimit) cap = kLookbackValueLimit;
+    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "population exceeds 2^30 - 1 records");
+    if (ctx->cfg.max_records > 0 && need > ctx->cfg.max_records)
+        return fail(ctx, QMC_ERR_CAPACITY, "population exceeds max_records");
+    if (ctx->cfg.max_records > 0) cap = std::min(cap, ctx->cfg.max_records);
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (int i = 0; i < 3; ++i) {
+        Rec* np = nullptr;
+        cudaError_t e = cudaMalloc((void**)&np, (size_t)cap * sizeof(Rec));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, QMC_ERR_OOM, "population buffer allocation failed");
+        }
+        const int64_t keep = std::min<int64_t>(hs.count[i], std::min(ctx->pop_cap, cap));
+        if (ctx->d_pop[i] && keep > 0)
+            CK(cudaMemcpyAsync(np, ctx->d_pop[i], (size_t)keep * sizeof(Rec), cudaMemcpyDeviceToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        if (ctx->d_pop[i]) cudaFree(ctx->d_pop[i]);
+        ctx->d_pop[i] = np;
+    }
+    ctx->pop_cap = cap;
+    ctx->graph_dirty = true;
+    return grow_merge_tiles(ctx);
+}
+
+int upload_calls(qmc_ctx* ctx, const std::vector<StepInfo>& info, const std::vector<uint8_t>& blob)
+{
+    int rc;
+    if ((int64_t)info.size() > ctx->info_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_info, (int64_t)info.size())) != QMC_OK) return rc;
+        ctx->info_cap = (int64_t)info.size();
+        ctx->graph_dirty = true;
+    }
+    if ((int64_t)blob.size() > ctx->progs_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_progs, (int64_t)blob.size())) != QMC_OK) return rc;
+        ctx->progs_cap = (int64_t)blob.size();
+        ctx->graph_dirty = true;
+    }
+    if ((int64_t)info.size() > ctx->history_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_history, (int64_t)info.size() * ctx->cfg.n_segments)) != QMC_OK) return rc;
+        ctx->history_cap = (int64_t)info.size();
+        ctx->graph_dirty = true;
+    }
+    CK(cudaMemcpyAsync(ctx->d_info, info.data(), info.size() * sizeof(StepInfo), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(ctx->d_progs, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->work));
+    return QMC_OK;
+}
+
+int capture_graph(qmc_ctx* ctx)
+{
+    if (!ctx->graph_dirty && ctx->graph) return QMC_OK;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    StepParams P = params(ctx);
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
+    launch_step(P, ctx->grid, ctx->work);
+    CK(cudaStreamEndCapture(ctx->work, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, QMC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    ctx->graph_dirty = false;
+    return QMC_OK;
+}
+
+int map_dev_error(qmc_ctx* ctx, uint32_t code)
+{
+    switch (code) {
+    case DERR_DT_TOO_LARGE: return fail(ctx, QMC_ERR_DT_TOO_LARGE, "spawn probability p >= 1: reduce dt");
+    case DERR_POP_OVERFLOW: return fail(ctx, QMC_ERR_POP_OVERFLOW, "a population component exceeds 2^31 - 1");
+    case DERR_TIMEOUT: return fail(ctx, QMC_ERR_DEVICE_TIMEOUT, "a bounded device wait expired");
+    default: return fail(ctx, QMC_ERR_CAPACITY, "capacity error");
+    }
+}
+
+int clear_dev_error(qmc_ctx* ctx)
+{
+    const uint32_t zero = 0;
+    CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, error), &zero, sizeof(zero),
+                       cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return QMC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int qmc_create(qmc_ctx** out, const qmc_config* cfg)
+{
+    if (!out || !cfg) return QMC_ERR_INVALID_ARG;
+    if (cfg->n_qubits < 1 || cfg->n_qubits > 32 || cfg->n_segments < 1 || cfg->n_diag < 1 ||
+        cfg->n_segments > (1 << 28) || (cfg->integrator != QMC_EULER && cfg->integrator != QMC_AB2) ||
+        cfg->initiator_min < 0)
+        return QMC_ERR_INVALID_ARG;
+    qmc_ctx* ctx = new qmc_ctx();
+    ctx->cfg = *cfg;
+    ctx->user_stream = (cudaStream_t)cfg->cuda_stream;
+    int rc = QMC_OK;
+    auto bail = [&](int code) { qmc_destroy(ctx); return code; };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->grid = std::max(1, ctx->sm_count) * 4;
+    if (cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    const int nseg = cfg->n_segments;
+    if ((rc = dalloc(ctx, &ctx->d_state, 1)) != QMC_OK) return bail(rc);
+    if (cudaMemset(ctx->d_state, 0, sizeof(DevState)) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    for (int i = 0; i < 3; ++i) {
+        if ((rc = dalloc(ctx, &ctx->d_segoff[i], nseg + 1)) != QMC_OK) return bail(rc);
+        if (cudaMemset(ctx->d_segoff[i], 0, (size_t)(nseg + 1) * 8) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    }
+    if ((rc = dalloc(ctx, &ctx->d_kd, nseg)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_sort_hist, kMaxPasses * 256)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_bseg, nseg + 1)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_tile_start, nseg + 1)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_segacc, nseg)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_obs, nseg)) != QMC_OK) return bail(rc);
+    ctx->heavy_cap = 4096;
+    if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
+    const int64_t hint = cfg->capacity_hint > 0 ? cfg->capacity_hint : (int64_t)1 << 16;
+    if ((rc = grow_spawn(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
+    if ((rc = grow_pop(ctx, hint)) != QMC_OK) return bail(rc);
+    if (cudaStreamSynchronize(ctx->work) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    *out = ctx;
+    return QMC_OK;
+}
+
+void qmc_destroy(qmc_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->work) cudaStreamSynchronize(ctx->work);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
+                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_heavy,
+                    ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
+                    ctx->d_part, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
+                    ctx->d_progs, ctx->d_obs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->ev) cudaEventDestroy(ctx->ev);
+    if (ctx->work) cudaStreamDestroy(ctx->work);
+    delete ctx;
+}
+
+const char* qmc_last_error(const qmc_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, const qmc_lindblad* lind,
+                      int32_t n_lind, const qmc_pauli_coef* coefs, int32_t n_coefs, const qmc_rate* rates,
+                      int32_t n_rates, const qmc_window* windows, int32_t n_windows)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (n_ham < 0 || n_lind < 0 || n_coefs < 0 || n_rates < 0 || n_windows < 0)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "negative array length");
+    Schedule s;
+    s.n = ctx->cfg.n_qubits;
+    if (n_ham) s.ham.assign(ham, ham + n_ham);
+    if (n_lind) s.lind.assign(lind, lind + n_lind);
+    if (n_coefs) s.coefs.assign(coefs, coefs + n_coefs);
+    if (n_rates) s.rates.assign(rates, rates + n_rates);
+    if (n_windows) s.windows.assign(windows, windows + n_windows);
+    std::string why;
+    if (validate_schedule(s, &why) != QMC_OK) return fail(ctx, QMC_ERR_INVALID_ARG, why);
+    ctx->sched = s;
+    ctx->has_sched = true;
+    return QMC_OK;
+}
+
+int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, const double* re,
+                         const double* im, int64_t nnz)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_sched) return fail(ctx, QMC_ERR_STATE, "load a schedule first");
+    if (nnz < 0 || (nnz > 0 && (!x || !y || !re || !im))) return fail(ctx, QMC_ERR_INVALID_ARG, "bad arrays");
+    const int n = ctx->cfg.n_qubits;
+    const uint64_t lim = (1ull << n) - 1;
+    std::vector<std::pair<uint64_t, int64_t>> order;
+    for (int64_t i = 0; i < nnz; ++i) {
+        if ((x[i] & ~lim) || (y[i] & ~lim)) return fail(ctx, QMC_ERR_INVALID_ARG, "x or y >= 2^n");
+        order.push_back({(x[i] << n) | y[i], i});
+    }
+    std::sort(order.begin(), order.end());
+    for (size_t i = 1; i < order.size(); ++i)
+        if (order[i].first == order[i - 1].first) return fail(ctx, QMC_ERR_INVALID_ARG, "duplicate (x, y)");
+    std::vector<uint64_t> keys(nnz);
+    std::vector<double> hre(nnz), him(nnz);
+    for (int64_t i = 0; i < nnz; ++i) {
+        keys[i] = order[i].first;
+        hre[i] = re[order[i].second];
+        him[i] = im[order[i].second];
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    const int64_t need = std::max<int64_t>(1, nnz) * ctx->cfg.n_segments;
+    if (need > ctx->pop_cap && (rc = grow_pop(ctx, need)) != QMC_OK) return rc;
+    uint64_t* d_keys = nullptr;
+    double *d_re = nullptr, *d_im = nullptr;
+    int64_t* d_vals = nullptr;
+    if ((rc = dalloc(ctx, &d_keys, nnz)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_re, nnz)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_im, nnz)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_vals, 2 * need)) != QMC_OK) return rc;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+    if (nnz) {
+        CK(cudaMemcpyAsync(d_keys, keys.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_re, hre.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_im, him.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
+    }
+    StepParams P = params(ctx);
+    launch_init(P, d_keys, d_re, d_im, nnz, ctx->cfg.n_diag, d_vals, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(ctx->d_segoff[2], 0, (size_t)(ctx->cfg.n_segments + 1) * 8, ctx->work));
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    cudaFree(d_keys);
+    cudaFree(d_re);
+    cudaFree(d_im);
+    cudaFree(d_vals);
+    if (hs.error) {
+        clear_dev_error(ctx);
+        return map_dev_error(ctx, hs.error);
+    }
+    ctx->step = 0;
+    ctx->t = ctx->t_prev = ctx->dt_last = 0.0;
+    ctx->prev_valid = false;
+    ctx->has_pop = true;
+    return leave(ctx);
+}
+
+int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, const uint64_t* keys,
+                        const int32_t* re, const int32_t* im)
+{
+    if (!ctx || (which != 0 && which != 1) || !counts) return QMC_ERR_INVALID_ARG;
+    const int nseg = ctx->cfg.n_segments;
+    std::vector<int64_t> off(nseg + 1, 0);
+    for (int s = 0; s < nseg; ++s) {
+        if (counts[s] < 0) return fail(ctx, QMC_ERR_INVALID_ARG, "negative count");
+        off[s + 1] = off[s] + counts[s];
+    }
+    const int64_t total = off[nseg];
+    const uint64_t lim = ctx->cfg.n_qubits == 32 ? ~0ull : ((1ull << (2 * ctx->cfg.n_qubits)) - 1);
+    std::vector<Rec> recs(total);
+    for (int s = 0; s < nseg; ++s) {
+        for (int64_t i = off[s]; i < off[s + 1]; ++i) {
+            if (keys[i] & ~lim) return fail(ctx, QMC_ERR_INVALID_ARG, "key beyond 2n bits");
+            if (re[i] == 0 && im[i] == 0) return fail(ctx, QMC_ERR_INVALID_ARG, "zero record");
+            if (re[i] == INT32_MIN || im[i] == INT32_MIN) return fail(ctx, QMC_ERR_INVALID_ARG, "value -2^31");
+            if (i > off[s] && keys[i] <= keys[i - 1]) return fail(ctx, QMC_ERR_INVALID_ARG, "keys not ascending");
+            recs[i] = Rec{keys[i], re[i], im[i]};
+        }
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if (total > ctx->pop_cap && (rc = grow_pop(ctx, total)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int slot = which == 0 ? hs.cur : (hs.cur + 2) % 3;
+    if (total)
+        CK(cudaMemcpyAsync(ctx->d_pop[slot], recs.data(), total * sizeof(Rec), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(ctx->d_segoff[slot], off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+    hs.count[slot] = total;
+    hs.error = 0;
+    CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    if (which == 0) ctx->has_pop = true;
+    return leave(ctx);
+}
+
+int qmc_set_clock(qmc_ctx* ctx, uint64_t step, double t, double t_prev, double dt_last, int32_t prev_valid)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, step), &step, 8, cudaMemcpyHostToDevice,
+                       ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    ctx->step = step;
+    ctx->t = t;
+    ctx->t_prev = t_prev;
+    ctx->dt_last = dt_last;
+    ctx->prev_valid = prev_valid != 0;
+    return leave(ctx);
+}
+
+int qmc_get_clock(const qmc_ctx* ctx, uint64_t* step, double* t, double* t_prev, double* dt_last,
+                  int32_t* prev_valid)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (step) *step = ctx->step;
+    if (t) *t = ctx->t;
+    if (t_prev) *t_prev = ctx->t_prev;
+    if (dt_last) *dt_last = ctx->dt_last;
+    if (prev_valid) *prev_valid = ctx->prev_valid ? 1 : 0;
+    return QMC_OK;
+}
+
+int qmc_spawn_prob_bound(const qmc_ctx* ctx, double t, double dt, double* p_bound)
+{
+    if (!ctx || !p_bound || !ctx->has_sched) return QMC_ERR_INVALID_ARG;
+    *p_bound = spawn_prob_bound(ctx->sched, t, dt * 1.5);
+    return QMC_OK;
+}
+
+int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_sched || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!(dt > 0.0) || nsteps < 0) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 0");
+    if (nsteps == 0) return QMC_OK;
+    // per-step column programs (identical consecutive programs are shared)
+    std::vector<StepInfo> info(nsteps);
+    std::vector<uint8_t> blob;
+    std::vector<uint8_t> tmp;
+    int64_t last_off[2] = {-1, -1};
+    std::vector<uint8_t> last_blob[2];
+    auto add_prog = [&](int pass, double tt, double dte, int64_t* off_out) -> int {
+        tmp.clear();
+        int rc = build_program(ctx->sched, tt, dte, &tmp);
+        if (rc != QMC_OK) return rc;
+        const ProgHeader* h = (const ProgHeader*)tmp.data();
+        if (h->n_entry > kMaxEntries)
+            return fail(ctx, QMC_ERR_INVALID_ARG, "column has more destinations than the heavy path holds");
+        if (last_off[pass] >= 0 && last_blob[pass] == tmp) {
+            *off_out = last_off[pass];
+            return QMC_OK;
+        }
+        const size_t at = (blob.size() + 15) & ~(size_t)15;
+        blob.resize(at);
+        blob.insert(blob.end(), tmp.begin(), tmp.end());
+        last_blob[pass] = tmp;
+        last_off[pass] = (int64_t)at;
+        *off_out = (int64_t)at;
+        return QMC_OK;
+    };
+    const double t0 = ctx->t;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const double ti = t0 + (double)i * dt;
+        const bool ab2 = ctx->cfg.integrator == QMC_AB2 &&
+                         (i > 0 || (ctx->prev_valid && ctx->dt_last == dt));
+        const double tp = i > 0 ? t0 + (double)(i - 1) * dt : ctx->t_prev;
+        info[i].ab2 = ab2 ? 1 : 0;
+        info[i].prog_off[1] = -1;
+        int rc = add_prog(0, ti, ab2 ? dt * 1.5 : dt, &info[i].prog_off[0]);
+        if (rc == QMC_OK && ab2) rc = add_prog(1, tp, dt * 0.5, &info[i].prog_off[1]);
+        if (rc != QMC_OK) {
+            if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
+            return rc;
+        }
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if ((rc = upload_calls(ctx, info, blob)) != QMC_OK) return rc;
+    int32_t zero = 0;
+    CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &zero, 4, cudaMemcpyHostToDevice,
+                       ctx->work));
+    int64_t done = 0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        if ((rc = capture_graph(ctx)) != QMC_OK) return rc;
+        for (int64_t i = done; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->graph, ctx->work));
+        DevState hs;
+        CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        done = hs.call_index;
+        if (!hs.error) break;
+        const uint32_t code = hs.error;
+        if ((rc = clear_dev_error(ctx)) != QMC_OK) return rc;
+        if (code == DERR_SPAWN_CAPACITY) {
+            if ((rc = grow_spawn(ctx, hs.spawn_total)) != QMC_OK) return rc;
+            if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
+        } else if (code == DERR_HEAVY_CAPACITY) {
+            const int64_t cap = std::max<int64_t>(hs.heavy_total * 2, ctx->heavy_cap * 2);
+            if ((rc = dalloc(ctx, &ctx->d_heavy, cap)) != QMC_OK) return rc;
+            ctx->heavy_cap = cap;
+            ctx->graph_dirty = true;
+        } else if (code == DERR_POP_CAPACITY) {
+            if ((rc = grow_pop(ctx, hs.next_total)) != QMC_OK) return rc;
+        } else if (code == DERR_TILE_CAPACITY) {
+            if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
+            if ((rc = grow_spawn(ctx, ctx->spawn_cap)) != QMC_OK) return rc;
+        } else {
+            // fatal for this call: the state is that of the last completed step
+            ctx->step += (uint64_t)done;
+            if (done > 0) {
+                ctx->t_prev = t0 + (double)(done - 1) * dt;
+                ctx->t = t0 + (double)done * dt;
+                ctx->dt_last = dt;
+                ctx->prev_valid = true;
+            }
+            ctx->last_call_steps = done;
+            leave(ctx);
+            return map_dev_error(ctx, code);
+        }
+        // redo from the failed step
+        CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &done, 4,
+                           cudaMemcpyHostToDevice, ctx->work));
+        (void)zero;
+    }
+    if (done != nsteps) return fail(ctx, QMC_ERR_CAPACITY, "could not complete the steps after growing buffers");
+    ctx->step += (uint64_t)nsteps;
+    ctx->t_prev = t0 + (double)(nsteps - 1) * dt;
+    ctx->t = t0 + (double)nsteps * dt;
+    ctx->dt_last = dt;
+    ctx->prev_valid = true;
+    ctx->last_call_steps = nsteps;
+    // grow ahead of need so the next call rarely retries
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    if (hs.max_spawn > ctx->spawn_cap * 3 / 4) {
+        if ((rc = grow_spawn(ctx, hs.max_spawn * 2)) != QMC_OK) return rc;
+        if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
+    }
+    if (hs.max_next > ctx->pop_cap * 3 / 4 && (ctx->cfg.max_records == 0 || ctx->pop_cap < ctx->cfg.max_records))
+        if ((rc = grow_pop(ctx, hs.max_next * 2)) != QMC_OK) return rc;
+    return leave(ctx);
+}
+
+int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* count)
+{
+    if (!ctx || !obs || !count) return QMC_ERR_INVALID_ARG;
+    const int64_t nsteps = std::min(cap_steps, ctx->last_call_steps);
+    *count = nsteps;
+    if (nsteps <= 0) return QMC_OK;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    std::vector<SegStats> h((size_t)nsteps * ctx->cfg.n_segments);
+    CK(cudaMemcpyAsync(h.data(), ctx->d_history, h.size() * sizeof(SegStats), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (size_t i = 0; i < h.size(); ++i)
+        obs[i] = qmc_obs{(int64_t)h[i].count, h[i].ntot, h[i].dre, h[i].dim};
+    return leave(ctx);
+}
+
+int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t* re, int32_t* im, int64_t cap,
+               int64_t* count)
+{
+    if (!ctx || !count || seg < 0 || seg >= ctx->cfg.n_segments || (which != 0 && which != 1))
+        return QMC_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int slot = which == 0 ? hs.cur : (hs.cur + 2) % 3;
+    int64_t off[2];
+    CK(cudaMemcpyAsync(off, ctx->d_segoff[slot] + seg, 16, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int64_t cnt = off[1] - off[0];
+    *count = cnt;
+    if (cnt > cap) return fail(ctx, QMC_ERR_INVALID_ARG, "export capacity too small");
+    if (cnt > 0) {
+        std::vector<Rec> r(cnt);
+        CK(cudaMemcpyAsync(r.data(), ctx->d_pop[slot] + off[0], cnt * sizeof(Rec), cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        for (int64_t i = 0; i < cnt; ++i) {
+            keys[i] = r[i].key;
+            re[i] = r[i].re;
+            im[i] = r[i].im;
+        }
+    }
+    return leave(ctx);
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// observables, overlap, checkpoint / restore
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t n_qubits;
+    uint64_t hash;
+    uint64_t step;
+    double t, t_prev, dt_last;
+    int32_t prev_valid;
+    int32_t nseg;
+    int64_t count[2];
+};
+
+uint64_t fnv(uint64_t h, const void* p, size_t len)
+{
+    const uint8_t* b = (const uint8_t*)p;
+    for (size_t i = 0; i < len; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+} // namespace
+
+extern "C" {
+
+int qmc_observables(qmc_ctx* ctx, qmc_obs* obs)
+{
+    if (!ctx || !obs) return QMC_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    StepParams P = params(ctx);
+    launch_obs(P, 0, ctx->d_obs, ctx->grid, ctx->work);
+    CK(cudaGetLastError());
+    std::vector<SegStats> h(ctx->cfg.n_segments);
+    CK(cudaMemcpyAsync(h.data(), ctx->d_obs, h.size() * sizeof(SegStats), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (size_t i = 0; i < h.size(); ++i) obs[i] = qmc_obs{(int64_t)h[i].count, h[i].ntot, h[i].dre, h[i].dim};
+    return leave(ctx);
+}
+
+int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* psi_re, const double* psi_im,
+                int32_t len, double* out_re, double* out_im)
+{
+    if (!ctx || seg < 0 || seg >= ctx->cfg.n_segments || len < 0 || !out_re || !out_im) return QMC_ERR_INVALID_ARG;
+    const int n = ctx->cfg.n_qubits;
+    const int nq = len * len;
+    std::vector<uint64_t> q(nq > 0 ? nq : 1);
+    for (int a = 0; a < len; ++a)
+        for (int b = 0; b < len; ++b) q[a * len + b] = (idx[a] << n) | idx[b];
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    uint64_t* d_q = nullptr;
+    int64_t* d_v = nullptr;
+    if ((rc = dalloc(ctx, &d_q, nq)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_v, 2 * (int64_t)nq)) != QMC_OK) return rc;
+    std::vector<int64_t> v(2 * (size_t)(nq > 0 ? nq : 1));
+    if (nq) {
+        CK(cudaMemcpyAsync(d_q, q.data(), nq * 8, cudaMemcpyHostToDevice, ctx->work));
+        launch_lookup(params(ctx), seg, d_q, nq, d_v, ctx->work);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(v.data(), d_v, 2 * (size_t)nq * 8, cudaMemcpyDeviceToHost, ctx->work));
+    }
+    CK(cudaStreamSynchronize(ctx->work));
+    cudaFree(d_q);
+    cudaFree(d_v);
+    // sum_{a,b} conj(psi_a) N_ab psi_b in a fixed order
+    double sr = 0.0, si = 0.0;
+    for (int a = 0; a < len; ++a) {
+        for (int b = 0; b < len; ++b) {
+            const double nr = (double)v[2 * (a * len + b)], ni = (double)v[2 * (a * len + b) + 1];
+            const double car = psi_re[a], cai = -psi_im[a];
+            const double pr = car * nr - cai * ni, pi = car * ni + cai * nr;
+            sr += pr * psi_re[b] - pi * psi_im[b];
+            si += pr * psi_im[b] + pi * psi_re[b];
+        }
+    }
+    *out_re = sr;
+    *out_im = si;
+    return leave(ctx);
+}
+
+int qmc_checkpoint(qmc_ctx* ctx, const char* path)
+{
+    if (!ctx || !path) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "nothing to checkpoint");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int nseg = ctx->cfg.n_segments;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "QMCCKPT1", 8);
+    h.version = 1;
+    h.n_qubits = ctx->cfg.n_qubits;
+    h.hash = schedule_hash(ctx->sched, ctx->cfg.seed, nseg, ctx->cfg.integrator, ctx->cfg.n_diag,
+                           ctx->cfg.initiator_min);
+    h.step = ctx->step;
+    h.t = ctx->t;
+    h.t_prev = ctx->t_prev;
+    h.dt_last = ctx->dt_last;
+    h.prev_valid = ctx->prev_valid ? 1 : 0;
+    h.nseg = nseg;
+    const int slots[2] = {hs.cur, (hs.cur + 2) % 3};
+    std::vector<int64_t> off[2];
+    std::vector<Rec> recs[2];
+    for (int w = 0; w < 2; ++w) {
+        off[w].resize(nseg + 1);
+        CK(cudaMemcpyAsync(off[w].data(), ctx->d_segoff[slots[w]], (nseg + 1) * 8, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        h.count[w] = (w == 1 && !ctx->prev_valid) ? 0 : hs.count[slots[w]];
+        if (w == 1 && !ctx->prev_valid) std::fill(off[w].begin(), off[w].end(), 0);
+        recs[w].resize(h.count[w]);
+        if (h.count[w])
+            CK(cudaMemcpyAsync(recs[w].data(), ctx->d_pop[slots[w]], h.count[w] * sizeof(Rec), cudaMemcpyDeviceToHost,
+                               ctx->work));
+    }
+    CK(cudaStreamSynchronize(ctx->work));
+    uint64_t sum = 1469598103934665603ull;
+    sum = fnv(sum, &h, sizeof(h));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, QMC_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    for (int w = 0; w < 2 && ok; ++w) {
+        ok = ok && std::fwrite(off[w].data(), 8, off[w].size(), f) == off[w].size();
+        sum = fnv(sum, off[w].data(), off[w].size() * 8);
+        if (h.count[w]) {
+            ok = ok && std::fwrite(recs[w].data(), sizeof(Rec), recs[w].size(), f) == recs[w].size();
+            sum = fnv(sum, recs[w].data(), recs[w].size() * sizeof(Rec));
+        }
+    }
+    ok = ok && std::fwrite(&sum, 8, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, QMC_ERR_IO, "checkpoint write failed");
+    return leave(ctx);
+}
+
+int qmc_restore(qmc_ctx* ctx, const char* path)
+{
+    if (!ctx || !path) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_sched) return fail(ctx, QMC_ERR_STATE, "load the same schedule before restoring");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, QMC_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader h;
+    const int nseg = ctx->cfg.n_segments;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+    if (!ok || std::memcmp(h.magic, "QMCCKPT1", 8) != 0 || h.version != 1) {
+        std::fclose(f);
+        return fail(ctx, QMC_ERR_CHECKPOINT, "not a checkpoint of this library");
+    }
+    const uint64_t hash = schedule_hash(ctx->sched, ctx->cfg.seed, nseg, ctx->cfg.integrator, ctx->cfg.n_diag,
+                                        ctx->cfg.initiator_min);
+    if (h.hash != hash || h.nseg != nseg || h.n_qubits != ctx->cfg.n_qubits || h.count[0] < 0 || h.count[1] < 0 ||
+        h.count[0] > ((int64_t)1 << 34) || h.count[1] > ((int64_t)1 << 34)) {
+        std::fclose(f);
+        return fail(ctx, QMC_ERR_CHECKPOINT, "checkpoint from another configuration or schedule");
+    }
+    uint64_t sum = fnv(1469598103934665603ull, &h, sizeof(h));
+    std::vector<int64_t> off[2];
+    std::vector<Rec> recs[2];
+    for (int w = 0; w < 2 && ok; ++w) {
+        off[w].resize(nseg + 1);
+        ok = ok && std::fread(off[w].data(), 8, off[w].size(), f) == off[w].size();
+        sum = fnv(sum, off[w].data(), off[w].size() * 8);
+        recs[w].resize(h.count[w]);
+        if (h.count[w]) {
+            ok = ok && std::fread(recs[w].data(), sizeof(Rec), recs[w].size(), f) == recs[w].size();
+            sum = fnv(sum, recs[w].data(), recs[w].size() * sizeof(Rec));
+        }
+    }
+    uint64_t stored = 0;
+    ok = ok && std::fread(&stored, 8, 1, f) == 1;
+    std::fclose(f);
+    if (!ok || stored != sum) return fail(ctx, QMC_ERR_CHECKPOINT, "checkpoint truncated or checksum mismatch");
+    for (int w = 0; w < 2; ++w)
+        if (off[w][0] != 0 || off[w][nseg] != h.count[w])
+            return fail(ctx, QMC_ERR_CHECKPOINT, "inconsistent segment offsets");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    const int64_t need = std::max(h.count[0], h.count[1]);
+    if (need > ctx->pop_cap && (rc = grow_pop(ctx, need)) != QMC_OK) return rc;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    hs.cur = 0;
+    hs.count[0] = h.count[0];
+    hs.count[1] = 0;
+    hs.count[2] = h.count[1];
+    hs.step = h.step;
+    hs.error = 0;
+    const int slots[2] = {0, 2};
+    for (int w = 0; w < 2; ++w) {
+        if (h.count[w])
+            CK(cudaMemcpyAsync(ctx->d_pop[slots[w]], recs[w].data(), h.count[w] * sizeof(Rec), cudaMemcpyHostToDevice,
+                               ctx->work));
+        CK(cudaMemcpyAsync(ctx->d_segoff[slots[w]], off[w].data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+    }
+    CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    ctx->step = h.step;
+    ctx->t = h.t;
+    ctx->t_prev = h.t_prev;
+    ctx->dt_last = h.dt_last;
+    ctx->prev_valid = h.prev_valid != 0;
+    ctx->has_pop = true;
+    return leave(ctx);
+}
+
+} // extern "C"
+
+extern "C" {
+
+int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap, int32_t* n_kernels)
+{
+    if (!ctx || !kernel_ms || !n_kernels || cap < 0) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_sched || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!(dt > 0.0) || nsteps < 1) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 1");
+    *n_kernels = kNumTimedKernels;
+    for (int i = 0; i < cap && i < kNumTimedKernels; ++i) kernel_ms[i] = 0.0;
+    cudaEvent_t ev[kNumTimedKernels + 1];
+    for (int i = 0; i <= kNumTimedKernels; ++i) CK(cudaEventCreate(&ev[i]));
+    int rc = QMC_OK;
+    for (int64_t s = 0; s < nsteps && rc == QMC_OK; ++s) {
+        // one ordinary step first, so programs, capacities and the clock are handled as in qmc_step
+        // (a step that needs buffers to grow is redone there); then time the same launch sequence
+        rc = qmc_step(ctx, dt, 1);
+        if (rc != QMC_OK) break;
+        // replay the step just taken: restore the pre-step slot and clock on the device
+        DevState hs;
+        CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        DevState back = hs;
+        back.cur = (hs.cur + 2) % 3;
+        back.step = hs.step - 1;
+        back.call_index = 0;
+        CK(cudaMemcpyAsync(ctx->d_state, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->work));
+        StepParams P = params(ctx);
+        launch_step(P, ctx->grid, ctx->work, ev);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->work));
+        DevState after;
+        CK(cudaMemcpyAsync(&after, ctx->d_state, sizeof(after), cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        if (after.error || after.cur != hs.cur || after.count[hs.cur] != hs.count[hs.cur]) {
+            rc = fail(ctx, QMC_ERR_STATE, "profiled replay of a step did not reproduce it");
+            break;
+        }
+        for (int i = 0; i < kNumTimedKernels && i < cap; ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            kernel_ms[i] += ms;
+        }
+    }
+    for (int i = 0; i <= kNumTimedKernels; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+const char* qmc_kernel_name(int32_t i)
+{
+    if (i < 0 || i >= kNumTimedKernels) return "";
+    return kKernelNames[i];
+}
+
+} // extern "C"
+
+extern "C" int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out)
+{
+    if (!ctx || !out) return QMC_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    out[0] = hs.acc_steps;
+    out[1] = hs.acc_walkers;
+    out[2] = hs.acc_kcur;
+    out[3] = hs.acc_kprev;
+    out[4] = hs.acc_spawn;
+    out[5] = hs.acc_knext;
+    out[6] = hs.acc_heavy;
+    out[7] = 0;
+    if (reset) {
+        int64_t z[7] = {0, 0, 0, 0, 0, 0, 0};
+        CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, acc_steps), z, sizeof(z),
+                           cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+    }
+    return leave(ctx);
+}

@@ -1,0 +1,140 @@
+// Library-internal data layouts shared by the host code and the kernels.
+//
+// Population record (16 B): one occupied state |x><y| of one vector,
+//   key = (x << n) | y, value re + i im (int32 each) [walkers, Eq. (3)].
+// Spawn record (16 B): key, meta, val.  meta = segment << 2 | target << 1 |
+//   noninit, where target selects which component of the destination
+//   receives val (0: re, 1: im) and noninit marks a spawn from a parent below
+//   the initiator threshold [End Matter, simulation methodology].
+//
+// Column program: the column of dt_eff * L(t) at |x><y| [Eq. (2)] for one step
+// and one pass, in the 2^-52 fixed-point units of the expanded terms.  Terms
+// are grouped by destination mask (dx << n | dy); a group's element is a sum
+// of +-Q' over parity terms, the sign being the parity of popc(x & zl) +
+// popc(y & zr).  Single-qubit groups that differ only by the qubit form a
+// "family"; the per-qubit self (diagonal) parts form "self families".  Both
+// are evaluated with popcounts, so the spawn probability of a parent costs a
+// few integer operations regardless of n.
+#pragma once
+#include <stdint.h>
+
+namespace qmc {
+
+struct Rec {
+    uint64_t key;
+    int32_t re, im;
+};
+
+struct SRec {
+    uint64_t key;
+    uint32_t meta;
+    int32_t val;
+};
+
+static_assert(sizeof(Rec) == 16, "population record must be 16 bytes");
+static_assert(sizeof(SRec) == 16, "spawn record must be 16 bytes");
+
+// ---- column program --------------------------------------------------------
+struct ProgHeader {
+    int32_t n_selffam, n_selfgen, n_fam, n_gen, n_gterm, n_entry;
+    int32_t off_selffam, off_selfgen, off_fam, off_gen, off_gterm, off_entry;
+    int64_t self_const_re, self_const_im; // parity-free part of the diagonal element
+    int64_t p_const;                      // sum of |Re| + |Im| over constant groups
+    int32_t bytes;                        // size of the whole blob
+    int32_t n_nonconst_gen;               // generic groups come non-constant first
+};
+
+// Self-family parity term: Q' * (|M| - 2 popc(pat & M)), pat = x, y or x ^ y.
+struct SelfFam {
+    uint32_t members;
+    uint32_t type; // 0: zl = e_q (pattern x); 1: zr = e_q (y); 2: both (x ^ y)
+    int64_t qre, qim;
+};
+
+// Self generic parity term (multi-qubit Z parity on the diagonal element).
+struct SelfGen {
+    uint32_t zl, zr;
+    int64_t qre, qim;
+};
+
+// Family of single-qubit groups: member q has destination mask
+// (alpha e_q) << n | (beta e_q) and element tab[pi], pi = 2 x_q + y_q.
+struct Fam {
+    uint32_t members;
+    uint32_t ab;   // bit 1: alpha (ket flips q), bit 0: beta (bra flips q)
+    int64_t a[4];  // |Re tab| + |Im tab|
+    int64_t tre[4], tim[4];
+};
+
+// Generic group: element = sum over terms [first, first + count) of +-Q'.
+struct Gen {
+    uint64_t mask_key;
+    int32_t first, count;
+    int32_t is_const, pad;
+    int64_t cre, cim; // the element when is_const
+};
+
+struct GTerm {
+    uint32_t zl, zr;
+    int64_t qre, qim;
+};
+
+// Destinations of the column in ascending mask order (the canonical order of
+// the multinomial choice).  kind 0: diagonal (mask 0); 1: family member
+// (idx = fam | q << 16); 2: generic group (idx = gen).
+struct Entry {
+    uint64_t mask_key;
+    uint32_t kind;
+    uint32_t idx;
+};
+
+// ---- device-resident step state ---------------------------------------------
+enum DevError : uint32_t {
+    DERR_NONE = 0,
+    DERR_SPAWN_CAPACITY = 1,
+    DERR_POP_CAPACITY = 2,
+    DERR_DT_TOO_LARGE = 3,
+    DERR_POP_OVERFLOW = 4,
+    DERR_TIMEOUT = 5,
+    DERR_HEAVY_CAPACITY = 6,
+    DERR_TILE_CAPACITY = 7,
+};
+
+constexpr int kMaxTileCounters = 32;
+
+struct DevState {
+    uint64_t step;        // global index of the next step
+    int64_t count[3];     // records in population slots 0..2
+    int32_t cur;          // slot of N(t); N(t - dt) is (cur + 2) % 3, output (cur + 1) % 3
+    int32_t call_index;   // step index inside the current qmc_step call
+    uint32_t error;       // sticky DevError
+    uint32_t error_aux;
+    int64_t spawn_total;  // spawn records requested this step
+    int64_t heavy_total;  // heavy work items requested this step
+    int64_t next_total;   // records produced by the merge this step
+    int64_t merge_tiles;  // merge tiles this step
+    int64_t max_spawn;    // high-water marks
+    int64_t max_next;
+    int64_t max_heavy;
+    int64_t max_tiles;
+    // cumulative counters since the last reset (qmc_counters)
+    int64_t acc_steps;
+    int64_t acc_walkers;  // sum over steps of N_tot of N(t + dt), all vectors
+    int64_t acc_kcur;     // parents read from N(t)
+    int64_t acc_kprev;    // parents read from N(t - dt) (AB2 steps)
+    int64_t acc_spawn;    // spawn records written
+    int64_t acc_knext;    // records written to N(t + dt)
+    int64_t acc_heavy;    // heavy work items
+    uint32_t seq;         // look-back epoch base, advanced by 16 every step
+    uint32_t pad2;
+    uint32_t tile_ctr[kMaxTileCounters];
+};
+
+// Per-step flags prepared by the host for each step of a call.
+struct StepInfo {
+    int64_t prog_off[2];  // byte offset of the pass-0 / pass-1 program, -1 if absent
+    int32_t ab2;          // 1: AB2 step (pass 1 over N(t - dt) present)
+    int32_t pad;
+};
+
+} // namespace qmc

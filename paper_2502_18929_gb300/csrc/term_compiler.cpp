@@ -1,0 +1,388 @@
+// Host term compiler [Eq. (1), Eq. (2)].
+//
+// Expansion (per step, pass scale dt_eff; every expanded coefficient is
+// rounded on its own to the 2^-52 grid, so element sums are exact integers):
+//   -i[H, rho], term h P with s = rate(t) dt_eff, v = h s:
+//       (-i v) P rho         and   (+i v) rho P
+//   gamma(t) (L rho L^dag - 1/2 L^dag L rho - 1/2 rho L^dag L),
+//   L = sum_a l_a P_a, s = gamma(t) dt_eff, hs = -s/2, for ordered pairs (a, b),
+//   z = l_a conj(l_b):
+//       (s z) P_a rho P_b
+//       (hs conj z) (P_a P_b) rho   and   (hs conj z) rho (P_a P_b)
+// A term c P_L rho P_R sends |x><y| to
+//   c i^{nY(L)} (-i)^{nY(R)} (-1)^{popc(x & zL) + popc(y & zR)} |x^xL><y^xR|,
+// nY = number of Y letters; the phase is folded into the stored Q'.
+//
+// Compiled with -ffp-contract=off: each product and sum above is rounded
+// exactly as written.
+#include "term_compiler.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <utility>
+
+#include "qmc_types.h"
+
+namespace qmc {
+namespace {
+
+constexpr double kOne52 = 4503599627370496.0;       // 2^52
+constexpr double kLimit62 = 4611686018427387904.0;  // 2^62
+
+struct Raw {
+    uint32_t xl, zl, xr, zr;
+    int64_t qre, qim;
+};
+
+inline int popc(uint32_t v) { return __builtin_popcount(v); }
+
+inline void rot(int64_t* re, int64_t* im, int k)
+{
+    int64_t a = *re, b = *im;
+    switch (k & 3) {
+    case 0: break;
+    case 1: *re = -b; *im = a; break;
+    case 2: *re = -a; *im = -b; break;
+    default: *re = b; *im = -a; break;
+    }
+}
+
+int quantise(double re, double im, int64_t* qre, int64_t* qim)
+{
+    double a = re * kOne52, b = im * kOne52;
+    if (!(std::fabs(a) < kLimit62) || !(std::fabs(b) < kLimit62)) return QMC_ERR_COEF_RANGE;
+    *qre = (int64_t)std::nearbyint(a);
+    *qim = (int64_t)std::nearbyint(b);
+    return QMC_OK;
+}
+
+double rate_value(const Schedule& s, int id, double t)
+{
+    const qmc_rate& r = s.rates[id];
+    if (r.kind == QMC_RATE_COS) return r.a * std::cos(r.b * t + r.c);
+    return r.a;
+}
+
+bool window_on(const Schedule& s, int id, double t)
+{
+    if (id < 0) return true;
+    return s.windows[id].t0 <= t && t < s.windows[id].t1;
+}
+
+// letter index: 0 I, 1 X, 2 Y, 3 Z
+inline int letter(uint32_t x, uint32_t z, int q)
+{
+    int xb = (x >> q) & 1, zb = (z >> q) & 1;
+    if (xb && zb) return 2;
+    if (xb) return 1;
+    if (zb) return 3;
+    return 0;
+}
+
+// P_a P_b = i^k P_c for Hermitian Pauli strings.
+void pauli_mul(int n, uint32_t xa, uint32_t za, uint32_t xb, uint32_t zb, uint32_t* xc,
+               uint32_t* zc, int* k)
+{
+    int kk = 0;
+    for (int q = 0; q < n; ++q) {
+        int la = letter(xa, za, q), lb = letter(xb, zb, q);
+        if (la == 0 || lb == 0 || la == lb) continue;
+        kk += (lb == la % 3 + 1) ? 1 : 3; // XY = iZ, YZ = iX, ZX = iY
+    }
+    *xc = xa ^ xb;
+    *zc = za ^ zb;
+    *k = kk & 3;
+}
+
+int expand(const Schedule& s, double t, double dt_eff, std::vector<Raw>* out)
+{
+    out->clear();
+    int rc;
+    for (const qmc_ham_term& h : s.ham) {
+        if (!window_on(s, h.window_id, t)) continue;
+        double sc = rate_value(s, h.rate_id, t) * dt_eff;
+        double v = h.h * sc;
+        uint32_t xm = (uint32_t)h.xm, zm = (uint32_t)h.zm;
+        int ny = popc(xm & zm);
+        Raw a{xm, zm, 0, 0, 0, 0}, b{0, 0, xm, zm, 0, 0};
+        if ((rc = quantise(0.0, -v, &a.qre, &a.qim)) != QMC_OK) return rc;
+        if ((rc = quantise(0.0, v, &b.qre, &b.qim)) != QMC_OK) return rc;
+        rot(&a.qre, &a.qim, ny);
+        rot(&b.qre, &b.qim, 4 - (ny & 3));
+        out->push_back(a);
+        out->push_back(b);
+    }
+    for (const qmc_lindblad& L : s.lind) {
+        if (!window_on(s, L.window_id, t)) continue;
+        double sc = rate_value(s, L.rate_id, t) * dt_eff;
+        double hs = -0.5 * sc;
+        for (int ia = 0; ia < L.count; ++ia) {
+            const qmc_pauli_coef& la = s.coefs[L.first + ia];
+            for (int ib = 0; ib < L.count; ++ib) {
+                const qmc_pauli_coef& lb = s.coefs[L.first + ib];
+                double zre = la.re * lb.re + la.im * lb.im;
+                double zim = la.im * lb.re - la.re * lb.im;
+                uint32_t xa = (uint32_t)la.xm, za = (uint32_t)la.zm;
+                uint32_t xb = (uint32_t)lb.xm, zb = (uint32_t)lb.zm;
+                Raw j{xa, za, xb, zb, 0, 0};
+                if ((rc = quantise(sc * zre, sc * zim, &j.qre, &j.qim)) != QMC_OK) return rc;
+                rot(&j.qre, &j.qim, popc(xa & za) - popc(xb & zb) + 4);
+                out->push_back(j);
+                int64_t cre, cim;
+                if ((rc = quantise(hs * zre, -(hs * zim), &cre, &cim)) != QMC_OK) return rc;
+                uint32_t xc, zc;
+                int k;
+                pauli_mul(s.n, xa, za, xb, zb, &xc, &zc, &k);
+                int nyc = popc(xc & zc);
+                Raw l{xc, zc, 0, 0, cre, cim}, r{0, 0, xc, zc, cre, cim};
+                rot(&l.qre, &l.qim, k + nyc);
+                rot(&r.qre, &r.qim, k - nyc + 4);
+                out->push_back(l);
+                out->push_back(r);
+            }
+        }
+    }
+    return QMC_OK;
+}
+
+template <typename T>
+void put(std::vector<uint8_t>* blob, size_t at, const T* src, size_t count)
+{
+    if (count) std::memcpy(blob->data() + at, src, count * sizeof(T));
+}
+
+size_t align8(size_t v) { return (v + 7) & ~(size_t)7; }
+
+} // namespace
+
+int validate_schedule(const Schedule& s, std::string* why)
+{
+    const uint64_t lim = (s.n >= 64) ? ~0ull : ((1ull << s.n) - 1);
+    auto bad = [&](const char* m) { if (why) *why = m; return QMC_ERR_INVALID_ARG; };
+    for (const auto& r : s.rates)
+        if (r.kind != QMC_RATE_CONST && r.kind != QMC_RATE_COS) return bad("unknown rate kind");
+    for (const auto& w : s.windows)
+        if (!(w.t0 <= w.t1)) return bad("window with t0 > t1");
+    for (const auto& h : s.ham) {
+        if (h.rate_id < 0 || h.rate_id >= (int)s.rates.size()) return bad("hamiltonian rate id");
+        if (h.window_id < -1 || h.window_id >= (int)s.windows.size()) return bad("hamiltonian window id");
+        if ((h.xm & ~lim) || (h.zm & ~lim)) return bad("hamiltonian mask beyond n qubits");
+    }
+    for (const auto& L : s.lind) {
+        if (L.rate_id < 0 || L.rate_id >= (int)s.rates.size()) return bad("lindblad rate id");
+        if (L.window_id < -1 || L.window_id >= (int)s.windows.size()) return bad("lindblad window id");
+        if (L.first < 0 || L.count < 1 || L.first + L.count > (int)s.coefs.size())
+            return bad("lindblad coefficient range");
+    }
+    for (const auto& c : s.coefs)
+        if ((c.xm & ~lim) || (c.zm & ~lim)) return bad("lindblad mask beyond n qubits");
+    return QMC_OK;
+}
+
+double spawn_prob_bound(const Schedule& s, double t, double dt_eff)
+{
+    std::vector<Raw> raw;
+    if (expand(s, t, dt_eff, &raw) != QMC_OK) return INFINITY;
+    double acc = 0.0;
+    for (const Raw& r : raw) acc += (std::fabs((double)r.qre) + std::fabs((double)r.qim)) / kOne52;
+    return acc;
+}
+
+int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_t>* blob)
+{
+    const int n = s.n;
+    std::vector<Raw> raw;
+    int rc = expand(s, t, dt_eff, &raw);
+    if (rc != QMC_OK) return rc;
+
+    // group by destination mask, merge equal parity terms (exact sums)
+    std::map<uint64_t, std::map<std::pair<uint32_t, uint32_t>, std::pair<int64_t, int64_t>>> groups;
+    for (const Raw& r : raw) {
+        uint64_t mk = ((uint64_t)r.xl << n) | (uint64_t)r.xr;
+        auto& g = groups[mk][{r.zl, r.zr}];
+        g.first += r.qre;
+        g.second += r.qim;
+    }
+
+    ProgHeader hdr;
+    std::memset(&hdr, 0, sizeof(hdr));
+    std::vector<SelfFam> selffam;
+    std::vector<SelfGen> selfgen;
+    std::vector<Fam> fams;
+    std::vector<Gen> gen_nc, gen_c;
+    std::vector<std::vector<GTerm>> gen_terms_nc, gen_terms_c;
+
+    // diagonal (self) group
+    {
+        std::map<std::tuple<uint32_t, int64_t, int64_t>, uint32_t> sf; // (type, q) -> members
+        auto it = groups.find(0);
+        if (it != groups.end()) {
+            for (const auto& kv : it->second) {
+                uint32_t zl = kv.first.first, zr = kv.first.second;
+                int64_t qre = kv.second.first, qim = kv.second.second;
+                if (qre == 0 && qim == 0) continue;
+                if (zl == 0 && zr == 0) {
+                    hdr.self_const_re += qre;
+                    hdr.self_const_im += qim;
+                } else if (zr == 0 && popc(zl) == 1) {
+                    sf[{0u, qre, qim}] |= zl;
+                } else if (zl == 0 && popc(zr) == 1) {
+                    sf[{1u, qre, qim}] |= zr;
+                } else if (zl == zr && popc(zl) == 1) {
+                    sf[{2u, qre, qim}] |= zl;
+                } else {
+                    selfgen.push_back(SelfGen{zl, zr, qre, qim});
+                }
+            }
+            groups.erase(it);
+        }
+        for (const auto& kv : sf)
+            selffam.push_back(SelfFam{kv.second, std::get<0>(kv.first), std::get<1>(kv.first),
+                                      std::get<2>(kv.first)});
+    }
+
+    // off-diagonal groups: single-qubit families or generic groups
+    std::map<std::vector<int64_t>, uint32_t> famkeys; // (ab, tre[4], tim[4]) -> members
+    for (const auto& gkv : groups) {
+        uint64_t mk = gkv.first;
+        uint32_t xl = (uint32_t)(mk >> n), xr = (uint32_t)(mk & ((n == 32) ? 0xFFFFFFFFull : ((1ull << n) - 1)));
+        uint32_t qm = xl | xr;
+        bool single = popc(qm) == 1;
+        std::vector<GTerm> terms;
+        for (const auto& kv : gkv.second) {
+            if (kv.second.first == 0 && kv.second.second == 0) continue;
+            terms.push_back(GTerm{kv.first.first, kv.first.second, kv.second.first, kv.second.second});
+            if ((kv.first.first & ~qm) || (kv.first.second & ~qm)) single = false;
+        }
+        if (terms.empty()) continue;
+        if (single) {
+            int q = __builtin_ctz(qm);
+            int64_t tre[4] = {0, 0, 0, 0}, tim[4] = {0, 0, 0, 0};
+            for (int pi = 0; pi < 4; ++pi) {
+                int xq = pi >> 1, yq = pi & 1;
+                for (const GTerm& g : terms) {
+                    int par = (xq & ((g.zl >> q) & 1)) ^ (yq & ((g.zr >> q) & 1));
+                    tre[pi] += par ? -g.qre : g.qre;
+                    tim[pi] += par ? -g.qim : g.qim;
+                }
+            }
+            bool allzero = true;
+            for (int pi = 0; pi < 4; ++pi) allzero = allzero && tre[pi] == 0 && tim[pi] == 0;
+            if (allzero) continue;
+            uint32_t ab = ((xl != 0) ? 2u : 0u) | ((xr != 0) ? 1u : 0u);
+            std::vector<int64_t> key = {(int64_t)ab, tre[0], tre[1], tre[2], tre[3],
+                                        tim[0], tim[1], tim[2], tim[3]};
+            famkeys[key] |= qm;
+            continue;
+        }
+        bool is_const = true;
+        for (const GTerm& g : terms) is_const = is_const && g.zl == 0 && g.zr == 0;
+        Gen G{};
+        G.mask_key = mk;
+        G.is_const = is_const ? 1 : 0;
+        if (is_const) {
+            for (const GTerm& g : terms) { G.cre += g.qre; G.cim += g.qim; }
+            if (G.cre == 0 && G.cim == 0) continue;
+            gen_c.push_back(G);
+            gen_terms_c.push_back(terms);
+        } else {
+            gen_nc.push_back(G);
+            gen_terms_nc.push_back(terms);
+        }
+    }
+    for (const auto& kv : famkeys) {
+        Fam f{};
+        f.members = kv.second;
+        f.ab = (uint32_t)kv.first[0];
+        for (int pi = 0; pi < 4; ++pi) {
+            f.tre[pi] = kv.first[1 + pi];
+            f.tim[pi] = kv.first[5 + pi];
+            f.a[pi] = std::llabs(f.tre[pi]) + std::llabs(f.tim[pi]);
+        }
+        fams.push_back(f);
+    }
+
+    std::vector<Gen> gens;
+    std::vector<GTerm> gterms;
+    hdr.n_nonconst_gen = (int32_t)gen_nc.size();
+    for (size_t i = 0; i < gen_nc.size(); ++i) {
+        Gen g = gen_nc[i];
+        g.first = (int32_t)gterms.size();
+        g.count = (int32_t)gen_terms_nc[i].size();
+        gterms.insert(gterms.end(), gen_terms_nc[i].begin(), gen_terms_nc[i].end());
+        gens.push_back(g);
+    }
+    for (size_t i = 0; i < gen_c.size(); ++i) {
+        Gen g = gen_c[i];
+        g.first = (int32_t)gterms.size();
+        g.count = (int32_t)gen_terms_c[i].size();
+        gterms.insert(gterms.end(), gen_terms_c[i].begin(), gen_terms_c[i].end());
+        hdr.p_const += std::llabs(g.cre) + std::llabs(g.cim);
+        gens.push_back(g);
+    }
+
+    // destinations in ascending mask order (the multinomial's canonical order)
+    std::vector<Entry> entries;
+    entries.push_back(Entry{0ull, 0u, 0u});
+    for (size_t f = 0; f < fams.size(); ++f) {
+        uint32_t m = fams[f].members;
+        while (m) {
+            int q = __builtin_ctz(m);
+            m &= m - 1;
+            uint64_t mk = (((fams[f].ab >> 1) & 1ull) << (q + n)) | ((uint64_t)(fams[f].ab & 1u) << q);
+            entries.push_back(Entry{mk, 1u, (uint32_t)f | ((uint32_t)q << 16)});
+        }
+    }
+    for (size_t g = 0; g < gens.size(); ++g) entries.push_back(Entry{gens[g].mask_key, 2u, (uint32_t)g});
+    std::sort(entries.begin(), entries.end(),
+              [](const Entry& a, const Entry& b) { return a.mask_key < b.mask_key; });
+
+    hdr.n_selffam = (int32_t)selffam.size();
+    hdr.n_selfgen = (int32_t)selfgen.size();
+    hdr.n_fam = (int32_t)fams.size();
+    hdr.n_gen = (int32_t)gens.size();
+    hdr.n_gterm = (int32_t)gterms.size();
+    hdr.n_entry = (int32_t)entries.size();
+
+    size_t base = align8(blob->size());
+    size_t off = align8(sizeof(ProgHeader));
+    hdr.off_selffam = (int32_t)off; off = align8(off + selffam.size() * sizeof(SelfFam));
+    hdr.off_selfgen = (int32_t)off; off = align8(off + selfgen.size() * sizeof(SelfGen));
+    hdr.off_fam = (int32_t)off;     off = align8(off + fams.size() * sizeof(Fam));
+    hdr.off_gen = (int32_t)off;     off = align8(off + gens.size() * sizeof(Gen));
+    hdr.off_gterm = (int32_t)off;   off = align8(off + gterms.size() * sizeof(GTerm));
+    hdr.off_entry = (int32_t)off;   off = align8(off + entries.size() * sizeof(Entry));
+    hdr.bytes = (int32_t)off;
+    blob->resize(base + off, 0);
+    put(blob, base, &hdr, 1);
+    put(blob, base + hdr.off_selffam, selffam.data(), selffam.size());
+    put(blob, base + hdr.off_selfgen, selfgen.data(), selfgen.size());
+    put(blob, base + hdr.off_fam, fams.data(), fams.size());
+    put(blob, base + hdr.off_gen, gens.data(), gens.size());
+    put(blob, base + hdr.off_gterm, gterms.data(), gterms.size());
+    put(blob, base + hdr.off_entry, entries.data(), entries.size());
+    return QMC_OK;
+}
+
+uint64_t schedule_hash(const Schedule& s, uint64_t seed, int32_t nseg, int32_t integrator,
+                       int64_t n_diag, int64_t init_min)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t len) {
+        const uint8_t* b = (const uint8_t*)p;
+        for (size_t i = 0; i < len; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    mix(&s.n, sizeof(s.n));
+    for (const auto& v : s.ham) { mix(&v.h, 8); mix(&v.xm, 8); mix(&v.zm, 8); mix(&v.rate_id, 4); mix(&v.window_id, 4); }
+    for (const auto& v : s.lind) { mix(&v.first, 4); mix(&v.count, 4); mix(&v.rate_id, 4); mix(&v.window_id, 4); }
+    for (const auto& v : s.coefs) { mix(&v.re, 8); mix(&v.im, 8); mix(&v.xm, 8); mix(&v.zm, 8); }
+    for (const auto& v : s.rates) { mix(&v.kind, 4); mix(&v.a, 8); mix(&v.b, 8); mix(&v.c, 8); }
+    for (const auto& v : s.windows) { mix(&v.t0, 8); mix(&v.t1, 8); }
+    mix(&seed, 8); mix(&nseg, 4); mix(&integrator, 4); mix(&n_diag, 8); mix(&init_min, 8);
+    return h;
+}
+
+} // namespace qmc

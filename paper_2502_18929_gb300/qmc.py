@@ -1,0 +1,328 @@
+"""ctypes binding of ``libqmc_gb300.so`` (include/qmc.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module
+converts NumPy / torch arguments to the C structs and back.  There is no CPU
+fallback: importing works without a GPU, but creating a context fails loudly
+if the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CAPACITY = -3
+ERR_DT_TOO_LARGE = -4
+ERR_POP_OVERFLOW = -5
+ERR_DEVICE_TIMEOUT = -6
+ERR_CUDA = -7
+ERR_STATE = -8
+ERR_COEF_RANGE = -9
+ERR_IO = -10
+ERR_CHECKPOINT = -11
+
+EULER = 0
+AB2 = 1
+
+EXPORTED = [
+    "qmc_create", "qmc_destroy", "qmc_last_error", "qmc_load_schedule", "qmc_init_populations",
+    "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
+    "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
+    "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters",
+]
+
+
+class QmcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_segments", C.c_int32), ("integrator", C.c_int32),
+                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("n_diag", C.c_int64),
+                ("initiator_min", C.c_int64), ("capacity_hint", C.c_int64), ("max_records", C.c_int64),
+                ("cuda_stream", C.c_void_p)]
+
+
+class HamTerm(C.Structure):
+    _fields_ = [("h", C.c_double), ("xm", C.c_uint64), ("zm", C.c_uint64), ("rate_id", C.c_int32),
+                ("window_id", C.c_int32)]
+
+
+class PauliCoef(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double), ("xm", C.c_uint64), ("zm", C.c_uint64)]
+
+
+class Lindblad(C.Structure):
+    _fields_ = [("first", C.c_int32), ("count", C.c_int32), ("rate_id", C.c_int32), ("window_id", C.c_int32)]
+
+
+class Rate(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("c", C.c_double)]
+
+
+class Window(C.Structure):
+    _fields_ = [("t0", C.c_double), ("t1", C.c_double)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("n_records", C.c_int64), ("n_walkers", C.c_int64), ("n_diag_re", C.c_int64),
+                ("n_diag_im", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        L.qmc_create.argtypes = [C.POINTER(vp), C.POINTER(Config)]
+        L.qmc_destroy.argtypes = [vp]
+        L.qmc_destroy.restype = None
+        L.qmc_last_error.argtypes = [vp]
+        L.qmc_last_error.restype = C.c_char_p
+        L.qmc_load_schedule.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp,
+                                        C.c_int32]
+        L.qmc_init_populations.argtypes = [vp, vp, vp, vp, vp, C.c_int64]
+        L.qmc_set_populations.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
+        L.qmc_set_clock.argtypes = [vp, C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_int32]
+        L.qmc_get_clock.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.qmc_step.argtypes = [vp, C.c_double, C.c_int64]
+        L.qmc_spawn_prob_bound.argtypes = [vp, C.c_double, C.c_double, vp]
+        L.qmc_observables.argtypes = [vp, vp]
+        L.qmc_step_history.argtypes = [vp, vp, C.c_int64, vp]
+        L.qmc_export.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int64, vp]
+        L.qmc_overlap.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int32, vp, vp]
+        L.qmc_checkpoint.argtypes = [vp, C.c_char_p]
+        L.qmc_restore.argtypes = [vp, C.c_char_p]
+        L.qmc_step_profile.argtypes = [vp, C.c_double, C.c_int64, vp, C.c_int32, vp]
+        L.qmc_counters.argtypes = [vp, C.c_int32, vp]
+        L.qmc_kernel_name.argtypes = [C.c_int32]
+        L.qmc_kernel_name.restype = C.c_char_p
+        for name in EXPORTED:
+            if name not in ("qmc_destroy", "qmc_last_error", "qmc_kernel_name", "qmc_column_eval"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _ptr(a):
+    return a.ctypes.data if a.size else None
+
+
+def current_stream_handle() -> int:
+    """The torch current CUDA stream (0 = legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+class QMC:
+    """One context: ``n_segments`` independent population vectors of one problem."""
+
+    def __init__(self, n_qubits: int, n_segments: int, seed: int, n_diag: int, integrator: int = AB2,
+                 initiator_min: int = 0, capacity_hint: int = 0, max_records: int = 0, stream: int | None = None):
+        self.L = lib()
+        self.n = n_qubits
+        self.nseg = n_segments
+        self.n_diag = n_diag
+        cfg = Config(n_qubits, n_segments, integrator, 0, seed, n_diag, initiator_min, capacity_hint,
+                     max_records, C.c_void_p(current_stream_handle() if stream is None else stream))
+        h = C.c_void_p()
+        rc = self.L.qmc_create(C.byref(h), C.byref(cfg))
+        if rc != OK:
+            raise QmcError(rc, "qmc_create failed (is a CUDA device present?)")
+        self.h = h
+
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            raise QmcError(rc, f"{what}: {self.L.qmc_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- problem -------------------------------------------------------------
+    def load_schedule(self, prob):
+        ham = (HamTerm * max(1, len(prob.ham)))(*[HamTerm(h, xm, zm, r, w) for h, xm, zm, r, w in prob.ham])
+        coefs, linds = [], []
+        for ops, r, w in prob.lind:
+            linds.append(Lindblad(len(coefs), len(ops), r, w))
+            for coef, xm, zm in ops:
+                coefs.append(PauliCoef(coef.real, coef.imag, xm, zm))
+        lind = (Lindblad * max(1, len(linds)))(*linds)
+        cf = (PauliCoef * max(1, len(coefs)))(*coefs)
+        rates = (Rate * max(1, len(prob.rates)))(*[Rate(k, 0, a, b, c) for k, a, b, c in prob.rates])
+        wins = (Window * max(1, len(prob.windows)))(*[Window(a, b) for a, b in prob.windows])
+        self._check(self.L.qmc_load_schedule(self.h, ham, len(prob.ham), lind, len(linds), cf, len(coefs),
+                                             rates, len(prob.rates), wins, len(prob.windows)),
+                    "qmc_load_schedule")
+
+    def init_populations(self, rho0):
+        x = _arr([e[0] for e in rho0], np.uint64)
+        y = _arr([e[1] for e in rho0], np.uint64)
+        re = _arr([e[2] for e in rho0], np.float64)
+        im = _arr([e[3] for e in rho0], np.float64)
+        self._check(self.L.qmc_init_populations(self.h, _ptr(x), _ptr(y), _ptr(re), _ptr(im), len(x)),
+                    "qmc_init_populations")
+
+    def set_populations(self, pops, which: int = 0):
+        """``pops``: list (one per vector) of (keys ascending, re, im)."""
+        counts = _arr([len(p[0]) for p in pops], np.int64)
+        keys = _arr(np.concatenate([np.asarray(p[0], dtype=np.uint64) for p in pops]), np.uint64)
+        re = _arr(np.concatenate([np.asarray(p[1], dtype=np.int32) for p in pops]), np.int32)
+        im = _arr(np.concatenate([np.asarray(p[2], dtype=np.int32) for p in pops]), np.int32)
+        self._check(self.L.qmc_set_populations(self.h, which, _ptr(counts), _ptr(keys), _ptr(re), _ptr(im)),
+                    "qmc_set_populations")
+
+    def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
+                  prev_valid: bool = False):
+        self._check(self.L.qmc_set_clock(self.h, step, t, t_prev, dt_last, int(prev_valid)), "qmc_set_clock")
+
+    def clock(self):
+        step = C.c_uint64()
+        t, tp, dl = C.c_double(), C.c_double(), C.c_double()
+        pv = C.c_int32()
+        self._check(self.L.qmc_get_clock(self.h, C.byref(step), C.byref(t), C.byref(tp), C.byref(dl),
+                                         C.byref(pv)), "qmc_get_clock")
+        return step.value, t.value, tp.value, dl.value, bool(pv.value)
+
+    def set_time(self, t: float):
+        step, _, tp, dl, pv = self.clock()
+        self.set_clock(step, t, tp, dl, pv)
+
+    # -- hot path --------------------------------------------------------------
+    def step(self, dt: float, nsteps: int = 1):
+        self._check(self.L.qmc_step(self.h, dt, nsteps), "qmc_step")
+
+    def step_rc(self, dt: float, nsteps: int = 1) -> int:
+        return self.L.qmc_step(self.h, dt, nsteps)
+
+    def step_profile(self, dt: float, nsteps: int = 1) -> dict:
+        """Per-kernel milliseconds summed over nsteps steps (CUDA events)."""
+        ms = np.zeros(32, dtype=np.float64)
+        nk = C.c_int32()
+        self._check(self.L.qmc_step_profile(self.h, dt, nsteps, ms.ctypes.data, 32, C.byref(nk)),
+                    "qmc_step_profile")
+        return {self.L.qmc_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+
+    def counters(self, reset: bool = False) -> dict:
+        """Cumulative device totals since the last reset (see qmc_counters)."""
+        out = np.zeros(8, dtype=np.int64)
+        self._check(self.L.qmc_counters(self.h, int(reset), out.ctypes.data), "qmc_counters")
+        names = ["steps", "walker_steps", "k_cur", "k_prev", "spawns", "k_next", "heavy_items"]
+        return {k: int(v) for k, v in zip(names, out)}
+
+    def spawn_prob_bound(self, t: float, dt: float) -> float:
+        p = C.c_double()
+        self._check(self.L.qmc_spawn_prob_bound(self.h, t, dt, C.byref(p)), "qmc_spawn_prob_bound")
+        return p.value
+
+    # -- results --------------------------------------------------------------
+    def observables(self) -> np.ndarray:
+        """(n_segments, 4) int64: K, N_tot, Re N^diag, Im N^diag."""
+        out = np.zeros((self.nseg, 4), dtype=np.int64)
+        self._check(self.L.qmc_observables(self.h, out.ctypes.data), "qmc_observables")
+        return out
+
+    def step_history(self, cap_steps: int = 1 << 20) -> np.ndarray:
+        """(steps, n_segments, 4) int64 for every step of the last ``step`` call."""
+        _, _, _, _, _ = self.clock()
+        buf = np.zeros((max(1, min(cap_steps, 1 << 22)), self.nseg, 4), dtype=np.int64)
+        cnt = C.c_int64()
+        self._check(self.L.qmc_step_history(self.h, buf.ctypes.data, buf.shape[0], C.byref(cnt)),
+                    "qmc_step_history")
+        return buf[:cnt.value]
+
+    def export(self, seg: int, which: int = 0):
+        cnt = C.c_int64()
+        rc = self.L.qmc_export(self.h, seg, which, None, None, None, 0, C.byref(cnt))
+        if rc not in (OK, ERR_INVALID_ARG):
+            self._check(rc, "qmc_export")
+        n = cnt.value
+        keys = np.zeros(n, dtype=np.uint64)
+        re = np.zeros(n, dtype=np.int32)
+        im = np.zeros(n, dtype=np.int32)
+        self._check(self.L.qmc_export(self.h, seg, which, _ptr(keys), _ptr(re), _ptr(im), n, C.byref(cnt)),
+                    "qmc_export")
+        return keys, re, im
+
+    def overlap(self, seg: int, psi: dict) -> complex:
+        idx = _arr(list(psi.keys()), np.uint64)
+        vals = np.array([complex(v) for v in psi.values()])
+        pr = _arr(vals.real, np.float64)
+        pi = _arr(vals.imag, np.float64)
+        orr, oi = C.c_double(), C.c_double()
+        self._check(self.L.qmc_overlap(self.h, seg, _ptr(idx), _ptr(pr), _ptr(pi), len(idx), C.byref(orr),
+                                       C.byref(oi)), "qmc_overlap")
+        return complex(orr.value, oi.value)
+
+    def checkpoint(self, path: str):
+        self._check(self.L.qmc_checkpoint(self.h, path.encode()), "qmc_checkpoint")
+
+    def restore(self, path: str):
+        self._check(self.L.qmc_restore(self.h, path.encode()), "qmc_restore")
+
+
+def column_eval(prob, x: int, y: int, t: float, dt_eff: float, cap: int = 4096):
+    """Host evaluation of the compiled column (qmc_column_eval): destinations in
+    canonical order as (mask, re, im) in 2^-52 units, and the spawn weight P."""
+    L = lib()
+    ham = (HamTerm * max(1, len(prob.ham)))(*[HamTerm(h, xm, zm, r, w) for h, xm, zm, r, w in prob.ham])
+    coefs, linds = [], []
+    for ops, r, w in prob.lind:
+        linds.append(Lindblad(len(coefs), len(ops), r, w))
+        for coef, xm, zm in ops:
+            coefs.append(PauliCoef(coef.real, coef.imag, xm, zm))
+    lind = (Lindblad * max(1, len(linds)))(*linds)
+    cf = (PauliCoef * max(1, len(coefs)))(*coefs)
+    rates = (Rate * max(1, len(prob.rates)))(*[Rate(k, 0, a, b, c) for k, a, b, c in prob.rates])
+    wins = (Window * max(1, len(prob.windows)))(*[Window(a, b) for a, b in prob.windows])
+    mask = np.zeros(cap, dtype=np.uint64)
+    vre = np.zeros(cap, dtype=np.int64)
+    vim = np.zeros(cap, dtype=np.int64)
+    p = C.c_int64()
+    vp = C.c_void_p
+    L.qmc_column_eval.argtypes = [C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp,
+                                  C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_int32, vp, vp, vp,
+                                  vp]
+    L.qmc_column_eval.restype = C.c_int
+    ne = L.qmc_column_eval(prob.n, ham, len(prob.ham), lind, len(linds), cf, len(coefs), rates, len(prob.rates),
+                           wins, len(prob.windows), t, dt_eff, x, y, cap, mask.ctypes.data, vre.ctypes.data,
+                           vim.ctypes.data, C.byref(p))
+    if ne < 0:
+        raise QmcError(ne, "qmc_column_eval failed")
+    return mask[:ne], vre[:ne], vim[:ne], p.value
