@@ -70,9 +70,22 @@ def workload(name: str):
                     t_end=float(n), rho0=P.rho_basis(0))
     if name == "spread32":
         prob = P.ghz_circuit(32)
-        return dict(name="spread32", desc="1e8 random states x 1 walker, GHZ-32 Liouvillian in a CNOT window",
-                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
-                    spread=10**8 // 64)
+        return dict(name="spread32", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "
+                    "1e8 distinct random states x 1 walker over 64 vectors",
+                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=5.13, t_start=5.0,
+                    spread=10**8 // 64, default_steps=10)
+    if name == "spread32s":
+        prob = P.ghz_circuit(32)
+        return dict(name="spread32s", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "
+                    "1.6e7 distinct random states x 1 walker over 64 vectors",
+                    prob=prob, nseg=64, n_diag=250000, dt=0.01, t_end=5.13, t_start=5.0,
+                    spread=250000, default_steps=10)
+    if name.startswith("ghz") and name.endswith("i") and name[3:-1].isdigit():
+        n = int(name[3:-1])
+        prob = P.ghz_circuit(n)
+        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8}.get(n, 10**7)
+        return dict(name=name, desc=f"GHZ-{n} preparation, initiator xi = 1e-3", prob=prob, nseg=16,
+                    n_diag=total // 16, dt=0.01, t_end=float(n), rho0=P.rho_basis(0), xi=1e-3)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -178,20 +191,23 @@ def run_gpu(args, rank: int, world: int):
     prob = wl["prob"]
     stream = torch.cuda.current_stream()
     seed = 1000 + rank
+    init_min = int(math.ceil(wl.get("xi", 0.0) * wl["n_diag"]))
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
-                  capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
+                  initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
     sim.load_schedule(prob)
     pl = step_list(wl)
     total = planner.total_steps(pl)
     W = args.warmup
-    K = args.steps if args.steps > 0 else total - W
+    K = args.steps if args.steps > 0 else wl.get("default_steps", total - W)
     if W + K > total:
         raise SystemExit(f"workload has {total} steps; warmup + steps = {W + K}")
 
-    # host inputs (e2e leg starts here)
-    t_e2e0 = time.perf_counter()
+    # host inputs are generated first; the e2e leg starts with their upload
+    pops = None
     if "spread" in wl:
         pops = [P.spread_population(prob.n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
+    t_e2e0 = time.perf_counter()
+    if pops is not None:
         h2d_init = sum(k.nbytes + r.nbytes + i.nbytes for k, r, i in pops)
         sim.set_populations(pops)
         sim.set_clock(0, wl["t_start"])
@@ -205,8 +221,8 @@ def run_gpu(args, rank: int, world: int):
 
     ck_path = None
     if not args.no_profile:
-        ck_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                               f".bench_ck_{rank}.bin")
+        import tempfile
+        ck_path = os.path.join(tempfile.gettempdir(), f"qmc_bench_ck_{os.getpid()}_{rank}.bin")
         sim.checkpoint(ck_path)
 
     if dist is not None:
@@ -291,7 +307,7 @@ def run_gpu(args, rank: int, world: int):
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl["name"], "description": wl["desc"], "n_qubits": prob.n,
                    "vectors_per_gpu": wl["nseg"], "n_diag": wl["n_diag"], "dt": wl["dt"],
-                   "integrator": "AB2", "timed_steps_of_job": f"{W}..{W + K} of {total}",
+                   "integrator": "AB2", "xi": wl.get("xi", 0.0), "timed_steps_of_job": f"{W}..{W + K} of {total}",
                    "records_per_step_avg": c["k_next"] / max(1, c["steps"]),
                    "spawns_per_step_avg": c["spawns"] / max(1, c["steps"]),
                    "key_steps_per_s": c["k_next"] * world / (ms_all * 1e-3),
@@ -359,7 +375,7 @@ def run_reference(args, rank: int, world: int):
     pl = step_list(wl)
     total = planner.total_steps(pl)
     W = args.warmup
-    K = args.steps if args.steps > 0 else total - W
+    K = args.steps if args.steps > 0 else wl.get("default_steps", total - W)
     per_step_budget = max(0.5, min(20.0, 120.0 / max(1, K + W)))
     res = cpu_baseline(wl, pl, 0, budget_s=per_step_budget * (K + W))
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
@@ -377,7 +393,7 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (0 = rest of the job)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dd12")
+    ap.add_argument("--workload", default="spread32")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

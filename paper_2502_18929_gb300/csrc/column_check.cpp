@@ -29,6 +29,7 @@ extern "C" int qmc_column_eval(int32_t n_qubits, const qmc_ham_term* ham, int32_
     const Prog p = prog_at(blob.data());
     int64_t sre, sim;
     *p_out = column_weight(p, (uint32_t)x, (uint32_t)y, &sre, &sim);
+    if (*p_out > p.h->p_bound) return QMC_ERR_STATE; // the spawn filter bound must hold
     const int ne = p.h->n_entry;
     for (int e = 0; e < ne && e < cap; ++e) {
         int64_t a, b;

@@ -37,6 +37,7 @@ struct Prog {
     const Gen* gen;
     const GTerm* gt;
     const Entry* ent;
+    const AffGroup* aff;
 };
 
 QMC_HD inline Prog prog_at(const uint8_t* base)
@@ -49,6 +50,7 @@ QMC_HD inline Prog prog_at(const uint8_t* base)
     p.gen = (const Gen*)(base + p.h->off_gen);
     p.gt = (const GTerm*)(base + p.h->off_gterm);
     p.ent = (const Entry*)(base + p.h->off_entry);
+    p.aff = (const AffGroup*)(base + p.h->off_aff);
     return p;
 }
 
@@ -69,17 +71,22 @@ QMC_HD inline void gen_value(const Prog& p, int g, uint32_t x, uint32_t y,
 }
 
 // Diagonal element (sre, sim) and P = 2^52 dt_eff sum_kl (|Re L| + |Im L|).
-QMC_HD inline int64_t column_weight(const Prog& p, uint32_t x, uint32_t y,
-                                                 int64_t* sre_out, int64_t* sim_out)
+// Everything that depends on the state through per-qubit patterns is one
+// affine form per member mask (three popcounts each); only multi-qubit
+// parity terms are evaluated term by term.
+QMC_HD inline int64_t column_weight(const Prog& p, uint32_t x, uint32_t y, int64_t* sre_out,
+                                    int64_t* sim_out)
 {
     const ProgHeader& h = *p.h;
     int64_t sre = h.self_const_re, sim = h.self_const_im;
-    for (int i = 0; i < h.n_selffam; ++i) {
-        const SelfFam f = p.sf[i];
-        const uint32_t pat = f.type == 0 ? x : (f.type == 1 ? y : (x ^ y));
-        const int c = qmc_popc(f.members) - 2 * qmc_popc(pat & f.members);
-        sre += f.qre * c;
-        sim += f.qim * c;
+    int64_t P = h.p_const;
+    for (int i = 0; i < h.n_aff; ++i) {
+        const AffGroup& g = p.aff[i];
+        const int32_t cx = qmc_popc(x & g.members), cy = qmc_popc(y & g.members);
+        const int32_t c11 = qmc_popc(x & y & g.members);
+        sre += g.s0re + g.sare * cx + g.sbre * cy + g.scre * c11;
+        sim += g.s0im + g.saim * cx + g.sbim * cy + g.scim * c11;
+        P += g.f0 + g.fx * cx + g.fy * cy + g.f11 * c11;
     }
     for (int i = 0; i < h.n_selfgen; ++i) {
         const SelfGen g = p.sg[i];
@@ -87,14 +94,7 @@ QMC_HD inline int64_t column_weight(const Prog& p, uint32_t x, uint32_t y,
         sre += par ? -g.qre : g.qre;
         sim += par ? -g.qim : g.qim;
     }
-    int64_t P = qmc_iabs64(sre) + qmc_iabs64(sim) + h.p_const;
-    for (int i = 0; i < h.n_fam; ++i) {
-        const Fam& f = p.fam[i];
-        const uint32_t M = f.members;
-        const int c3 = qmc_popc(M & x & y), c2 = qmc_popc(M & x & ~y), c1 = qmc_popc(M & ~x & y);
-        const int c0 = qmc_popc(M) - c1 - c2 - c3;
-        P += f.a[0] * c0 + f.a[1] * c1 + f.a[2] * c2 + f.a[3] * c3;
-    }
+    P += qmc_iabs64(sre) + qmc_iabs64(sim);
     for (int g = 0; g < h.n_nonconst_gen; ++g) {
         int64_t vr, vi;
         gen_value(p, g, x, y, &vr, &vi);

@@ -28,7 +28,7 @@ namespace {
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
-constexpr int kStage = 128; // spawn records staged per warp
+constexpr int kStage = 64; // spawn records staged per warp
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11).
@@ -91,6 +91,46 @@ __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned
     return false;
 }
 
+// Warp-parallel decoupled look-back for tile t (all 32 lanes of one warp):
+// lane i reads the status of tile t - 1 - i - 32 w in window w, the warp sums
+// aggregates up to the nearest inclusive prefix.  Returns the exclusive
+// prefix of tile t (to every lane).  Bounded waits; on timeout the error is
+// raised and the partial sum returned.
+__device__ unsigned long long warp_lookback(const unsigned long long* status, int64_t t, uint32_t epoch,
+                                            DevState* st, int lane)
+{
+    unsigned long long excl = 0;
+    int64_t hi = t - 1; // nearest unread predecessor
+    while (hi >= 0) {
+        const int64_t j = hi - lane;
+        unsigned long long v = 0;
+        bool ready = j < 0;
+        for (uint32_t it = 0; it < kSpinLimit; ++it) {
+            if (!ready) {
+                v = ld_vol(status + j);
+                ready = (uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u;
+            }
+            if (__all_sync(kFull, ready)) break;
+            if (read_error(st) == DERR_TIMEOUT) break;
+            if (it > 32) __nanosleep(64);
+        }
+        if (!__all_sync(kFull, ready)) {
+            if (lane == 0) set_error(st, DERR_TIMEOUT);
+            break;
+        }
+        const bool incl = j >= 0 && ((v >> 30) & 3u) == kFlagIncl;
+        const uint32_t bal = __ballot_sync(kFull, incl);
+        const int stop = bal ? __ffs(bal) - 1 : 31;          // lanes 0..stop contribute
+        unsigned long long c = (j >= 0 && lane <= stop) ? (v & 0x3FFFFFFFull) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        excl += c;
+        if (bal) break;
+        hi -= 32;
+    }
+    return excl;
+}
+
 // Segment of record i in a population slot: upper_bound(off[1..nseg], i).
 __device__ __forceinline__ int seg_of(const int64_t* off, int nseg, int64_t i)
 {
@@ -146,16 +186,14 @@ __global__ void k_prologue(StepParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Spawning, light parents: one lane per parent, one Philox call per two
-// walkers.  T = R >> 12 (52 bits); the walker spawns iff T < P and then goes
-// to the (destination, channel) whose cumulative-weight interval holds T.
+// Spawning, light parents.  A warp takes 32 consecutive parents; their
+// walker pairs (one Philox call per two walkers) are spread evenly over the
+// lanes.  T = R >> 12 (52 bits); the walker spawns iff T < P.  The
+// destination of a spawned walker is chosen by the whole warp: lanes evaluate
+// destinations in parallel, a warp scan gives the cumulative weights, and the
+// lane whose interval holds T wins.
 // ---------------------------------------------------------------------------
-struct SpawnCtx {
-    Prog prog[2];
-    const Rec* src[2];
-    const int64_t* off[2];
-    int64_t k0, total;
-};
+constexpr int kProgSmem = 12288;
 
 __device__ __forceinline__ void warp_flush(SRec* stage, int n, const StepParams& P, int lane)
 {
@@ -172,19 +210,169 @@ __device__ __forceinline__ void warp_flush(SRec* stage, int n, const StepParams&
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads) k_spawn_light(StepParams P)
+// Warp-wide choice of (destination, channel) holding T in the column of
+// |x><y| (all lanes pass the same arguments).  Returns false if T is not
+// covered (impossible when T < P).
+__device__ __forceinline__ bool warp_choose(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim,
+                                            int64_t T, int lane, uint64_t* mask, int* chan, int64_t* v)
 {
-    __shared__ SRec stage_all[kThreads / 32][kStage];
+    const int ne = p.h->n_entry;
+    int64_t carry = 0;
+    for (int b0 = 0; b0 < ne; b0 += 32) {
+        const int e = b0 + lane;
+        int64_t vr = 0, vi = 0;
+        if (e < ne) entry_value(p, p.ent[e], x, y, sre, sim, &vr, &vi);
+        const int64_t wr = iabs64(vr), w = wr + iabs64(vi);
+        int64_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int64_t lo = carry + incl - w;
+        const bool hit = e < ne && T >= lo && T < lo + w;
+        const uint32_t bal = __ballot_sync(kFull, hit);
+        if (bal) {
+            const int win = __ffs(bal) - 1;
+            const int c = (T - lo < wr) ? 0 : 1;
+            const int64_t val = c ? vi : vr;
+            *chan = __shfl_sync(kFull, c, win);
+            *v = __shfl_sync(kFull, val, win);
+            *mask = __shfl_sync(kFull, e < ne ? p.ent[e].mask_key : 0ull, win);
+            return true;
+        }
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    return false;
+}
+
+// Copy a program into shared memory if it fits; returns the copy to use once
+// the block has synchronised (the caller must __syncthreads() before reading).
+__device__ __forceinline__ const uint8_t* stage_prog(const uint8_t* g, uint8_t* s)
+{
+    const int bytes = ((const ProgHeader*)g)->bytes;
+    if (bytes > kProgSmem) return g;
+    for (int i = threadIdx.x; i < bytes / 8; i += blockDim.x)
+        ((uint64_t*)s)[i] = ((const uint64_t*)g)[i];
+    return s;
+}
+
+// A walker whose draw T lies below the step's bound on P: a spawn candidate.
+struct SpawnEvent {
+    uint64_t key;
+    int64_t T;
+    uint32_t seg;
+    uint32_t info; // bit0 comp, bit1 phase, bit2 noninit, bit3 parent component > 0
+};
+
+constexpr int kEvQ = 96;
+constexpr int kSpawnSmem = 2 * kProgSmem + (kThreads / 32) * (kEvQ * (int)sizeof(SpawnEvent) + kStage * 16);
+
+// Destination (entry, channel) holding T, found by one lane walking the
+// column in canonical order.
+__device__ __forceinline__ bool lane_choose(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim,
+                                            int64_t T, uint64_t* mask, int* chan, int64_t* v)
+{
+    const int ne = p.h->n_entry;
+    for (int e = 0; e < ne; ++e) {
+        const Entry E = p.ent[e];
+        int64_t vr, vi;
+        entry_value(p, E, x, y, sre, sim, &vr, &vi);
+        const int64_t wr = iabs64(vr);
+        if (T < wr) { *mask = E.mask_key; *chan = 0; *v = vr; return true; }
+        T -= wr;
+        const int64_t wi = iabs64(vi);
+        if (T < wi) { *mask = E.mask_key; *chan = 1; *v = vi; return true; }
+        T -= wi;
+    }
+    return false;
+}
+
+// Resolve up to 32 queued candidates, one per lane: exact weight P of the
+// parent's column, the spawn test T < P, and the destination.
+__device__ __forceinline__ void drain_events(SpawnEvent* q, int* qn, SRec* stage, int* staged, const Prog& prog0,
+                                             const Prog& prog1, const StepParams& P, int n, uint32_t ymask, int lane)
+{
+    const int cnt = *qn < 32 ? *qn : 32;
+    SRec rec;
+    bool ok = false;
+    if (lane < cnt) {
+        const SpawnEvent ev = q[lane];
+        const int comp = ev.info & 1u, phase = (ev.info >> 1) & 1u, non = (ev.info >> 2) & 1u;
+        const int sg = (ev.info >> 3) & 1u ? 1 : -1;
+        const uint32_t x = (uint32_t)(ev.key >> n), y = (uint32_t)(ev.key & ymask);
+        const Prog& prog = phase ? prog1 : prog0;
+        int64_t sre, sim;
+        const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+        if (Pw >= (1ll << 52)) {
+            set_error(P.st, DERR_DT_TOO_LARGE);
+        } else if (ev.T < Pw) {
+            uint64_t mk;
+            int chan;
+            int64_t v;
+            ok = lane_choose(prog, x, y, sre, sim, ev.T, &mk, &chan, &v);
+            if (ok) rec = make_spawn(ev.key ^ mk, (int)ev.seg, comp, chan, v, sg, phase ? -1 : 1, non, 1);
+            else set_error(P.st, DERR_TILE_CAPACITY);
+        }
+    }
+    __syncwarp();
+    const int rest = *qn - cnt;
+    for (int j = lane; j < rest; j += 32) {
+        const SpawnEvent e2 = q[cnt + j];
+        __syncwarp(__activemask());
+        q[j] = e2;
+    }
+    __syncwarp();
+    *qn = rest;
+    const uint32_t bal = __ballot_sync(kFull, ok);
+    const int nrec = __popc(bal);
+    if (*staged + nrec > kStage) {
+        warp_flush(stage, *staged, P, lane);
+        *staged = 0;
+    }
+    if (ok) stage[*staged + __popc(bal & ((1u << lane) - 1u))] = rec;
+    *staged += nrec;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void enqueue2(SpawnEvent* q, int* qn, bool s0, bool s1, const SpawnEvent& e0,
+                                         const SpawnEvent& e1, int lane)
+{
+    const uint32_t b0 = __ballot_sync(kFull, s0), b1 = __ballot_sync(kFull, s1);
+    const uint32_t lt = (1u << lane) - 1u;
+    if (s0) q[*qn + __popc(b0 & lt)] = e0;
+    if (s1) q[*qn + __popc(b0) + __popc(b1 & lt)] = e1;
+    *qn += __popc(b0) + __popc(b1);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_spawn_light(StepParams P)
+{
+    extern __shared__ __align__(16) uint8_t spawn_smem[];
     DevState* st = P.st;
     if (read_error(st)) return;
+    uint8_t* sprog0 = spawn_smem;
+    uint8_t* sprog1 = spawn_smem + kProgSmem;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SpawnEvent* evq = (SpawnEvent*)(spawn_smem + 2 * kProgSmem) + warp * kEvQ;
+    SRec* stage = (SRec*)(spawn_smem + 2 * kProgSmem + (kThreads / 32) * kEvQ * sizeof(SpawnEvent)) + warp * kStage;
+
     const int ci = st->call_index;
     const StepInfo inf = P.info[ci];
     const int cur = st->cur, prv = (cur + 2) % 3;
     const int64_t K0 = st->count[cur];
     const int64_t K1 = inf.ab2 ? st->count[prv] : 0;
     const int64_t total = K0 + K1;
-    const Prog prog0 = prog_at(P.progs + inf.prog_off[0]);
-    const Prog prog1 = prog_at(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]));
+    const uint8_t* pb0 = stage_prog(P.progs + inf.prog_off[0], sprog0);
+    const uint8_t* pb1 = stage_prog(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]), sprog1);
+    __syncthreads();
+    const Prog prog0 = prog_at(pb0);
+    const Prog prog1 = prog_at(pb1);
+    // filter: a walker can only spawn if T < P <= p_bound (every walker is a
+    // candidate when the bound reaches 2^52, so p >= 1 is still detected)
+    const int64_t lim52 = 1ll << 52;
+    const int64_t bound0 = prog0.h->p_bound >= lim52 ? lim52 : prog0.h->p_bound;
+    const int64_t bound1 = prog1.h->p_bound >= lim52 ? lim52 : prog1.h->p_bound;
     const Rec* src0 = P.pop[cur];
     const Rec* src1 = P.pop[prv];
     const int64_t* off0 = P.segoff[cur];
@@ -192,123 +380,141 @@ __global__ void __launch_bounds__(kThreads) k_spawn_light(StepParams P)
     const int n = P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    SRec* stage = stage_all[warp];
-    int staged = 0;
     const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    const int64_t chunk = ((total + nwarps - 1) / nwarps + 31) / 32 * 32;
+    const int64_t w_begin = gw * chunk;
+    const int64_t w_end = min(total, w_begin + chunk);
+    int staged = 0, qn = 0;
+    int cur_phase = -1, seg = 0;
+    int64_t seg_end = 0;
 
-    for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * 32; base < total;
-         base += nwarps * 32) {
+    for (int64_t base = w_begin; base < w_end; base += 32) {
         const int64_t i = base + lane;
-        int phase = 0, seg = 0, my_pairs = 0, pairs_re = 0;
-        int64_t m_re = 0, m_im = 0, P_w = 0, sre = 0, sim = 0;
+        const bool valid = i < w_end;
+        const int phase = (valid && i >= K0) ? 1 : 0;
+        const int64_t j = phase ? i - K0 : i;
+        if (valid && (phase != cur_phase || j >= seg_end)) {
+            const int64_t* off = phase ? off1 : off0;
+            seg = seg_of(off, P.nseg, j);
+            seg_end = off[seg + 1];
+            cur_phase = phase;
+        }
         Rec par{0ull, 0, 0};
-        uint32_t x = 0, y = 0;
-        int noninit = 0;
-        uint2 kd = make_uint2(0u, 0u);
-        if (i < total) {
-            phase = i >= K0 ? 1 : 0;
-            const int64_t j = phase ? i - K0 : i;
+        int64_t m_re = 0, m_im = 0;
+        int my_pairs = 0, pairs_re = 0, noninit = 0;
+        if (valid) {
             par = phase ? src1[j] : src0[j];
-            seg = seg_of(phase ? off1 : off0, P.nseg, j);
-            x = (uint32_t)(par.key >> n);
-            y = (uint32_t)(par.key & ymask);
-            P_w = column_weight(phase ? prog1 : prog0, x, y, &sre, &sim);
-            if (P_w >= (1ll << 52)) {
-                set_error(st, DERR_DT_TOO_LARGE);
-                P_w = 0;
-            }
             m_re = iabs64(par.re);
             m_im = iabs64(par.im);
             noninit = (P.init_min > 0 && (m_re + m_im) < P.init_min) ? 1 : 0;
-            kd = P.kd[seg];
-            if (P_w > 0) {
-                if (m_re + m_im > kHeavyWalkers) {
-                    // hand over to the heavy path in chunks of kHeavyChunk walkers
-                    for (int comp = 0; comp < 2; ++comp) {
-                        const int64_t m = comp ? m_im : m_re;
-                        const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
-                        if (chunks == 0) continue;
-                        const unsigned long long hb =
-                            atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
-                        for (int64_t c = 0; c < chunks; ++c) {
-                            const int64_t pos = (int64_t)hb + c;
-                            if (pos < P.heavy_cap) {
-                                HeavyItem it;
-                                it.parent = j;
-                                it.phase = phase;
-                                it.comp = comp;
-                                it.chunk = (int32_t)c;
-                                it.seg = seg;
-                                P.heavy[pos] = it;
-                            } else {
-                                set_error(st, DERR_HEAVY_CAPACITY);
-                            }
+            if (m_re + m_im > kHeavyWalkers) {
+                for (int comp = 0; comp < 2; ++comp) {
+                    const int64_t m = comp ? m_im : m_re;
+                    const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
+                    if (chunks == 0) continue;
+                    const unsigned long long hb =
+                        atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
+                    for (int64_t c = 0; c < chunks; ++c) {
+                        const int64_t pos = (int64_t)hb + c;
+                        if (pos < P.heavy_cap) {
+                            HeavyItem it;
+                            it.parent = j;
+                            it.phase = phase;
+                            it.comp = comp;
+                            it.chunk = (int32_t)c;
+                            it.seg = seg;
+                            P.heavy[pos] = it;
+                        } else {
+                            set_error(st, DERR_HEAVY_CAPACITY);
                         }
                     }
-                } else {
-                    pairs_re = (int)((m_re + 1) / 2);
-                    my_pairs = pairs_re + (int)((m_im + 1) / 2);
                 }
+            } else {
+                pairs_re = (int)((m_re + 1) / 2);
+                my_pairs = pairs_re + (int)((m_im + 1) / 2);
             }
         }
-        const Prog& prog = phase ? prog1 : prog0;
-        const int sigma = phase ? -1 : 1;
         const int max_pairs = __reduce_max_sync(kFull, my_pairs);
-        for (int jp = 0; jp < max_pairs; ++jp) {
-            SRec r[2];
-            bool v[2] = {false, false};
-            if (jp < my_pairs) {
-                const int comp = jp < pairs_re ? 0 : 1;
-                const int j2 = comp ? jp - pairs_re : jp;
+        if (max_pairs == 0) continue;
+        if (max_pairs == 1) {
+            // at most one walker pair per lane: each lane draws for its own parent
+            int64_t T0 = -1, T1 = -1;
+            uint32_t info = 0;
+            if (my_pairs == 1) {
+                const int comp = pairs_re ? 0 : 1;
                 const int64_t m = comp ? m_im : m_re;
-                const int sg = (comp ? par.im : par.re) > 0 ? 1 : -1;
+                const int64_t bnd = phase ? bound1 : bound0;
                 const uint4 w = philox10(
                     make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                               (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                    kd);
+                               (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), 0u),
+                    P.kd[seg]);
+                const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
+                const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
+                if (R0 < bnd) T0 = R0;
+                if (m > 1 && R1 < bnd) T1 = R1;
+                const int val = comp ? par.im : par.re;
+                info = (uint32_t)comp | ((uint32_t)phase << 1) | ((uint32_t)noninit << 2) | ((val > 0 ? 1u : 0u) << 3);
+            }
+            enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{par.key, T0, (uint32_t)seg, info},
+                     SpawnEvent{par.key, T1, (uint32_t)seg, info}, lane);
+            while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
+            continue;
+        }
+        // several pairs per lane: spread all pairs of the warp evenly over the lanes
+        int incl = my_pairs;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (2 * (int64_t)j2 + h >= m) break;
-                    const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
-                    int64_t T = (int64_t)(R >> 12);
-                    if (T >= P_w) continue;
-                    for (int e = 0; e < prog.h->n_entry; ++e) {
-                        const Entry E = prog.ent[e];
-                        int64_t vr, vi;
-                        entry_value(prog, E, x, y, sre, sim, &vr, &vi);
-                        const int64_t wr = iabs64(vr);
-                        if (T < wr) {
-                            r[h] = make_spawn(par.key ^ E.mask_key, seg, comp, 0, vr, sg, sigma, noninit, 1);
-                            v[h] = true;
-                            break;
-                        }
-                        T -= wr;
-                        const int64_t wi = iabs64(vi);
-                        if (T < wi) {
-                            r[h] = make_spawn(par.key ^ E.mask_key, seg, comp, 1, vi, sg, sigma, noninit, 1);
-                            v[h] = true;
-                            break;
-                        }
-                        T -= wi;
-                    }
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int tot_pairs = __shfl_sync(kFull, incl, 31);
+        for (int r = 0; r < tot_pairs; r += 32) {
+            const int g = r + lane;
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int im = __shfl_sync(kFull, incl, mid);
+                if (im > g) hi = mid; else lo = mid + 1;
             }
-            const uint32_t b0 = __ballot_sync(kFull, v[0]);
-            const uint32_t b1 = __ballot_sync(kFull, v[1]);
-            const int cnt = __popc(b0) + __popc(b1);
-            if (cnt == 0) continue;
-            if (staged + cnt > kStage) {
-                warp_flush(stage, staged, P, lane);
-                staged = 0;
+            const int owner = lo;
+            const bool act = g < tot_pairs;
+            const int o_incl = __shfl_sync(kFull, incl, owner);
+            const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
+            const int local = g - (o_incl - o_pairs);
+            const uint64_t okey = __shfl_sync(kFull, par.key, owner);
+            const int o_pre = __shfl_sync(kFull, pairs_re, owner);
+            const int64_t o_mre = __shfl_sync(kFull, m_re, owner);
+            const int64_t o_mim = __shfl_sync(kFull, m_im, owner);
+            const int o_phase = __shfl_sync(kFull, phase, owner);
+            const int o_seg = __shfl_sync(kFull, seg, owner);
+            const int o_non = __shfl_sync(kFull, noninit, owner);
+            const int32_t o_re = __shfl_sync(kFull, par.re, owner);
+            const int32_t o_im = __shfl_sync(kFull, par.im, owner);
+            int64_t T0 = -1, T1 = -1;
+            uint32_t info = 0;
+            if (act) {
+                const int comp = local < o_pre ? 0 : 1;
+                const int j2 = comp ? local - o_pre : local;
+                const int64_t m = comp ? o_mim : o_mre;
+                const int64_t bnd = o_phase ? bound1 : bound0;
+                const uint4 w = philox10(
+                    make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
+                               (uint32_t)o_phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
+                    P.kd[o_seg]);
+                const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
+                const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
+                if (R0 < bnd) T0 = R0;
+                if (2 * (int64_t)j2 + 1 < m && R1 < bnd) T1 = R1;
+                const int val = comp ? o_im : o_re;
+                info = (uint32_t)comp | ((uint32_t)o_phase << 1) | ((uint32_t)o_non << 2) | ((val > 0 ? 1u : 0u) << 3);
             }
-            if (v[0]) stage[staged + __popc(b0 & lt)] = r[0];
-            if (v[1]) stage[staged + __popc(b0) + __popc(b1 & lt)] = r[1];
-            staged += cnt;
-            __syncwarp();
+            enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{okey, T0, (uint32_t)o_seg, info},
+                     SpawnEvent{okey, T1, (uint32_t)o_seg, info}, lane);
+            while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
         }
     }
+    while (qn > 0) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
     if (staged) warp_flush(stage, staged, P, lane);
 }
 
@@ -345,6 +551,10 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         const uint32_t x = (uint32_t)(par.key >> n), y = (uint32_t)(par.key & ymask);
         int64_t sre, sim;
         const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+        if (Pw >= (1ll << 52)) {
+            if (threadIdx.x == 0) set_error(st, DERR_DT_TOO_LARGE);
+            return;
+        }
         const int ne = prog.h->n_entry;
         if (ne > kMaxEntries) {
             if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
@@ -464,7 +674,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(StepParams P)
         if (h[i]) atomicAdd(&P.sort_hist[i], h[i]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort_scatter(StepParams P, int pass, const SRec* __restrict__ src,
+__global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int pass, const SRec* __restrict__ src,
                                                           SRec* __restrict__ dst)
 {
     __shared__ SRec buf[kSortTile];
@@ -557,11 +767,25 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(StepParams P, int pas
                 st_vol(my, lb_word(epoch, kFlagIncl, tot));
             } else {
                 st_vol(my, lb_word(epoch, kFlagAgg, tot));
-                for (int64_t j = tile - 1; j >= 0; --j) {
-                    unsigned long long v;
-                    if (!lb_wait(P.sort_status + j * 256 + d, epoch, &v, st)) break;
-                    excl += (unsigned int)(v & 0x3FFFFFFFu);
-                    if (((v >> 30) & 3u) == kFlagIncl) break;
+                // look back 8 predecessors per probe (independent loads)
+                bool done = false;
+                for (int64_t hi = tile - 1; hi >= 0 && !done; hi -= 8) {
+                    unsigned long long v[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) v[w] = hi - w >= 0 ? ld_vol(P.sort_status + (hi - w) * 256 + d) : 0ull;
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        if (done || hi - w < 0) continue;
+                        unsigned long long x = v[w];
+                        if (!((uint32_t)(x >> 32) == epoch && ((x >> 30) & 3u) != 0u)) {
+                            if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st)) {
+                                done = true;
+                                continue;
+                            }
+                        }
+                        excl += (unsigned int)(x & 0x3FFFFFFFu);
+                        if (((x >> 30) & 3u) == kFlagIncl) done = true;
+                    }
                 }
                 st_vol(my, lb_word(epoch, kFlagIncl, excl + tot));
             }
@@ -700,25 +924,249 @@ __global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
 }
 
 // ---------------------------------------------------------------------------
+// Bulk (TMA) copies into shared memory, completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (it > 16) __nanosleep(32);
+    }
+    set_error(st, DERR_TIMEOUT);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // Annihilation.  A run is all items (at most one N(t) record and any number of
 // spawn records) with one key.  Value = N(t) + initiator spawns +
-// (occupied ? non-initiator spawns : 0); zero runs are dropped.  A tile emits
-// the runs whose first item lies in it, reading past its end if its last run
-// continues (only spawn records can follow, since N(t) sorts first on ties).
+// (occupied ? non-initiator spawns : 0); zero runs are dropped.  Tiles of the
+// merged sequence are staged by bulk copies (double-buffered); each thread
+// merges kMergeItems items and emits the runs whose first item it holds,
+// reading past its items (and past the tile, where only spawn records can
+// follow, since N(t) sorts first on equal keys) to finish its last run.
 // ---------------------------------------------------------------------------
-struct MItem {
-    uint64_t key;
-    int32_t v0, v1;
+struct MTile {
+    int64_t t;
+    int64_t a_glob, b_glob, b_seg_end;
+    uint64_t prev_key;
+    int32_t na, nb, seg, has_prev;
 };
 
-__global__ void __launch_bounds__(kThreads) k_merge(StepParams P, const SRec* __restrict__ sorted)
+__device__ __forceinline__ uint64_t it_key(const uint4* buf, int i)
 {
-    __shared__ MItem items[kMergeTile];
-    __shared__ uint8_t cls[kMergeTile];    // bit0: from N(t); bit1: target im; bit2: non-initiator
-    __shared__ int64_t s_tile;
+    return ((const uint64_t*)&buf[i])[0];
+}
+
+// Walk the thread's items; pass 0 counts (and gathers statistics), pass 1
+// writes at out + obase.
+__device__ __forceinline__ int merge_thread(const uint4* buf, const MTile& m, const SRec* __restrict__ sorted,
+                                            int pass, Rec* out, int64_t obase, int64_t pop_cap, DevState* st,
+                                            uint32_t n, uint32_t ymask, long long* ntot, long long* dre,
+                                            long long* dim)
+{
+    const int na = m.na, nb = m.nb, nt = na + nb;
+    const int d0 = threadIdx.x * kMergeItems;
+    if (d0 >= nt) return 0;
+    int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (it_key(buf, mid) <= it_key(buf, na + d0 - mid - 1)) lo = mid + 1; else hi = mid;
+    }
+    int ia = lo, ib = d0 - lo;
+    bool has_prev;
+    uint64_t prev;
+    if (d0 == 0) {
+        has_prev = m.has_prev != 0;
+        prev = m.prev_key;
+    } else {
+        has_prev = true;
+        const uint64_t ka = ia > 0 ? it_key(buf, ia - 1) : 0ull;
+        const uint64_t kb = ib > 0 ? it_key(buf, na + ib - 1) : 0ull;
+        prev = ka > kb ? ka : kb;
+    }
+    const int cnt = min(kMergeItems, nt - d0);
+    int nout = 0;
+    bool open = false, occupied = false;
+    uint64_t rkey = 0;
+    long long sre = 0, sim = 0, nre = 0, nim = 0;
+    auto close_run = [&]() {
+        long long vr = sre, vi = sim;
+        if (occupied) { vr += nre; vi += nim; }
+        if (vr == 0 && vi == 0) return;
+        if (vr > 2147483647ll || vr < -2147483647ll || vi > 2147483647ll || vi < -2147483647ll) {
+            set_error(st, DERR_POP_OVERFLOW);
+            return;
+        }
+        if (pass == 0) {
+            *ntot += (vr < 0 ? -vr : vr) + (vi < 0 ? -vi : vi);
+            if ((uint32_t)(rkey >> n) == (uint32_t)(rkey & ymask)) {
+                *dre += vr;
+                *dim += vi;
+            }
+        } else {
+            const int64_t pos = obase + nout;
+            if (pos < pop_cap) out[pos] = Rec{rkey, (int32_t)vr, (int32_t)vi};
+            else set_error(st, DERR_POP_CAPACITY);
+        }
+        ++nout;
+    };
+    auto add_item = [&](int idx, bool isA) {
+        const uint4 w = buf[idx];
+        if (isA) {
+            occupied = true;
+            sre += (int32_t)w.z;
+            sim += (int32_t)w.w;
+        } else {
+            const uint32_t meta = w.z;
+            const long long v = (int32_t)w.w;
+            if (meta & 1u) { if (meta & 2u) nim += v; else nre += v; }
+            else { if (meta & 2u) sim += v; else sre += v; }
+        }
+    };
+    bool leading = true;
+    for (int k = 0; k < cnt; ++k) {
+        bool takeA;
+        if (ia >= na) takeA = false;
+        else if (ib >= nb) takeA = true;
+        else takeA = it_key(buf, ia) <= it_key(buf, na + ib);
+        const int idx = takeA ? ia++ : na + ib++;
+        const uint64_t key = it_key(buf, idx);
+        if (leading) {
+            if (has_prev && key == prev) continue; // run owned by an earlier thread or tile
+            leading = false;
+        }
+        if (open && key == rkey) {
+            add_item(idx, takeA);
+            continue;
+        }
+        if (open) close_run();
+        open = true;
+        occupied = false;
+        rkey = key;
+        sre = sim = nre = nim = 0;
+        add_item(idx, takeA);
+    }
+    if (open) {
+        // finish the last run: later items of this tile, then spawns past the tile
+        for (;;) {
+            bool takeA;
+            if (ia >= na && ib >= nb) break;
+            if (ia >= na) takeA = false;
+            else if (ib >= nb) takeA = true;
+            else takeA = it_key(buf, ia) <= it_key(buf, na + ib);
+            const int idx = takeA ? ia : na + ib;
+            if (it_key(buf, idx) != rkey) break;
+            if (takeA) ++ia; else ++ib;
+            add_item(idx, takeA);
+        }
+        if (ia >= na && ib >= nb) {
+            for (int64_t jb = m.b_glob + nb; jb < m.b_seg_end; ++jb) {
+                const SRec r = sorted[jb];
+                if (r.key != rkey) break;
+                const long long v = r.val;
+                if (r.meta & 1u) { if (r.meta & 2u) nim += v; else nre += v; }
+                else { if (r.meta & 2u) sim += v; else sre += v; }
+            }
+        }
+        close_run();
+    }
+    return nout;
+}
+
+__device__ __forceinline__ void merge_tile_meta(const StepParams& P, const SRec* __restrict__ sorted, int64_t t,
+                                                const Rec* A, const int64_t* aoff, MTile* m)
+{
+    const int s = tile_seg(P.tile_start, P.nseg, t);
+    const int64_t a_base = aoff[s], na_seg = aoff[s + 1] - a_base;
+    const int64_t b_base = P.bseg[s], nb_seg = P.bseg[s + 1] - b_base;
+    const int64_t ia0 = P.part[2 * t], ib0 = P.part[2 * t + 1];
+    int64_t ia1 = na_seg, ib1 = nb_seg;
+    if (t + 1 < P.tile_start[s + 1]) {
+        ia1 = P.part[2 * t + 2];
+        ib1 = P.part[2 * t + 3];
+    }
+    m->t = t;
+    m->seg = s;
+    m->a_glob = a_base + ia0;
+    m->b_glob = b_base + ib0;
+    m->b_seg_end = b_base + nb_seg;
+    m->na = (int32_t)(ia1 - ia0);
+    m->nb = (int32_t)(ib1 - ib0);
+    m->has_prev = (ia0 > 0 || ib0 > 0) ? 1 : 0;
+    uint64_t pk = 0;
+    if (ia0 > 0) pk = A[a_base + ia0 - 1].key;
+    if (ib0 > 0) {
+        const uint64_t kb = sorted[b_base + ib0 - 1].key;
+        pk = pk > kb ? pk : kb;
+    }
+    m->prev_key = pk;
+}
+
+__device__ __forceinline__ void merge_issue(const MTile& m, const Rec* A, const SRec* sorted, uint4* buf, uint64_t* bar)
+{
+    const uint32_t abytes = (uint32_t)m.na * 16u, bbytes = (uint32_t)m.nb * 16u;
+    mbar_arrive_expect(bar, abytes + bbytes);
+    if (abytes) bulk_load(buf, A + m.a_glob, abytes, bar);
+    if (bbytes) bulk_load(buf + m.na, sorted + m.b_glob, bbytes, bar);
+}
+
+constexpr int kMergeSmem = 2 * kMergeTile * 16;
+
+__global__ void __launch_bounds__(kThreads, 3) k_merge(StepParams P, const SRec* __restrict__ sorted)
+{
+    extern __shared__ __align__(128) uint4 mbuf[];   // 2 stages x kMergeTile items
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ MTile tiles[2];
     __shared__ int s_wcount[kThreads / 32];
-    __shared__ unsigned long long s_base;
     __shared__ long long s_red[3][kThreads / 32];
+    __shared__ unsigned long long s_base;
     DevState* st = P.st;
     if (read_error(st)) return;
     const int cur = st->cur, nxt = (cur + 1) % 3;
@@ -727,129 +1175,45 @@ __global__ void __launch_bounds__(kThreads) k_merge(StepParams P, const SRec* __
     Rec* out = P.pop[nxt];
     const int64_t* aoff = P.segoff[cur];
     const uint32_t epoch = st->seq + 15u;
-    const int n = P.n;
+    const uint32_t n = (uint32_t)P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        const int64_t t0 = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
+        tiles[0].t = t0;
+        if (t0 < T) {
+            merge_tile_meta(P, sorted, t0, A, aoff, &tiles[0]);
+            merge_issue(tiles[0], A, sorted, mbuf, &bar[0]);
+        }
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+    bool timed_out[2] = {false, false};
+    int stage = 0;
     for (;;) {
-        if (tid == 0) s_tile = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
-        __syncthreads();
-        const int64_t t = s_tile;
+        const int64_t t = tiles[stage].t;
         if (t >= T) break;
-        const int s = tile_seg(P.tile_start, P.nseg, t);
-        const int64_t a_base = aoff[s], na_seg = aoff[s + 1] - a_base;
-        const int64_t b_base = P.bseg[s], nb_seg = P.bseg[s + 1] - b_base;
-        const int64_t ia0 = P.part[2 * t], ib0 = P.part[2 * t + 1];
-        int64_t ia1 = na_seg, ib1 = nb_seg;
-        if (t + 1 < P.tile_start[s + 1]) {
-            ia1 = P.part[2 * t + 2];
-            ib1 = P.part[2 * t + 3];
-        }
-        const int na = (int)(ia1 - ia0), nb = (int)(ib1 - ib0), nt = na + nb;
-        // stage A part then B part
-        for (int j = tid; j < na; j += kThreads) {
-            const Rec r = A[a_base + ia0 + j];
-            items[j] = MItem{r.key, r.re, r.im};
-            cls[j] = 1u;
-        }
-        for (int j = tid; j < nb; j += kThreads) {
-            const SRec r = sorted[b_base + ib0 + j];
-            items[na + j] = MItem{r.key, r.val, 0};
-            cls[na + j] = (uint8_t)(((r.meta >> 1) & 1u) << 1 | (r.meta & 1u) << 2);
-        }
-        // key of the merged item just before this tile (same segment)
-        bool has_prev = false;
-        uint64_t prev_key = 0;
-        if (ia0 > 0 || ib0 > 0) {
-            has_prev = true;
-            if (ia0 > 0 && ib0 > 0) {
-                const uint64_t ka = A[a_base + ia0 - 1].key, kb = sorted[b_base + ib0 - 1].key;
-                prev_key = ka > kb ? ka : kb;
-            } else if (ia0 > 0) {
-                prev_key = A[a_base + ia0 - 1].key;
-            } else {
-                prev_key = sorted[b_base + ib0 - 1].key;
+        if (tid == 0) {
+            const int64_t tn = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
+            tiles[stage ^ 1].t = tn;
+            if (tn < T) {
+                merge_tile_meta(P, sorted, tn, A, aoff, &tiles[stage ^ 1]);
+                fence_proxy_async();
+                merge_issue(tiles[stage ^ 1], A, sorted, mbuf + (stage ^ 1) * kMergeTile, &bar[stage ^ 1]);
             }
         }
-        __syncthreads();
-        // per-thread merge of kMergeItems items (merge path in shared memory)
-        MItem mi[kMergeItems];
-        uint8_t mc[kMergeItems];
-        const int d0 = tid * kMergeItems;
-        int cnt = 0;
-        if (d0 < nt) {
-            int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (items[mid].key <= items[na + d0 - mid - 1].key) lo = mid + 1; else hi = mid;
-            }
-            int ia = lo, ib = d0 - lo;
-            cnt = min(kMergeItems, nt - d0);
-            for (int k = 0; k < kMergeItems; ++k) {
-                if (k >= cnt) break;
-                bool takeA;
-                if (ia >= na) takeA = false;
-                else if (ib >= nb) takeA = true;
-                else takeA = items[ia].key <= items[na + ib].key;
-                const int src = takeA ? ia++ : na + ib++;
-                mi[k] = items[src];
-                mc[k] = cls[src];
-            }
-        }
-        __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
-            items[d0 + k] = mi[k];
-            cls[d0 + k] = mc[k];
-        }
-        __syncthreads();
-        // runs whose head lies in this tile; each handled by the head's thread
-        Rec outrec[kMergeItems];
-        int nout = 0;
+        const bool ok = mbar_wait(&bar[stage], parity[stage], st);
+        if (!ok) timed_out[stage] = true;
+        parity[stage] ^= 1u;
+        const uint4* buf = mbuf + stage * kMergeTile;
+        const MTile m = tiles[stage];
         long long my_ntot = 0, my_dre = 0, my_dim = 0;
-        for (int k = 0; k < cnt; ++k) {
-            const int pos = d0 + k;
-            const uint64_t key = items[pos].key;
-            const bool head = pos == 0 ? !(has_prev && prev_key == key) : items[pos - 1].key != key;
-            if (!head) continue;
-            long long sre = 0, sim = 0, nre = 0, nim = 0;
-            bool occupied = false;
-            int q = pos;
-            for (; q < nt && items[q].key == key; ++q) {
-                const uint8_t c = cls[q];
-                if (c & 1u) {
-                    occupied = true;
-                    sre += items[q].v0;
-                    sim += items[q].v1;
-                } else {
-                    long long* dst_re = (c & 4u) ? &nre : &sre;
-                    long long* dst_im = (c & 4u) ? &nim : &sim;
-                    if (c & 2u) *dst_im += items[q].v0; else *dst_re += items[q].v0;
-                }
-            }
-            if (q == nt) {
-                // the run may continue in later tiles: only spawn records follow
-                for (int64_t jb = ib1; jb < nb_seg; ++jb) {
-                    const SRec r = sorted[b_base + jb];
-                    if (r.key != key) break;
-                    long long* dst_re = (r.meta & 1u) ? &nre : &sre;
-                    long long* dst_im = (r.meta & 1u) ? &nim : &sim;
-                    if ((r.meta >> 1) & 1u) *dst_im += r.val; else *dst_re += r.val;
-                }
-            }
-            if (occupied) { sre += nre; sim += nim; }
-            if (sre == 0 && sim == 0) continue;
-            if (sre > 2147483647ll || sre < -2147483647ll || sim > 2147483647ll || sim < -2147483647ll) {
-                set_error(st, DERR_POP_OVERFLOW);
-                continue;
-            }
-            outrec[nout++] = Rec{key, (int32_t)sre, (int32_t)sim};
-            my_ntot += (sre < 0 ? -sre : sre) + (sim < 0 ? -sim : sim);
-            if ((uint32_t)(key >> n) == (uint32_t)(key & ymask)) {
-                my_dre += sre;
-                my_dim += sim;
-            }
-        }
-        // block scan of output counts
+        int nout = 0;
+        if (ok) nout = merge_thread(buf, m, sorted, 0, out, 0, P.pop_cap, st, n, ymask, &my_ntot, &my_dre, &my_dim);
+        // block scan of output counts, block sums of the statistics
         int incl = nout;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -875,23 +1239,20 @@ __global__ void __launch_bounds__(kThreads) k_merge(StepParams P, const SRec* __
             if (w < warp) woff += s_wcount[w];
             tile_count += s_wcount[w];
         }
-        if (tid == 0) {
-            // decoupled look-back over merge tiles (global output order)
+        if (warp == 0) {
             unsigned long long* my = P.merge_status + t;
             unsigned long long excl = 0;
             if (t == 0) {
-                st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)tile_count));
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)tile_count));
             } else {
-                st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)tile_count));
-                for (int64_t j = t - 1; j >= 0; --j) {
-                    unsigned long long v;
-                    if (!lb_wait(P.merge_status + j, epoch, &v, st)) break;
-                    excl += v & 0x3FFFFFFFull;
-                    if (((v >> 30) & 3u) == kFlagIncl) break;
-                }
-                st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tile_count)));
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)tile_count));
+                excl = warp_lookback(P.merge_status, t, epoch, st, lane);
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tile_count)));
             }
-            s_base = excl;
+            if (lane == 0) s_base = excl;
+        }
+        if (tid == 0) {
+            const unsigned long long excl = s_base;
             if (t == T - 1) {
                 st->next_total = (int64_t)(excl + tile_count);
                 if ((int64_t)(excl + tile_count) > st->max_next) st->max_next = (int64_t)(excl + tile_count);
@@ -903,21 +1264,29 @@ __global__ void __launch_bounds__(kThreads) k_merge(StepParams P, const SRec* __
                     b += s_red[1][w];
                     c += s_red[2][w];
                 }
-                atomicAdd(&P.segacc[s].count, (unsigned long long)tile_count);
-                atomicAdd((unsigned long long*)&P.segacc[s].ntot, (unsigned long long)a);
-                atomicAdd((unsigned long long*)&P.segacc[s].dre, (unsigned long long)b);
-                atomicAdd((unsigned long long*)&P.segacc[s].dim, (unsigned long long)c);
+                atomicAdd(&P.segacc[m.seg].count, (unsigned long long)tile_count);
+                atomicAdd((unsigned long long*)&P.segacc[m.seg].ntot, (unsigned long long)a);
+                atomicAdd((unsigned long long*)&P.segacc[m.seg].dre, (unsigned long long)b);
+                atomicAdd((unsigned long long*)&P.segacc[m.seg].dim, (unsigned long long)c);
             }
         }
         __syncthreads();
-        const int64_t obase = (int64_t)s_base + woff + incl - nout;
-        for (int k = 0; k < nout; ++k) {
-            const int64_t pos = obase + k;
-            if (pos < P.pop_cap) out[pos] = outrec[k];
-            else set_error(st, DERR_POP_CAPACITY);
+        if (ok && nout) {
+            long long d1 = 0, d2 = 0, d3 = 0;
+            merge_thread(buf, m, sorted, 1, out, (int64_t)s_base + woff + incl - nout, P.pop_cap, st, n, ymask,
+                         &d1, &d2, &d3);
         }
         __syncthreads();
+        stage ^= 1;
     }
+    // A prefetched tile beyond the end issues no copy, so nothing is in flight
+    // here unless a wait gave up; then wait once more (bounded) for that copy
+    // before the shared memory is released.
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (timed_out[s]) mbar_wait(&bar[s], parity[s] ^ 1u, st);
+    }
+    __syncthreads();
 }
 
 // Segment offsets of N(t + dt), history, rotation (single CTA).
@@ -1113,24 +1482,52 @@ const char* const kKernelNames[kNumTimedKernels] = {
     "k_prologue", "k_spawn_light", "k_spawn_heavy", "k_sort_hist", "k_sort_scatter",
     "k_spawn_segoff", "k_merge_plan", "k_merge_part", "k_merge", "k_finalize"};
 
+namespace {
+// persistent grids: resident CTAs per SM x SMs, per kernel
+int g_grid_spawn = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0, g_grid_misc = 0;
+
+int resident(const void* fn, int smem, int sms)
+{
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess || per < 1) per = 1;
+    return per * sms;
+}
+} // namespace
+
+void configure_kernels()
+{
+    cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
+    cudaFuncSetAttribute(k_spawn_light, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpawnSmem);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_grid_spawn = resident((const void*)k_spawn_light, kSpawnSmem, sms);
+    g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
+    g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
+    g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms);
+    g_grid_misc = 2 * sms;
+}
+
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev)
 {
+    if (g_grid_spawn == 0) configure_kernels();
+    (void)grid;
     // ev (optional): kNumTimedKernels + 1 events; kernel i runs between ev[i] and ev[i + 1]
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], stream); };
     mark(0);
     k_prologue<<<1, kThreads, 0, stream>>>(P);
     mark(1);
-    k_spawn_light<<<grid, kThreads, 0, stream>>>(P);
+    k_spawn_light<<<g_grid_spawn, kThreads, kSpawnSmem, stream>>>(P);
     mark(2);
-    k_spawn_heavy<<<grid, kThreads, 0, stream>>>(P);
+    k_spawn_heavy<<<g_grid_heavy, kThreads, 0, stream>>>(P);
     mark(3);
     const int np = P.key_passes + P.seg_passes;
-    k_sort_hist<<<grid, kThreads, 0, stream>>>(P);
+    k_sort_hist<<<g_grid_misc, kThreads, 0, stream>>>(P);
     mark(4);
     SRec* a = P.spawn;
     SRec* b = P.spawn_alt;
     for (int p = 0; p < np; ++p) {
-        k_sort_scatter<<<grid, kThreads, 0, stream>>>(P, p, a, b);
+        k_sort_scatter<<<g_grid_sort, kThreads, 0, stream>>>(P, p, a, b);
         SRec* t = a;
         a = b;
         b = t;
@@ -1141,9 +1538,9 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(6);
     k_merge_plan<<<1, 1024, 0, stream>>>(P);
     mark(7);
-    k_merge_part<<<grid, kThreads, 0, stream>>>(P, sorted);
+    k_merge_part<<<g_grid_misc, kThreads, 0, stream>>>(P, sorted);
     mark(8);
-    k_merge<<<grid, kThreads, 0, stream>>>(P, sorted);
+    k_merge<<<g_grid_merge, kThreads, kMergeSmem, stream>>>(P, sorted);
     mark(9);
     k_finalize<<<1, 1024, 0, stream>>>(P);
     mark(10);

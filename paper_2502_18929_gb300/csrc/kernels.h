@@ -10,8 +10,8 @@ namespace qmc {
 constexpr int kThreads = 256;
 constexpr int kSortItems = 8;                        // records per thread per sort tile
 constexpr int kSortTile = kThreads * kSortItems;     // 2048 records
-constexpr int kMergeItems = 8;
-constexpr int kMergeTile = kThreads * kMergeItems;   // 2048 merged items
+constexpr int kMergeItems = 7;                       // 7 x 16 B stride: lanes spread over all bank groups
+constexpr int kMergeTile = kThreads * kMergeItems;   // 1792 merged items
 constexpr int kHeavyWalkers = 256;                   // parents above this go to the heavy path
 constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
@@ -73,6 +73,7 @@ struct StepParams {
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
 // launch sequence can be captured once in a CUDA graph and replayed.
 constexpr int kNumTimedKernels = 10;
+void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);

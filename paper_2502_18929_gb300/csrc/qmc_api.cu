@@ -255,7 +255,8 @@ int qmc_create(qmc_ctx** out, const qmc_config* cfg)
     auto bail = [&](int code) { qmc_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(QMC_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
-    ctx->grid = std::max(1, ctx->sm_count) * 4;
+    ctx->grid = std::max(1, ctx->sm_count) * 3;
+    configure_kernels();
     if (cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) != cudaSuccess) return bail(QMC_ERR_CUDA);
     if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(QMC_ERR_CUDA);
     const int nseg = cfg->n_segments;

@@ -38,6 +38,8 @@ static_assert(sizeof(SRec) == 16, "spawn record must be 16 bytes");
 struct ProgHeader {
     int32_t n_selffam, n_selfgen, n_fam, n_gen, n_gterm, n_entry;
     int32_t off_selffam, off_selfgen, off_fam, off_gen, off_gterm, off_entry;
+    int32_t n_aff, off_aff;
+    int64_t p_bound;                      // >= P of every state (filter for the spawn test)
     int64_t self_const_re, self_const_im; // parity-free part of the diagonal element
     int64_t p_const;                      // sum of |Re| + |Im| over constant groups
     int32_t bytes;                        // size of the whole blob
@@ -64,6 +66,19 @@ struct Fam {
     uint32_t ab;   // bit 1: alpha (ket flips q), bit 0: beta (bra flips q)
     int64_t a[4];  // |Re tab| + |Im tab|
     int64_t tre[4], tim[4];
+};
+
+// Affine form of everything that depends on (x, y) only through the three
+// counts cx = popc(x & M), cy = popc(y & M), c11 = popc(x & y & M) for one
+// member mask M: the self-family part of the diagonal element,
+//   s0 + sa cx + sb cy + sc c11   (complex),
+// and the summed weight of the families with that mask,
+//   f0 + fx cx + fy cy + f11 c11  (= sum over members of |Re T| + |Im T|).
+struct AffGroup {
+    uint32_t members;
+    uint32_t pad;
+    int64_t s0re, s0im, sare, saim, sbre, sbim, scre, scim;
+    int64_t f0, fx, fy, f11;
 };
 
 // Generic group: element = sum over terms [first, first + count) of +-Q'.

@@ -305,6 +305,63 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
         fams.push_back(f);
     }
 
+    // affine forms per member mask (self families and families)
+    std::map<uint32_t, AffGroup> aff;
+    auto group = [&](uint32_t M) -> AffGroup& {
+        auto it = aff.find(M);
+        if (it == aff.end()) {
+            AffGroup g{};
+            g.members = M;
+            it = aff.emplace(M, g).first;
+        }
+        return it->second;
+    };
+    for (const SelfFam& f : selffam) {
+        AffGroup& g = group(f.members);
+        const int64_t m = popc(f.members);
+        g.s0re += f.qre * m;
+        g.s0im += f.qim * m;
+        if (f.type == 0 || f.type == 2) { g.sare -= 2 * f.qre; g.saim -= 2 * f.qim; }
+        if (f.type == 1 || f.type == 2) { g.sbre -= 2 * f.qre; g.sbim -= 2 * f.qim; }
+        if (f.type == 2) { g.scre += 4 * f.qre; g.scim += 4 * f.qim; }
+    }
+    for (const Fam& f : fams) {
+        AffGroup& g = group(f.members);
+        const int64_t m = popc(f.members);
+        // pi = 2 x_q + y_q: a[0] (00), a[1] (01), a[2] (10), a[3] (11)
+        g.f0 += f.a[0] * m;
+        g.fx += f.a[2] - f.a[0];
+        g.fy += f.a[1] - f.a[0];
+        g.f11 += f.a[3] - f.a[2] - f.a[1] + f.a[0];
+    }
+    std::vector<AffGroup> affs;
+    for (const auto& kv : aff) affs.push_back(kv.second);
+
+    // Upper bound of P over all states (triangle inequality across groups; each
+    // affine form maximised exactly over its feasible counts).  Used only to
+    // skip the exact weight when a walker's draw already exceeds it.
+    {
+        int64_t b = std::llabs(hdr.self_const_re) + std::llabs(hdr.self_const_im);
+        for (const Gen& g : gen_c) b += std::llabs(g.cre) + std::llabs(g.cim);
+        for (const AffGroup& g : affs) {
+            const int m = popc(g.members);
+            int64_t best = 0;
+            for (int cx = 0; cx <= m; ++cx)
+                for (int cy = 0; cy <= m; ++cy)
+                    for (int c11 = std::max(0, cx + cy - m); c11 <= std::min(cx, cy); ++c11) {
+                        const int64_t er = g.s0re + g.sare * cx + g.sbre * cy + g.scre * c11;
+                        const int64_t ei = g.s0im + g.saim * cx + g.sbim * cy + g.scim * c11;
+                        const int64_t f = g.f0 + g.fx * cx + g.fy * cy + g.f11 * c11;
+                        best = std::max<int64_t>(best, (int64_t)(std::llabs(er) + std::llabs(ei)) + f);
+                    }
+            b += best;
+        }
+        for (const SelfGen& g : selfgen) b += std::llabs(g.qre) + std::llabs(g.qim);
+        for (size_t i = 0; i < gen_nc.size(); ++i)
+            for (const GTerm& g : gen_terms_nc[i]) b += std::llabs(g.qre) + std::llabs(g.qim);
+        hdr.p_bound = b;
+    }
+
     std::vector<Gen> gens;
     std::vector<GTerm> gterms;
     hdr.n_nonconst_gen = (int32_t)gen_nc.size();
@@ -355,6 +412,8 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     hdr.off_gen = (int32_t)off;     off = align8(off + gens.size() * sizeof(Gen));
     hdr.off_gterm = (int32_t)off;   off = align8(off + gterms.size() * sizeof(GTerm));
     hdr.off_entry = (int32_t)off;   off = align8(off + entries.size() * sizeof(Entry));
+    hdr.off_aff = (int32_t)off;     off = align8(off + affs.size() * sizeof(AffGroup));
+    hdr.n_aff = (int32_t)affs.size();
     hdr.bytes = (int32_t)off;
     blob->resize(base + off, 0);
     put(blob, base, &hdr, 1);
@@ -364,6 +423,7 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     put(blob, base + hdr.off_gen, gens.data(), gens.size());
     put(blob, base + hdr.off_gterm, gterms.data(), gterms.size());
     put(blob, base + hdr.off_entry, entries.data(), entries.size());
+    put(blob, base + hdr.off_aff, affs.data(), affs.size());
     return QMC_OK;
 }
 
