@@ -193,7 +193,7 @@ __global__ void k_prologue(StepParams P)
 // destinations in parallel, a warp scan gives the cumulative weights, and the
 // lane whose interval holds T wins.
 // ---------------------------------------------------------------------------
-constexpr int kProgSmem = 12288;
+constexpr int kProgSmem = 8192;
 
 __device__ __forceinline__ void warp_flush(SRec* stage, int n, const StepParams& P, int lane)
 {
@@ -210,42 +210,6 @@ __device__ __forceinline__ void warp_flush(SRec* stage, int n, const StepParams&
     __syncwarp();
 }
 
-// Warp-wide choice of (destination, channel) holding T in the column of
-// |x><y| (all lanes pass the same arguments).  Returns false if T is not
-// covered (impossible when T < P).
-__device__ __forceinline__ bool warp_choose(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim,
-                                            int64_t T, int lane, uint64_t* mask, int* chan, int64_t* v)
-{
-    const int ne = p.h->n_entry;
-    int64_t carry = 0;
-    for (int b0 = 0; b0 < ne; b0 += 32) {
-        const int e = b0 + lane;
-        int64_t vr = 0, vi = 0;
-        if (e < ne) entry_value(p, p.ent[e], x, y, sre, sim, &vr, &vi);
-        const int64_t wr = iabs64(vr), w = wr + iabs64(vi);
-        int64_t incl = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int64_t lo = carry + incl - w;
-        const bool hit = e < ne && T >= lo && T < lo + w;
-        const uint32_t bal = __ballot_sync(kFull, hit);
-        if (bal) {
-            const int win = __ffs(bal) - 1;
-            const int c = (T - lo < wr) ? 0 : 1;
-            const int64_t val = c ? vi : vr;
-            *chan = __shfl_sync(kFull, c, win);
-            *v = __shfl_sync(kFull, val, win);
-            *mask = __shfl_sync(kFull, e < ne ? p.ent[e].mask_key : 0ull, win);
-            return true;
-        }
-        carry += __shfl_sync(kFull, incl, 31);
-    }
-    return false;
-}
-
 // Copy a program into shared memory if it fits; returns the copy to use once
 // the block has synchronised (the caller must __syncthreads() before reading).
 __device__ __forceinline__ const uint8_t* stage_prog(const uint8_t* g, uint8_t* s)
@@ -255,6 +219,66 @@ __device__ __forceinline__ const uint8_t* stage_prog(const uint8_t* g, uint8_t* 
     for (int i = threadIdx.x; i < bytes / 8; i += blockDim.x)
         ((uint64_t*)s)[i] = ((const uint64_t*)g)[i];
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) copies into shared memory, completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (it > 16) __nanosleep(32);
+    }
+    set_error(st, DERR_TIMEOUT);
+    return false;
 }
 
 // A walker whose draw T lies below the step's bound on P: a spawn candidate.
@@ -346,16 +370,22 @@ __device__ __forceinline__ void enqueue2(SpawnEvent* q, int* qn, bool s0, bool s
     __syncwarp();
 }
 
+constexpr int kWarpTile = 256;   // parents per warp-owned staged tile (4 KB)
+constexpr int kSpawnSmemAll = kSpawnSmem + (kThreads / 32) * 2 * kWarpTile * 16;
+
 __global__ void __launch_bounds__(kThreads, 2) k_spawn_light(StepParams P)
 {
-    extern __shared__ __align__(16) uint8_t spawn_smem[];
+    extern __shared__ __align__(128) uint8_t spawn_smem[];
+    __shared__ __align__(8) uint64_t sbar[kThreads / 32][2];
     DevState* st = P.st;
     if (read_error(st)) return;
-    uint8_t* sprog0 = spawn_smem;
-    uint8_t* sprog1 = spawn_smem + kProgSmem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SpawnEvent* evq = (SpawnEvent*)(spawn_smem + 2 * kProgSmem) + warp * kEvQ;
-    SRec* stage = (SRec*)(spawn_smem + 2 * kProgSmem + (kThreads / 32) * kEvQ * sizeof(SpawnEvent)) + warp * kStage;
+    Rec* wtile = (Rec*)spawn_smem + warp * 2 * kWarpTile;   // this warp's 2 stages
+    uint8_t* sprog0 = spawn_smem + (kThreads / 32) * 2 * kWarpTile * 16;
+    uint8_t* sprog1 = sprog0 + kProgSmem;
+    SpawnEvent* evq = (SpawnEvent*)(sprog1 + kProgSmem) + warp * kEvQ;
+    SRec* stage = (SRec*)(sprog1 + kProgSmem + (kThreads / 32) * kEvQ * sizeof(SpawnEvent)) + warp * kStage;
+    uint64_t* bar = sbar[warp];
 
     const int ci = st->call_index;
     const StepInfo inf = P.info[ci];
@@ -363,9 +393,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_light(StepParams P)
     const int64_t K0 = st->count[cur];
     const int64_t K1 = inf.ab2 ? st->count[prv] : 0;
     const int64_t total = K0 + K1;
+    const Rec* src0 = P.pop[cur];
+    const Rec* src1 = P.pop[prv];
     const uint8_t* pb0 = stage_prog(P.progs + inf.prog_off[0], sprog0);
     const uint8_t* pb1 = stage_prog(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]), sprog1);
-    __syncthreads();
+    // each warp owns one contiguous range of parents, staged kWarpTile at a time
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    const int64_t chunk = ((total + nwarps - 1) / nwarps + 31) / 32 * 32;
+    const int64_t w_begin = min(total, gw * chunk);
+    const int64_t w_end = min(total, w_begin + chunk);
+    auto issue = [&](int64_t g0, int s) {
+        const int64_t g1 = min(w_end, g0 + kWarpTile);
+        const int64_t a1 = min(g1, K0);
+        const uint32_t na = g0 < a1 ? (uint32_t)(a1 - g0) : 0u;
+        const uint32_t nb = (uint32_t)(g1 - g0) - na;
+        mbar_arrive_expect(&bar[s], (na + nb) * 16u);
+        if (na) bulk_load(wtile + s * kWarpTile, src0 + g0, na * 16u, &bar[s]);
+        if (nb) bulk_load(wtile + s * kWarpTile + na, src1 + (g0 + na - K0), nb * 16u, &bar[s]);
+    };
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        if (w_begin < w_end) issue(w_begin, 0);
+    }
+    __syncthreads();   // programs staged, barriers initialised
     const Prog prog0 = prog_at(pb0);
     const Prog prog1 = prog_at(pb1);
     // filter: a walker can only spawn if T < P <= p_bound (every walker is a
@@ -373,149 +426,164 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_light(StepParams P)
     const int64_t lim52 = 1ll << 52;
     const int64_t bound0 = prog0.h->p_bound >= lim52 ? lim52 : prog0.h->p_bound;
     const int64_t bound1 = prog1.h->p_bound >= lim52 ? lim52 : prog1.h->p_bound;
-    const Rec* src0 = P.pop[cur];
-    const Rec* src1 = P.pop[prv];
     const int64_t* off0 = P.segoff[cur];
     const int64_t* off1 = P.segoff[prv];
     const int n = P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-
-    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
-    const int64_t chunk = ((total + nwarps - 1) / nwarps + 31) / 32 * 32;
-    const int64_t w_begin = gw * chunk;
-    const int64_t w_end = min(total, w_begin + chunk);
     int staged = 0, qn = 0;
     int cur_phase = -1, seg = 0;
     int64_t seg_end = 0;
+    uint32_t parity[2] = {0u, 0u};
+    bool timed_out[2] = {false, false};
+    int s = 0;
 
-    for (int64_t base = w_begin; base < w_end; base += 32) {
-        const int64_t i = base + lane;
-        const bool valid = i < w_end;
-        const int phase = (valid && i >= K0) ? 1 : 0;
-        const int64_t j = phase ? i - K0 : i;
-        if (valid && (phase != cur_phase || j >= seg_end)) {
-            const int64_t* off = phase ? off1 : off0;
-            seg = seg_of(off, P.nseg, j);
-            seg_end = off[seg + 1];
-            cur_phase = phase;
+    for (int64_t g0 = w_begin; g0 < w_end; g0 += kWarpTile) {
+        if (lane == 0 && g0 + kWarpTile < w_end) {
+            fence_proxy_async();
+            issue(g0 + kWarpTile, s ^ 1);
         }
-        Rec par{0ull, 0, 0};
-        int64_t m_re = 0, m_im = 0;
-        int my_pairs = 0, pairs_re = 0, noninit = 0;
-        if (valid) {
-            par = phase ? src1[j] : src0[j];
-            m_re = iabs64(par.re);
-            m_im = iabs64(par.im);
-            noninit = (P.init_min > 0 && (m_re + m_im) < P.init_min) ? 1 : 0;
-            if (m_re + m_im > kHeavyWalkers) {
-                for (int comp = 0; comp < 2; ++comp) {
-                    const int64_t m = comp ? m_im : m_re;
-                    const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
-                    if (chunks == 0) continue;
-                    const unsigned long long hb =
-                        atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
-                    for (int64_t c = 0; c < chunks; ++c) {
-                        const int64_t pos = (int64_t)hb + c;
-                        if (pos < P.heavy_cap) {
-                            HeavyItem it;
-                            it.parent = j;
-                            it.phase = phase;
-                            it.comp = comp;
-                            it.chunk = (int32_t)c;
-                            it.seg = seg;
-                            P.heavy[pos] = it;
-                        } else {
-                            set_error(st, DERR_HEAVY_CAPACITY);
+        const bool ok = mbar_wait(&bar[s], parity[s], st);
+        if (!ok) timed_out[s] = true;
+        parity[s] ^= 1u;
+        const Rec* tp = wtile + s * kWarpTile;
+        const int tn_items = (int)min((int64_t)kWarpTile, w_end - g0);
+        for (int it = 0; it < tn_items && ok; it += 32) {
+            const int li = it + lane;
+            const int64_t i = g0 + li;
+            const bool valid = li < tn_items;
+            const int phase = (valid && i >= K0) ? 1 : 0;
+            const int64_t j = phase ? i - K0 : i;
+            if (valid && (phase != cur_phase || j >= seg_end)) {
+                const int64_t* off = phase ? off1 : off0;
+                seg = seg_of(off, P.nseg, j);
+                seg_end = off[seg + 1];
+                cur_phase = phase;
+            }
+            Rec par{0ull, 0, 0};
+            int64_t m_re = 0, m_im = 0;
+            int my_pairs = 0, pairs_re = 0, noninit = 0;
+            if (valid) {
+                par = tp[li];
+                m_re = iabs64(par.re);
+                m_im = iabs64(par.im);
+                noninit = (P.init_min > 0 && (m_re + m_im) < P.init_min) ? 1 : 0;
+                if (m_re + m_im > kHeavyWalkers) {
+                    for (int comp = 0; comp < 2; ++comp) {
+                        const int64_t m = comp ? m_im : m_re;
+                        const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
+                        if (chunks == 0) continue;
+                        const unsigned long long hb =
+                            atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
+                        for (int64_t c = 0; c < chunks; ++c) {
+                            const int64_t pos = (int64_t)hb + c;
+                            if (pos < P.heavy_cap) {
+                                HeavyItem h;
+                                h.parent = j;
+                                h.phase = phase;
+                                h.comp = comp;
+                                h.chunk = (int32_t)c;
+                                h.seg = seg;
+                                P.heavy[pos] = h;
+                            } else {
+                                set_error(st, DERR_HEAVY_CAPACITY);
+                            }
                         }
                     }
+                } else {
+                    pairs_re = (int)((m_re + 1) / 2);
+                    my_pairs = pairs_re + (int)((m_im + 1) / 2);
                 }
-            } else {
-                pairs_re = (int)((m_re + 1) / 2);
-                my_pairs = pairs_re + (int)((m_im + 1) / 2);
             }
-        }
-        const int max_pairs = __reduce_max_sync(kFull, my_pairs);
-        if (max_pairs == 0) continue;
-        if (max_pairs == 1) {
-            // at most one walker pair per lane: each lane draws for its own parent
-            int64_t T0 = -1, T1 = -1;
-            uint32_t info = 0;
-            if (my_pairs == 1) {
-                const int comp = pairs_re ? 0 : 1;
-                const int64_t m = comp ? m_im : m_re;
-                const int64_t bnd = phase ? bound1 : bound0;
-                const uint4 w = philox10(
-                    make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                               (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), 0u),
-                    P.kd[seg]);
-                const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
-                const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
-                if (R0 < bnd) T0 = R0;
-                if (m > 1 && R1 < bnd) T1 = R1;
-                const int val = comp ? par.im : par.re;
-                info = (uint32_t)comp | ((uint32_t)phase << 1) | ((uint32_t)noninit << 2) | ((val > 0 ? 1u : 0u) << 3);
+            const int max_pairs = __reduce_max_sync(kFull, my_pairs);
+            if (max_pairs == 0) continue;
+            if (max_pairs == 1) {
+                int64_t T0 = -1, T1 = -1;
+                uint32_t info = 0;
+                if (my_pairs == 1) {
+                    const int comp = pairs_re ? 0 : 1;
+                    const int64_t m = comp ? m_im : m_re;
+                    const int64_t bnd = phase ? bound1 : bound0;
+                    const uint4 w = philox10(
+                        make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
+                                   (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), 0u),
+                        P.kd[seg]);
+                    const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
+                    const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
+                    if (R0 < bnd) T0 = R0;
+                    if (m > 1 && R1 < bnd) T1 = R1;
+                    const int val = comp ? par.im : par.re;
+                    info = (uint32_t)comp | ((uint32_t)phase << 1) | ((uint32_t)noninit << 2) |
+                           ((val > 0 ? 1u : 0u) << 3);
+                }
+                enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{par.key, T0, (uint32_t)seg, info},
+                         SpawnEvent{par.key, T1, (uint32_t)seg, info}, lane);
+                while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
+                continue;
             }
-            enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{par.key, T0, (uint32_t)seg, info},
-                     SpawnEvent{par.key, T1, (uint32_t)seg, info}, lane);
-            while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
-            continue;
-        }
-        // several pairs per lane: spread all pairs of the warp evenly over the lanes
-        int incl = my_pairs;
+            // several pairs per lane: spread all pairs of the warp evenly over the lanes
+            int incl = my_pairs;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int tot_pairs = __shfl_sync(kFull, incl, 31);
-        for (int r = 0; r < tot_pairs; r += 32) {
-            const int g = r + lane;
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                const int im = __shfl_sync(kFull, incl, mid);
-                if (im > g) hi = mid; else lo = mid + 1;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
             }
-            const int owner = lo;
-            const bool act = g < tot_pairs;
-            const int o_incl = __shfl_sync(kFull, incl, owner);
-            const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
-            const int local = g - (o_incl - o_pairs);
-            const uint64_t okey = __shfl_sync(kFull, par.key, owner);
-            const int o_pre = __shfl_sync(kFull, pairs_re, owner);
-            const int64_t o_mre = __shfl_sync(kFull, m_re, owner);
-            const int64_t o_mim = __shfl_sync(kFull, m_im, owner);
-            const int o_phase = __shfl_sync(kFull, phase, owner);
-            const int o_seg = __shfl_sync(kFull, seg, owner);
-            const int o_non = __shfl_sync(kFull, noninit, owner);
-            const int32_t o_re = __shfl_sync(kFull, par.re, owner);
-            const int32_t o_im = __shfl_sync(kFull, par.im, owner);
-            int64_t T0 = -1, T1 = -1;
-            uint32_t info = 0;
-            if (act) {
-                const int comp = local < o_pre ? 0 : 1;
-                const int j2 = comp ? local - o_pre : local;
-                const int64_t m = comp ? o_mim : o_mre;
-                const int64_t bnd = o_phase ? bound1 : bound0;
-                const uint4 w = philox10(
-                    make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
-                               (uint32_t)o_phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                    P.kd[o_seg]);
-                const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
-                const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
-                if (R0 < bnd) T0 = R0;
-                if (2 * (int64_t)j2 + 1 < m && R1 < bnd) T1 = R1;
-                const int val = comp ? o_im : o_re;
-                info = (uint32_t)comp | ((uint32_t)o_phase << 1) | ((uint32_t)o_non << 2) | ((val > 0 ? 1u : 0u) << 3);
+            const int tot_pairs = __shfl_sync(kFull, incl, 31);
+            for (int r = 0; r < tot_pairs; r += 32) {
+                const int g = r + lane;
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int im = __shfl_sync(kFull, incl, mid);
+                    if (im > g) hi = mid; else lo = mid + 1;
+                }
+                const int owner = lo;
+                const bool act = g < tot_pairs;
+                const int o_incl = __shfl_sync(kFull, incl, owner);
+                const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
+                const int local = g - (o_incl - o_pairs);
+                const uint64_t okey = __shfl_sync(kFull, par.key, owner);
+                const int o_pre = __shfl_sync(kFull, pairs_re, owner);
+                const int64_t o_mre = __shfl_sync(kFull, m_re, owner);
+                const int64_t o_mim = __shfl_sync(kFull, m_im, owner);
+                const int o_phase = __shfl_sync(kFull, phase, owner);
+                const int o_seg = __shfl_sync(kFull, seg, owner);
+                const int o_non = __shfl_sync(kFull, noninit, owner);
+                const int32_t o_re = __shfl_sync(kFull, par.re, owner);
+                const int32_t o_im = __shfl_sync(kFull, par.im, owner);
+                int64_t T0 = -1, T1 = -1;
+                uint32_t info = 0;
+                if (act) {
+                    const int comp = local < o_pre ? 0 : 1;
+                    const int j2 = comp ? local - o_pre : local;
+                    const int64_t m = comp ? o_mim : o_mre;
+                    const int64_t bnd = o_phase ? bound1 : bound0;
+                    const uint4 w = philox10(
+                        make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
+                                   (uint32_t)o_phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
+                        P.kd[o_seg]);
+                    const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
+                    const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
+                    if (R0 < bnd) T0 = R0;
+                    if (2 * (int64_t)j2 + 1 < m && R1 < bnd) T1 = R1;
+                    const int val = comp ? o_im : o_re;
+                    info = (uint32_t)comp | ((uint32_t)o_phase << 1) | ((uint32_t)o_non << 2) |
+                           ((val > 0 ? 1u : 0u) << 3);
+                }
+                enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{okey, T0, (uint32_t)o_seg, info},
+                         SpawnEvent{okey, T1, (uint32_t)o_seg, info}, lane);
+                while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
             }
-            enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{okey, T0, (uint32_t)o_seg, info},
-                     SpawnEvent{okey, T1, (uint32_t)o_seg, info}, lane);
-            while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
         }
+        __syncwarp();   // the warp's stage is read before it is refilled
+        s ^= 1;
     }
     while (qn > 0) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
     if (staged) warp_flush(stage, staged, P, lane);
+    if (lane == 0) {
+        for (int q = 0; q < 2; ++q)
+            if (timed_out[q]) mbar_wait(&bar[q], parity[q] ^ 1u, st);
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -924,66 +992,6 @@ __global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
 }
 
 // ---------------------------------------------------------------------------
-// Bulk (TMA) copies into shared memory, completed on an mbarrier.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes a
-// multiple of 16.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for a phase of an mbarrier.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st)
-{
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (it > 16) __nanosleep(32);
-    }
-    set_error(st, DERR_TIMEOUT);
-    return false;
-}
-
-// ---------------------------------------------------------------------------
 // Annihilation.  A run is all items (at most one N(t) record and any number of
 // spawn records) with one key.  Value = N(t) + initiator spawns +
 // (occupied ? non-initiator spawns : 0); zero runs are dropped.  Tiles of the
@@ -1157,7 +1165,7 @@ __device__ __forceinline__ void merge_issue(const MTile& m, const Rec* A, const 
     if (bbytes) bulk_load(buf + m.na, sorted + m.b_glob, bbytes, bar);
 }
 
-constexpr int kMergeSmem = 2 * kMergeTile * 16;
+constexpr int kMergeSmem = 2 * kMergeTile * 16;   // 2 input stages
 
 __global__ void __launch_bounds__(kThreads, 3) k_merge(StepParams P, const SRec* __restrict__ sorted)
 {
@@ -1497,11 +1505,11 @@ int resident(const void* fn, int smem, int sms)
 void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
-    cudaFuncSetAttribute(k_spawn_light, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpawnSmem);
+    cudaFuncSetAttribute(k_spawn_light, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpawnSmemAll);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_grid_spawn = resident((const void*)k_spawn_light, kSpawnSmem, sms);
+    g_grid_spawn = resident((const void*)k_spawn_light, kSpawnSmemAll, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms);
@@ -1517,7 +1525,7 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(0);
     k_prologue<<<1, kThreads, 0, stream>>>(P);
     mark(1);
-    k_spawn_light<<<g_grid_spawn, kThreads, kSpawnSmem, stream>>>(P);
+    k_spawn_light<<<g_grid_spawn, kThreads, kSpawnSmemAll, stream>>>(P);
     mark(2);
     k_spawn_heavy<<<g_grid_heavy, kThreads, 0, stream>>>(P);
     mark(3);

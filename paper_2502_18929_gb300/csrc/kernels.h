@@ -17,6 +17,7 @@ constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work i
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
 constexpr int kMaxPasses = 12;
 constexpr int kCtrMerge = kMaxPasses;                // tile counter index of the merge
+constexpr int kCtrSpawn = kMaxPasses + 1;            // tile counter index of the light spawn
 constexpr uint32_t kTagStep = 0x53544550u;
 constexpr uint32_t kTagInit = 0x494E4954u;
 constexpr uint32_t kKindSpawn = 0u;
