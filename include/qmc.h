@@ -230,6 +230,36 @@ int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* ps
 int qmc_checkpoint(qmc_ctx* ctx, const char* path);
 int qmc_restore(qmc_ctx* ctx, const char* path);
 
+/* ---- observables without device allocation -------------------------------- */
+
+/* Largest n_segments accepted by qmc_observables_noalloc. */
+#define QMC_NOALLOC_MAX_SEGMENTS 4096
+
+/* Per-vector observables (as qmc_observables) of a population the caller keeps
+ * in device memory, computed without allocating any device memory.  The paper
+ * has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code running under an external memory manager that has already
+ * reserved the device memory, and code that must not risk the implicit
+ * synchronisation cudaMalloc and cudaFree can cause.
+ *   records      device, 16 bytes per record (uint64 key (x << n) | y,
+ *                int32 re, int32 im), 16-byte aligned, sorted by vector
+ *   seg_offsets  device, n_segments + 1 int64 offsets of each vector's records
+ *   out          device, n_segments qmc_obs, written
+ *   cuda_stream  stream to issue the work on (0 = legacy default stream);
+ *                the call returns without synchronising it.
+ * The accumulators are a library-owned static device array of
+ * QMC_NOALLOC_MAX_SEGMENTS entries (128 KiB), held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (set-up, once per device, with that device current);
+ * make this first call before any stream capture.  Every call clears and
+ * reuses the same array, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race: serialise them.
+ * Errors: INVALID_ARG (null pointers, n_segments < 1 or above
+ * QMC_NOALLOC_MAX_SEGMENTS, n_qubits outside 1..32, records not 16-byte
+ * aligned), CUDA (set-up or launch failed). */
+int qmc_observables_noalloc(const void* records, const int64_t* seg_offsets, int32_t n_segments,
+                            int32_t n_qubits, qmc_obs* out, void* cuda_stream);
+
 /* ---- host-only utility -------------------------------------------------- */
 
 /* Compile the column of dt_eff * L(t) [Eq. (2)] exactly as qmc_step does and

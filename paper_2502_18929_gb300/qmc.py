@@ -34,7 +34,7 @@ EXPORTED = [
     "qmc_create", "qmc_destroy", "qmc_last_error", "qmc_load_schedule", "qmc_init_populations",
     "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
-    "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters",
+    "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
 ]
 
 
@@ -115,6 +115,7 @@ def lib():
         L.qmc_restore.argtypes = [vp, C.c_char_p]
         L.qmc_step_profile.argtypes = [vp, C.c_double, C.c_int64, vp, C.c_int32, vp]
         L.qmc_counters.argtypes = [vp, C.c_int32, vp]
+        L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
         for name in EXPORTED:
