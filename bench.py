@@ -89,6 +89,64 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def host_inputs(wl, rank):
+    """Synthetic inputs in pinned host memory (generated before any timing)."""
+    import torch
+    if "spread" not in wl:
+        return None
+    pops = [P.spread_population(wl["prob"].n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
+    counts = np.array([len(p[0]) for p in pops], dtype=np.int64)
+    keys = torch.from_numpy(np.concatenate([p[0] for p in pops]).view(np.int64)).pin_memory()
+    re = torch.from_numpy(np.concatenate([p[1] for p in pops])).pin_memory()
+    im = torch.from_numpy(np.concatenate([p[2] for p in pops])).pin_memory()
+    return counts, keys, re, im
+
+
+def load_inputs(sim, wl, inputs):
+    """Upload the inputs; returns the bytes copied host -> device."""
+    if inputs is None:
+        sim.init_populations(wl["rho0"])
+        return len(wl["rho0"]) * 32
+    counts, keys, re, im = inputs
+    sim.set_populations_packed(counts, keys.numpy().view(np.uint64), re.numpy(), im.numpy())
+    sim.set_clock(0, wl["t_start"])
+    return int(keys.numel() * 8 + re.numel() * 4 + im.numel() * 4 + counts.nbytes)
+
+
+def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist):
+    import torch
+    from paper_2502_18929_gb300 import qmc
+    prob = wl["prob"]
+    sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
+                  initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
+    sim.load_schedule(prob)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    h2d = load_inputs(sim, wl, inputs)
+    d2h = 0
+    walkers = 0
+    idx = 0
+    for tp0, d, n in pl:
+        lo, hi = idx, idx + n
+        idx = hi
+        b = min(hi, nsteps)
+        if lo >= b:
+            break
+        step, _, tpp, dl, pv = sim.clock()
+        sim.set_clock(step, tp0, tpp, dl, pv)
+        sim.step(d, b - lo)
+        hist = sim.step_history()
+        d2h += hist.nbytes
+        walkers += int(hist[:, :, 1].sum())
+        h2d += 0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sim.close()
+    return {"seconds": t1 - t0, "walker_steps": walkers, "h2d_bytes": h2d, "d2h_bytes": d2h}
+
+
 def step_list(wl):
     pl = planner.plan(wl["prob"], wl["t_end"], wl["dt"], t_start=wl.get("t_start", 0.0))
     return pl
@@ -161,6 +219,34 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def source_sha() -> str:
+    import hashlib
+    src = b"".join(open(os.path.join(ROOT, "paper_2502_18929_gb300", "csrc", f), "rb").read()
+                   for f in ("kernels.cu", "column_eval.h", "kernels.h", "qmc_types.h"))
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, units_launch: float):
+    """DRAM bytes (read + write) of one launch of `kernel`, scaled from the ncu
+    capture summarised in profiles/ by the units processed (parents plus spawn
+    records for the spawn kernel; merged items plus outputs for the merge).
+    None when no capture exists or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_spread32s.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    import re
+    sha = re.search(r"sha256\[:16\] = ([0-9a-f]+)", txt)
+    units = re.search(r"Units of the captured launch: ([0-9]+)", txt)
+    rd = re.search(r"\| DRAM read \| ([0-9.]+) (\w+)", txt)
+    wr = re.search(r"\| DRAM write \| ([0-9.]+) (\w+)", txt)
+    if not (sha and units and rd and wr) or sha.group(1) != source_sha():
+        return None
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    total = float(rd.group(1)) * scale.get(rd.group(2), 1.0) + float(wr.group(1)) * scale.get(wr.group(2), 1.0)
+    return total * units_launch / float(units.group(1))
+
+
 def kernel_bytes(name: str, c: dict) -> float:
     """Algorithmic bytes of a kernel over the counted steps (16-byte records)."""
     r = 16.0
@@ -202,18 +288,8 @@ def run_gpu(args, rank: int, world: int):
     if W + K > total:
         raise SystemExit(f"workload has {total} steps; warmup + steps = {W + K}")
 
-    # host inputs are generated first; the e2e leg starts with their upload
-    pops = None
-    if "spread" in wl:
-        pops = [P.spread_population(prob.n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
-    t_e2e0 = time.perf_counter()
-    if pops is not None:
-        h2d_init = sum(k.nbytes + r.nbytes + i.nbytes for k, r, i in pops)
-        sim.set_populations(pops)
-        sim.set_clock(0, wl["t_start"])
-    else:
-        h2d_init = len(wl["rho0"]) * 32
-        sim.init_populations(wl["rho0"])
+    inputs = host_inputs(wl, rank)
+    load_inputs(sim, wl, inputs)
     run_range(sim, pl, 0, W)
     torch.cuda.synchronize()
     sim.counters(reset=True)
@@ -242,19 +318,7 @@ def run_gpu(args, rank: int, world: int):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     c = sim.counters(reset=True)
-    # D2H read of the per-vector observables of the final state (the result)
-    obs = sim.observables()
-    t_e2e1 = time.perf_counter()
     walkers = c["walker_steps"]
-    if dist is not None:
-        tt = torch.tensor([ms, float(walkers), t_e2e1 - t_e2e0], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = tt.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        ms_all, walkers_all, e2e_s = mx[0].item(), sm_[1].item(), mx[2].item()
-    else:
-        ms_all, walkers_all, e2e_s = ms, float(walkers), t_e2e1 - t_e2e0
 
     # per-kernel times over the same timed steps (replayed from the checkpoint)
     roof = None
@@ -286,11 +350,30 @@ def run_gpu(args, rank: int, world: int):
         avg_ms = kernel_ms[top] / max(1, launches)
         bytes_per_launch = kernel_bytes(top, cp) / max(1, launches)
         achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+        units = {"k_spawn_light": cp["k_cur"] + cp["k_prev"] + cp["spawns"],
+                 "k_merge": cp["k_cur"] + cp["spawns"] + cp["k_next"]}.get(top, 0) / max(1, launches)
+        traffic = measured_traffic(top, units) if units else None
         roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "avg_launch_ms": round(avg_ms, 5),
+                "traffic": None if traffic is None else round(traffic), "avg_launch_ms": round(avg_ms, 5),
                 "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "kernel_share": {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}}
+
+    # end to end through the public API: a fresh context, inputs uploaded from
+    # pinned host memory, every step, and a D2H read of each call's per-step
+    # observables (the step's result), timed on the host clock
+    sim.close()
+    e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist)
+    if dist is not None:
+        tt = torch.tensor([ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])],
+                          dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm_ = tt.clone()
+        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+        ms_all, walkers_all, e2e_s, e2e_w = mx[0].item(), sm_[1].item(), mx[2].item(), sm_[3].item()
+    else:
+        ms_all, walkers_all, e2e_s, e2e_w = ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -314,8 +397,10 @@ def run_gpu(args, rank: int, world: int):
                    "l2": ("inputs larger than L2" if ws > L2_BYTES else
                           "working set below L2 (no flush between steps)"),
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": walkers_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_init / max(1, W + K),
-                "d2h_bytes_per_step": obs.nbytes / max(1, K)},
+        "e2e": {"value": e2e_w / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d_bytes"] / (W + K),
+                "d2h_bytes_per_step": e2e["d2h_bytes"] / (W + K), "steps": W + K,
+                "includes": "input upload from pinned host memory, all warm-up and timed steps, "
+                            "D2H of per-step observables after every call"},
         "gpu_launches": int(c["steps"] * (9 + npasses)),
         "clocks": clocks,
     }

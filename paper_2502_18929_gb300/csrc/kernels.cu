@@ -25,6 +25,7 @@ namespace qmc {
 
 namespace {
 
+int g_grid_misc = 0;   // grid of the simple grid-stride kernels (set by configure_kernels)
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
@@ -1429,7 +1430,9 @@ __global__ void k_init_compact(StepParams P, const uint64_t* __restrict__ keys, 
     }
 }
 
-// Per-segment K, N_tot, N^diag of one population slot.
+// Per-segment K, N_tot, N^diag of one population slot.  Each block takes a
+// contiguous range; a thread accumulates while its segment stays the same and
+// flushes with atomics when it changes (records are sorted by segment).
 __global__ void k_obs(StepParams P, int which, SegStats* __restrict__ out)
 {
     const DevState* st = P.st;
@@ -1439,17 +1442,36 @@ __global__ void k_obs(StepParams P, int which, SegStats* __restrict__ out)
     const int64_t K = off[P.nseg];
     const int n = P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(K, b0 + per);
+    int cs = -1;
+    int64_t cs_end = 0;
+    unsigned long long c = 0;
+    long long ntot = 0, dre = 0, dim = 0;
+    auto flush = [&]() {
+        if (cs < 0 || c == 0) return;
+        atomicAdd(&out[cs].count, c);
+        atomicAdd((unsigned long long*)&out[cs].ntot, (unsigned long long)ntot);
+        atomicAdd((unsigned long long*)&out[cs].dre, (unsigned long long)dre);
+        atomicAdd((unsigned long long*)&out[cs].dim, (unsigned long long)dim);
+    };
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        if (cs < 0 || i >= cs_end) {
+            flush();
+            cs = seg_of(off, P.nseg, i);
+            cs_end = off[cs + 1];
+            c = 0;
+            ntot = dre = dim = 0;
+        }
         const Rec r = pop[i];
-        const int s = seg_of(off, P.nseg, i);
-        const long long a = (r.re < 0 ? -(long long)r.re : r.re) + (r.im < 0 ? -(long long)r.im : r.im);
-        atomicAdd(&out[s].count, 1ull);
-        atomicAdd((unsigned long long*)&out[s].ntot, (unsigned long long)a);
+        ++c;
+        ntot += (r.re < 0 ? -(long long)r.re : r.re) + (r.im < 0 ? -(long long)r.im : r.im);
         if ((uint32_t)(r.key >> n) == (uint32_t)(r.key & ymask)) {
-            atomicAdd((unsigned long long*)&out[s].dre, (unsigned long long)(long long)r.re);
-            atomicAdd((unsigned long long*)&out[s].dim, (unsigned long long)(long long)r.im);
+            dre += r.re;
+            dim += r.im;
         }
     }
+    flush();
 }
 
 // Values of query keys in one segment of N(t) (0 when absent).
@@ -1473,7 +1495,36 @@ __global__ void k_lookup(StepParams P, int seg, const uint64_t* __restrict__ q, 
     }
 }
 
+// Pack host-uploaded (key, re, im) arrays into records of one slot and check
+// them: keys ascending within each vector, below 2^(2n), values nonzero and not
+// -2^31.  A violation sets *bad (the caller rejects the call).
+__global__ void k_pack_records(const uint64_t* __restrict__ keys, const int32_t* __restrict__ re,
+                               const int32_t* __restrict__ im, const int64_t* __restrict__ off, int nseg, int n,
+                               Rec* __restrict__ dst, int* bad)
+{
+    const int64_t K = off[nseg];
+    const uint64_t lim = n == 32 ? ~0ull : ((1ull << (2 * n)) - 1ull);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[i];
+        const int32_t a = re[i], b = im[i];
+        bool ok = (key & ~lim) == 0 && (a != 0 || b != 0) && a != INT32_MIN && b != INT32_MIN;
+        if (ok && i > 0 && keys[i - 1] >= key) {
+            // a new vector may start at i
+            const int s = seg_of(off, nseg, i);
+            if (off[s] != i) ok = false;
+        }
+        if (!ok) atomicExch(bad, 1);
+        dst[i] = Rec{key, a, b};
+    }
+}
+
 } // namespace
+
+void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg, int n,
+                 Rec* dst, int* bad, cudaStream_t stream)
+{
+    k_pack_records<<<g_grid_misc ? g_grid_misc : 304, kThreads, 0, stream>>>(keys, re, im, off, nseg, n, dst, bad);
+}
 
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream)
 {
@@ -1492,7 +1543,7 @@ const char* const kKernelNames[kNumTimedKernels] = {
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0, g_grid_misc = 0;
+int g_grid_spawn = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0;
 
 int resident(const void* fn, int smem, int sms)
 {

@@ -400,17 +400,7 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
         off[s + 1] = off[s] + counts[s];
     }
     const int64_t total = off[nseg];
-    const uint64_t lim = ctx->cfg.n_qubits == 32 ? ~0ull : ((1ull << (2 * ctx->cfg.n_qubits)) - 1);
-    std::vector<Rec> recs(total);
-    for (int s = 0; s < nseg; ++s) {
-        for (int64_t i = off[s]; i < off[s + 1]; ++i) {
-            if (keys[i] & ~lim) return fail(ctx, QMC_ERR_INVALID_ARG, "key beyond 2n bits");
-            if (re[i] == 0 && im[i] == 0) return fail(ctx, QMC_ERR_INVALID_ARG, "zero record");
-            if (re[i] == INT32_MIN || im[i] == INT32_MIN) return fail(ctx, QMC_ERR_INVALID_ARG, "value -2^31");
-            if (i > off[s] && keys[i] <= keys[i - 1]) return fail(ctx, QMC_ERR_INVALID_ARG, "keys not ascending");
-            recs[i] = Rec{keys[i], re[i], im[i]};
-        }
-    }
+    if (total > 0 && (!keys || !re || !im)) return fail(ctx, QMC_ERR_INVALID_ARG, "null arrays");
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     if (total > ctx->pop_cap && (rc = grow_pop(ctx, total)) != QMC_OK) return rc;
@@ -418,9 +408,42 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
     CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
     const int slot = which == 0 ? hs.cur : (hs.cur + 2) % 3;
-    if (total)
-        CK(cudaMemcpyAsync(ctx->d_pop[slot], recs.data(), total * sizeof(Rec), cudaMemcpyHostToDevice, ctx->work));
+    // upload the caller's arrays as they are (pinned memory copies at full
+    // link speed), then pack and check on the device
+    uint64_t* d_keys = nullptr;
+    int32_t *d_re = nullptr, *d_im = nullptr;
+    int* d_bad = nullptr;
+    if ((rc = dalloc(ctx, &d_keys, total)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_re, total)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_im, total)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_bad, 1)) != QMC_OK) return rc;
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), ctx->work));
+    if (total) {
+        CK(cudaMemcpyAsync(d_keys, keys, total * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_re, re, total * 4, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_im, im, total * 4, cudaMemcpyHostToDevice, ctx->work));
+    }
     CK(cudaMemcpyAsync(ctx->d_segoff[slot], off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+    if (total) launch_pack(d_keys, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->cfg.n_qubits, ctx->d_pop[slot], d_bad,
+                           ctx->work);
+    CK(cudaGetLastError());
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    cudaFree(d_keys);
+    cudaFree(d_re);
+    cudaFree(d_im);
+    cudaFree(d_bad);
+    if (bad) {
+        // leave the slot empty rather than half-valid
+        std::vector<int64_t> zero(nseg + 1, 0);
+        CK(cudaMemcpyAsync(ctx->d_segoff[slot], zero.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+        hs.count[slot] = 0;
+        CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        return fail(ctx, QMC_ERR_INVALID_ARG,
+                    "records must be nonzero, keys < 2^(2n) and strictly ascending within each vector");
+    }
     hs.count[slot] = total;
     hs.error = 0;
     CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));

@@ -209,6 +209,16 @@ class QMC:
         self._check(self.L.qmc_set_populations(self.h, which, _ptr(counts), _ptr(keys), _ptr(re), _ptr(im)),
                     "qmc_set_populations")
 
+    def set_populations_packed(self, counts, keys, re, im, which: int = 0):
+        """As set_populations, from back-to-back arrays (any host memory; pinned
+        memory uploads at full link speed)."""
+        counts = _arr(counts, np.int64)
+        for a, dt in ((keys, np.uint64), (re, np.int32), (im, np.int32)):
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("keys must be C-contiguous uint64 and re/im int32")
+        self._check(self.L.qmc_set_populations(self.h, which, _ptr(counts), _ptr(keys), _ptr(re), _ptr(im)),
+                    "qmc_set_populations")
+
     def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
                   prev_valid: bool = False):
         self._check(self.L.qmc_set_clock(self.h, step, t, t_prev, dt_last, int(prev_valid)), "qmc_set_clock")
