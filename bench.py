@@ -1,7 +1,7 @@
 """Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload dd12|ghz4|spread32|ghzN]
+                    [--workload spread32|spread32s|dd12|ghz4|ghzN|ghzNi]
 
 One "step" is one dt step of every population vector through the whole hot
 path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
@@ -9,10 +9,12 @@ of the spawns, annihilation + initiator rule + compaction, per-vector
 observables.  value = sum over the timed steps of N_tot (walkers of N(t + dt),
 all vectors, all ranks) / max-over-ranks device time.
 
-Default workload ``dd12``: staggered-XX dynamical decoupling on a 12-qubit ring
-with ZZ crosstalk, 64 vectors x 1e6 walkers, dt = 0.005 (pulse windows
-sub-stepped so p < 1/2), t in [0, 20).  By default the timed region is the
-whole trajectory after the warm-up steps.
+Default workload ``spread32``: the 32-qubit GHZ Liouvillian (CNOT 4 -> 5
+window, amplitude damping and dephasing on every qubit), 64 vectors holding
+1e8 distinct random states of one walker each, dt = 0.01 (AB2), t from 5.0:
+the working set (1.6 GB per population slot) is far larger than L2.  The other
+workloads (dd12: staggered-XX dynamical decoupling on a 12-qubit ring, whose
+populations fit in L2; ghzN: GHZ preparation from |0><0|) run the same path.
 
 Multi-GPU: vectors are independent, so each rank runs its own 64 vectors
 (seed offset by rank) with no collective on the data path ("weak" scaling).
@@ -229,7 +231,7 @@ def source_sha() -> str:
 def measured_traffic(kernel: str, units_launch: float):
     """DRAM bytes (read + write) of one launch of `kernel`, scaled from the ncu
     capture summarised in profiles/ by the units processed (parents plus spawn
-    records for the spawn kernel; merged items plus outputs for the merge).
+    candidates for the draw kernel; merged items plus outputs for the merge).
     None when no capture exists or the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_spread32s.md")
     if not os.path.exists(path):
@@ -250,8 +252,10 @@ def measured_traffic(kernel: str, units_launch: float):
 def kernel_bytes(name: str, c: dict) -> float:
     """Algorithmic bytes of a kernel over the counted steps (16-byte records)."""
     r = 16.0
-    if name == "k_spawn_light":
-        return r * (c["k_cur"] + c["k_prev"] + c["spawns"])
+    if name == "k_spawn_draw":     # parents read, candidates written
+        return r * (c["k_cur"] + c["k_prev"] + c["candidates"])
+    if name == "k_spawn_choose":   # candidates and their parents' keys read, spawn records written
+        return (r + 8.0) * c["candidates"] + r * c["spawns"]
     if name == "k_merge":
         return r * (c["k_cur"] + c["spawns"] + c["k_next"])
     if name == "k_sort_scatter":
@@ -350,7 +354,7 @@ def run_gpu(args, rank: int, world: int):
         avg_ms = kernel_ms[top] / max(1, launches)
         bytes_per_launch = kernel_bytes(top, cp) / max(1, launches)
         achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-        units = {"k_spawn_light": cp["k_cur"] + cp["k_prev"] + cp["spawns"],
+        units = {"k_spawn_draw": cp["k_cur"] + cp["k_prev"] + cp["candidates"],
                  "k_merge": cp["k_cur"] + cp["spawns"] + cp["k_next"]}.get(top, 0) / max(1, launches)
         traffic = measured_traffic(top, units) if units else None
         roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,

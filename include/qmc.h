@@ -205,7 +205,9 @@ int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* cou
  * out[0] steps, [1] walker-steps (sum over steps of N_tot of N(t + dt)),
  * [2] records read from N(t), [3] records read from N(t - dt) (AB2 steps),
  * [4] spawn records, [5] records written to N(t + dt), [6] heavy work items,
- * [7] reserved (0).  reset != 0 zeroes them after reading.  Synchronises. */
+ * [7] spawn candidates (walker draws below the step's bound on p, each
+ * checked against the exact column).  reset != 0 zeroes them after reading.
+ * Synchronises. */
 int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out);
 
 /* Copy the records of vector seg (which = 0: N(t), 1: N(t - dt)) to host

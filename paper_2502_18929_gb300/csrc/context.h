@@ -15,6 +15,7 @@ using qmc::HeavyItem;
 using qmc::Rec;
 using qmc::Schedule;
 using qmc::SegStats;
+using qmc::SpawnCand;
 using qmc::SRec;
 using qmc::StepInfo;
 
@@ -38,6 +39,8 @@ struct qmc_ctx {
     SRec* d_spawn = nullptr;
     SRec* d_spawn_alt = nullptr;
     int64_t spawn_cap = 0;
+    SpawnCand* d_cand = nullptr;
+    int64_t cand_cap = 0;
     HeavyItem* d_heavy = nullptr;
     int64_t heavy_cap = 0;
     uint2* d_kd = nullptr;

@@ -1,7 +1,9 @@
 // One step of real-time population-dynamics QMC on sm_103a (arXiv:2502.18929).
 //
 //   k_prologue      per-step Philox keys, counter resets
-//   k_spawn_light   spawning [End Matter, spawn step] for parents with few walkers
+//   k_spawn_draw    walker draws [End Matter, spawn step] for parents with few
+//                   walkers; draws below the bound on P become candidates
+//   k_spawn_choose  exact spawn test and destination of every candidate
 //   k_spawn_heavy   the same for heavy parents, one CTA per walker chunk,
 //                   aggregated per destination in shared memory
 //   k_sort_hist     digit histograms of all LSD radix passes
@@ -179,6 +181,7 @@ __global__ void k_prologue(StepParams P)
     for (int i = threadIdx.x; i < kMaxTileCounters; i += blockDim.x) st->tile_ctr[i] = 0u;
     if (threadIdx.x == 0) {
         st->spawn_total = 0;
+        st->cand_total = 0;
         st->heavy_total = 0;
         st->next_total = 0;
         st->merge_tiles = 0;
@@ -187,12 +190,14 @@ __global__ void k_prologue(StepParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Spawning, light parents.  A warp takes 32 consecutive parents; their
-// walker pairs (one Philox call per two walkers) are spread evenly over the
-// lanes.  T = R >> 12 (52 bits); the walker spawns iff T < P.  The
-// destination of a spawned walker is chosen by the whole warp: lanes evaluate
-// destinations in parallel, a warp scan gives the cumulative weights, and the
-// lane whose interval holds T wins.
+// Spawning, light parents [End Matter, spawn step], in two kernels.
+//   k_spawn_draw: a warp takes consecutive parents; their walker pairs (one
+//     Philox call per two walkers) are spread evenly over the lanes; a walker
+//     whose T = R >> 12 (52 bits) lies below the program's bound on P becomes
+//     a candidate.  Parents with many walkers become heavy work items.
+//   k_spawn_choose: one thread per candidate evaluates the exact weight P of
+//     the parent's column; the walker spawns iff T < P, onto the destination
+//     whose cumulative-weight interval holds T (canonical order).
 // ---------------------------------------------------------------------------
 constexpr int kProgSmem = 8192;
 
@@ -282,19 +287,8 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st)
     return false;
 }
 
-// A walker whose draw T lies below the step's bound on P: a spawn candidate.
-struct SpawnEvent {
-    uint64_t key;
-    int64_t T;
-    uint32_t seg;
-    uint32_t info; // bit0 comp, bit1 phase, bit2 noninit, bit3 parent component > 0
-};
-
-constexpr int kEvQ = 96;
-constexpr int kSpawnSmem = 2 * kProgSmem + (kThreads / 32) * (kEvQ * (int)sizeof(SpawnEvent) + kStage * 16);
-
-// Destination (entry, channel) holding T, found by one lane walking the
-// column in canonical order.
+// Destination (entry, channel) holding T, found by walking the column in
+// canonical order.
 __device__ __forceinline__ bool lane_choose(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim,
                                             int64_t T, uint64_t* mask, int* chan, int64_t* v)
 {
@@ -313,278 +307,356 @@ __device__ __forceinline__ bool lane_choose(const Prog& p, uint32_t x, uint32_t 
     return false;
 }
 
-// Resolve up to 32 queued candidates, one per lane: exact weight P of the
-// parent's column, the spawn test T < P, and the destination.
-__device__ __forceinline__ void drain_events(SpawnEvent* q, int* qn, SRec* stage, int* staged, const Prog& prog0,
-                                             const Prog& prog1, const StepParams& P, int n, uint32_t ymask, int lane)
+constexpr int kCandStage = 128;   // candidates staged per warp
+constexpr int kCandFlush = 64;    // a warp flushes once more than this are staged
+constexpr uint64_t kT52 = (1ull << 52) - 1ull;
+
+// Append a warp's staged candidates to the candidate list of the step.
+__device__ __forceinline__ void cand_flush(const SpawnCand* stage, int n, const StepParams& P, int lane)
 {
-    const int cnt = *qn < 32 ? *qn : 32;
-    SRec rec;
-    bool ok = false;
-    if (lane < cnt) {
-        const SpawnEvent ev = q[lane];
-        const int comp = ev.info & 1u, phase = (ev.info >> 1) & 1u, non = (ev.info >> 2) & 1u;
-        const int sg = (ev.info >> 3) & 1u ? 1 : -1;
-        const uint32_t x = (uint32_t)(ev.key >> n), y = (uint32_t)(ev.key & ymask);
-        const Prog& prog = phase ? prog1 : prog0;
-        int64_t sre, sim;
-        const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
-        if (Pw >= (1ll << 52)) {
-            set_error(P.st, DERR_DT_TOO_LARGE);
-        } else if (ev.T < Pw) {
-            uint64_t mk;
-            int chan;
-            int64_t v;
-            ok = lane_choose(prog, x, y, sre, sim, ev.T, &mk, &chan, &v);
-            if (ok) rec = make_spawn(ev.key ^ mk, (int)ev.seg, comp, chan, v, sg, phase ? -1 : 1, non, 1);
-            else set_error(P.st, DERR_TILE_CAPACITY);
-        }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long*)&P.st->cand_total, (unsigned long long)n);
+    base = __shfl_sync(kFull, base, 0);
+    if ((int64_t)base + n > P.cand_cap && lane == 0) set_error(P.st, DERR_CAND_CAPACITY);
+    const uint4* s4 = (const uint4*)stage;
+    uint4* d4 = (uint4*)P.cand;
+    for (int j = lane; j < n; j += 32) {
+        const int64_t pos = (int64_t)base + j;
+        if (pos < P.cand_cap) d4[pos] = s4[j];
     }
     __syncwarp();
-    const int rest = *qn - cnt;
-    for (int j = lane; j < rest; j += 32) {
-        const SpawnEvent e2 = q[cnt + j];
-        __syncwarp(__activemask());
-        q[j] = e2;
-    }
+}
+
+// Stage the lanes' candidates c0 (first walker of the pair) and c1 (second);
+// flushes once the stage holds more than kCandFlush.  Whole warp.
+__device__ __forceinline__ void cand_push(SpawnCand* stage, int* staged, bool c0, bool c1, uint32_t parent,
+                                          uint32_t seg, uint64_t t0, uint64_t t1, const StepParams& P, int lane)
+{
+    const uint32_t b0 = __ballot_sync(kFull, c0), b1 = __ballot_sync(kFull, c1);
+    if ((b0 | b1) == 0u) return;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int n0 = __popc(b0);
+    uint4* s4 = (uint4*)stage;
+    if (c0) s4[*staged + __popc(b0 & lt)] = make_uint4(parent, seg, (uint32_t)t0, (uint32_t)(t0 >> 32));
+    if (c1) s4[*staged + n0 + __popc(b1 & lt)] = make_uint4(parent, seg, (uint32_t)t1, (uint32_t)(t1 >> 32));
+    *staged += n0 + __popc(b1);
     __syncwarp();
-    *qn = rest;
-    const uint32_t bal = __ballot_sync(kFull, ok);
-    const int nrec = __popc(bal);
-    if (*staged + nrec > kStage) {
-        warp_flush(stage, *staged, P, lane);
+    if (*staged > kCandFlush) {
+        cand_flush(stage, *staged, P, lane);
         *staged = 0;
     }
-    if (ok) stage[*staged + __popc(bal & ((1u << lane) - 1u))] = rec;
-    *staged += nrec;
-    __syncwarp();
 }
 
-__device__ __forceinline__ void enqueue2(SpawnEvent* q, int* qn, bool s0, bool s1, const SpawnEvent& e0,
-                                         const SpawnEvent& e1, int lane)
+// One parent record, read once (streamed past L1).
+__device__ __forceinline__ Rec load_parent(const Rec* p)
 {
-    const uint32_t b0 = __ballot_sync(kFull, s0), b1 = __ballot_sync(kFull, s1);
+    const uint4 v = __ldcs((const uint4*)p);
+    Rec r;
+    r.key = ((uint64_t)v.y << 32) | v.x;
+    r.re = (int32_t)v.z;
+    r.im = (int32_t)v.w;
+    return r;
+}
+
+// Emit the heavy work items of one parent (one per kHeavyChunk walkers of
+// each component).
+__device__ void emit_heavy(const StepParams& P, int64_t parent, int phase, int seg, uint32_t are, uint32_t aim)
+{
+    for (int comp = 0; comp < 2; ++comp) {
+        const int64_t m = comp ? aim : are;
+        const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
+        if (chunks == 0) continue;
+        const unsigned long long hb = atomicAdd((unsigned long long*)&P.st->heavy_total, (unsigned long long)chunks);
+        for (int64_t c = 0; c < chunks; ++c) {
+            const int64_t pos = (int64_t)hb + c;
+            if (pos < P.heavy_cap) {
+                HeavyItem h;
+                h.parent = parent;
+                h.phase = phase;
+                h.comp = comp;
+                h.chunk = (int32_t)c;
+                h.seg = seg;
+                P.heavy[pos] = h;
+            } else {
+                set_error(P.st, DERR_HEAVY_CAPACITY);
+            }
+        }
+    }
+}
+
+// Flags of a candidate: comp, phase, noninit, sign of the parent component.
+__device__ __forceinline__ uint64_t cand_flags(int comp, int phase, int noninit, int32_t val)
+{
+    return ((uint64_t)comp << 52) | ((uint64_t)phase << 53) | ((uint64_t)noninit << 54) |
+           ((uint64_t)(val > 0 ? 1 : 0) << 55);
+}
+
+// Slow path of one group of 32 parents (whole warp): parents with more than
+// one walker pair, and heavy parents (emitted as heavy work items).  All pairs
+// of the group are spread evenly over the lanes.
+__device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCand* stage, int* staged, bool valid,
+                                                Rec par, uint32_t j, int phase, int seg, uint2 kd, uint64_t bnd,
+                                                int lane)
+{
+    const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
+    const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
+    const uint64_t mtot = (uint64_t)are + aim;
+    const bool heavy = mtot > (uint64_t)kHeavyWalkers;
+    const int noninit = (P.init_min > 0 && (int64_t)mtot < P.init_min) ? 1 : 0;
+    if (heavy) emit_heavy(P, j, phase, seg, are, aim);
+    const uint32_t pre = heavy ? 0u : (are + 1u) >> 1, pim = heavy ? 0u : (aim + 1u) >> 1;
+    const int my_pairs = (int)(pre + pim);
+    int incl = my_pairs;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int tot_pairs = __shfl_sync(kFull, incl, 31);
+    for (int r = 0; r < tot_pairs; r += 32) {
+        const int g = r + lane;
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int im = __shfl_sync(kFull, incl, mid);
+            if (im > g) hi = mid; else lo = mid + 1;
+        }
+        const int owner = lo;
+        const bool act = g < tot_pairs;
+        const int o_incl = __shfl_sync(kFull, incl, owner);
+        const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
+        const int local = g - (o_incl - o_pairs);
+        const uint64_t okey = __shfl_sync(kFull, par.key, owner);
+        const int o_pre = __shfl_sync(kFull, (int)pre, owner);
+        const uint32_t o_are = __shfl_sync(kFull, are, owner);
+        const uint32_t o_aim = __shfl_sync(kFull, aim, owner);
+        const int o_seg = __shfl_sync(kFull, seg, owner);
+        const int o_non = __shfl_sync(kFull, noninit, owner);
+        const int32_t o_re = __shfl_sync(kFull, par.re, owner);
+        const int32_t o_im = __shfl_sync(kFull, par.im, owner);
+        const uint32_t o_j = __shfl_sync(kFull, j, owner);
+        const uint2 o_kd = make_uint2(__shfl_sync(kFull, kd.x, owner), __shfl_sync(kFull, kd.y, owner));
+        bool c0 = false, c1 = false;
+        uint64_t t0 = 0, t1 = 0;
+        if (act) {
+            const int comp = local < o_pre ? 0 : 1;
+            const int j2 = comp ? local - o_pre : local;
+            const uint32_t m = comp ? o_aim : o_are;
+            const uint4 w = philox10(
+                make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
+                           (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
+                o_kd);
+            const uint64_t R0 = (((uint64_t)w.y << 32) | w.x) >> 12;
+            const uint64_t R1 = (((uint64_t)w.w << 32) | w.z) >> 12;
+            const uint64_t fl = cand_flags(comp, phase, o_non, comp ? o_im : o_re);
+            c0 = R0 < bnd;
+            c1 = 2u * (uint32_t)j2 + 1u < m && R1 < bnd;
+            t0 = R0 | fl;
+            t1 = R1 | fl;
+        }
+        cand_push(stage, staged, c0, c1, o_j, (uint32_t)o_seg, t0, t1, P, lane);
+    }
+}
+
+// Second walker pairs of parents with two pairs, queued per warp and drawn 32
+// at a time: (parent index, vector) in a ring of kPairRing entries.
+constexpr int kPairRing = 64;
+
+__device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand* stage, int* staged,
+                                                  const uint2* ring, int head, int cnt, const Rec* src, int phase,
+                                                  bool all_cand, uint64_t b12, int lane)
+{
+    bool c0 = false, c1 = false;
+    uint64_t t0 = 0, t1 = 0;
+    uint2 it = make_uint2(0u, 0u);
+    if (lane < cnt) {
+        it = ring[(head + lane) & (kPairRing - 1)];
+        const Rec par = load_parent(src + it.x);
+        const uint32_t are = par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re;
+        const uint32_t aim = par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im;
+        // pairs are numbered real component first: the second pair is pair 1
+        // of the real component (3 or 4 real walkers) or pair 0 of the
+        // imaginary one
+        const uint32_t comp = are >= 3u ? 0u : 1u;
+        const uint32_t j2 = are >= 3u ? 1u : (aim >= 3u && are == 0u ? 1u : 0u);
+        const uint32_t m = comp ? aim : are;
+        const uint4 w = philox10(make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
+                                            (uint32_t)phase | (comp << 1) | (kKindSpawn << 2), j2),
+                                 P.kd[it.y]);
+        const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
+        const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
+        c0 = all_cand || X0 < b12;
+        c1 = 2u * j2 + 1u < m && (all_cand || X1 < b12);
+        const int noninit = (P.init_min > 0 && (int64_t)((uint64_t)are + aim) < P.init_min) ? 1 : 0;
+        const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
+        t0 = (X0 >> 12) | fl;
+        t1 = (X1 >> 12) | fl;
+    }
+    cand_push(stage, staged, c0, c1, it.x, it.y, t0, t1, P, lane);
+}
+
+// Walker draws of one population slot (phase 0: N(t), phase 1: N(t - dt)).
+// The warp owns parents [wb, we) of the slot and reads them 32 at a time,
+// one group ahead.  In the common group every parent has at most two walker
+// pairs: each lane draws its parent's first pair (one Philox call, its raw
+// 64-bit output X compared with bound << 12: T = X >> 12 < bound iff
+// X < bound << 12), and second pairs are queued and drawn 32 at a time.
+// Groups with more pairs per parent, or heavy parents, take the general path.
+__device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint2* ring,
+                                          const Rec* src, const int64_t* off, int64_t wb, int64_t we, int phase,
+                                          uint64_t bound, int lane)
+{
+    // bound = 2^52 (every walker a candidate): X < 2^64 always holds
+    const bool all_cand = bound >= (1ull << 52);
+    const uint64_t b12 = all_cand ? ~0ull : bound << 12;
+    const bool init_rule = P.init_min > 0;
     const uint32_t lt = (1u << lane) - 1u;
-    if (s0) q[*qn + __popc(b0 & lt)] = e0;
-    if (s1) q[*qn + __popc(b0) + __popc(b1 & lt)] = e1;
-    *qn += __popc(b0) + __popc(b1);
-    __syncwarp();
+    int seg = 0;
+    int64_t seg_end = -1;
+    uint2 kd = make_uint2(0u, 0u);
+    int head = 0, cnt = 0;   // ring of queued second pairs
+    Rec nxt{0ull, 0, 0};
+    if (wb + lane < we) nxt = load_parent(src + wb + lane);
+    for (int64_t g0 = wb; g0 < we; g0 += 32) {
+        const int64_t i = g0 + lane;
+        const bool valid = i < we;
+        const Rec par = nxt;
+        if (i + 32 < we) nxt = load_parent(src + i + 32);
+        if (valid && i >= seg_end) {
+            seg = seg_of(off, P.nseg, i);
+            seg_end = __ldg(&off[seg + 1]);
+            kd = P.kd[seg];
+        }
+        const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
+        const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
+        const uint32_t pre = (are + 1u) >> 1, pim = (aim + 1u) >> 1;
+        if (!__all_sync(kFull, are <= 4u && aim <= 4u && pre + pim <= 2u)) {
+            draw_group_general(P, stage, staged, valid, par, (uint32_t)i, phase, seg, kd, bound, lane);
+            continue;
+        }
+        // queue the second pairs
+        const bool two = pre + pim == 2u;
+        const uint32_t bt = __ballot_sync(kFull, two);
+        if (bt) {
+            if (two) ring[(head + cnt + __popc(bt & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)i, (uint32_t)seg);
+            cnt += __popc(bt);
+            __syncwarp();
+            if (cnt >= 32) {
+                draw_second_pairs(P, stage, staged, ring, head, 32, src, phase, all_cand, b12, lane);
+                head = (head + 32) & (kPairRing - 1);
+                cnt -= 32;
+                __syncwarp();
+            }
+        }
+        // first pair: pair 0 of the real component if it has walkers, else of the imaginary one
+        const uint32_t comp = are == 0u ? 1u : 0u;
+        const uint32_t m = comp ? aim : are;
+        const uint4 w = philox10(make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
+                                            (uint32_t)phase | (comp << 1) | (kKindSpawn << 2), 0u),
+                                 kd);
+        const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
+        const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
+        const bool c0 = m != 0u && (all_cand || X0 < b12);
+        const bool c1 = m >= 2u && (all_cand || X1 < b12);
+        const uint32_t b0 = __ballot_sync(kFull, c0), b1 = __ballot_sync(kFull, c1);
+        if ((b0 | b1) == 0u) continue;
+        const int noninit = (init_rule && (int64_t)((uint64_t)are + aim) < P.init_min) ? 1 : 0;
+        const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
+        cand_push(stage, staged, c0, c1, (uint32_t)i, (uint32_t)seg, (X0 >> 12) | fl, (X1 >> 12) | fl, P, lane);
+    }
+    if (cnt > 0) draw_second_pairs(P, stage, staged, ring, head, cnt, src, phase, all_cand, b12, lane);
 }
 
-constexpr int kWarpTile = 256;   // parents per warp-owned staged tile (4 KB)
-constexpr int kSpawnSmemAll = kSpawnSmem + (kThreads / 32) * 2 * kWarpTile * 16;
-
-__global__ void __launch_bounds__(kThreads, 2) k_spawn_light(StepParams P)
+__global__ void __launch_bounds__(kThreads, 4) k_spawn_draw(StepParams P)
 {
-    extern __shared__ __align__(128) uint8_t spawn_smem[];
-    __shared__ __align__(8) uint64_t sbar[kThreads / 32][2];
+    __shared__ __align__(16) SpawnCand sstage[kThreads / 32][kCandStage];
+    __shared__ __align__(16) uint2 sring[kThreads / 32][kPairRing];
     DevState* st = P.st;
     if (read_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Rec* wtile = (Rec*)spawn_smem + warp * 2 * kWarpTile;   // this warp's 2 stages
-    uint8_t* sprog0 = spawn_smem + (kThreads / 32) * 2 * kWarpTile * 16;
-    uint8_t* sprog1 = sprog0 + kProgSmem;
-    SpawnEvent* evq = (SpawnEvent*)(sprog1 + kProgSmem) + warp * kEvQ;
-    SRec* stage = (SRec*)(sprog1 + kProgSmem + (kThreads / 32) * kEvQ * sizeof(SpawnEvent)) + warp * kStage;
-    uint64_t* bar = sbar[warp];
-
-    const int ci = st->call_index;
-    const StepInfo inf = P.info[ci];
+    SpawnCand* stage = sstage[warp];
+    const StepInfo inf = P.info[st->call_index];
     const int cur = st->cur, prv = (cur + 2) % 3;
-    const int64_t K0 = st->count[cur];
-    const int64_t K1 = inf.ab2 ? st->count[prv] : 0;
-    const int64_t total = K0 + K1;
-    const Rec* src0 = P.pop[cur];
-    const Rec* src1 = P.pop[prv];
-    const uint8_t* pb0 = stage_prog(P.progs + inf.prog_off[0], sprog0);
-    const uint8_t* pb1 = stage_prog(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]), sprog1);
-    // each warp owns one contiguous range of parents, staged kWarpTile at a time
-    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
-    const int64_t chunk = ((total + nwarps - 1) / nwarps + 31) / 32 * 32;
-    const int64_t w_begin = min(total, gw * chunk);
-    const int64_t w_end = min(total, w_begin + chunk);
-    auto issue = [&](int64_t g0, int s) {
-        const int64_t g1 = min(w_end, g0 + kWarpTile);
-        const int64_t a1 = min(g1, K0);
-        const uint32_t na = g0 < a1 ? (uint32_t)(a1 - g0) : 0u;
-        const uint32_t nb = (uint32_t)(g1 - g0) - na;
-        mbar_arrive_expect(&bar[s], (na + nb) * 16u);
-        if (na) bulk_load(wtile + s * kWarpTile, src0 + g0, na * 16u, &bar[s]);
-        if (nb) bulk_load(wtile + s * kWarpTile + na, src1 + (g0 + na - K0), nb * 16u, &bar[s]);
-    };
-    if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-        if (w_begin < w_end) issue(w_begin, 0);
-    }
-    __syncthreads();   // programs staged, barriers initialised
-    const Prog prog0 = prog_at(pb0);
-    const Prog prog1 = prog_at(pb1);
     // filter: a walker can only spawn if T < P <= p_bound (every walker is a
     // candidate when the bound reaches 2^52, so p >= 1 is still detected)
     const int64_t lim52 = 1ll << 52;
-    const int64_t bound0 = prog0.h->p_bound >= lim52 ? lim52 : prog0.h->p_bound;
-    const int64_t bound1 = prog1.h->p_bound >= lim52 ? lim52 : prog1.h->p_bound;
-    const int64_t* off0 = P.segoff[cur];
-    const int64_t* off1 = P.segoff[prv];
+    const int64_t pb0 = ((const ProgHeader*)(P.progs + inf.prog_off[0]))->p_bound;
+    const int64_t pb1 = ((const ProgHeader*)(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0])))->p_bound;
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    int staged = 0;
+    for (int phase = 0; phase < (inf.ab2 ? 2 : 1); ++phase) {
+        const int slot = phase ? prv : cur;
+        const int64_t K = st->count[slot];
+        // each warp owns one contiguous range of the slot, a multiple of 32
+        const int64_t chunk = ((K + nwarps - 1) / nwarps + 31) / 32 * 32;
+        const int64_t wb = min(K, gw * chunk), we = min(K, wb + chunk);
+        const int64_t pb = phase ? pb1 : pb0;
+        draw_slot(P, stage, &staged, sring[warp], P.pop[slot], P.segoff[slot], wb, we, phase,
+                  (uint64_t)(pb >= lim52 ? lim52 : pb), lane);
+    }
+    if (staged) cand_flush(stage, staged, P, lane);
+}
+
+// One thread per candidate: exact weight P of the parent's column, the spawn
+// test T < P, and the destination.  Programs are staged in shared memory.
+__global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
+{
+    __shared__ __align__(16) uint8_t sprog[2][kProgSmem];
+    __shared__ __align__(16) SRec sstage[kThreads / 32][kStage];
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const StepInfo inf = P.info[st->call_index];
+    const int cur = st->cur, prv = (cur + 2) % 3;
+    const Rec* src0 = P.pop[cur];
+    const Rec* src1 = P.pop[prv];
+    const uint8_t* pb0 = stage_prog(P.progs + inf.prog_off[0], sprog[0]);
+    const uint8_t* pb1 = stage_prog(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]), sprog[1]);
+    __syncthreads();   // programs staged
+    const int64_t total = min(st->cand_total, P.cand_cap);
     const int n = P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-    int staged = 0, qn = 0;
-    int cur_phase = -1, seg = 0;
-    int64_t seg_end = 0;
-    uint32_t parity[2] = {0u, 0u};
-    bool timed_out[2] = {false, false};
-    int s = 0;
-
-    for (int64_t g0 = w_begin; g0 < w_end; g0 += kWarpTile) {
-        if (lane == 0 && g0 + kWarpTile < w_end) {
-            fence_proxy_async();
-            issue(g0 + kWarpTile, s ^ 1);
-        }
-        const bool ok = mbar_wait(&bar[s], parity[s], st);
-        if (!ok) timed_out[s] = true;
-        parity[s] ^= 1u;
-        const Rec* tp = wtile + s * kWarpTile;
-        const int tn_items = (int)min((int64_t)kWarpTile, w_end - g0);
-        for (int it = 0; it < tn_items && ok; it += 32) {
-            const int li = it + lane;
-            const int64_t i = g0 + li;
-            const bool valid = li < tn_items;
-            const int phase = (valid && i >= K0) ? 1 : 0;
-            const int64_t j = phase ? i - K0 : i;
-            if (valid && (phase != cur_phase || j >= seg_end)) {
-                const int64_t* off = phase ? off1 : off0;
-                seg = seg_of(off, P.nseg, j);
-                seg_end = off[seg + 1];
-                cur_phase = phase;
-            }
-            Rec par{0ull, 0, 0};
-            int64_t m_re = 0, m_im = 0;
-            int my_pairs = 0, pairs_re = 0, noninit = 0;
-            if (valid) {
-                par = tp[li];
-                m_re = iabs64(par.re);
-                m_im = iabs64(par.im);
-                noninit = (P.init_min > 0 && (m_re + m_im) < P.init_min) ? 1 : 0;
-                if (m_re + m_im > kHeavyWalkers) {
-                    for (int comp = 0; comp < 2; ++comp) {
-                        const int64_t m = comp ? m_im : m_re;
-                        const int64_t chunks = (m + kHeavyChunk - 1) / kHeavyChunk;
-                        if (chunks == 0) continue;
-                        const unsigned long long hb =
-                            atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
-                        for (int64_t c = 0; c < chunks; ++c) {
-                            const int64_t pos = (int64_t)hb + c;
-                            if (pos < P.heavy_cap) {
-                                HeavyItem h;
-                                h.parent = j;
-                                h.phase = phase;
-                                h.comp = comp;
-                                h.chunk = (int32_t)c;
-                                h.seg = seg;
-                                P.heavy[pos] = h;
-                            } else {
-                                set_error(st, DERR_HEAVY_CAPACITY);
-                            }
-                        }
-                    }
-                } else {
-                    pairs_re = (int)((m_re + 1) / 2);
-                    my_pairs = pairs_re + (int)((m_im + 1) / 2);
-                }
-            }
-            const int max_pairs = __reduce_max_sync(kFull, my_pairs);
-            if (max_pairs == 0) continue;
-            if (max_pairs == 1) {
-                int64_t T0 = -1, T1 = -1;
-                uint32_t info = 0;
-                if (my_pairs == 1) {
-                    const int comp = pairs_re ? 0 : 1;
-                    const int64_t m = comp ? m_im : m_re;
-                    const int64_t bnd = phase ? bound1 : bound0;
-                    const uint4 w = philox10(
-                        make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                                   (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), 0u),
-                        P.kd[seg]);
-                    const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
-                    const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
-                    if (R0 < bnd) T0 = R0;
-                    if (m > 1 && R1 < bnd) T1 = R1;
-                    const int val = comp ? par.im : par.re;
-                    info = (uint32_t)comp | ((uint32_t)phase << 1) | ((uint32_t)noninit << 2) |
-                           ((val > 0 ? 1u : 0u) << 3);
-                }
-                enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{par.key, T0, (uint32_t)seg, info},
-                         SpawnEvent{par.key, T1, (uint32_t)seg, info}, lane);
-                while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
-                continue;
-            }
-            // several pairs per lane: spread all pairs of the warp evenly over the lanes
-            int incl = my_pairs;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int tot_pairs = __shfl_sync(kFull, incl, 31);
-            for (int r = 0; r < tot_pairs; r += 32) {
-                const int g = r + lane;
-                int lo = 0, hi = 31;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    const int im = __shfl_sync(kFull, incl, mid);
-                    if (im > g) hi = mid; else lo = mid + 1;
-                }
-                const int owner = lo;
-                const bool act = g < tot_pairs;
-                const int o_incl = __shfl_sync(kFull, incl, owner);
-                const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
-                const int local = g - (o_incl - o_pairs);
-                const uint64_t okey = __shfl_sync(kFull, par.key, owner);
-                const int o_pre = __shfl_sync(kFull, pairs_re, owner);
-                const int64_t o_mre = __shfl_sync(kFull, m_re, owner);
-                const int64_t o_mim = __shfl_sync(kFull, m_im, owner);
-                const int o_phase = __shfl_sync(kFull, phase, owner);
-                const int o_seg = __shfl_sync(kFull, seg, owner);
-                const int o_non = __shfl_sync(kFull, noninit, owner);
-                const int32_t o_re = __shfl_sync(kFull, par.re, owner);
-                const int32_t o_im = __shfl_sync(kFull, par.im, owner);
-                int64_t T0 = -1, T1 = -1;
-                uint32_t info = 0;
-                if (act) {
-                    const int comp = local < o_pre ? 0 : 1;
-                    const int j2 = comp ? local - o_pre : local;
-                    const int64_t m = comp ? o_mim : o_mre;
-                    const int64_t bnd = o_phase ? bound1 : bound0;
-                    const uint4 w = philox10(
-                        make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
-                                   (uint32_t)o_phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                        P.kd[o_seg]);
-                    const int64_t R0 = (int64_t)((((uint64_t)w.y << 32) | w.x) >> 12);
-                    const int64_t R1 = (int64_t)((((uint64_t)w.w << 32) | w.z) >> 12);
-                    if (R0 < bnd) T0 = R0;
-                    if (2 * (int64_t)j2 + 1 < m && R1 < bnd) T1 = R1;
-                    const int val = comp ? o_im : o_re;
-                    info = (uint32_t)comp | ((uint32_t)o_phase << 1) | ((uint32_t)o_non << 2) |
-                           ((val > 0 ? 1u : 0u) << 3);
-                }
-                enqueue2(evq, &qn, T0 >= 0, T1 >= 0, SpawnEvent{okey, T0, (uint32_t)o_seg, info},
-                         SpawnEvent{okey, T1, (uint32_t)o_seg, info}, lane);
-                while (qn >= 32) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
+    SRec* stage = sstage[warp];
+    int staged = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kThreads + warp * 32; base < total; base += stride) {
+        const int64_t i = base + lane;
+        SRec rec;
+        bool ok = false;
+        if (i < total) {
+            const uint4 cv = __ldcs((const uint4*)P.cand + i);
+            const uint64_t tf = ((uint64_t)cv.w << 32) | cv.z;
+            const int comp = (int)((tf >> 52) & 1u), phase = (int)((tf >> 53) & 1u);
+            const int non = (int)((tf >> 54) & 1u), sg = ((tf >> 55) & 1u) ? 1 : -1;
+            const int64_t T = (int64_t)(tf & kT52);
+            const uint64_t key = __ldg(&(phase ? src1 : src0)[cv.x].key);
+            const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & ymask);
+            const Prog prog = prog_at(phase ? pb1 : pb0);
+            int64_t sre, sim;
+            const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+            if (Pw >= (1ll << 52)) {
+                set_error(st, DERR_DT_TOO_LARGE);
+            } else if (T < Pw) {
+                uint64_t mk;
+                int chan;
+                int64_t v;
+                ok = lane_choose(prog, x, y, sre, sim, T, &mk, &chan, &v);
+                if (ok) rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
+                else set_error(st, DERR_TILE_CAPACITY);
             }
         }
-        __syncwarp();   // the warp's stage is read before it is refilled
-        s ^= 1;
+        const uint32_t bal = __ballot_sync(kFull, ok);
+        const int nrec = __popc(bal);
+        if (staged + nrec > kStage) {
+            warp_flush(stage, staged, P, lane);
+            staged = 0;
+        }
+        if (ok) stage[staged + __popc(bal & ((1u << lane) - 1u))] = rec;
+        staged += nrec;
+        __syncwarp();
     }
-    while (qn > 0) drain_events(evq, &qn, stage, &staged, prog0, prog1, P, n, ymask, lane);
     if (staged) warp_flush(stage, staged, P, lane);
-    if (lane == 0) {
-        for (int q = 0; q < 2; ++q)
-            if (timed_out[q]) mbar_wait(&bar[q], parity[q] ^ 1u, st);
-    }
-    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -1346,8 +1418,10 @@ __global__ void k_finalize(StepParams P)
         st->acc_spawn += st->spawn_total;
         st->acc_knext += carry;
         st->acc_heavy += st->heavy_total;
+        st->acc_cand += st->cand_total;
         off[P.nseg] = carry;
         if (st->spawn_total > st->max_spawn) st->max_spawn = st->spawn_total;
+        if (st->cand_total > st->max_cand) st->max_cand = st->cand_total;
         if (st->heavy_total > st->max_heavy) st->max_heavy = st->heavy_total;
         st->count[nxt] = carry;
         st->cur = nxt;
@@ -1538,12 +1612,12 @@ void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int6
 }
 
 const char* const kKernelNames[kNumTimedKernels] = {
-    "k_prologue", "k_spawn_light", "k_spawn_heavy", "k_sort_hist", "k_sort_scatter",
+    "k_prologue", "k_spawn_draw", "k_spawn_choose", "k_spawn_heavy", "k_sort_hist", "k_sort_scatter",
     "k_spawn_segoff", "k_merge_plan", "k_merge_part", "k_merge", "k_finalize"};
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0;
+int g_grid_spawn = 0, g_grid_choose = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0;
 
 int resident(const void* fn, int smem, int sms)
 {
@@ -1556,11 +1630,11 @@ int resident(const void* fn, int smem, int sms)
 void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
-    cudaFuncSetAttribute(k_spawn_light, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpawnSmemAll);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_grid_spawn = resident((const void*)k_spawn_light, kSpawnSmemAll, sms);
+    g_grid_spawn = resident((const void*)k_spawn_draw, 0, sms);
+    g_grid_choose = resident((const void*)k_spawn_choose, 0, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms);
@@ -1576,13 +1650,15 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(0);
     k_prologue<<<1, kThreads, 0, stream>>>(P);
     mark(1);
-    k_spawn_light<<<g_grid_spawn, kThreads, kSpawnSmemAll, stream>>>(P);
+    k_spawn_draw<<<g_grid_spawn, kThreads, 0, stream>>>(P);
     mark(2);
-    k_spawn_heavy<<<g_grid_heavy, kThreads, 0, stream>>>(P);
+    k_spawn_choose<<<g_grid_choose, kThreads, 0, stream>>>(P);
     mark(3);
+    k_spawn_heavy<<<g_grid_heavy, kThreads, 0, stream>>>(P);
+    mark(4);
     const int np = P.key_passes + P.seg_passes;
     k_sort_hist<<<g_grid_misc, kThreads, 0, stream>>>(P);
-    mark(4);
+    mark(5);
     SRec* a = P.spawn;
     SRec* b = P.spawn_alt;
     for (int p = 0; p < np; ++p) {
@@ -1591,18 +1667,18 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
         a = b;
         b = t;
     }
-    mark(5);
+    mark(6);
     const SRec* sorted = a;
     k_spawn_segoff<<<(P.nseg + 1 + kThreads - 1) / kThreads, kThreads, 0, stream>>>(P, sorted);
-    mark(6);
-    k_merge_plan<<<1, 1024, 0, stream>>>(P);
     mark(7);
-    k_merge_part<<<g_grid_misc, kThreads, 0, stream>>>(P, sorted);
+    k_merge_plan<<<1, 1024, 0, stream>>>(P);
     mark(8);
-    k_merge<<<g_grid_merge, kThreads, kMergeSmem, stream>>>(P, sorted);
+    k_merge_part<<<g_grid_misc, kThreads, 0, stream>>>(P, sorted);
     mark(9);
-    k_finalize<<<1, 1024, 0, stream>>>(P);
+    k_merge<<<g_grid_merge, kThreads, kMergeSmem, stream>>>(P, sorted);
     mark(10);
+    k_finalize<<<1, 1024, 0, stream>>>(P);
+    mark(11);
 }
 
 void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,

@@ -31,6 +31,14 @@ struct HeavyItem {
     int32_t seg;
 };
 
+// A walker whose draw T lies below its program's bound on P: a spawn
+// candidate, resolved against the exact column by k_spawn_choose.  16 bytes.
+struct __align__(16) SpawnCand {
+    uint32_t parent;  // index of the parent inside its population slot
+    uint32_t seg;     // population vector
+    uint64_t tf;      // T (52 bits) | comp << 52 | phase << 53 | noninit << 54 | (parent component > 0) << 55
+};
+
 struct SegStats {
     unsigned long long count;
     long long ntot, dre, dim;
@@ -47,6 +55,8 @@ struct StepParams {
     SRec* spawn;          // spawn records (sort ping-pong A)
     SRec* spawn_alt;      // sort ping-pong B
     int64_t spawn_cap;
+    SpawnCand* cand;      // spawn candidates of the step
+    int64_t cand_cap;
     HeavyItem* heavy;
     int64_t heavy_cap;
     uint2* kd;            // per-segment Philox key of the current step
@@ -73,7 +83,7 @@ struct StepParams {
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
 // launch sequence can be captured once in a CUDA graph and replayed.
-constexpr int kNumTimedKernels = 10;
+constexpr int kNumTimedKernels = 11;
 void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);

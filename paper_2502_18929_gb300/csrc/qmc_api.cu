@@ -76,6 +76,8 @@ StepParams params(qmc_ctx* c)
     P.spawn = c->d_spawn;
     P.spawn_alt = c->d_spawn_alt;
     P.spawn_cap = c->spawn_cap;
+    P.cand = c->d_cand;
+    P.cand_cap = c->cand_cap;
     P.heavy = c->d_heavy;
     P.heavy_cap = c->heavy_cap;
     P.kd = c->d_kd;
@@ -128,6 +130,16 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
     ctx->sort_tiles_cap = (cap + kSortTile - 1) / kSortTile + 1;
     if ((rc = dalloc(ctx, &ctx->d_sort_status, ctx->sort_tiles_cap * 256)) != QMC_OK) return rc;
     CK(cudaMemsetAsync(ctx->d_sort_status, 0, (size_t)ctx->sort_tiles_cap * 256 * 8, ctx->work));
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
+int grow_cand(qmc_ctx* ctx, int64_t need)
+{
+    const int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->d_cand, cap)) != QMC_OK) return rc;
+    ctx->cand_cap = cap;
     ctx->graph_dirty = true;
     return QMC_OK;
 }
@@ -276,6 +288,7 @@ int qmc_create(qmc_ctx** out, const qmc_config* cfg)
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
     const int64_t hint = cfg->capacity_hint > 0 ? cfg->capacity_hint : (int64_t)1 << 16;
     if ((rc = grow_spawn(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
+    if ((rc = grow_cand(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
     if ((rc = grow_pop(ctx, hint)) != QMC_OK) return bail(rc);
     if (cudaStreamSynchronize(ctx->work) != cudaSuccess) return bail(QMC_ERR_CUDA);
     *out = ctx;
@@ -288,7 +301,7 @@ void qmc_destroy(qmc_ctx* ctx)
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
-                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_heavy,
+                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_part, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
                     ctx->d_progs, ctx->d_obs};
@@ -553,6 +566,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         if (code == DERR_SPAWN_CAPACITY) {
             if ((rc = grow_spawn(ctx, hs.spawn_total)) != QMC_OK) return rc;
             if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
+        } else if (code == DERR_CAND_CAPACITY) {
+            if ((rc = grow_cand(ctx, hs.cand_total)) != QMC_OK) return rc;
         } else if (code == DERR_HEAVY_CAPACITY) {
             const int64_t cap = std::max<int64_t>(hs.heavy_total * 2, ctx->heavy_cap * 2);
             if ((rc = dalloc(ctx, &ctx->d_heavy, cap)) != QMC_OK) return rc;
@@ -596,6 +611,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         if ((rc = grow_spawn(ctx, hs.max_spawn * 2)) != QMC_OK) return rc;
         if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
     }
+    if (hs.max_cand > ctx->cand_cap * 3 / 4)
+        if ((rc = grow_cand(ctx, hs.max_cand * 2)) != QMC_OK) return rc;
     if (hs.max_next > ctx->pop_cap * 3 / 4 && (ctx->cfg.max_records == 0 || ctx->pop_cap < ctx->cfg.max_records))
         if ((rc = grow_pop(ctx, hs.max_next * 2)) != QMC_OK) return rc;
     return leave(ctx);
@@ -937,9 +954,9 @@ extern "C" int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out)
     out[4] = hs.acc_spawn;
     out[5] = hs.acc_knext;
     out[6] = hs.acc_heavy;
-    out[7] = 0;
+    out[7] = hs.acc_cand;
     if (reset) {
-        int64_t z[7] = {0, 0, 0, 0, 0, 0, 0};
+        int64_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, acc_steps), z, sizeof(z),
                            cudaMemcpyHostToDevice, ctx->work));
         CK(cudaStreamSynchronize(ctx->work));

@@ -113,6 +113,7 @@ enum DevError : uint32_t {
     DERR_TIMEOUT = 5,
     DERR_HEAVY_CAPACITY = 6,
     DERR_TILE_CAPACITY = 7,
+    DERR_CAND_CAPACITY = 8,
 };
 
 constexpr int kMaxTileCounters = 32;
@@ -128,6 +129,8 @@ struct DevState {
     int64_t heavy_total;  // heavy work items requested this step
     int64_t next_total;   // records produced by the merge this step
     int64_t merge_tiles;  // merge tiles this step
+    int64_t cand_total;   // spawn candidates (draws below the bound) this step
+    int64_t max_cand;
     int64_t max_spawn;    // high-water marks
     int64_t max_next;
     int64_t max_heavy;
@@ -140,6 +143,7 @@ struct DevState {
     int64_t acc_spawn;    // spawn records written
     int64_t acc_knext;    // records written to N(t + dt)
     int64_t acc_heavy;    // heavy work items
+    int64_t acc_cand;     // spawn candidates
     uint32_t seq;         // look-back epoch base, advanced by 16 every step
     uint32_t pad2;
     uint32_t tile_ctr[kMaxTileCounters];

@@ -254,7 +254,7 @@ class QMC:
         """Cumulative device totals since the last reset (see qmc_counters)."""
         out = np.zeros(8, dtype=np.int64)
         self._check(self.L.qmc_counters(self.h, int(reset), out.ctypes.data), "qmc_counters")
-        names = ["steps", "walker_steps", "k_cur", "k_prev", "spawns", "k_next", "heavy_items"]
+        names = ["steps", "walker_steps", "k_cur", "k_prev", "spawns", "k_next", "heavy_items", "candidates"]
         return {k: int(v) for k, v in zip(names, out)}
 
     def spawn_prob_bound(self, t: float, dt: float) -> float:

@@ -121,6 +121,56 @@ def test_spread_n32_cnot_window():
         assert_same(gpu, orc, where=f"n32 step {k}")
 
 
+def _mixed_counts_state(n, nseg, count, seed):
+    """Distinct random states whose (re, im) cover every walker-pair layout of
+    a light parent: one walker, both components (one or two walkers each),
+    three or four walkers in one component, and a few larger parents."""
+    rng = np.random.default_rng(seed)
+    pops = []
+    for s in range(nseg):
+        k, _, _ = P.spread_population(n, count + 53 * s, seed + 100 + s)
+        u = rng.random(len(k))
+        sgn = lambda: rng.choice(np.array([-1, 1], np.int32), size=len(k))
+        mag_small = rng.integers(1, 3, size=len(k)).astype(np.int32)
+        mag_34 = rng.integers(3, 5, size=len(k)).astype(np.int32)
+        mag_big = rng.integers(5, 41, size=len(k)).astype(np.int32)
+        re = np.zeros(len(k), np.int32)
+        im = np.zeros(len(k), np.int32)
+        one = u < 0.55
+        re[one & (u < 0.3)] = sgn()[one & (u < 0.3)]
+        im[one & (u >= 0.3)] = sgn()[one & (u >= 0.3)]
+        both = (u >= 0.55) & (u < 0.75)
+        re[both] = (sgn() * mag_small)[both]
+        im[both] = (sgn() * mag_small[::-1])[both]
+        r34 = (u >= 0.75) & (u < 0.85)
+        re[r34] = (sgn() * mag_34)[r34]
+        i34 = (u >= 0.85) & (u < 0.95)
+        im[i34] = (sgn() * mag_34)[i34]
+        big = u >= 0.995
+        re[big] = (sgn() * mag_big)[big]
+        im[big & (u >= 0.998)] = (sgn() * mag_small)[big & (u >= 0.998)]
+        two = (u >= 0.95) & (u < 0.995)
+        re[two] = (sgn() * 2)[two]
+        pops.append((k, re, im))
+    return pops
+
+
+def test_all_walker_pair_layouts():
+    """Every layout of walker pairs in light parents (first pairs drawn per
+    lane, second pairs queued, groups with larger parents on the general
+    path), under AB2 with both population slots, at n = 32."""
+    prob = P.ghz_circuit(32)
+    gpu, orc = make_pair(prob, 3, 21, 10**6)
+    cur = _mixed_counts_state(32, 3, 20000, 11)
+    prev = _mixed_counts_state(32, 3, 19000, 12)
+    _load_state(gpu, orc, cur, prev, 77, 5.2, 0.01)
+    for k in range(3):
+        gpu.step(0.01, 1)
+        assert orc.step(0.01, 1) == O.OK
+        assert_same(gpu, orc, where=f"pair layouts step {k}")
+        assert_same(gpu, orc, which=1, where=f"pair layouts prev {k}")
+
+
 def test_heavy_and_light_parents():
     """A state with 1e5 walkers (four heavy chunks) next to light states."""
     prob = P.ghz_circuit(5)
