@@ -66,7 +66,9 @@ typedef struct {
     int32_t n_qubits;      /* 1..32                                              */
     int32_t n_segments;    /* number of independent vectors, >= 1                */
     int32_t integrator;    /* QMC_EULER or QMC_AB2 (AB2 starts with one Euler)   */
-    int32_t reserved0;
+    int32_t max_ctas;      /* cap on the CTAs of each persistent or grid-stride
+                              kernel of a step (0: fill the GPU); lets a small
+                              problem run many tiles per CTA                    */
     uint64_t seed;
     int64_t n_diag;        /* N^diag: walkers on the diagonal of N(0) = N^diag rho(0) */
     int64_t initiator_min; /* initiator threshold ceil(xi N^diag) in walkers; 0 = off */

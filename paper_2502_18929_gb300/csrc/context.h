@@ -49,7 +49,7 @@ struct qmc_ctx {
     int64_t sort_tiles_cap = 0;
     int64_t* d_bseg = nullptr;
     int64_t* d_tile_start = nullptr;
-    int64_t* d_part = nullptr;
+    qmc::MTileG* d_mtiles = nullptr;
     unsigned long long* d_merge_status = nullptr;
     int64_t merge_tiles_cap = 0;
     SegStats* d_segacc = nullptr;

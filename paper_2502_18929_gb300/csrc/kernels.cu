@@ -56,9 +56,28 @@ __device__ __forceinline__ void set_error(DevState* st, uint32_t code)
     atomicCAS(&st->error, 0u, code);
 }
 
+// A bounded wait that gave up: DERR_TIMEOUT, with the wait site and an index
+// (tile or stage use) in error_aux for the host's message.
+__device__ __forceinline__ void set_timeout(DevState* st, uint32_t site, int64_t idx)
+{
+    if (atomicCAS(&st->error, 0u, (uint32_t)DERR_TIMEOUT) == 0u)
+        st->error_aux = (site << 24) | (uint32_t)(idx & 0xFFFFFF);
+}
+
 __device__ __forceinline__ uint32_t read_error(const DevState* st)
 {
     return *(volatile const uint32_t*)&st->error;
+}
+
+// The error flag as one CTA sees it: read once and shared, so that every
+// thread of the CTA takes the same early exit (another CTA may raise the flag
+// while this one starts).
+__device__ __forceinline__ bool cta_error(const DevState* st)
+{
+    __shared__ uint32_t s_err;
+    if (threadIdx.x == 0) s_err = read_error(st);
+    __syncthreads();
+    return s_err != 0;
 }
 
 __device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p)
@@ -79,7 +98,7 @@ __device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, uint32_t f
 // Wait (bounded) until *addr carries this epoch and a flag; returns false on
 // timeout after raising DERR_TIMEOUT.
 __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned long long* out,
-                        DevState* st)
+                        DevState* st, uint32_t site, int64_t idx)
 {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         unsigned long long v = ld_vol(addr);
@@ -90,7 +109,7 @@ __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned
         if (read_error(st) == DERR_TIMEOUT) break;
         if (it > 32) __nanosleep(64);
     }
-    set_error(st, DERR_TIMEOUT);
+    set_timeout(st, site, idx);
     return false;
 }
 
@@ -100,7 +119,7 @@ __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned
 // prefix of tile t (to every lane).  Bounded waits; on timeout the error is
 // raised and the partial sum returned.
 __device__ unsigned long long warp_lookback(const unsigned long long* status, int64_t t, uint32_t epoch,
-                                            DevState* st, int lane)
+                                            DevState* st, int lane, uint32_t site)
 {
     unsigned long long excl = 0;
     int64_t hi = t - 1; // nearest unread predecessor
@@ -118,7 +137,7 @@ __device__ unsigned long long warp_lookback(const unsigned long long* status, in
             if (it > 32) __nanosleep(64);
         }
         if (!__all_sync(kFull, ready)) {
-            if (lane == 0) set_error(st, DERR_TIMEOUT);
+            if (lane == 0) set_timeout(st, site, t);
             break;
         }
         const bool incl = j >= 0 && ((v >> 30) & 3u) == kFlagIncl;
@@ -277,13 +296,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
 }
 
 // Bounded wait for a phase of an mbarrier.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st)
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st, uint32_t site, int64_t idx)
 {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (it > 16) __nanosleep(32);
     }
-    set_error(st, DERR_TIMEOUT);
+    set_timeout(st, site, idx);
     return false;
 }
 
@@ -572,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_spawn_draw(StepParams P)
     __shared__ __align__(16) SpawnCand sstage[kThreads / 32][kCandStage];
     __shared__ __align__(16) uint2 sring[kThreads / 32][kPairRing];
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     SpawnCand* stage = sstage[warp];
     const StepInfo inf = P.info[st->call_index];
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
     __shared__ __align__(16) uint8_t sprog[2][kProgSmem];
     __shared__ __align__(16) SRec sstage[kThreads / 32][kStage];
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const StepInfo inf = P.info[st->call_index];
     const int cur = st->cur, prv = (cur + 2) % 3;
@@ -675,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
     __shared__ unsigned long long s_base;
     __shared__ int s_nout;
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int64_t nitems = min(st->heavy_total, P.heavy_cap);
     if (nitems == 0) return;
     const int ci = st->call_index;
@@ -801,7 +820,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(StepParams P)
 {
     __shared__ unsigned int h[kMaxPasses * 256];
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int64_t S = min(st->spawn_total, P.spawn_cap);
     const int np = P.key_passes + P.seg_passes;
     for (int i = threadIdx.x; i < np * 256; i += kThreads) h[i] = 0u;
@@ -825,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
     __shared__ unsigned int lstart[256];
     __shared__ unsigned int s_tile;
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int64_t S = min(st->spawn_total, P.spawn_cap);
     const int64_t ntiles = (S + kSortTile - 1) / kSortTile;
     if (ntiles > P.sort_tiles_cap) {
@@ -919,7 +938,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
                         if (done || hi - w < 0) continue;
                         unsigned long long x = v[w];
                         if (!((uint32_t)(x >> 32) == epoch && ((x >> 30) & 3u) != 0u)) {
-                            if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st)) {
+                            if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st, 1u, hi - w)) {
                                 done = true;
                                 continue;
                             }
@@ -992,7 +1011,7 @@ __global__ void k_merge_plan(StepParams P)
 {
     __shared__ int64_t wsum[32];
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int cur = st->cur;
     const int64_t* aoff = P.segoff[cur];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1039,8 +1058,20 @@ __device__ __forceinline__ int tile_seg(const int64_t* tile_start, int nseg, int
     return lo;
 }
 
-// Merge-path partition: for every tile, how many of its segment's N(t)
-// records precede it (ties: N(t) before spawns).
+// Merge-path split of one segment at diagonal d: how many of the first d
+// merged items are N(t) records (ties: N(t) before spawns).
+__device__ __forceinline__ int64_t merge_split(const Rec* A, const SRec* B, int64_t na, int64_t nb, int64_t d)
+{
+    int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (A[mid].key <= B[d - mid - 1].key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Metadata of every merge tile: its slices of N(t) and of the sorted spawns
+// (merge-path splits at both ends) and the key just before it.
 __global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
 {
     DevState* st = P.st;
@@ -1054,46 +1085,54 @@ __global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
         const int64_t a0 = aoff[s], na = aoff[s + 1] - a0;
         const int64_t b0 = P.bseg[s], nb = P.bseg[s + 1] - b0;
         const int64_t d = (t - P.tile_start[s]) * kMergeTile;
-        int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (A[a0 + mid].key <= sorted[b0 + d - mid - 1].key) lo = mid + 1; else hi = mid;
+        const int64_t d1 = min(d + (int64_t)kMergeTile, na + nb);
+        const int64_t ia0 = merge_split(A + a0, sorted + b0, na, nb, d), ib0 = d - ia0;
+        const int64_t ia1 = merge_split(A + a0, sorted + b0, na, nb, d1), ib1 = d1 - ia1;
+        uint64_t pk = 0;
+        if (ia0 > 0) pk = A[a0 + ia0 - 1].key;
+        if (ib0 > 0) {
+            const uint64_t kb = sorted[b0 + ib0 - 1].key;
+            pk = pk > kb ? pk : kb;
         }
-        P.part[2 * t] = lo;
-        P.part[2 * t + 1] = d - lo;
+        MTileG g;
+        g.a_glob = a0 + ia0;
+        g.b_glob = b0 + ib0;
+        g.b_seg_end = b0 + nb;
+        g.prev_key = pk;
+        g.na = (int32_t)(ia1 - ia0);
+        g.nb = (int32_t)(ib1 - ib0);
+        g.seg = s;
+        g.has_prev = (ia0 > 0 || ib0 > 0) ? 1 : 0;
+        P.mtiles[t] = g;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Annihilation.  A run is all items (at most one N(t) record and any number of
-// spawn records) with one key.  Value = N(t) + initiator spawns +
-// (occupied ? non-initiator spawns : 0); zero runs are dropped.  Tiles of the
-// merged sequence are staged by bulk copies (double-buffered); each thread
+// Annihilation [End Matter, annihilation step].  A run is all items (at most
+// one N(t) record and any number of spawn records) with one key.  Value =
+// N(t) + initiator spawns + (occupied ? non-initiator spawns : 0); zero runs
+// are dropped.  A producer warp stages the tiles of the merged sequence in
+// shared memory by bulk copies (two stages); each of the 256 merging threads
 // merges kMergeItems items and emits the runs whose first item it holds,
 // reading past its items (and past the tile, where only spawn records can
-// follow, since N(t) sorts first on equal keys) to finish its last run.
+// follow, since N(t) sorts first on equal keys) to finish its last run.  The
+// tile's runs are compacted in shared memory; a publisher warp places them by
+// a decoupled look-back over the tiles and writes them out with one bulk
+// store, while the merging warps go on with the next tile.
 // ---------------------------------------------------------------------------
-struct MTile {
-    int64_t t;
-    int64_t a_glob, b_glob, b_seg_end;
-    uint64_t prev_key;
-    int32_t na, nb, seg, has_prev;
-};
-
 __device__ __forceinline__ uint64_t it_key(const uint4* buf, int i)
 {
     return ((const uint64_t*)&buf[i])[0];
 }
 
-// Walk the thread's items; pass 0 counts (and gathers statistics), pass 1
-// writes at out + obase.
-__device__ __forceinline__ int merge_thread(const uint4* buf, const MTile& m, const SRec* __restrict__ sorted,
-                                            int pass, Rec* out, int64_t obase, int64_t pop_cap, DevState* st,
-                                            uint32_t n, uint32_t ymask, long long* ntot, long long* dre,
-                                            long long* dim)
+// Walk the thread's items of a tile; the runs it owns go to raw[0 ..),
+// their statistics to ntot / dre / dim.  Returns the number of runs.
+__device__ __forceinline__ int merge_walk(const uint4* buf, const MTileG& m, const SRec* __restrict__ sorted,
+                                          uint4* raw, DevState* st, uint32_t n, uint32_t ymask, long long* ntot,
+                                          long long* dre, long long* dim)
 {
     const int na = m.na, nb = m.nb, nt = na + nb;
-    const int d0 = threadIdx.x * kMergeItems;
+    const int d0 = (int)threadIdx.x * kMergeItems;
     if (d0 >= nt) return 0;
     int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
     while (lo < hi) {
@@ -1125,17 +1164,12 @@ __device__ __forceinline__ int merge_thread(const uint4* buf, const MTile& m, co
             set_error(st, DERR_POP_OVERFLOW);
             return;
         }
-        if (pass == 0) {
-            *ntot += (vr < 0 ? -vr : vr) + (vi < 0 ? -vi : vi);
-            if ((uint32_t)(rkey >> n) == (uint32_t)(rkey & ymask)) {
-                *dre += vr;
-                *dim += vi;
-            }
-        } else {
-            const int64_t pos = obase + nout;
-            if (pos < pop_cap) out[pos] = Rec{rkey, (int32_t)vr, (int32_t)vi};
-            else set_error(st, DERR_POP_CAPACITY);
+        *ntot += (vr < 0 ? -vr : vr) + (vi < 0 ? -vi : vi);
+        if ((uint32_t)(rkey >> n) == (uint32_t)(rkey & ymask)) {
+            *dre += vr;
+            *dim += vi;
         }
+        raw[nout] = make_uint4((uint32_t)rkey, (uint32_t)(rkey >> 32), (uint32_t)(int32_t)vr, (uint32_t)(int32_t)vi);
         ++nout;
     };
     auto add_item = [&](int idx, bool isA) {
@@ -1201,107 +1235,177 @@ __device__ __forceinline__ int merge_thread(const uint4* buf, const MTile& m, co
     return nout;
 }
 
-__device__ __forceinline__ void merge_tile_meta(const StepParams& P, const SRec* __restrict__ sorted, int64_t t,
-                                                const Rec* A, const int64_t* aoff, MTile* m)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
-    const int s = tile_seg(P.tile_start, P.nseg, t);
-    const int64_t a_base = aoff[s], na_seg = aoff[s + 1] - a_base;
-    const int64_t b_base = P.bseg[s], nb_seg = P.bseg[s + 1] - b_base;
-    const int64_t ia0 = P.part[2 * t], ib0 = P.part[2 * t + 1];
-    int64_t ia1 = na_seg, ib1 = nb_seg;
-    if (t + 1 < P.tile_start[s + 1]) {
-        ia1 = P.part[2 * t + 2];
-        ib1 = P.part[2 * t + 3];
-    }
-    m->t = t;
-    m->seg = s;
-    m->a_glob = a_base + ia0;
-    m->b_glob = b_base + ib0;
-    m->b_seg_end = b_base + nb_seg;
-    m->na = (int32_t)(ia1 - ia0);
-    m->nb = (int32_t)(ib1 - ib0);
-    m->has_prev = (ia0 > 0 || ib0 > 0) ? 1 : 0;
-    uint64_t pk = 0;
-    if (ia0 > 0) pk = A[a_base + ia0 - 1].key;
-    if (ib0 > 0) {
-        const uint64_t kb = sorted[b_base + ib0 - 1].key;
-        pk = pk > kb ? pk : kb;
-    }
-    m->prev_key = pk;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-__device__ __forceinline__ void merge_issue(const MTile& m, const Rec* A, const SRec* sorted, uint4* buf, uint64_t* bar)
+// Barrier of the 256 merging threads only (the producer warp runs apart).
+__device__ __forceinline__ void merge_bar()
 {
-    const uint32_t abytes = (uint32_t)m.na * 16u, bbytes = (uint32_t)m.nb * 16u;
-    mbar_arrive_expect(bar, abytes + bbytes);
-    if (abytes) bulk_load(buf, A + m.a_glob, abytes, bar);
-    if (bbytes) bulk_load(buf + m.na, sorted + m.b_glob, bbytes, bar);
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
 }
 
-constexpr int kMergeSmem = 2 * kMergeTile * 16;   // 2 input stages
-
-__global__ void __launch_bounds__(kThreads, 3) k_merge(StepParams P, const SRec* __restrict__ sorted)
+// 1-D bulk copy shared -> global (bulk async-group); both addresses 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
 {
-    extern __shared__ __align__(128) uint4 mbuf[];   // 2 stages x kMergeTile items
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ MTile tiles[2];
-    __shared__ int s_wcount[kThreads / 32];
-    __shared__ long long s_red[3][kThreads / 32];
-    __shared__ unsigned long long s_base;
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Shared memory: 2 input stages (each also holds its tile's compacted output
+// until the bulk store has read it) and 2 buffers of raw runs (kMergeTile
+// 16-byte items each).
+constexpr int kMergeSmem = 4 * kMergeTile * 16;
+
+// Per-tile hand-over from the merging warps to the publisher warp.
+struct MSlot {
+    int64_t t;
+    long long ntot, dre, dim;
+    int32_t count, seg;
+};
+
+// Warp roles: 0..7 merge, 8 produces (tickets, bulk loads), 9 publishes
+// (look-back, statistics, bulk store of the compacted output).
+__global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const SRec* __restrict__ sorted)
+{
+    extern __shared__ __align__(128) uint4 msm[];
+    uint4* inbuf = msm;                       // [2][kMergeTile]
+    uint4* rawb = msm + 2 * kMergeTile;       // [2][kMergeTile]
+    __shared__ __align__(8) uint64_t full[2], empty[2], ready[2];
+    __shared__ MTileG meta[2];
+    __shared__ int64_t meta_t[2];
+    __shared__ MSlot slot[2];
+    __shared__ int s_wcount[2][kThreads / 32];
+    __shared__ long long s_red[2][3][kThreads / 32];
+    __shared__ int s_abort;
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int cur = st->cur, nxt = (cur + 1) % 3;
     const int64_t T = st->merge_tiles;
     const Rec* A = P.pop[cur];
     Rec* out = P.pop[nxt];
-    const int64_t* aoff = P.segoff[cur];
-    const uint32_t epoch = st->seq + 15u;
     const uint32_t n = (uint32_t)P.n;
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kMergeWarps = kThreads / 32;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-        const int64_t t0 = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
-        tiles[0].t = t0;
-        if (t0 < T) {
-            merge_tile_meta(P, sorted, t0, A, aoff, &tiles[0]);
-            merge_issue(tiles[0], A, sorted, mbuf, &bar[0]);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&ready[s], kMergeWarps);
         }
+        mbar_fence_init();
+        s_abort = 0;
     }
     __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
-    bool timed_out[2] = {false, false};
-    int stage = 0;
-    for (;;) {
-        const int64_t t = tiles[stage].t;
-        if (t >= T) break;
-        if (tid == 0) {
-            const int64_t tn = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
-            tiles[stage ^ 1].t = tn;
-            if (tn < T) {
-                merge_tile_meta(P, sorted, tn, A, aoff, &tiles[stage ^ 1]);
-                fence_proxy_async();
-                merge_issue(tiles[stage ^ 1], A, sorted, mbuf + (stage ^ 1) * kMergeTile, &bar[stage ^ 1]);
+
+    if (warp == kMergeWarps) {
+        // producer: take tiles in order (one ticket each), stage them
+        if (lane != 0) return;
+        int issued[2] = {0, 0};
+        int end_stage = -1;
+        for (int k = 0;; ++k) {
+            const int s = k & 1;
+            if (k >= 2 && !mbar_wait(&empty[s], (uint32_t)(((k >> 1) - 1) & 1), st, 3u, k)) break;
+            const int64_t t = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
+            meta_t[s] = t;
+            if (t >= T) {
+                mbar_arrive(&full[s]);   // end marker
+                end_stage = s;
+                break;
             }
+            const MTileG m = P.mtiles[t];
+            meta[s] = m;
+            const uint32_t abytes = (uint32_t)m.na * 16u, bbytes = (uint32_t)m.nb * 16u;
+            fence_proxy_async();
+            mbar_arrive_expect(&full[s], abytes + bbytes);
+            if (abytes) bulk_load(inbuf + s * kMergeTile, A + m.a_glob, abytes, &full[s]);
+            if (bbytes) bulk_load(inbuf + s * kMergeTile + m.na, sorted + m.b_glob, bbytes, &full[s]);
+            ++issued[s];
         }
-        const bool ok = mbar_wait(&bar[stage], parity[stage], st);
-        if (!ok) timed_out[stage] = true;
-        parity[stage] ^= 1u;
-        const uint4* buf = mbuf + stage * kMergeTile;
-        const MTile m = tiles[stage];
+        // No copy may still be writing shared memory when the CTA exits.  The
+        // end marker goes to a stage only after its last copy was consumed
+        // (and its phase parity no longer names that copy); on the other
+        // stage the last copy's phase is the current or the previous one.
+        for (int s = 0; s < 2; ++s)
+            if (issued[s] && s != end_stage) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), st, 4u, s);
+        return;
+    }
+
+    if (warp == kMergeWarps + 1) {
+        // publisher: place each tile after its predecessors, store it
+        const uint32_t epoch = st->seq + 15u;
+        for (int k = 0;; ++k) {
+            const int s = k & 1;
+            if (!mbar_wait(&ready[s], (uint32_t)((k >> 1) & 1), st, 6u, k)) break;
+            const MSlot sl = slot[s];
+            if (sl.t >= T) break;
+            unsigned long long* my = P.merge_status + sl.t;
+            unsigned long long excl = 0;
+            if (sl.t == 0) {
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)sl.count));
+            } else {
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)sl.count));
+                excl = warp_lookback(P.merge_status, sl.t, epoch, st, lane, 2u);
+                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + sl.count)));
+            }
+            if (lane == 0) {
+                if (sl.t == T - 1) {
+                    st->next_total = (int64_t)(excl + sl.count);
+                    if ((int64_t)(excl + sl.count) > st->max_next) st->max_next = (int64_t)(excl + sl.count);
+                }
+                if (sl.count) {
+                    atomicAdd(&P.segacc[sl.seg].count, (unsigned long long)sl.count);
+                    atomicAdd((unsigned long long*)&P.segacc[sl.seg].ntot, (unsigned long long)sl.ntot);
+                    atomicAdd((unsigned long long*)&P.segacc[sl.seg].dre, (unsigned long long)sl.dre);
+                    atomicAdd((unsigned long long*)&P.segacc[sl.seg].dim, (unsigned long long)sl.dim);
+                    const int64_t base = (int64_t)excl;
+                    int64_t cnt = sl.count;
+                    if (base + cnt > P.pop_cap) {
+                        set_error(st, DERR_POP_CAPACITY);
+                        cnt = base < P.pop_cap ? P.pop_cap - base : 0;
+                    }
+                    if (cnt > 0) {
+                        bulk_store(out + base, inbuf + s * kMergeTile, (uint32_t)cnt * 16u);
+                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    }
+                }
+                mbar_arrive(&empty[s]);   // stage s (input and output) may be refilled
+            }
+            __syncwarp();
+        }
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        return;
+    }
+
+    // merging threads
+    for (int k = 0;; ++k) {
+        const int s = k & 1;
+        const bool ok = mbar_wait(&full[s], (uint32_t)((k >> 1) & 1), st, 5u, k);
+        if (!ok) s_abort = 1;
+        const int64_t t = ok ? meta_t[s] : T;
         long long my_ntot = 0, my_dre = 0, my_dim = 0;
         int nout = 0;
-        if (ok) nout = merge_thread(buf, m, sorted, 0, out, 0, P.pop_cap, st, n, ymask, &my_ntot, &my_dre, &my_dim);
-        // block scan of output counts, block sums of the statistics
+        int seg = 0;
+        uint4* raw = rawb + s * kMergeTile;
+        if (t < T) {
+            const MTileG m = meta[s];
+            seg = m.seg;
+            nout = merge_walk(inbuf + s * kMergeTile, m, sorted, raw + tid * kMergeItems, st, n, ymask, &my_ntot,
+                              &my_dre, &my_dim);
+        }
+        // block scan of run counts, block sums of the statistics
         int incl = nout;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += v;
         }
-        if (lane == 31) s_wcount[warp] = incl;
+        if (lane == 31) s_wcount[s][warp] = incl;
         long long r0 = my_ntot, r1 = my_dre, r2 = my_dim;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1310,64 +1414,45 @@ __global__ void __launch_bounds__(kThreads, 3) k_merge(StepParams P, const SRec*
             r2 += __shfl_down_sync(kFull, r2, o);
         }
         if (lane == 0) {
-            s_red[0][warp] = r0;
-            s_red[1][warp] = r1;
-            s_red[2][warp] = r2;
+            s_red[s][0][warp] = r0;
+            s_red[s][1][warp] = r1;
+            s_red[s][2][warp] = r2;
         }
-        __syncthreads();
+        merge_bar();   // walks of the tile done, counts known
+        if (s_abort || t >= T) {
+            // tell the publisher to stop
+            if (tid == 0) slot[s].t = T;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[s]);
+            break;
+        }
         int woff = 0, tile_count = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            if (w < warp) woff += s_wcount[w];
-            tile_count += s_wcount[w];
+#pragma unroll
+        for (int w = 0; w < kMergeWarps; ++w) {
+            if (w < warp) woff += s_wcount[s][w];
+            tile_count += s_wcount[s][w];
         }
-        if (warp == 0) {
-            unsigned long long* my = P.merge_status + t;
-            unsigned long long excl = 0;
-            if (t == 0) {
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)tile_count));
-            } else {
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)tile_count));
-                excl = warp_lookback(P.merge_status, t, epoch, st, lane);
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tile_count)));
-            }
-            if (lane == 0) s_base = excl;
-        }
+        // compact the runs over the consumed input stage
+        uint4* ob = inbuf + s * kMergeTile;
+        const int pos = woff + incl - nout;
+        for (int r = 0; r < nout; ++r) ob[pos + r] = raw[tid * kMergeItems + r];
+        fence_proxy_async();   // generic writes of ob before the bulk store reads them
         if (tid == 0) {
-            const unsigned long long excl = s_base;
-            if (t == T - 1) {
-                st->next_total = (int64_t)(excl + tile_count);
-                if ((int64_t)(excl + tile_count) > st->max_next) st->max_next = (int64_t)(excl + tile_count);
+            MSlot sl;
+            sl.t = t;
+            sl.count = tile_count;
+            sl.seg = seg;
+            sl.ntot = sl.dre = sl.dim = 0;
+            for (int w = 0; w < kMergeWarps; ++w) {
+                sl.ntot += s_red[s][0][w];
+                sl.dre += s_red[s][1][w];
+                sl.dim += s_red[s][2][w];
             }
-            if (tile_count) {
-                long long a = 0, b = 0, c = 0;
-                for (int w = 0; w < kThreads / 32; ++w) {
-                    a += s_red[0][w];
-                    b += s_red[1][w];
-                    c += s_red[2][w];
-                }
-                atomicAdd(&P.segacc[m.seg].count, (unsigned long long)tile_count);
-                atomicAdd((unsigned long long*)&P.segacc[m.seg].ntot, (unsigned long long)a);
-                atomicAdd((unsigned long long*)&P.segacc[m.seg].dre, (unsigned long long)b);
-                atomicAdd((unsigned long long*)&P.segacc[m.seg].dim, (unsigned long long)c);
-            }
+            slot[s] = sl;
         }
-        __syncthreads();
-        if (ok && nout) {
-            long long d1 = 0, d2 = 0, d3 = 0;
-            merge_thread(buf, m, sorted, 1, out, (int64_t)s_base + woff + incl - nout, P.pop_cap, st, n, ymask,
-                         &d1, &d2, &d3);
-        }
-        __syncthreads();
-        stage ^= 1;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[s]);
     }
-    // A prefetched tile beyond the end issues no copy, so nothing is in flight
-    // here unless a wait gave up; then wait once more (bounded) for that copy
-    // before the shared memory is released.
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s)
-            if (timed_out[s]) mbar_wait(&bar[s], parity[s] ^ 1u, st);
-    }
-    __syncthreads();
 }
 
 // Segment offsets of N(t + dt), history, rotation (single CTA).
@@ -1375,7 +1460,7 @@ __global__ void k_finalize(StepParams P)
 {
     __shared__ long long wsum[32];
     DevState* st = P.st;
-    if (read_error(st)) return;
+    if (cta_error(st)) return;
     const int cur = st->cur, nxt = (cur + 1) % 3;
     int64_t* off = P.segoff[nxt];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1603,7 +1688,8 @@ void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, con
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream)
 {
     cudaMemsetAsync(out, 0, sizeof(SegStats) * P.nseg, stream);
-    k_obs<<<grid, kThreads, 0, stream>>>(P, which, out);
+    if (g_grid_misc == 0) configure_kernels();
+    k_obs<<<grid > 0 && grid < g_grid_misc ? grid : g_grid_misc, kThreads, 0, stream>>>(P, which, out);
 }
 
 void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int64_t* out, cudaStream_t stream)
@@ -1619,10 +1705,10 @@ namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
 int g_grid_spawn = 0, g_grid_choose = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0;
 
-int resident(const void* fn, int smem, int sms)
+int resident(const void* fn, int smem, int sms, int threads = kThreads)
 {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess || per < 1) per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) per = 1;
     return per * sms;
 }
 } // namespace
@@ -1637,32 +1723,33 @@ void configure_kernels()
     g_grid_choose = resident((const void*)k_spawn_choose, 0, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
-    g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms);
+    g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms, kMergeThreads);
     g_grid_misc = 2 * sms;
 }
 
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev)
 {
     if (g_grid_spawn == 0) configure_kernels();
-    (void)grid;
+    // grid > 0 caps every persistent or grid-stride kernel at that many CTAs
+    auto cap = [grid](int g) { return grid > 0 && grid < g ? grid : g; };
     // ev (optional): kNumTimedKernels + 1 events; kernel i runs between ev[i] and ev[i + 1]
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], stream); };
     mark(0);
     k_prologue<<<1, kThreads, 0, stream>>>(P);
     mark(1);
-    k_spawn_draw<<<g_grid_spawn, kThreads, 0, stream>>>(P);
+    k_spawn_draw<<<cap(g_grid_spawn), kThreads, 0, stream>>>(P);
     mark(2);
-    k_spawn_choose<<<g_grid_choose, kThreads, 0, stream>>>(P);
+    k_spawn_choose<<<cap(g_grid_choose), kThreads, 0, stream>>>(P);
     mark(3);
-    k_spawn_heavy<<<g_grid_heavy, kThreads, 0, stream>>>(P);
+    k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
     mark(4);
     const int np = P.key_passes + P.seg_passes;
-    k_sort_hist<<<g_grid_misc, kThreads, 0, stream>>>(P);
+    k_sort_hist<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
     mark(5);
     SRec* a = P.spawn;
     SRec* b = P.spawn_alt;
     for (int p = 0; p < np; ++p) {
-        k_sort_scatter<<<g_grid_sort, kThreads, 0, stream>>>(P, p, a, b);
+        k_sort_scatter<<<cap(g_grid_sort), kThreads, 0, stream>>>(P, p, a, b);
         SRec* t = a;
         a = b;
         b = t;
@@ -1673,9 +1760,9 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(7);
     k_merge_plan<<<1, 1024, 0, stream>>>(P);
     mark(8);
-    k_merge_part<<<g_grid_misc, kThreads, 0, stream>>>(P, sorted);
+    k_merge_part<<<cap(g_grid_misc), kThreads, 0, stream>>>(P, sorted);
     mark(9);
-    k_merge<<<g_grid_merge, kThreads, kMergeSmem, stream>>>(P, sorted);
+    k_merge<<<cap(g_grid_merge), kMergeThreads, kMergeSmem, stream>>>(P, sorted);
     mark(10);
     k_finalize<<<1, 1024, 0, stream>>>(P);
     mark(11);

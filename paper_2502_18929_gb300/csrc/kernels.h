@@ -10,8 +10,9 @@ namespace qmc {
 constexpr int kThreads = 256;
 constexpr int kSortItems = 8;                        // records per thread per sort tile
 constexpr int kSortTile = kThreads * kSortItems;     // 2048 records
-constexpr int kMergeItems = 7;                       // 7 x 16 B stride: lanes spread over all bank groups
-constexpr int kMergeTile = kThreads * kMergeItems;   // 1792 merged items
+constexpr int kMergeItems = 5;                       // 5 x 16 B stride: lanes spread over all bank groups
+constexpr int kMergeTile = kThreads * kMergeItems;   // 1280 merged items
+constexpr int kMergeThreads = kThreads + 64;         // merge CTA: 8 merging warps, a producer and a publisher
 constexpr int kHeavyWalkers = 256;                   // parents above this go to the heavy path
 constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
@@ -37,6 +38,16 @@ struct __align__(16) SpawnCand {
     uint32_t parent;  // index of the parent inside its population slot
     uint32_t seg;     // population vector
     uint64_t tf;      // T (52 bits) | comp << 52 | phase << 53 | noninit << 54 | (parent component > 0) << 55
+};
+
+// One merge tile: its slices of the segment's N(t) records and sorted spawns,
+// and the largest key before it (runs with that key belong to an earlier tile).
+struct MTileG {
+    int64_t a_glob;     // first N(t) record (index in the slot)
+    int64_t b_glob;     // first spawn record (index in the sorted spawns)
+    int64_t b_seg_end;  // end of the segment's spawns
+    uint64_t prev_key;
+    int32_t na, nb, seg, has_prev;
 };
 
 struct SegStats {
@@ -65,7 +76,7 @@ struct StepParams {
     int64_t sort_tiles_cap;
     int64_t* bseg;        // nseg + 1: offsets of each segment in the sorted spawns
     int64_t* tile_start;  // nseg + 1: first merge tile of each segment
-    int64_t* part;        // 2 per merge tile: local (a, b) start of the tile
+    MTileG* mtiles;       // per merge tile
     unsigned long long* merge_status; // per merge tile look-back word
     int64_t merge_tiles_cap;
     SegStats* segacc;     // per-segment accumulators of the merge

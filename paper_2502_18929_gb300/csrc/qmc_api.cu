@@ -86,7 +86,7 @@ StepParams params(qmc_ctx* c)
     P.sort_tiles_cap = c->sort_tiles_cap;
     P.bseg = c->d_bseg;
     P.tile_start = c->d_tile_start;
-    P.part = c->d_part;
+    P.mtiles = c->d_mtiles;
     P.merge_status = c->d_merge_status;
     P.merge_tiles_cap = c->merge_tiles_cap;
     P.segacc = c->d_segacc;
@@ -149,7 +149,7 @@ int grow_merge_tiles(qmc_ctx* ctx)
     const int64_t cap = (ctx->pop_cap + ctx->spawn_cap) / kMergeTile + ctx->cfg.n_segments + 2;
     if (cap <= ctx->merge_tiles_cap) return QMC_OK;
     int rc;
-    if ((rc = dalloc(ctx, &ctx->d_part, 2 * cap)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_mtiles, cap)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &ctx->d_merge_status, cap)) != QMC_OK) return rc;
     CK(cudaMemsetAsync(ctx->d_merge_status, 0, (size_t)cap * 8, ctx->work));
     ctx->merge_tiles_cap = cap;
@@ -230,12 +230,14 @@ int capture_graph(qmc_ctx* ctx)
     return QMC_OK;
 }
 
-int map_dev_error(qmc_ctx* ctx, uint32_t code)
+int map_dev_error(qmc_ctx* ctx, uint32_t code, uint32_t aux = 0)
 {
+    char site[64];
+    std::snprintf(site, sizeof(site), " (wait site %u, index %u)", aux >> 24, aux & 0xFFFFFFu);
     switch (code) {
     case DERR_DT_TOO_LARGE: return fail(ctx, QMC_ERR_DT_TOO_LARGE, "spawn probability p >= 1: reduce dt");
     case DERR_POP_OVERFLOW: return fail(ctx, QMC_ERR_POP_OVERFLOW, "a population component exceeds 2^31 - 1");
-    case DERR_TIMEOUT: return fail(ctx, QMC_ERR_DEVICE_TIMEOUT, "a bounded device wait expired");
+    case DERR_TIMEOUT: return fail(ctx, QMC_ERR_DEVICE_TIMEOUT, std::string("a bounded device wait expired") + site);
     default: return fail(ctx, QMC_ERR_CAPACITY, "capacity error");
     }
 }
@@ -267,7 +269,7 @@ int qmc_create(qmc_ctx** out, const qmc_config* cfg)
     auto bail = [&](int code) { qmc_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(QMC_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
-    ctx->grid = std::max(1, ctx->sm_count) * 3;
+    ctx->grid = cfg->max_ctas > 0 ? cfg->max_ctas : 0;   // 0: each kernel fills the GPU
     configure_kernels();
     if (cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) != cudaSuccess) return bail(QMC_ERR_CUDA);
     if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(QMC_ERR_CUDA);
@@ -303,7 +305,7 @@ void qmc_destroy(qmc_ctx* ctx)
     void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
                     ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
-                    ctx->d_part, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
+                    ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
                     ctx->d_progs, ctx->d_obs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -393,7 +395,7 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
     cudaFree(d_vals);
     if (hs.error) {
         clear_dev_error(ctx);
-        return map_dev_error(ctx, hs.error);
+        return map_dev_error(ctx, hs.error, hs.error_aux);
     }
     ctx->step = 0;
     ctx->t = ctx->t_prev = ctx->dt_last = 0.0;
@@ -589,7 +591,7 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
             }
             ctx->last_call_steps = done;
             leave(ctx);
-            return map_dev_error(ctx, code);
+            return map_dev_error(ctx, code, hs.error_aux);
         }
         // redo from the failed step
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &done, 4,

@@ -46,7 +46,7 @@ class QmcError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_segments", C.c_int32), ("integrator", C.c_int32),
-                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("n_diag", C.c_int64),
+                ("max_ctas", C.c_int32), ("seed", C.c_uint64), ("n_diag", C.c_int64),
                 ("initiator_min", C.c_int64), ("capacity_hint", C.c_int64), ("max_records", C.c_int64),
                 ("cuda_stream", C.c_void_p)]
 
@@ -148,12 +148,13 @@ class QMC:
     """One context: ``n_segments`` independent population vectors of one problem."""
 
     def __init__(self, n_qubits: int, n_segments: int, seed: int, n_diag: int, integrator: int = AB2,
-                 initiator_min: int = 0, capacity_hint: int = 0, max_records: int = 0, stream: int | None = None):
+                 initiator_min: int = 0, capacity_hint: int = 0, max_records: int = 0, stream: int | None = None,
+                 max_ctas: int = 0):
         self.L = lib()
         self.n = n_qubits
         self.nseg = n_segments
         self.n_diag = n_diag
-        cfg = Config(n_qubits, n_segments, integrator, 0, seed, n_diag, initiator_min, capacity_hint,
+        cfg = Config(n_qubits, n_segments, integrator, max_ctas, seed, n_diag, initiator_min, capacity_hint,
                      max_records, C.c_void_p(current_stream_handle() if stream is None else stream))
         h = C.c_void_p()
         rc = self.L.qmc_create(C.byref(h), C.byref(cfg))

@@ -17,9 +17,9 @@ from paper_2502_18929_gb300 import qmc
 pytestmark = pytest.mark.gpu
 
 
-def make_pair(prob, nseg, seed, n_diag, integrator=qmc.AB2, init_min=0, capacity_hint=0):
+def make_pair(prob, nseg, seed, n_diag, integrator=qmc.AB2, init_min=0, capacity_hint=0, max_ctas=0):
     gpu = qmc.QMC(prob.n, nseg, seed, n_diag, integrator=integrator, initiator_min=init_min,
-                  capacity_hint=capacity_hint)
+                  capacity_hint=capacity_hint, max_ctas=max_ctas)
     gpu.load_schedule(prob)
     orc = O.OracleSim(prob, nseg, seed, integrator=integrator, init_min=init_min, n_diag=n_diag)
     return gpu, orc
@@ -169,6 +169,22 @@ def test_all_walker_pair_layouts():
         assert orc.step(0.01, 1) == O.OK
         assert_same(gpu, orc, where=f"pair layouts step {k}")
         assert_same(gpu, orc, which=1, where=f"pair layouts prev {k}")
+
+
+@pytest.mark.parametrize("max_ctas", [1, 3, 7])
+def test_many_tiles_per_cta(max_ctas):
+    """Grids capped at a few CTAs: every persistent kernel runs many tiles per
+    CTA (both merge staging buffers, the end marker on either stage, sort and
+    merge look-back across CTAs that each hold several tiles)."""
+    prob = P.ghz_circuit(32)
+    gpu, orc = make_pair(prob, 2, 31, 10**6, max_ctas=max_ctas)
+    cur = _spread_state(32, 2, 14000 + max_ctas, 17)
+    prev = _spread_state(32, 2, 13000, 18)
+    _load_state(gpu, orc, cur, prev, 999, 5.3, 0.01)
+    for k in range(2):
+        gpu.step(0.01, 1)
+        assert orc.step(0.01, 1) == O.OK
+        assert_same(gpu, orc, where=f"many tiles step {k}")
 
 
 def test_heavy_and_light_parents():
