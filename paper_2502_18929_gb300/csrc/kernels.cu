@@ -1256,10 +1256,11 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// Shared memory: 2 input stages (each also holds its tile's compacted output
-// until the bulk store has read it) and 2 buffers of raw runs (kMergeTile
-// 16-byte items each).
-constexpr int kMergeSmem = 4 * kMergeTile * 16;
+// Shared memory: kMergeStages input stages (each also holds its tile's
+// compacted output until the bulk store has read it) and one buffer of raw
+// runs (kMergeTile 16-byte items each).
+constexpr int kMergeStages = 4;
+constexpr int kMergeSmem = (kMergeStages + 1) * kMergeTile * 16;
 
 // Per-tile hand-over from the merging warps to the publisher warp.
 struct MSlot {
@@ -1273,12 +1274,12 @@ struct MSlot {
 __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const SRec* __restrict__ sorted)
 {
     extern __shared__ __align__(128) uint4 msm[];
-    uint4* inbuf = msm;                       // [2][kMergeTile]
-    uint4* rawb = msm + 2 * kMergeTile;       // [2][kMergeTile]
-    __shared__ __align__(8) uint64_t full[2], empty[2], ready[2];
-    __shared__ MTileG meta[2];
-    __shared__ int64_t meta_t[2];
-    __shared__ MSlot slot[2];
+    uint4* inbuf = msm;                                // [kMergeStages][kMergeTile]
+    uint4* raw = msm + kMergeStages * kMergeTile;      // [kMergeTile]
+    __shared__ __align__(8) uint64_t full[kMergeStages], empty[kMergeStages], ready[kMergeStages];
+    __shared__ MTileG meta[kMergeStages];
+    __shared__ int64_t meta_t[kMergeStages];
+    __shared__ MSlot slot[kMergeStages];
     __shared__ int s_wcount[2][kThreads / 32];
     __shared__ long long s_red[2][3][kThreads / 32];
     __shared__ int s_abort;
@@ -1293,7 +1294,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kMergeWarps = kThreads / 32;
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kMergeStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
             mbar_init(&ready[s], kMergeWarps);
@@ -1306,11 +1307,12 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
     if (warp == kMergeWarps) {
         // producer: take tiles in order (one ticket each), stage them
         if (lane != 0) return;
-        int issued[2] = {0, 0};
+        int issued[kMergeStages] = {};
         int end_stage = -1;
         for (int k = 0;; ++k) {
-            const int s = k & 1;
-            if (k >= 2 && !mbar_wait(&empty[s], (uint32_t)(((k >> 1) - 1) & 1), st, 3u, k)) break;
+            const int s = k % kMergeStages;
+            if (k >= kMergeStages && !mbar_wait(&empty[s], (uint32_t)((k / kMergeStages - 1) & 1), st, 3u, k))
+                break;
             const int64_t t = (int64_t)atomicAdd(&st->tile_ctr[kCtrMerge], 1u);
             meta_t[s] = t;
             if (t >= T) {
@@ -1331,33 +1333,34 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
         // end marker goes to a stage only after its last copy was consumed
         // (and its phase parity no longer names that copy); on the other
         // stage the last copy's phase is the current or the previous one.
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < kMergeStages; ++s)
             if (issued[s] && s != end_stage) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), st, 4u, s);
         return;
     }
 
+    const uint32_t epoch = st->seq + 15u;
     if (warp == kMergeWarps + 1) {
-        // publisher: place each tile after its predecessors, store it
-        const uint32_t epoch = st->seq + 15u;
+        // publisher: place each tile after its predecessors (the merging
+        // warps published its aggregate), store it.  A stage is released once
+        // its bulk store has read it: right away when the tile stores
+        // nothing, else after the next store is issued.
+        int pending = -1;
         for (int k = 0;; ++k) {
-            const int s = k & 1;
-            if (!mbar_wait(&ready[s], (uint32_t)((k >> 1) & 1), st, 6u, k)) break;
+            const int s = k % kMergeStages;
+            if (!mbar_wait(&ready[s], (uint32_t)((k / kMergeStages) & 1), st, 6u, k)) break;
             const MSlot sl = slot[s];
             if (sl.t >= T) break;
-            unsigned long long* my = P.merge_status + sl.t;
             unsigned long long excl = 0;
-            if (sl.t == 0) {
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)sl.count));
-            } else {
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, (uint32_t)sl.count));
+            if (sl.t > 0) {
                 excl = warp_lookback(P.merge_status, sl.t, epoch, st, lane, 2u);
-                if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + sl.count)));
+                if (lane == 0) st_vol(P.merge_status + sl.t, lb_word(epoch, kFlagIncl, (uint32_t)(excl + sl.count)));
             }
             if (lane == 0) {
                 if (sl.t == T - 1) {
                     st->next_total = (int64_t)(excl + sl.count);
                     if ((int64_t)(excl + sl.count) > st->max_next) st->max_next = (int64_t)(excl + sl.count);
                 }
+                bool stored = false;
                 if (sl.count) {
                     atomicAdd(&P.segacc[sl.seg].count, (unsigned long long)sl.count);
                     atomicAdd((unsigned long long*)&P.segacc[sl.seg].ntot, (unsigned long long)sl.ntot);
@@ -1371,10 +1374,19 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
                     }
                     if (cnt > 0) {
                         bulk_store(out + base, inbuf + s * kMergeTile, (uint32_t)cnt * 16u);
-                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                        stored = true;
                     }
                 }
-                mbar_arrive(&empty[s]);   // stage s (input and output) may be refilled
+                if (stored) {
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    if (pending >= 0) mbar_arrive(&empty[pending]);
+                    pending = s;
+                } else {
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    if (pending >= 0) mbar_arrive(&empty[pending]);
+                    pending = -1;
+                    mbar_arrive(&empty[s]);
+                }
             }
             __syncwarp();
         }
@@ -1384,14 +1396,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
 
     // merging threads
     for (int k = 0;; ++k) {
-        const int s = k & 1;
-        const bool ok = mbar_wait(&full[s], (uint32_t)((k >> 1) & 1), st, 5u, k);
+        const int s = k % kMergeStages, h = k & 1;
+        const bool ok = mbar_wait(&full[s], (uint32_t)((k / kMergeStages) & 1), st, 5u, k);
         if (!ok) s_abort = 1;
         const int64_t t = ok ? meta_t[s] : T;
         long long my_ntot = 0, my_dre = 0, my_dim = 0;
         int nout = 0;
         int seg = 0;
-        uint4* raw = rawb + s * kMergeTile;
         if (t < T) {
             const MTileG m = meta[s];
             seg = m.seg;
@@ -1405,7 +1416,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
             const int v = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += v;
         }
-        if (lane == 31) s_wcount[s][warp] = incl;
+        if (lane == 31) s_wcount[h][warp] = incl;
         long long r0 = my_ntot, r1 = my_dre, r2 = my_dim;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1414,9 +1425,9 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
             r2 += __shfl_down_sync(kFull, r2, o);
         }
         if (lane == 0) {
-            s_red[s][0][warp] = r0;
-            s_red[s][1][warp] = r1;
-            s_red[s][2][warp] = r2;
+            s_red[h][0][warp] = r0;
+            s_red[h][1][warp] = r1;
+            s_red[h][2][warp] = r2;
         }
         merge_bar();   // walks of the tile done, counts known
         if (s_abort || t >= T) {
@@ -1429,24 +1440,27 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
         int woff = 0, tile_count = 0;
 #pragma unroll
         for (int w = 0; w < kMergeWarps; ++w) {
-            if (w < warp) woff += s_wcount[s][w];
-            tile_count += s_wcount[s][w];
+            if (w < warp) woff += s_wcount[h][w];
+            tile_count += s_wcount[h][w];
         }
         // compact the runs over the consumed input stage
         uint4* ob = inbuf + s * kMergeTile;
         const int pos = woff + incl - nout;
         for (int r = 0; r < nout; ++r) ob[pos + r] = raw[tid * kMergeItems + r];
         fence_proxy_async();   // generic writes of ob before the bulk store reads them
+        merge_bar();           // raw runs read before the next walk rewrites them
         if (tid == 0) {
+            // the tile's aggregate (inclusive prefix for the first tile), at once
+            st_vol(P.merge_status + t, lb_word(epoch, t == 0 ? kFlagIncl : kFlagAgg, (uint32_t)tile_count));
             MSlot sl;
             sl.t = t;
             sl.count = tile_count;
             sl.seg = seg;
             sl.ntot = sl.dre = sl.dim = 0;
             for (int w = 0; w < kMergeWarps; ++w) {
-                sl.ntot += s_red[s][0][w];
-                sl.dre += s_red[s][1][w];
-                sl.dim += s_red[s][2][w];
+                sl.ntot += s_red[h][0][w];
+                sl.dre += s_red[h][1][w];
+                sl.dim += s_red[h][2][w];
             }
             slot[s] = sl;
         }
