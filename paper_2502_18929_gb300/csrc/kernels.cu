@@ -479,7 +479,9 @@ __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCan
 
 // Second walker pairs of parents with two pairs, queued per warp and drawn 32
 // at a time: (parent index, vector) in a ring of kPairRing entries.
-constexpr int kPairRing = 64;
+constexpr int kPairRing = 128;
+constexpr int kDrawChunk = 64;    // parents per staged chunk (1 KB)
+constexpr int kDrawStages = 4;    // staged chunks per warp
 
 __device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand* stage, int* staged,
                                                   const uint2* ring, int head, int cnt, const Rec* src, int phase,
@@ -515,15 +517,17 @@ __device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand
 }
 
 // Walker draws of one population slot (phase 0: N(t), phase 1: N(t - dt)).
-// The warp owns parents [wb, we) of the slot and reads them 32 at a time,
-// one group ahead.  In the common group every parent has at most two walker
-// pairs: each lane draws its parent's first pair (one Philox call, its raw
-// 64-bit output X compared with bound << 12: T = X >> 12 < bound iff
-// X < bound << 12), and second pairs are queued and drawn 32 at a time.
-// Groups with more pairs per parent, or heavy parents, take the general path.
+// The warp owns parents [wb, we) of the slot and reads them 64 at a time
+// (lane l takes parents g0 + l and g0 + 32 + l), one group ahead.  In the
+// common group every parent has at most two walker pairs: each lane draws its
+// parents' first pairs (one Philox call each, the raw 64-bit output X compared
+// with bound << 12: T = X >> 12 < bound iff X < bound << 12), and second pairs
+// are queued and drawn 32 at a time.  A half-group with more pairs per parent,
+// or heavy parents, takes the general path.
 __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint2* ring,
-                                          const Rec* src, const int64_t* off, int64_t wb, int64_t we, int phase,
-                                          uint64_t bound, int lane)
+                                          Rec* buf, uint64_t* bar, uint32_t* chunk_no, const Rec* src,
+                                          const int64_t* off, int64_t wb, int64_t we, int phase, uint64_t bound,
+                                          int lane)
 {
     // bound = 2^52 (every walker a candidate): X < 2^64 always holds
     const bool all_cand = bound >= (1ull << 52);
@@ -534,66 +538,127 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
     int64_t seg_end = -1;
     uint2 kd = make_uint2(0u, 0u);
     int head = 0, cnt = 0;   // ring of queued second pairs
-    Rec nxt{0ull, 0, 0};
-    if (wb + lane < we) nxt = load_parent(src + wb + lane);
-    for (int64_t g0 = wb; g0 < we; g0 += 32) {
-        const int64_t i = g0 + lane;
-        const bool valid = i < we;
-        const Rec par = nxt;
-        if (i + 32 < we) nxt = load_parent(src + i + 32);
-        if (valid && i >= seg_end) {
-            seg = seg_of(off, P.nseg, i);
+    // chunks of kDrawChunk parents staged by bulk copies, kDrawStages - 1 ahead;
+    // the warp's c-th chunk overall uses stage c % kDrawStages
+    const int64_t nch = (we - wb + kDrawChunk - 1) / kDrawChunk;
+    const uint32_t c0 = *chunk_no;
+    bool gave_up = false;
+    auto issue = [&](int64_t j) {
+        const uint32_t c = c0 + (uint32_t)j;
+        const int64_t g = wb + j * kDrawChunk;
+        const uint32_t bytes = (uint32_t)min((int64_t)kDrawChunk, we - g) * 16u;
+        uint64_t* b = bar + c % kDrawStages;
+        fence_proxy_async();
+        mbar_arrive_expect(b, bytes);
+        bulk_load(buf + (c % kDrawStages) * kDrawChunk, src + g, bytes, b);
+    };
+    if (lane == 0)
+        for (int64_t j = 0; j < kDrawStages - 1 && j < nch; ++j) issue(j);
+    for (int64_t j = 0; j < nch; ++j) {
+        const int64_t g0 = wb + j * kDrawChunk;
+        const uint32_t c = c0 + (uint32_t)j;
+        if (lane == 0 && j + kDrawStages - 1 < nch) issue(j + kDrawStages - 1);
+        const Rec* tb = buf + (c % kDrawStages) * kDrawChunk;
+        const bool ok = mbar_wait(bar + c % kDrawStages, (c / kDrawStages) & 1u, P.st, 7u, j);
+        if (!ok) gave_up = true;
+        const int64_t iA = g0 + lane, iB = iA + 32;
+        const bool vA = ok && iA < we, vB = ok && iB < we;
+        Rec pA{0ull, 0, 0}, pB{0ull, 0, 0};
+        if (vA) pA = tb[lane];
+        if (vB) pB = tb[lane + 32];
+        __syncwarp();   // the stage is read before it is refilled
+        if (vA && iA >= seg_end) {
+            seg = seg_of(off, P.nseg, iA);
             seg_end = __ldg(&off[seg + 1]);
             kd = P.kd[seg];
         }
-        const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
-        const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
-        const uint32_t pre = (are + 1u) >> 1, pim = (aim + 1u) >> 1;
-        if (!__all_sync(kFull, are <= 4u && aim <= 4u && pre + pim <= 2u)) {
-            draw_group_general(P, stage, staged, valid, par, (uint32_t)i, phase, seg, kd, bound, lane);
+        const int segA = seg;
+        const uint2 kdA = kd;
+        if (vB && iB >= seg_end) {
+            seg = seg_of(off, P.nseg, iB);
+            seg_end = __ldg(&off[seg + 1]);
+            kd = P.kd[seg];
+        }
+        const uint32_t areA = vA ? (pA.re < 0 ? 0u - (uint32_t)pA.re : (uint32_t)pA.re) : 0u;
+        const uint32_t aimA = vA ? (pA.im < 0 ? 0u - (uint32_t)pA.im : (uint32_t)pA.im) : 0u;
+        const uint32_t areB = vB ? (pB.re < 0 ? 0u - (uint32_t)pB.re : (uint32_t)pB.re) : 0u;
+        const uint32_t aimB = vB ? (pB.im < 0 ? 0u - (uint32_t)pB.im : (uint32_t)pB.im) : 0u;
+        const uint32_t prA = ((areA + 1u) >> 1) + ((aimA + 1u) >> 1);
+        const uint32_t prB = ((areB + 1u) >> 1) + ((aimB + 1u) >> 1);
+        if (!__all_sync(kFull, (areA | aimA | areB | aimB) <= 4u && prA <= 2u && prB <= 2u)) {
+            draw_group_general(P, stage, staged, vA, pA, (uint32_t)iA, phase, segA, kdA, bound, lane);
+            draw_group_general(P, stage, staged, vB, pB, (uint32_t)iB, phase, seg, kd, bound, lane);
             continue;
         }
         // queue the second pairs
-        const bool two = pre + pim == 2u;
-        const uint32_t bt = __ballot_sync(kFull, two);
-        if (bt) {
-            if (two) ring[(head + cnt + __popc(bt & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)i, (uint32_t)seg);
-            cnt += __popc(bt);
+        const uint32_t btA = __ballot_sync(kFull, prA == 2u), btB = __ballot_sync(kFull, prB == 2u);
+        if (btA | btB) {
+            const int q = head + cnt;
+            if (prA == 2u) ring[(q + __popc(btA & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)iA, (uint32_t)segA);
+            if (prB == 2u)
+                ring[(q + __popc(btA) + __popc(btB & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)iB, (uint32_t)seg);
+            cnt += __popc(btA) + __popc(btB);
             __syncwarp();
-            if (cnt >= 32) {
+            while (cnt >= 32) {
                 draw_second_pairs(P, stage, staged, ring, head, 32, src, phase, all_cand, b12, lane);
                 head = (head + 32) & (kPairRing - 1);
                 cnt -= 32;
                 __syncwarp();
             }
         }
-        // first pair: pair 0 of the real component if it has walkers, else of the imaginary one
-        const uint32_t comp = are == 0u ? 1u : 0u;
-        const uint32_t m = comp ? aim : are;
-        const uint4 w = philox10(make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                                            (uint32_t)phase | (comp << 1) | (kKindSpawn << 2), 0u),
-                                 kd);
-        const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
-        const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
-        const bool c0 = m != 0u && (all_cand || X0 < b12);
-        const bool c1 = m >= 2u && (all_cand || X1 < b12);
-        const uint32_t b0 = __ballot_sync(kFull, c0), b1 = __ballot_sync(kFull, c1);
-        if ((b0 | b1) == 0u) continue;
-        const int noninit = (init_rule && (int64_t)((uint64_t)are + aim) < P.init_min) ? 1 : 0;
-        const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
-        cand_push(stage, staged, c0, c1, (uint32_t)i, (uint32_t)seg, (X0 >> 12) | fl, (X1 >> 12) | fl, P, lane);
+        // first pairs: pair 0 of the real component if it has walkers, else of the imaginary one
+        const uint32_t compA = areA == 0u ? 1u : 0u, compB = areB == 0u ? 1u : 0u;
+        const uint32_t mA = compA ? aimA : areA, mB = compB ? aimB : areB;
+        const uint4 wA = philox10(make_uint4((uint32_t)pA.key, (uint32_t)(pA.key >> 32),
+                                             (uint32_t)phase | (compA << 1) | (kKindSpawn << 2), 0u),
+                                  kdA);
+        const uint4 wB = philox10(make_uint4((uint32_t)pB.key, (uint32_t)(pB.key >> 32),
+                                             (uint32_t)phase | (compB << 1) | (kKindSpawn << 2), 0u),
+                                  kd);
+        const uint64_t XA0 = ((uint64_t)wA.y << 32) | wA.x, XA1 = ((uint64_t)wA.w << 32) | wA.z;
+        const uint64_t XB0 = ((uint64_t)wB.y << 32) | wB.x, XB1 = ((uint64_t)wB.w << 32) | wB.z;
+        const bool cA0 = mA != 0u && (all_cand || XA0 < b12), cA1 = mA >= 2u && (all_cand || XA1 < b12);
+        const bool cB0 = mB != 0u && (all_cand || XB0 < b12), cB1 = mB >= 2u && (all_cand || XB1 < b12);
+        if (__any_sync(kFull, cA0 || cA1)) {
+            const int non = (init_rule && (int64_t)((uint64_t)areA + aimA) < P.init_min) ? 1 : 0;
+            const uint64_t fl = cand_flags((int)compA, phase, non, compA ? pA.im : pA.re);
+            cand_push(stage, staged, cA0, cA1, (uint32_t)iA, (uint32_t)segA, (XA0 >> 12) | fl, (XA1 >> 12) | fl, P,
+                      lane);
+        }
+        if (__any_sync(kFull, cB0 || cB1)) {
+            const int non = (init_rule && (int64_t)((uint64_t)areB + aimB) < P.init_min) ? 1 : 0;
+            const uint64_t fl = cand_flags((int)compB, phase, non, compB ? pB.im : pB.re);
+            cand_push(stage, staged, cB0, cB1, (uint32_t)iB, (uint32_t)seg, (XB0 >> 12) | fl, (XB1 >> 12) | fl, P,
+                      lane);
+        }
     }
     if (cnt > 0) draw_second_pairs(P, stage, staged, ring, head, cnt, src, phase, all_cand, b12, lane);
+    if (gave_up) {
+        // a copy may still be landing in the last stages: wait for them once more (bounded)
+        for (int64_t j = nch > kDrawStages ? nch - kDrawStages : 0; j < nch; ++j) {
+            const uint32_t c = c0 + (uint32_t)j;
+            mbar_wait(bar + c % kDrawStages, (c / kDrawStages) & 1u, P.st, 7u, j);
+        }
+    }
+    *chunk_no = c0 + (uint32_t)nch;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_spawn_draw(StepParams P)
+__global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
 {
     __shared__ __align__(16) SpawnCand sstage[kThreads / 32][kCandStage];
     __shared__ __align__(16) uint2 sring[kThreads / 32][kPairRing];
+    __shared__ __align__(128) Rec sbuf[kThreads / 32][kDrawStages * kDrawChunk];
+    __shared__ __align__(8) uint64_t sbar[kThreads / 32][kDrawStages];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     SpawnCand* stage = sstage[warp];
+    if (lane == 0) {
+        for (int q = 0; q < kDrawStages; ++q) mbar_init(&sbar[warp][q], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t chunk_no = 0;
     const StepInfo inf = P.info[st->call_index];
     const int cur = st->cur, prv = (cur + 2) % 3;
     // filter: a walker can only spawn if T < P <= p_bound (every walker is a
@@ -607,12 +672,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_spawn_draw(StepParams P)
     for (int phase = 0; phase < (inf.ab2 ? 2 : 1); ++phase) {
         const int slot = phase ? prv : cur;
         const int64_t K = st->count[slot];
-        // each warp owns one contiguous range of the slot, a multiple of 32
-        const int64_t chunk = ((K + nwarps - 1) / nwarps + 31) / 32 * 32;
+        // each warp owns one contiguous range of the slot, a multiple of 64
+        const int64_t chunk = ((K + nwarps - 1) / nwarps + 63) / 64 * 64;
         const int64_t wb = min(K, gw * chunk), we = min(K, wb + chunk);
         const int64_t pb = phase ? pb1 : pb0;
-        draw_slot(P, stage, &staged, sring[warp], P.pop[slot], P.segoff[slot], wb, we, phase,
-                  (uint64_t)(pb >= lim52 ? lim52 : pb), lane);
+        draw_slot(P, stage, &staged, sring[warp], sbuf[warp], sbar[warp], &chunk_no, P.pop[slot], P.segoff[slot],
+                  wb, we, phase, (uint64_t)(pb >= lim52 ? lim52 : pb), lane);
     }
     if (staged) cand_flush(stage, staged, P, lane);
 }
