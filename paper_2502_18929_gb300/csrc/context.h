@@ -40,6 +40,10 @@ struct qmc_ctx {
     SRec* d_spawn_alt = nullptr;
     int64_t spawn_cap = 0;
     SpawnCand* d_cand = nullptr;
+    uint32_t* d_bucket = nullptr;
+    unsigned long long* d_bscan_status = nullptr;
+    uint32_t* d_win = nullptr;
+    uint32_t* d_big_list = nullptr;
     int64_t cand_cap = 0;
     HeavyItem* d_heavy = nullptr;
     int64_t heavy_cap = 0;

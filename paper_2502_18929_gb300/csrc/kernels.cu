@@ -201,6 +201,10 @@ __global__ void k_prologue(StepParams P)
     if (threadIdx.x == 0) {
         st->spawn_total = 0;
         st->cand_total = 0;
+        // LSD radix sort when the bucket sort does not apply (it may still fall back to it)
+        st->sort_fallback = P.sort_mode == 0 ? 1u : 0u;
+        st->big_windows = 0u;
+        st->sort_final = P.sort_mode == 0 ? (uint32_t)((P.key_passes + P.seg_passes) & 1) : 1u;
         st->heavy_total = 0;
         st->next_total = 0;
         st->merge_tiles = 0;
@@ -653,6 +657,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
     if (cta_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     SpawnCand* stage = sstage[warp];
+    if (P.sort_mode)   // bucket counters of this step's spawn sort
+        for (int b = blockIdx.x * kThreads + threadIdx.x; b < (1 << P.bucket_bits); b += gridDim.x * kThreads)
+            P.bucket[b] = 0u;
     if (lane == 0) {
         for (int q = 0; q < kDrawStages; ++q) mbar_init(&sbar[warp][q], 1);
         mbar_fence_init();
@@ -885,7 +892,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(StepParams P)
 {
     __shared__ unsigned int h[kMaxPasses * 256];
     DevState* st = P.st;
-    if (cta_error(st)) return;
+    if (cta_error(st) || !st->sort_fallback) return;
     const int64_t S = min(st->spawn_total, P.spawn_cap);
     const int np = P.key_passes + P.seg_passes;
     for (int i = threadIdx.x; i < np * 256; i += kThreads) h[i] = 0u;
@@ -909,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
     __shared__ unsigned int lstart[256];
     __shared__ unsigned int s_tile;
     DevState* st = P.st;
-    if (cta_error(st)) return;
+    if (cta_error(st) || !st->sort_fallback) return;
     const int64_t S = min(st->spawn_total, P.spawn_cap);
     const int64_t ntiles = (S + kSortTile - 1) / kSortTile;
     if (ntiles > P.sort_tiles_cap) {
@@ -1055,11 +1062,294 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
     }
 }
 
-// Offsets of each segment inside the sorted spawns (lower bounds).
-__global__ void k_spawn_segoff(StepParams P, const SRec* __restrict__ sorted)
+// ---------------------------------------------------------------------------
+// Spawn sort by buckets.  The sort key is (vector, key); its top bucket_bits
+// bits (all vector bits and the top bucket_kb key bits) pick one of up to
+// 2^kBucketBits buckets.  One counting pass places every spawn record in its
+// bucket (order inside a bucket arbitrary).  Buckets come in sort-key order,
+// so any run of whole buckets sorted by key is in final order: the records
+// are cut into windows of whole buckets, window k starting at the bucket that
+// holds record k * kSortWin, and each window is sorted in shared memory (a
+// warp for up to kSmallBucket records, a CTA for up to kBigBucket).  When the
+// whole sort key fits the bucket digit the counting pass alone sorts.  A
+// bucket too large for a window sends the step to the LSD radix sort instead
+// (st->sort_fallback).
+// ---------------------------------------------------------------------------
+constexpr int kSmallBucket = 256;   // records a warp sorts
+constexpr int kBigBucket = 4096;    // records a CTA sorts
+constexpr int kSortWin = 224;       // sort windows: whole buckets from every kSortWin-th record
+
+__device__ __forceinline__ uint32_t bucket_of(const SRec& r, const StepParams& P)
+{
+    const uint32_t seg = r.meta >> 2;
+    const int kb = P.bucket_kb;
+    uint32_t d = seg << kb;
+    if (kb) d |= (uint32_t)(r.key >> (2 * P.n - kb));
+    return d;
+}
+
+// Bucket sizes of the step's spawn records.
+__global__ void __launch_bounds__(kThreads) k_bucket_hist(StepParams P)
 {
     DevState* st = P.st;
     if (read_error(st)) return;
+    const int64_t S = min(st->spawn_total, P.spawn_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < S; i += (int64_t)gridDim.x * kThreads)
+        atomicAdd(&P.bucket[bucket_of(P.spawn[i], P)], 1u);
+}
+
+// Exclusive scan of the bucket sizes into bucket cursors: 1024 buckets per
+// CTA, CTAs placed in ticket order by a decoupled look-back; decides between
+// the bucket sort and the LSD fallback.
+__global__ void __launch_bounds__(1024) k_bucket_scan(StepParams P)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t wmax[32];
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_excl;
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[kCtrBucket], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int nb = 1 << P.bucket_bits;
+    const int b = (int)tile * 1024 + tid;
+    const uint32_t c = b < nb ? P.bucket[b] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t wm = __reduce_max_sync(kFull, c);
+    if (lane == 31) wsum[warp] = incl;
+    if (lane == 0) wmax[warp] = wm;
+    __syncthreads();
+    uint32_t base = 0, tot = 0, gmax = 0;
+    for (int w = 0; w < 32; ++w) {
+        if (w < warp) base += wsum[w];
+        tot += wsum[w];
+        gmax = wmax[w] > gmax ? wmax[w] : gmax;
+    }
+    if (warp == 0) {
+        const uint32_t epoch = st->seq + 14u;
+        unsigned long long* my = P.bscan_status + tile;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, tot));
+        } else {
+            if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, tot));
+            excl = warp_lookback(P.bscan_status, tile, epoch, st, lane, 8u);
+            if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tot)));
+        }
+        if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    if (b < nb) {
+        const uint32_t start = (uint32_t)s_excl + base + incl - c;
+        P.bucket[b] = start;
+        // window k of the bucket sorts starts at the bucket holding position k * kSortWin
+        for (uint32_t k = (start + kSortWin - 1) / kSortWin; k * kSortWin < start + c; ++k) P.win[k] = start;
+    }
+    if (tid == 0 && P.sort_mode == 1 && gmax > (uint32_t)(kBigBucket - kSortWin)) {
+        // a bucket too large for the bucket sorts: LSD radix sort for this step
+        st->sort_fallback = 1u;
+        st->sort_final = (uint32_t)((P.key_passes + P.seg_passes) & 1);
+    }
+}
+
+// Counting pass: spawn -> spawn_alt, each record into its bucket.  Afterwards
+// bucket[b] is the end of bucket b.
+__global__ void __launch_bounds__(kThreads) k_bucket_scatter(StepParams P)
+{
+    DevState* st = P.st;
+    if (read_error(st) || st->sort_fallback) return;
+    const int64_t S = min(st->spawn_total, P.spawn_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < S; i += (int64_t)gridDim.x * kThreads) {
+        const SRec r = P.spawn[i];
+        const uint32_t pos = atomicAdd(&P.bucket[bucket_of(r, P)], 1u);
+        if ((int64_t)pos < S) P.spawn_alt[pos] = r;
+    }
+}
+
+// Bitonic sort (N a power of two) by (G >> 12, K): G holds the record's
+// vector above its 12-bit index in the window, K its key; a window may span
+// vectors.  Threads [t0, N/2) step nthr take the compare-exchanges, sync()
+// orders the stages.
+template <typename Sync>
+__device__ __forceinline__ void bitonic_sort(uint64_t* K, uint32_t* G, int N, int t0, int nthr, Sync sync)
+{
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = t0; t < (N >> 1); t += nthr) {
+                const int low = t & (j - 1);
+                const int i = ((t - low) << 1) + low;   // bit j of i is clear
+                const int l = i + j;
+                const bool asc = (i & k) == 0;
+                const uint64_t a = K[i], c = K[l];
+                const uint32_t ga = G[i], gc = G[l];
+                const bool gt = (ga >> 12) != (gc >> 12) ? (ga >> 12) > (gc >> 12) : a > c;
+                if (gt == asc) {
+                    K[i] = c;
+                    K[l] = a;
+                    G[i] = gc;
+                    G[l] = ga;
+                }
+            }
+            sync();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(int n)
+{
+    int N = 2;
+    while (N < n) N <<= 1;
+    return N;
+}
+
+constexpr int kSmallSortSmem = (kThreads / 32) * kSmallBucket * (16 + 8 + 4);
+
+// Bounds of sort window k: [win[k], win[k + 1]), the last one ending at S.
+__device__ __forceinline__ void window_bounds(const StepParams& P, int64_t k, int64_t nwin, uint32_t S,
+                                              uint32_t* lo, uint32_t* hi)
+{
+    *lo = P.win[k];
+    *hi = k + 1 < nwin ? P.win[k + 1] : S;
+}
+
+// Sort windows of up to kSmallBucket records, one warp each, in place; larger
+// windows go to the list of k_bucket_sort_big.
+__global__ void __launch_bounds__(kThreads) k_bucket_sort_small(StepParams P)
+{
+    extern __shared__ __align__(16) uint8_t ssm[];
+    DevState* st = P.st;
+    if (read_error(st) || st->sort_fallback || P.sort_mode != 1) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4* Rw = (uint4*)ssm + warp * kSmallBucket;
+    uint64_t* Kw = (uint64_t*)(ssm + (kThreads / 32) * kSmallBucket * 16) + warp * kSmallBucket;
+    uint32_t* Gw = (uint32_t*)(ssm + (kThreads / 32) * kSmallBucket * 24) + warp * kSmallBucket;
+    const uint32_t S = (uint32_t)min(st->spawn_total, P.spawn_cap);
+    const int64_t nwin = ((int64_t)S + kSortWin - 1) / kSortWin;
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    uint4* A = (uint4*)P.spawn_alt;
+    for (int64_t k = (int64_t)blockIdx.x * (kThreads / 32) + warp; k < nwin; k += nwarps) {
+        uint32_t start, end;
+        window_bounds(P, k, nwin, S, &start, &end);
+        const int n = (int)(end - start);
+        if (n <= 1) continue;
+        if (n > kSmallBucket) {
+            if (lane == 0) {
+                const uint32_t q = atomicAdd(&st->big_windows, 1u);
+                P.big_list[q] = (uint32_t)k;
+            }
+            continue;
+        }
+        if (n <= 32) {
+            // one record per lane, bitonic network over the lanes
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (lane < n) v = A[start + lane];
+            uint64_t key = lane < n ? (((uint64_t)v.y << 32) | v.x) : ~0ull;
+            uint32_t seg = lane < n ? (v.z >> 2) : 0xFFFFFFFFu;
+            int idx = lane;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    const uint64_t ok = __shfl_xor_sync(kFull, key, j);
+                    const uint32_t os = __shfl_xor_sync(kFull, seg, j);
+                    const int oi = __shfl_xor_sync(kFull, idx, j);
+                    const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
+                    const bool lt = os != seg ? os < seg : ok < key;
+                    const bool gt = os != seg ? os > seg : ok > key;
+                    if (keep_min ? lt : gt) {
+                        key = ok;
+                        seg = os;
+                        idx = oi;
+                    }
+                }
+            }
+            const uint4 r = make_uint4(__shfl_sync(kFull, v.x, idx), __shfl_sync(kFull, v.y, idx),
+                                       __shfl_sync(kFull, v.z, idx), __shfl_sync(kFull, v.w, idx));
+            if (lane < n) A[start + lane] = r;
+            continue;
+        }
+        const int N = pow2_at_least(n);
+        for (int j = lane; j < N; j += 32) {
+            if (j < n) {
+                const uint4 v = A[start + j];
+                Rw[j] = v;
+                Kw[j] = ((uint64_t)v.y << 32) | v.x;
+                Gw[j] = ((v.z >> 2) << 12) | (uint32_t)j;
+            } else {
+                Kw[j] = ~0ull;
+                Gw[j] = 0xFFFFF000u | (uint32_t)j;
+            }
+        }
+        __syncwarp();
+        bitonic_sort(Kw, Gw, N, lane, 32, [] { __syncwarp(); });
+        for (int j = lane; j < n; j += 32) A[start + j] = Rw[Gw[j] & 0xFFFu];
+        __syncwarp();
+    }
+}
+
+constexpr int kBigSortSmem = kBigBucket * (16 + 8 + 4);
+
+// Windows of kSmallBucket + 1 .. kBigBucket records (listed by
+// k_bucket_sort_small), one CTA each.
+__global__ void __launch_bounds__(kThreads) k_bucket_sort_big(StepParams P)
+{
+    extern __shared__ __align__(16) uint8_t bsm[];
+    uint4* R = (uint4*)bsm;
+    uint64_t* K = (uint64_t*)(bsm + kBigBucket * 16);
+    uint32_t* G = (uint32_t*)(bsm + kBigBucket * 24);
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback || P.sort_mode != 1) return;
+    const int tid = threadIdx.x;
+    const uint32_t S = (uint32_t)min(st->spawn_total, P.spawn_cap);
+    const int64_t nwin = ((int64_t)S + kSortWin - 1) / kSortWin;
+    const uint32_t nbig = st->big_windows;
+    uint4* A = (uint4*)P.spawn_alt;
+    for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
+        uint32_t start, end;
+        window_bounds(P, (int64_t)P.big_list[q], nwin, S, &start, &end);
+        const int n = (int)(end - start);
+        if (n > kBigBucket) {   // excluded by the fallback rule
+            if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
+            continue;
+        }
+        const int N = pow2_at_least(n);
+        for (int j = tid; j < N; j += kThreads) {
+            if (j < n) {
+                const uint4 v = A[start + j];
+                R[j] = v;
+                K[j] = ((uint64_t)v.y << 32) | v.x;
+                G[j] = ((v.z >> 2) << 12) | (uint32_t)j;
+            } else {
+                K[j] = ~0ull;
+                G[j] = 0xFFFFF000u | (uint32_t)j;
+            }
+        }
+        __syncthreads();
+        bitonic_sort(K, G, N, tid, kThreads, [] { __syncthreads(); });
+        for (int j = tid; j < n; j += kThreads) A[start + j] = R[G[j] & 0xFFFu];
+        __syncthreads();
+    }
+}
+
+// Offsets of each segment inside the sorted spawns (lower bounds).
+// The sorted spawn records of the step (where the bucket or LSD sort left them).
+__device__ __forceinline__ const SRec* sorted_spawns(const StepParams& P)
+{
+    return P.st->sort_final ? P.spawn_alt : P.spawn;
+}
+
+__global__ void k_spawn_segoff(StepParams P)
+{
+    DevState* st = P.st;
+    if (read_error(st)) return;
+    const SRec* __restrict__ sorted = sorted_spawns(P);
     const int64_t S = min(st->spawn_total, P.spawn_cap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.nseg; s += gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = S;
@@ -1137,10 +1427,11 @@ __device__ __forceinline__ int64_t merge_split(const Rec* A, const SRec* B, int6
 
 // Metadata of every merge tile: its slices of N(t) and of the sorted spawns
 // (merge-path splits at both ends) and the key just before it.
-__global__ void k_merge_part(StepParams P, const SRec* __restrict__ sorted)
+__global__ void k_merge_part(StepParams P)
 {
     DevState* st = P.st;
     if (read_error(st)) return;
+    const SRec* __restrict__ sorted = sorted_spawns(P);
     const int cur = st->cur;
     const int64_t T = st->merge_tiles;
     const Rec* A = P.pop[cur];
@@ -1336,7 +1627,7 @@ struct MSlot {
 
 // Warp roles: 0..7 merge, 8 produces (tickets, bulk loads), 9 publishes
 // (look-back, statistics, bulk store of the compacted output).
-__global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const SRec* __restrict__ sorted)
+__global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
 {
     extern __shared__ __align__(128) uint4 msm[];
     uint4* inbuf = msm;                                // [kMergeStages][kMergeTile]
@@ -1352,6 +1643,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P, const 
     if (cta_error(st)) return;
     const int cur = st->cur, nxt = (cur + 1) % 3;
     const int64_t T = st->merge_tiles;
+    const SRec* __restrict__ sorted = sorted_spawns(P);
     const Rec* A = P.pop[cur];
     Rec* out = P.pop[nxt];
     const uint32_t n = (uint32_t)P.n;
@@ -1583,6 +1875,7 @@ __global__ void k_finalize(StepParams P)
         st->acc_knext += carry;
         st->acc_heavy += st->heavy_total;
         st->acc_cand += st->cand_total;
+        if (st->sort_fallback) st->acc_sort_lsd += 1; else st->acc_sort_bucket += 1;
         off[P.nseg] = carry;
         if (st->spawn_total > st->max_spawn) st->max_spawn = st->spawn_total;
         if (st->cand_total > st->max_cand) st->max_cand = st->cand_total;
@@ -1777,12 +2070,13 @@ void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int6
 }
 
 const char* const kKernelNames[kNumTimedKernels] = {
-    "k_prologue", "k_spawn_draw", "k_spawn_choose", "k_spawn_heavy", "k_sort_hist", "k_sort_scatter",
-    "k_spawn_segoff", "k_merge_plan", "k_merge_part", "k_merge", "k_finalize"};
+    "k_prologue",     "k_spawn_draw",  "k_spawn_choose", "k_spawn_heavy", "k_bucket_hist",
+    "k_bucket_scan",  "k_bucket_scatter", "k_bucket_sort", "k_sort_hist",  "k_sort_scatter",
+    "k_spawn_segoff", "k_merge_plan",  "k_merge_part",   "k_merge",       "k_finalize"};
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_choose = 0, g_grid_heavy = 0, g_grid_sort = 0, g_grid_merge = 0;
+int g_grid_spawn = 0, g_grid_choose = 0, g_grid_heavy = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
 
 int resident(const void* fn, int smem, int sms, int threads = kThreads)
 {
@@ -1795,6 +2089,8 @@ int resident(const void* fn, int smem, int sms, int threads = kThreads)
 void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
+    cudaFuncSetAttribute(k_bucket_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSortSmem);
+    cudaFuncSetAttribute(k_bucket_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSortSmem);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1803,6 +2099,8 @@ void configure_kernels()
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms, kMergeThreads);
+    g_grid_bsmall = resident((const void*)k_bucket_sort_small, kSmallSortSmem, sms);
+    g_grid_bbig = resident((const void*)k_bucket_sort_big, kBigSortSmem, sms);
     g_grid_misc = 2 * sms;
 }
 
@@ -1822,9 +2120,28 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(3);
     k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
     mark(4);
+    if (P.sort_mode) {
+        k_bucket_hist<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
+        mark(5);
+        k_bucket_scan<<<((1 << P.bucket_bits) + 1023) / 1024, 1024, 0, stream>>>(P);
+        mark(6);
+        k_bucket_scatter<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
+        mark(7);
+        if (P.sort_mode == 1) {
+            k_bucket_sort_small<<<cap(g_grid_bsmall), kThreads, kSmallSortSmem, stream>>>(P);
+            k_bucket_sort_big<<<cap(g_grid_bbig), kThreads, kBigSortSmem, stream>>>(P);
+        }
+        mark(8);
+    } else {
+        mark(5);
+        mark(6);
+        mark(7);
+        mark(8);
+    }
+    // LSD radix sort: every pass returns at once unless the step sorts this way
     const int np = P.key_passes + P.seg_passes;
     k_sort_hist<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
-    mark(5);
+    mark(9);
     SRec* a = P.spawn;
     SRec* b = P.spawn_alt;
     for (int p = 0; p < np; ++p) {
@@ -1833,18 +2150,17 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
         a = b;
         b = t;
     }
-    mark(6);
-    const SRec* sorted = a;
-    k_spawn_segoff<<<(P.nseg + 1 + kThreads - 1) / kThreads, kThreads, 0, stream>>>(P, sorted);
-    mark(7);
-    k_merge_plan<<<1, 1024, 0, stream>>>(P);
-    mark(8);
-    k_merge_part<<<cap(g_grid_misc), kThreads, 0, stream>>>(P, sorted);
-    mark(9);
-    k_merge<<<cap(g_grid_merge), kMergeThreads, kMergeSmem, stream>>>(P, sorted);
     mark(10);
-    k_finalize<<<1, 1024, 0, stream>>>(P);
+    k_spawn_segoff<<<(P.nseg + 1 + kThreads - 1) / kThreads, kThreads, 0, stream>>>(P);
     mark(11);
+    k_merge_plan<<<1, 1024, 0, stream>>>(P);
+    mark(12);
+    k_merge_part<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
+    mark(13);
+    k_merge<<<cap(g_grid_merge), kMergeThreads, kMergeSmem, stream>>>(P);
+    mark(14);
+    k_finalize<<<1, 1024, 0, stream>>>(P);
+    mark(15);
 }
 
 void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,

@@ -17,8 +17,10 @@ constexpr int kHeavyWalkers = 256;                   // parents above this go to
 constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
 constexpr int kMaxPasses = 12;
+constexpr int kBucketBits = 20;                    // largest bucket digit of the spawn sort
 constexpr int kCtrMerge = kMaxPasses;                // tile counter index of the merge
 constexpr int kCtrSpawn = kMaxPasses + 1;            // tile counter index of the light spawn
+constexpr int kCtrBucket = kMaxPasses + 2;           // tile counter index of the bucket scan
 constexpr uint32_t kTagStep = 0x53544550u;
 constexpr uint32_t kTagInit = 0x494E4954u;
 constexpr uint32_t kKindSpawn = 0u;
@@ -87,14 +89,21 @@ struct StepParams {
     int seg_bits;
     int key_passes;
     int seg_passes;
-    int pad;
+    int sort_mode;        // 0: LSD radix sort; 1: bucket pass + bucket sorts; 2: bucket pass alone
+    int bucket_bits;      // bits of the bucket digit (<= kBucketBits)
+    int bucket_kb;        // key bits in the bucket digit (below all segment bits)
+    int pad2;
+    uint32_t* bucket;     // 2^bucket_bits bucket counters / cursors
+    unsigned long long* bscan_status; // look-back words of the bucket scan, 2^(kBucketBits - 10)
+    uint32_t* win;        // sort window starts, one per kSortWin spawn records
+    uint32_t* big_list;   // sort windows too large for a warp
     uint64_t seed;
     int64_t init_min;
 };
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
 // launch sequence can be captured once in a CUDA graph and replayed.
-constexpr int kNumTimedKernels = 11;
+constexpr int kNumTimedKernels = 15;
 void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);

@@ -97,6 +97,23 @@ StepParams params(qmc_ctx* c)
     P.seg_bits = seg_bits_of(c->cfg.n_segments);
     P.key_passes = (2 * c->cfg.n_qubits + 7) / 8;
     P.seg_passes = (P.seg_bits + 7) / 8;
+    {
+        // bucket digit: every segment bit and the top key bits, sized so that
+        // a full spawn buffer puts about 24 records in a bucket (10 to
+        // kBucketBits bits, never more than the sort key has)
+        const int total = P.seg_bits + 2 * c->cfg.n_qubits;
+        int want = 10;
+        while (want < kBucketBits && ((int64_t)24 << want) < c->spawn_cap) ++want;
+        if (want < P.seg_bits) want = P.seg_bits;
+        P.bucket_bits = total < want ? total : want;
+        P.bucket_kb = P.bucket_bits - P.seg_bits;
+        // (window sorts keep the vector in 20 bits above a 12-bit index, padding at vector 2^20 - 1)
+        P.sort_mode = (P.bucket_bits > kBucketBits || P.seg_bits > 19) ? 0 : (P.bucket_bits == total ? 2 : 1);
+        P.bucket = c->d_bucket;
+        P.bscan_status = c->d_bscan_status;
+        P.win = c->d_win;
+        P.big_list = c->d_big_list;
+    }
     P.seed = c->cfg.seed;
     P.init_min = c->cfg.initiator_min;
     return P;
@@ -126,6 +143,9 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
     int rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn, cap)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn_alt, cap)) != QMC_OK) return rc;
+    // sort windows: one per 224 spawn records (the bucket sort's window length)
+    if ((rc = dalloc(ctx, &ctx->d_win, cap / 224 + 2)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_big_list, cap / 224 + 2)) != QMC_OK) return rc;
     ctx->spawn_cap = cap;
     ctx->sort_tiles_cap = (cap + kSortTile - 1) / kSortTile + 1;
     if ((rc = dalloc(ctx, &ctx->d_sort_status, ctx->sort_tiles_cap * 256)) != QMC_OK) return rc;
@@ -281,6 +301,10 @@ int qmc_create(qmc_ctx** out, const qmc_config* cfg)
         if (cudaMemset(ctx->d_segoff[i], 0, (size_t)(nseg + 1) * 8) != cudaSuccess) return bail(QMC_ERR_CUDA);
     }
     if ((rc = dalloc(ctx, &ctx->d_kd, nseg)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_bucket, (int64_t)1 << kBucketBits)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_bscan_status, (int64_t)1 << (kBucketBits - 10))) != QMC_OK) return bail(rc);
+    if (cudaMemsetAsync(ctx->d_bscan_status, 0, (size_t)8 << (kBucketBits - 10), ctx->work) != cudaSuccess)
+        return bail(QMC_ERR_CUDA);
     if ((rc = dalloc(ctx, &ctx->d_sort_hist, kMaxPasses * 256)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_bseg, nseg + 1)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_tile_start, nseg + 1)) != QMC_OK) return bail(rc);
@@ -303,7 +327,7 @@ void qmc_destroy(qmc_ctx* ctx)
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
-                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_heavy,
+                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
                     ctx->d_progs, ctx->d_obs};
@@ -957,8 +981,10 @@ extern "C" int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out)
     out[5] = hs.acc_knext;
     out[6] = hs.acc_heavy;
     out[7] = hs.acc_cand;
+    out[8] = hs.acc_sort_bucket;
+    out[9] = hs.acc_sort_lsd;
     if (reset) {
-        int64_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int64_t z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, acc_steps), z, sizeof(z),
                            cudaMemcpyHostToDevice, ctx->work));
         CK(cudaStreamSynchronize(ctx->work));

@@ -144,8 +144,12 @@ struct DevState {
     int64_t acc_knext;    // records written to N(t + dt)
     int64_t acc_heavy;    // heavy work items
     int64_t acc_cand;     // spawn candidates
+    int64_t acc_sort_bucket;  // steps whose spawns took the bucket sort
+    int64_t acc_sort_lsd;     // steps whose spawns took the LSD radix sort
     uint32_t seq;         // look-back epoch base, advanced by 16 every step
-    uint32_t pad2;
+    uint32_t sort_fallback;   // 1: this step's spawns take the LSD radix sort
+    uint32_t sort_final;      // 1: the sorted spawns end in the second spawn buffer
+    uint32_t big_windows;     // sort windows listed for the CTA sort
     uint32_t tile_ctr[kMaxTileCounters];
 };
 

@@ -187,6 +187,39 @@ def test_many_tiles_per_cta(max_ctas):
         assert_same(gpu, orc, where=f"many tiles step {k}")
 
 
+def test_spawn_sort_paths():
+    """The spawn sort's two paths, each bit-exact against the oracle: random
+    states (small buckets, bucket sort), and states sharing the top 16 key
+    bits under a large dt, so that one bucket overflows and the step takes
+    the LSD radix sort."""
+    prob = P.ghz_circuit(32)
+    gpu, orc = make_pair(prob, 1, 41, 10**6)
+    cur = _spread_state(32, 1, 12000, 19)
+    prev = _spread_state(32, 1, 11000, 20)
+    _load_state(gpu, orc, cur, prev, 400, 5.1, 0.1)
+    gpu.counters(reset=True)
+    gpu.step(0.1, 1)
+    assert orc.step(0.1, 1) == O.OK
+    assert_same(gpu, orc, where="bucket sort")
+    c = gpu.counters()
+    assert c["sort_bucket_steps"] == 1 and c["sort_lsd_steps"] == 0
+
+    gpu, orc = make_pair(prob, 1, 42, 10**6)
+    top = np.uint64(0xBEEF) << np.uint64(48)
+    low = np.uint64((1 << 48) - 1)
+    packed = []
+    for k, r, i in _spread_state(32, 1, 12000, 21) + _spread_state(32, 1, 11000, 22):
+        k2 = np.unique((k & low) | top)
+        packed.append((k2, r[:len(k2)], i[:len(k2)]))
+    _load_state(gpu, orc, [packed[0]], [packed[1]], 400, 5.1, 0.1)
+    gpu.counters(reset=True)
+    gpu.step(0.1, 1)
+    assert orc.step(0.1, 1) == O.OK
+    assert_same(gpu, orc, where="LSD fallback")
+    c = gpu.counters()
+    assert c["sort_lsd_steps"] == 1 and c["sort_bucket_steps"] == 0
+
+
 def test_heavy_and_light_parents():
     """A state with 1e5 walkers (four heavy chunks) next to light states."""
     prob = P.ghz_circuit(5)
