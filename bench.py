@@ -252,16 +252,21 @@ def measured_traffic(kernel: str, units_launch: float):
 def kernel_bytes(name: str, c: dict) -> float:
     """Algorithmic bytes of a kernel over the counted steps (16-byte records)."""
     r = 16.0
+    lsd = c.get("sort_lsd_steps", 0) / max(1, c["steps"])   # share of steps on the LSD sort
     if name == "k_spawn_draw":     # parents read, candidates written
         return r * (c["k_cur"] + c["k_prev"] + c["candidates"])
     if name == "k_spawn_choose":   # candidates and their parents' keys read, spawn records written
         return (r + 8.0) * c["candidates"] + r * c["spawns"]
     if name == "k_merge":
         return r * (c["k_cur"] + c["spawns"] + c["k_next"])
+    if name == "k_bucket_hist":
+        return r * c["spawns"] * (1.0 - lsd)
+    if name in ("k_bucket_scatter", "k_bucket_sort"):
+        return 2.0 * r * c["spawns"] * (1.0 - lsd)
     if name == "k_sort_scatter":
-        return r * 2.0 * c["spawns"] * c.get("passes", 1)
+        return 2.0 * r * c["spawns"] * c.get("passes", 1) * lsd
     if name == "k_sort_hist":
-        return r * c["spawns"]
+        return r * c["spawns"] * lsd
     return 0.0
 
 
@@ -323,6 +328,7 @@ def run_gpu(args, rank: int, world: int):
     ms = ev0.elapsed_time(ev1)
     c = sim.counters(reset=True)
     walkers = c["walker_steps"]
+    launches_per_step = sim.step_launches()   # the step graph as timed (same buffers)
 
     # per-kernel times over the same timed steps (replayed from the checkpoint)
     roof = None
@@ -386,7 +392,6 @@ def run_gpu(args, rank: int, world: int):
     if rank != 0:
         return
     value = walkers_all / (ms_all * 1e-3)
-    npasses = (2 * prob.n + 7) // 8 + (math.ceil(math.log2(wl["nseg"])) + 7) // 8
     ws = 3 * c["k_next"] / max(1, c["steps"]) * 16 * (world if world > 1 else 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -405,7 +410,7 @@ def run_gpu(args, rank: int, world: int):
                 "d2h_bytes_per_step": e2e["d2h_bytes"] / (W + K), "steps": W + K,
                 "includes": "input upload from pinned host memory, all warm-up and timed steps, "
                             "D2H of per-step observables after every call"},
-        "gpu_launches": int(c["steps"] * (9 + npasses)),
+        "gpu_launches": int(c["steps"] * launches_per_step),
         "clocks": clocks,
     }
     if roof is not None:

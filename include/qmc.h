@@ -182,9 +182,16 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps);
  * replay reproduces the step exactly; a mismatch returns STATE).  Adds the
  * per-kernel milliseconds, summed over the steps, to host kernel_ms[0 .. cap)
  * (zeroed first) and sets *n_kernels; qmc_kernel_name(i) names kernel i.
- * For measurement; slower than qmc_step (one synchronisation per step). */
+ * The replays leave the cumulative counters (qmc_counters) as the steps set
+ * them.  For measurement; slower than qmc_step (one synchronisation per step). */
 int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap,
                      int32_t* n_kernels);
+
+/* Kernel launches of one step as the context would issue it now (host
+ * *launches).  The count depends on n_qubits, n_segments and the current
+ * spawn capacity (which picks the spawn sort); kernels that find no work for
+ * a step still launch and are counted.  Errors: INVALID_ARG. */
+int qmc_step_launches(const qmc_ctx* ctx, int32_t* launches);
 const char* qmc_kernel_name(int32_t i);
 
 /* Upper bound of the spawn probability p over all states for a step of size

@@ -2163,6 +2163,15 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(15);
 }
 
+int step_launch_count(const StepParams& P)
+{
+    const int np = P.key_passes + P.seg_passes;
+    const int bucket = P.sort_mode == 0 ? 0 : (P.sort_mode == 1 ? 5 : 3);
+    // prologue, draw, choose, heavy; bucket sort; LSD histogram and passes;
+    // segment offsets, merge plan, partition, merge, finalize
+    return 4 + bucket + 1 + np + 5;
+}
+
 void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,
                  int64_t nnz, int64_t n_diag, int64_t* tmp_vals, cudaStream_t stream)
 {

@@ -107,6 +107,7 @@ constexpr int kNumTimedKernels = 15;
 void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+int step_launch_count(const StepParams& P);   // kernels launch_step issues
 void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg, int n,
                  Rec* dst, int* bad, cudaStream_t stream);
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);

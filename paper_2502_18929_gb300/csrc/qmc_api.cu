@@ -947,6 +947,12 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
             rc = fail(ctx, QMC_ERR_STATE, "profiled replay of a step did not reproduce it");
             break;
         }
+        // the replay is a measurement, not a step: the cumulative counters keep
+        // the values of the step it repeated
+        const size_t acc0 = offsetof(DevState, acc_steps), acc1 = offsetof(DevState, acc_sort_lsd) + 8;
+        CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + acc0, (const uint8_t*)&hs + acc0, acc1 - acc0,
+                           cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
         for (int i = 0; i < kNumTimedKernels && i < cap; ++i) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
@@ -955,6 +961,13 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
     }
     for (int i = 0; i <= kNumTimedKernels; ++i) cudaEventDestroy(ev[i]);
     return rc;
+}
+
+int qmc_step_launches(const qmc_ctx* ctx, int32_t* launches)
+{
+    if (!ctx || !launches) return QMC_ERR_INVALID_ARG;
+    *launches = step_launch_count(params(const_cast<qmc_ctx*>(ctx)));
+    return QMC_OK;
 }
 
 const char* qmc_kernel_name(int32_t i)

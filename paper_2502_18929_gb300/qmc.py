@@ -35,6 +35,7 @@ EXPORTED = [
     "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
+    "qmc_step_launches",
 ]
 
 
@@ -115,6 +116,7 @@ def lib():
         L.qmc_restore.argtypes = [vp, C.c_char_p]
         L.qmc_step_profile.argtypes = [vp, C.c_double, C.c_int64, vp, C.c_int32, vp]
         L.qmc_counters.argtypes = [vp, C.c_int32, vp]
+        L.qmc_step_launches.argtypes = [vp, vp]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
@@ -258,6 +260,12 @@ class QMC:
         names = ["steps", "walker_steps", "k_cur", "k_prev", "spawns", "k_next", "heavy_items", "candidates",
                  "sort_bucket_steps", "sort_lsd_steps"]
         return {k: int(v) for k, v in zip(names, out)}
+
+    def step_launches(self) -> int:
+        """Kernel launches of one step as the context would issue it now."""
+        n = C.c_int32()
+        self._check(self.L.qmc_step_launches(self.h, C.byref(n)), "qmc_step_launches")
+        return n.value
 
     def spawn_prob_bound(self, t: float, dt: float) -> float:
         p = C.c_double()
