@@ -26,6 +26,16 @@ QMC_HD inline int qmc_popc(uint32_t v)
 
 QMC_HD inline int64_t qmc_iabs64(int64_t v) { return v < 0 ? -v : v; }
 
+// Index of the lowest set bit (v != 0).
+QMC_HD inline int qmc_ctz(uint32_t v)
+{
+#ifdef __CUDA_ARCH__
+    return __ffs(v) - 1;
+#else
+    return __builtin_ctz(v);
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Column program access
 // ---------------------------------------------------------------------------
@@ -38,6 +48,7 @@ struct Prog {
     const GTerm* gt;
     const Entry* ent;
     const AffGroup* aff;
+    const Run* run;
 };
 
 QMC_HD inline Prog prog_at(const uint8_t* base)
@@ -51,6 +62,7 @@ QMC_HD inline Prog prog_at(const uint8_t* base)
     p.gt = (const GTerm*)(base + p.h->off_gterm);
     p.ent = (const Entry*)(base + p.h->off_entry);
     p.aff = (const AffGroup*)(base + p.h->off_aff);
+    p.run = (const Run*)(base + p.h->off_run);
     return p;
 }
 
@@ -120,6 +132,57 @@ QMC_HD inline void entry_value(const Prog& p, const Entry& e, uint32_t x, uint32
     } else {
         gen_value(p, (int)e.idx, x, y, vr, vi);
     }
+}
+
+// Destination of a walker with T < P: walking the column in canonical order
+// (ascending mask, Re before Im within a destination), the (mask, channel)
+// whose cumulative-weight interval holds T, and its value.  A family run is
+// skipped whole by its summed weight (member weights depend on x_q, y_q
+// only); inside the run members are visited in ascending q.  Returns false
+// if T lies beyond the column (T >= P).
+QMC_HD inline bool choose_destination(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim, int64_t T,
+                                      uint64_t* mask, int* chan, int64_t* v)
+{
+    const int nr = p.h->n_run;
+    for (int r = 0; r < nr; ++r) {
+        const Run R = p.run[r];
+        if (R.kind != 1u) {
+            const Entry E = p.ent[R.idx];
+            int64_t vr, vi;
+            entry_value(p, E, x, y, sre, sim, &vr, &vi);
+            const int64_t wr = qmc_iabs64(vr);
+            if (T < wr) { *mask = E.mask_key; *chan = 0; *v = vr; return true; }
+            T -= wr;
+            const int64_t wi = qmc_iabs64(vi);
+            if (T < wi) { *mask = E.mask_key; *chan = 1; *v = vi; return true; }
+            T -= wi;
+            continue;
+        }
+        const Fam& f = p.fam[R.idx];
+        const uint32_t M = R.members;
+        const uint32_t m3 = x & y & M, m2 = x & ~y & M, m1 = ~x & y & M, m0 = ~x & ~y & M;
+        const int64_t W = f.a[3] * qmc_popc(m3) + f.a[2] * qmc_popc(m2) + f.a[1] * qmc_popc(m1) +
+                          f.a[0] * qmc_popc(m0);
+        if (T >= W) {
+            T -= W;
+            continue;
+        }
+        uint32_t nz = (f.a[3] ? m3 : 0u) | (f.a[2] ? m2 : 0u) | (f.a[1] ? m1 : 0u) | (f.a[0] ? m0 : 0u);
+        while (nz) {
+            const int q = qmc_ctz(nz);
+            nz &= nz - 1u;
+            const int pi = (int)((((x >> q) & 1u) << 1) | ((y >> q) & 1u));
+            const int64_t wr = qmc_iabs64(f.tre[pi]);
+            const uint64_t mk = ((uint64_t)((f.ab >> 1) & 1u) << (q + (int)R.shift)) | ((uint64_t)(f.ab & 1u) << q);
+            if (T < wr) { *mask = mk; *chan = 0; *v = f.tre[pi]; return true; }
+            T -= wr;
+            const int64_t wi = qmc_iabs64(f.tim[pi]);
+            if (T < wi) { *mask = mk; *chan = 1; *v = f.tim[pi]; return true; }
+            T -= wi;
+        }
+        return false;
+    }
+    return false;
 }
 
 } // namespace qmc

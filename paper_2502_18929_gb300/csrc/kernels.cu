@@ -310,26 +310,6 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st, uint32_t
     return false;
 }
 
-// Destination (entry, channel) holding T, found by walking the column in
-// canonical order.
-__device__ __forceinline__ bool lane_choose(const Prog& p, uint32_t x, uint32_t y, int64_t sre, int64_t sim,
-                                            int64_t T, uint64_t* mask, int* chan, int64_t* v)
-{
-    const int ne = p.h->n_entry;
-    for (int e = 0; e < ne; ++e) {
-        const Entry E = p.ent[e];
-        int64_t vr, vi;
-        entry_value(p, E, x, y, sre, sim, &vr, &vi);
-        const int64_t wr = iabs64(vr);
-        if (T < wr) { *mask = E.mask_key; *chan = 0; *v = vr; return true; }
-        T -= wr;
-        const int64_t wi = iabs64(vi);
-        if (T < wi) { *mask = E.mask_key; *chan = 1; *v = vi; return true; }
-        T -= wi;
-    }
-    return false;
-}
-
 constexpr int kCandStage = 128;   // candidates staged per warp
 constexpr int kCandFlush = 64;    // a warp flushes once more than this are staged
 constexpr uint64_t kT52 = (1ull << 52) - 1ull;
@@ -732,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
                 uint64_t mk;
                 int chan;
                 int64_t v;
-                ok = lane_choose(prog, x, y, sre, sim, T, &mk, &chan, &v);
+                ok = choose_destination(prog, x, y, sre, sim, T, &mk, &chan, &v);
                 if (ok) rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
                 else set_error(st, DERR_TILE_CAPACITY);
             }

@@ -39,6 +39,7 @@ struct ProgHeader {
     int32_t n_selffam, n_selfgen, n_fam, n_gen, n_gterm, n_entry;
     int32_t off_selffam, off_selfgen, off_fam, off_gen, off_gterm, off_entry;
     int32_t n_aff, off_aff;
+    int32_t n_run, off_run;
     int64_t p_bound;                      // >= P of every state (filter for the spawn test)
     int64_t self_const_re, self_const_im; // parity-free part of the diagonal element
     int64_t p_const;                      // sum of |Re| + |Im| over constant groups
@@ -101,6 +102,17 @@ struct Entry {
     uint64_t mask_key;
     uint32_t kind;
     uint32_t idx;
+};
+
+// The entries as runs: a run of consecutive members of one family (ascending
+// q, kind 1: idx = family, members = their q bits), or a single entry of
+// kind 0 or 2 (idx = its entry index).  The destination choice walks runs and
+// skips a family run by its summed weight.
+struct Run {
+    uint32_t kind;
+    uint32_t idx;
+    uint32_t members;
+    uint32_t shift;   // family runs: n (a member's ket bit is q + n)
 };
 
 // ---- device-resident step state ---------------------------------------------

@@ -397,6 +397,22 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     std::sort(entries.begin(), entries.end(),
               [](const Entry& a, const Entry& b) { return a.mask_key < b.mask_key; });
 
+    // runs of consecutive members of one family (see Run)
+    std::vector<Run> runs;
+    for (size_t e = 0; e < entries.size(); ++e) {
+        const Entry& E = entries[e];
+        if (E.kind == 1u) {
+            const uint32_t f = E.idx & 0xFFFFu, q = E.idx >> 16;
+            if (!runs.empty() && runs.back().kind == 1u && runs.back().idx == f) {
+                runs.back().members |= 1u << q;
+                continue;
+            }
+            runs.push_back(Run{1u, f, 1u << q, (uint32_t)n});
+        } else {
+            runs.push_back(Run{E.kind, (uint32_t)e, 0u, 0u});
+        }
+    }
+
     hdr.n_selffam = (int32_t)selffam.size();
     hdr.n_selfgen = (int32_t)selfgen.size();
     hdr.n_fam = (int32_t)fams.size();
@@ -414,6 +430,8 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     hdr.off_entry = (int32_t)off;   off = align8(off + entries.size() * sizeof(Entry));
     hdr.off_aff = (int32_t)off;     off = align8(off + affs.size() * sizeof(AffGroup));
     hdr.n_aff = (int32_t)affs.size();
+    hdr.off_run = (int32_t)off;     off = align8(off + runs.size() * sizeof(Run));
+    hdr.n_run = (int32_t)runs.size();
     hdr.bytes = (int32_t)off;
     blob->resize(base + off, 0);
     put(blob, base, &hdr, 1);
@@ -424,6 +442,7 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     put(blob, base + hdr.off_gterm, gterms.data(), gterms.size());
     put(blob, base + hdr.off_entry, entries.data(), entries.size());
     put(blob, base + hdr.off_aff, affs.data(), affs.size());
+    put(blob, base + hdr.off_run, runs.data(), runs.size());
     return QMC_OK;
 }
 
