@@ -118,6 +118,45 @@ typedef struct {
  * OOM, CUDA. */
 int qmc_create(qmc_ctx** out, const qmc_config* cfg);
 
+/* One problem instance of a batch: its own qubit count, population vectors,
+ * seed, N^diag, initiator threshold and schedule (the arrays have the meaning
+ * of qmc_load_schedule's; borrowed for the call only). */
+typedef struct {
+    int32_t n_qubits;       /* 1..32                                           */
+    int32_t n_vectors;      /* >= 1                                            */
+    uint64_t seed;
+    int64_t n_diag;         /* >= 1                                            */
+    int64_t initiator_min;  /* 0 = off                                         */
+    const qmc_ham_term* ham;
+    int32_t n_ham;
+    int32_t n_lind;
+    const qmc_lindblad* lind;
+    const qmc_pauli_coef* coefs;
+    int32_t n_coefs;
+    int32_t n_rates;
+    const qmc_rate* rates;
+    const qmc_window* windows;
+    int32_t n_windows;
+    int32_t pad;
+} qmc_instance;
+
+/* Batched step (no counterpart in the paper; its vectors are independent by
+ * Eq. (3), so independent problems can share every launch).  Create one
+ * context for n_instances problem instances: instance i's vectors are the
+ * segments [sum_{j<i} n_vectors_j, ... + n_vectors_i) of every per-vector
+ * call (observables, export, overlap, history).  A vector draws exactly the
+ * random numbers it would draw in a context of its instance alone made by
+ * qmc_create with the same seed (its index inside the instance keys the
+ * stream), so each instance's populations are bit-identical to such a run.
+ * All instances share dt, the clock and integrator, capacity_hint,
+ * max_records, max_ctas and cuda_stream from cfg (cfg's n_qubits,
+ * n_segments, seed, n_diag and initiator_min are ignored).
+ * qmc_init_populations gives every instance the same rho(0) (its (x, y)
+ * must fit the smallest instance); qmc_load_schedule is refused (STATE).
+ * Errors: INVALID_ARG (an instance out of range, a schedule that does not
+ * validate, more than 2^28 vectors), OOM, CUDA. */
+int qmc_batch_create(qmc_ctx** out, const qmc_instance* inst, int32_t n_instances, const qmc_config* cfg);
+
 /* Free all device and host memory of the context (NULL is a no-op). */
 void qmc_destroy(qmc_ctx* ctx);
 

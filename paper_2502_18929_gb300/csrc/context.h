@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/qmc.h"
 #include "kernels.h"
@@ -28,9 +29,20 @@ struct qmc_ctx {
     int sm_count = 0;
     int grid = 0;
 
-    Schedule sched;
-    bool has_sched = false;
+    // Problem instances: one for a context made by qmc_create, several for
+    // qmc_batch_create.  Instance i owns segments [seg0, seg0 + nvec).
+    struct Instance {
+        Schedule sched;
+        bool has_sched = false;
+        int32_t n = 0, nvec = 0, seg0 = 0;
+        uint64_t seed = 0;
+        int64_t n_diag = 0, init_min = 0;
+    };
+    std::vector<Instance> inst;
+    bool batch = false;
     bool has_pop = false;
+    qmc::SegInfo* d_seginfo = nullptr;
+    qmc::InstInfo* d_inst = nullptr;
 
     DevState* d_state = nullptr;
     Rec* d_pop[3] = {nullptr, nullptr, nullptr};

@@ -191,8 +191,10 @@ __global__ void k_prologue(StepParams P)
     if (read_error(st)) return;
     const uint64_t step = st->step;
     for (int s = threadIdx.x; s < P.nseg; s += blockDim.x) {
-        uint4 o = philox10(make_uint4((uint32_t)step, (uint32_t)(step >> 32), (uint32_t)s, kTagStep),
-                           make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+        const SegInfo si = P.seginfo[s];
+        const uint64_t seed = P.inst[si.inst].seed;
+        uint4 o = philox10(make_uint4((uint32_t)step, (uint32_t)(step >> 32), (uint32_t)si.vec, kTagStep),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
         P.kd[s] = make_uint2(o.x, o.y);
         P.segacc[s] = SegStats{0ull, 0ll, 0ll, 0ll};
     }
@@ -387,6 +389,37 @@ __device__ void emit_heavy(const StepParams& P, int64_t parent, int phase, int s
     }
 }
 
+// Column program of one instance for one pass of the current step.
+__device__ __forceinline__ const uint8_t* prog_ptr(const StepParams& P, const StepInfo& inf, int inst, int phase)
+{
+    const int64_t* tab = (const int64_t*)(P.progs + inf.tab_off);
+    return P.progs + tab[2 * inst + phase];
+}
+
+// Draw parameters of one vector in one pass of the current step: its Philox
+// key, bound << 12 on the raw draw (all: every walker is a candidate, the
+// bound having reached 2^52), and its instance's initiator threshold.
+struct SegDraw {
+    uint64_t b12;
+    int64_t init_min;
+    uint2 kd;
+    bool all;
+};
+
+__device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo& inf, int seg, int phase)
+{
+    const SegInfo si = P.seginfo[seg];
+    const int64_t pb = ((const ProgHeader*)prog_ptr(P, inf, si.inst, phase))->p_bound;
+    SegDraw d;
+    d.all = pb >= (1ll << 52);
+    d.b12 = d.all ? ~0ull : (uint64_t)pb << 12;
+    d.init_min = P.inst[si.inst].init_min;
+    d.kd = P.kd[seg];
+    return d;
+}
+
+__device__ __forceinline__ bool below(const SegDraw& d, uint64_t X) { return d.all || X < d.b12; }
+
 // Flags of a candidate: comp, phase, noninit, sign of the parent component.
 __device__ __forceinline__ uint64_t cand_flags(int comp, int phase, int noninit, int32_t val)
 {
@@ -398,14 +431,14 @@ __device__ __forceinline__ uint64_t cand_flags(int comp, int phase, int noninit,
 // one walker pair, and heavy parents (emitted as heavy work items).  All pairs
 // of the group are spread evenly over the lanes.
 __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCand* stage, int* staged, bool valid,
-                                                Rec par, uint32_t j, int phase, int seg, uint2 kd, uint64_t bnd,
+                                                Rec par, uint32_t j, int phase, int seg, const SegDraw& sd,
                                                 int lane)
 {
     const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
     const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
     const uint64_t mtot = (uint64_t)are + aim;
     const bool heavy = mtot > (uint64_t)kHeavyWalkers;
-    const int noninit = (P.init_min > 0 && (int64_t)mtot < P.init_min) ? 1 : 0;
+    const int noninit = (sd.init_min > 0 && (int64_t)mtot < sd.init_min) ? 1 : 0;
     if (heavy) emit_heavy(P, j, phase, seg, are, aim);
     const uint32_t pre = heavy ? 0u : (are + 1u) >> 1, pim = heavy ? 0u : (aim + 1u) >> 1;
     const int my_pairs = (int)(pre + pim);
@@ -438,7 +471,10 @@ __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCan
         const int32_t o_re = __shfl_sync(kFull, par.re, owner);
         const int32_t o_im = __shfl_sync(kFull, par.im, owner);
         const uint32_t o_j = __shfl_sync(kFull, j, owner);
-        const uint2 o_kd = make_uint2(__shfl_sync(kFull, kd.x, owner), __shfl_sync(kFull, kd.y, owner));
+        SegDraw od;
+        od.kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
+        od.b12 = __shfl_sync(kFull, sd.b12, owner);
+        od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
         bool c0 = false, c1 = false;
         uint64_t t0 = 0, t1 = 0;
         if (act) {
@@ -448,14 +484,14 @@ __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCan
             const uint4 w = philox10(
                 make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
                            (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                o_kd);
-            const uint64_t R0 = (((uint64_t)w.y << 32) | w.x) >> 12;
-            const uint64_t R1 = (((uint64_t)w.w << 32) | w.z) >> 12;
+                od.kd);
+            const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
+            const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
             const uint64_t fl = cand_flags(comp, phase, o_non, comp ? o_im : o_re);
-            c0 = R0 < bnd;
-            c1 = 2u * (uint32_t)j2 + 1u < m && R1 < bnd;
-            t0 = R0 | fl;
-            t1 = R1 | fl;
+            c0 = below(od, X0);
+            c1 = 2u * (uint32_t)j2 + 1u < m && below(od, X1);
+            t0 = (X0 >> 12) | fl;
+            t1 = (X1 >> 12) | fl;
         }
         cand_push(stage, staged, c0, c1, o_j, (uint32_t)o_seg, t0, t1, P, lane);
     }
@@ -467,9 +503,9 @@ constexpr int kPairRing = 128;
 constexpr int kDrawChunk = 64;    // parents per staged chunk (1 KB)
 constexpr int kDrawStages = 4;    // staged chunks per warp
 
-__device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand* stage, int* staged,
-                                                  const uint2* ring, int head, int cnt, const Rec* src, int phase,
-                                                  bool all_cand, uint64_t b12, int lane)
+__device__ __forceinline__ void draw_second_pairs(const StepParams& P, const StepInfo& inf, SpawnCand* stage,
+                                                  int* staged, const uint2* ring, int head, int cnt, const Rec* src,
+                                                  int phase, int lane)
 {
     bool c0 = false, c1 = false;
     uint64_t t0 = 0, t1 = 0;
@@ -485,14 +521,15 @@ __device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand
         const uint32_t comp = are >= 3u ? 0u : 1u;
         const uint32_t j2 = are >= 3u ? 1u : (aim >= 3u && are == 0u ? 1u : 0u);
         const uint32_t m = comp ? aim : are;
+        const SegDraw sd = seg_draw(P, inf, (int)it.y, phase);
         const uint4 w = philox10(make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
                                             (uint32_t)phase | (comp << 1) | (kKindSpawn << 2), j2),
-                                 P.kd[it.y]);
+                                 sd.kd);
         const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
         const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
-        c0 = all_cand || X0 < b12;
-        c1 = 2u * j2 + 1u < m && (all_cand || X1 < b12);
-        const int noninit = (P.init_min > 0 && (int64_t)((uint64_t)are + aim) < P.init_min) ? 1 : 0;
+        c0 = below(sd, X0);
+        c1 = 2u * j2 + 1u < m && below(sd, X1);
+        const int noninit = (sd.init_min > 0 && (int64_t)((uint64_t)are + aim) < sd.init_min) ? 1 : 0;
         const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
         t0 = (X0 >> 12) | fl;
         t1 = (X1 >> 12) | fl;
@@ -510,17 +547,17 @@ __device__ __forceinline__ void draw_second_pairs(const StepParams& P, SpawnCand
 // or heavy parents, takes the general path.
 __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint2* ring,
                                           Rec* buf, uint64_t* bar, uint32_t* chunk_no, const Rec* src,
-                                          const int64_t* off, int64_t wb, int64_t we, int phase, uint64_t bound,
+                                          const int64_t* off, int64_t wb, int64_t we, int phase, const StepInfo& inf,
                                           int lane)
 {
-    // bound = 2^52 (every walker a candidate): X < 2^64 always holds
-    const bool all_cand = bound >= (1ull << 52);
-    const uint64_t b12 = all_cand ? ~0ull : bound << 12;
-    const bool init_rule = P.init_min > 0;
     const uint32_t lt = (1u << lane) - 1u;
     int seg = 0;
     int64_t seg_end = -1;
-    uint2 kd = make_uint2(0u, 0u);
+    SegDraw sd;   // draw parameters of the lane's current vector
+    sd.b12 = 0ull;
+    sd.init_min = 0;
+    sd.kd = make_uint2(0u, 0u);
+    sd.all = false;
     int head = 0, cnt = 0;   // ring of queued second pairs
     // chunks of kDrawChunk parents staged by bulk copies, kDrawStages - 1 ahead;
     // the warp's c-th chunk overall uses stage c % kDrawStages
@@ -554,14 +591,14 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         if (vA && iA >= seg_end) {
             seg = seg_of(off, P.nseg, iA);
             seg_end = __ldg(&off[seg + 1]);
-            kd = P.kd[seg];
+            sd = seg_draw(P, inf, seg, phase);
         }
         const int segA = seg;
-        const uint2 kdA = kd;
+        const SegDraw sdA = sd;
         if (vB && iB >= seg_end) {
             seg = seg_of(off, P.nseg, iB);
             seg_end = __ldg(&off[seg + 1]);
-            kd = P.kd[seg];
+            sd = seg_draw(P, inf, seg, phase);
         }
         const uint32_t areA = vA ? (pA.re < 0 ? 0u - (uint32_t)pA.re : (uint32_t)pA.re) : 0u;
         const uint32_t aimA = vA ? (pA.im < 0 ? 0u - (uint32_t)pA.im : (uint32_t)pA.im) : 0u;
@@ -570,8 +607,8 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         const uint32_t prA = ((areA + 1u) >> 1) + ((aimA + 1u) >> 1);
         const uint32_t prB = ((areB + 1u) >> 1) + ((aimB + 1u) >> 1);
         if (!__all_sync(kFull, (areA | aimA | areB | aimB) <= 4u && prA <= 2u && prB <= 2u)) {
-            draw_group_general(P, stage, staged, vA, pA, (uint32_t)iA, phase, segA, kdA, bound, lane);
-            draw_group_general(P, stage, staged, vB, pB, (uint32_t)iB, phase, seg, kd, bound, lane);
+            draw_group_general(P, stage, staged, vA, pA, (uint32_t)iA, phase, segA, sdA, lane);
+            draw_group_general(P, stage, staged, vB, pB, (uint32_t)iB, phase, seg, sd, lane);
             continue;
         }
         // queue the second pairs
@@ -584,7 +621,7 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
             cnt += __popc(btA) + __popc(btB);
             __syncwarp();
             while (cnt >= 32) {
-                draw_second_pairs(P, stage, staged, ring, head, 32, src, phase, all_cand, b12, lane);
+                draw_second_pairs(P, inf, stage, staged, ring, head, 32, src, phase, lane);
                 head = (head + 32) & (kPairRing - 1);
                 cnt -= 32;
                 __syncwarp();
@@ -595,28 +632,28 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         const uint32_t mA = compA ? aimA : areA, mB = compB ? aimB : areB;
         const uint4 wA = philox10(make_uint4((uint32_t)pA.key, (uint32_t)(pA.key >> 32),
                                              (uint32_t)phase | (compA << 1) | (kKindSpawn << 2), 0u),
-                                  kdA);
+                                  sdA.kd);
         const uint4 wB = philox10(make_uint4((uint32_t)pB.key, (uint32_t)(pB.key >> 32),
                                              (uint32_t)phase | (compB << 1) | (kKindSpawn << 2), 0u),
-                                  kd);
+                                  sd.kd);
         const uint64_t XA0 = ((uint64_t)wA.y << 32) | wA.x, XA1 = ((uint64_t)wA.w << 32) | wA.z;
         const uint64_t XB0 = ((uint64_t)wB.y << 32) | wB.x, XB1 = ((uint64_t)wB.w << 32) | wB.z;
-        const bool cA0 = mA != 0u && (all_cand || XA0 < b12), cA1 = mA >= 2u && (all_cand || XA1 < b12);
-        const bool cB0 = mB != 0u && (all_cand || XB0 < b12), cB1 = mB >= 2u && (all_cand || XB1 < b12);
+        const bool cA0 = mA != 0u && below(sdA, XA0), cA1 = mA >= 2u && below(sdA, XA1);
+        const bool cB0 = mB != 0u && below(sd, XB0), cB1 = mB >= 2u && below(sd, XB1);
         if (__any_sync(kFull, cA0 || cA1)) {
-            const int non = (init_rule && (int64_t)((uint64_t)areA + aimA) < P.init_min) ? 1 : 0;
+            const int non = (sdA.init_min > 0 && (int64_t)((uint64_t)areA + aimA) < sdA.init_min) ? 1 : 0;
             const uint64_t fl = cand_flags((int)compA, phase, non, compA ? pA.im : pA.re);
             cand_push(stage, staged, cA0, cA1, (uint32_t)iA, (uint32_t)segA, (XA0 >> 12) | fl, (XA1 >> 12) | fl, P,
                       lane);
         }
         if (__any_sync(kFull, cB0 || cB1)) {
-            const int non = (init_rule && (int64_t)((uint64_t)areB + aimB) < P.init_min) ? 1 : 0;
+            const int non = (sd.init_min > 0 && (int64_t)((uint64_t)areB + aimB) < sd.init_min) ? 1 : 0;
             const uint64_t fl = cand_flags((int)compB, phase, non, compB ? pB.im : pB.re);
             cand_push(stage, staged, cB0, cB1, (uint32_t)iB, (uint32_t)seg, (XB0 >> 12) | fl, (XB1 >> 12) | fl, P,
                       lane);
         }
     }
-    if (cnt > 0) draw_second_pairs(P, stage, staged, ring, head, cnt, src, phase, all_cand, b12, lane);
+    if (cnt > 0) draw_second_pairs(P, inf, stage, staged, ring, head, cnt, src, phase, lane);
     if (gave_up) {
         // a copy may still be landing in the last stages: wait for them once more (bounded)
         for (int64_t j = nch > kDrawStages ? nch - kDrawStages : 0; j < nch; ++j) {
@@ -648,11 +685,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
     uint32_t chunk_no = 0;
     const StepInfo inf = P.info[st->call_index];
     const int cur = st->cur, prv = (cur + 2) % 3;
-    // filter: a walker can only spawn if T < P <= p_bound (every walker is a
-    // candidate when the bound reaches 2^52, so p >= 1 is still detected)
-    const int64_t lim52 = 1ll << 52;
-    const int64_t pb0 = ((const ProgHeader*)(P.progs + inf.prog_off[0]))->p_bound;
-    const int64_t pb1 = ((const ProgHeader*)(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0])))->p_bound;
+    // filter: a walker can only spawn if T < P <= p_bound of its instance's
+    // program (every walker is a candidate when the bound reaches 2^52, so
+    // p >= 1 is still detected); see seg_draw
     const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
     const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
     int staged = 0;
@@ -662,9 +697,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
         // each warp owns one contiguous range of the slot, a multiple of 64
         const int64_t chunk = ((K + nwarps - 1) / nwarps + 63) / 64 * 64;
         const int64_t wb = min(K, gw * chunk), we = min(K, wb + chunk);
-        const int64_t pb = phase ? pb1 : pb0;
         draw_slot(P, stage, &staged, sring[warp], sbuf[warp], sbar[warp], &chunk_no, P.pop[slot], P.segoff[slot],
-                  wb, we, phase, (uint64_t)(pb >= lim52 ? lim52 : pb), lane);
+                  wb, we, phase, inf, lane);
     }
     if (staged) cand_flush(stage, staged, P, lane);
 }
@@ -682,12 +716,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
     const int cur = st->cur, prv = (cur + 2) % 3;
     const Rec* src0 = P.pop[cur];
     const Rec* src1 = P.pop[prv];
-    const uint8_t* pb0 = stage_prog(P.progs + inf.prog_off[0], sprog[0]);
-    const uint8_t* pb1 = stage_prog(P.progs + (inf.ab2 ? inf.prog_off[1] : inf.prog_off[0]), sprog[1]);
+    // one instance: its two programs staged in shared memory; several: each
+    // candidate reads its instance's program from global memory (L2-resident)
+    const bool single = P.ninst == 1;
+    const uint8_t* pb0 = single ? stage_prog(prog_ptr(P, inf, 0, 0), sprog[0]) : nullptr;
+    const uint8_t* pb1 = single ? stage_prog(prog_ptr(P, inf, 0, inf.ab2 ? 1 : 0), sprog[1]) : nullptr;
     __syncthreads();   // programs staged
     const int64_t total = min(st->cand_total, P.cand_cap);
-    const int n = P.n;
-    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     SRec* stage = sstage[warp];
     int staged = 0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -702,8 +737,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
             const int non = (int)((tf >> 54) & 1u), sg = ((tf >> 55) & 1u) ? 1 : -1;
             const int64_t T = (int64_t)(tf & kT52);
             const uint64_t key = __ldg(&(phase ? src1 : src0)[cv.x].key);
-            const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & ymask);
-            const Prog prog = prog_at(phase ? pb1 : pb0);
+            const SegInfo si = P.seginfo[cv.y];
+            const int n = si.n;
+            const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & (n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)));
+            const Prog prog = prog_at(single ? (phase ? pb1 : pb0) : prog_ptr(P, inf, si.inst, phase));
             int64_t sre, sim;
             const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
             if (Pw >= (1ll << 52)) {
@@ -752,13 +789,14 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
     const int ci = st->call_index;
     const StepInfo inf = P.info[ci];
     const int cur = st->cur, prv = (cur + 2) % 3;
-    const int n = P.n;
-    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const HeavyItem it = P.heavy[item];
-        const Prog prog = prog_at(P.progs + inf.prog_off[it.phase]);
+        const SegInfo si = P.seginfo[it.seg];
+        const int n = si.n;
+        const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+        const Prog prog = prog_at(prog_ptr(P, inf, si.inst, it.phase));
         const Rec par = (it.phase ? P.pop[prv] : P.pop[cur])[it.parent];
         const uint32_t x = (uint32_t)(par.key >> n), y = (uint32_t)(par.key & ymask);
         int64_t sre, sim;
@@ -833,7 +871,8 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         // emit one record per nonzero (destination, channel)
         const int sg = (comp ? par.im : par.re) > 0 ? 1 : -1;
         const int sigma = it.phase ? -1 : 1;
-        const int noninit = (P.init_min > 0 && (iabs64(par.re) + iabs64(par.im)) < P.init_min) ? 1 : 0;
+        const int64_t init_min = P.inst[si.inst].init_min;
+        const int noninit = (init_min > 0 && (iabs64(par.re) + iabs64(par.im)) < init_min) ? 1 : 0;
         int my_n = 0;
         for (int b = tid; b < nb; b += kThreads) my_n += hist[b] ? 1 : 0;
         int my_off = 0;
@@ -1626,8 +1665,6 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
     const SRec* __restrict__ sorted = sorted_spawns(P);
     const Rec* A = P.pop[cur];
     Rec* out = P.pop[nxt];
-    const uint32_t n = (uint32_t)P.n;
-    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kMergeWarps = kThreads / 32;
     if (tid == 0) {
@@ -1743,6 +1780,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
         if (t < T) {
             const MTileG m = meta[s];
             seg = m.seg;
+            const uint32_t n = (uint32_t)P.seginfo[seg].n;   // the tile's vector's qubit count
+            const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
             nout = merge_walk(inbuf + s * kMergeTile, m, sorted, raw + tid * kMergeItems, st, n, ymask, &my_ntot,
                               &my_dre, &my_dim);
         }
@@ -1871,18 +1910,27 @@ __global__ void k_finalize(StepParams P)
 // Initial populations: N(0) = N^diag rho(0), stochastic rounding per
 // component with the kind-1 stream of each segment.
 // ---------------------------------------------------------------------------
-__global__ void k_init_values(StepParams P, const uint64_t* __restrict__ keys, const double* __restrict__ re,
-                              const double* __restrict__ im, int64_t nnz, int64_t n_diag,
+// Key of element (x, y) of rho(0) in a vector of n qubits.
+__device__ __forceinline__ uint64_t init_key(const uint64_t* x, const uint64_t* y, int64_t e, int n)
+{
+    return (x[e] << n) | y[e];
+}
+
+__global__ void k_init_values(StepParams P, const uint64_t* __restrict__ xs, const uint64_t* __restrict__ ys,
+                              const double* __restrict__ re, const double* __restrict__ im, int64_t nnz,
                               int64_t* __restrict__ vals)
 {
     const int64_t total = nnz * P.nseg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(i / nnz);
         const int64_t e = i - (int64_t)s * nnz;
-        const uint4 kk = philox10(make_uint4(0u, 0u, (uint32_t)s, kTagInit),
-                                  make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+        const SegInfo si = P.seginfo[s];
+        const InstInfo in = P.inst[si.inst];
+        const int64_t n_diag = in.n_diag;
+        const uint4 kk = philox10(make_uint4(0u, 0u, (uint32_t)si.vec, kTagInit),
+                                  make_uint2((uint32_t)in.seed, (uint32_t)(in.seed >> 32)));
         const uint2 kd = make_uint2(kk.x, kk.y);
-        const uint64_t key = keys[e];
+        const uint64_t key = init_key(xs, ys, e, si.n);
         for (int comp = 0; comp < 2; ++comp) {
             const double v = __dmul_rn((double)n_diag, comp ? im[e] : re[e]);
             const double fl = floor(v);
@@ -1902,8 +1950,8 @@ __global__ void k_init_values(StepParams P, const uint64_t* __restrict__ keys, c
 }
 
 // Compact nonzero values per segment into slot 'cur' (single CTA, in order).
-__global__ void k_init_compact(StepParams P, const uint64_t* __restrict__ keys, int64_t nnz,
-                               const int64_t* __restrict__ vals)
+__global__ void k_init_compact(StepParams P, const uint64_t* __restrict__ xs, const uint64_t* __restrict__ ys,
+                               int64_t nnz, const int64_t* __restrict__ vals)
 {
     __shared__ int s_cnt[kThreads];
     DevState* st = P.st;
@@ -1929,7 +1977,7 @@ __global__ void k_init_compact(StepParams P, const uint64_t* __restrict__ keys, 
             const int excl = s_cnt[tid] - (keep ? 1 : 0);
             const int blk = s_cnt[kThreads - 1];
             if (keep && pos + excl < P.pop_cap)
-                dst[pos + excl] = Rec{keys[e], (int32_t)vals[2 * i], (int32_t)vals[2 * i + 1]};
+                dst[pos + excl] = Rec{init_key(xs, ys, e, P.seginfo[s].n), (int32_t)vals[2 * i], (int32_t)vals[2 * i + 1]};
             pos += blk;
             __syncthreads();
         }
@@ -1951,8 +1999,8 @@ __global__ void k_obs(StepParams P, int which, SegStats* __restrict__ out)
     const Rec* pop = P.pop[slot];
     const int64_t* off = P.segoff[slot];
     const int64_t K = off[P.nseg];
-    const int n = P.n;
-    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    int n = 32;
+    uint32_t ymask = 0xFFFFFFFFu;
     const int64_t per = (K + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(K, b0 + per);
     int cs = -1;
@@ -1971,6 +2019,8 @@ __global__ void k_obs(StepParams P, int which, SegStats* __restrict__ out)
             flush();
             cs = seg_of(off, P.nseg, i);
             cs_end = off[cs + 1];
+            n = P.seginfo[cs].n;
+            ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
             c = 0;
             ntot = dre = dim = 0;
         }
@@ -2010,20 +2060,18 @@ __global__ void k_lookup(StepParams P, int seg, const uint64_t* __restrict__ q, 
 // them: keys ascending within each vector, below 2^(2n), values nonzero and not
 // -2^31.  A violation sets *bad (the caller rejects the call).
 __global__ void k_pack_records(const uint64_t* __restrict__ keys, const int32_t* __restrict__ re,
-                               const int32_t* __restrict__ im, const int64_t* __restrict__ off, int nseg, int n,
-                               Rec* __restrict__ dst, int* bad)
+                               const int32_t* __restrict__ im, const int64_t* __restrict__ off, int nseg,
+                               const SegInfo* __restrict__ seginfo, Rec* __restrict__ dst, int* bad)
 {
     const int64_t K = off[nseg];
-    const uint64_t lim = n == 32 ? ~0ull : ((1ull << (2 * n)) - 1ull);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = keys[i];
         const int32_t a = re[i], b = im[i];
+        const int s = seg_of(off, nseg, i);
+        const int n = seginfo[s].n;
+        const uint64_t lim = n == 32 ? ~0ull : ((1ull << (2 * n)) - 1ull);
         bool ok = (key & ~lim) == 0 && (a != 0 || b != 0) && a != INT32_MIN && b != INT32_MIN;
-        if (ok && i > 0 && keys[i - 1] >= key) {
-            // a new vector may start at i
-            const int s = seg_of(off, nseg, i);
-            if (off[s] != i) ok = false;
-        }
+        if (ok && i > 0 && keys[i - 1] >= key && off[s] != i) ok = false;   // sorted inside each vector
         if (!ok) atomicExch(bad, 1);
         dst[i] = Rec{key, a, b};
     }
@@ -2031,10 +2079,11 @@ __global__ void k_pack_records(const uint64_t* __restrict__ keys, const int32_t*
 
 } // namespace
 
-void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg, int n,
-                 Rec* dst, int* bad, cudaStream_t stream)
+void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg,
+                 const SegInfo* seginfo, Rec* dst, int* bad, cudaStream_t stream)
 {
-    k_pack_records<<<g_grid_misc ? g_grid_misc : 304, kThreads, 0, stream>>>(keys, re, im, off, nseg, n, dst, bad);
+    k_pack_records<<<g_grid_misc ? g_grid_misc : 304, kThreads, 0, stream>>>(keys, re, im, off, nseg, seginfo, dst,
+                                                                             bad);
 }
 
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream)
@@ -2152,13 +2201,13 @@ int step_launch_count(const StepParams& P)
     return 4 + bucket + 1 + np + 5;
 }
 
-void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,
-                 int64_t nnz, int64_t n_diag, int64_t* tmp_vals, cudaStream_t stream)
+void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,
+                 int64_t nnz, int64_t* tmp_vals, cudaStream_t stream)
 {
     const int64_t total = nnz * P.nseg;
     const int blocks = (int)((total + kThreads - 1) / kThreads < 4096 ? (total + kThreads - 1) / kThreads : 4096);
-    k_init_values<<<blocks > 0 ? blocks : 1, kThreads, 0, stream>>>(P, keys, re, im, nnz, n_diag, tmp_vals);
-    k_init_compact<<<1, kThreads, 0, stream>>>(P, keys, nnz, tmp_vals);
+    k_init_values<<<blocks > 0 ? blocks : 1, kThreads, 0, stream>>>(P, x, y, re, im, nnz, tmp_vals);
+    k_init_compact<<<1, kThreads, 0, stream>>>(P, x, y, nnz, tmp_vals);
 }
 
 } // namespace qmc

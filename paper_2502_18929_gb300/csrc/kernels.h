@@ -84,7 +84,7 @@ struct StepParams {
     SegStats* segacc;     // per-segment accumulators of the merge
     SegStats* history;    // [steps of call][nseg]
     int64_t history_cap;  // steps
-    int n;
+    int n;                // largest qubit count of the instances (key width of the sorts)
     int nseg;
     int seg_bits;
     int key_passes;
@@ -97,8 +97,10 @@ struct StepParams {
     unsigned long long* bscan_status; // look-back words of the bucket scan, 2^(kBucketBits - 10)
     uint32_t* win;        // sort window starts, one per kSortWin spawn records
     uint32_t* big_list;   // sort windows too large for a warp
-    uint64_t seed;
-    int64_t init_min;
+    const SegInfo* seginfo;   // per segment
+    const InstInfo* inst;     // per instance
+    int ninst;
+    int pad3;
 };
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
@@ -108,11 +110,11 @@ void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int step_launch_count(const StepParams& P);   // kernels launch_step issues
-void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg, int n,
-                 Rec* dst, int* bad, cudaStream_t stream);
+void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg,
+                 const SegInfo* seginfo, Rec* dst, int* bad, cudaStream_t stream);
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);
 void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int64_t* out, cudaStream_t stream);
-void launch_init(const StepParams& P, const uint64_t* keys, const double* re, const double* im,
-                 int64_t nnz, int64_t n_diag, int64_t* tmp_vals, cudaStream_t stream);
+void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,
+                 int64_t nnz, int64_t* tmp_vals, cudaStream_t stream);
 
 } // namespace qmc

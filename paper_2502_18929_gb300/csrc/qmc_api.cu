@@ -61,6 +61,44 @@ int seg_bits_of(int nseg)
     return b;
 }
 
+// Hash of the problem(s) and configuration a checkpoint belongs to.
+uint64_t context_hash(const qmc_ctx* c)
+{
+    if (!c->batch) {
+        const qmc_ctx::Instance& I = c->inst[0];
+        return schedule_hash(I.sched, I.seed, I.nvec, c->cfg.integrator, I.n_diag, I.init_min);
+    }
+    uint64_t h = 1469598103934665603ull;
+    for (const auto& I : c->inst) {
+        const uint64_t v[2] = {schedule_hash(I.sched, I.seed, I.nvec, c->cfg.integrator, I.n_diag, I.init_min),
+                               (uint64_t)I.n};
+        const uint8_t* b = (const uint8_t*)v;
+        for (size_t i = 0; i < sizeof(v); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+    return h;
+}
+
+// The instance that owns segment seg.
+const qmc_ctx::Instance& instance_of(const qmc_ctx* c, int seg)
+{
+    size_t lo = 0, hi = c->inst.size() - 1;
+    while (lo < hi) {
+        const size_t mid = (lo + hi + 1) / 2;
+        if (c->inst[mid].seg0 <= seg) lo = mid; else hi = mid - 1;
+    }
+    return c->inst[lo];
+}
+
+bool has_schedules(const qmc_ctx* c)
+{
+    for (const auto& I : c->inst)
+        if (!I.has_sched) return false;
+    return true;
+}
+
 StepParams params(qmc_ctx* c)
 {
     StepParams P;
@@ -114,8 +152,9 @@ StepParams params(qmc_ctx* c)
         P.win = c->d_win;
         P.big_list = c->d_big_list;
     }
-    P.seed = c->cfg.seed;
-    P.init_min = c->cfg.initiator_min;
+    P.seginfo = c->d_seginfo;
+    P.inst = c->d_inst;
+    P.ninst = (int)c->inst.size();
     return P;
 }
 
@@ -275,15 +314,18 @@ int clear_dev_error(qmc_ctx* ctx)
 
 extern "C" {
 
-int qmc_create(qmc_ctx** out, const qmc_config* cfg)
+} // extern "C"
+
+namespace {
+
+// Shared by qmc_create and qmc_batch_create: cfg carries the totals
+// (n_qubits = largest instance, n_segments = all vectors); inst the instances.
+int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::Instance>&& inst, bool batch)
 {
-    if (!out || !cfg) return QMC_ERR_INVALID_ARG;
-    if (cfg->n_qubits < 1 || cfg->n_qubits > 32 || cfg->n_segments < 1 || cfg->n_diag < 1 ||
-        cfg->n_segments > (1 << 28) || (cfg->integrator != QMC_EULER && cfg->integrator != QMC_AB2) ||
-        cfg->initiator_min < 0)
-        return QMC_ERR_INVALID_ARG;
     qmc_ctx* ctx = new qmc_ctx();
     ctx->cfg = *cfg;
+    ctx->inst = std::move(inst);
+    ctx->batch = batch;
     ctx->user_stream = (cudaStream_t)cfg->cuda_stream;
     int rc = QMC_OK;
     auto bail = [&](int code) { qmc_destroy(ctx); return code; };
@@ -316,9 +358,89 @@ int qmc_create(qmc_ctx** out, const qmc_config* cfg)
     if ((rc = grow_spawn(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
     if ((rc = grow_cand(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
     if ((rc = grow_pop(ctx, hint)) != QMC_OK) return bail(rc);
+    {
+        // segment and instance tables
+        std::vector<SegInfo> si(nseg);
+        std::vector<InstInfo> ii(ctx->inst.size());
+        for (size_t i = 0; i < ctx->inst.size(); ++i) {
+            const qmc_ctx::Instance& I = ctx->inst[i];
+            ii[i] = InstInfo{I.seed, I.n_diag, I.init_min, I.n, I.nvec};
+            for (int v = 0; v < I.nvec; ++v) si[I.seg0 + v] = SegInfo{(int32_t)i, I.n, v, 0};
+        }
+        if ((rc = dalloc(ctx, &ctx->d_seginfo, nseg)) != QMC_OK) return bail(rc);
+        if ((rc = dalloc(ctx, &ctx->d_inst, (int64_t)ii.size())) != QMC_OK) return bail(rc);
+        if (cudaMemcpy(ctx->d_seginfo, si.data(), si.size() * sizeof(SegInfo), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->d_inst, ii.data(), ii.size() * sizeof(InstInfo), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(QMC_ERR_CUDA);
+    }
     if (cudaStreamSynchronize(ctx->work) != cudaSuccess) return bail(QMC_ERR_CUDA);
     *out = ctx;
     return QMC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int qmc_create(qmc_ctx** out, const qmc_config* cfg)
+{
+    if (!out || !cfg) return QMC_ERR_INVALID_ARG;
+    if (cfg->n_qubits < 1 || cfg->n_qubits > 32 || cfg->n_segments < 1 || cfg->n_diag < 1 ||
+        cfg->n_segments > (1 << 28) || (cfg->integrator != QMC_EULER && cfg->integrator != QMC_AB2) ||
+        cfg->initiator_min < 0)
+        return QMC_ERR_INVALID_ARG;
+    std::vector<qmc_ctx::Instance> inst(1);
+    inst[0].n = cfg->n_qubits;
+    inst[0].nvec = cfg->n_segments;
+    inst[0].seg0 = 0;
+    inst[0].seed = cfg->seed;
+    inst[0].n_diag = cfg->n_diag;
+    inst[0].init_min = cfg->initiator_min;
+    return create_context(out, cfg, std::move(inst), false);
+}
+
+int qmc_batch_create(qmc_ctx** out, const qmc_instance* inst, int32_t n_instances, const qmc_config* cfg)
+{
+    if (!out || !inst || !cfg || n_instances < 1) return QMC_ERR_INVALID_ARG;
+    if (cfg->integrator != QMC_EULER && cfg->integrator != QMC_AB2) return QMC_ERR_INVALID_ARG;
+    std::vector<qmc_ctx::Instance> v((size_t)n_instances);
+    int64_t nseg = 0;
+    int nmax = 0;
+    for (int i = 0; i < n_instances; ++i) {
+        const qmc_instance& q = inst[i];
+        if (q.n_qubits < 1 || q.n_qubits > 32 || q.n_vectors < 1 || q.n_diag < 1 || q.initiator_min < 0)
+            return QMC_ERR_INVALID_ARG;
+        if (q.n_ham < 0 || q.n_lind < 0 || q.n_coefs < 0 || q.n_rates < 0 || q.n_windows < 0 ||
+            (q.n_ham && !q.ham) || (q.n_lind && !q.lind) || (q.n_coefs && !q.coefs) || (q.n_rates && !q.rates) ||
+            (q.n_windows && !q.windows))
+            return QMC_ERR_INVALID_ARG;
+        qmc_ctx::Instance& I = v[i];
+        I.n = q.n_qubits;
+        I.nvec = q.n_vectors;
+        I.seg0 = (int32_t)nseg;
+        I.seed = q.seed;
+        I.n_diag = q.n_diag;
+        I.init_min = q.initiator_min;
+        I.sched.n = q.n_qubits;
+        I.sched.ham.assign(q.ham, q.ham + q.n_ham);
+        I.sched.lind.assign(q.lind, q.lind + q.n_lind);
+        I.sched.coefs.assign(q.coefs, q.coefs + q.n_coefs);
+        I.sched.rates.assign(q.rates, q.rates + q.n_rates);
+        I.sched.windows.assign(q.windows, q.windows + q.n_windows);
+        std::string why;
+        if (validate_schedule(I.sched, &why) != QMC_OK) return QMC_ERR_INVALID_ARG;
+        I.has_sched = true;
+        nseg += q.n_vectors;
+        nmax = std::max(nmax, q.n_qubits);
+        if (nseg > (1 << 28)) return QMC_ERR_INVALID_ARG;
+    }
+    qmc_config c = *cfg;
+    c.n_qubits = nmax;
+    c.n_segments = (int32_t)nseg;
+    c.seed = 0;
+    c.n_diag = 1;
+    c.initiator_min = 0;
+    return create_context(out, &c, std::move(v), true);
 }
 
 void qmc_destroy(qmc_ctx* ctx)
@@ -330,7 +452,7 @@ void qmc_destroy(qmc_ctx* ctx)
                     ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
-                    ctx->d_progs, ctx->d_obs};
+                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
@@ -349,6 +471,7 @@ int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, cons
                       int32_t n_rates, const qmc_window* windows, int32_t n_windows)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (ctx->batch) return fail(ctx, QMC_ERR_STATE, "a batch takes its schedules at qmc_batch_create");
     if (n_ham < 0 || n_lind < 0 || n_coefs < 0 || n_rates < 0 || n_windows < 0)
         return fail(ctx, QMC_ERR_INVALID_ARG, "negative array length");
     Schedule s;
@@ -360,8 +483,8 @@ int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, cons
     if (n_windows) s.windows.assign(windows, windows + n_windows);
     std::string why;
     if (validate_schedule(s, &why) != QMC_OK) return fail(ctx, QMC_ERR_INVALID_ARG, why);
-    ctx->sched = s;
-    ctx->has_sched = true;
+    ctx->inst[0].sched = s;
+    ctx->inst[0].has_sched = true;
     return QMC_OK;
 }
 
@@ -369,22 +492,26 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
                          const double* im, int64_t nnz)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
-    if (!ctx->has_sched) return fail(ctx, QMC_ERR_STATE, "load a schedule first");
+    if (!has_schedules(ctx)) return fail(ctx, QMC_ERR_STATE, "load a schedule first");
     if (nnz < 0 || (nnz > 0 && (!x || !y || !re || !im))) return fail(ctx, QMC_ERR_INVALID_ARG, "bad arrays");
-    const int n = ctx->cfg.n_qubits;
-    const uint64_t lim = (1ull << n) - 1;
-    std::vector<std::pair<uint64_t, int64_t>> order;
+    // every instance takes the same rho(0); (x, y) must fit the smallest one
+    int nmin = 32;
+    for (const auto& I : ctx->inst) nmin = std::min(nmin, (int)I.n);
+    const uint64_t lim = (1ull << nmin) - 1;
+    std::vector<std::pair<std::pair<uint64_t, uint64_t>, int64_t>> order;
     for (int64_t i = 0; i < nnz; ++i) {
         if ((x[i] & ~lim) || (y[i] & ~lim)) return fail(ctx, QMC_ERR_INVALID_ARG, "x or y >= 2^n");
-        order.push_back({(x[i] << n) | y[i], i});
+        order.push_back({{x[i], y[i]}, i});
     }
+    // (x, y) lexicographic = key order (x << n) | y for every n that holds them
     std::sort(order.begin(), order.end());
     for (size_t i = 1; i < order.size(); ++i)
         if (order[i].first == order[i - 1].first) return fail(ctx, QMC_ERR_INVALID_ARG, "duplicate (x, y)");
-    std::vector<uint64_t> keys(nnz);
+    std::vector<uint64_t> hx(nnz), hy(nnz);
     std::vector<double> hre(nnz), him(nnz);
     for (int64_t i = 0; i < nnz; ++i) {
-        keys[i] = order[i].first;
+        hx[i] = order[i].first.first;
+        hy[i] = order[i].first.second;
         hre[i] = re[order[i].second];
         him[i] = im[order[i].second];
     }
@@ -392,10 +519,11 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     const int64_t need = std::max<int64_t>(1, nnz) * ctx->cfg.n_segments;
     if (need > ctx->pop_cap && (rc = grow_pop(ctx, need)) != QMC_OK) return rc;
-    uint64_t* d_keys = nullptr;
+    uint64_t *d_x = nullptr, *d_y = nullptr;
     double *d_re = nullptr, *d_im = nullptr;
     int64_t* d_vals = nullptr;
-    if ((rc = dalloc(ctx, &d_keys, nnz)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_x, nnz)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &d_y, nnz)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &d_re, nnz)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &d_im, nnz)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &d_vals, 2 * need)) != QMC_OK) return rc;
@@ -403,17 +531,19 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
     std::memset(&hs, 0, sizeof(hs));
     CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
     if (nnz) {
-        CK(cudaMemcpyAsync(d_keys, keys.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_x, hx.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_y, hy.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
         CK(cudaMemcpyAsync(d_re, hre.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
         CK(cudaMemcpyAsync(d_im, him.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
     }
     StepParams P = params(ctx);
-    launch_init(P, d_keys, d_re, d_im, nnz, ctx->cfg.n_diag, d_vals, ctx->work);
+    launch_init(P, d_x, d_y, d_re, d_im, nnz, d_vals, ctx->work);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(ctx->d_segoff[2], 0, (size_t)(ctx->cfg.n_segments + 1) * 8, ctx->work));
     CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
-    cudaFree(d_keys);
+    cudaFree(d_x);
+    cudaFree(d_y);
     cudaFree(d_re);
     cudaFree(d_im);
     cudaFree(d_vals);
@@ -463,7 +593,7 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
         CK(cudaMemcpyAsync(d_im, im, total * 4, cudaMemcpyHostToDevice, ctx->work));
     }
     CK(cudaMemcpyAsync(ctx->d_segoff[slot], off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
-    if (total) launch_pack(d_keys, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->cfg.n_qubits, ctx->d_pop[slot], d_bad,
+    if (total) launch_pack(d_keys, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->d_seginfo, ctx->d_pop[slot], d_bad,
                            ctx->work);
     CK(cudaGetLastError());
     int bad = 0;
@@ -521,42 +651,49 @@ int qmc_get_clock(const qmc_ctx* ctx, uint64_t* step, double* t, double* t_prev,
 
 int qmc_spawn_prob_bound(const qmc_ctx* ctx, double t, double dt, double* p_bound)
 {
-    if (!ctx || !p_bound || !ctx->has_sched) return QMC_ERR_INVALID_ARG;
-    *p_bound = spawn_prob_bound(ctx->sched, t, dt * 1.5);
+    if (!ctx || !p_bound || !has_schedules(ctx)) return QMC_ERR_INVALID_ARG;
+    double b = 0.0;
+    for (const auto& I : ctx->inst) b = std::max(b, spawn_prob_bound(I.sched, t, dt * 1.5));
+    *p_bound = b;
     return QMC_OK;
 }
 
 int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
-    if (!ctx->has_sched || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
     if (!(dt > 0.0) || nsteps < 0) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 0");
     if (nsteps == 0) return QMC_OK;
-    // per-step column programs (identical consecutive programs are shared)
+    // per-step column programs of every instance (identical consecutive
+    // programs of an instance and pass are shared), and per step a table of
+    // their offsets
+    const int ni = (int)ctx->inst.size();
     std::vector<StepInfo> info(nsteps);
     std::vector<uint8_t> blob;
     std::vector<uint8_t> tmp;
-    int64_t last_off[2] = {-1, -1};
-    std::vector<uint8_t> last_blob[2];
-    auto add_prog = [&](int pass, double tt, double dte, int64_t* off_out) -> int {
+    std::vector<int64_t> last_off(2 * (size_t)ni, -1);
+    std::vector<std::vector<uint8_t>> last_blob(2 * (size_t)ni);
+    auto add_prog = [&](int k, int pass, double tt, double dte, int64_t* off_out) -> int {
         tmp.clear();
-        int rc = build_program(ctx->sched, tt, dte, &tmp);
+        int rc = build_program(ctx->inst[k].sched, tt, dte, &tmp);
         if (rc != QMC_OK) return rc;
         const ProgHeader* h = (const ProgHeader*)tmp.data();
         if (h->n_entry > kMaxEntries)
             return fail(ctx, QMC_ERR_INVALID_ARG, "column has more destinations than the heavy path holds");
-        if (last_off[pass] >= 0 && last_blob[pass] == tmp) {
-            *off_out = last_off[pass];
+        const size_t slot = 2 * (size_t)k + pass;
+        if (last_off[slot] >= 0 && last_blob[slot] == tmp) {
+            *off_out = last_off[slot];
             return QMC_OK;
         }
         const size_t at = (blob.size() + 15) & ~(size_t)15;
         blob.resize(at);
         blob.insert(blob.end(), tmp.begin(), tmp.end());
-        last_blob[pass] = tmp;
-        last_off[pass] = (int64_t)at;
+        last_blob[slot] = tmp;
+        last_off[slot] = (int64_t)at;
         *off_out = (int64_t)at;
         return QMC_OK;
     };
+    std::vector<int64_t> tab(2 * (size_t)ni);
     const double t0 = ctx->t;
     for (int64_t i = 0; i < nsteps; ++i) {
         const double ti = t0 + (double)i * dt;
@@ -564,13 +701,19 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
                          (i > 0 || (ctx->prev_valid && ctx->dt_last == dt));
         const double tp = i > 0 ? t0 + (double)(i - 1) * dt : ctx->t_prev;
         info[i].ab2 = ab2 ? 1 : 0;
-        info[i].prog_off[1] = -1;
-        int rc = add_prog(0, ti, ab2 ? dt * 1.5 : dt, &info[i].prog_off[0]);
-        if (rc == QMC_OK && ab2) rc = add_prog(1, tp, dt * 0.5, &info[i].prog_off[1]);
-        if (rc != QMC_OK) {
-            if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
-            return rc;
+        for (int k = 0; k < ni; ++k) {
+            int rc = add_prog(k, 0, ti, ab2 ? dt * 1.5 : dt, &tab[2 * k]);
+            tab[2 * k + 1] = tab[2 * k];
+            if (rc == QMC_OK && ab2) rc = add_prog(k, 1, tp, dt * 0.5, &tab[2 * k + 1]);
+            if (rc != QMC_OK) {
+                if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
+                return rc;
+            }
         }
+        const size_t at = (blob.size() + 15) & ~(size_t)15;
+        blob.resize(at + tab.size() * sizeof(int64_t));
+        std::memcpy(blob.data() + at, tab.data(), tab.size() * sizeof(int64_t));
+        info[i].tab_off = (int64_t)at;
     }
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
@@ -742,7 +885,7 @@ int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* ps
                 int32_t len, double* out_re, double* out_im)
 {
     if (!ctx || seg < 0 || seg >= ctx->cfg.n_segments || len < 0 || !out_re || !out_im) return QMC_ERR_INVALID_ARG;
-    const int n = ctx->cfg.n_qubits;
+    const int n = instance_of(ctx, seg).n;
     const int nq = len * len;
     std::vector<uint64_t> q(nq > 0 ? nq : 1);
     for (int a = 0; a < len; ++a)
@@ -794,8 +937,7 @@ int qmc_checkpoint(qmc_ctx* ctx, const char* path)
     std::memcpy(h.magic, "QMCCKPT1", 8);
     h.version = 1;
     h.n_qubits = ctx->cfg.n_qubits;
-    h.hash = schedule_hash(ctx->sched, ctx->cfg.seed, nseg, ctx->cfg.integrator, ctx->cfg.n_diag,
-                           ctx->cfg.initiator_min);
+    h.hash = context_hash(ctx);
     h.step = ctx->step;
     h.t = ctx->t;
     h.t_prev = ctx->t_prev;
@@ -839,7 +981,7 @@ int qmc_checkpoint(qmc_ctx* ctx, const char* path)
 int qmc_restore(qmc_ctx* ctx, const char* path)
 {
     if (!ctx || !path) return QMC_ERR_INVALID_ARG;
-    if (!ctx->has_sched) return fail(ctx, QMC_ERR_STATE, "load the same schedule before restoring");
+    if (!has_schedules(ctx)) return fail(ctx, QMC_ERR_STATE, "load the same schedule before restoring");
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(ctx, QMC_ERR_IO, std::string("cannot open ") + path);
     CkptHeader h;
@@ -849,8 +991,7 @@ int qmc_restore(qmc_ctx* ctx, const char* path)
         std::fclose(f);
         return fail(ctx, QMC_ERR_CHECKPOINT, "not a checkpoint of this library");
     }
-    const uint64_t hash = schedule_hash(ctx->sched, ctx->cfg.seed, nseg, ctx->cfg.integrator, ctx->cfg.n_diag,
-                                        ctx->cfg.initiator_min);
+    const uint64_t hash = context_hash(ctx);
     if (h.hash != hash || h.nseg != nseg || h.n_qubits != ctx->cfg.n_qubits || h.count[0] < 0 || h.count[1] < 0 ||
         h.count[0] > ((int64_t)1 << 34) || h.count[1] > ((int64_t)1 << 34)) {
         std::fclose(f);
@@ -915,7 +1056,7 @@ extern "C" {
 int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap, int32_t* n_kernels)
 {
     if (!ctx || !kernel_ms || !n_kernels || cap < 0) return QMC_ERR_INVALID_ARG;
-    if (!ctx->has_sched || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
     if (!(dt > 0.0) || nsteps < 1) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 1");
     *n_kernels = kNumTimedKernels;
     for (int i = 0; i < cap && i < kNumTimedKernels; ++i) kernel_ms[i] = 0.0;

@@ -167,9 +167,29 @@ struct DevState {
 
 // Per-step flags prepared by the host for each step of a call.
 struct StepInfo {
-    int64_t prog_off[2];  // byte offset of the pass-0 / pass-1 program, -1 if absent
+    int64_t tab_off;      // byte offset of int64[instances][2]: each instance's pass-0 / pass-1
+                          // program offset (pass 1 repeats pass 0 when absent)
     int32_t ab2;          // 1: AB2 step (pass 1 over N(t - dt) present)
     int32_t pad;
+};
+
+// Per population vector (segment): its problem instance, that instance's
+// qubit count, and the vector's index inside the instance (which keys its
+// random stream, so an instance run alone or in a batch draws the same).
+struct SegInfo {
+    int32_t inst;
+    int32_t n;
+    int32_t vec;
+    int32_t pad;
+};
+
+// Per problem instance.
+struct InstInfo {
+    uint64_t seed;
+    int64_t n_diag;
+    int64_t init_min;   // initiator threshold in walkers (0: off)
+    int32_t n;
+    int32_t nvec;
 };
 
 } // namespace qmc

@@ -35,7 +35,7 @@ EXPORTED = [
     "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
-    "qmc_step_launches",
+    "qmc_step_launches", "qmc_batch_create",
 ]
 
 
@@ -117,6 +117,7 @@ def lib():
         L.qmc_step_profile.argtypes = [vp, C.c_double, C.c_int64, vp, C.c_int32, vp]
         L.qmc_counters.argtypes = [vp, C.c_int32, vp]
         L.qmc_step_launches.argtypes = [vp, vp]
+        L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
@@ -144,6 +145,28 @@ def current_stream_handle() -> int:
     except Exception:
         pass
     return 0
+
+
+class Instance(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_vectors", C.c_int32), ("seed", C.c_uint64), ("n_diag", C.c_int64),
+                ("initiator_min", C.c_int64), ("ham", C.c_void_p), ("n_ham", C.c_int32), ("n_lind", C.c_int32),
+                ("lind", C.c_void_p), ("coefs", C.c_void_p), ("n_coefs", C.c_int32), ("n_rates", C.c_int32),
+                ("rates", C.c_void_p), ("windows", C.c_void_p), ("n_windows", C.c_int32), ("pad", C.c_int32)]
+
+
+def _schedule_arrays(prob):
+    """ctypes arrays of a problem's schedule (kept alive by the caller)."""
+    ham = (HamTerm * max(1, len(prob.ham)))(*[HamTerm(h, xm, zm, r, w) for h, xm, zm, r, w in prob.ham])
+    coefs, linds = [], []
+    for ops, r, w in prob.lind:
+        linds.append(Lindblad(len(coefs), len(ops), r, w))
+        for coef, xm, zm in ops:
+            coefs.append(PauliCoef(coef.real, coef.imag, xm, zm))
+    lind = (Lindblad * max(1, len(linds)))(*linds)
+    cf = (PauliCoef * max(1, len(coefs)))(*coefs)
+    rates = (Rate * max(1, len(prob.rates)))(*[Rate(k, 0, a, b, c) for k, a, b, c in prob.rates])
+    wins = (Window * max(1, len(prob.windows)))(*[Window(a, b) for a, b in prob.windows])
+    return ham, len(prob.ham), lind, len(linds), cf, len(coefs), rates, len(prob.rates), wins, len(prob.windows)
 
 
 class QMC:
@@ -180,20 +203,39 @@ class QMC:
             pass
 
     # -- problem -------------------------------------------------------------
+    @classmethod
+    def batch(cls, problems, n_vectors, seeds, n_diags, integrator: int = AB2, initiator_mins=None,
+              capacity_hint: int = 0, max_records: int = 0, stream: int | None = None, max_ctas: int = 0):
+        """One context stepping several problem instances (qmc_batch_create):
+        instance i's vectors are segments offsets[i] .. offsets[i + 1]."""
+        self = cls.__new__(cls)
+        self.L = lib()
+        k = len(problems)
+        mins = initiator_mins if initiator_mins is not None else [0] * k
+        keep, arr = [], (Instance * k)()
+        for i, prob in enumerate(problems):
+            a = _schedule_arrays(prob)
+            keep.append(a)
+            ham, nh, lind, nl, cf, nc, rates, nr, wins, nw = a
+            arr[i] = Instance(prob.n, int(n_vectors[i]), int(seeds[i]), int(n_diags[i]), int(mins[i]),
+                              C.cast(ham, C.c_void_p), nh, nl, C.cast(lind, C.c_void_p), C.cast(cf, C.c_void_p),
+                              nc, nr, C.cast(rates, C.c_void_p), C.cast(wins, C.c_void_p), nw, 0)
+        cfg = Config(max(p.n for p in problems), int(sum(n_vectors)), integrator, max_ctas, 0, 1, 0, capacity_hint,
+                     max_records, C.c_void_p(current_stream_handle() if stream is None else stream))
+        h = C.c_void_p()
+        rc = self.L.qmc_batch_create(C.byref(h), arr, k, C.byref(cfg))
+        if rc != OK:
+            raise QmcError(rc, "qmc_batch_create failed")
+        self.h = h
+        self.n = cfg.n_qubits
+        self.nseg = cfg.n_segments
+        self.n_diag = None
+        self.offsets = np.concatenate([[0], np.cumsum(n_vectors)]).astype(np.int64)
+        return self
+
     def load_schedule(self, prob):
-        ham = (HamTerm * max(1, len(prob.ham)))(*[HamTerm(h, xm, zm, r, w) for h, xm, zm, r, w in prob.ham])
-        coefs, linds = [], []
-        for ops, r, w in prob.lind:
-            linds.append(Lindblad(len(coefs), len(ops), r, w))
-            for coef, xm, zm in ops:
-                coefs.append(PauliCoef(coef.real, coef.imag, xm, zm))
-        lind = (Lindblad * max(1, len(linds)))(*linds)
-        cf = (PauliCoef * max(1, len(coefs)))(*coefs)
-        rates = (Rate * max(1, len(prob.rates)))(*[Rate(k, 0, a, b, c) for k, a, b, c in prob.rates])
-        wins = (Window * max(1, len(prob.windows)))(*[Window(a, b) for a, b in prob.windows])
-        self._check(self.L.qmc_load_schedule(self.h, ham, len(prob.ham), lind, len(linds), cf, len(coefs),
-                                             rates, len(prob.rates), wins, len(prob.windows)),
-                    "qmc_load_schedule")
+        a = _schedule_arrays(prob)
+        self._check(self.L.qmc_load_schedule(self.h, *a), "qmc_load_schedule")
 
     def init_populations(self, rho0):
         x = _arr([e[0] for e in rho0], np.uint64)
