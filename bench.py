@@ -1,7 +1,7 @@
 """Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload spread32|spread32s|dd12|ghz4|ghzN|ghzNi]
+                    [--workload spread32|spread32s|dd12|ghz4|ghzN|ghzNi|batch256]
 
 One "step" is one dt step of every population vector through the whole hot
 path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
@@ -421,6 +421,103 @@ def run_gpu(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------------------
+# Batched step: many independent problem instances in one context
+# ---------------------------------------------------------------------------
+def batch_instances(k: int = 256, seed: int = 0):
+    """GHZ circuits, n ~ U{4..16}, amplitude damping and dephasing at
+    gamma0 cos(omega t) with gamma0 ~ U[0.01, 0.05], omega ~ U[0.5, 2],
+    N^diag log-uniform in [1e4, 1e6], one vector each."""
+    rng = np.random.default_rng(seed)
+    probs, ndiag, seeds = [], [], []
+    for i in range(k):
+        n = int(rng.integers(4, 17))
+        g0 = float(rng.uniform(0.01, 0.05))
+        om = float(rng.uniform(0.5, 2.0))
+        probs.append(P.ghz_circuit(n, gamma1=g0, gamma_phi=g0, rate_kind=P.RATE_COS, omega1=om, omega_phi=om))
+        ndiag.append(int(10 ** rng.uniform(4.0, 6.0)))
+        seeds.append(7 * i + 1)
+    return probs, ndiag, seeds
+
+
+def run_batch(args, rank: int, world: int):
+    """256 instances stepped by one context (qmc_batch_create), against the
+    same instances stepped one context each, one after the other.  Both start
+    from |0><0| and pre-roll 100 steps (t = 1, the end of the Hadamard pulse)
+    untimed; then W warm-up and K timed steps of dt = 0.01."""
+    import torch
+    from paper_2502_18929_gb300 import qmc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+    probs, ndiag, seeds = batch_instances(256, rank)
+    k = len(probs)
+    dt, pre, W = 0.01, 100, max(3, args.warmup)
+    K = args.steps if args.steps > 0 else 20
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(sim, nsteps):
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        ev0.record(stream)
+        sim.step(dt, nsteps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), time.perf_counter() - h0
+
+    batch = qmc.QMC.batch(probs, [1] * k, seeds, ndiag, stream=stream.cuda_stream)
+    batch.init_populations(P.rho_basis(0))
+    batch.step(dt, pre + W)
+    batch.counters(reset=True)
+    sampler = ClockSampler(local)
+    ms, host_s = timed(batch, K)
+    clocks = sampler.stop()
+    c = batch.counters(reset=True)
+    launches = batch.step_launches()
+    batch.close()
+
+    alone_ms, alone_host, alone_walkers = 0.0, 0.0, 0
+    for i in range(k):
+        sim = qmc.QMC(probs[i].n, 1, seeds[i], ndiag[i], stream=stream.cuda_stream)
+        sim.load_schedule(probs[i])
+        sim.init_populations(P.rho_basis(0))
+        sim.step(dt, pre + W)
+        sim.counters(reset=True)
+        m, h = timed(sim, K)
+        alone_ms += m
+        alone_host += h
+        alone_walkers += sim.counters()["walker_steps"]
+        sim.close()
+    if alone_walkers != c["walker_steps"]:
+        raise SystemExit("batched and per-instance runs disagree on the walker count")
+    value = c["walker_steps"] / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "batch256",
+                   "description": "256 GHZ instances (n 4..16, cos-modulated damping and dephasing, N^diag "
+                                  "1e4..1e6, one vector each) stepped by one context",
+                   "n_qubits": "4..16", "instances": k, "dt": dt, "integrator": "AB2",
+                   "timed_steps_of_job": f"{pre + W}..{pre + W + K}",
+                   "records_per_step_avg": c["k_next"] / max(1, c["steps"]),
+                   "spawns_per_step_avg": c["spawns"] / max(1, c["steps"]),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": c["walker_steps"] / host_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0,
+                "includes": "host time of the qmc_step call (column programs of every instance and step, "
+                            "upload, graph launches)"},
+        "unbatched": {"value": alone_walkers / (alone_ms * 1e-3), "unit": UNIT,
+                      "ms_per_step": alone_ms / K, "host_s": alone_host,
+                      "note": "the same 256 instances, one context each, stepped one after the other"},
+        "batched_speedup": (alone_ms / ms) if ms > 0 else None,
+        "gpu_launches": int(K * launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 def cpu_baseline(wl, pl, start_step: int, budget_s: float = 15.0):
@@ -496,6 +593,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch256":
+        run_batch(args, rank, world)
     else:
         run_gpu(args, rank, world)
 
