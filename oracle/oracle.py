@@ -63,6 +63,8 @@ def lib():
         L.orc_get_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_set_active.restype = C.c_int
         L.orc_set_active.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_set_proposal.restype = C.c_int
+        L.orc_set_proposal.argtypes = [C.c_void_p, C.c_int]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
         L.orc_count.restype = C.c_int64
@@ -159,6 +161,12 @@ class OracleSim:
     def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
                   prev_valid: bool = False):
         lib().orc_set_clock(self.handle, step, t, t_prev, dt_last, int(prev_valid))
+
+    def set_proposal(self, kind: int):
+        """Spawn choice: 0 exact |L|-weighted (the paper's), 1 static-weight proposal."""
+        rc = lib().orc_set_proposal(self.handle, kind)
+        if rc != OK:
+            raise RuntimeError(f"orc_set_proposal failed: {rc}")
 
     def set_active(self, segs):
         """Step only the listed vectors (the others keep their populations)."""

@@ -34,6 +34,15 @@
  *     first after a change of dt) is Euler.
  *   - Initialisation N(0) = N^diag rho(0) [walker averaging, Eq. (3)]:
  *     stochastic rounding of each component.
+ *   - Proposal spawning (not in the paper; the library's optional
+ *     alternative to the exact |L|-weighted choice): a walker attempts with
+ *     p_att = the sum over destinations of their static weights (each
+ *     destination's sum of |Re| + |Im| over its quantised terms, a bound on
+ *     |Re L| + |Im L| for every state), picks a destination with probability
+ *     static weight / p_att, and spawns onto its Re or Im channel with the
+ *     exact element weights inside that interval: the expected spawn per
+ *     destination and channel is the plain method's, without evaluating
+ *     the rest of the column.
  */
 #include <math.h>
 #include <stdint.h>
@@ -323,6 +332,52 @@ static int build_column(const problem* p, uint64_t x, uint64_t y, double t, doub
     return ORC_OK;
 }
 
+/* Static weight of every destination of dt_eff * L(t): the sum over its
+ * expanded terms of |Re c| + |Im c| of the quantised coefficient (the Pauli
+ * phases only permute and negate components, so this bounds |Re L| + |Im L|
+ * of that destination for every source state).  Destination masks do not
+ * depend on the state (a Pauli string flips the bits of its X part). */
+static int build_static(const problem* p, double t, double dt_eff, column* col)
+{
+    const int n = p->n;
+    col->len = 0;
+    int rc;
+    for (int i = 0; i < p->nh; ++i) {
+        const ham_term* ht = &p->ham[i];
+        if (!window_on(p, ht->win, t)) continue;
+        double s = rate_value(p, ht->rate, t) * dt_eff;
+        double v = ht->h * s;
+        cint qk, qb;
+        if ((rc = quantise(0.0, -v, &qk)) != ORC_OK) return rc;
+        if ((rc = quantise(0.0, v, &qb)) != ORC_OK) return rc;
+        cint a = {llabs(qk.re) + llabs(qk.im), 0}, b = {llabs(qb.re) + llabs(qb.im), 0};
+        if ((rc = column_add(col, ht->xm << n, a)) != ORC_OK) return rc;
+        if ((rc = column_add(col, ht->xm, b)) != ORC_OK) return rc;
+    }
+    for (int i = 0; i < p->nl; ++i) {
+        const lind_op* lo = &p->lind[i];
+        if (!window_on(p, lo->win, t)) continue;
+        double s = rate_value(p, lo->rate, t) * dt_eff;
+        double hs = -0.5 * s;
+        for (int a = 0; a < lo->count; ++a) {
+            const pauli_coef* la = &p->lp[lo->start + a];
+            for (int b = 0; b < lo->count; ++b) {
+                const pauli_coef* lb = &p->lp[lo->start + b];
+                double zre = la->re * lb->re + la->im * lb->im;
+                double zim = la->im * lb->re - la->re * lb->im;
+                cint qj, qa;
+                if ((rc = quantise(s * zre, s * zim, &qj)) != ORC_OK) return rc;
+                if ((rc = quantise(hs * zre, -(hs * zim), &qa)) != ORC_OK) return rc;
+                cint aj = {llabs(qj.re) + llabs(qj.im), 0}, aa = {llabs(qa.re) + llabs(qa.im), 0};
+                if ((rc = column_add(col, (la->xm << n) | lb->xm, aj)) != ORC_OK) return rc;
+                if ((rc = column_add(col, (la->xm ^ lb->xm) << n, aa)) != ORC_OK) return rc;
+                if ((rc = column_add(col, la->xm ^ lb->xm, aa)) != ORC_OK) return rc;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
 /* Exported for tests: the quantised column, sorted by mask.  Returns the
  * number of entries (which may exceed cap; only cap are written) or < 0. */
 int orc_column(const void* pp, uint64_t x, uint64_t y, double t, double dt_eff, int cap,
@@ -364,6 +419,7 @@ typedef struct {
     uint64_t step;        /* global step index */
     double t, t_prev, dt_last;
     int prev_valid;
+    int proposal;         /* 0: exact |L|-weighted choice; 1: static-weight proposal */
 } state;
 
 static int pop_reserve(pop* p, int64_t cap)
@@ -540,8 +596,21 @@ void orc_get_clock(void* sp, uint64_t* step, double* tt)
  * including one landing on the parent itself (the diagonal, "death/cloning"
  * element, which is one of the kl in the paper's sum), becomes one record.
  */
+/* Value of the column at mask (0 if absent). */
+static cint column_at(const column* c, uint64_t mask)
+{
+    int lo = 0, hi = c->len;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (c->e[mid].mask < mask) lo = mid + 1; else hi = mid;
+    }
+    cint z = {0, 0};
+    if (lo < c->len && c->e[lo].mask == mask) z = c->e[lo].v;
+    return z;
+}
+
 static int spawn_parent(const state* s, const rec* par, int phase, double t, double dt_eff,
-                        int sigma, const uint32_t kd[2], column* col, spawn_list* out)
+                        int sigma, const uint32_t kd[2], column* col, const column* st, spawn_list* out)
 {
     const problem* p = s->prob;
     const int n = p->n;
@@ -550,11 +619,19 @@ static int spawn_parent(const state* s, const rec* par, int phase, double t, dou
     int rc = build_column(p, x, y, t, dt_eff, col);
     if (rc != ORC_OK) return rc;
 
-    /* P = 2^52 * dt_eff * sum_kl (|Re L_kl| + |Im L_kl|) */
+    /* P = 2^52 * dt_eff * sum_kl (|Re L_kl| + |Im L_kl|); with the proposal the
+     * attempt probability is the static sum instead */
     int64_t P = 0;
-    for (int e = 0; e < col->len; ++e) {
-        P += llabs(col->e[e].v.re) + llabs(col->e[e].v.im);
-        if (P >= P_LIMIT) return ORC_ERR_DT_TOO_LARGE;
+    if (s->proposal == 0) {
+        for (int e = 0; e < col->len; ++e) {
+            P += llabs(col->e[e].v.re) + llabs(col->e[e].v.im);
+            if (P >= P_LIMIT) return ORC_ERR_DT_TOO_LARGE;
+        }
+    } else {
+        for (int e = 0; e < st->len; ++e) {
+            P += st->e[e].v.re;
+            if (P >= P_LIMIT) return ORC_ERR_DT_TOO_LARGE;
+        }
     }
     int64_t walkers = llabs((int64_t)par->re) + llabs((int64_t)par->im);
     int noninit = (s->init_min > 0 && walkers < s->init_min) ? 1 : 0;
@@ -575,6 +652,34 @@ static int spawn_parent(const state* s, const rec* par, int phase, double t, dou
                                  : (((uint64_t)w[1] << 32) | w[0]);
             int64_t T = (int64_t)(R >> 12);
             if (T >= P) continue; /* this walker does not spawn */
+            if (s->proposal == 1) {
+                /* destination by static weights (ascending mask), then the Re or
+                 * Im channel by the exact element weights inside its interval */
+                for (int e = 0; e < st->len; ++e) {
+                    const int64_t sw = st->e[e].v.re;
+                    if (T >= sw) {
+                        T -= sw;
+                        continue;
+                    }
+                    const cint v = column_at(col, st->e[e].mask);
+                    const int64_t wr = llabs(v.re), wi = llabs(v.im);
+                    int chan = T < wr ? 0 : (T < wr + wi ? 1 : -1);
+                    if (chan >= 0) {
+                        int64_t dre = 0, dim = 0;
+                        if (chan == 0) {
+                            int64_t sv = sigma * sg * (v.re > 0 ? 1 : -1);
+                            if (comp == 0) dre = sv; else dim = sv;
+                        } else {
+                            int64_t sv = sigma * sg * (v.im > 0 ? 1 : -1);
+                            if (comp == 0) dim = sv; else dre = -sv;
+                        }
+                        rc = spawn_push(out, par->key ^ st->e[e].mask, dre, dim, noninit);
+                        if (rc != ORC_OK) return rc;
+                    }
+                    break;
+                }
+                continue;
+            }
             /* multinomial over (destination, channel) in ascending mask order,
              * Re channel before Im channel */
             for (int e = 0; e < col->len; ++e) {
@@ -646,7 +751,7 @@ int orc_step(void* sp, double dt, int nsteps)
 {
     state* s = (state*)sp;
     if (!(dt > 0.0) || nsteps < 0) return ORC_ERR_INVALID_ARG;
-    column col = {0, 0, 0};
+    column col = {0, 0, 0}, st_cur = {0, 0, 0}, st_prev = {0, 0, 0};
     spawn_list spl = {0, 0, 0};
     pop next = {0, 0, 0};
     int rc = ORC_OK;
@@ -656,6 +761,11 @@ int orc_step(void* sp, double dt, int nsteps)
         int ab2 = (s->integrator == 1 && s->prev_valid && s->dt_last == dt);
         double dt_cur = ab2 ? dt * 1.5 : dt;
         double dt_prev = dt * 0.5;
+        if (s->proposal) {
+            rc = build_static(s->prob, t, dt_cur, &st_cur);
+            if (rc == ORC_OK && ab2) rc = build_static(s->prob, s->t_prev, dt_prev, &st_prev);
+            if (rc != ORC_OK) break;
+        }
         for (int seg = 0; seg < s->nseg && rc == ORC_OK; ++seg) {
             if (!s->active[seg]) continue;
             uint32_t kd[2];
@@ -663,11 +773,11 @@ int orc_step(void* sp, double dt, int nsteps)
             spl.len = 0;
             const pop* cur = &s->cur[seg];
             for (int64_t i = 0; i < cur->len && rc == ORC_OK; ++i)
-                rc = spawn_parent(s, &cur->r[i], 0, t, dt_cur, 1, kd, &col, &spl);
+                rc = spawn_parent(s, &cur->r[i], 0, t, dt_cur, 1, kd, &col, &st_cur, &spl);
             if (ab2) {
                 const pop* prv = &s->prev[seg];
                 for (int64_t i = 0; i < prv->len && rc == ORC_OK; ++i)
-                    rc = spawn_parent(s, &prv->r[i], 1, s->t_prev, dt_prev, -1, kd, &col, &spl);
+                    rc = spawn_parent(s, &prv->r[i], 1, s->t_prev, dt_prev, -1, kd, &col, &st_prev, &spl);
             }
             if (rc != ORC_OK) break;
             /* spawns from N(t - dt) that land on states unoccupied in N(t) are
@@ -688,9 +798,21 @@ int orc_step(void* sp, double dt, int nsteps)
         s->t = t0 + (double)(it + 1) * dt;
     }
     free(col.e);
+    free(st_cur.e);
+    free(st_prev.e);
     free(spl.s);
     free(next.r);
     return rc;
+}
+
+/* Spawn choice of the following steps: 0 exact |L|-weighted (the paper's),
+ * 1 static-weight proposal (see the header). */
+int orc_set_proposal(void* sp, int kind)
+{
+    state* s = (state*)sp;
+    if (kind < 0 || kind > 1) return ORC_ERR_INVALID_ARG;
+    s->proposal = kind;
+    return ORC_OK;
 }
 
 int64_t orc_count(void* sp, int seg, int which)
