@@ -165,6 +165,23 @@ const char* qmc_last_error(const qmc_ctx* ctx);
 
 /* ---- problem ------------------------------------------------------------ */
 
+/* Destination choice of the spawn step.
+ * QMC_PROPOSAL_EXACT (default): the paper's rule [End Matter, spawn step] --
+ *   a walker spawns with probability p = dt sum_kl (|Re L| + |Im L|) and
+ *   picks (destination, channel) with probability |c(L)| / sum.
+ * QMC_PROPOSAL_STATIC (no counterpart in the paper): a walker attempts with
+ *   p_att = the sum over destinations of their static weights (each
+ *   destination's sum of |Re| + |Im| over its expanded, quantised terms, a
+ *   bound on |Re L| + |Im L| for every state), picks a destination with
+ *   probability static weight / p_att, and spawns onto its Re or Im channel
+ *   with probabilities |Re L| / static weight and |Im L| / static weight.
+ *   Every destination and channel receives the same expected spawn as with
+ *   the exact rule, and only the chosen destination's element is evaluated.
+ * Applies from the next qmc_step.  Errors: INVALID_ARG. */
+#define QMC_PROPOSAL_EXACT 0
+#define QMC_PROPOSAL_STATIC 1
+int qmc_set_proposal(qmc_ctx* ctx, int32_t kind);
+
 /* Load H(t) and the Lindblad operators [Eq. (1)].  The library expands
  * -i[H, rho] and gamma (L rho L^dag - 1/2 {L^dag L, rho}) into Pauli
  * superoperator terms and, per step, into the column tables of Eq. (2).

@@ -49,6 +49,7 @@ struct Prog {
     const Entry* ent;
     const AffGroup* aff;
     const Run* run;
+    const StatSlot* stat;
 };
 
 QMC_HD inline Prog prog_at(const uint8_t* base)
@@ -63,6 +64,7 @@ QMC_HD inline Prog prog_at(const uint8_t* base)
     p.ent = (const Entry*)(base + p.h->off_entry);
     p.aff = (const AffGroup*)(base + p.h->off_aff);
     p.run = (const Run*)(base + p.h->off_run);
+    p.stat = (const StatSlot*)(base + p.h->off_stat);
     return p;
 }
 
@@ -182,6 +184,54 @@ QMC_HD inline bool choose_destination(const Prog& p, uint32_t x, uint32_t y, int
         }
         return false;
     }
+    return false;
+}
+
+// Index of the destination entry with this mask, or -1.
+QMC_HD inline int find_entry(const Prog& p, uint64_t mask)
+{
+    int lo = 0, hi = p.h->n_entry;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (p.ent[mid].mask_key < mask) lo = mid + 1; else hi = mid;
+    }
+    return (lo < p.h->n_entry && p.ent[lo].mask_key == mask) ? lo : -1;
+}
+
+// Element of the column at a destination mask (0 where the column has no
+// entry).  The diagonal element needs the self-family forms.
+QMC_HD inline void value_at_mask(const Prog& p, uint64_t mask, uint32_t x, uint32_t y, int64_t* vr, int64_t* vi)
+{
+    *vr = 0;
+    *vi = 0;
+    const int e = find_entry(p, mask);
+    if (e < 0) return;
+    int64_t sre = 0, sim = 0;
+    if (p.ent[e].kind == 0u) (void)column_weight(p, x, y, &sre, &sim);
+    entry_value(p, p.ent[e], x, y, sre, sim, vr, vi);
+}
+
+// Proposal spawning of an attempting walker with T in [0, p_att): the static
+// slot whose interval holds T, then the Re channel if the offset inside it is
+// below |Re L|, the Im channel if below |Re L| + |Im L|, else no spawn.
+// Returns false for no spawn.
+QMC_HD inline bool proposal_choose(const Prog& p, uint32_t x, uint32_t y, int64_t T, uint64_t* mask, int* chan,
+                                   int64_t* v)
+{
+    int lo = 0, hi = p.h->n_stat;   // first slot with end > T
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (p.stat[mid].end > T) hi = mid; else lo = mid + 1;
+    }
+    if (lo >= p.h->n_stat) return false;
+    const int64_t start = lo ? p.stat[lo - 1].end : 0;
+    const int64_t U = T - start;
+    int64_t vr, vi;
+    value_at_mask(p, p.stat[lo].mask, x, y, &vr, &vi);
+    const int64_t wr = qmc_iabs64(vr), wi = qmc_iabs64(vi);
+    *mask = p.stat[lo].mask;
+    if (U < wr) { *chan = 0; *v = vr; return true; }
+    if (U < wr + wi) { *chan = 1; *v = vi; return true; }
     return false;
 }
 

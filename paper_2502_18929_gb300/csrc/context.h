@@ -40,6 +40,7 @@ struct qmc_ctx {
     };
     std::vector<Instance> inst;
     bool batch = false;
+    int proposal = 0;   // spawn choice rule (qmc_set_proposal)
     bool has_pop = false;
     qmc::SegInfo* d_seginfo = nullptr;
     qmc::InstInfo* d_inst = nullptr;

@@ -409,7 +409,8 @@ struct SegDraw {
 __device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo& inf, int seg, int phase)
 {
     const SegInfo si = P.seginfo[seg];
-    const int64_t pb = ((const ProgHeader*)prog_ptr(P, inf, si.inst, phase))->p_bound;
+    const ProgHeader* h = (const ProgHeader*)prog_ptr(P, inf, si.inst, phase);
+    const int64_t pb = P.proposal ? h->p_att : h->p_bound;   // attempt bound of the choice rule
     SegDraw d;
     d.all = pb >= (1ll << 52);
     d.b12 = d.all ? ~0ull : (uint64_t)pb << 12;
@@ -741,17 +742,29 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
             const int n = si.n;
             const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & (n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)));
             const Prog prog = prog_at(single ? (phase ? pb1 : pb0) : prog_ptr(P, inf, si.inst, phase));
-            int64_t sre, sim;
-            const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
-            if (Pw >= (1ll << 52)) {
-                set_error(st, DERR_DT_TOO_LARGE);
-            } else if (T < Pw) {
+            if (P.proposal) {
+                // static-weight proposal: every candidate is an attempt (T < p_att)
                 uint64_t mk;
                 int chan;
                 int64_t v;
-                ok = choose_destination(prog, x, y, sre, sim, T, &mk, &chan, &v);
-                if (ok) rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
-                else set_error(st, DERR_TILE_CAPACITY);
+                if (prog.h->p_att >= (1ll << 52)) set_error(st, DERR_DT_TOO_LARGE);
+                else if (proposal_choose(prog, x, y, T, &mk, &chan, &v)) {
+                    ok = true;
+                    rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
+                }
+            } else {
+                int64_t sre, sim;
+                const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+                if (Pw >= (1ll << 52)) {
+                    set_error(st, DERR_DT_TOO_LARGE);
+                } else if (T < Pw) {
+                    uint64_t mk;
+                    int chan;
+                    int64_t v;
+                    ok = choose_destination(prog, x, y, sre, sim, T, &mk, &chan, &v);
+                    if (ok) rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
+                    else set_error(st, DERR_TILE_CAPACITY);
+                }
             }
         }
         const uint32_t bal = __ballot_sync(kFull, ok);
@@ -799,28 +812,48 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         const Prog prog = prog_at(prog_ptr(P, inf, si.inst, it.phase));
         const Rec par = (it.phase ? P.pop[prv] : P.pop[cur])[it.parent];
         const uint32_t x = (uint32_t)(par.key >> n), y = (uint32_t)(par.key & ymask);
-        int64_t sre, sim;
-        const int64_t Pw = column_weight(prog, x, y, &sre, &sim);
+        // bins of the walkers' draw T: plain, two per destination entry (Re,
+        // Im; widths |Re L|, |Im L| over [0, P)); proposal, three per static
+        // slot (Re, Im and the rest of the slot's static weight, which spawns
+        // nothing; over [0, p_att))
+        const bool prop = P.proposal != 0;
+        int64_t Pw;
+        int nb;
+        if (prop) {
+            Pw = prog.h->p_att;
+            nb = 3 * prog.h->n_stat;
+        } else {
+            int64_t sre, sim;
+            Pw = column_weight(prog, x, y, &sre, &sim);
+            nb = 2 * prog.h->n_entry;
+            if (nb <= 2 * kMaxEntries)
+                for (int e = tid; e < prog.h->n_entry; e += kThreads) {
+                    int64_t vr, vi;
+                    entry_value(prog, prog.ent[e], x, y, sre, sim, &vr, &vi);
+                    vals[2 * e] = vr;
+                    vals[2 * e + 1] = vi;
+                }
+        }
         if (Pw >= (1ll << 52)) {
             if (threadIdx.x == 0) set_error(st, DERR_DT_TOO_LARGE);
             return;
         }
-        const int ne = prog.h->n_entry;
-        if (ne > kMaxEntries) {
+        if (nb > 2 * kMaxEntries) {
             if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
             return;
         }
-        // entry values and weights
-        for (int e = tid; e < ne; e += kThreads) {
-            int64_t vr, vi;
-            entry_value(prog, prog.ent[e], x, y, sre, sim, &vr, &vi);
-            vals[2 * e] = vr;
-            vals[2 * e + 1] = vi;
-        }
-        for (int b = tid; b < 2 * ne; b += kThreads) hist[b] = 0;
+        if (prop)
+            for (int k = tid; k < prog.h->n_stat; k += kThreads) {
+                int64_t vr, vi;
+                value_at_mask(prog, prog.stat[k].mask, x, y, &vr, &vi);
+                const int64_t width = prog.stat[k].end - (k ? prog.stat[k - 1].end : 0);
+                vals[3 * k] = vr;
+                vals[3 * k + 1] = vi;
+                vals[3 * k + 2] = width - iabs64(vr) - iabs64(vi);   // no-spawn remainder
+            }
+        for (int b = tid; b < nb; b += kThreads) hist[b] = 0;
         __syncthreads();
-        // inclusive prefix of |vals| (blocked per thread, then across threads)
-        const int nb = 2 * ne;
+        // inclusive prefix of the bin widths (blocked per thread, then across threads)
         const int per = (nb + kThreads - 1) / kThreads;
         const int b0 = tid * per, b1 = min(nb, b0 + per);
         int64_t acc = 0;
@@ -873,6 +906,9 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         const int sigma = it.phase ? -1 : 1;
         const int64_t init_min = P.inst[si.inst].init_min;
         const int noninit = (init_min > 0 && (iabs64(par.re) + iabs64(par.im)) < init_min) ? 1 : 0;
+        if (prop)   // the remainder bins spawn nothing
+            for (int b = 3 * tid + 2; b < nb; b += 3 * kThreads) hist[b] = 0;
+        __syncthreads();
         int my_n = 0;
         for (int b = tid; b < nb; b += kThreads) my_n += hist[b] ? 1 : 0;
         int my_off = 0;
@@ -886,9 +922,9 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         int k = 0;
         for (int b = tid; b < nb; b += kThreads) {
             if (!hist[b]) continue;
-            const int e = b >> 1, chan = b & 1;
-            const SRec r = make_spawn(par.key ^ prog.ent[e].mask_key, it.seg, comp, chan, vals[b], sg,
-                                      sigma, noninit, hist[b]);
+            const int chan = prop ? b % 3 : (b & 1);
+            const uint64_t mk = prop ? prog.stat[b / 3].mask : prog.ent[b >> 1].mask_key;
+            const SRec r = make_spawn(par.key ^ mk, it.seg, comp, chan, vals[b], sg, sigma, noninit, hist[b]);
             const int64_t pos = (int64_t)s_base + my_off + k;
             if (pos < P.spawn_cap) P.spawn[pos] = r;
             ++k;

@@ -100,7 +100,7 @@ struct StepParams {
     const SegInfo* seginfo;   // per segment
     const InstInfo* inst;     // per instance
     int ninst;
-    int pad3;
+    int proposal;         // 0: exact |L|-weighted destination choice; 1: static-weight proposal
 };
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same

@@ -155,6 +155,7 @@ StepParams params(qmc_ctx* c)
     P.seginfo = c->d_seginfo;
     P.inst = c->d_inst;
     P.ninst = (int)c->inst.size();
+    P.proposal = c->proposal;
     return P;
 }
 
@@ -485,6 +486,18 @@ int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, cons
     if (validate_schedule(s, &why) != QMC_OK) return fail(ctx, QMC_ERR_INVALID_ARG, why);
     ctx->inst[0].sched = s;
     ctx->inst[0].has_sched = true;
+    return QMC_OK;
+}
+
+int qmc_set_proposal(qmc_ctx* ctx, int32_t kind)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "unknown proposal kind");
+    if (ctx->proposal != kind) {
+        ctx->proposal = kind;
+        ctx->graph_dirty = true;
+    }
     return QMC_OK;
 }
 

@@ -40,11 +40,21 @@ struct ProgHeader {
     int32_t off_selffam, off_selfgen, off_fam, off_gen, off_gterm, off_entry;
     int32_t n_aff, off_aff;
     int32_t n_run, off_run;
+    int32_t n_stat, off_stat;
     int64_t p_bound;                      // >= P of every state (filter for the spawn test)
+    int64_t p_att;                        // proposal spawning: sum of the static weights (>= 2^52: too large)
     int64_t self_const_re, self_const_im; // parity-free part of the diagonal element
     int64_t p_const;                      // sum of |Re| + |Im| over constant groups
     int32_t bytes;                        // size of the whole blob
     int32_t n_nonconst_gen;               // generic groups come non-constant first
+};
+
+// Proposal spawning: every destination with a nonzero static weight (sum of
+// |Re| + |Im| over its expanded terms), in ascending mask order, with the
+// end of its interval in the cumulative static weights.
+struct StatSlot {
+    uint64_t mask;
+    int64_t end;
 };
 
 // Self-family parity term: Q' * (|M| - 2 popc(pat & M)), pat = x, y or x ^ y.

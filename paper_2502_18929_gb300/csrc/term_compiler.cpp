@@ -397,6 +397,26 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     std::sort(entries.begin(), entries.end(),
               [](const Entry& a, const Entry& b) { return a.mask_key < b.mask_key; });
 
+    // static weights per destination mask, from the expanded terms before
+    // any merging (the proposal spawning's destination law)
+    std::vector<StatSlot> stat;
+    {
+        std::map<uint64_t, int64_t> sw;
+        for (const Raw& r : raw) {
+            const uint64_t mk = ((uint64_t)r.xl << n) | (uint64_t)r.xr;
+            const int64_t a = std::llabs(r.qre) + std::llabs(r.qim);
+            int64_t& acc = sw[mk];
+            acc = (acc >= (1ll << 52) || a >= (1ll << 52)) ? (1ll << 52) : std::min<int64_t>(acc + a, 1ll << 52);
+        }
+        int64_t run = 0;
+        for (const auto& kv : sw) {
+            if (kv.second == 0) continue;
+            run = std::min<int64_t>(run + kv.second, 1ll << 52);
+            stat.push_back(StatSlot{kv.first, run});
+        }
+        hdr.p_att = run;
+    }
+
     // runs of consecutive members of one family (see Run)
     std::vector<Run> runs;
     for (size_t e = 0; e < entries.size(); ++e) {
@@ -431,6 +451,8 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     hdr.off_aff = (int32_t)off;     off = align8(off + affs.size() * sizeof(AffGroup));
     hdr.n_aff = (int32_t)affs.size();
     hdr.off_run = (int32_t)off;     off = align8(off + runs.size() * sizeof(Run));
+    hdr.off_stat = (int32_t)off;    off = align8(off + stat.size() * sizeof(StatSlot));
+    hdr.n_stat = (int32_t)stat.size();
     hdr.n_run = (int32_t)runs.size();
     hdr.bytes = (int32_t)off;
     blob->resize(base + off, 0);
@@ -443,6 +465,7 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     put(blob, base + hdr.off_entry, entries.data(), entries.size());
     put(blob, base + hdr.off_aff, affs.data(), affs.size());
     put(blob, base + hdr.off_run, runs.data(), runs.size());
+    put(blob, base + hdr.off_stat, stat.data(), stat.size());
     return QMC_OK;
 }
 

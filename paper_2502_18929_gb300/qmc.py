@@ -35,7 +35,7 @@ EXPORTED = [
     "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
-    "qmc_step_launches", "qmc_batch_create",
+    "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal",
 ]
 
 
@@ -117,6 +117,7 @@ def lib():
         L.qmc_step_profile.argtypes = [vp, C.c_double, C.c_int64, vp, C.c_int32, vp]
         L.qmc_counters.argtypes = [vp, C.c_int32, vp]
         L.qmc_step_launches.argtypes = [vp, vp]
+        L.qmc_set_proposal.argtypes = [vp, C.c_int32]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -232,6 +233,10 @@ class QMC:
         self.n_diag = None
         self.offsets = np.concatenate([[0], np.cumsum(n_vectors)]).astype(np.int64)
         return self
+
+    def set_proposal(self, kind: int):
+        """Spawn choice: EXACT (0, the paper's) or STATIC (1, static-weight proposal)."""
+        self._check(self.L.qmc_set_proposal(self.h, kind), "qmc_set_proposal")
 
     def load_schedule(self, prob):
         a = _schedule_arrays(prob)
