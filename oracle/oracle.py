@@ -65,6 +65,8 @@ def lib():
         L.orc_set_active.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_set_proposal.restype = C.c_int
         L.orc_set_proposal.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_mlp.restype = C.c_int
+        L.orc_set_mlp.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 7 + [C.c_float]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
         L.orc_count.restype = C.c_int64
@@ -162,8 +164,20 @@ class OracleSim:
                   prev_valid: bool = False):
         lib().orc_set_clock(self.handle, step, t, t_prev, dt_last, int(prev_valid))
 
+    def set_mlp(self, net):
+        """Network of the learned proposal: a dict with out_masks (uint64), w1,
+        b1, w2, b2, w3, b3 (float32, row-major) and eps."""
+        arrs = [np.ascontiguousarray(net["out_masks"], dtype=np.uint64)] + \
+            [np.ascontiguousarray(net[k], dtype=np.float32) for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+        H, I = arrs[1].shape
+        rc = lib().orc_set_mlp(self.handle, I, H, len(arrs[0]), *[a.ctypes.data for a in arrs],
+                               float(net["eps"]))
+        if rc != OK:
+            raise RuntimeError(f"orc_set_mlp failed: {rc}")
+
     def set_proposal(self, kind: int):
-        """Spawn choice: 0 exact |L|-weighted (the paper's), 1 static-weight proposal."""
+        """Spawn choice: 0 exact |L|-weighted (the paper's), 1 static-weight
+        proposal, 2 learned proposal (after set_mlp)."""
         rc = lib().orc_set_proposal(self.handle, kind)
         if rc != OK:
             raise RuntimeError(f"orc_set_proposal failed: {rc}")

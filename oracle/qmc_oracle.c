@@ -43,6 +43,15 @@
  *     exact element weights inside that interval: the expected spawn per
  *     destination and channel is the plain method's, without evaluating
  *     the rest of the column.
+ *   - Learned proposal (not in the paper): the attempt is the same; the
+ *     destination is drawn from integer weights Q_k (summing to 2^24) that mix
+ *     a small network's softmax over the destinations with the static
+ *     proposal (share eps), and each channel receives floor(A) +
+ *     Bernoulli(frac A) walkers with A = w * 2^24 / (Q_k * p_att), so that the
+ *     expectation is again w / 2^52 per walker.  The network runs in single
+ *     precision with its operations in a fixed order (see mlp_logit), the
+ *     exponential is the polynomial of mlp_exp, and A is one double-precision
+ *     quotient, exactly as the library evaluates them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -90,6 +99,7 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
 #define TAG_INIT 0x494E4954u /* per segment key for initial rounding */
 #define KIND_SPAWN 0u
 #define KIND_INIT 1u
+#define KIND_LEARNED 2u
 
 static void derive_key(uint64_t seed, uint64_t step, uint32_t seg, uint32_t tag, uint32_t kd[2])
 {
@@ -419,8 +429,134 @@ typedef struct {
     uint64_t step;        /* global step index */
     double t, t_prev, dt_last;
     int prev_valid;
-    int proposal;         /* 0: exact |L|-weighted choice; 1: static-weight proposal */
+    int proposal;         /* 0: exact |L|-weighted choice; 1: static proposal; 2: learned */
+    /* learned proposal: network (see mlp_logit) */
+    int mlp_in, mlp_hidden, mlp_out;
+    float* w1; float* b1; float* w2; float* b2; float* w3; float* b3;
+    uint64_t* out_mask;   /* destination mask of each output, as given */
+    float eps;            /* static share of the mixture */
 } state;
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal arithmetic, single precision in a fixed order.          */
+/* ------------------------------------------------------------------------ */
+/* e^x for x <= 0: 2^(x log2 e) = 2^k 2^f, 2^f by its Taylor polynomial of
+ * degree 7 in Horner form (fused multiply-adds), 2^k by the exponent bits. */
+static float mlp_exp(float x)
+{
+    if (x < -87.0f) return 0.0f;
+    const float y = x * 1.44269504f;
+    const float k = floorf(y);
+    const float f = y - k;
+    float p = 1.52527338e-5f;
+    p = fmaf(p, f, 1.54035304e-4f);
+    p = fmaf(p, f, 1.33335581e-3f);
+    p = fmaf(p, f, 9.61812911e-3f);
+    p = fmaf(p, f, 5.55041087e-2f);
+    p = fmaf(p, f, 2.40226507e-1f);
+    p = fmaf(p, f, 6.93147181e-1f);
+    p = fmaf(p, f, 1.0f);
+    const uint32_t bits = (uint32_t)((int)k + 127) << 23;
+    float scale;
+    memcpy(&scale, &bits, 4);
+    return p * scale;
+}
+
+/* Hidden layers for the source |x><y| at time t: inputs are the n bits of x,
+ * the n bits of y (1 or 0) and t; ReLU after each layer.  h2 receives the
+ * second hidden layer. */
+static void mlp_hidden(const state* s, uint64_t x, uint64_t y, double t, float* h1, float* h2)
+{
+    const int n = s->prob->n, H = s->mlp_hidden, I = s->mlp_in;
+    const float tf = (float)t;
+    for (int j = 0; j < H; ++j) {
+        float a = s->b1[j];
+        for (int i = 0; i < 2 * n; ++i) {
+            const uint64_t bit = i < n ? (x >> i) & 1u : (y >> (i - n)) & 1u;
+            if (bit) a = a + s->w1[j * I + i];
+        }
+        a = fmaf(s->w1[j * I + 2 * n], tf, a);
+        h1[j] = a > 0.0f ? a : 0.0f;
+    }
+    for (int j = 0; j < H; ++j) {
+        float a = s->b2[j];
+        for (int i = 0; i < H; ++i) a = fmaf(s->w2[j * H + i], h1[i], a);
+        h2[j] = a > 0.0f ? a : 0.0f;
+    }
+}
+
+static float mlp_logit(const state* s, const float* h2, int g)
+{
+    const int H = s->mlp_hidden;
+    float a = s->b3[g];
+    for (int i = 0; i < H; ++i) a = fmaf(s->w3[g * H + i], h2[i], a);
+    return a;
+}
+
+/* Output index of a destination mask, or -1. */
+static int mlp_output(const state* s, uint64_t mask)
+{
+    for (int g = 0; g < s->mlp_out; ++g)
+        if (s->out_mask[g] == mask) return g;
+    return -1;
+}
+
+/* Integer proposal weights Q[0 .. st->len) (sum 2^24) of the source. */
+static void learned_weights(const state* s, const column* st, int64_t p_att, uint64_t x, uint64_t y, double t,
+                            int64_t* Q)
+{
+    float h1[64], h2[64];
+    mlp_hidden(s, x, y, t, h1, h2);
+    const int ns = st->len;
+    float m = -INFINITY;
+    for (int k = 0; k < ns; ++k) {
+        const int g = st->e[k].v.re > 0 ? mlp_output(s, st->e[k].mask) : -1;
+        if (g >= 0) {
+            const float l = mlp_logit(s, h2, g);
+            if (l > m) m = l;
+        }
+    }
+    float S = 0.0f;
+    for (int k = 0; k < ns; ++k) {
+        const int g = st->e[k].v.re > 0 ? mlp_output(s, st->e[k].mask) : -1;
+        if (g >= 0) S = S + mlp_exp(mlp_logit(s, h2, g) - m);
+    }
+    const float omeps = 1.0f - s->eps;
+    int64_t sum = 0;
+    int arg = -1;
+    for (int k = 0; k < ns; ++k) {
+        Q[k] = 0;
+        if (st->e[k].v.re <= 0) continue;
+        const int g = mlp_output(s, st->e[k].mask);
+        int64_t L = 0;
+        if (g >= 0 && S > 0.0f) {
+            const float q = mlp_exp(mlp_logit(s, h2, g) - m) / S;
+            L = (int64_t)floorf((omeps * q) * 16777216.0f);
+        }
+        const int64_t St = (int64_t)floor((double)s->eps * (double)st->e[k].v.re / (double)p_att * 16777216.0);
+        Q[k] = L + St;
+        if (Q[k] < 1) Q[k] = 1;
+        sum += Q[k];
+        if (arg < 0 || Q[k] > Q[arg]) arg = k;
+    }
+    Q[arg] += ((int64_t)1 << 24) - sum;
+}
+
+/* Per-walker randomness of the learned proposal: two Philox calls. */
+static void learned_draws(uint64_t key, int phase, int comp, int64_t j, const uint32_t kd[2], uint32_t* V,
+                          double* ure, double* uim)
+{
+    uint32_t a[4], b[4];
+    uint32_t ctr[4] = {(uint32_t)key, (uint32_t)(key >> 32),
+                       (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_LEARNED << 2),
+                       (uint32_t)(((j >> 1) << 2) | ((j & 1) << 1))};
+    orc_philox(ctr, kd, a);
+    ctr[3] |= 1u;
+    orc_philox(ctr, kd, b);
+    *V = a[0] >> 8;
+    *ure = (double)((((uint64_t)a[1]) << 21) | (a[2] >> 11)) * (1.0 / 9007199254740992.0);
+    *uim = (double)((((uint64_t)b[0]) << 21) | (b[1] >> 11)) * (1.0 / 9007199254740992.0);
+}
 
 static int pop_reserve(pop* p, int64_t cap)
 {
@@ -476,6 +612,7 @@ void orc_state_free(void* sp)
     if (!s) return;
     for (int i = 0; i < s->nseg; ++i) { free(s->cur[i].r); free(s->prev[i].r); }
     free(s->cur); free(s->prev); free(s->active);
+    free(s->w1); free(s->b1); free(s->w2); free(s->b2); free(s->w3); free(s->b3); free(s->out_mask);
     free(s);
 }
 
@@ -635,6 +772,12 @@ static int spawn_parent(const state* s, const rec* par, int phase, double t, dou
     }
     int64_t walkers = llabs((int64_t)par->re) + llabs((int64_t)par->im);
     int noninit = (s->init_min > 0 && walkers < s->init_min) ? 1 : 0;
+    int64_t Qbuf[256];
+    int64_t* Qw = Qbuf;
+    if (s->proposal == 2) {
+        if (st->len > 256) return ORC_ERR_INVALID_ARG;
+        learned_weights(s, st, P, x, y, t, Qw);
+    }
 
     for (int comp = 0; comp < 2; ++comp) {
         int64_t val = comp == 0 ? par->re : par->im;
@@ -652,6 +795,35 @@ static int spawn_parent(const state* s, const rec* par, int phase, double t, dou
                                  : (((uint64_t)w[1] << 32) | w[0]);
             int64_t T = (int64_t)(R >> 12);
             if (T >= P) continue; /* this walker does not spawn */
+            if (s->proposal == 2) {
+                /* learned proposal: destination by Q, counts by the amplitude */
+                uint32_t V;
+                double ure, uim;
+                learned_draws(par->key, phase, comp, j, kd, &V, &ure, &uim);
+                int k = 0;
+                int64_t cum = 0;
+                for (k = 0; k < st->len; ++k) {
+                    cum += Qw[k];
+                    if ((int64_t)V < cum) break;
+                }
+                if (k >= st->len) continue;
+                const cint v = column_at(col, st->e[k].mask);
+                for (int chan = 0; chan < 2; ++chan) {
+                    const int64_t w = llabs(chan ? v.im : v.re);
+                    if (w == 0) continue;
+                    const double A = ((double)w * 16777216.0) / ((double)Qw[k] * (double)P);
+                    const double fl = floor(A);
+                    int64_t cnt = (int64_t)fl + (((chan ? uim : ure) < A - fl) ? 1 : 0);
+                    if (cnt == 0) continue;
+                    int64_t dre = 0, dim = 0;
+                    int64_t sv = sigma * sg * ((chan ? v.im : v.re) > 0 ? 1 : -1) * cnt;
+                    if (chan == 0) { if (comp == 0) dre = sv; else dim = sv; }
+                    else { if (comp == 0) dim = sv; else dre = -sv; }
+                    rc = spawn_push(out, par->key ^ st->e[k].mask, dre, dim, noninit);
+                    if (rc != ORC_OK) return rc;
+                }
+                continue;
+            }
             if (s->proposal == 1) {
                 /* destination by static weights (ascending mask), then the Re or
                  * Im channel by the exact element weights inside its interval */
@@ -810,8 +982,39 @@ int orc_step(void* sp, double dt, int nsteps)
 int orc_set_proposal(void* sp, int kind)
 {
     state* s = (state*)sp;
-    if (kind < 0 || kind > 1) return ORC_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 2 || (kind == 2 && !s->w1)) return ORC_ERR_INVALID_ARG;
     s->proposal = kind;
+    return ORC_OK;
+}
+
+/* Network of the learned proposal (weights copied): n_in = 2n + 1 inputs,
+ * n_hidden <= 64, n_out destination masks; w1 is n_hidden x n_in, w2
+ * n_hidden x n_hidden, w3 n_out x n_hidden, all row-major. */
+int orc_set_mlp(void* sp, int n_in, int n_hidden, int n_out, const uint64_t* out_mask, const float* w1,
+                const float* b1, const float* w2, const float* b2, const float* w3, const float* b3, float eps)
+{
+    state* s = (state*)sp;
+    if (n_in != 2 * s->prob->n + 1 || n_hidden < 1 || n_hidden > 64 || n_out < 1 || !(eps > 0.0f) || eps > 1.0f)
+        return ORC_ERR_INVALID_ARG;
+    s->mlp_in = n_in;
+    s->mlp_hidden = n_hidden;
+    s->mlp_out = n_out;
+    s->eps = eps;
+#define ORC_COPY(dst, src, cnt, T)                                       \
+    do {                                                                 \
+        free(dst);                                                       \
+        dst = (T*)malloc(sizeof(T) * (size_t)(cnt));                     \
+        if (!dst) return ORC_ERR_OOM;                                    \
+        memcpy(dst, src, sizeof(T) * (size_t)(cnt));                     \
+    } while (0)
+    ORC_COPY(s->w1, w1, n_hidden * n_in, float);
+    ORC_COPY(s->b1, b1, n_hidden, float);
+    ORC_COPY(s->w2, w2, n_hidden * n_hidden, float);
+    ORC_COPY(s->b2, b2, n_hidden, float);
+    ORC_COPY(s->w3, w3, n_out * n_hidden, float);
+    ORC_COPY(s->b3, b3, n_out, float);
+    ORC_COPY(s->out_mask, out_mask, n_out, uint64_t);
+#undef ORC_COPY
     return ORC_OK;
 }
 

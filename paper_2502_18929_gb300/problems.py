@@ -281,3 +281,40 @@ def spread_population(n: int, count: int, seed: int) -> tuple[np.ndarray, np.nda
     re = np.where(sel == 0, 1, np.where(sel == 1, -1, 0)).astype(np.int32)
     im = np.where(sel == 2, 1, np.where(sel == 3, -1, 0)).astype(np.int32)
     return keys, re, im
+
+
+def destination_masks(prob) -> np.ndarray:
+    """Every destination mask (dx << n) | dy that a term of the problem can
+    reach (a Pauli string flips the bits of its X part), sorted."""
+    n = prob.n
+    out = set()
+    for h, xm, zm, r, w in prob.ham:
+        out.add(int(xm) << n)
+        out.add(int(xm))
+    for ops, r, w in prob.lind:
+        for _, xa, _ in ops:
+            for _, xb, _ in ops:
+                out.add((int(xa) << n) | int(xb))
+                out.add((int(xa) ^ int(xb)) << n)
+                out.add(int(xa) ^ int(xb))
+    return np.array(sorted(out), dtype=np.uint64)
+
+
+def random_network(prob, hidden: int = 32, seed: int = 0, eps: float = 0.25, scale: float = 1.0) -> dict:
+    """Randomly initialised network of the learned proposal for a problem:
+    inputs the n bits of x, the n bits of y and t; one output per
+    destination mask (float32, row-major weights)."""
+    rng = np.random.default_rng(seed)
+    masks = destination_masks(prob)
+    I = 2 * prob.n + 1
+    f32 = np.float32
+    return {
+        "out_masks": masks,
+        "w1": (rng.standard_normal((hidden, I)) * scale / np.sqrt(I)).astype(f32),
+        "b1": (rng.standard_normal(hidden) * 0.1).astype(f32),
+        "w2": (rng.standard_normal((hidden, hidden)) * scale / np.sqrt(hidden)).astype(f32),
+        "b2": (rng.standard_normal(hidden) * 0.1).astype(f32),
+        "w3": (rng.standard_normal((len(masks), hidden)) * scale / np.sqrt(hidden)).astype(f32),
+        "b3": (rng.standard_normal(len(masks)) * 0.5).astype(f32),
+        "eps": float(eps),
+    }

@@ -20,8 +20,10 @@ from oracle import oracle as O
 from paper_2502_18929_gb300 import problems as P
 
 
-def _densities(prob, rho0, V, seed, dt, nsteps, proposal, integrator=O.AB2, n_diag=10000):
+def _densities(prob, rho0, V, seed, dt, nsteps, proposal, integrator=O.AB2, n_diag=10000, net=None):
     sim = O.OracleSim(prob, V, seed=seed, integrator=integrator, n_diag=n_diag)
+    if net is not None:
+        sim.set_mlp(net)
     sim.set_proposal(proposal)
     sim.init(rho0)
     assert sim.step(dt, nsteps) == O.OK
@@ -71,3 +73,40 @@ def test_static_proposal_differs_from_plain_draws():
     a = _densities(prob, P.rho_basis(0), 2, 7, 0.01, 150, proposal=0)
     b = _densities(prob, P.rho_basis(0), 2, 7, 0.01, 150, proposal=1)
     assert not np.allclose(a, b)
+
+
+def test_learned_proposal_exact_mean_ghz4_ab2():
+    """Learned proposal with an untrained (random) network mixed with 25 %
+    static proposal: still unbiased, the mean equals the dense AB2 recursion
+    (any q whose support covers the column's is unbiased)."""
+    prob = P.ghz_circuit(4)
+    rho0 = P.rho_basis(0)
+    net = P.random_network(prob, hidden=16, seed=3, eps=0.25, scale=2.0)
+    rhos = _densities(prob, rho0, 16, 31, 0.01, 400, proposal=2, net=net)
+    ref = Dn.evolve(prob, Dn.rho_from_entries(4, rho0), 0.01, 400, "ab2")
+    se = rhos.std(0, ddof=1) / np.sqrt(rhos.shape[0])
+    sig = np.abs(ref) > 0.01
+    z = np.abs(rhos.mean(0) - ref)[sig] / se[sig]
+    assert z.max() < 4.5, z.max()
+
+
+def test_learned_proposal_one_step_mean():
+    """One Euler step with a random network and a small static share (5 %),
+    where amplitudes above 1 occur: the 400-vector mean matches (I + dt L) N."""
+    prob = P.ghz_circuit(3)
+    rho0 = [(0, 0, 0.5, 0.0), (1, 1, 0.25, 0.0), (0, 1, 0.2, 0.1), (1, 0, 0.2, -0.1), (3, 3, 0.25, 0.0)]
+    V = 400
+    sim = O.OracleSim(prob, V, seed=9, integrator=O.EULER, n_diag=4000)
+    sim.set_mlp(P.random_network(prob, hidden=8, seed=4, eps=0.05, scale=3.0))
+    sim.set_proposal(2)
+    sim.init(rho0)
+    n0 = np.array([sim.density(s) for s in range(V)])
+    sim.set_clock(250, 2.5)
+    assert sim.step(0.05, 1) == O.OK
+    n1 = np.array([sim.density(s) for s in range(V)])
+    Lm = Dn.liouvillian(prob, 2.5)
+    pred = np.array([Dn.unvec((np.eye(64) + 0.05 * Lm) @ Dn.vec(r), 8) for r in n0])
+    diff = n1 - pred
+    se = diff.std(0, ddof=1) / np.sqrt(V) + 1e-9
+    z = np.abs(diff.mean(0)) / se
+    assert z.max() < 4.8, z.max()
