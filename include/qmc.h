@@ -180,7 +180,38 @@ const char* qmc_last_error(const qmc_ctx* ctx);
  * Applies from the next qmc_step.  Errors: INVALID_ARG. */
 #define QMC_PROPOSAL_EXACT 0
 #define QMC_PROPOSAL_STATIC 1
+#define QMC_PROPOSAL_LEARNED 2
 int qmc_set_proposal(qmc_ctx* ctx, int32_t kind);
+
+/* Network of the learned proposal (no counterpart in the paper).  With
+ * QMC_PROPOSAL_LEARNED the attempt is the static proposal's; the destination
+ * is drawn from integer weights Q_k summing to 2^24 that mix the network's
+ * softmax over the source's destinations (share 1 - eps) with the static
+ * proposal (share eps, so every destination keeps Q_k >= 1), and each
+ * channel receives floor(A) + Bernoulli(frac A) walkers with
+ * A = |c(L)| 2^24 / (Q_k p_att): the same expected spawn as the exact rule.
+ * Inputs: the n bits of x, the n bits of y (1.0 or 0.0) and t; two hidden
+ * layers with ReLU; one logit per destination mask.  Single precision in a
+ * fixed order (reproducible on the CPU), exp by a degree-7 polynomial of
+ * 2^f.  At most 256 destinations per column (else qmc_step returns
+ * INVALID_ARG).  Borrowed for the call (copied to the device). */
+typedef struct {
+    int32_t n_in;               /* 2 n_qubits + 1                          */
+    int32_t n_hidden;           /* 1..64                                   */
+    int32_t n_out;              /* 1..4096 destination masks               */
+    float eps;                  /* static share, in (0, 1]                 */
+    const uint64_t* out_masks;  /* n_out distinct masks (dx << n) | dy     */
+    const float* w1;            /* n_hidden x n_in, row-major              */
+    const float* b1;            /* n_hidden                                */
+    const float* w2;            /* n_hidden x n_hidden                     */
+    const float* b2;            /* n_hidden                                */
+    const float* w3;            /* n_out x n_hidden                        */
+    const float* b3;            /* n_out                                   */
+} qmc_mlp;
+
+/* Load the learned proposal's network (one context of one instance).
+ * Errors: INVALID_ARG (sizes, masks not distinct), STATE (a batch), OOM. */
+int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* mlp);
 
 /* Load H(t) and the Lindblad operators [Eq. (1)].  The library expands
  * -i[H, rho] and gamma (L rho L^dag - 1/2 {L^dag L, rho}) into Pauli

@@ -539,7 +539,7 @@ static void learned_weights(const state* s, const column* st, int64_t p_att, uin
         sum += Q[k];
         if (arg < 0 || Q[k] > Q[arg]) arg = k;
     }
-    Q[arg] += ((int64_t)1 << 24) - sum;
+    if (arg >= 0) Q[arg] += ((int64_t)1 << 24) - sum;
 }
 
 /* Per-walker randomness of the learned proposal: two Philox calls. */

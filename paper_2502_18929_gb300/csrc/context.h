@@ -41,6 +41,11 @@ struct qmc_ctx {
     std::vector<Instance> inst;
     bool batch = false;
     int proposal = 0;   // spawn choice rule (qmc_set_proposal)
+    float* d_mlp = nullptr;          // learned proposal network
+    uint64_t* d_mlp_mask = nullptr;
+    int32_t* d_mlp_idx = nullptr;
+    int mlp_in = 0, mlp_hidden = 0, mlp_out = 0;
+    float mlp_eps = 0.f;
     bool has_pop = false;
     qmc::SegInfo* d_seginfo = nullptr;
     qmc::InstInfo* d_inst = nullptr;

@@ -4,6 +4,8 @@
 //   k_spawn_draw    walker draws [End Matter, spawn step] for parents with few
 //                   walkers; draws below the bound on P become candidates
 //   k_spawn_choose  exact spawn test and destination of every candidate
+//   k_spawn_learned (learned proposal, in place of k_spawn_choose) the
+//                   network's destination weights and the walker counts
 //   k_spawn_heavy   the same for heavy parents, one CTA per walker chunk,
 //                   aggregated per destination in shared memory
 //   k_sort_hist     digit histograms of all LSD radix passes
@@ -16,7 +18,9 @@
 //   k_finalize      segment offsets of N(t + dt), history, rotate the slots
 //
 // Integer-only: weights are exact 2^-52 fixed point, so spawning, annihilation
-// and the observables are bit-identical to any other exact evaluation.
+// and the observables are bit-identical to any other exact evaluation.  The
+// learned proposal's network runs in single precision with each operation
+// rounded explicitly, reproducible by a CPU that takes the same steps.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -421,6 +425,13 @@ __device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo&
 
 __device__ __forceinline__ bool below(const SegDraw& d, uint64_t X) { return d.all || X < d.b12; }
 
+// Low 52 bits of a candidate: its draw T, or under the learned proposal (whose
+// destination does not depend on T) the walker's index j in its component.
+__device__ __forceinline__ uint64_t cand_low(const StepParams& P, uint64_t X, uint32_t j)
+{
+    return P.proposal == 2 ? (uint64_t)j : (X >> 12);
+}
+
 // Flags of a candidate: comp, phase, noninit, sign of the parent component.
 __device__ __forceinline__ uint64_t cand_flags(int comp, int phase, int noninit, int32_t val)
 {
@@ -491,8 +502,8 @@ __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCan
             const uint64_t fl = cand_flags(comp, phase, o_non, comp ? o_im : o_re);
             c0 = below(od, X0);
             c1 = 2u * (uint32_t)j2 + 1u < m && below(od, X1);
-            t0 = (X0 >> 12) | fl;
-            t1 = (X1 >> 12) | fl;
+            t0 = cand_low(P, X0, 2u * (uint32_t)j2) | fl;
+            t1 = cand_low(P, X1, 2u * (uint32_t)j2 + 1u) | fl;
         }
         cand_push(stage, staged, c0, c1, o_j, (uint32_t)o_seg, t0, t1, P, lane);
     }
@@ -532,8 +543,8 @@ __device__ __forceinline__ void draw_second_pairs(const StepParams& P, const Ste
         c1 = 2u * j2 + 1u < m && below(sd, X1);
         const int noninit = (sd.init_min > 0 && (int64_t)((uint64_t)are + aim) < sd.init_min) ? 1 : 0;
         const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
-        t0 = (X0 >> 12) | fl;
-        t1 = (X1 >> 12) | fl;
+        t0 = cand_low(P, X0, 2u * j2) | fl;
+        t1 = cand_low(P, X1, 2u * j2 + 1u) | fl;
     }
     cand_push(stage, staged, c0, c1, it.x, it.y, t0, t1, P, lane);
 }
@@ -644,14 +655,14 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         if (__any_sync(kFull, cA0 || cA1)) {
             const int non = (sdA.init_min > 0 && (int64_t)((uint64_t)areA + aimA) < sdA.init_min) ? 1 : 0;
             const uint64_t fl = cand_flags((int)compA, phase, non, compA ? pA.im : pA.re);
-            cand_push(stage, staged, cA0, cA1, (uint32_t)iA, (uint32_t)segA, (XA0 >> 12) | fl, (XA1 >> 12) | fl, P,
-                      lane);
+            cand_push(stage, staged, cA0, cA1, (uint32_t)iA, (uint32_t)segA, cand_low(P, XA0, 0u) | fl,
+                      cand_low(P, XA1, 1u) | fl, P, lane);
         }
         if (__any_sync(kFull, cB0 || cB1)) {
             const int non = (sd.init_min > 0 && (int64_t)((uint64_t)areB + aimB) < sd.init_min) ? 1 : 0;
             const uint64_t fl = cand_flags((int)compB, phase, non, compB ? pB.im : pB.re);
-            cand_push(stage, staged, cB0, cB1, (uint32_t)iB, (uint32_t)seg, (XB0 >> 12) | fl, (XB1 >> 12) | fl, P,
-                      lane);
+            cand_push(stage, staged, cB0, cB1, (uint32_t)iB, (uint32_t)seg, cand_low(P, XB0, 0u) | fl,
+                      cand_low(P, XB1, 1u) | fl, P, lane);
         }
     }
     if (cnt > 0) draw_second_pairs(P, inf, stage, staged, ring, head, cnt, src, phase, lane);
@@ -781,6 +792,273 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
 }
 
 // ---------------------------------------------------------------------------
+// Learned proposal (the library's extension; not in the paper).  A parent's
+// attempting walker (T < p_att, as for the static proposal) draws its
+// destination slot k from integer weights Q_k summing to 2^24 and each
+// channel c of slot k receives floor(A) + Bernoulli(frac A) walkers with
+// A = |c(L)| 2^24 / (Q_k p_att), so that the expected spawn is |c(L)| / 2^52
+// per walker as in the plain method.  Q mixes the network's softmax over the
+// column's destinations (share 1 - eps) with the static proposal (share eps):
+//   L_k = floor((1 - eps) q_k 2^24),  S_k = floor(eps s_k / p_att 2^24),
+//   Q_k = max(1, L_k + S_k) for s_k > 0 (else 0),
+// the first largest Q_k absorbing 2^24 - sum Q.  The network runs in single
+// precision with every operation rounded explicitly in a fixed order (no
+// contraction), so that a CPU evaluating the same steps gets the same bits.
+// ---------------------------------------------------------------------------
+
+// e^x (x <= 0, else unused): 2^(x log2 e) = 2^k 2^f with k = floor, 2^f by
+// the degree-7 Taylor polynomial of e^(f ln 2) in Horner form, 2^k placed in
+// the exponent field.  Below -87 the result is 0.
+__device__ __forceinline__ float lp_exp(float x)
+{
+    if (x < -87.0f) return 0.0f;
+    const float y = __fmul_rn(x, 1.44269504f);
+    const float k = floorf(y);
+    const float f = __fsub_rn(y, k);
+    float p = 1.52527338e-5f;   // (ln 2)^7 / 7!
+    p = __fmaf_rn(p, f, 1.54035304e-4f);
+    p = __fmaf_rn(p, f, 1.33335581e-3f);
+    p = __fmaf_rn(p, f, 9.61812911e-3f);
+    p = __fmaf_rn(p, f, 5.55041087e-2f);
+    p = __fmaf_rn(p, f, 2.40226507e-1f);
+    p = __fmaf_rn(p, f, 6.93147181e-1f);
+    p = __fmaf_rn(p, f, 1.0f);
+    return __fmul_rn(p, __int_as_float((int)(((uint32_t)((int)k + 127)) << 23)));
+}
+
+// Network layout in P.mlp: w1 [H x I], b1 [H], w2 [H x H], b2 [H], w3 [G x H], b3 [G].
+struct LpNet {
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+    int I, H;
+};
+
+__device__ __forceinline__ LpNet lp_net(const StepParams& P)
+{
+    LpNet w;
+    w.I = P.mlp_in;
+    w.H = P.mlp_hidden;
+    w.w1 = P.mlp;
+    w.b1 = w.w1 + w.H * w.I;
+    w.w2 = w.b1 + w.H;
+    w.b2 = w.w2 + w.H * w.H;
+    w.w3 = w.b2 + w.H;
+    w.b3 = w.w3 + P.mlp_out * w.H;
+    return w;
+}
+
+// First hidden layer, neuron j: b1 + the weights of the set input bits (x
+// bits 0..n-1, then y bits), in ascending input order, then + w t by a fused
+// multiply-add; ReLU.
+__device__ __forceinline__ float lp_h1(const LpNet& w, int j, uint32_t x, uint32_t y, int n, float tf)
+{
+    const float* row = w.w1 + j * w.I;
+    float a = __ldg(&w.b1[j]);
+    for (int i = 0; i < n; ++i)
+        if ((x >> i) & 1u) a = __fadd_rn(a, __ldg(&row[i]));
+    for (int i = 0; i < n; ++i)
+        if ((y >> i) & 1u) a = __fadd_rn(a, __ldg(&row[n + i]));
+    a = __fmaf_rn(__ldg(&row[2 * n]), tf, a);
+    return a > 0.0f ? a : 0.0f;
+}
+
+// Second hidden layer, neuron j: b2 then fused multiply-adds in ascending order; ReLU.
+__device__ __forceinline__ float lp_h2(const LpNet& w, int j, const float* h1)
+{
+    const float* row = w.w2 + j * w.H;
+    float a = __ldg(&w.b2[j]);
+    for (int i = 0; i < w.H; ++i) a = __fmaf_rn(__ldg(&row[i]), h1[i], a);
+    return a > 0.0f ? a : 0.0f;
+}
+
+// Logit of output g: b3 then fused multiply-adds in ascending order.
+__device__ __forceinline__ float lp_logit(const LpNet& w, int g, const float* h2)
+{
+    const float* row = w.w3 + g * w.H;
+    float a = __ldg(&w.b3[g]);
+    for (int i = 0; i < w.H; ++i) a = __fmaf_rn(__ldg(&row[i]), h2[i], a);
+    return a;
+}
+
+// Output index of a destination mask (masks sorted on the device), or -1.
+__device__ __forceinline__ int lp_output(const StepParams& P, uint64_t mask)
+{
+    int lo = 0, hi = P.mlp_out;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&P.mlp_mask[mid]) < mask) lo = mid + 1; else hi = mid;
+    }
+    return (lo < P.mlp_out && __ldg(&P.mlp_mask[lo]) == mask) ? __ldg(&P.mlp_idx[lo]) : -1;
+}
+
+// Static weight of slot k.
+__device__ __forceinline__ int64_t slot_width(const Prog& prog, int k)
+{
+    return prog.stat[k].end - (k ? prog.stat[k - 1].end : 0);
+}
+
+// Q_k from the slot's exponential e (valid when has_out) and the softmax sum S.
+__device__ __forceinline__ int64_t lp_q(float e, bool has_out, float S, float eps, int64_t width, int64_t p_att)
+{
+    if (width <= 0) return 0;
+    int64_t L = 0;
+    if (has_out && S > 0.0f) {
+        const float q = __fdiv_rn(e, S);
+        L = (int64_t)floorf(__fmul_rn(__fmul_rn(__fsub_rn(1.0f, eps), q), 16777216.0f));
+    }
+    const int64_t St = (int64_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)eps, (double)width), (double)p_att),
+                                                16777216.0));
+    const int64_t Q = L + St;
+    return Q < 1 ? 1 : Q;
+}
+
+// The walker's randomness: two Philox calls keyed like its spawn draw with the
+// learned kind; V (24 bits) picks the slot, u_re and u_im (53 bits each) the
+// Bernoulli parts of the two channels.
+__device__ __forceinline__ void lp_draws(uint64_t key, int phase, int comp, uint32_t j, uint2 kd, uint32_t* V,
+                                         double* ure, double* uim)
+{
+    uint4 c = make_uint4((uint32_t)key, (uint32_t)(key >> 32), (uint32_t)phase | ((uint32_t)comp << 1) | (kKindLearned << 2),
+                         ((j >> 1) << 2) | ((j & 1u) << 1));
+    const uint4 a = philox10(c, kd);
+    c.w |= 1u;
+    const uint4 b = philox10(c, kd);
+    *V = a.x >> 8;
+    *ure = __dmul_rn((double)((((uint64_t)a.y) << 21) | (a.z >> 11)), 1.0 / 9007199254740992.0);
+    *uim = __dmul_rn((double)((((uint64_t)b.x) << 21) | (b.y >> 11)), 1.0 / 9007199254740992.0);
+}
+
+// Walkers on channel value v of a slot with proposal weight Q: floor(A) +
+// (u < frac A), A = |v| 2^24 / (Q p_att).
+__device__ __forceinline__ int64_t lp_count(int64_t v, int64_t Q, int64_t p_att, double u)
+{
+    const int64_t w = iabs64(v);
+    if (w == 0) return 0;
+    const double A = __ddiv_rn(__dmul_rn((double)w, 16777216.0), __dmul_rn((double)Q, (double)p_att));
+    const double fl = floor(A);
+    return (int64_t)fl + (u < __dsub_rn(A, fl) ? 1 : 0);
+}
+
+// Light parents under the learned proposal: one thread per candidate (an
+// attempting walker); the network is evaluated for the candidate's source,
+// and up to two records (Re, Im channel of the drawn destination) are staged.
+__global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
+{
+    __shared__ __align__(16) uint8_t sprog[2][kProgSmem];
+    __shared__ __align__(16) SRec sstage[kThreads / 32][kStage];
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const StepInfo inf = P.info[st->call_index];
+    const int cur = st->cur, prv = (cur + 2) % 3;
+    const Rec* src0 = P.pop[cur];
+    const Rec* src1 = P.pop[prv];
+    // one instance (the learned proposal takes no batch): both programs staged
+    const uint8_t* pb0 = stage_prog(prog_ptr(P, inf, 0, 0), sprog[0]);
+    const uint8_t* pb1 = stage_prog(prog_ptr(P, inf, 0, inf.ab2 ? 1 : 0), sprog[1]);
+    __syncthreads();
+    const LpNet net = lp_net(P);
+    const int64_t total = min(st->cand_total, P.cand_cap);
+    SRec* stage = sstage[warp];
+    int staged = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kThreads + warp * 32; base < total; base += stride) {
+        const int64_t i = base + lane;
+        SRec rec[2];
+        bool ok[2] = {false, false};
+        if (i < total) {
+            const uint4 cv = __ldcs((const uint4*)P.cand + i);
+            const uint64_t tf = ((uint64_t)cv.w << 32) | cv.z;
+            const int comp = (int)((tf >> 52) & 1u), phase = (int)((tf >> 53) & 1u);
+            const int non = (int)((tf >> 54) & 1u), sg = ((tf >> 55) & 1u) ? 1 : -1;
+            const uint32_t j = (uint32_t)(tf & kT52);
+            const uint64_t key = __ldg(&(phase ? src1 : src0)[cv.x].key);
+            const int n = P.seginfo[cv.y].n;
+            const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & (n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)));
+            const Prog prog = prog_at(phase ? pb1 : pb0);
+            const int64_t p_att = prog.h->p_att;
+            const int ns = prog.h->n_stat;
+            if (p_att >= (1ll << 52)) {
+                set_error(st, DERR_DT_TOO_LARGE);
+            } else {
+                const float tf32 = __double2float_rn(inf.t[phase]);
+                float h1[kMaxHidden], h2[kMaxHidden];
+                for (int q = 0; q < net.H; ++q) h1[q] = lp_h1(net, q, x, y, n, tf32);
+                for (int q = 0; q < net.H; ++q) h2[q] = lp_h2(net, q, h1);
+                // e[k]: logit, then its exponential; g[k] >= 0 where the slot has an output
+                float e[kMaxLearnedSlots];
+                int16_t g[kMaxLearnedSlots];
+                float m = -INFINITY;
+                for (int k = 0; k < ns; ++k) {
+                    g[k] = (int16_t)(slot_width(prog, k) > 0 ? lp_output(P, prog.stat[k].mask) : -1);
+                    if (g[k] >= 0) {
+                        e[k] = lp_logit(net, g[k], h2);
+                        if (e[k] > m) m = e[k];
+                    }
+                }
+                float S = 0.0f;
+                for (int k = 0; k < ns; ++k)
+                    if (g[k] >= 0) {
+                        e[k] = lp_exp(__fsub_rn(e[k], m));
+                        S = __fadd_rn(S, e[k]);
+                    }
+                int64_t sum = 0, qa = -1;
+                int arg = -1;
+                for (int k = 0; k < ns; ++k) {
+                    const int64_t w = slot_width(prog, k);
+                    if (w <= 0) continue;
+                    const int64_t Q = lp_q(e[k], g[k] >= 0, S, P.mlp_eps, w, p_att);
+                    sum += Q;
+                    if (arg < 0 || Q > qa) {
+                        arg = k;
+                        qa = Q;
+                    }
+                }
+                uint32_t V;
+                double u[2];
+                lp_draws(key, phase, comp, j, P.kd[cv.y], &V, &u[0], &u[1]);
+                int64_t cum = 0, Qk = 0;
+                int k = 0;
+                for (; k < ns; ++k) {
+                    const int64_t w = slot_width(prog, k);
+                    Qk = w <= 0 ? 0 : lp_q(e[k], g[k] >= 0, S, P.mlp_eps, w, p_att);
+                    if (k == arg) Qk += (1ll << 24) - sum;
+                    cum += Qk;
+                    if ((int64_t)V < cum) break;
+                }
+                if (k < ns) {
+                    int64_t v[2];
+                    value_at_mask(prog, prog.stat[k].mask, x, y, &v[0], &v[1]);
+                    for (int c = 0; c < 2; ++c) {
+                        const int64_t cnt = lp_count(v[c], Qk, p_att, u[c]);
+                        if (cnt == 0) continue;
+                        if (cnt > 0x7FFFFFFFll) {
+                            set_error(st, DERR_POP_OVERFLOW);
+                            continue;
+                        }
+                        ok[c] = true;
+                        rec[c] = make_spawn(key ^ prog.stat[k].mask, (int)cv.y, comp, c, v[c], sg, phase ? -1 : 1, non,
+                                            (int32_t)cnt);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t bal = __ballot_sync(kFull, ok[c]);
+            const int nrec = __popc(bal);
+            if (staged + nrec > kStage) {
+                warp_flush(stage, staged, P, lane);
+                staged = 0;
+            }
+            if (ok[c]) stage[staged + __popc(bal & ((1u << lane) - 1u))] = rec[c];
+            staged += nrec;
+            __syncwarp();
+        }
+    }
+    if (staged) warp_flush(stage, staged, P, lane);
+}
+
+// ---------------------------------------------------------------------------
 // Spawning, heavy parents: one CTA per chunk of kHeavyChunk walkers of one
 // parent component.  The column is evaluated once into shared memory as a
 // cumulative weight table; each spawned walker finds its interval by binary
@@ -791,8 +1069,11 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
 {
     __shared__ int64_t cum[2 * kMaxEntries];
     __shared__ int64_t vals[2 * kMaxEntries];
-    __shared__ int hist[2 * kMaxEntries];
+    __shared__ __align__(8) int hist[2 * kMaxEntries];
     __shared__ int64_t warp_tot[kThreads / 32];
+    __shared__ float s_h1[kMaxHidden], s_h2[kMaxHidden], s_e[kMaxLearnedSlots];
+    __shared__ int16_t s_g[kMaxLearnedSlots];
+    __shared__ float s_S;
     __shared__ unsigned long long s_base;
     __shared__ int s_nout;
     DevState* st = P.st;
@@ -803,6 +1084,8 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
     const StepInfo inf = P.info[ci];
     const int cur = st->cur, prv = (cur + 2) % 3;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // learned proposal: 64-bit walker counts per (slot, channel) bin, over hist
+    unsigned long long* lh = (unsigned long long*)hist;
 
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const HeavyItem it = P.heavy[item];
@@ -813,15 +1096,16 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         const Rec par = (it.phase ? P.pop[prv] : P.pop[cur])[it.parent];
         const uint32_t x = (uint32_t)(par.key >> n), y = (uint32_t)(par.key & ymask);
         // bins of the walkers' draw T: plain, two per destination entry (Re,
-        // Im; widths |Re L|, |Im L| over [0, P)); proposal, three per static
-        // slot (Re, Im and the rest of the slot's static weight, which spawns
-        // nothing; over [0, p_att))
-        const bool prop = P.proposal != 0;
+        // Im; widths |Re L|, |Im L| over [0, P)); static proposal, three per
+        // static slot (Re, Im and the rest of the slot's static weight, which
+        // spawns nothing; over [0, p_att)); learned proposal, two per slot
+        // (walker counts; the slot comes from the weights Q, not from T)
+        const bool prop = P.proposal == 1, learned = P.proposal == 2;
         int64_t Pw;
         int nb;
-        if (prop) {
+        if (prop || learned) {
             Pw = prog.h->p_att;
-            nb = 3 * prog.h->n_stat;
+            nb = (learned ? 2 : 3) * prog.h->n_stat;
         } else {
             int64_t sre, sim;
             Pw = column_weight(prog, x, y, &sre, &sim);
@@ -838,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
             if (threadIdx.x == 0) set_error(st, DERR_DT_TOO_LARGE);
             return;
         }
-        if (nb > 2 * kMaxEntries) {
+        if (nb > 2 * kMaxEntries || (learned && prog.h->n_stat > kMaxLearnedSlots)) {
             if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
             return;
         }
@@ -846,34 +1130,86 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
             for (int k = tid; k < prog.h->n_stat; k += kThreads) {
                 int64_t vr, vi;
                 value_at_mask(prog, prog.stat[k].mask, x, y, &vr, &vi);
-                const int64_t width = prog.stat[k].end - (k ? prog.stat[k - 1].end : 0);
+                const int64_t width = slot_width(prog, k);
                 vals[3 * k] = vr;
                 vals[3 * k + 1] = vi;
                 vals[3 * k + 2] = width - iabs64(vr) - iabs64(vi);   // no-spawn remainder
             }
-        for (int b = tid; b < nb; b += kThreads) hist[b] = 0;
-        __syncthreads();
-        // inclusive prefix of the bin widths (blocked per thread, then across threads)
-        const int per = (nb + kThreads - 1) / kThreads;
-        const int b0 = tid * per, b1 = min(nb, b0 + per);
-        int64_t acc = 0;
-        for (int b = b0; b < b1; ++b) acc += iabs64(vals[b]);
-        int64_t incl = acc;
+        const int ns = prog.h->n_stat;
+        if (learned) {
+            // the source's weights Q (cum[k], then their inclusive prefix)
+            const LpNet net = lp_net(P);
+            const float tf32 = __double2float_rn(inf.t[it.phase]);
+            for (int k = tid; k < ns; k += kThreads) {
+                int64_t vr, vi;
+                value_at_mask(prog, prog.stat[k].mask, x, y, &vr, &vi);
+                vals[2 * k] = vr;
+                vals[2 * k + 1] = vi;
+            }
+            for (int b = tid; b < nb; b += kThreads) lh[b] = 0ull;
+            if (tid < net.H) s_h1[tid] = lp_h1(net, tid, x, y, n, tf32);
+            __syncthreads();
+            if (tid < net.H) s_h2[tid] = lp_h2(net, tid, s_h1);
+            __syncthreads();
+            for (int k = tid; k < ns; k += kThreads) {
+                const int g = slot_width(prog, k) > 0 ? lp_output(P, prog.stat[k].mask) : -1;
+                s_g[k] = (int16_t)g;
+                if (g >= 0) s_e[k] = lp_logit(net, g, s_h2);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float m = -INFINITY;
+                for (int k = 0; k < ns; ++k)
+                    if (s_g[k] >= 0 && s_e[k] > m) m = s_e[k];
+                float S = 0.0f;
+                for (int k = 0; k < ns; ++k)
+                    if (s_g[k] >= 0) {
+                        s_e[k] = lp_exp(__fsub_rn(s_e[k], m));
+                        S = __fadd_rn(S, s_e[k]);
+                    }
+                s_S = S;
+            }
+            __syncthreads();
+            for (int k = tid; k < ns; k += kThreads)
+                cum[k] = lp_q(s_e[k], s_g[k] >= 0, s_S, P.mlp_eps, slot_width(prog, k), Pw);
+            __syncthreads();
+            if (tid == 0) {
+                int64_t sum = 0;
+                int arg = -1;
+                for (int k = 0; k < ns; ++k) {
+                    if (slot_width(prog, k) <= 0) continue;
+                    sum += cum[k];
+                    if (arg < 0 || cum[k] > cum[arg]) arg = k;
+                }
+                if (arg >= 0) cum[arg] += (1ll << 24) - sum;
+                for (int k = 1; k < ns; ++k) cum[k] += cum[k - 1];
+            }
+            __syncthreads();
+        } else {
+            for (int b = tid; b < nb; b += kThreads) hist[b] = 0;
+            __syncthreads();
+            // inclusive prefix of the bin widths (blocked per thread, then across threads)
+            const int per = (nb + kThreads - 1) / kThreads;
+            const int b0 = tid * per, b1 = min(nb, b0 + per);
+            int64_t acc = 0;
+            for (int b = b0; b < b1; ++b) acc += iabs64(vals[b]);
+            int64_t incl = acc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) warp_tot[warp] = incl;
+            __syncthreads();
+            int64_t woff = 0;
+            for (int w = 0; w < warp; ++w) woff += warp_tot[w];
+            int64_t run = woff + incl - acc;
+            for (int b = b0; b < b1; ++b) {
+                run += iabs64(vals[b]);
+                cum[b] = run;
+            }
+            __syncthreads();
         }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        int64_t woff = 0;
-        for (int w = 0; w < warp; ++w) woff += warp_tot[w];
-        int64_t run = woff + incl - acc;
-        for (int b = b0; b < b1; ++b) {
-            run += iabs64(vals[b]);
-            cum[b] = run;
-        }
-        __syncthreads();
 
         const int comp = it.comp;
         const int64_t m = iabs64(comp ? par.im : par.re);
@@ -891,6 +1227,24 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
                 const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
                 const int64_t T = (int64_t)(R >> 12);
                 if (T >= Pw) continue;
+                if (learned) {
+                    uint32_t V;
+                    double u[2];
+                    lp_draws(par.key, it.phase, comp, (uint32_t)(2 * j2 + h), kd, &V, &u[0], &u[1]);
+                    int lo = 0, hi = ns;   // first slot with cum > V
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (cum[mid] > (int64_t)V) hi = mid; else lo = mid + 1;
+                    }
+                    if (lo >= ns) continue;
+                    const int64_t Qk = cum[lo] - (lo ? cum[lo - 1] : 0);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int64_t cnt = lp_count(vals[2 * lo + c], Qk, Pw, u[c]);
+                        if (cnt) atomicAdd(&lh[2 * lo + c], (unsigned long long)cnt);
+                    }
+                    continue;
+                }
                 int lo = 0, hi = nb - 1; // first b with cum[b] > T
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
@@ -909,8 +1263,9 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         if (prop)   // the remainder bins spawn nothing
             for (int b = 3 * tid + 2; b < nb; b += 3 * kThreads) hist[b] = 0;
         __syncthreads();
+        auto count_of = [&](int b) -> int64_t { return learned ? (int64_t)lh[b] : (int64_t)hist[b]; };
         int my_n = 0;
-        for (int b = tid; b < nb; b += kThreads) my_n += hist[b] ? 1 : 0;
+        for (int b = tid; b < nb; b += kThreads) my_n += count_of(b) ? 1 : 0;
         int my_off = 0;
         if (my_n) my_off = atomicAdd(&s_nout, my_n);
         __syncthreads();
@@ -921,10 +1276,12 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         __syncthreads();
         int k = 0;
         for (int b = tid; b < nb; b += kThreads) {
-            if (!hist[b]) continue;
+            const int64_t cnt = count_of(b);
+            if (!cnt) continue;
+            if (cnt > 0x7FFFFFFFll) set_error(st, DERR_POP_OVERFLOW);
             const int chan = prop ? b % 3 : (b & 1);
-            const uint64_t mk = prop ? prog.stat[b / 3].mask : prog.ent[b >> 1].mask_key;
-            const SRec r = make_spawn(par.key ^ mk, it.seg, comp, chan, vals[b], sg, sigma, noninit, hist[b]);
+            const uint64_t mk = prop ? prog.stat[b / 3].mask : (learned ? prog.stat[b >> 1].mask : prog.ent[b >> 1].mask_key);
+            const SRec r = make_spawn(par.key ^ mk, it.seg, comp, chan, vals[b], sg, sigma, noninit, (int32_t)cnt);
             const int64_t pos = (int64_t)s_base + my_off + k;
             if (pos < P.spawn_cap) P.spawn[pos] = r;
             ++k;
@@ -2141,7 +2498,7 @@ const char* const kKernelNames[kNumTimedKernels] = {
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_choose = 0, g_grid_heavy = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
+int g_grid_spawn = 0, g_grid_choose = 0, g_grid_learned = 0, g_grid_heavy = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
 
 int resident(const void* fn, int smem, int sms, int threads = kThreads)
 {
@@ -2161,6 +2518,7 @@ void configure_kernels()
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     g_grid_spawn = resident((const void*)k_spawn_draw, 0, sms);
     g_grid_choose = resident((const void*)k_spawn_choose, 0, sms);
+    g_grid_learned = resident((const void*)k_spawn_learned, 0, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms, kMergeThreads);
@@ -2181,7 +2539,10 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(1);
     k_spawn_draw<<<cap(g_grid_spawn), kThreads, 0, stream>>>(P);
     mark(2);
-    k_spawn_choose<<<cap(g_grid_choose), kThreads, 0, stream>>>(P);
+    if (P.proposal == 2)   // timed in the choose slot
+        k_spawn_learned<<<cap(g_grid_learned), kThreads, 0, stream>>>(P);
+    else
+        k_spawn_choose<<<cap(g_grid_choose), kThreads, 0, stream>>>(P);
     mark(3);
     k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
     mark(4);

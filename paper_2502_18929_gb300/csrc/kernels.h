@@ -16,6 +16,8 @@ constexpr int kMergeThreads = kThreads + 64;         // merge CTA: 8 merging war
 constexpr int kHeavyWalkers = 256;                   // parents above this go to the heavy path
 constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
+constexpr int kMaxLearnedSlots = 256;                // destinations per column (learned proposal)
+constexpr int kMaxHidden = 64;                       // hidden width of the learned proposal's network
 constexpr int kMaxPasses = 12;
 constexpr int kBucketBits = 20;                    // largest bucket digit of the spawn sort
 constexpr int kCtrMerge = kMaxPasses;                // tile counter index of the merge
@@ -25,6 +27,7 @@ constexpr uint32_t kTagStep = 0x53544550u;
 constexpr uint32_t kTagInit = 0x494E4954u;
 constexpr uint32_t kKindSpawn = 0u;
 constexpr uint32_t kKindInit = 1u;
+constexpr uint32_t kKindLearned = 2u;
 
 struct HeavyItem {
     int64_t parent;  // index inside its population slot
@@ -100,7 +103,12 @@ struct StepParams {
     const SegInfo* seginfo;   // per segment
     const InstInfo* inst;     // per instance
     int ninst;
-    int proposal;         // 0: exact |L|-weighted destination choice; 1: static-weight proposal
+    int proposal;         // 0: exact |L|-weighted destination choice; 1: static; 2: learned proposal
+    const float* mlp;     // learned proposal: w1, b1, w2, b2, w3, b3 back to back
+    const uint64_t* mlp_mask;   // output masks, sorted
+    const int32_t* mlp_idx;     // output index of each sorted mask
+    int mlp_in, mlp_hidden, mlp_out;
+    float mlp_eps;
 };
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same

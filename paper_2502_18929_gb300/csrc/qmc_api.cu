@@ -156,6 +156,13 @@ StepParams params(qmc_ctx* c)
     P.inst = c->d_inst;
     P.ninst = (int)c->inst.size();
     P.proposal = c->proposal;
+    P.mlp = c->d_mlp;
+    P.mlp_mask = c->d_mlp_mask;
+    P.mlp_idx = c->d_mlp_idx;
+    P.mlp_in = c->mlp_in;
+    P.mlp_hidden = c->mlp_hidden;
+    P.mlp_out = c->mlp_out;
+    P.mlp_eps = c->mlp_eps;
     return P;
 }
 
@@ -453,7 +460,8 @@ void qmc_destroy(qmc_ctx* ctx)
                     ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
-                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst};
+                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_mask,
+                    ctx->d_mlp_idx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
@@ -492,13 +500,58 @@ int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, cons
 int qmc_set_proposal(qmc_ctx* ctx, int32_t kind)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
-    if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC)
+    if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC && kind != QMC_PROPOSAL_LEARNED)
         return fail(ctx, QMC_ERR_INVALID_ARG, "unknown proposal kind");
+    if (kind == QMC_PROPOSAL_LEARNED && !ctx->d_mlp)
+        return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
     if (ctx->proposal != kind) {
         ctx->proposal = kind;
         ctx->graph_dirty = true;
     }
     return QMC_OK;
+}
+
+int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* m)
+{
+    if (!ctx || !m) return QMC_ERR_INVALID_ARG;
+    if (ctx->batch) return fail(ctx, QMC_ERR_STATE, "the learned proposal takes a context of one instance");
+    const int n = ctx->inst[0].n, I = m->n_in, H = m->n_hidden, G = m->n_out;
+    if (I != 2 * n + 1 || H < 1 || H > 64 || G < 1 || G > 4096 || !(m->eps > 0.0f) || m->eps > 1.0f ||
+        !m->out_masks || !m->w1 || !m->b1 || !m->w2 || !m->b2 || !m->w3 || !m->b3)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "network sizes or pointers out of range");
+    std::vector<std::pair<uint64_t, int32_t>> order(G);
+    for (int g = 0; g < G; ++g) order[g] = {m->out_masks[g], g};
+    std::sort(order.begin(), order.end());
+    for (int g = 1; g < G; ++g)
+        if (order[g].first == order[g - 1].first) return fail(ctx, QMC_ERR_INVALID_ARG, "output masks repeat");
+    std::vector<uint64_t> masks(G);
+    std::vector<int32_t> idx(G);
+    for (int g = 0; g < G; ++g) {
+        masks[g] = order[g].first;
+        idx[g] = order[g].second;
+    }
+    std::vector<float> w;
+    w.insert(w.end(), m->w1, m->w1 + (size_t)H * I);
+    w.insert(w.end(), m->b1, m->b1 + H);
+    w.insert(w.end(), m->w2, m->w2 + (size_t)H * H);
+    w.insert(w.end(), m->b2, m->b2 + H);
+    w.insert(w.end(), m->w3, m->w3 + (size_t)G * H);
+    w.insert(w.end(), m->b3, m->b3 + G);
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_mlp, (int64_t)w.size())) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_mlp_mask, G)) != QMC_OK) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_mlp_idx, G)) != QMC_OK) return rc;
+    CK(cudaMemcpyAsync(ctx->d_mlp, w.data(), w.size() * 4, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(ctx->d_mlp_mask, masks.data(), (size_t)G * 8, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(ctx->d_mlp_idx, idx.data(), (size_t)G * 4, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    ctx->mlp_in = I;
+    ctx->mlp_hidden = H;
+    ctx->mlp_out = G;
+    ctx->mlp_eps = m->eps;
+    ctx->graph_dirty = true;
+    return leave(ctx);
 }
 
 int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, const double* re,
@@ -693,6 +746,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         const ProgHeader* h = (const ProgHeader*)tmp.data();
         if (h->n_entry > kMaxEntries)
             return fail(ctx, QMC_ERR_INVALID_ARG, "column has more destinations than the heavy path holds");
+        if (ctx->proposal == QMC_PROPOSAL_LEARNED && h->n_stat > kMaxLearnedSlots)
+            return fail(ctx, QMC_ERR_INVALID_ARG, "learned proposal: more than 256 destinations per column");
         const size_t slot = 2 * (size_t)k + pass;
         if (last_off[slot] >= 0 && last_blob[slot] == tmp) {
             *off_out = last_off[slot];
@@ -714,6 +769,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
                          (i > 0 || (ctx->prev_valid && ctx->dt_last == dt));
         const double tp = i > 0 ? t0 + (double)(i - 1) * dt : ctx->t_prev;
         info[i].ab2 = ab2 ? 1 : 0;
+        info[i].t[0] = ti;
+        info[i].t[1] = ab2 ? tp : ti;
         for (int k = 0; k < ni; ++k) {
             int rc = add_prog(k, 0, ti, ab2 ? dt * 1.5 : dt, &tab[2 * k]);
             tab[2 * k + 1] = tab[2 * k];

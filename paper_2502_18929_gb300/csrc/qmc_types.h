@@ -181,6 +181,7 @@ struct StepInfo {
                           // program offset (pass 1 repeats pass 0 when absent)
     int32_t ab2;          // 1: AB2 step (pass 1 over N(t - dt) present)
     int32_t pad;
+    double t[2];          // time of pass 0 (t) and pass 1 (t - dt): input of the learned proposal
 };
 
 // Per population vector (segment): its problem instance, that instance's

@@ -29,13 +29,14 @@ ERR_CHECKPOINT = -11
 
 EULER = 0
 AB2 = 1
+PROPOSAL_EXACT, PROPOSAL_STATIC, PROPOSAL_LEARNED = 0, 1, 2
 
 EXPORTED = [
     "qmc_create", "qmc_destroy", "qmc_last_error", "qmc_load_schedule", "qmc_init_populations",
     "qmc_set_populations", "qmc_set_clock", "qmc_get_clock", "qmc_step", "qmc_spawn_prob_bound",
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
-    "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal",
+    "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
 ]
 
 
@@ -118,6 +119,7 @@ def lib():
         L.qmc_counters.argtypes = [vp, C.c_int32, vp]
         L.qmc_step_launches.argtypes = [vp, vp]
         L.qmc_set_proposal.argtypes = [vp, C.c_int32]
+        L.qmc_set_proposal_mlp.argtypes = [vp, C.POINTER(Mlp)]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -146,6 +148,12 @@ def current_stream_handle() -> int:
     except Exception:
         pass
     return 0
+
+
+class Mlp(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_out", C.c_int32), ("eps", C.c_float),
+                ("out_masks", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p),
+                ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
 
 
 class Instance(C.Structure):
@@ -235,8 +243,18 @@ class QMC:
         return self
 
     def set_proposal(self, kind: int):
-        """Spawn choice: EXACT (0, the paper's) or STATIC (1, static-weight proposal)."""
+        """Spawn choice: EXACT (0, the paper's), STATIC (1, static-weight
+        proposal) or LEARNED (2, after set_mlp)."""
         self._check(self.L.qmc_set_proposal(self.h, kind), "qmc_set_proposal")
+
+    def set_mlp(self, net):
+        """Network of the learned proposal: a dict with out_masks (uint64), w1,
+        b1, w2, b2, w3, b3 (float32, row-major) and eps."""
+        arrs = [np.ascontiguousarray(net["out_masks"], dtype=np.uint64)] + \
+            [np.ascontiguousarray(net[k], dtype=np.float32) for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+        H, I = arrs[1].shape
+        m = Mlp(I, H, len(arrs[0]), float(net["eps"]), *[a.ctypes.data for a in arrs])
+        self._check(self.L.qmc_set_proposal_mlp(self.h, C.byref(m)), "qmc_set_proposal_mlp")
 
     def load_schedule(self, prob):
         a = _schedule_arrays(prob)
