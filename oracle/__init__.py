@@ -8,4 +8,6 @@ shares no code with the CUDA library (``paper_2502_18929_gb300``).
 * ``oracle.py``    -- ctypes wrapper around it.
 * ``dense.py``     -- dense FP64 Liouvillian of Eq. (2) and the deterministic
   Euler / AB2 recursions, for tiny n.
+* ``learn.py``     -- FP64 training events, loss and gradient of the learned
+  proposal's network (the library's extension; not in the paper).
 """

@@ -47,6 +47,8 @@ def lib():
         L.orc_column.restype = C.c_int
         L.orc_column.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
                                  C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_static.restype = C.c_int
+        L.orc_static.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p]
         L.orc_state_new.restype = C.c_void_p
         L.orc_state_new.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
                                     C.c_int64]
@@ -120,6 +122,17 @@ class OracleProblem:
         if n < 0:
             raise RuntimeError(f"orc_column failed: {n}")
         return mask[:n].copy(), qre[:n].copy(), qim[:n].copy()
+
+    def static(self, t: float, dt_eff: float):
+        """Static weights of dt_eff * L(t): (mask, weight) sorted by mask, in
+        units of 2^-52 (a bound on |Re L| + |Im L| of that destination)."""
+        cap = 4096
+        mask = np.zeros(cap, dtype=np.uint64)
+        w = np.zeros(cap, dtype=np.int64)
+        n = lib().orc_static(self.handle, t, dt_eff, cap, mask.ctypes.data, w.ctypes.data)
+        if n < 0:
+            raise RuntimeError(f"orc_static failed: {n}")
+        return mask[:n].copy(), w[:n].copy()
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -407,6 +407,23 @@ int orc_column(const void* pp, uint64_t x, uint64_t y, double t, double dt_eff, 
     return len;
 }
 
+/* Exported for tests: the static weights (see build_static), sorted by
+ * mask.  Returns the number of entries (only cap are written) or < 0. */
+int orc_static(const void* pp, double t, double dt_eff, int cap, uint64_t* mask, int64_t* weight)
+{
+    const problem* p = (const problem*)pp;
+    column col = {0, 0, 0};
+    int rc = build_static(p, t, dt_eff, &col);
+    if (rc != ORC_OK) { free(col.e); return rc; }
+    for (int i = 0; i < col.len && i < cap; ++i) {
+        mask[i] = col.e[i].mask;
+        weight[i] = col.e[i].v.re;
+    }
+    int len = col.len;
+    free(col.e);
+    return len;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Populations                                                             */
 /* ------------------------------------------------------------------------ */
