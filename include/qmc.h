@@ -213,6 +213,52 @@ typedef struct {
  * Errors: INVALID_ARG (sizes, masks not distinct), STATE (a batch), OOM. */
 int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* mlp);
 
+/* ---- Training of the learned proposal (no counterpart in the paper) ----
+ * The network is trained towards the heat-bath choice of the plain method
+ * (destination share |Re L| + |Im L| over the column's sum) on events the
+ * method generates.  Sizes come from the network loaded by
+ * qmc_set_proposal_mlp; parameters are packed w1 [H x I], b1 [H],
+ * w2 [H x H], b2 [H], w3 [G x H], b3 [G] (qmc_learn_param_count floats).
+ * Every array argument is DEVICE memory owned by the caller; per-event
+ * arrays are feature-major: element (row r, event e) at r * ld + e. */
+
+/* Number of packed parameters.  Errors: STATE (no network). */
+int qmc_learn_param_count(qmc_ctx* ctx, int64_t* n_params);
+
+/* Training events from N(t) at the current time t: E = min(K, max_events)
+ * parent records, record floor(e K / max_events) for event e (all K records
+ * when K <= max_events), over the vectors' records in vector order.  Per
+ * event: feat [2n + 1][max_events] (x bits, y bits as 1.0 / 0.0, then
+ * float(t)); target [G][max_events]: for each output whose destination has a
+ * positive static weight, float(double(w_k) / double(W)) with w_k = |Re| + |Im|
+ * of the quantised column element of dt L(t) and W the sum over those
+ * outputs (0 when W = 0), -1 for the other outputs; weight [max_events]:
+ * float(|re| + |im|) of the parent, 0 when W = 0.  *n_events (host) = E.
+ * Synchronises.  Errors: INVALID_ARG, STATE (no network, schedule or
+ * populations), COEF_RANGE, OOM. */
+int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, float* target, float* weight,
+                     int64_t* n_events);
+
+/* Weighted cross-entropy of the network's softmax over each event's present
+ * outputs (target >= 0) against the targets, sum_e w_e CE_e / sum_e w_e, and
+ * its gradient with respect to the packed parameters `params` (forward and
+ * backward on the GPU in single precision, sums over events in a fixed
+ * order).  grad: device, n_params floats; *loss (host) in double.
+ * Synchronises.  Errors: INVALID_ARG (n_events outside [1, ld], events x
+ * (4 H + G + 1) above 2^28), STATE, OOM. */
+int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
+                   int64_t ld, int64_t n_events, float* grad, double* loss);
+
+/* One Adam step (Kingma & Ba, 2015) on params with first and second moments
+ * m, v (device, n_params floats each; zero before step t = 1).  Asynchronous
+ * on the context's stream.  Errors: INVALID_ARG (count or hyperparameters). */
+int qmc_learn_adam(qmc_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t n_params, int64_t t,
+                   float lr, float beta1, float beta2, float eps);
+
+/* Copy trained parameters (device, packed) into the network the learned
+ * proposal evaluates.  Errors: STATE (no network). */
+int qmc_learn_load(qmc_ctx* ctx, const float* params);
+
 /* Load H(t) and the Lindblad operators [Eq. (1)].  The library expands
  * -i[H, rho] and gamma (L rho L^dag - 1/2 {L^dag L, rho}) into Pauli
  * superoperator terms and, per step, into the column tables of Eq. (2).

@@ -45,6 +45,11 @@ struct qmc_ctx {
     uint64_t* d_mlp_mask = nullptr;
     int32_t* d_mlp_idx = nullptr;
     int mlp_in = 0, mlp_hidden = 0, mlp_out = 0;
+    uint8_t* d_learn_prog = nullptr;   // training: program at the current time
+    int64_t learn_prog_cap = 0;
+    float* d_learn_scratch = nullptr;  // training: per-event activations and gradients
+    int64_t learn_scratch_cap = 0;
+    double* d_learn_small = nullptr;   // training: [0] event count (int64), [1] weight sum, [2] loss
     float mlp_eps = 0.f;
     bool has_pop = false;
     qmc::SegInfo* d_seginfo = nullptr;

@@ -118,6 +118,40 @@ void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int step_launch_count(const StepParams& P);   // kernels launch_step issues
+
+// Training events of the learned proposal (learn.cu).  Device pointers.
+struct LearnArgs {
+    const DevState* st;
+    Rec* pop[3];
+    const uint8_t* prog;        // program of dt L(t) at the current time
+    const uint64_t* masks;      // the network's output masks, sorted
+    const int32_t* idx;         // output index of each sorted mask
+    int n, G;
+    double t;
+    int64_t max_events, ld;
+    float* feat;                // [2n + 1][ld]
+    float* target;              // [G][ld]
+    float* weight;              // [ld]
+    int64_t* n_events;          // out: events written
+};
+
+// Loss and gradient of the learned proposal's network over events.
+struct LearnGrad {
+    const float* params;        // packed w1, b1, w2, b2, w3, b3
+    const float* feat;
+    const float* target;
+    const float* weight;
+    int64_t ld, E;
+    int I, H, G;
+    float *h1t, *h2t, *dzt, *d2t, *d1t, *lossv;   // scratch [rows][ld]
+    double* wsum;
+};
+
+void launch_learn_events(const LearnArgs& A, cudaStream_t stream);
+void launch_learn_grad(const LearnGrad& A, float* grad, double* loss, cudaStream_t stream);
+int learn_grad_launch_count();
+void launch_learn_adam(float* p, const float* g, float* m, float* v, int64_t n, int64_t t, float lr, float b1,
+                       float b2, float eps, cudaStream_t stream);
 void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, const int64_t* off, int nseg,
                  const SegInfo* seginfo, Rec* dst, int* bad, cudaStream_t stream);
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);

@@ -461,7 +461,7 @@ void qmc_destroy(qmc_ctx* ctx)
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
                     ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_mask,
-                    ctx->d_mlp_idx};
+                    ctx->d_mlp_idx, ctx->d_learn_prog, ctx->d_learn_scratch, ctx->d_learn_small};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
@@ -551,6 +551,128 @@ int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* m)
     ctx->mlp_out = G;
     ctx->mlp_eps = m->eps;
     ctx->graph_dirty = true;
+    return leave(ctx);
+}
+
+namespace {
+int64_t mlp_param_count(const qmc_ctx* c)
+{
+    const int64_t I = c->mlp_in, H = c->mlp_hidden, G = c->mlp_out;
+    return H * I + H + H * H + H + G * H + G;
+}
+} // namespace
+
+int qmc_learn_param_count(qmc_ctx* ctx, int64_t* n_params)
+{
+    if (!ctx || !n_params) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    *n_params = mlp_param_count(ctx);
+    return QMC_OK;
+}
+
+int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, float* target, float* weight,
+                     int64_t* n_events)
+{
+    if (!ctx || !feat || !target || !weight || !n_events) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!(dt > 0.0) || max_events < 1) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and max_events >= 1");
+    std::vector<uint8_t> blob;
+    int rc = build_program(ctx->inst[0].sched, ctx->t, dt, &blob);
+    if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
+    if (rc != QMC_OK) return rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if ((int64_t)blob.size() > ctx->learn_prog_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_learn_prog, (int64_t)blob.size())) != QMC_OK) return rc;
+        ctx->learn_prog_cap = (int64_t)blob.size();
+    }
+    if (!ctx->d_learn_small && (rc = dalloc(ctx, &ctx->d_learn_small, 4)) != QMC_OK) return rc;
+    CK(cudaMemcpyAsync(ctx->d_learn_prog, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->work));
+    LearnArgs A;
+    A.st = ctx->d_state;
+    for (int s = 0; s < 3; ++s) A.pop[s] = ctx->d_pop[s];
+    A.prog = ctx->d_learn_prog;
+    A.masks = ctx->d_mlp_mask;
+    A.idx = ctx->d_mlp_idx;
+    A.n = ctx->inst[0].n;
+    A.G = ctx->mlp_out;
+    A.t = ctx->t;
+    A.max_events = max_events;
+    A.ld = max_events;
+    A.feat = feat;
+    A.target = target;
+    A.weight = weight;
+    A.n_events = (int64_t*)ctx->d_learn_small;
+    launch_learn_events(A, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(n_events, ctx->d_learn_small, 8, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return leave(ctx);
+}
+
+int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
+                   int64_t ld, int64_t n_events, float* grad, double* loss)
+{
+    if (!ctx || !params || !feat || !target || !weight || !grad || !loss) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    if (n_events < 1 || ld < n_events) return fail(ctx, QMC_ERR_INVALID_ARG, "need 1 <= n_events <= ld");
+    const int64_t H = ctx->mlp_hidden, G = ctx->mlp_out;
+    const int64_t rows = 4 * H + G + 1;
+    if (rows * ld > ((int64_t)1 << 28)) return fail(ctx, QMC_ERR_INVALID_ARG, "events x (4 hidden + outputs) above 2^28");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if (rows * ld > ctx->learn_scratch_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_learn_scratch, rows * ld)) != QMC_OK) return rc;
+        ctx->learn_scratch_cap = rows * ld;
+    }
+    if (!ctx->d_learn_small && (rc = dalloc(ctx, &ctx->d_learn_small, 4)) != QMC_OK) return rc;
+    LearnGrad A;
+    A.params = params;
+    A.feat = feat;
+    A.target = target;
+    A.weight = weight;
+    A.ld = ld;
+    A.E = n_events;
+    A.I = ctx->mlp_in;
+    A.H = (int)H;
+    A.G = (int)G;
+    float* s = ctx->d_learn_scratch;
+    A.h1t = s;
+    A.h2t = s + H * ld;
+    A.d2t = s + 2 * H * ld;
+    A.d1t = s + 3 * H * ld;
+    A.dzt = s + 4 * H * ld;
+    A.lossv = s + (4 * H + G) * ld;
+    A.wsum = ctx->d_learn_small + 1;
+    launch_learn_grad(A, grad, ctx->d_learn_small + 2, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(loss, ctx->d_learn_small + 2, 8, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return leave(ctx);
+}
+
+int qmc_learn_adam(qmc_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t n_params, int64_t t,
+                   float lr, float beta1, float beta2, float eps)
+{
+    if (!ctx || !params || !grad || !m || !v) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    if (n_params != mlp_param_count(ctx) || t < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(ctx, QMC_ERR_INVALID_ARG, "Adam: parameter count or hyperparameters out of range");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    launch_learn_adam(params, grad, m, v, n_params, t, lr, beta1, beta2, eps, ctx->work);
+    CK(cudaGetLastError());
+    return leave(ctx);
+}
+
+int qmc_learn_load(qmc_ctx* ctx, const float* params)
+{
+    if (!ctx || !params) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    CK(cudaMemcpyAsync(ctx->d_mlp, params, (size_t)mlp_param_count(ctx) * 4, cudaMemcpyDeviceToDevice, ctx->work));
     return leave(ctx);
 }
 

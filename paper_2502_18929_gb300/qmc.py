@@ -37,6 +37,7 @@ EXPORTED = [
     "qmc_observables", "qmc_step_history", "qmc_export", "qmc_overlap", "qmc_checkpoint", "qmc_restore",
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
+    "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
 ]
 
 
@@ -120,6 +121,12 @@ def lib():
         L.qmc_step_launches.argtypes = [vp, vp]
         L.qmc_set_proposal.argtypes = [vp, C.c_int32]
         L.qmc_set_proposal_mlp.argtypes = [vp, C.POINTER(Mlp)]
+        L.qmc_learn_param_count.argtypes = [vp, vp]
+        L.qmc_learn_events.argtypes = [vp, C.c_double, C.c_int64, vp, vp, vp, vp]
+        L.qmc_learn_grad.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, vp, vp]
+        L.qmc_learn_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                     C.c_float]
+        L.qmc_learn_load.argtypes = [vp, vp]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -255,6 +262,44 @@ class QMC:
         H, I = arrs[1].shape
         m = Mlp(I, H, len(arrs[0]), float(net["eps"]), *[a.ctypes.data for a in arrs])
         self._check(self.L.qmc_set_proposal_mlp(self.h, C.byref(m)), "qmc_set_proposal_mlp")
+        self._mlp_out = len(arrs[0])
+
+    # -- training of the learned proposal (device tensors) ---------------------
+    def learn_param_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.L.qmc_learn_param_count(self.h, C.byref(n)), "qmc_learn_param_count")
+        return n.value
+
+    def learn_events(self, dt: float, max_events: int):
+        """Events from N(t): (feat [2n+1, max_events], target [G, max_events],
+        weight [max_events]) float32 CUDA tensors and the event count."""
+        import torch
+        G = self._mlp_out
+        feat = torch.empty((2 * self.n + 1, max_events), dtype=torch.float32, device="cuda")
+        target = torch.empty((G, max_events), dtype=torch.float32, device="cuda")
+        weight = torch.empty(max_events, dtype=torch.float32, device="cuda")
+        ne = C.c_int64()
+        self._check(self.L.qmc_learn_events(self.h, dt, max_events, feat.data_ptr(), target.data_ptr(),
+                                            weight.data_ptr(), C.byref(ne)), "qmc_learn_events")
+        return feat, target, weight, ne.value
+
+    def learn_grad(self, params, feat, target, weight, n_events: int):
+        """(loss, grad) of the packed parameters over the first n_events events."""
+        import torch
+        grad = torch.empty_like(params)
+        loss = C.c_double()
+        self._check(self.L.qmc_learn_grad(self.h, params.data_ptr(), feat.data_ptr(), target.data_ptr(),
+                                          weight.data_ptr(), feat.shape[1], n_events, grad.data_ptr(),
+                                          C.byref(loss)), "qmc_learn_grad")
+        return loss.value, grad
+
+    def learn_adam(self, params, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8):
+        self._check(self.L.qmc_learn_adam(self.h, params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                          params.numel(), t, lr, beta1, beta2, eps), "qmc_learn_adam")
+
+    def learn_load(self, params):
+        self._check(self.L.qmc_learn_load(self.h, params.data_ptr()), "qmc_learn_load")
 
     def load_schedule(self, prob):
         a = _schedule_arrays(prob)
