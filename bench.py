@@ -360,13 +360,15 @@ def run_gpu(args, rank: int, world: int):
         avg_ms = kernel_ms[top] / max(1, launches)
         bytes_per_launch = kernel_bytes(top, cp) / max(1, launches)
         achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-        units = {"k_spawn_draw": cp["k_cur"] + cp["k_prev"] + cp["candidates"],
-                 "k_merge": cp["k_cur"] + cp["spawns"] + cp["k_next"]}.get(top, 0) / max(1, launches)
+        unit_counts = {"k_spawn_draw": (cp["k_cur"] + cp["k_prev"] + cp["candidates"]) / max(1, cp["steps"]),
+                       "k_merge": (cp["k_cur"] + cp["spawns"] + cp["k_next"]) / max(1, cp["steps"])}
+        units = unit_counts.get(top, 0) * cp["steps"] / max(1, launches)
         traffic = measured_traffic(top, units) if units else None
         roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": None if traffic is None else round(traffic), "avg_launch_ms": round(avg_ms, 5),
                 "algorithmic_bytes_per_launch": round(bytes_per_launch),
+                "units_per_launch": {k: round(v) for k, v in unit_counts.items()},
                 "kernel_share": {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}}
 
     # end to end through the public API: a fresh context, inputs uploaded from
