@@ -78,6 +78,7 @@ struct qmc_ctx {
     int64_t* d_tile_start = nullptr;
     qmc::MTileG* d_mtiles = nullptr;
     unsigned long long* d_merge_status = nullptr;
+    int64_t launches_since_clear = 0;   // step launches since the look-back status arrays were cleared
     int64_t merge_tiles_cap = 0;
     SegStats* d_segacc = nullptr;
     SegStats* d_history = nullptr;

@@ -94,9 +94,23 @@ __device__ __forceinline__ void st_vol(unsigned long long* p, unsigned long long
     *(volatile unsigned long long*)p = v;
 }
 
-__device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, uint32_t flag, uint32_t v)
+// Look-back status word: epoch (26 bits) << 38 | flag (2 bits) << 36 | value
+// (36 bits).  Epochs advance by 16 per step; the host clears the status
+// arrays at least every 2^20 step launches, so a stale word never carries the
+// current epoch.
+constexpr unsigned long long kLbValMask = (1ull << 36) - 1ull;
+constexpr uint32_t kLbEpochMask = (1u << 26) - 1u;
+
+__device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, uint32_t flag, unsigned long long v)
 {
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (v & 0x3FFFFFFFu);
+    return ((unsigned long long)(epoch & kLbEpochMask) << 38) | ((unsigned long long)flag << 36) | (v & kLbValMask);
+}
+
+__device__ __forceinline__ uint32_t lb_flag(unsigned long long v) { return (uint32_t)(v >> 36) & 3u; }
+
+__device__ __forceinline__ bool lb_ready(unsigned long long v, uint32_t epoch)
+{
+    return (uint32_t)(v >> 38) == (epoch & kLbEpochMask) && lb_flag(v) != 0u;
 }
 
 // Wait (bounded) until *addr carries this epoch and a flag; returns false on
@@ -106,7 +120,7 @@ __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned
 {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         unsigned long long v = ld_vol(addr);
-        if ((uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u) {
+        if (lb_ready(v, epoch)) {
             *out = v;
             return true;
         }
@@ -134,7 +148,7 @@ __device__ unsigned long long warp_lookback(const unsigned long long* status, in
         for (uint32_t it = 0; it < kSpinLimit; ++it) {
             if (!ready) {
                 v = ld_vol(status + j);
-                ready = (uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u;
+                ready = lb_ready(v, epoch);
             }
             if (__all_sync(kFull, ready)) break;
             if (read_error(st) == DERR_TIMEOUT) break;
@@ -144,10 +158,10 @@ __device__ unsigned long long warp_lookback(const unsigned long long* status, in
             if (lane == 0) set_timeout(st, site, t);
             break;
         }
-        const bool incl = j >= 0 && ((v >> 30) & 3u) == kFlagIncl;
+        const bool incl = j >= 0 && lb_flag(v) == kFlagIncl;
         const uint32_t bal = __ballot_sync(kFull, incl);
         const int stop = bal ? __ffs(bal) - 1 : 31;          // lanes 0..stop contribute
-        unsigned long long c = (j >= 0 && lane <= stop) ? (v & 0x3FFFFFFFull) : 0ull;
+        unsigned long long c = (j >= 0 && lane <= stop) ? (v & kLbValMask) : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         excl += c;
@@ -1421,14 +1435,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
                     for (int w = 0; w < 8; ++w) {
                         if (done || hi - w < 0) continue;
                         unsigned long long x = v[w];
-                        if (!((uint32_t)(x >> 32) == epoch && ((x >> 30) & 3u) != 0u)) {
+                        if (!lb_ready(x, epoch)) {
                             if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st, 1u, hi - w)) {
                                 done = true;
                                 continue;
                             }
                         }
-                        excl += (unsigned int)(x & 0x3FFFFFFFu);
-                        if (((x >> 30) & 3u) == kFlagIncl) done = true;
+                        excl += (unsigned int)(x & kLbValMask);
+                        if (lb_flag(x) == kFlagIncl) done = true;
                     }
                 }
                 st_vol(my, lb_word(epoch, kFlagIncl, excl + tot));
@@ -1553,7 +1567,7 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(StepParams P)
         } else {
             if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, tot));
             excl = warp_lookback(P.bscan_status, tile, epoch, st, lane, 8u);
-            if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, (uint32_t)(excl + tot)));
+            if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, excl + tot));
         }
         if (lane == 0) s_excl = excl;
     }
@@ -2120,7 +2134,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
             unsigned long long excl = 0;
             if (sl.t > 0) {
                 excl = warp_lookback(P.merge_status, sl.t, epoch, st, lane, 2u);
-                if (lane == 0) st_vol(P.merge_status + sl.t, lb_word(epoch, kFlagIncl, (uint32_t)(excl + sl.count)));
+                if (lane == 0) st_vol(P.merge_status + sl.t, lb_word(epoch, kFlagIncl, excl + (unsigned long long)sl.count));
             }
             if (lane == 0) {
                 if (sl.t == T - 1) {
@@ -2220,7 +2234,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
         merge_bar();           // raw runs read before the next walk rewrites them
         if (tid == 0) {
             // the tile's aggregate (inclusive prefix for the first tile), at once
-            st_vol(P.merge_status + t, lb_word(epoch, t == 0 ? kFlagIncl : kFlagAgg, (uint32_t)tile_count));
+            st_vol(P.merge_status + t, lb_word(epoch, t == 0 ? kFlagIncl : kFlagAgg, (unsigned long long)tile_count));
             MSlot sl;
             sl.t = t;
             sl.count = tile_count;

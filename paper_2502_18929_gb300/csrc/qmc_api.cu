@@ -22,7 +22,14 @@ using namespace qmc;
 
 namespace {
 
-constexpr int64_t kLookbackValueLimit = (1ll << 30) - 1;
+// Records per population slot and spawn records per step: parent indices are
+// 32-bit and look-back values 36-bit; 2^31 - 1 keeps every signed 32-bit
+// intermediate in range.
+constexpr int64_t kLookbackValueLimit = (1ll << 31) - 1;
+// Look-back status words carry a 26-bit epoch that advances by 16 per step
+// launch; clearing the status arrays at least every 2^20 launches keeps a
+// stale word from ever carrying the current epoch.
+constexpr int64_t kStatusClearLaunches = (int64_t)1 << 20;
 
 int fail(qmc_ctx* c, int code, const std::string& why)
 {
@@ -182,11 +189,28 @@ int leave(qmc_ctx* ctx)
     return QMC_OK;
 }
 
+// Account for n step launches about to be issued on the work stream, clearing
+// the look-back status arrays first when the epoch could otherwise wrap.
+int note_launches(qmc_ctx* ctx, int64_t n)
+{
+    if (ctx->launches_since_clear + n > kStatusClearLaunches) {
+        if (ctx->d_sort_status)
+            CK(cudaMemsetAsync(ctx->d_sort_status, 0, (size_t)ctx->sort_tiles_cap * 256 * 8, ctx->work));
+        if (ctx->d_merge_status)
+            CK(cudaMemsetAsync(ctx->d_merge_status, 0, (size_t)ctx->merge_tiles_cap * 8, ctx->work));
+        if (ctx->d_bscan_status)
+            CK(cudaMemsetAsync(ctx->d_bscan_status, 0, (size_t)8 << (kBucketBits - 10), ctx->work));
+        ctx->launches_since_clear = 0;
+    }
+    ctx->launches_since_clear += n;
+    return QMC_OK;
+}
+
 int grow_spawn(qmc_ctx* ctx, int64_t need)
 {
     int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
     if (cap > kLookbackValueLimit) cap = kLookbackValueLimit;
-    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "spawn records exceed 2^30 - 1 per step");
+    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "spawn records exceed 2^31 - 1 per step");
     int rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn, cap)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn_alt, cap)) != QMC_OK) return rc;
@@ -229,7 +253,7 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
 {
     int64_t cap = std::max<int64_t>(need + need / 2, 1 << 12);
     if (cap > kLookbackValueLimit) cap = kLookbackValueLimit;
-    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "population exceeds 2^30 - 1 records");
+    if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "population exceeds 2^31 - 1 records");
     if (ctx->cfg.max_records > 0 && need > ctx->cfg.max_records)
         return fail(ctx, QMC_ERR_CAPACITY, "population exceeds max_records");
     if (ctx->cfg.max_records > 0) cap = std::min(cap, ctx->cfg.max_records);
@@ -916,7 +940,10 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     int64_t done = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
         if ((rc = capture_graph(ctx)) != QMC_OK) return rc;
-        for (int64_t i = done; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->graph, ctx->work));
+        for (int64_t i = done; i < nsteps; ++i) {
+            if ((rc = note_launches(ctx, 1)) != QMC_OK) return rc;
+            CK(cudaGraphLaunch(ctx->graph, ctx->work));
+        }
         DevState hs;
         CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
         CK(cudaStreamSynchronize(ctx->work));
@@ -1270,6 +1297,7 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
         back.call_index = 0;
         CK(cudaMemcpyAsync(ctx->d_state, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->work));
         StepParams P = params(ctx);
+        if ((rc = note_launches(ctx, 1)) != QMC_OK) break;
         launch_step(P, ctx->grid, ctx->work, ev);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->work));
