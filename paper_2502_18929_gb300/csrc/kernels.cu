@@ -1075,9 +1075,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
 // ---------------------------------------------------------------------------
 // Spawning, heavy parents: one CTA per chunk of kHeavyChunk walkers of one
 // parent component.  The column is evaluated once into shared memory as a
-// cumulative weight table; each spawned walker finds its interval by binary
-// search; counts are aggregated per (destination, channel) and emitted as one
-// record each.
+// cumulative weight table; each spawned walker finds its interval from a
+// table of the first bin of every 2^s-wide slice of [0, P) (at most 1024
+// slices) and a short forward scan, usually one or two cumulative weights;
+// counts are aggregated per (destination, channel) and emitted as one record
+// each.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
 {
@@ -1090,6 +1092,7 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
     __shared__ float s_S;
     __shared__ unsigned long long s_base;
     __shared__ int s_nout;
+    __shared__ uint16_t sidx[1025];   // first bin of each 2^ish-wide slice of [0, Pw)
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int64_t nitems = min(st->heavy_total, P.heavy_cap);
@@ -1224,6 +1227,22 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
             }
             __syncthreads();
         }
+        // index of the first bin of each 2^s-wide slice of [0, Pw)
+        int ish = 0;
+        if (!learned && nb > 0) {
+            while ((Pw >> ish) >= 1024) ++ish;
+            const int nbk = (int)(Pw >> ish) + 1;
+            for (int k = tid; k < nbk; k += kThreads) {
+                const int64_t t0 = (int64_t)k << ish;
+                int lo = 0, hi = nb - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cum[mid] > t0) hi = mid; else lo = mid + 1;
+                }
+                sidx[k] = (uint16_t)lo;
+            }
+            __syncthreads();
+        }
 
         const int comp = it.comp;
         const int64_t m = iabs64(comp ? par.im : par.re);
@@ -1259,11 +1278,8 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
                     }
                     continue;
                 }
-                int lo = 0, hi = nb - 1; // first b with cum[b] > T
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cum[mid] > T) hi = mid; else lo = mid + 1;
-                }
+                int lo = sidx[T >> ish];   // first b with cum[b] > T
+                while (lo < nb - 1 && cum[lo] <= T) ++lo;
                 atomicAdd(&hist[lo], 1);
             }
         }
