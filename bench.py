@@ -1,7 +1,7 @@
 """Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload spread32|spread32s|dd12|ghz4|ghzN|ghzNi|batch256]
+                    [--workload spread32|spread32s|dd12|dd12i|ghz4|ghzN|ghzNi|batch256]
 
 One "step" is one dt step of every population vector through the whole hot
 path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
@@ -56,10 +56,12 @@ def load_peaks():
 # workloads
 # ---------------------------------------------------------------------------
 def workload(name: str):
-    if name == "dd12":
+    if name in ("dd12", "dd12i"):
         prob = P.dd_ring(12, seed=0, t_end=20.0)
-        return dict(name="dd12", desc="staggered-XX DD, 12-qubit ring, ZZ crosstalk, X basis",
-                    prob=prob, nseg=64, n_diag=10**6, dt=0.005, t_end=20.0, rho0=P.rho_basis(0))
+        xi = 1e-3 if name == "dd12i" else 0.0
+        return dict(name=name, desc="staggered-XX DD, 12-qubit ring, ZZ crosstalk, X basis" +
+                    (", initiator xi = 1e-3" if xi else ""),
+                    prob=prob, nseg=64, n_diag=10**6, dt=0.005, t_end=20.0, rho0=P.rho_basis(0), xi=xi)
     if name == "ghz4":
         prob = P.ghz_circuit(4)
         return dict(name="ghz4", desc="GHZ-4 preparation", prob=prob, nseg=16, n_diag=10**4, dt=0.01,

@@ -8,6 +8,7 @@
 //                   network's destination weights and the walker counts
 //   k_spawn_heavy   the same for heavy parents, one CTA per walker chunk,
 //                   aggregated per destination in shared memory
+//                   (k_spawn_heavy_learned under the learned proposal)
 //   k_sort_hist     digit histograms of all LSD radix passes
 //   k_sort_scatter  one stable LSD pass, decoupled look-back, smem exchange
 //   k_spawn_segoff  segment boundaries of the sorted spawns
@@ -1081,7 +1082,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
 // counts are aggregated per (destination, channel) and emitted as one record
 // each.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
+template <bool kLearned>
+__device__ __forceinline__ void spawn_heavy(const StepParams& P)
 {
     __shared__ int64_t cum[2 * kMaxEntries];
     __shared__ int64_t vals[2 * kMaxEntries];
@@ -1093,6 +1095,7 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
     __shared__ unsigned long long s_base;
     __shared__ int s_nout;
     __shared__ uint16_t sidx[1025];   // first bin of each 2^ish-wide slice of [0, Pw)
+    __shared__ int64_t s_col[3];      // P, Re and Im of the diagonal element of the parent's column
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int64_t nitems = min(st->heavy_total, P.heavy_cap);
@@ -1117,15 +1120,23 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         // static slot (Re, Im and the rest of the slot's static weight, which
         // spawns nothing; over [0, p_att)); learned proposal, two per slot
         // (walker counts; the slot comes from the weights Q, not from T)
-        const bool prop = P.proposal == 1, learned = P.proposal == 2;
+        const bool prop = P.proposal == 1, learned = kLearned;
         int64_t Pw;
         int nb;
         if (prop || learned) {
             Pw = prog.h->p_att;
             nb = (learned ? 2 : 3) * prog.h->n_stat;
         } else {
-            int64_t sre, sim;
-            Pw = column_weight(prog, x, y, &sre, &sim);
+            // the column's weight and diagonal element, once per chunk
+            if (tid == 0) {
+                int64_t a, b;
+                s_col[0] = column_weight(prog, x, y, &a, &b);
+                s_col[1] = a;
+                s_col[2] = b;
+            }
+            __syncthreads();
+            Pw = s_col[0];
+            const int64_t sre = s_col[1], sim = s_col[2];
             nb = 2 * prog.h->n_entry;
             if (nb <= 2 * kMaxEntries)
                 for (int e = tid; e < prog.h->n_entry; e += kThreads) {
@@ -1227,10 +1238,12 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
             }
             __syncthreads();
         }
-        // index of the first bin of each 2^s-wide slice of [0, Pw)
+        // index of the first bin of each 2^s-wide slice of [0, Pw): about
+        // eight slices per bin, at most 1024
         int ish = 0;
         if (!learned && nb > 0) {
-            while ((Pw >> ish) >= 1024) ++ish;
+            const int64_t slices = nb < 128 ? 8 * nb : 1024;
+            while ((Pw >> ish) >= slices) ++ish;
             const int nbk = (int)(Pw >> ish) + 1;
             for (int k = tid; k < nbk; k += kThreads) {
                 const int64_t t0 = (int64_t)k << ish;
@@ -1249,6 +1262,7 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         const int64_t w_lo = (int64_t)it.chunk * kHeavyChunk;
         const int64_t w_hi = min(m, w_lo + kHeavyChunk);
         const uint2 kd = P.kd[it.seg];
+        const uint64_t b12 = (uint64_t)Pw << 12;
         for (int64_t j2 = w_lo / 2 + tid; 2 * j2 < w_hi; j2 += kThreads) {
             const uint4 w = philox10(
                 make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
@@ -1258,8 +1272,8 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
             for (int h = 0; h < 2; ++h) {
                 if (2 * j2 + h >= w_hi) break;
                 const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
+                if (R >= b12) continue;   // T = R >> 12 >= P
                 const int64_t T = (int64_t)(R >> 12);
-                if (T >= Pw) continue;
                 if (learned) {
                     uint32_t V;
                     double u[2];
@@ -1319,6 +1333,11 @@ __global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P)
         __syncthreads();
     }
 }
+
+// The plain and static-proposal kernel carries none of the learned
+// proposal's state (fewer registers, more resident CTAs).
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P) { spawn_heavy<false>(P); }
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy_learned(StepParams P) { spawn_heavy<true>(P); }
 
 // ---------------------------------------------------------------------------
 // LSD radix sort of spawn records by (segment, key).
@@ -2528,7 +2547,7 @@ const char* const kKernelNames[kNumTimedKernels] = {
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_choose = 0, g_grid_learned = 0, g_grid_heavy = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
+int g_grid_spawn = 0, g_grid_choose = 0, g_grid_learned = 0, g_grid_heavy = 0, g_grid_heavy_learned = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
 
 int resident(const void* fn, int smem, int sms, int threads = kThreads)
 {
@@ -2550,6 +2569,7 @@ void configure_kernels()
     g_grid_choose = resident((const void*)k_spawn_choose, 0, sms);
     g_grid_learned = resident((const void*)k_spawn_learned, 0, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
+    g_grid_heavy_learned = resident((const void*)k_spawn_heavy_learned, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms, kMergeThreads);
     g_grid_bsmall = resident((const void*)k_bucket_sort_small, kSmallSortSmem, sms);
@@ -2574,7 +2594,10 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     else
         k_spawn_choose<<<cap(g_grid_choose), kThreads, 0, stream>>>(P);
     mark(3);
-    k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
+    if (P.proposal == 2)
+        k_spawn_heavy_learned<<<cap(g_grid_heavy_learned), kThreads, 0, stream>>>(P);
+    else
+        k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
     mark(4);
     if (P.sort_mode) {
         k_bucket_hist<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
