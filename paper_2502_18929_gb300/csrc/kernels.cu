@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
 
 // One thread per candidate: exact weight P of the parent's column, the spawn
 // test T < P, and the destination.  Programs are staged in shared memory.
-__global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
+__global__ void __launch_bounds__(kThreads, 4) k_spawn_choose(StepParams P)
 {
     __shared__ __align__(16) uint8_t sprog[2][kProgSmem];
     __shared__ __align__(16) SRec sstage[kThreads / 32][kStage];
