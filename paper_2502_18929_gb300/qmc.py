@@ -274,7 +274,7 @@ class QMC:
         """Events from N(t): (feat [2n+1, max_events], target [G, max_events],
         weight [max_events]) float32 CUDA tensors and the event count."""
         import torch
-        G = self._mlp_out
+        G = getattr(self, "_mlp_out", 1)   # without a network the library reports the error
         feat = torch.empty((2 * self.n + 1, max_events), dtype=torch.float32, device="cuda")
         target = torch.empty((G, max_events), dtype=torch.float32, device="cuda")
         weight = torch.empty(max_events, dtype=torch.float32, device="cuda")
