@@ -327,6 +327,37 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
 int qmc_step_launches(const qmc_ctx* ctx, int32_t* launches);
 const char* qmc_kernel_name(int32_t i);
 
+/* Launch shapes of the step (not in the paper; results never depend on
+ * them: every draw is keyed by step, vector, key and walker, and the heavy
+ * and light spawn paths produce the same spawns).
+ *   max_ctas        CTAs of every persistent kernel (0: fill the GPU)
+ *   heavy_walkers   parents with more walkers take the per-parent heavy path
+ *                   (16 .. 2^20; default 256)
+ *   bucket_records  target records per bucket of the spawn sort, which sets
+ *                   the bucket digit's width (4 .. 256; default 24) */
+typedef struct {
+    int32_t max_ctas;
+    int32_t heavy_walkers;
+    int32_t bucket_records;
+    int32_t pad;
+} qmc_tuning;
+
+/* Set or read the launch shapes.  Errors: INVALID_ARG (out of range). */
+int qmc_set_tuning(qmc_ctx* ctx, const qmc_tuning* tuning);
+int qmc_get_tuning(const qmc_ctx* ctx, qmc_tuning* tuning);
+
+/* Autotuner: from the current state, time nsteps steps of size dt (1 .. 64)
+ * under candidate launch shapes, one knob at a time (CTAs per kernel: the
+ * whole GPU, two or one per SM; heavy threshold 64, 256, 1024 walkers;
+ * bucket target 12, 24, 48 records), keep a candidate that is at least 2 %
+ * faster, and leave the best shapes set.  The populations, clock and
+ * counters are restored after every trial, so the state afterwards is the
+ * state before (the steps after the call are bit-identical to those without
+ * it).  *out (host, may be NULL) receives the chosen shapes.  Needs room for a
+ * copy of N(t) and N(t - dt) on the device.  Errors: STATE, INVALID_ARG, OOM,
+ * and any error of the steps themselves. */
+int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out);
+
 /* Upper bound of the spawn probability p over all states for a step of size
  * dt at time t (AB2 factor 3/2 included): sum over the expanded terms of
  * |Re c| + |Im c| times |rate| times dt.  Host-only; used to choose dt. */

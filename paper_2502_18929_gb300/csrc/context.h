@@ -28,6 +28,8 @@ struct qmc_ctx {
     int device = 0;
     int sm_count = 0;
     int grid = 0;
+    int heavy_walkers = qmc::kHeavyWalkers;   // launch shapes (qmc_set_tuning)
+    int bucket_records = 24;
 
     // Problem instances: one for a context made by qmc_create, several for
     // qmc_batch_create.  Instance i owns segments [seg0, seg0 + nvec).

@@ -464,7 +464,7 @@ __device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCan
     const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
     const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
     const uint64_t mtot = (uint64_t)are + aim;
-    const bool heavy = mtot > (uint64_t)kHeavyWalkers;
+    const bool heavy = mtot > (uint64_t)P.heavy_walkers;
     const int noninit = (sd.init_min > 0 && (int64_t)mtot < sd.init_min) ? 1 : 0;
     if (heavy) emit_heavy(P, j, phase, seg, are, aim);
     const uint32_t pre = heavy ? 0u : (are + 1u) >> 1, pim = heavy ? 0u : (aim + 1u) >> 1;

@@ -13,7 +13,7 @@ constexpr int kSortTile = kThreads * kSortItems;     // 2048 records
 constexpr int kMergeItems = 5;                       // 5 x 16 B stride: lanes spread over all bank groups
 constexpr int kMergeTile = kThreads * kMergeItems;   // 1280 merged items
 constexpr int kMergeThreads = kThreads + 64;         // merge CTA: 8 merging warps, a producer and a publisher
-constexpr int kHeavyWalkers = 256;                   // parents above this go to the heavy path
+constexpr int kHeavyWalkers = 256;                   // default: parents above this take the heavy path
 constexpr int64_t kHeavyChunk = 32768;               // walkers per heavy work item
 constexpr int kMaxEntries = 1024;                    // destinations per column (heavy path)
 constexpr int kMaxLearnedSlots = 256;                // destinations per column (learned proposal)
@@ -105,6 +105,7 @@ struct StepParams {
     int ninst;
     int proposal;         // 0: exact |L|-weighted destination choice; 1: static; 2: learned proposal
     const float* mlp;     // learned proposal: w1, b1, w2, b2, w3, b3 back to back
+    int heavy_walkers;    // parents with more walkers take the heavy path
     const uint64_t* mlp_mask;   // output masks, sorted
     const int32_t* mlp_idx;     // output index of each sorted mask
     int mlp_in, mlp_hidden, mlp_out;

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <chrono>
 
 #include "../../include/qmc.h"
 #include "kernels.h"
@@ -148,7 +149,7 @@ StepParams params(qmc_ctx* c)
         // kBucketBits bits, never more than the sort key has)
         const int total = P.seg_bits + 2 * c->cfg.n_qubits;
         int want = 10;
-        while (want < kBucketBits && ((int64_t)24 << want) < c->spawn_cap) ++want;
+        while (want < kBucketBits && ((int64_t)c->bucket_records << want) < c->spawn_cap) ++want;
         if (want < P.seg_bits) want = P.seg_bits;
         P.bucket_bits = total < want ? total : want;
         P.bucket_kb = P.bucket_bits - P.seg_bits;
@@ -163,6 +164,7 @@ StepParams params(qmc_ctx* c)
     P.inst = c->d_inst;
     P.ninst = (int)c->inst.size();
     P.proposal = c->proposal;
+    P.heavy_walkers = c->heavy_walkers;
     P.mlp = c->d_mlp;
     P.mlp_mask = c->d_mlp_mask;
     P.mlp_idx = c->d_mlp_idx;
@@ -697,6 +699,139 @@ int qmc_learn_load(qmc_ctx* ctx, const float* params)
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     CK(cudaMemcpyAsync(ctx->d_mlp, params, (size_t)mlp_param_count(ctx) * 4, cudaMemcpyDeviceToDevice, ctx->work));
+    return leave(ctx);
+}
+
+int qmc_set_tuning(qmc_ctx* ctx, const qmc_tuning* t)
+{
+    if (!ctx || !t) return QMC_ERR_INVALID_ARG;
+    if (t->max_ctas < 0 || t->heavy_walkers < 16 || t->heavy_walkers > (1 << 20) || t->bucket_records < 4 ||
+        t->bucket_records > 256)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "launch shapes out of range");
+    ctx->grid = t->max_ctas;
+    ctx->heavy_walkers = t->heavy_walkers;
+    ctx->bucket_records = t->bucket_records;
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
+int qmc_get_tuning(const qmc_ctx* ctx, qmc_tuning* t)
+{
+    if (!ctx || !t) return QMC_ERR_INVALID_ARG;
+    t->max_ctas = ctx->grid;
+    t->heavy_walkers = ctx->heavy_walkers;
+    t->bucket_records = ctx->bucket_records;
+    t->pad = 0;
+    return QMC_OK;
+}
+
+int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
+    if (!(dt > 0.0) || nsteps < 1 || nsteps > 64) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0, 1 <= nsteps <= 64");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    // snapshot of N(t), N(t - dt), their offsets, the device state and the clock
+    DevState hs0;
+    CK(cudaMemcpyAsync(&hs0, ctx->d_state, sizeof(hs0), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int nseg = ctx->cfg.n_segments;
+    const int slot[2] = {hs0.cur, (hs0.cur + 2) % 3};
+    Rec* keep[2] = {nullptr, nullptr};
+    int64_t* keep_off[2] = {nullptr, nullptr};
+    auto release = [&]() {
+        for (int w = 0; w < 2; ++w) {
+            if (keep[w]) cudaFree(keep[w]);
+            if (keep_off[w]) cudaFree(keep_off[w]);
+        }
+    };
+    for (int w = 0; w < 2; ++w) {
+        const int64_t cnt = hs0.count[slot[w]];
+        if (cudaMalloc((void**)&keep[w], (size_t)std::max<int64_t>(cnt, 1) * sizeof(Rec)) != cudaSuccess ||
+            cudaMalloc((void**)&keep_off[w], (size_t)(nseg + 1) * 8) != cudaSuccess) {
+            cudaGetLastError();
+            release();
+            return fail(ctx, QMC_ERR_OOM, "autotune: no room for a copy of the populations");
+        }
+        if (cnt) CK(cudaMemcpyAsync(keep[w], ctx->d_pop[slot[w]], cnt * sizeof(Rec), cudaMemcpyDeviceToDevice, ctx->work));
+        CK(cudaMemcpyAsync(keep_off[w], ctx->d_segoff[slot[w]], (size_t)(nseg + 1) * 8, cudaMemcpyDeviceToDevice,
+                           ctx->work));
+    }
+    const uint64_t step0 = ctx->step;
+    const double t0 = ctx->t, tp0 = ctx->t_prev, dl0 = ctx->dt_last;
+    const bool pv0 = ctx->prev_valid;
+    auto restore = [&]() -> int {
+        // buffers may have grown (new pointers, larger capacity) during a trial
+        for (int w = 0; w < 2; ++w) {
+            const int64_t cnt = hs0.count[slot[w]];
+            if (cnt) CK(cudaMemcpyAsync(ctx->d_pop[slot[w]], keep[w], cnt * sizeof(Rec), cudaMemcpyDeviceToDevice,
+                                        ctx->work));
+            CK(cudaMemcpyAsync(ctx->d_segoff[slot[w]], keep_off[w], (size_t)(nseg + 1) * 8, cudaMemcpyDeviceToDevice,
+                               ctx->work));
+        }
+        DevState now;
+        CK(cudaMemcpyAsync(&now, ctx->d_state, sizeof(now), cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        DevState back = hs0;
+        back.seq = now.seq;   // look-back epochs only move forward
+        back.error = 0;
+        CK(cudaMemcpyAsync(ctx->d_state, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        ctx->step = step0;
+        ctx->t = t0;
+        ctx->t_prev = tp0;
+        ctx->dt_last = dl0;
+        ctx->prev_valid = pv0;
+        return QMC_OK;
+    };
+    qmc_tuning best;
+    qmc_get_tuning(ctx, &best);
+    auto trial = [&](const qmc_tuning& tu, double* ms) -> int {
+        int r;
+        if ((r = qmc_set_tuning(ctx, &tu)) != QMC_OK) return r;
+        if ((r = restore()) != QMC_OK) return r;
+        if ((r = capture_graph(ctx)) != QMC_OK) return r;   // not part of the timed steps
+        CK(cudaStreamSynchronize(ctx->work));
+        const auto a = std::chrono::steady_clock::now();
+        r = qmc_step(ctx, dt, nsteps);
+        if (r == QMC_OK) CK(cudaStreamSynchronize(ctx->work));
+        const auto b = std::chrono::steady_clock::now();
+        *ms = r == QMC_OK ? std::chrono::duration<double, std::milli>(b - a).count() : 1e300;
+        return QMC_OK;
+    };
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    double best_ms = 0.0;
+    // the first trial also builds the step graph and warms the caches: time it twice
+    if ((rc = trial(best, &best_ms)) != QMC_OK || (rc = trial(best, &best_ms)) != QMC_OK) {
+        release();
+        return rc;
+    }
+    const int32_t ctas[3] = {0, 2 * sms, sms};
+    const int32_t heavy[3] = {64, 256, 1024};
+    const int32_t bucket[3] = {12, 24, 48};
+    for (int knob = 0; knob < 3 && rc == QMC_OK; ++knob) {
+        for (int v = 0; v < 3 && rc == QMC_OK; ++v) {
+            qmc_tuning cand = best;
+            int32_t* field = knob == 0 ? &cand.max_ctas : (knob == 1 ? &cand.heavy_walkers : &cand.bucket_records);
+            const int32_t value = knob == 0 ? ctas[v] : (knob == 1 ? heavy[v] : bucket[v]);
+            if (*field == value) continue;
+            *field = value;
+            double ms = 0.0;
+            if ((rc = trial(cand, &ms)) != QMC_OK) break;
+            if (ms < 0.98 * best_ms) {
+                best = cand;
+                best_ms = ms;
+            }
+        }
+    }
+    if (rc == QMC_OK) rc = qmc_set_tuning(ctx, &best);
+    if (rc == QMC_OK) rc = restore();
+    release();
+    if (rc != QMC_OK) return rc;
+    if (out) *out = best;
     return leave(ctx);
 }
 

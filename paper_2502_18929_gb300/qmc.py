@@ -38,6 +38,7 @@ EXPORTED = [
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
+    "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune",
 ]
 
 
@@ -127,6 +128,9 @@ def lib():
         L.qmc_learn_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_float,
                                      C.c_float]
         L.qmc_learn_load.argtypes = [vp, vp]
+        L.qmc_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.qmc_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.qmc_autotune.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(Tuning)]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -155,6 +159,11 @@ def current_stream_handle() -> int:
     except Exception:
         pass
     return 0
+
+
+class Tuning(C.Structure):
+    _fields_ = [("max_ctas", C.c_int32), ("heavy_walkers", C.c_int32), ("bucket_records", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class Mlp(C.Structure):
@@ -263,6 +272,23 @@ class QMC:
         m = Mlp(I, H, len(arrs[0]), float(net["eps"]), *[a.ctypes.data for a in arrs])
         self._check(self.L.qmc_set_proposal_mlp(self.h, C.byref(m)), "qmc_set_proposal_mlp")
         self._mlp_out = len(arrs[0])
+
+    # -- launch shapes ----------------------------------------------------------
+    def set_tuning(self, max_ctas: int = 0, heavy_walkers: int = 256, bucket_records: int = 24):
+        t = Tuning(max_ctas, heavy_walkers, bucket_records, 0)
+        self._check(self.L.qmc_set_tuning(self.h, C.byref(t)), "qmc_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.L.qmc_get_tuning(self.h, C.byref(t)), "qmc_get_tuning")
+        return {"max_ctas": t.max_ctas, "heavy_walkers": t.heavy_walkers, "bucket_records": t.bucket_records}
+
+    def autotune(self, dt: float, nsteps: int = 4) -> dict:
+        """Time candidate launch shapes from the current state (which is kept)
+        and leave the fastest set; returns them."""
+        t = Tuning()
+        self._check(self.L.qmc_autotune(self.h, dt, nsteps, C.byref(t)), "qmc_autotune")
+        return {"max_ctas": t.max_ctas, "heavy_walkers": t.heavy_walkers, "bucket_records": t.bucket_records}
 
     # -- training of the learned proposal (device tensors) ---------------------
     def learn_param_count(self) -> int:
