@@ -117,13 +117,25 @@ def load_inputs(sim, wl, inputs):
     return int(keys.numel() * 8 + re.numel() * 4 + im.numel() * 4 + counts.nbytes)
 
 
-def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist):
+def piece_dt(pl, step: int) -> float:
+    """Step size of the plan piece holding step `step`."""
+    idx = 0
+    for t0, d, n in pl:
+        if step < idx + n:
+            return d
+        idx += n
+    return pl[-1][1]
+
+
+def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist, tuning=None):
     import torch
     from paper_2502_18929_gb300 import qmc
     prob = wl["prob"]
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
                   initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
     sim.load_schedule(prob)
+    if tuning is not None:
+        sim.set_tuning(**tuning)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -303,6 +315,10 @@ def run_gpu(args, rank: int, world: int):
     load_inputs(sim, wl, inputs)
     run_range(sim, pl, 0, W)
     torch.cuda.synchronize()
+    tuning = None
+    if args.autotune:
+        # launch shapes timed from the warmed-up state, which the tuner restores
+        tuning = sim.autotune(piece_dt(pl, W), 3)
     sim.counters(reset=True)
     nkeys_start = int(sim.observables()[:, 0].sum())
 
@@ -377,7 +393,7 @@ def run_gpu(args, rank: int, world: int):
     # pinned host memory, every step, and a D2H read of each call's per-step
     # observables (the step's result), timed on the host clock
     sim.close()
-    e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist)
+    e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist, tuning)
     if dist is not None:
         tt = torch.tensor([ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])],
                           dtype=torch.float64, device="cuda")
@@ -409,7 +425,8 @@ def run_gpu(args, rank: int, world: int):
                    "key_steps_per_s": c["k_next"] * world / (ms_all * 1e-3),
                    "l2": ("inputs larger than L2" if ws > L2_BYTES else
                           "working set below L2 (no flush between steps)"),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch_shapes": tuning if tuning is not None else "default"},
         "e2e": {"value": e2e_w / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d_bytes"] / (W + K),
                 "d2h_bytes_per_step": e2e["d2h_bytes"] / (W + K), "steps": W + K,
                 "includes": "input upload from pinned host memory, all warm-up and timed steps, "
@@ -591,6 +608,8 @@ def main():
     ap.add_argument("--workload", default="spread32")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time candidate launch shapes after the warm-up (state kept) and use the fastest")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
