@@ -110,3 +110,22 @@ def test_learned_proposal_one_step_mean():
     se = diff.std(0, ddof=1) / np.sqrt(V) + 1e-9
     z = np.abs(diff.mean(0)) / se
     assert z.max() < 4.8, z.max()
+
+
+def test_learned_proposal_with_an_empty_column():
+    """After the only pulse has ended no term is active: the static column is
+    empty, nothing attempts and the population stays as it was (the learned
+    weights of an empty column are never indexed)."""
+    prob = P.Problem(n=2, name="h-pulse")
+    P.add_hadamard_pulse(prob, 0, 0.0, 1.0)
+    sim = O.OracleSim(prob, 2, seed=3, integrator=O.EULER, n_diag=500)
+    sim.set_mlp(P.random_network(prob, hidden=4, seed=1, eps=0.5))
+    sim.set_proposal(2)
+    sim.init([(0, 0, 0.6, 0.0), (1, 1, 0.4, 0.0), (0, 1, 0.2, 0.1)])
+    before = [sim.population(s) for s in range(2)]
+    sim.set_clock(150, 1.5)
+    assert sim.step(0.01, 5) == O.OK
+    for s in range(2):
+        k0, r0, i0 = before[s]
+        k1, r1, i1 = sim.population(s)
+        assert np.array_equal(k0, k1) and np.array_equal(r0, r1) and np.array_equal(i0, i1)
