@@ -117,6 +117,18 @@ def load_inputs(sim, wl, inputs):
     return int(keys.numel() * 8 + re.numel() * 4 + im.numel() * 4 + counts.nbytes)
 
 
+def set_proposal(sim, prob, kind: str):
+    """Choice rule of the spawn step: the paper's exact rule, the static-weight
+    proposal, or the learned proposal with an untrained network (32 hidden
+    units, static share 0.1)."""
+    from paper_2502_18929_gb300 import qmc
+    if kind == "static":
+        sim.set_proposal(qmc.PROPOSAL_STATIC)
+    elif kind == "learned":
+        sim.set_mlp(P.random_network(prob, hidden=32, seed=0, eps=0.1))
+        sim.set_proposal(qmc.PROPOSAL_LEARNED)
+
+
 def piece_dt(pl, step: int) -> float:
     """Step size of the plan piece holding step `step`."""
     idx = 0
@@ -127,13 +139,14 @@ def piece_dt(pl, step: int) -> float:
     return pl[-1][1]
 
 
-def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist, tuning=None):
+def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist, tuning=None, proposal="exact"):
     import torch
     from paper_2502_18929_gb300 import qmc
     prob = wl["prob"]
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
                   initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
     sim.load_schedule(prob)
+    set_proposal(sim, prob, proposal)
     if tuning is not None:
         sim.set_tuning(**tuning)
     torch.cuda.synchronize()
@@ -304,6 +317,7 @@ def run_gpu(args, rank: int, world: int):
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
                   initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
     sim.load_schedule(prob)
+    set_proposal(sim, prob, args.proposal)
     pl = step_list(wl)
     total = planner.total_steps(pl)
     W = args.warmup
@@ -393,7 +407,7 @@ def run_gpu(args, rank: int, world: int):
     # pinned host memory, every step, and a D2H read of each call's per-step
     # observables (the step's result), timed on the host clock
     sim.close()
-    e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist, tuning)
+    e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist, tuning, args.proposal)
     if dist is not None:
         tt = torch.tensor([ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])],
                           dtype=torch.float64, device="cuda")
@@ -426,7 +440,8 @@ def run_gpu(args, rank: int, world: int):
                    "l2": ("inputs larger than L2" if ws > L2_BYTES else
                           "working set below L2 (no flush between steps)"),
                    "parallelism": f"replicas x{world}",
-                   "launch_shapes": tuning if tuning is not None else "default"},
+                   "launch_shapes": tuning if tuning is not None else "default",
+                   "proposal": args.proposal},
         "e2e": {"value": e2e_w / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d_bytes"] / (W + K),
                 "d2h_bytes_per_step": e2e["d2h_bytes"] / (W + K), "steps": W + K,
                 "includes": "input upload from pinned host memory, all warm-up and timed steps, "
@@ -608,6 +623,8 @@ def main():
     ap.add_argument("--workload", default="spread32")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--proposal", default="exact", choices=["exact", "static", "learned"],
+                    help="spawn choice rule (learned: an untrained network)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes after the warm-up (state kept) and use the fastest")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
