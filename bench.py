@@ -117,6 +117,19 @@ def load_inputs(sim, wl, inputs):
     return int(keys.numel() * 8 + re.numel() * 4 + im.numel() * 4 + counts.nbytes)
 
 
+def reduce_over_ranks(dist, values, device):
+    """Whole-job figures of replicas: values = (ms, walker-steps, e2e seconds,
+    e2e walker-steps) of this rank; returns the max of the times and the sum of
+    the counts over all ranks (no data moves between ranks otherwise)."""
+    import torch
+    tt = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm_ = tt.clone()
+    dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm_[1].item(), mx[2].item(), sm_[3].item()
+
+
 def set_proposal(sim, prob, kind: str):
     """Choice rule of the spawn step: the paper's exact rule, the static-weight
     proposal, or the learned proposal with an untrained network (32 hidden
@@ -409,13 +422,8 @@ def run_gpu(args, rank: int, world: int):
     sim.close()
     e2e = run_e2e(wl, pl, inputs, W + K, seed, init_min, stream, dist, tuning, args.proposal)
     if dist is not None:
-        tt = torch.tensor([ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])],
-                          dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = tt.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        ms_all, walkers_all, e2e_s, e2e_w = mx[0].item(), sm_[1].item(), mx[2].item(), sm_[3].item()
+        ms_all, walkers_all, e2e_s, e2e_w = reduce_over_ranks(
+            dist, (ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])), "cuda")
     else:
         ms_all, walkers_all, e2e_s, e2e_w = ms, float(walkers), e2e["seconds"], float(e2e["walker_steps"])
 
