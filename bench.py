@@ -76,13 +76,13 @@ def workload(name: str):
         prob = P.ghz_circuit(32)
         return dict(name="spread32", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "
                     "1e8 distinct random states x 1 walker over 64 vectors",
-                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=5.13, t_start=5.0,
+                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
                     spread=10**8 // 64, default_steps=10)
     if name == "spread32s":
         prob = P.ghz_circuit(32)
         return dict(name="spread32s", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "
                     "1.6e7 distinct random states x 1 walker over 64 vectors",
-                    prob=prob, nseg=64, n_diag=250000, dt=0.01, t_end=5.13, t_start=5.0,
+                    prob=prob, nseg=64, n_diag=250000, dt=0.01, t_end=6.0, t_start=5.0,
                     spread=250000, default_steps=10)
     if name.startswith("ghz") and name.endswith("i") and name[3:-1].isdigit():
         n = int(name[3:-1])
@@ -91,6 +91,31 @@ def workload(name: str):
         return dict(name=name, desc=f"GHZ-{n} preparation, initiator xi = 1e-3", prob=prob, nseg=16,
                     n_diag=total // 16, dt=0.01, t_end=float(n), rho0=P.rho_basis(0), xi=1e-3)
     raise SystemExit(f"unknown workload {name}")
+
+
+def capacity_hint(wl, nsteps: int) -> int:
+    """Population slot capacity for a run of nsteps steps from the spread
+    state: the records grow by about 1.3 % of the initial count per step in
+    the CNOT window (new keys reached by spawns), so size for 2 % per step
+    plus a quarter, and no buffer has to grow (and a step be redone) inside
+    the timed region.  0 (library default) for workloads that start from a
+    single state and grow as they go."""
+    if "spread" not in wl:
+        return 0
+    base = wl["spread"] * wl["nseg"]
+    return int(base * (1.0 + 0.02 * nsteps) * 1.25)
+
+
+def plan_steps(wl, warmup: int, steps: int):
+    """(plan, total steps of the plan, timed steps K) for a run of `warmup`
+    untimed and `steps` timed steps (0: the workload's default); raises
+    SystemExit when the workload is shorter than warmup + steps."""
+    pl = step_list(wl)
+    total = planner.total_steps(pl)
+    K = steps if steps > 0 else wl.get("default_steps", total - warmup)
+    if warmup + K > total:
+        raise SystemExit(f"workload {wl['name']} has {total} steps; warmup + steps = {warmup + K}")
+    return pl, total, K
 
 
 def host_inputs(wl, rank):
@@ -157,7 +182,7 @@ def run_e2e(wl, pl, inputs, nsteps, seed, init_min, stream, dist, tuning=None, p
     from paper_2502_18929_gb300 import qmc
     prob = wl["prob"]
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
-                  initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
+                  initiator_min=init_min, capacity_hint=capacity_hint(wl, nsteps))
     sim.load_schedule(prob)
     set_proposal(sim, prob, proposal)
     if tuning is not None:
@@ -327,16 +352,12 @@ def run_gpu(args, rank: int, world: int):
     stream = torch.cuda.current_stream()
     seed = 1000 + rank
     init_min = int(math.ceil(wl.get("xi", 0.0) * wl["n_diag"]))
+    W = args.warmup
+    pl, total, K = plan_steps(wl, W, args.steps)
     sim = qmc.QMC(prob.n, wl["nseg"], seed, wl["n_diag"], integrator=qmc.AB2, stream=stream.cuda_stream,
-                  initiator_min=init_min, capacity_hint=wl.get("spread", 0) * wl["nseg"] * 5 // 4)
+                  initiator_min=init_min, capacity_hint=capacity_hint(wl, W + K))
     sim.load_schedule(prob)
     set_proposal(sim, prob, args.proposal)
-    pl = step_list(wl)
-    total = planner.total_steps(pl)
-    W = args.warmup
-    K = args.steps if args.steps > 0 else wl.get("default_steps", total - W)
-    if W + K > total:
-        raise SystemExit(f"workload has {total} steps; warmup + steps = {W + K}")
 
     inputs = host_inputs(wl, rank)
     load_inputs(sim, wl, inputs)
@@ -373,6 +394,9 @@ def run_gpu(args, rank: int, world: int):
     ms = ev0.elapsed_time(ev1)
     c = sim.counters(reset=True)
     walkers = c["walker_steps"]
+    if c["redo_launches"]:
+        raise SystemExit(f"{c['redo_launches']} step launches were redone inside the timed region "
+                         "(a buffer grew): raise the capacity hint")
     launches_per_step = sim.step_launches()   # the step graph as timed (same buffers)
 
     # per-kernel times over the same timed steps (replayed from the checkpoint)
@@ -429,7 +453,7 @@ def run_gpu(args, rank: int, world: int):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, pl, W, budget_s=args.cpu_budget)
+        cpu = cpu_baseline(wl, budget_s=args.cpu_budget, all_cores=not args.cpu_single)
 
     if rank != 0:
         return
@@ -449,7 +473,7 @@ def run_gpu(args, rank: int, world: int):
                           "working set below L2 (no flush between steps)"),
                    "parallelism": f"replicas x{world}",
                    "launch_shapes": tuning if tuning is not None else "default",
-                   "proposal": args.proposal},
+                   "proposal": args.proposal, "redo_launches_timed": c["redo_launches"]},
         "e2e": {"value": e2e_w / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d_bytes"] / (W + K),
                 "d2h_bytes_per_step": e2e["d2h_bytes"] / (W + K), "steps": W + K,
                 "includes": "input upload from pinned host memory, all warm-up and timed steps, "
@@ -564,14 +588,53 @@ def run_batch(args, rank: int, world: int):
 # ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def cpu_baseline(wl, pl, start_step: int, budget_s: float = 15.0):
-    """The oracle as it stands, single-threaded, on one vector of the same
-    workload: the first steps from the initial state until the budget is used."""
+CPU_SAMPLE_STATES = 50000   # states of one spread-workload vector in a CPU sample
+
+
+def cpu_info() -> dict:
+    """Host CPU model and the cores this process may use."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model name") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                k, _, v = line.partition(":")
+                if k.strip() == "Model name" and v.strip():
+                    model = v.strip()
+                    break
+        except Exception:
+            pass
+    try:
+        nproc = len(os.sched_getaffinity(0))
+    except AttributeError:
+        nproc = os.cpu_count() or 1
+    import platform
+    return {"cpu_model": model or platform.processor() or "unknown", "nproc": nproc,
+            "machine": platform.machine()}
+
+
+def oracle_vector(name: str, vec: int, budget_s: float):
+    """One vector of workload `name` stepped by the oracle, single-threaded,
+    until `budget_s` seconds have passed (whole steps): returns (walker-steps,
+    seconds, steps).  Spread workloads take CPU_SAMPLE_STATES random states of
+    the same distribution at the same time; the others start from their
+    initial state.  Module-level so a spawned worker process can run it."""
     from oracle import oracle as O
+    wl = workload(name)
+    pl = step_list(wl)
     prob = wl["prob"]
-    sim = O.OracleSim(prob, 1, 1000, integrator=O.AB2, n_diag=wl["n_diag"])
+    sim = O.OracleSim(prob, 1, 1000 + vec, integrator=O.AB2, n_diag=wl["n_diag"])
     if "spread" in wl:
-        k, r, i = P.spread_population(prob.n, min(wl["spread"], 200000), 0)
+        k, r, i = P.spread_population(prob.n, min(wl["spread"], CPU_SAMPLE_STATES), 10 * vec)
         sim.set_population(0, k, r, i)
         sim.set_clock(0, wl["t_start"])
     else:
@@ -579,7 +642,6 @@ def cpu_baseline(wl, pl, start_step: int, budget_s: float = 15.0):
     t0 = time.perf_counter()
     walkers = 0
     steps = 0
-    idx = 0
     for tp0, d, n in pl:
         for j in range(n):
             if j == 0:
@@ -590,35 +652,65 @@ def cpu_baseline(wl, pl, start_step: int, budget_s: float = 15.0):
                 raise RuntimeError(f"oracle step failed {rc}")
             walkers += int(sim.stats(0)[1])
             steps += 1
-            idx += 1
             if time.perf_counter() - t0 > budget_s:
                 break
         if time.perf_counter() - t0 > budget_s:
             break
-    el = time.perf_counter() - t0
-    sample = f"1 vector of {wl['name']}"
-    if "spread" in wl:
-        sample += f" ({min(wl['spread'], 200000)} states)"
-    return {"value": walkers / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample}, first {steps} steps, {el:.1f} s"}
+    return walkers, time.perf_counter() - t0, steps
+
+
+def _oracle_worker(a):
+    return oracle_vector(*a)
+
+
+def cpu_baseline(wl, budget_s: float = 15.0, all_cores: bool = True):
+    """The oracle as it stands on the host cores: one vector single-threaded,
+    and (all_cores) one vector per core in spawned worker processes (vectors
+    are independent, so this is the thread-per-vector form; the workers start
+    with the spawn method and share nothing with this process's CUDA state).
+    Each leg runs whole steps until its budget is used."""
+    info = cpu_info()
+    w1, s1, n1 = oracle_vector(wl["name"], 0, budget_s)
+    states = f"{min(wl['spread'], CPU_SAMPLE_STATES)} random states" if "spread" in wl else "its initial state"
+    sample = (f"1 vector of {wl['name']} from {states}, first {n1} steps (Euler, then AB2), "
+              f"{s1:.1f} s")
+    res = {"value": w1 / s1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "cpu_model": info["cpu_model"], "nproc": info["nproc"], "machine": info["machine"]}
+    if all_cores and info["nproc"] > 1:
+        import multiprocessing as mp
+        nw = info["nproc"]
+        with mp.get_context("spawn").Pool(nw) as pool:
+            out = pool.map(_oracle_worker, [(wl["name"], v, budget_s) for v in range(nw)])
+        wa = sum(o[0] for o in out)
+        sa = max(o[1] for o in out)
+        res["all_cores"] = {"value": wa / sa, "unit": UNIT, "cores": nw, "kind": "oracle",
+                            "sample": f"{nw} vectors, one per worker process, each from {states}, "
+                                      f"{min(o[2] for o in out)}-{max(o[2] for o in out)} steps, "
+                                      f"{sa:.1f} s wall"}
+    return res
 
 
 def run_reference(args, rank: int, world: int):
+    """The oracle as the reference arm: rank 0 alone, all host cores (one
+    vector per worker process), each worker running whole steps for a budget
+    that keeps the run within a few minutes."""
     if rank != 0:
         return
     wl = workload(args.workload)
-    pl = step_list(wl)
-    total = planner.total_steps(pl)
     W = args.warmup
-    K = args.steps if args.steps > 0 else wl.get("default_steps", total - W)
-    per_step_budget = max(0.5, min(20.0, 120.0 / max(1, K + W)))
-    res = cpu_baseline(wl, pl, 0, budget_s=per_step_budget * (K + W))
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+    pl, total, K = plan_steps(wl, W, args.steps)
+    budget = max(5.0, min(60.0, 4.0 * (K + W)))
+    res = cpu_baseline(wl, budget_s=budget, all_cores=True)
+    arm = res.get("all_cores", res)
+    cpu = dict(arm)
+    cpu.update({"cpu_model": res["cpu_model"], "nproc": res["nproc"], "single_core": res["value"],
+                "single_core_sample": res["sample"]})
+    line = {"impl": "reference", "metric": METRIC, "value": arm["value"], "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": W, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl["name"], "description": wl["desc"]},
-            "cpu_baseline": res,
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": cpu,
+            "e2e": {"value": arm["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -636,6 +728,7 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes after the warm-up (state kept) and use the fastest")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-single", action="store_true", help="cpu_baseline: skip the all-core oracle leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -374,14 +374,17 @@ int qmc_observables(qmc_ctx* ctx, qmc_obs* obs);
  * steps recorded (<= cap_steps). */
 int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* count);
 
-/* Cumulative totals since the last reset, all vectors (host out[10]):
+/* Cumulative totals since the last reset, all vectors (host out[11]):
  * out[0] steps, [1] walker-steps (sum over steps of N_tot of N(t + dt)),
  * [2] records read from N(t), [3] records read from N(t - dt) (AB2 steps),
  * [4] spawn records, [5] records written to N(t + dt), [6] heavy work items,
  * [7] spawn candidates (walker draws below the step's bound on p, each
  * checked against the exact column), [8] steps whose spawn records were
  * sorted by buckets, [9] steps that took the LSD radix sort (a bucket too
- * large for the bucket sort).  reset != 0 zeroes them after reading.
+ * large for the bucket sort), [10] step launches repeated because a buffer
+ * had to grow first (a capacity error inside a qmc_step call: the steps from
+ * the failed one on run again, bit-identically).  reset != 0 zeroes them
+ * after reading.
  * Synchronises. */
 int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out);
 

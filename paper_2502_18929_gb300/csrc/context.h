@@ -96,6 +96,7 @@ struct qmc_ctx {
     double t = 0.0, t_prev = 0.0, dt_last = 0.0;
     bool prev_valid = false;
     int64_t last_call_steps = 0;
+    int64_t acc_redo = 0;   // step launches repeated after a buffer grew (qmc_counters out[10])
 
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;

@@ -1115,6 +1115,7 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
             return map_dev_error(ctx, code, hs.error_aux);
         }
         // redo from the failed step
+        ctx->acc_redo += nsteps - done;
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &done, 4,
                            cudaMemcpyHostToDevice, ctx->work));
         (void)zero;
@@ -1492,7 +1493,9 @@ extern "C" int qmc_counters(qmc_ctx* ctx, int32_t reset, int64_t* out)
     out[7] = hs.acc_cand;
     out[8] = hs.acc_sort_bucket;
     out[9] = hs.acc_sort_lsd;
+    out[10] = ctx->acc_redo;
     if (reset) {
+        ctx->acc_redo = 0;
         int64_t z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, acc_steps), z, sizeof(z),
                            cudaMemcpyHostToDevice, ctx->work));

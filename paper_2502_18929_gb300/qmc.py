@@ -391,10 +391,10 @@ class QMC:
 
     def counters(self, reset: bool = False) -> dict:
         """Cumulative device totals since the last reset (see qmc_counters)."""
-        out = np.zeros(10, dtype=np.int64)
+        out = np.zeros(11, dtype=np.int64)
         self._check(self.L.qmc_counters(self.h, int(reset), out.ctypes.data), "qmc_counters")
         names = ["steps", "walker_steps", "k_cur", "k_prev", "spawns", "k_next", "heavy_items", "candidates",
-                 "sort_bucket_steps", "sort_lsd_steps"]
+                 "sort_bucket_steps", "sort_lsd_steps", "redo_launches"]
         return {k: int(v) for k, v in zip(names, out)}
 
     def step_launches(self) -> int:
