@@ -78,8 +78,18 @@ def lib():
                                  C.c_void_p]
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_mlp_exp.restype = C.c_float
+        L.orc_mlp_exp.argtypes = [C.c_float]
+        L.orc_learned_q.restype = C.c_int
+        L.orc_learned_q.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
+
+
+def mlp_exp(x: float) -> float:
+    """The learned proposal's single-precision e^x (x <= 0)."""
+    return float(lib().orc_mlp_exp(float(x)))
 
 
 def philox(ctr, key) -> np.ndarray:
@@ -187,6 +197,19 @@ class OracleSim:
                                float(net["eps"]))
         if rc != OK:
             raise RuntimeError(f"orc_set_mlp failed: {rc}")
+
+    def learned_q(self, x: int, y: int, t: float, dt_eff: float):
+        """The learned proposal's integer weights for the source |x><y|: (masks,
+        Q, p_att) over the static column of dt_eff L(t) (after set_mlp)."""
+        cap = 256
+        mask = np.zeros(cap, dtype=np.uint64)
+        Q = np.zeros(cap, dtype=np.int64)
+        pa = np.zeros(1, dtype=np.int64)
+        k = lib().orc_learned_q(self.handle, t, dt_eff, x, y, cap, mask.ctypes.data, Q.ctypes.data,
+                                pa.ctypes.data)
+        if k < 0:
+            raise RuntimeError(f"orc_learned_q failed: {k}")
+        return mask[:k], Q[:k], int(pa[0])
 
     def set_proposal(self, kind: int):
         """Spawn choice: 0 exact |L|-weighted (the paper's), 1 static-weight

@@ -1035,6 +1035,37 @@ int orc_set_mlp(void* sp, int n_in, int n_hidden, int n_out, const uint64_t* out
     return ORC_OK;
 }
 
+/* The learned proposal's e^x (mlp_exp), exported for its accuracy test. */
+float orc_mlp_exp(float x) { return mlp_exp(x); }
+
+/* Integer proposal weights of the learned proposal (learned_weights) for the
+ * source |x><y| under the static column of dt_eff L(t): up to cap
+ * destinations in ascending mask order (mask[k], Q[k]), *p_att the attempt
+ * weight (sum of the static weights).  Returns the number of destinations or
+ * a negative error.  Exported for the tests of the network's forward pass. */
+int orc_learned_q(void* sp, double t, double dt_eff, uint64_t x, uint64_t y, int cap, uint64_t* mask,
+                  int64_t* Q, int64_t* p_att)
+{
+    state* s = (state*)sp;
+    if (!s->w1) return ORC_ERR_INVALID_ARG;
+    column st = {0, 0, 0};
+    int rc = build_static(s->prob, t, dt_eff, &st);
+    if (rc != ORC_OK) { free(st.e); return rc; }
+    if (st.len > 256 || st.len > cap) { free(st.e); return ORC_ERR_INVALID_ARG; }
+    int64_t P = 0;
+    for (int e = 0; e < st.len; ++e) P += st.e[e].v.re;
+    int64_t Qw[256];
+    learned_weights(s, &st, P, x, y, t, Qw);
+    for (int e = 0; e < st.len; ++e) {
+        mask[e] = st.e[e].mask;
+        Q[e] = Qw[e];
+    }
+    *p_att = P;
+    const int len = st.len;
+    free(st.e);
+    return len;
+}
+
 int64_t orc_count(void* sp, int seg, int which)
 {
     state* s = (state*)sp;

@@ -91,6 +91,6 @@ def test_uniform_words_are_unbiased():
         vals.append(((int(w[1]) << 32) | int(w[0])) >> 12)
         vals.append(((int(w[3]) << 32) | int(w[2])) >> 12)
     u = np.array(vals, dtype=np.float64) / 2.0**52
-    assert abs(u.mean() - 0.5) < 4 * (1 / np.sqrt(12 * len(u)))
+    assert abs(u.mean() - 0.5) < 3 * (1 / np.sqrt(12 * len(u)))
     frac = (u < 0.1).mean()
-    assert abs(frac - 0.1) < 4 * np.sqrt(0.09 / len(u))
+    assert abs(frac - 0.1) < 3 * np.sqrt(0.09 / len(u))
