@@ -78,6 +78,8 @@ def lib():
                                  C.c_void_p]
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_walker_T.restype = C.c_int64
+        L.orc_walker_T.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_int64]
         L.orc_mlp_exp.restype = C.c_float
         L.orc_mlp_exp.argtypes = [C.c_float]
         L.orc_learned_q.restype = C.c_int
@@ -85,6 +87,13 @@ def lib():
                                     C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
+
+
+def walker_T(kd, rank: int, phase: int, comp: int, j: int, re_walkers: int) -> int:
+    """The 52-bit spawn draw of walker j of component comp of the parent at
+    `rank` in pass `phase` under the step key kd (two uint32)."""
+    k = np.ascontiguousarray(kd, dtype=np.uint32)
+    return int(lib().orc_walker_T(k.ctypes.data, rank, phase, comp, j, re_walkers))
 
 
 def mlp_exp(x: float) -> float:

@@ -19,7 +19,7 @@
  *   - Spawning [End Matter, spawn step]: N^sp ~ B(m, p) with
  *     p = dt * sum_kl (|Re L| + |Im L|), spread over (kl, channel) by a
  *     multinomial with probabilities |c(L)| / sum.  Written as m independent
- *     walkers, each drawing one 64-bit Philox word R: T = R >> 12; the walker
+ *     walkers, each with a uniform 52-bit draw T (see walker_T); the walker
  *     spawns iff T < P (P = p * 2^52) and then goes to the entry whose
  *     cumulative-weight interval holds T (reading R2).  The sign rule is the
  *     paper's: Re channel s * sgn(Re L), Im channel i * s * sgn(Im L).
@@ -97,9 +97,11 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
 /* Stream layout (reading R3; the paper names no generator). */
 #define TAG_STEP 0x53544550u /* per (step, segment) key derivation */
 #define TAG_INIT 0x494E4954u /* per segment key for initial rounding */
-#define KIND_SPAWN 0u
 #define KIND_INIT 1u
 #define KIND_LEARNED 2u
+#define KIND_GROUP 3u   /* first walkers of four parents (one rank group) */
+#define KIND_EXTRA 4u   /* further walkers of one parent, four per call */
+#define KIND_LOW 5u     /* low 20 bits of one walker's draw */
 
 static void derive_key(uint64_t seed, uint64_t step, uint32_t seg, uint32_t tag, uint32_t kd[2])
 {
@@ -763,7 +765,39 @@ static cint column_at(const column* c, uint64_t mask)
     return z;
 }
 
-static int spawn_parent(const state* s, const rec* par, int phase, double t, double dt_eff,
+/*
+ * The 52-bit draw T of walker j of component comp (0 real, 1 imaginary) of
+ * the parent at rank r -- its index in the vector's key-sorted population --
+ * in pass phase (0: N(t), 1: N(t - dt)), with the step's key kd (reading R3;
+ * the paper names no generator).  The parent's walkers are numbered
+ * w = 0 .. m - 1, real walkers first.  T = W << 20 | L, where W is a 32-bit
+ * word -- for w = 0 word r % 4 of the call keyed by the rank group r / 4 (one
+ * call serves the first walkers of four parents), for w >= 1 word (w - 1) % 4
+ * of the parent's call (w - 1) / 4 -- and L the top 20 bits of word 0 of the
+ * walker's own call.  Every word comes from a distinct Philox counter, so the
+ * T of all walkers are independent and uniform on [0, 2^52).
+ */
+static int64_t walker_T(const uint32_t kd[2], int64_t r, int phase, int comp, int64_t j, int64_t are)
+{
+    const int64_t w = (comp ? are : 0) + j;
+    uint32_t o[4];
+    uint32_t W;
+    if (w == 0) {
+        const uint32_t ctr[4] = {(uint32_t)(r >> 2), 0u, (uint32_t)phase | (KIND_GROUP << 2), 0u};
+        orc_philox(ctr, kd, o);
+        W = o[r & 3];
+    } else {
+        const uint32_t ctr[4] = {(uint32_t)r, (uint32_t)((w - 1) >> 2), (uint32_t)phase | (KIND_EXTRA << 2), 0u};
+        orc_philox(ctr, kd, o);
+        W = o[(w - 1) & 3];
+    }
+    const uint32_t ctr2[4] = {(uint32_t)r, (uint32_t)j, (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_LOW << 2),
+                              0u};
+    orc_philox(ctr2, kd, o);
+    return (int64_t)((((uint64_t)W) << 20) | (o[0] >> 12));
+}
+
+static int spawn_parent(const state* s, const rec* par, int64_t rank, int phase, double t, double dt_eff,
                         int sigma, const uint32_t kd[2], column* col, const column* st, spawn_list* out)
 {
     const problem* p = s->prob;
@@ -800,17 +834,8 @@ static int spawn_parent(const state* s, const rec* par, int phase, double t, dou
         int64_t val = comp == 0 ? par->re : par->im;
         int64_t m = llabs(val);
         int64_t sg = val > 0 ? 1 : -1;
-        uint32_t w[4] = {0, 0, 0, 0};
         for (int64_t j = 0; j < m; ++j) {
-            if ((j & 1) == 0) {
-                uint32_t ctr[4] = {(uint32_t)par->key, (uint32_t)(par->key >> 32),
-                                   (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_SPAWN << 2),
-                                   (uint32_t)(j >> 1)};
-                orc_philox(ctr, kd, w);
-            }
-            uint64_t R = (j & 1) ? (((uint64_t)w[3] << 32) | w[2])
-                                 : (((uint64_t)w[1] << 32) | w[0]);
-            int64_t T = (int64_t)(R >> 12);
+            int64_t T = walker_T(kd, rank, phase, comp, j, llabs((int64_t)par->re));
             if (T >= P) continue; /* this walker does not spawn */
             if (s->proposal == 2) {
                 /* learned proposal: destination by Q, counts by the amplitude */
@@ -962,11 +987,11 @@ int orc_step(void* sp, double dt, int nsteps)
             spl.len = 0;
             const pop* cur = &s->cur[seg];
             for (int64_t i = 0; i < cur->len && rc == ORC_OK; ++i)
-                rc = spawn_parent(s, &cur->r[i], 0, t, dt_cur, 1, kd, &col, &st_cur, &spl);
+                rc = spawn_parent(s, &cur->r[i], i, 0, t, dt_cur, 1, kd, &col, &st_cur, &spl);
             if (ab2) {
                 const pop* prv = &s->prev[seg];
                 for (int64_t i = 0; i < prv->len && rc == ORC_OK; ++i)
-                    rc = spawn_parent(s, &prv->r[i], 1, s->t_prev, dt_prev, -1, kd, &col, &st_prev, &spl);
+                    rc = spawn_parent(s, &prv->r[i], i, 1, s->t_prev, dt_prev, -1, kd, &col, &st_prev, &spl);
             }
             if (rc != ORC_OK) break;
             /* spawns from N(t - dt) that land on states unoccupied in N(t) are
@@ -1033,6 +1058,12 @@ int orc_set_mlp(void* sp, int n_in, int n_hidden, int n_out, const uint64_t* out
     ORC_COPY(s->out_mask, out_mask, n_out, uint64_t);
 #undef ORC_COPY
     return ORC_OK;
+}
+
+/* walker_T, exported for the tests of the draws' distribution. */
+int64_t orc_walker_T(const uint32_t kd[2], int64_t r, int phase, int comp, int64_t j, int64_t are)
+{
+    return walker_T(kd, r, phase, comp, j, are);
 }
 
 /* The learned proposal's e^x (mlp_exp), exported for its accuracy test. */

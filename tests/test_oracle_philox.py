@@ -94,3 +94,30 @@ def test_uniform_words_are_unbiased():
     assert abs(u.mean() - 0.5) < 3 * (1 / np.sqrt(12 * len(u)))
     frac = (u < 0.1).mean()
     assert abs(frac - 0.1) < 3 * np.sqrt(0.09 / len(u))
+
+
+def test_walker_draws_uniform_and_independent():
+    """The spawn draws T (52 bits) of the walkers of many parents: the first
+    walkers of four consecutive ranks share one Philox call, further walkers
+    take four words of their parent's call, and every walker adds its own low
+    bits.  T must be uniform on [0, 2^52) (chi-square over 64 bins of the top
+    bits and of the low 20 bits) and the draws of neighbouring walkers
+    uncorrelated -- the law of the per-walker Bernoulli(p) spawn test needs
+    exactly that."""
+    from scipy import stats
+    kd = [0x9E3779B9, 0x7F4A7C15]
+    T, Tn, Tw = [], [], []
+    for r in range(6000):
+        are = 1 + r % 2      # 1 or 2 real walkers, then 1 imaginary one
+        t0 = O.walker_T(kd, r, r & 1, 0, 0, are)
+        T.append(t0)
+        Tn.append(O.walker_T(kd, r + 1, r & 1, 0, 0, 1))      # first walker of the next rank
+        Tw.append(O.walker_T(kd, r, r & 1, 1, 0, are))   # first imaginary walker
+    T, Tn, Tw = (np.array(a, dtype=np.float64) for a in (T, Tn, Tw))
+    assert T.min() >= 0 and T.max() < 2.0 ** 52
+    for vals in (np.floor(T / 2.0 ** 46), np.mod(T, 2.0 ** 20) // 2.0 ** 14):
+        counts = np.bincount(vals.astype(np.int64), minlength=64)
+        assert stats.chisquare(counts).pvalue > 1e-3
+    for other in (Tn, Tw):
+        rho = np.corrcoef(T, other)[0, 1]
+        assert abs(rho) < 3.0 / np.sqrt(len(T))
