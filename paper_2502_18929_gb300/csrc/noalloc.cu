@@ -41,25 +41,83 @@ __device__ __forceinline__ int seg_index(const int64_t* off, int nseg, int64_t i
     return lo;
 }
 
-// records: 16-byte (uint64 key, int32 re, int32 im), keys (x << n) | y.
+// Add the warp's per-lane sums to the accumulators, one set of atomics per
+// vector the warp holds.  Lanes hold nondecreasing vector indices (each lane
+// walks consecutive records of the warp's range), so the lanes of one vector
+// are contiguous: a segmented sum down the warp leaves each vector's total in
+// its first lane.  seg < 0: the lane holds nothing.
+__device__ __forceinline__ void warp_flush(ObsAcc* acc, int seg, unsigned long long cnt, long long ntot,
+                                           long long dre, long long dim, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int so = __shfl_down_sync(0xFFFFFFFFu, seg, d);
+        const unsigned long long c = __shfl_down_sync(0xFFFFFFFFu, cnt, d);
+        const long long t = __shfl_down_sync(0xFFFFFFFFu, ntot, d);
+        const long long r = __shfl_down_sync(0xFFFFFFFFu, dre, d);
+        const long long i = __shfl_down_sync(0xFFFFFFFFu, dim, d);
+        if (lane + d < 32 && so == seg) {
+            cnt += c;
+            ntot += t;
+            dre += r;
+            dim += i;
+        }
+    }
+    const int up = __shfl_up_sync(0xFFFFFFFFu, seg, 1);
+    if (seg >= 0 && (lane == 0 || up != seg) && cnt) {
+        atomicAdd(&acc[seg].count, cnt);
+        atomicAdd((unsigned long long*)&acc[seg].ntot, (unsigned long long)ntot);
+        if (dre) atomicAdd((unsigned long long*)&acc[seg].dre, (unsigned long long)dre);
+        if (dim) atomicAdd((unsigned long long*)&acc[seg].dim, (unsigned long long)dim);
+    }
+}
+
+// records: 16-byte (uint64 key, int32 re, int32 im), keys (x << n) | y;
+// vector s holds records [off[s], off[s + 1]).  Each warp owns a contiguous
+// range of [off[0], off[nseg]); lane l takes its records l, l + 32, ...
+// and sums them per vector in registers, so a vector costs one set of
+// atomics per warp that touches it instead of one per record.
 __global__ void k_noalloc_accumulate(const uint4* __restrict__ rec, const int64_t* __restrict__ off, int nseg, int n,
                                      ObsAcc* acc)
 {
-    const int64_t K = off[nseg];
+    const int lane = threadIdx.x & 31;
+    const int64_t first = off[0], total = off[nseg] - first;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t chunk = ((total + nwarps - 1) / nwarps + 31) / 32 * 32;
+    const int64_t wb = first + min(total, gw * chunk), we = first + min(total, (gw + 1) * chunk);
     const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 r = rec[i];
-        const uint64_t key = ((uint64_t)r.y << 32) | r.x;
-        const int32_t re = (int32_t)r.z, im = (int32_t)r.w;
-        const int s = seg_index(off, nseg, i);
-        atomicAdd(&acc[s].count, 1ull);
-        atomicAdd((unsigned long long*)&acc[s].ntot,
-                  (unsigned long long)((re < 0 ? -(long long)re : re) + (im < 0 ? -(long long)im : im)));
-        if ((uint32_t)(key >> n) == (uint32_t)(key & ymask)) {
-            atomicAdd((unsigned long long*)&acc[s].dre, (unsigned long long)(long long)re);
-            atomicAdd((unsigned long long*)&acc[s].dim, (unsigned long long)(long long)im);
+    int cur = -1;
+    int64_t cur_end = -1;
+    unsigned long long cnt = 0ull;
+    long long ntot = 0, dre = 0, dim = 0;
+    for (int64_t j = wb; j < we; j += 32) {
+        const int64_t i = j + lane;
+        const bool valid = i < we;
+        int s = valid ? cur : -1;   // a lane past the range holds nothing (keeps lanes' vectors nondecreasing)
+        if (valid && i >= cur_end) {
+            s = seg_index(off, nseg, i);
+            cur_end = off[s + 1];
+        }
+        if (__any_sync(0xFFFFFFFFu, s != cur)) {
+            warp_flush(acc, cur, cnt, ntot, dre, dim, lane);
+            cur = s;
+            cnt = 0ull;
+            ntot = dre = dim = 0;
+        }
+        if (valid) {
+            const uint4 r = __ldcs(rec + i);
+            const uint64_t key = ((uint64_t)r.y << 32) | r.x;
+            const int32_t re = (int32_t)r.z, im = (int32_t)r.w;
+            cnt += 1ull;
+            ntot += (re < 0 ? -(long long)re : re) + (im < 0 ? -(long long)im : im);
+            if ((uint32_t)(key >> n) == (uint32_t)(key & ymask)) {
+                dre += re;
+                dim += im;
+            }
         }
     }
+    warp_flush(acc, cur, cnt, ntot, dre, dim, lane);
 }
 
 __global__ void k_noalloc_store(const ObsAcc* acc, int nseg, qmc_obs* out)
@@ -96,7 +154,7 @@ extern "C" int qmc_observables_noalloc(const void* records, const int64_t* seg_o
     if (!records || !seg_offsets || !out || n_segments < 1 || n_qubits < 1 || n_qubits > 32)
         return QMC_ERR_INVALID_ARG;
     if (n_segments > QMC_NOALLOC_MAX_SEGMENTS) return QMC_ERR_INVALID_ARG;
-    if (((uintptr_t)records & 15u) != 0) return QMC_ERR_INVALID_ARG;
+    if (((uintptr_t)records & 15u) != 0 || ((uintptr_t)seg_offsets & 7u) != 0) return QMC_ERR_INVALID_ARG;
     ObsAcc* acc = nullptr;
     int rc = acc_address(&acc);
     if (rc != QMC_OK) return rc;
