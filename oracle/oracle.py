@@ -78,6 +78,8 @@ def lib():
                                  C.c_void_p]
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_zsum.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_antiherm.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_walker_T.restype = C.c_int64
         L.orc_walker_T.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_int64]
         L.orc_mlp_exp.restype = C.c_float
@@ -251,6 +253,18 @@ class OracleSim:
             lib().orc_export(self.handle, seg, which, keys.ctypes.data, re.ctypes.data,
                              im.ctypes.data)
         return keys, re, im
+
+    def zsum(self, seg: int) -> np.ndarray:
+        """Per qubit q: sum over diagonal records of Re N_xx (-1)^(x_q)."""
+        out = np.zeros(self.n, dtype=np.int64)
+        lib().orc_zsum(self.handle, seg, out.ctypes.data)
+        return out
+
+    def antiherm(self, seg: int) -> int:
+        """||N - N^dagger||_F^2 of one vector, an exact integer."""
+        out = np.zeros(2, dtype=np.uint64)
+        lib().orc_antiherm(self.handle, seg, out.ctypes.data)
+        return int(out[0]) + (int(out[1]) << 64)
 
     def stats(self, seg: int):
         out = np.zeros(4, dtype=np.int64)

@@ -1060,6 +1060,68 @@ int orc_set_mlp(void* sp, int n_in, int n_hidden, int n_out, const uint64_t* out
     return ORC_OK;
 }
 
+/* Sum over the diagonal records of vector seg of Re N_xx (-1)^(x_q), for
+ * q = 0 .. n - 1 (out[q]): N^diag <Z_q> in the walker representation
+ * [walker averaging, Eq. (3): rho = N / N^diag].  Bit q of x is qubit q. */
+void orc_zsum(void* sp, int seg, int64_t* out)
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    const pop* p = &s->cur[seg];
+    const uint64_t ymask = (((uint64_t)1) << n) - 1;
+    for (int q = 0; q < n; ++q) out[q] = 0;
+    for (int64_t i = 0; i < p->len; ++i) {
+        const uint64_t x = p->r[i].key >> n, y = p->r[i].key & ymask;
+        if (x != y) continue;
+        for (int q = 0; q < n; ++q) out[q] += ((x >> q) & 1u) ? -(int64_t)p->r[i].re : (int64_t)p->r[i].re;
+    }
+}
+
+/* Value of vector seg's N(t) at key (0 when unoccupied). */
+static void value_at_key(const pop* p, uint64_t key, int64_t* re, int64_t* im)
+{
+    int64_t lo = 0, hi = p->len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (p->r[mid].key < key) lo = mid + 1; else hi = mid;
+    }
+    *re = 0;
+    *im = 0;
+    if (lo < p->len && p->r[lo].key == key) {
+        *re = p->r[lo].re;
+        *im = p->r[lo].im;
+    }
+}
+
+/* ||N - N^dagger||_F^2 of vector seg's N(t), exactly (out[0] low and out[1]
+ * high 64 bits) [End Matter on Hermiticity preservation: epsilon =
+ * ||rho - rho^dagger||_F with rho = N / N^diag].  The sum runs over every
+ * entry (x, y) where N or N^dagger is nonzero: each record's entry
+ * N_xy - conj(N_yx), and the transposed entry -conj(N_xy) of every record
+ * whose transposed key is unoccupied. */
+void orc_antiherm(void* sp, int seg, uint64_t out[2])
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    const pop* p = &s->cur[seg];
+    const uint64_t ymask = (((uint64_t)1) << n) - 1;
+    unsigned __int128 acc = 0;
+    for (int64_t i = 0; i < p->len; ++i) {
+        const uint64_t x = p->r[i].key >> n, y = p->r[i].key & ymask;
+        int64_t tre, tim;
+        value_at_key(p, (y << n) | x, &tre, &tim);
+        const int64_t dre = (int64_t)p->r[i].re - tre, dim = (int64_t)p->r[i].im + tim;
+        acc += (unsigned __int128)((__int128)dre * dre) + (unsigned __int128)((__int128)dim * dim);
+        if (tre == 0 && tim == 0) {
+            /* the transposed entry is -conj(N_xy) */
+            const int64_t a = p->r[i].re, b = p->r[i].im;
+            acc += (unsigned __int128)((__int128)a * a) + (unsigned __int128)((__int128)b * b);
+        }
+    }
+    out[0] = (uint64_t)acc;
+    out[1] = (uint64_t)(acc >> 64);
+}
+
 /* walker_T, exported for the tests of the draws' distribution. */
 int64_t orc_walker_T(const uint32_t kd[2], int64_t r, int phase, int comp, int64_t j, int64_t are)
 {
