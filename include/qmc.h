@@ -363,6 +363,19 @@ int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out);
  * |Re c| + |Im c| times |rate| times dt.  Host-only; used to choose dt. */
 int qmc_spawn_prob_bound(const qmc_ctx* ctx, double t, double dt, double* p_bound);
 
+/* Bounded device waits.  A kernel that places its tile after other CTAs'
+ * tiles (the decoupled look-back of the spawn sort, of the bucket scan and of
+ * the merge [End Matter, annihilation step: the merged output's positions])
+ * polls another CTA's status word at most `polls` times (about 64 ns apart
+ * after the first 32) before it gives up: the step then returns
+ * QMC_ERR_DEVICE_TIMEOUT with the wait's site and tile in qmc_last_error, the
+ * context keeps the populations of the last completed step, and the next
+ * qmc_step call (after the limit is raised again) repeats the failed step
+ * bit-identically.  Default 2^22 polls; 0 makes every such wait fail at its
+ * first poll (for tests of the failure path).  Waits on a CTA's own bulk
+ * copies keep their fixed limit.  Errors: INVALID_ARG (above 2^30). */
+int qmc_set_spin_limit(qmc_ctx* ctx, uint32_t polls);
+
 /* ---- results --------------------------------------------------------------- */
 
 /* Per-vector observables of N(t) into obs[0 .. n_segments) (host).
@@ -401,6 +414,31 @@ int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t
 int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* psi_re,
                 const double* psi_im, int32_t len, double* out_re, double* out_im);
 
+/* N^diag <Z_q> of every vector after each step of the last qmc_step call
+ * [walker averaging, Eq. (3): <Z_q> = Tr(Z_q rho), rho = N / N^diag]: host
+ * out[step][vector][q] (q < n_qubits of the context) = sum over the diagonal
+ * records of Re N_xx (-1)^(x_q), bit q of x being qubit q; entries with q at
+ * or above a batch instance's own qubit count are 0.  Accumulated inside the
+ * merge of each step.  *count receives the number of steps (<= cap_steps). */
+int qmc_z_history(qmc_ctx* ctx, int64_t* out, int64_t cap_steps, int64_t* count);
+
+/* Overlap of every vector of N(t) with a target |psi> on len <= 64 basis
+ * states (host idx[len], psi_re[len], psi_im[len]; each idx < 2^n of every
+ * instance): out_re/out_im[vector] = sum over a, b of conj(psi_a) N_ab psi_b,
+ * evaluated on the device from the exact populations in the same order and
+ * rounding as qmc_overlap (fidelity F = |value| / N^diag for a normalised
+ * psi) [Markovian circuit dynamics].  One launch and one synchronisation for
+ * all vectors.  Errors: INVALID_ARG, STATE (no population). */
+int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, const double* psi_im, int32_t len,
+                    double* out_re, double* out_im);
+
+/* ||N - N^dagger||_F^2 of every vector of N(t), exactly, as host out[2 s]
+ * (low 64 bits) and out[2 s + 1] (high 64 bits) [End Matter on Hermiticity
+ * preservation: epsilon = ||rho - rho^dagger||_F, rho = N / N^diag, so
+ * epsilon = sqrt(value) / N^diag for one vector].  Each record's transposed
+ * state is found by binary search in its vector.  Synchronises. */
+int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out);
+
 /* ---- checkpoint / resume ------------------------------------------------- */
 
 /* Write (clock, seed, configuration hash, N(t), N(t - dt)) to path; restore
@@ -423,7 +461,10 @@ int qmc_restore(qmc_ctx* ctx, const char* path);
  * synchronisation cudaMalloc and cudaFree can cause.
  *   records      device, 16 bytes per record (uint64 key (x << n) | y,
  *                int32 re, int32 im), 16-byte aligned, sorted by vector
- *   seg_offsets  device, n_segments + 1 int64 offsets of each vector's records
+ *   seg_offsets  device, 8-byte aligned, n_segments + 1 nondecreasing int64
+ *                offsets: vector s holds records [seg_offsets[s],
+ *                seg_offsets[s + 1]) (empty vectors allowed; records before
+ *                seg_offsets[0] are not read)
  *   out          device, n_segments qmc_obs, written
  *   cuda_stream  stream to issue the work on (0 = legacy default stream);
  *                the call returns without synchronising it.
@@ -436,7 +477,10 @@ int qmc_restore(qmc_ctx* ctx, const char* path);
  * streams, other threads) race: serialise them.
  * Errors: INVALID_ARG (null pointers, n_segments < 1 or above
  * QMC_NOALLOC_MAX_SEGMENTS, n_qubits outside 1..32, records not 16-byte
- * aligned), CUDA (set-up or launch failed). */
+ * or seg_offsets not 8-byte aligned), CUDA (set-up or launch failed).
+ * Each warp sums its records per vector in registers and adds the sums with
+ * one set of atomics per vector it touches, so the cost is one read of the
+ * records whatever the vector sizes. */
 int qmc_observables_noalloc(const void* records, const int64_t* seg_offsets, int32_t n_segments,
                             int32_t n_qubits, qmc_obs* out, void* cuda_stream);
 

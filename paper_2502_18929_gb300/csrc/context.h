@@ -30,6 +30,7 @@ struct qmc_ctx {
     int grid = 0;
     int heavy_walkers = qmc::kHeavyWalkers;   // launch shapes (qmc_set_tuning)
     int bucket_records = 24;
+    uint32_t spin_limit = qmc::kDefaultSpinLimit;   // qmc_set_spin_limit
 
     // Problem instances: one for a context made by qmc_create, several for
     // qmc_batch_create.  Instance i owns segments [seg0, seg0 + nvec).
@@ -60,6 +61,7 @@ struct qmc_ctx {
     DevState* d_state = nullptr;
     Rec* d_pop[3] = {nullptr, nullptr, nullptr};
     int64_t* d_segoff[3] = {nullptr, nullptr, nullptr};
+    int64_t* d_gofs[3] = {nullptr, nullptr, nullptr};   // rank-group offsets (written by each step's prologue)
     int64_t pop_cap = 0;
     SRec* d_spawn = nullptr;
     SRec* d_spawn_alt = nullptr;
@@ -85,6 +87,10 @@ struct qmc_ctx {
     SegStats* d_segacc = nullptr;
     SegStats* d_history = nullptr;
     int64_t history_cap = 0;
+    long long* d_zacc = nullptr;     // [nseg][32] diagonal sums of the step being merged
+    long long* d_zhist = nullptr;    // [history_cap][nseg][n] N^diag <Z_q> per step of the last call
+    uint8_t* d_aux = nullptr;        // scratch of the on-demand observables (overlaps, anti-Hermiticity)
+    int64_t aux_cap = 0;
     StepInfo* d_info = nullptr;
     int64_t info_cap = 0;
     uint8_t* d_progs = nullptr;

@@ -34,8 +34,11 @@ namespace {
 
 int g_grid_misc = 0;   // grid of the simple grid-stride kernels (set by configure_kernels)
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
+// Polls of an mbarrier phase (a CTA's own bulk copies and its warps'
+// hand-overs) before the wait gives up.  Waits on other CTAs' look-back words
+// take the context's limit instead (StepParams::spin_limit).
+constexpr uint32_t kMbarSpinLimit = 1u << 22;
 constexpr int kStage = 64; // spawn records staged per warp
 
 // ---------------------------------------------------------------------------
@@ -117,9 +120,9 @@ __device__ __forceinline__ bool lb_ready(unsigned long long v, uint32_t epoch)
 // Wait (bounded) until *addr carries this epoch and a flag; returns false on
 // timeout after raising DERR_TIMEOUT.
 __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned long long* out,
-                        DevState* st, uint32_t site, int64_t idx)
+                        DevState* st, uint32_t site, int64_t idx, uint32_t limit)
 {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         unsigned long long v = ld_vol(addr);
         if (lb_ready(v, epoch)) {
             *out = v;
@@ -138,7 +141,7 @@ __device__ bool lb_wait(const unsigned long long* addr, uint32_t epoch, unsigned
 // prefix of tile t (to every lane).  Bounded waits; on timeout the error is
 // raised and the partial sum returned.
 __device__ unsigned long long warp_lookback(const unsigned long long* status, int64_t t, uint32_t epoch,
-                                            DevState* st, int lane, uint32_t site)
+                                            DevState* st, int lane, uint32_t site, uint32_t limit)
 {
     unsigned long long excl = 0;
     int64_t hi = t - 1; // nearest unread predecessor
@@ -146,7 +149,7 @@ __device__ unsigned long long warp_lookback(const unsigned long long* status, in
         const int64_t j = hi - lane;
         unsigned long long v = 0;
         bool ready = j < 0;
-        for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        for (uint32_t it = 0; it < limit; ++it) {
             if (!ready) {
                 v = ld_vol(status + j);
                 ready = lb_ready(v, epoch);
@@ -217,8 +220,40 @@ __global__ void k_prologue(StepParams P)
         P.kd[s] = make_uint2(o.x, o.y);
         P.segacc[s] = SegStats{0ull, 0ll, 0ll, 0ll};
     }
+    for (int64_t i = threadIdx.x; i < 32 * (int64_t)P.nseg; i += blockDim.x) P.zacc[i] = 0ll;
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) P.sort_hist[i] = 0u;
     for (int i = threadIdx.x; i < kMaxTileCounters; i += blockDim.x) st->tile_ctr[i] = 0u;
+    // rank-group offsets of N(t) and N(t - dt) (the draw kernel's work units):
+    // gof[s] = sum over the vectors before s of ceil(K / 4)
+    __shared__ long long wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int w = 0; w < 2; ++w) {
+        const int slot = w ? (st->cur + 2) % 3 : st->cur;
+        const int64_t* off = P.segoff[slot];
+        int64_t* gof = P.gofs[slot];
+        long long carry = 0;
+        for (int base = 0; base < P.nseg; base += kThreads) {
+            const int s = base + threadIdx.x;
+            const long long c = s < P.nseg ? (long long)((off[s + 1] - off[s] + 3) / 4) : 0ll;
+            long long incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            long long wo = 0, blk = 0;
+            for (int q = 0; q < kThreads / 32; ++q) {
+                if (q < warp) wo += wsum[q];
+                blk += wsum[q];
+            }
+            if (s < P.nseg) gof[s] = carry + wo + incl - c;
+            carry += blk;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) gof[P.nseg] = carry;
+    }
     if (threadIdx.x == 0) {
         st->spawn_total = 0;
         st->cand_total = 0;
@@ -235,12 +270,15 @@ __global__ void k_prologue(StepParams P)
 
 // ---------------------------------------------------------------------------
 // Spawning, light parents [End Matter, spawn step], in two kernels.
-//   k_spawn_draw: a warp takes consecutive parents; their walker pairs (one
-//     Philox call per two walkers) are spread evenly over the lanes; a walker
-//     whose T = R >> 12 (52 bits) lies below the program's bound on P becomes
-//     a candidate.  Parents with many walkers become heavy work items.
-//   k_spawn_choose: one thread per candidate evaluates the exact weight P of
-//     the parent's column; the walker spawns iff T < P, onto the destination
+//   k_spawn_draw: a warp takes rank groups of four consecutive parents, one
+//     group per lane: one Philox call gives the 32-bit draw words W of the
+//     four parents' first walkers, further walkers take four words per call
+//     of their parent; a walker whose W passes the program's prefilter
+//     (W <= P_bound >> 20) becomes a candidate.  Parents with many walkers
+//     become heavy work items.
+//   k_spawn_choose: one thread per candidate completes the walker's draw
+//     T = W << 20 | L (52 bits), evaluates the exact weight P of the
+//     parent's column; the walker spawns iff T < P, onto the destination
 //     whose cumulative-weight interval holds T (canonical order).
 // ---------------------------------------------------------------------------
 constexpr int kProgSmem = 8192;
@@ -323,7 +361,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
 // Bounded wait for a phase of an mbarrier.
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st, uint32_t site, int64_t idx)
 {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < kMbarSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (it > 16) __nanosleep(32);
     }
@@ -332,8 +370,8 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st, uint32_t
 }
 
 constexpr int kCandStage = 128;   // candidates staged per warp
-constexpr int kCandFlush = 64;    // a warp flushes once more than this are staged
-constexpr uint64_t kT52 = (1ull << 52) - 1ull;
+constexpr int kCandFlush = 96;    // a warp flushes once more than this are staged (at most 32 join at a time)
+constexpr uint32_t kJ20 = (1u << 20) - 1u;
 
 // Append a warp's staged candidates to the candidate list of the step.
 __device__ __forceinline__ void cand_flush(const SpawnCand* stage, int n, const StepParams& P, int lane)
@@ -351,19 +389,15 @@ __device__ __forceinline__ void cand_flush(const SpawnCand* stage, int n, const 
     __syncwarp();
 }
 
-// Stage the lanes' candidates c0 (first walker of the pair) and c1 (second);
-// flushes once the stage holds more than kCandFlush.  Whole warp.
-__device__ __forceinline__ void cand_push(SpawnCand* stage, int* staged, bool c0, bool c1, uint32_t parent,
-                                          uint32_t seg, uint64_t t0, uint64_t t1, const StepParams& P, int lane)
+// Stage the lanes' candidates (at most one per lane); flushes once the stage
+// holds more than kCandFlush.  Whole warp.
+__device__ __forceinline__ void cand_push(SpawnCand* stage, int* staged, bool c, const uint4& v, const StepParams& P,
+                                          int lane)
 {
-    const uint32_t b0 = __ballot_sync(kFull, c0), b1 = __ballot_sync(kFull, c1);
-    if ((b0 | b1) == 0u) return;
-    const uint32_t lt = (1u << lane) - 1u;
-    const int n0 = __popc(b0);
-    uint4* s4 = (uint4*)stage;
-    if (c0) s4[*staged + __popc(b0 & lt)] = make_uint4(parent, seg, (uint32_t)t0, (uint32_t)(t0 >> 32));
-    if (c1) s4[*staged + n0 + __popc(b1 & lt)] = make_uint4(parent, seg, (uint32_t)t1, (uint32_t)(t1 >> 32));
-    *staged += n0 + __popc(b1);
+    const uint32_t b = __ballot_sync(kFull, c);
+    if (b == 0u) return;
+    if (c) ((uint4*)stage)[*staged + __popc(b & ((1u << lane) - 1u))] = v;
+    *staged += __popc(b);
     __syncwarp();
     if (*staged > kCandFlush) {
         cand_flush(stage, *staged, P, lane);
@@ -371,15 +405,13 @@ __device__ __forceinline__ void cand_push(SpawnCand* stage, int* staged, bool c0
     }
 }
 
-// One parent record, read once (streamed past L1).
-__device__ __forceinline__ Rec load_parent(const Rec* p)
+// Candidate word w: the walker's index j in its component (20 bits), the
+// component, the pass, the initiator flag and the sign of the parent's
+// component (SpawnCand).
+__device__ __forceinline__ uint32_t cand_meta(uint32_t j, int comp, int phase, int noninit, int32_t val)
 {
-    const uint4 v = __ldcs((const uint4*)p);
-    Rec r;
-    r.key = ((uint64_t)v.y << 32) | v.x;
-    r.re = (int32_t)v.z;
-    r.im = (int32_t)v.w;
-    return r;
+    return j | ((uint32_t)comp << 20) | ((uint32_t)phase << 21) | ((uint32_t)noninit << 22) |
+           ((uint32_t)(val > 0 ? 1 : 0) << 23);
 }
 
 // Emit the heavy work items of one parent (one per kHeavyChunk walkers of
@@ -416,10 +448,11 @@ __device__ __forceinline__ const uint8_t* prog_ptr(const StepParams& P, const St
 }
 
 // Draw parameters of one vector in one pass of the current step: its Philox
-// key, bound << 12 on the raw draw (all: every walker is a candidate, the
-// bound having reached 2^52), and its instance's initiator threshold.
+// key, the prefilter bound on a walker's 32-bit word W (T = W << 20 | L < P
+// needs W <= P >> 20; all: every walker is a candidate, the bound having
+// reached 2^52), and its instance's initiator threshold.
 struct SegDraw {
-    uint64_t b12;
+    uint32_t pre;
     int64_t init_min;
     uint2 kd;
     bool all;
@@ -432,275 +465,248 @@ __device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo&
     const int64_t pb = P.proposal ? h->p_att : h->p_bound;   // attempt bound of the choice rule
     SegDraw d;
     d.all = pb >= (1ll << 52);
-    d.b12 = d.all ? ~0ull : (uint64_t)pb << 12;
+    d.pre = d.all ? 0xFFFFFFFFu : (uint32_t)(pb >> 20);
     d.init_min = P.inst[si.inst].init_min;
     d.kd = P.kd[seg];
     return d;
 }
 
-__device__ __forceinline__ bool below(const SegDraw& d, uint64_t X) { return d.all || X < d.b12; }
+__device__ __forceinline__ bool passes(const SegDraw& d, uint32_t W) { return d.all || W <= d.pre; }
 
-// Low 52 bits of a candidate: its draw T, or under the learned proposal (whose
-// destination does not depend on T) the walker's index j in its component.
-__device__ __forceinline__ uint64_t cand_low(const StepParams& P, uint64_t X, uint32_t j)
+// The walker draw's counters [reading R3]: for the parent at rank r of its
+// vector (index in the key-sorted population) in pass phase, walker w (real
+// walkers first) has T = W << 20 | L with W word r % 4 of the group call
+// (w = 0) or word (w - 1) % 4 of the parent's call (w - 1) / 4, and L the top
+// 20 bits of word 0 of the walker's own call (component comp, index j).
+__device__ __forceinline__ uint4 group_words(uint32_t g, int phase, uint2 kd)
 {
-    return P.proposal == 2 ? (uint64_t)j : (X >> 12);
+    return philox10(make_uint4(g, 0u, (uint32_t)phase | (kKindGroup << 2), 0u), kd);
 }
 
-// Flags of a candidate: comp, phase, noninit, sign of the parent component.
-__device__ __forceinline__ uint64_t cand_flags(int comp, int phase, int noninit, int32_t val)
+__device__ __forceinline__ uint4 extra_words(uint32_t rank, uint32_t b, int phase, uint2 kd)
 {
-    return ((uint64_t)comp << 52) | ((uint64_t)phase << 53) | ((uint64_t)noninit << 54) |
-           ((uint64_t)(val > 0 ? 1 : 0) << 55);
+    return philox10(make_uint4(rank, b, (uint32_t)phase | (kKindExtra << 2), 0u), kd);
 }
 
-// Slow path of one group of 32 parents (whole warp): parents with more than
-// one walker pair, and heavy parents (emitted as heavy work items).  All pairs
-// of the group are spread evenly over the lanes.
-__device__ __forceinline__ void draw_group_general(const StepParams& P, SpawnCand* stage, int* staged, bool valid,
-                                                Rec par, uint32_t j, int phase, int seg, const SegDraw& sd,
-                                                int lane)
+__device__ __forceinline__ int64_t walker_T(uint32_t W, uint32_t rank, uint32_t j, int comp, int phase, uint2 kd)
 {
-    const uint32_t are = valid ? (par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re) : 0u;
-    const uint32_t aim = valid ? (par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im) : 0u;
-    const uint64_t mtot = (uint64_t)are + aim;
-    const bool heavy = mtot > (uint64_t)P.heavy_walkers;
-    const int noninit = (sd.init_min > 0 && (int64_t)mtot < sd.init_min) ? 1 : 0;
-    if (heavy) emit_heavy(P, j, phase, seg, are, aim);
-    const uint32_t pre = heavy ? 0u : (are + 1u) >> 1, pim = heavy ? 0u : (aim + 1u) >> 1;
-    const int my_pairs = (int)(pre + pim);
-    int incl = my_pairs;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
+    const uint4 o = philox10(make_uint4(rank, j, (uint32_t)phase | ((uint32_t)comp << 1) | (kKindLow << 2), 0u), kd);
+    return (int64_t)((((uint64_t)W) << 20) | (o.x >> 12));
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& o, int k)
+{
+    return k == 0 ? o.x : (k == 1 ? o.y : (k == 2 ? o.z : o.w));
+}
+
+// Vector holding group G of a slot: the largest s with gof[s] <= G (s = nseg
+// for G = the slot's group count).
+__device__ __forceinline__ int group_seg(const int64_t* gof, int nseg, int64_t G)
+{
+    int lo = 0, hi = nseg;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&gof[mid]) <= G) lo = mid; else hi = mid - 1;
     }
-    const int tot_pairs = __shfl_sync(kFull, incl, 31);
-    for (int r = 0; r < tot_pairs; r += 32) {
-        const int g = r + lane;
-        int lo = 0, hi = 31;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const int im = __shfl_sync(kFull, incl, mid);
-            if (im > g) hi = mid; else lo = mid + 1;
-        }
-        const int owner = lo;
-        const bool act = g < tot_pairs;
-        const int o_incl = __shfl_sync(kFull, incl, owner);
-        const int o_pairs = __shfl_sync(kFull, my_pairs, owner);
-        const int local = g - (o_incl - o_pairs);
-        const uint64_t okey = __shfl_sync(kFull, par.key, owner);
-        const int o_pre = __shfl_sync(kFull, (int)pre, owner);
-        const uint32_t o_are = __shfl_sync(kFull, are, owner);
-        const uint32_t o_aim = __shfl_sync(kFull, aim, owner);
-        const int o_seg = __shfl_sync(kFull, seg, owner);
-        const int o_non = __shfl_sync(kFull, noninit, owner);
-        const int32_t o_re = __shfl_sync(kFull, par.re, owner);
-        const int32_t o_im = __shfl_sync(kFull, par.im, owner);
-        const uint32_t o_j = __shfl_sync(kFull, j, owner);
-        SegDraw od;
-        od.kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
-        od.b12 = __shfl_sync(kFull, sd.b12, owner);
-        od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
-        bool c0 = false, c1 = false;
-        uint64_t t0 = 0, t1 = 0;
-        if (act) {
-            const int comp = local < o_pre ? 0 : 1;
-            const int j2 = comp ? local - o_pre : local;
-            const uint32_t m = comp ? o_aim : o_are;
-            const uint4 w = philox10(
-                make_uint4((uint32_t)okey, (uint32_t)(okey >> 32),
-                           (uint32_t)phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                od.kd);
-            const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
-            const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
-            const uint64_t fl = cand_flags(comp, phase, o_non, comp ? o_im : o_re);
-            c0 = below(od, X0);
-            c1 = 2u * (uint32_t)j2 + 1u < m && below(od, X1);
-            t0 = cand_low(P, X0, 2u * (uint32_t)j2) | fl;
-            t1 = cand_low(P, X1, 2u * (uint32_t)j2 + 1u) | fl;
-        }
-        cand_push(stage, staged, c0, c1, o_j, (uint32_t)o_seg, t0, t1, P, lane);
-    }
+    return lo;
 }
 
-// Second walker pairs of parents with two pairs, queued per warp and drawn 32
-// at a time: (parent index, vector) in a ring of kPairRing entries.
-constexpr int kPairRing = 128;
-constexpr int kDrawChunk = 64;    // parents per staged chunk (1 KB)
-constexpr int kDrawStages = 4;    // staged chunks per warp
-
-__device__ __forceinline__ void draw_second_pairs(const StepParams& P, const StepInfo& inf, SpawnCand* stage,
-                                                  int* staged, const uint2* ring, int head, int cnt, const Rec* src,
-                                                  int phase, int lane)
-{
-    bool c0 = false, c1 = false;
-    uint64_t t0 = 0, t1 = 0;
-    uint2 it = make_uint2(0u, 0u);
-    if (lane < cnt) {
-        it = ring[(head + lane) & (kPairRing - 1)];
-        const Rec par = load_parent(src + it.x);
-        const uint32_t are = par.re < 0 ? 0u - (uint32_t)par.re : (uint32_t)par.re;
-        const uint32_t aim = par.im < 0 ? 0u - (uint32_t)par.im : (uint32_t)par.im;
-        // pairs are numbered real component first: the second pair is pair 1
-        // of the real component (3 or 4 real walkers) or pair 0 of the
-        // imaginary one
-        const uint32_t comp = are >= 3u ? 0u : 1u;
-        const uint32_t j2 = are >= 3u ? 1u : (aim >= 3u && are == 0u ? 1u : 0u);
-        const uint32_t m = comp ? aim : are;
-        const SegDraw sd = seg_draw(P, inf, (int)it.y, phase);
-        const uint4 w = philox10(make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                                            (uint32_t)phase | (comp << 1) | (kKindSpawn << 2), j2),
-                                 sd.kd);
-        const uint64_t X0 = ((uint64_t)w.y << 32) | w.x;
-        const uint64_t X1 = ((uint64_t)w.w << 32) | w.z;
-        c0 = below(sd, X0);
-        c1 = 2u * j2 + 1u < m && below(sd, X1);
-        const int noninit = (sd.init_min > 0 && (int64_t)((uint64_t)are + aim) < sd.init_min) ? 1 : 0;
-        const uint64_t fl = cand_flags((int)comp, phase, noninit, comp ? par.im : par.re);
-        t0 = cand_low(P, X0, 2u * j2) | fl;
-        t1 = cand_low(P, X1, 2u * j2 + 1u) | fl;
-    }
-    cand_push(stage, staged, c0, c1, it.x, it.y, t0, t1, P, lane);
-}
+constexpr int kDrawGroups = 32;                 // rank groups per warp iteration, one per lane
+constexpr int kDrawRecs = 4 * kDrawGroups;      // records staged per iteration (2 KB)
+constexpr int kDrawStages = 3;                  // staged iterations per warp
+constexpr int kDrawWarps = kThreads / 32;
+constexpr int kDrawSmem = kDrawWarps * (kDrawStages * kDrawRecs * 16 + kCandStage * 16);
 
 // Walker draws of one population slot (phase 0: N(t), phase 1: N(t - dt)).
-// The warp owns parents [wb, we) of the slot and reads them 64 at a time
-// (lane l takes parents g0 + l and g0 + 32 + l), one group ahead.  In the
-// common group every parent has at most two walker pairs: each lane draws its
-// parents' first pairs (one Philox call each, the raw 64-bit output X compared
-// with bound << 12: T = X >> 12 < bound iff X < bound << 12), and second pairs
-// are queued and drawn 32 at a time.  A half-group with more pairs per parent,
-// or heavy parents, takes the general path.
-__device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint2* ring,
-                                          Rec* buf, uint64_t* bar, uint32_t* chunk_no, const Rec* src,
-                                          const int64_t* off, int64_t wb, int64_t we, int phase, const StepInfo& inf,
-                                          int lane)
+// The slot's records form rank groups of four consecutive records of one
+// vector (the last group of a vector may be shorter); the warp owns groups
+// [gb, ge) and takes them 32 at a time, lane l group G0 + l, their records
+// staged by one bulk copy per iteration (kDrawStages - 1 iterations ahead).
+// A lane draws its group call (one Philox call: the first walkers of its four
+// parents) and compares each word with the vector's prefilter bound;
+// further walkers of parents with two or more take their parents' calls
+// (four walkers each), spread evenly over the lanes.  Parents with more than
+// heavy_walkers walkers become heavy work items (all their walkers).
+__device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, Rec* buf, uint64_t* bar,
+                                          uint32_t* use_no, const Rec* src, const int64_t* off, const int64_t* gof,
+                                          int64_t gb, int64_t ge, int phase, const StepInfo& inf, int lane)
 {
-    const uint32_t lt = (1u << lane) - 1u;
+    const int nseg = P.nseg;
+    const int64_t Gt = gof[nseg];
+    const int64_t nit = (ge - gb + kDrawGroups - 1) / kDrawGroups;
+    const uint32_t u0 = *use_no;
+    bool gave_up = false;
+    // lane 0: a cursor over the slot's vectors for the copies issued ahead
+    // (the iterations' record ranges follow one another)
+    int cs = 0;
+    int64_t c_gof = 0, c_gend = 0, c_off = 0, next_r = 0;
+    if (lane == 0 && nit > 0) {
+        cs = group_seg(gof, nseg, gb);
+        c_gof = __ldg(&gof[cs]);
+        c_gend = __ldg(&gof[cs + 1]);
+        c_off = __ldg(&off[cs]);
+        next_r = c_off + 4 * (gb - c_gof);
+    }
+    auto rec_at = [&](int64_t B) -> int64_t {   // first record of group B (B > the last one asked)
+        if (B >= Gt) return __ldg(&off[nseg]);
+        while (B >= c_gend) {
+            ++cs;
+            c_gof = c_gend;
+            c_gend = __ldg(&gof[cs + 1]);
+            c_off = __ldg(&off[cs]);
+        }
+        return c_off + 4 * (B - c_gof);
+    };
+    // lane 0: bulk copy of iteration k's records into stage (u0 + k) % kDrawStages
+    auto issue = [&](int64_t k) {
+        const uint32_t u = u0 + (uint32_t)k;
+        const int64_t B = min(ge, gb + (k + 1) * kDrawGroups);
+        const int64_t r0 = next_r, r1 = rec_at(B);
+        next_r = r1;
+        const uint32_t bytes = (uint32_t)(r1 - r0) * 16u;
+        uint64_t* b = bar + u % kDrawStages;
+        fence_proxy_async();
+        mbar_arrive_expect(b, bytes);
+        bulk_load(buf + (u % kDrawStages) * kDrawRecs, src + r0, bytes, b);
+    };
+    if (lane == 0)
+        for (int64_t k = 0; k < kDrawStages - 1 && k < nit; ++k) issue(k);
+    // the lane's vector (cached while its groups stay inside it)
     int seg = 0;
-    int64_t seg_end = -1;
-    SegDraw sd;   // draw parameters of the lane's current vector
-    sd.b12 = 0ull;
+    int64_t seg_gend = -1, seg_off = 0, seg_gof = 0, seg_K = 0;
+    SegDraw sd;
+    sd.pre = 0u;
     sd.init_min = 0;
     sd.kd = make_uint2(0u, 0u);
     sd.all = false;
-    int head = 0, cnt = 0;   // ring of queued second pairs
-    // chunks of kDrawChunk parents staged by bulk copies, kDrawStages - 1 ahead;
-    // the warp's c-th chunk overall uses stage c % kDrawStages
-    const int64_t nch = (we - wb + kDrawChunk - 1) / kDrawChunk;
-    const uint32_t c0 = *chunk_no;
-    bool gave_up = false;
-    auto issue = [&](int64_t j) {
-        const uint32_t c = c0 + (uint32_t)j;
-        const int64_t g = wb + j * kDrawChunk;
-        const uint32_t bytes = (uint32_t)min((int64_t)kDrawChunk, we - g) * 16u;
-        uint64_t* b = bar + c % kDrawStages;
-        fence_proxy_async();
-        mbar_arrive_expect(b, bytes);
-        bulk_load(buf + (c % kDrawStages) * kDrawChunk, src + g, bytes, b);
-    };
-    if (lane == 0)
-        for (int64_t j = 0; j < kDrawStages - 1 && j < nch; ++j) issue(j);
-    for (int64_t j = 0; j < nch; ++j) {
-        const int64_t g0 = wb + j * kDrawChunk;
-        const uint32_t c = c0 + (uint32_t)j;
-        if (lane == 0 && j + kDrawStages - 1 < nch) issue(j + kDrawStages - 1);
-        const Rec* tb = buf + (c % kDrawStages) * kDrawChunk;
-        const bool ok = mbar_wait(bar + c % kDrawStages, (c / kDrawStages) & 1u, P.st, 7u, j);
+    for (int64_t k = 0; k < nit; ++k) {
+        const uint32_t u = u0 + (uint32_t)k;
+        const int64_t G0 = gb + k * kDrawGroups;
+        const int64_t Gend = min(ge, G0 + kDrawGroups);
+        if (lane == 0 && k + kDrawStages - 1 < nit) issue(k + kDrawStages - 1);
+        const Rec* tb = buf + (u % kDrawStages) * kDrawRecs;
+        const bool ok = mbar_wait(bar + u % kDrawStages, (u / kDrawStages) & 1u, P.st, 7u, k);
         if (!ok) gave_up = true;
-        const int64_t iA = g0 + lane, iB = iA + 32;
-        const bool vA = ok && iA < we, vB = ok && iB < we;
-        Rec pA{0ull, 0, 0}, pB{0ull, 0, 0};
-        if (vA) pA = tb[lane];
-        if (vB) pB = tb[lane + 32];
-        __syncwarp();   // the stage is read before it is refilled
-        if (vA && iA >= seg_end) {
-            seg = seg_of(off, P.nseg, iA);
-            seg_end = __ldg(&off[seg + 1]);
+        const int64_t G = G0 + lane;
+        const bool valid = ok && G < Gend;
+        if (valid && G >= seg_gend) {
+            seg = group_seg(gof, nseg, G);
+            seg_gend = __ldg(&gof[seg + 1]);
+            seg_off = __ldg(&off[seg]);
+            seg_gof = __ldg(&gof[seg]);
+            seg_K = __ldg(&off[seg + 1]) - seg_off;
             sd = seg_draw(P, inf, seg, phase);
         }
-        const int segA = seg;
-        const SegDraw sdA = sd;
-        if (vB && iB >= seg_end) {
-            seg = seg_of(off, P.nseg, iB);
-            seg_end = __ldg(&off[seg + 1]);
-            sd = seg_draw(P, inf, seg, phase);
+        const uint32_t g = (uint32_t)(G - seg_gof);
+        const int64_t first = seg_off + 4 * (int64_t)g;
+        const int cnt = valid ? (int)min((int64_t)4, seg_K - 4 * (int64_t)g) : 0;
+        // the stage starts at the first record of group G0, lane 0's
+        const int64_t r0 = __shfl_sync(kFull, first, 0);
+        const int pos = (int)(first - r0);
+        const uint4 gw = group_words(g, phase, sd.kd);
+        int ne[4];         // extra calls of the lane's four parents
+        int total_ne = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            Rec r{0ull, 0, 0};
+            if (i < cnt) r = tb[pos + i];
+            const uint32_t are = r.re < 0 ? 0u - (uint32_t)r.re : (uint32_t)r.re;
+            const uint32_t aim = r.im < 0 ? 0u - (uint32_t)r.im : (uint32_t)r.im;
+            const uint64_t m = (uint64_t)are + aim;
+            const bool heavy = m > (uint64_t)P.heavy_walkers;
+            if (__any_sync(kFull, heavy) && heavy) emit_heavy(P, first + i, phase, seg, are, aim);
+            const int comp = are ? 0 : 1;
+            const int noninit = (sd.init_min > 0 && (int64_t)m < sd.init_min) ? 1 : 0;
+            const uint32_t W = word_of(gw, i);
+            const bool c = i < cnt && !heavy && passes(sd, W);
+            cand_push(stage, staged, c,
+                      make_uint4((uint32_t)(first + i), (uint32_t)seg, W,
+                                 cand_meta(0u, comp, phase, noninit, comp ? r.im : r.re)),
+                      P, lane);
+            ne[i] = (i < cnt && !heavy && m >= 2) ? (int)((m + 2) / 4) : 0;
+            total_ne += ne[i];
         }
-        const uint32_t areA = vA ? (pA.re < 0 ? 0u - (uint32_t)pA.re : (uint32_t)pA.re) : 0u;
-        const uint32_t aimA = vA ? (pA.im < 0 ? 0u - (uint32_t)pA.im : (uint32_t)pA.im) : 0u;
-        const uint32_t areB = vB ? (pB.re < 0 ? 0u - (uint32_t)pB.re : (uint32_t)pB.re) : 0u;
-        const uint32_t aimB = vB ? (pB.im < 0 ? 0u - (uint32_t)pB.im : (uint32_t)pB.im) : 0u;
-        const uint32_t prA = ((areA + 1u) >> 1) + ((aimA + 1u) >> 1);
-        const uint32_t prB = ((areB + 1u) >> 1) + ((aimB + 1u) >> 1);
-        if (!__all_sync(kFull, (areA | aimA | areB | aimB) <= 4u && prA <= 2u && prB <= 2u)) {
-            draw_group_general(P, stage, staged, vA, pA, (uint32_t)iA, phase, segA, sdA, lane);
-            draw_group_general(P, stage, staged, vB, pB, (uint32_t)iB, phase, seg, sd, lane);
-            continue;
+        // further walkers: the warp's extra calls, 32 at a time
+        int incl = total_ne;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
         }
-        // queue the second pairs
-        const uint32_t btA = __ballot_sync(kFull, prA == 2u), btB = __ballot_sync(kFull, prB == 2u);
-        if (btA | btB) {
-            const int q = head + cnt;
-            if (prA == 2u) ring[(q + __popc(btA & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)iA, (uint32_t)segA);
-            if (prB == 2u)
-                ring[(q + __popc(btA) + __popc(btB & lt)) & (kPairRing - 1)] = make_uint2((uint32_t)iB, (uint32_t)seg);
-            cnt += __popc(btA) + __popc(btB);
-            __syncwarp();
-            while (cnt >= 32) {
-                draw_second_pairs(P, inf, stage, staged, ring, head, 32, src, phase, lane);
-                head = (head + 32) & (kPairRing - 1);
-                cnt -= 32;
-                __syncwarp();
+        const int tot = __shfl_sync(kFull, incl, 31);
+        for (int rr = 0; rr < tot; rr += 32) {
+            const int gi = rr + lane;
+            int lo = 0, hi = 31;   // owner: the first lane whose inclusive count exceeds gi
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__shfl_sync(kFull, incl, mid) > gi) hi = mid; else lo = mid + 1;
+            }
+            const int owner = lo;
+            const bool act = gi < tot;
+            int local = gi - (__shfl_sync(kFull, incl, owner) - __shfl_sync(kFull, total_ne, owner));
+            int o_ne[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o_ne[q] = __shfl_sync(kFull, ne[q], owner);
+            const int o_pos = __shfl_sync(kFull, pos, owner);
+            const uint32_t o_first = __shfl_sync(kFull, (uint32_t)first, owner);
+            const int o_seg = __shfl_sync(kFull, seg, owner);
+            const uint32_t o_g = __shfl_sync(kFull, g, owner);
+            const uint2 o_kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
+            SegDraw od;
+            od.kd = o_kd;
+            od.pre = __shfl_sync(kFull, sd.pre, owner);
+            od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
+            od.init_min = __shfl_sync(kFull, sd.init_min, owner);
+            int i = 0;   // the owner's parent holding call `local`, then the call's index in it
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (i == q && local >= o_ne[q]) {
+                    local -= o_ne[q];
+                    ++i;
+                }
+            }
+            Rec r{0ull, 0, 0};
+            if (act) r = tb[o_pos + i];
+            const uint32_t are = r.re < 0 ? 0u - (uint32_t)r.re : (uint32_t)r.re;
+            const uint32_t aim = r.im < 0 ? 0u - (uint32_t)r.im : (uint32_t)r.im;
+            const uint64_t m = (uint64_t)are + aim;
+            const uint32_t rank = 4u * o_g + (uint32_t)i;
+            const uint4 xw = extra_words(rank, (uint32_t)local, phase, o_kd);
+            const int noninit = (od.init_min > 0 && (int64_t)m < od.init_min) ? 1 : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint64_t w = 1ull + 4ull * (uint64_t)local + (uint64_t)q;
+                const uint32_t W = word_of(xw, q);
+                const bool c = act && w < m && passes(od, W);
+                const int comp = w < are ? 0 : 1;
+                const uint32_t j = (uint32_t)(comp ? w - are : w);
+                cand_push(stage, staged, c,
+                          make_uint4(o_first + (uint32_t)i, (uint32_t)o_seg, W,
+                                     cand_meta(j, comp, phase, noninit, comp ? r.im : r.re)),
+                          P, lane);
             }
         }
-        // first pairs: pair 0 of the real component if it has walkers, else of the imaginary one
-        const uint32_t compA = areA == 0u ? 1u : 0u, compB = areB == 0u ? 1u : 0u;
-        const uint32_t mA = compA ? aimA : areA, mB = compB ? aimB : areB;
-        const uint4 wA = philox10(make_uint4((uint32_t)pA.key, (uint32_t)(pA.key >> 32),
-                                             (uint32_t)phase | (compA << 1) | (kKindSpawn << 2), 0u),
-                                  sdA.kd);
-        const uint4 wB = philox10(make_uint4((uint32_t)pB.key, (uint32_t)(pB.key >> 32),
-                                             (uint32_t)phase | (compB << 1) | (kKindSpawn << 2), 0u),
-                                  sd.kd);
-        const uint64_t XA0 = ((uint64_t)wA.y << 32) | wA.x, XA1 = ((uint64_t)wA.w << 32) | wA.z;
-        const uint64_t XB0 = ((uint64_t)wB.y << 32) | wB.x, XB1 = ((uint64_t)wB.w << 32) | wB.z;
-        const bool cA0 = mA != 0u && below(sdA, XA0), cA1 = mA >= 2u && below(sdA, XA1);
-        const bool cB0 = mB != 0u && below(sd, XB0), cB1 = mB >= 2u && below(sd, XB1);
-        if (__any_sync(kFull, cA0 || cA1)) {
-            const int non = (sdA.init_min > 0 && (int64_t)((uint64_t)areA + aimA) < sdA.init_min) ? 1 : 0;
-            const uint64_t fl = cand_flags((int)compA, phase, non, compA ? pA.im : pA.re);
-            cand_push(stage, staged, cA0, cA1, (uint32_t)iA, (uint32_t)segA, cand_low(P, XA0, 0u) | fl,
-                      cand_low(P, XA1, 1u) | fl, P, lane);
-        }
-        if (__any_sync(kFull, cB0 || cB1)) {
-            const int non = (sd.init_min > 0 && (int64_t)((uint64_t)areB + aimB) < sd.init_min) ? 1 : 0;
-            const uint64_t fl = cand_flags((int)compB, phase, non, compB ? pB.im : pB.re);
-            cand_push(stage, staged, cB0, cB1, (uint32_t)iB, (uint32_t)seg, cand_low(P, XB0, 0u) | fl,
-                      cand_low(P, XB1, 1u) | fl, P, lane);
-        }
+        __syncwarp();   // every read of the stage done before it is refilled
     }
-    if (cnt > 0) draw_second_pairs(P, inf, stage, staged, ring, head, cnt, src, phase, lane);
     if (gave_up) {
         // a copy may still be landing in the last stages: wait for them once more (bounded)
-        for (int64_t j = nch > kDrawStages ? nch - kDrawStages : 0; j < nch; ++j) {
-            const uint32_t c = c0 + (uint32_t)j;
-            mbar_wait(bar + c % kDrawStages, (c / kDrawStages) & 1u, P.st, 7u, j);
+        for (int64_t k = nit > kDrawStages ? nit - kDrawStages : 0; k < nit; ++k) {
+            const uint32_t u = u0 + (uint32_t)k;
+            mbar_wait(bar + u % kDrawStages, (u / kDrawStages) & 1u, P.st, 7u, k);
         }
     }
-    *chunk_no = c0 + (uint32_t)nch;
+    *use_no = u0 + (uint32_t)nit;
 }
 
 __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
 {
-    __shared__ __align__(16) SpawnCand sstage[kThreads / 32][kCandStage];
-    __shared__ __align__(16) uint2 sring[kThreads / 32][kPairRing];
-    __shared__ __align__(128) Rec sbuf[kThreads / 32][kDrawStages * kDrawChunk];
-    __shared__ __align__(8) uint64_t sbar[kThreads / 32][kDrawStages];
+    extern __shared__ __align__(128) uint4 dsm[];
+    __shared__ __align__(8) uint64_t sbar[kDrawWarps][kDrawStages];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SpawnCand* stage = sstage[warp];
+    Rec* buf = (Rec*)(dsm + warp * (kDrawStages * kDrawRecs));
+    SpawnCand* stage = (SpawnCand*)(dsm + kDrawWarps * kDrawStages * kDrawRecs + warp * kCandStage);
     if (P.sort_mode)   // bucket counters of this step's spawn sort
         for (int b = blockIdx.x * kThreads + threadIdx.x; b < (1 << P.bucket_bits); b += gridDim.x * kThreads)
             P.bucket[b] = 0u;
@@ -709,30 +715,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
         mbar_fence_init();
     }
     __syncwarp();
-    uint32_t chunk_no = 0;
+    uint32_t use_no = 0;
     const StepInfo inf = P.info[st->call_index];
     const int cur = st->cur, prv = (cur + 2) % 3;
-    // filter: a walker can only spawn if T < P <= p_bound of its instance's
-    // program (every walker is a candidate when the bound reaches 2^52, so
-    // p >= 1 is still detected); see seg_draw
-    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * kDrawWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kDrawWarps + warp;
     int staged = 0;
     for (int phase = 0; phase < (inf.ab2 ? 2 : 1); ++phase) {
         const int slot = phase ? prv : cur;
-        const int64_t K = st->count[slot];
-        // each warp owns one contiguous range of the slot, a multiple of 64
-        const int64_t chunk = ((K + nwarps - 1) / nwarps + 63) / 64 * 64;
-        const int64_t wb = min(K, gw * chunk), we = min(K, wb + chunk);
-        draw_slot(P, stage, &staged, sring[warp], sbuf[warp], sbar[warp], &chunk_no, P.pop[slot], P.segoff[slot],
-                  wb, we, phase, inf, lane);
+        const int64_t* gof = P.gofs[slot];
+        const int64_t Gt = gof[P.nseg];
+        // each warp owns one contiguous range of the slot's rank groups, a multiple of 32
+        const int64_t chunk = ((Gt + nwarps - 1) / nwarps + kDrawGroups - 1) / kDrawGroups * kDrawGroups;
+        const int64_t gb = min(Gt, gw * chunk), ge = min(Gt, gb + chunk);
+        draw_slot(P, stage, &staged, buf, sbar[warp], &use_no, P.pop[slot], P.segoff[slot], gof, gb, ge, phase, inf,
+                  lane);
     }
     if (staged) cand_flush(stage, staged, P, lane);
 }
 
 // One thread per candidate: exact weight P of the parent's column, the spawn
 // test T < P, and the destination.  Programs are staged in shared memory.
-__global__ void __launch_bounds__(kThreads, 4) k_spawn_choose(StepParams P)
+__global__ void __launch_bounds__(kThreads, 3) k_spawn_choose(StepParams P)
 {
     __shared__ __align__(16) uint8_t sprog[2][kProgSmem];
     __shared__ __align__(16) SRec sstage[kThreads / 32][kStage];
@@ -759,10 +763,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_spawn_choose(StepParams P)
         bool ok = false;
         if (i < total) {
             const uint4 cv = __ldcs((const uint4*)P.cand + i);
-            const uint64_t tf = ((uint64_t)cv.w << 32) | cv.z;
-            const int comp = (int)((tf >> 52) & 1u), phase = (int)((tf >> 53) & 1u);
-            const int non = (int)((tf >> 54) & 1u), sg = ((tf >> 55) & 1u) ? 1 : -1;
-            const int64_t T = (int64_t)(tf & kT52);
+            const int comp = (int)((cv.w >> 20) & 1u), phase = (int)((cv.w >> 21) & 1u);
+            const int non = (int)((cv.w >> 22) & 1u), sg = ((cv.w >> 23) & 1u) ? 1 : -1;
+            // the walker's full draw from its rank in the vector
+            const uint32_t rank = cv.x - (uint32_t)__ldg(&P.segoff[phase ? prv : cur][cv.y]);
+            const int64_t T = walker_T(cv.z, rank, cv.w & kJ20, comp, phase, P.kd[cv.y]);
             const uint64_t key = __ldg(&(phase ? src1 : src0)[cv.x].key);
             const SegInfo si = P.seginfo[cv.y];
             const int n = si.n;
@@ -774,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_spawn_choose(StepParams P)
                 int chan;
                 int64_t v;
                 if (prog.h->p_att >= (1ll << 52)) set_error(st, DERR_DT_TOO_LARGE);
-                else if (proposal_choose(prog, x, y, T, &mk, &chan, &v)) {
+                else if (T < prog.h->p_att && proposal_choose(prog, x, y, T, &mk, &chan, &v)) {
                     ok = true;
                     rec = make_spawn(key ^ mk, (int)cv.y, comp, chan, v, sg, phase ? -1 : 1, non, 1);
                 }
@@ -982,10 +987,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
         bool ok[2] = {false, false};
         if (i < total) {
             const uint4 cv = __ldcs((const uint4*)P.cand + i);
-            const uint64_t tf = ((uint64_t)cv.w << 32) | cv.z;
-            const int comp = (int)((tf >> 52) & 1u), phase = (int)((tf >> 53) & 1u);
-            const int non = (int)((tf >> 54) & 1u), sg = ((tf >> 55) & 1u) ? 1 : -1;
-            const uint32_t j = (uint32_t)(tf & kT52);
+            const int comp = (int)((cv.w >> 20) & 1u), phase = (int)((cv.w >> 21) & 1u);
+            const int non = (int)((cv.w >> 22) & 1u), sg = ((cv.w >> 23) & 1u) ? 1 : -1;
+            const uint32_t j = cv.w & kJ20;
+            const uint32_t rank = cv.x - (uint32_t)__ldg(&P.segoff[phase ? prv : cur][cv.y]);
+            const int64_t T = walker_T(cv.z, rank, j, comp, phase, P.kd[cv.y]);
             const uint64_t key = __ldg(&(phase ? src1 : src0)[cv.x].key);
             const int n = P.seginfo[cv.y].n;
             const uint32_t x = (uint32_t)(key >> n), y = (uint32_t)(key & (n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)));
@@ -994,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
             const int ns = prog.h->n_stat;
             if (p_att >= (1ll << 52)) {
                 set_error(st, DERR_DT_TOO_LARGE);
-            } else {
+            } else if (T < p_att) {   // an attempting walker
                 const float tf32 = __double2float_rn(inf.t[phase]);
                 float h1[kMaxHidden], h2[kMaxHidden];
                 for (int q = 0; q < net.H; ++q) h1[q] = lp_h1(net, q, x, y, n, tf32);
@@ -1259,25 +1265,35 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
 
         const int comp = it.comp;
         const int64_t m = iabs64(comp ? par.im : par.re);
+        // the chunk: walkers [w_lo, w_hi) of the component, numbered in the
+        // parent (real walkers first) from wb on
         const int64_t w_lo = (int64_t)it.chunk * kHeavyChunk;
         const int64_t w_hi = min(m, w_lo + kHeavyChunk);
+        const int64_t wb = comp ? iabs64(par.re) : 0;
+        const int64_t gw_lo = wb + w_lo, gw_hi = wb + w_hi;
         const uint2 kd = P.kd[it.seg];
-        const uint64_t b12 = (uint64_t)Pw << 12;
-        for (int64_t j2 = w_lo / 2 + tid; 2 * j2 < w_hi; j2 += kThreads) {
-            const uint4 w = philox10(
-                make_uint4((uint32_t)par.key, (uint32_t)(par.key >> 32),
-                           (uint32_t)it.phase | ((uint32_t)comp << 1) | (kKindSpawn << 2), (uint32_t)j2),
-                kd);
+        const uint32_t rank = (uint32_t)(it.parent - P.segoff[it.phase ? prv : cur][it.seg]);
+        const uint32_t pre = (uint32_t)(Pw >> 20);
+        // draw units: unit 0 is walker 0 (a word of the rank group's call),
+        // unit v >= 1 the parent's call v - 1 (walkers 4v - 3 .. 4v)
+        const int64_t v_lo = gw_lo == 0 ? 0 : 1 + ((gw_lo - 1) >> 2);
+        const int64_t v_hi = (gw_hi - 1 == 0 ? 0 : 1 + ((gw_hi - 2) >> 2)) + 1;
+        for (int64_t v = v_lo + tid; v < v_hi; v += kThreads) {
+            const uint4 o = v == 0 ? group_words(rank >> 2, it.phase, kd) : extra_words(rank, (uint32_t)(v - 1), it.phase, kd);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (2 * j2 + h >= w_hi) break;
-                const uint64_t R = h ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
-                if (R >= b12) continue;   // T = R >> 12 >= P
-                const int64_t T = (int64_t)(R >> 12);
+            for (int q = 0; q < 4; ++q) {
+                if (v == 0 && q > 0) break;
+                const int64_t w = v == 0 ? 0 : 4 * v - 3 + q;
+                if (w < gw_lo || w >= gw_hi) continue;
+                const uint32_t W = v == 0 ? word_of(o, (int)(rank & 3u)) : word_of(o, q);
+                if (W > pre) continue;   // T >= (pre + 1) << 20 > P
+                const uint32_t j = (uint32_t)(w - wb);
+                const int64_t T = walker_T(W, rank, j, comp, it.phase, kd);
+                if (T >= Pw) continue;
                 if (learned) {
                     uint32_t V;
                     double u[2];
-                    lp_draws(par.key, it.phase, comp, (uint32_t)(2 * j2 + h), kd, &V, &u[0], &u[1]);
+                    lp_draws(par.key, it.phase, comp, j, kd, &V, &u[0], &u[1]);
                     int lo = 0, hi = ns;   // first slot with cum > V
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -1471,7 +1487,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
                         if (done || hi - w < 0) continue;
                         unsigned long long x = v[w];
                         if (!lb_ready(x, epoch)) {
-                            if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st, 1u, hi - w)) {
+                            if (!lb_wait(P.sort_status + (hi - w) * 256 + d, epoch, &x, st, 1u, hi - w, P.spin_limit)) {
                                 done = true;
                                 continue;
                             }
@@ -1601,7 +1617,7 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(StepParams P)
             if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, tot));
         } else {
             if (lane == 0) st_vol(my, lb_word(epoch, kFlagAgg, tot));
-            excl = warp_lookback(P.bscan_status, tile, epoch, st, lane, 8u);
+            excl = warp_lookback(P.bscan_status, tile, epoch, st, lane, 8u, P.spin_limit);
             if (lane == 0) st_vol(my, lb_word(epoch, kFlagIncl, excl + tot));
         }
         if (lane == 0) s_excl = excl;
@@ -1946,7 +1962,7 @@ __device__ __forceinline__ uint64_t it_key(const uint4* buf, int i)
 // their statistics to ntot / dre / dim.  Returns the number of runs.
 __device__ __forceinline__ int merge_walk(const uint4* buf, const MTileG& m, const SRec* __restrict__ sorted,
                                           uint4* raw, DevState* st, uint32_t n, uint32_t ymask, long long* ntot,
-                                          long long* dre, long long* dim)
+                                          long long* dre, long long* dim, long long* zrow)
 {
     const int na = m.na, nb = m.nb, nt = na + nb;
     const int d0 = (int)threadIdx.x * kMergeItems;
@@ -1985,6 +2001,9 @@ __device__ __forceinline__ int merge_walk(const uint4* buf, const MTileG& m, con
         if ((uint32_t)(rkey >> n) == (uint32_t)(rkey & ymask)) {
             *dre += vr;
             *dim += vi;
+            // <Z_q> on the diagonal: Re N_xx of the states with bit q of x set
+            for (uint32_t xb = (uint32_t)(rkey >> n); xb; xb &= xb - 1u)
+                atomicAdd((unsigned long long*)&zrow[__ffs(xb) - 1], (unsigned long long)vr);
         }
         raw[nout] = make_uint4((uint32_t)rkey, (uint32_t)(rkey >> 32), (uint32_t)(int32_t)vr, (uint32_t)(int32_t)vi);
         ++nout;
@@ -2168,7 +2187,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
             if (sl.t >= T) break;
             unsigned long long excl = 0;
             if (sl.t > 0) {
-                excl = warp_lookback(P.merge_status, sl.t, epoch, st, lane, 2u);
+                excl = warp_lookback(P.merge_status, sl.t, epoch, st, lane, 2u, P.spin_limit);
                 if (lane == 0) st_vol(P.merge_status + sl.t, lb_word(epoch, kFlagIncl, excl + (unsigned long long)sl.count));
             }
             if (lane == 0) {
@@ -2225,7 +2244,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
             const uint32_t n = (uint32_t)P.seginfo[seg].n;   // the tile's vector's qubit count
             const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
             nout = merge_walk(inbuf + s * kMergeTile, m, sorted, raw + tid * kMergeItems, st, n, ymask, &my_ntot,
-                              &my_dre, &my_dim);
+                              &my_dre, &my_dim, P.zacc + 32 * (int64_t)seg);
         }
         // block scan of run counts, block sums of the statistics
         int incl = nout;
@@ -2306,6 +2325,10 @@ __global__ void k_finalize(StepParams P)
             if (ci < P.history_cap) {
                 SegStats h = P.segacc[s];
                 P.history[(int64_t)ci * P.nseg + s] = h;
+                // N^diag <Z_q> = sum of Re N_xx (-1)^(x_q) = Re N^diag - 2 (the part with bit q set)
+                const int nq = P.seginfo[s].n;
+                long long* zh = P.zhist + ((int64_t)ci * P.nseg + s) * P.n;
+                for (int q = 0; q < P.n; ++q) zh[q] = q < nq ? h.dre - 2 * P.zacc[32 * (int64_t)s + q] : 0ll;
             }
         }
         long long incl = c;
@@ -2498,6 +2521,120 @@ __global__ void k_lookup(StepParams P, int seg, const uint64_t* __restrict__ q, 
     }
 }
 
+// Overlap of every vector of N(t) with a target |psi> given on len basis
+// states idx[a] (psi as (re, im) pairs): sum over a, b of conj(psi_a) N_ab
+// psi_b [fidelity, Markovian circuit dynamics], one CTA per vector.  The
+// values N_ab are looked up exactly; the sum runs in one thread in the fixed
+// order (a, then b) with every product and sum rounded as written.
+__global__ void k_overlap_all(StepParams P, const uint64_t* __restrict__ idx, const double* __restrict__ psi, int len,
+                              double* __restrict__ out)
+{
+    __shared__ long long v[2 * kMaxOverlapLen * kMaxOverlapLen];
+    const DevState* st = P.st;
+    const int slot = st->cur;
+    const int seg = blockIdx.x;
+    const Rec* pop = P.pop[slot];
+    const int64_t lo0 = P.segoff[slot][seg], hi0 = P.segoff[slot][seg + 1];
+    const int n = P.seginfo[seg].n;
+    for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
+        const uint64_t key = (idx[e / len] << n) | idx[e % len];
+        int64_t lo = lo0, hi = hi0;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (pop[mid].key < key) lo = mid + 1; else hi = mid;
+        }
+        long long re = 0, im = 0;
+        if (lo < hi0 && pop[lo].key == key) {
+            re = pop[lo].re;
+            im = pop[lo].im;
+        }
+        v[2 * e] = re;
+        v[2 * e + 1] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sr = 0.0, si = 0.0;
+        for (int a = 0; a < len; ++a) {
+            for (int b = 0; b < len; ++b) {
+                const double nr = (double)v[2 * (a * len + b)], ni = (double)v[2 * (a * len + b) + 1];
+                const double car = psi[2 * a], cai = -psi[2 * a + 1];
+                const double pr = __dsub_rn(__dmul_rn(car, nr), __dmul_rn(cai, ni));
+                const double pi = __dadd_rn(__dmul_rn(car, ni), __dmul_rn(cai, nr));
+                sr = __dadd_rn(sr, __dsub_rn(__dmul_rn(pr, psi[2 * b]), __dmul_rn(pi, psi[2 * b + 1])));
+                si = __dadd_rn(si, __dadd_rn(__dmul_rn(pr, psi[2 * b + 1]), __dmul_rn(pi, psi[2 * b])));
+            }
+        }
+        out[2 * seg] = sr;
+        out[2 * seg + 1] = si;
+    }
+}
+
+// Add a non-negative 128-bit value to a (low, high) pair of 64-bit words.
+__device__ __forceinline__ void add_u128(unsigned long long* w, unsigned __int128 v)
+{
+    const unsigned long long lo = (unsigned long long)v;
+    unsigned long long hi = (unsigned long long)(v >> 64);
+    if (lo) {
+        const unsigned long long old = atomicAdd(&w[0], lo);
+        if (old + lo < old) ++hi;   // carry out of the low word
+    }
+    if (hi) atomicAdd(&w[1], hi);
+}
+
+// ||N - N^dagger||_F^2 of every vector of N(t) [End Matter on Hermiticity
+// preservation], exactly: each record contributes |N_xy - conj(N_yx)|^2 (the
+// transposed record found by binary search in its vector; the diagonal is its
+// own transpose) and, when the transposed state is unoccupied, also the
+// transposed entry's |N_xy|^2.  Each CTA takes a contiguous range of records;
+// a thread's sums go out once per vector it leaves.
+__global__ void k_antiherm(StepParams P, unsigned long long* __restrict__ out)
+{
+    const DevState* st = P.st;
+    const int slot = st->cur;
+    const Rec* pop = P.pop[slot];
+    const int64_t* off = P.segoff[slot];
+    const int64_t K = off[P.nseg];
+    const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(K, b0 + per);
+    int cs = -1, n = 32;
+    int64_t cs_lo = 0, cs_end = 0;
+    unsigned __int128 acc = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        if (cs < 0 || i >= cs_end) {
+            if (cs >= 0 && acc) add_u128(out + 2 * cs, acc);
+            acc = 0;
+            cs = seg_of(off, P.nseg, i);
+            cs_lo = off[cs];
+            cs_end = off[cs + 1];
+            n = P.seginfo[cs].n;
+        }
+        const Rec r = pop[i];
+        const uint64_t ymask = n == 32 ? 0xFFFFFFFFull : ((1ull << n) - 1ull);
+        const uint64_t x = r.key >> n, y = r.key & ymask;
+        const uint64_t tk = (y << n) | x;
+        long long tre = 0, tim = 0;
+        if (tk == r.key) {
+            tre = r.re;
+            tim = r.im;
+        } else {
+            int64_t lo = cs_lo, hi = cs_end;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (pop[mid].key < tk) lo = mid + 1; else hi = mid;
+            }
+            if (lo < cs_end && pop[lo].key == tk) {
+                tre = pop[lo].re;
+                tim = pop[lo].im;
+            }
+        }
+        const long long dre = (long long)r.re - tre, dim = (long long)r.im + tim;
+        acc += (unsigned __int128)((__int128)dre * dre) + (unsigned __int128)((__int128)dim * dim);
+        if (tre == 0 && tim == 0)
+            acc += (unsigned __int128)((__int128)r.re * r.re) + (unsigned __int128)((__int128)r.im * r.im);
+    }
+    if (cs >= 0 && acc) add_u128(out + 2 * cs, acc);
+}
+
 // Pack host-uploaded (key, re, im) arrays into records of one slot and check
 // them: keys ascending within each vector, below 2^(2n), values nonzero and not
 // -2^31.  A violation sets *bad (the caller rejects the call).
@@ -2560,12 +2697,13 @@ int resident(const void* fn, int smem, int sms, int threads = kThreads)
 void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
+    cudaFuncSetAttribute(k_spawn_draw, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrawSmem);
     cudaFuncSetAttribute(k_bucket_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSortSmem);
     cudaFuncSetAttribute(k_bucket_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSortSmem);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_grid_spawn = resident((const void*)k_spawn_draw, 0, sms);
+    g_grid_spawn = resident((const void*)k_spawn_draw, kDrawSmem, sms);
     g_grid_choose = resident((const void*)k_spawn_choose, 0, sms);
     g_grid_learned = resident((const void*)k_spawn_learned, 0, sms);
     g_grid_heavy = resident((const void*)k_spawn_heavy, 0, sms);
@@ -2587,7 +2725,7 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(0);
     k_prologue<<<1, kThreads, 0, stream>>>(P);
     mark(1);
-    k_spawn_draw<<<cap(g_grid_spawn), kThreads, 0, stream>>>(P);
+    k_spawn_draw<<<cap(g_grid_spawn), kThreads, kDrawSmem, stream>>>(P);
     mark(2);
     if (P.proposal == 2)   // timed in the choose slot
         k_spawn_learned<<<cap(g_grid_learned), kThreads, 0, stream>>>(P);
@@ -2649,6 +2787,19 @@ int step_launch_count(const StepParams& P)
     // prologue, draw, choose, heavy; bucket sort; LSD histogram and passes;
     // segment offsets, merge plan, partition, merge, finalize
     return 4 + bucket + 1 + np + 5;
+}
+
+void launch_overlap_all(const StepParams& P, const uint64_t* idx, const double* psi, int len, double* out,
+                        cudaStream_t stream)
+{
+    k_overlap_all<<<P.nseg, kThreads, 0, stream>>>(P, idx, psi, len, out);
+}
+
+void launch_antiherm(const StepParams& P, unsigned long long* out, int grid, cudaStream_t stream)
+{
+    if (g_grid_spawn == 0) configure_kernels();
+    cudaMemsetAsync(out, 0, (size_t)P.nseg * 16, stream);
+    k_antiherm<<<grid > 0 ? grid : g_grid_misc, kThreads, 0, stream>>>(P, out);
 }
 
 void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,

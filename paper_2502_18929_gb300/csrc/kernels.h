@@ -19,15 +19,18 @@ constexpr int kMaxEntries = 1024;                    // destinations per column 
 constexpr int kMaxLearnedSlots = 256;                // destinations per column (learned proposal)
 constexpr int kMaxHidden = 64;                       // hidden width of the learned proposal's network
 constexpr int kMaxPasses = 12;
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;     // look-back polls before a wait gives up
 constexpr int kBucketBits = 20;                    // largest bucket digit of the spawn sort
 constexpr int kCtrMerge = kMaxPasses;                // tile counter index of the merge
 constexpr int kCtrSpawn = kMaxPasses + 1;            // tile counter index of the light spawn
 constexpr int kCtrBucket = kMaxPasses + 2;           // tile counter index of the bucket scan
 constexpr uint32_t kTagStep = 0x53544550u;
 constexpr uint32_t kTagInit = 0x494E4954u;
-constexpr uint32_t kKindSpawn = 0u;
 constexpr uint32_t kKindInit = 1u;
 constexpr uint32_t kKindLearned = 2u;
+constexpr uint32_t kKindGroup = 3u;     // spawn draws: first walkers of a rank group of four parents
+constexpr uint32_t kKindExtra = 4u;     // spawn draws: further walkers of one parent, four per call
+constexpr uint32_t kKindLow = 5u;       // spawn draws: the low 20 bits of one walker's T
 
 struct HeavyItem {
     int64_t parent;  // index inside its population slot
@@ -37,12 +40,15 @@ struct HeavyItem {
     int32_t seg;
 };
 
-// A walker whose draw T lies below its program's bound on P: a spawn
-// candidate, resolved against the exact column by k_spawn_choose.  16 bytes.
+// A walker whose 32-bit draw word W passes its program's prefilter (W <=
+// P_bound >> 20): a spawn candidate, completed (T = W << 20 | L) and resolved
+// against the exact column by k_spawn_choose.  16 bytes.
 struct __align__(16) SpawnCand {
     uint32_t parent;  // index of the parent inside its population slot
     uint32_t seg;     // population vector
-    uint64_t tf;      // T (52 bits) | comp << 52 | phase << 53 | noninit << 54 | (parent component > 0) << 55
+    uint32_t W;       // the walker's 32-bit draw word
+    uint32_t meta;    // j (walker index in its component, 20 bits) | comp << 20 | phase << 21 |
+                      // noninit << 22 | (parent component > 0) << 23
 };
 
 // One merge tile: its slices of the segment's N(t) records and sorted spawns,
@@ -67,6 +73,7 @@ struct StepParams {
     const uint8_t* progs;
     Rec* pop[3];
     int64_t* segoff[3];   // nseg + 1 offsets per slot
+    int64_t* gofs[3];     // nseg + 1 rank-group offsets per slot (k_prologue, for N(t) and N(t - dt))
     int64_t pop_cap;
     SRec* spawn;          // spawn records (sort ping-pong A)
     SRec* spawn_alt;      // sort ping-pong B
@@ -87,6 +94,8 @@ struct StepParams {
     SegStats* segacc;     // per-segment accumulators of the merge
     SegStats* history;    // [steps of call][nseg]
     int64_t history_cap;  // steps
+    long long* zacc;      // [nseg][32]: sum of Re N_xx over the diagonal records of N(t + dt) with bit q of x set
+    long long* zhist;     // [steps of call][nseg][n]: sum over the diagonal of Re N_xx (-1)^(x_q)
     int n;                // largest qubit count of the instances (key width of the sorts)
     int nseg;
     int seg_bits;
@@ -95,7 +104,7 @@ struct StepParams {
     int sort_mode;        // 0: LSD radix sort; 1: bucket pass + bucket sorts; 2: bucket pass alone
     int bucket_bits;      // bits of the bucket digit (<= kBucketBits)
     int bucket_kb;        // key bits in the bucket digit (below all segment bits)
-    int pad2;
+    uint32_t spin_limit;  // polls of another CTA's look-back word before a wait gives up (0: none)
     uint32_t* bucket;     // 2^bucket_bits bucket counters / cursors
     unsigned long long* bscan_status; // look-back words of the bucket scan, 2^(kBucketBits - 10)
     uint32_t* win;        // sort window starts, one per kSortWin spawn records
@@ -157,6 +166,12 @@ void launch_pack(const uint64_t* keys, const int32_t* re, const int32_t* im, con
                  const SegInfo* seginfo, Rec* dst, int* bad, cudaStream_t stream);
 void launch_obs(const StepParams& P, int which, SegStats* out, int grid, cudaStream_t stream);
 void launch_lookup(const StepParams& P, int seg, const uint64_t* q, int nq, int64_t* out, cudaStream_t stream);
+// Overlaps sum_ab conj(psi_a) N_ab psi_b of every vector of N(t) (out: nseg x (re, im)).
+constexpr int kMaxOverlapLen = 64;
+void launch_overlap_all(const StepParams& P, const uint64_t* idx, const double* psi, int len, double* out,
+                        cudaStream_t stream);
+// ||N - N^dagger||_F^2 of every vector of N(t), exactly (out: nseg x (low, high) 64-bit words, zeroed here).
+void launch_antiherm(const StepParams& P, unsigned long long* out, int grid, cudaStream_t stream);
 void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,
                  int64_t nnz, int64_t* tmp_vals, cudaStream_t stream);
 

@@ -117,6 +117,7 @@ StepParams params(qmc_ctx* c)
     for (int i = 0; i < 3; ++i) {
         P.pop[i] = c->d_pop[i];
         P.segoff[i] = c->d_segoff[i];
+        P.gofs[i] = c->d_gofs[i];
     }
     P.pop_cap = c->pop_cap;
     P.spawn = c->d_spawn;
@@ -137,6 +138,8 @@ StepParams params(qmc_ctx* c)
     P.merge_tiles_cap = c->merge_tiles_cap;
     P.segacc = c->d_segacc;
     P.history = c->d_history;
+    P.zacc = c->d_zacc;
+    P.zhist = c->d_zhist;
     P.history_cap = c->history_cap;
     P.n = c->cfg.n_qubits;
     P.nseg = c->cfg.n_segments;
@@ -165,6 +168,7 @@ StepParams params(qmc_ctx* c)
     P.ninst = (int)c->inst.size();
     P.proposal = c->proposal;
     P.heavy_walkers = c->heavy_walkers;
+    P.spin_limit = c->spin_limit;
     P.mlp = c->d_mlp;
     P.mlp_mask = c->d_mlp_mask;
     P.mlp_idx = c->d_mlp_idx;
@@ -296,6 +300,9 @@ int upload_calls(qmc_ctx* ctx, const std::vector<StepInfo>& info, const std::vec
     }
     if ((int64_t)info.size() > ctx->history_cap) {
         if ((rc = dalloc(ctx, &ctx->d_history, (int64_t)info.size() * ctx->cfg.n_segments)) != QMC_OK) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_zhist, (int64_t)info.size() * ctx->cfg.n_segments * ctx->cfg.n_qubits)) !=
+            QMC_OK)
+            return rc;
         ctx->history_cap = (int64_t)info.size();
         ctx->graph_dirty = true;
     }
@@ -374,6 +381,7 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     if (cudaMemset(ctx->d_state, 0, sizeof(DevState)) != cudaSuccess) return bail(QMC_ERR_CUDA);
     for (int i = 0; i < 3; ++i) {
         if ((rc = dalloc(ctx, &ctx->d_segoff[i], nseg + 1)) != QMC_OK) return bail(rc);
+        if ((rc = dalloc(ctx, &ctx->d_gofs[i], nseg + 1)) != QMC_OK) return bail(rc);
         if (cudaMemset(ctx->d_segoff[i], 0, (size_t)(nseg + 1) * 8) != cudaSuccess) return bail(QMC_ERR_CUDA);
     }
     if ((rc = dalloc(ctx, &ctx->d_kd, nseg)) != QMC_OK) return bail(rc);
@@ -385,6 +393,7 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     if ((rc = dalloc(ctx, &ctx->d_bseg, nseg + 1)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_tile_start, nseg + 1)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_segacc, nseg)) != QMC_OK) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_zacc, 32 * (int64_t)nseg)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_obs, nseg)) != QMC_OK) return bail(rc);
     ctx->heavy_cap = 4096;
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
@@ -483,9 +492,9 @@ void qmc_destroy(qmc_ctx* ctx)
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
-                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
+                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_gofs[0], ctx->d_gofs[1], ctx->d_gofs[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
-                    ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_info,
+                    ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_zacc, ctx->d_zhist, ctx->d_aux, ctx->d_info,
                     ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_mask,
                     ctx->d_mlp_idx, ctx->d_learn_prog, ctx->d_learn_scratch, ctx->d_learn_small};
     for (void* p : ptrs)
@@ -711,6 +720,15 @@ int qmc_set_tuning(qmc_ctx* ctx, const qmc_tuning* t)
     ctx->grid = t->max_ctas;
     ctx->heavy_walkers = t->heavy_walkers;
     ctx->bucket_records = t->bucket_records;
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
+int qmc_set_spin_limit(qmc_ctx* ctx, uint32_t polls)
+{
+    if (!ctx) return QMC_ERR_INVALID_ARG;
+    if (polls > ((uint32_t)1 << 30)) return fail(ctx, QMC_ERR_INVALID_ARG, "spin limit above 2^30 polls");
+    ctx->spin_limit = polls;
     ctx->graph_dirty = true;
     return QMC_OK;
 }
@@ -1158,6 +1176,20 @@ int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* cou
     return leave(ctx);
 }
 
+int qmc_z_history(qmc_ctx* ctx, int64_t* out, int64_t cap_steps, int64_t* count)
+{
+    if (!ctx || !out || !count) return QMC_ERR_INVALID_ARG;
+    const int64_t nsteps = std::min(cap_steps, ctx->last_call_steps);
+    *count = nsteps;
+    if (nsteps <= 0) return QMC_OK;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    CK(cudaMemcpyAsync(out, ctx->d_zhist, (size_t)nsteps * ctx->cfg.n_segments * ctx->cfg.n_qubits * 8,
+                       cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return leave(ctx);
+}
+
 int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t* re, int32_t* im, int64_t cap,
                int64_t* count)
 {
@@ -1274,6 +1306,68 @@ int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* ps
     }
     *out_re = sr;
     *out_im = si;
+    return leave(ctx);
+}
+
+namespace {
+int aux_reserve(qmc_ctx* ctx, int64_t bytes)
+{
+    if (bytes <= ctx->aux_cap) return QMC_OK;
+    int rc = dalloc(ctx, &ctx->d_aux, bytes);
+    if (rc == QMC_OK) ctx->aux_cap = bytes;
+    return rc;
+}
+} // namespace
+
+int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, const double* psi_im, int32_t len,
+                    double* out_re, double* out_im)
+{
+    if (!ctx || len < 1 || len > kMaxOverlapLen || !idx || !psi_re || !psi_im || !out_re || !out_im)
+        return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "no population");
+    const int nseg = ctx->cfg.n_segments;
+    int nmin = 64;
+    for (const auto& I : ctx->inst) nmin = std::min(nmin, (int)I.n);
+    for (int a = 0; a < len; ++a)
+        if (nmin < 64 && (idx[a] >> nmin)) return fail(ctx, QMC_ERR_INVALID_ARG, "target index >= 2^n");
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    const int64_t bytes = 8 * (int64_t)len + 16 * (int64_t)len + 16 * (int64_t)nseg;
+    if ((rc = aux_reserve(ctx, bytes)) != QMC_OK) return rc;
+    std::vector<double> psi(2 * (size_t)len);
+    for (int a = 0; a < len; ++a) {
+        psi[2 * a] = psi_re[a];
+        psi[2 * a + 1] = psi_im[a];
+    }
+    uint64_t* d_idx = (uint64_t*)ctx->d_aux;
+    double* d_psi = (double*)(ctx->d_aux + 8 * len);
+    double* d_out = (double*)(ctx->d_aux + 24 * len);
+    CK(cudaMemcpyAsync(d_idx, idx, 8 * (size_t)len, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(d_psi, psi.data(), 16 * (size_t)len, cudaMemcpyHostToDevice, ctx->work));
+    launch_overlap_all(params(ctx), d_idx, d_psi, len, d_out, ctx->work);
+    CK(cudaGetLastError());
+    std::vector<double> h(2 * (size_t)nseg);
+    CK(cudaMemcpyAsync(h.data(), d_out, 16 * (size_t)nseg, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (int s = 0; s < nseg; ++s) {
+        out_re[s] = h[2 * s];
+        out_im[s] = h[2 * s + 1];
+    }
+    return leave(ctx);
+}
+
+int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out)
+{
+    if (!ctx || !out) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "no population");
+    const int nseg = ctx->cfg.n_segments;
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if ((rc = aux_reserve(ctx, 16 * (int64_t)nseg)) != QMC_OK) return rc;
+    launch_antiherm(params(ctx), (unsigned long long*)ctx->d_aux, ctx->grid, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, ctx->d_aux, 16 * (size_t)nseg, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
     return leave(ctx);
 }
 

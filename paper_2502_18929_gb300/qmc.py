@@ -38,7 +38,8 @@ EXPORTED = [
     "qmc_step_profile", "qmc_kernel_name", "qmc_column_eval", "qmc_counters", "qmc_observables_noalloc",
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
-    "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune",
+    "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
+    "qmc_overlap_all", "qmc_antihermiticity",
 ]
 
 
@@ -131,6 +132,10 @@ def lib():
         L.qmc_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.qmc_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.qmc_autotune.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(Tuning)]
+        L.qmc_set_spin_limit.argtypes = [vp, C.c_uint32]
+        L.qmc_z_history.argtypes = [vp, vp, C.c_int64, vp]
+        L.qmc_overlap_all.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp]
+        L.qmc_antihermiticity.argtypes = [vp, vp]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -278,6 +283,11 @@ class QMC:
         t = Tuning(max_ctas, heavy_walkers, bucket_records, 0)
         self._check(self.L.qmc_set_tuning(self.h, C.byref(t)), "qmc_set_tuning")
 
+    def set_spin_limit(self, polls: int = 1 << 22):
+        """Polls of another CTA's look-back word before a device wait gives up
+        (the step then fails with ERR_DEVICE_TIMEOUT); 0 fails every such wait."""
+        self._check(self.L.qmc_set_spin_limit(self.h, polls), "qmc_set_spin_limit")
+
     def get_tuning(self) -> dict:
         t = Tuning()
         self._check(self.L.qmc_get_tuning(self.h, C.byref(t)), "qmc_get_tuning")
@@ -423,6 +433,40 @@ class QMC:
         self._check(self.L.qmc_step_history(self.h, buf.ctypes.data, buf.shape[0], C.byref(cnt)),
                     "qmc_step_history")
         return buf[:cnt.value]
+
+    def theta_history(self, cap_steps: int = 1 << 20) -> np.ndarray:
+        """(steps, n_segments) sign-problem phase theta = atan2(Im N^diag,
+        Re N^diag) after each step of the last ``step`` call, from the exact
+        per-step N^diag the merge accumulates [End Matter, sign-problem
+        suppression]."""
+        h = self.step_history(cap_steps)
+        return np.arctan2(h[:, :, 3].astype(np.float64), h[:, :, 2].astype(np.float64))
+
+    def z_history(self, cap_steps: int = 1 << 20) -> np.ndarray:
+        """(steps, n_segments, n_qubits) int64: N^diag <Z_q> after each step of
+        the last ``step`` call (sum over the diagonal of Re N_xx (-1)^(x_q))."""
+        buf = np.zeros((max(1, min(cap_steps, 1 << 22)), self.nseg, self.n), dtype=np.int64)
+        cnt = C.c_int64()
+        self._check(self.L.qmc_z_history(self.h, buf.ctypes.data, buf.shape[0], C.byref(cnt)), "qmc_z_history")
+        return buf[:cnt.value]
+
+    def overlap_all(self, psi: dict) -> np.ndarray:
+        """complex (n_segments,): sum_ab conj(psi_a) N_ab psi_b of every vector."""
+        idx = _arr(list(psi.keys()), np.uint64)
+        vals = np.array([complex(v) for v in psi.values()])
+        pr = _arr(vals.real, np.float64)
+        pi = _arr(vals.imag, np.float64)
+        orr = np.zeros(self.nseg, dtype=np.float64)
+        oi = np.zeros(self.nseg, dtype=np.float64)
+        self._check(self.L.qmc_overlap_all(self.h, _ptr(idx), _ptr(pr), _ptr(pi), len(idx), orr.ctypes.data,
+                                           oi.ctypes.data), "qmc_overlap_all")
+        return orr + 1j * oi
+
+    def antihermiticity(self) -> list:
+        """Exact ||N - N^dagger||_F^2 of every vector (Python ints)."""
+        out = np.zeros(2 * self.nseg, dtype=np.uint64)
+        self._check(self.L.qmc_antihermiticity(self.h, out.ctypes.data), "qmc_antihermiticity")
+        return [int(out[2 * s]) + (int(out[2 * s + 1]) << 64) for s in range(self.nseg)]
 
     def export(self, seg: int, which: int = 0):
         cnt = C.c_int64()
