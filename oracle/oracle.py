@@ -79,6 +79,8 @@ def lib():
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_zsum.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_next_value.restype = C.c_int
+        L.orc_next_value.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_void_p]
         L.orc_antiherm.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.orc_walker_T.restype = C.c_int64
         L.orc_walker_T.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_int64]
@@ -253,6 +255,15 @@ class OracleSim:
             lib().orc_export(self.handle, seg, which, keys.ctypes.data, re.ctypes.data,
                              im.ctypes.data)
         return keys, re, im
+
+    def next_value(self, seg: int, dt: float, key: int):
+        """(re, im) that the next step of size dt leaves at `key` of vector
+        seg, computed from the parents that can reach it (no step taken)."""
+        out = np.zeros(2, dtype=np.int64)
+        rc = lib().orc_next_value(self.handle, seg, dt, key, out.ctypes.data)
+        if rc != OK:
+            raise RuntimeError(f"orc_next_value failed: {rc}")
+        return int(out[0]), int(out[1])
 
     def zsum(self, seg: int) -> np.ndarray:
         """Per qubit q: sum over diagonal records of Re N_xx (-1)^(x_q)."""

@@ -1019,6 +1019,73 @@ int orc_step(void* sp, double dt, int nsteps)
     return rc;
 }
 
+static void value_at_key(const pop* p, uint64_t key, int64_t* re, int64_t* im);
+
+/*
+ * The value N(t + dt) of vector seg at one key after the next step of size dt
+ * (what orc_step(dt, 1) would leave there), without stepping: every parent
+ * that can spawn onto the key -- the occupied states key ^ mask of N(t) and,
+ * in an AB2 step, of N(t - dt), for every destination mask with a nonzero
+ * static weight -- replays its walkers exactly as in the step (spawn_parent,
+ * same ranks and draws), and the spawns landing on the key are annihilated
+ * with N(t)'s value there under the initiator rule.  For checking sampled
+ * outputs of a large step one key at a time.  out = (re, im).
+ */
+int orc_next_value(void* sp, int seg, double dt, uint64_t key, int64_t out[2])
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg || !(dt > 0.0)) return ORC_ERR_INVALID_ARG;
+    const double t = s->t;
+    const int ab2 = (s->integrator == 1 && s->prev_valid && s->dt_last == dt);
+    const double dt_cur = ab2 ? dt * 1.5 : dt;
+    uint32_t kd[2];
+    derive_key(s->seed, s->step, (uint32_t)seg, TAG_STEP, kd);
+    column col = {0, 0, 0}, st_cur = {0, 0, 0}, st_prev = {0, 0, 0}, m_cur = {0, 0, 0}, m_prev = {0, 0, 0};
+    spawn_list spl = {0, 0, 0};
+    int rc = build_static(s->prob, t, dt_cur, &m_cur);
+    if (rc == ORC_OK && ab2) rc = build_static(s->prob, s->t_prev, dt * 0.5, &m_prev);
+    if (rc == ORC_OK && s->proposal) {
+        rc = build_static(s->prob, t, dt_cur, &st_cur);
+        if (rc == ORC_OK && ab2) rc = build_static(s->prob, s->t_prev, dt * 0.5, &st_prev);
+    }
+    int64_t re = 0, im = 0, cre = 0, cim = 0;
+    const pop* cur = &s->cur[seg];
+    value_at_key(cur, key, &cre, &cim);
+    const int occupied = cre != 0 || cim != 0;
+    for (int phase = 0; phase < (ab2 ? 2 : 1) && rc == ORC_OK; ++phase) {
+        const pop* src = phase ? &s->prev[seg] : cur;
+        const column* masks = phase ? &m_prev : &m_cur;
+        for (int e = 0; e < masks->len && rc == ORC_OK; ++e) {
+            const uint64_t pk = key ^ masks->e[e].mask;
+            /* the parent's rank: its index in the sorted population */
+            int64_t lo = 0, hi = src->len;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) / 2;
+                if (src->r[mid].key < pk) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= src->len || src->r[lo].key != pk) continue;
+            spl.len = 0;
+            rc = phase ? spawn_parent(s, &src->r[lo], lo, 1, s->t_prev, dt * 0.5, -1, kd, &col, &st_prev, &spl)
+                       : spawn_parent(s, &src->r[lo], lo, 0, t, dt_cur, 1, kd, &col, &st_cur, &spl);
+            for (int64_t j = 0; j < spl.len && rc == ORC_OK; ++j) {
+                if (spl.s[j].key != key) continue;
+                if (!occupied && spl.s[j].noninit) continue;
+                re += spl.s[j].re;
+                im += spl.s[j].im;
+            }
+        }
+    }
+    free(col.e);
+    free(st_cur.e);
+    free(st_prev.e);
+    free(m_cur.e);
+    free(m_prev.e);
+    free(spl.s);
+    out[0] = cre + re;
+    out[1] = cim + im;
+    return rc;
+}
+
 /* Spawn choice of the following steps: 0 exact |L|-weighted (the paper's),
  * 1 static-weight proposal (see the header). */
 int orc_set_proposal(void* sp, int kind)

@@ -236,6 +236,76 @@ def pure_noise(n: int, gamma1: float, gamma_phi: float, rate_kind: int = RATE_CO
 # Initial density matrices (sparse) and observable targets
 # ---------------------------------------------------------------------------
 
+def _pauli_mat(n: int, xm: int, zm: int) -> np.ndarray:
+    """Matrix of a Pauli string (qubit q is bit q of the basis index)."""
+    one = {(0, 0): np.eye(2), (1, 0): np.array([[0, 1], [1, 0]]), (0, 1): np.diag([1.0, -1.0]),
+           (1, 1): np.array([[0, -1j], [1j, 0]])}
+    m = np.ones((1, 1), dtype=np.complex128)
+    for q in reversed(range(n)):
+        m = np.kron(m, one[((xm >> q) & 1, (zm >> q) & 1)])
+    return m
+
+
+def pauli_terms(M: np.ndarray, n: int, tol: float = 1e-14) -> list:
+    """Pauli-string expansion of an operator on n qubits: [(coef, xm, zm)]
+    with M = sum coef P (coef = Tr(P M) / 2^n), tiny terms dropped."""
+    D = 1 << n
+    out = []
+    for xm in range(D):
+        for zm in range(D):
+            c = complex(np.trace(_pauli_mat(n, xm, zm) @ M)) / D
+            if abs(c) > tol:
+                out.append((c, xm, zm))
+    return out
+
+
+def redfield_two_qubits(omega1: float = 0.25, omega2: float = 0.5, gamma1: float = 1.0, gamma2: float = 4.0,
+                        alpha: float = 3.0, kappa: float = 1.0):
+    """Two qubits collectively coupled to one bosonic bath, as the Redfield
+    master equation Eq. (4) [Non-Markovian dynamics; End Matter on the Redfield
+    equation]: drho/dt = -i sum_ij A_ij [s_j^+ s_i^-, rho] + sum_k lambda_k
+    D[L_k] rho, with the frequency matrix A of the End Matter (Lamb shifts
+    alpha and kappa given as inputs).
+
+    The dissipator comes from the bath's rate matrix over the jump operators
+    s_1^-, s_2^- (reading, the paper prints only its eigenvalues):
+        G = [[g1 / 2, (g1 + g2) / 4 + i kappa], [(g1 + g2) / 4 - i kappa, g2 / 2]],
+    whose eigenvalues are the paper's lambda_k = (g1 + g2) / 4 -/+
+    sqrt((g1^2 + g2^2 + 8 kappa^2) / 8) (one of them negative: non-Markovian);
+    with G = U diag(lambda) U^dag, L_k = sum_j conj(U_jk) s_j^-, so that
+    sum_ij G_ij (s_j rho s_i^dag - {s_i^dag s_j, rho} / 2) = sum_k lambda_k
+    (L_k rho L_k^dag - {L_k^dag L_k, rho} / 2).  As the paper does, the problem
+    is written in the basis |0~> = |00>, |1~> = L_1^dag |00>, |2~> =
+    L_2^dag |00>, |3~> ~ L_2^dag L_1^dag |00> (normalised), basis state b
+    stored at index b.  Returns (Problem, info) with info = dict(lam, A, G, V)
+    (V: the new basis vectors as columns, in the computational basis)."""
+    # qubit q is bit q: s_q^- = |0><1| on qubit q
+    sm1 = np.array([[0, 1], [0, 0]], dtype=np.complex128)
+    eye = np.eye(2, dtype=np.complex128)
+    s = [np.kron(eye, sm1), np.kron(sm1, eye)]
+    A = np.array([[omega1 + alpha, alpha + kappa / 2 - 1j * (gamma1 - gamma2) / 8],
+                  [alpha + kappa / 2 - 1j * (gamma2 - gamma1) / 8, omega2 + alpha + kappa]])
+    H = sum(A[i, j] * s[j].conj().T @ s[i] for i in range(2) for j in range(2))
+    G = np.array([[gamma1 / 2, (gamma1 + gamma2) / 4 + 1j * kappa],
+                  [(gamma1 + gamma2) / 4 - 1j * kappa, gamma2 / 2]])
+    lam, U = np.linalg.eigh(G)
+    L = [sum(np.conj(U[j, k]) * s[j] for j in range(2)) for k in range(2)]
+    v0 = np.zeros(4, dtype=np.complex128)
+    v0[0] = 1.0
+    v3 = L[1].conj().T @ L[0].conj().T @ v0
+    V = np.stack([v0, L[0].conj().T @ v0, L[1].conj().T @ v0, v3 / np.linalg.norm(v3)], axis=1)
+    Ht = V.conj().T @ H @ V
+    Lt = [V.conj().T @ Lk @ V for Lk in L]
+    p = Problem(2, name="redfield2")
+    one = p.rate(RATE_CONST, 1.0)
+    for c, xm, zm in pauli_terms(Ht, 2):
+        p.ham.append((float(c.real), xm, zm, one, ALWAYS))
+    for k in range(2):
+        rk = p.rate(RATE_CONST, float(lam[k]))
+        p.lind.append((pauli_terms(Lt[k], 2), rk, ALWAYS))
+    return p, {"lam": lam, "A": A, "G": G, "V": V}
+
+
 def rho_basis(x: int = 0) -> list:
     """``|x><x|`` as sparse entries ``(x, y, re, im)``."""
     return [(x, x, 1.0, 0.0)]
@@ -266,17 +336,22 @@ def spread_population(n: int, count: int, seed: int) -> tuple[np.ndarray, np.nda
     walker of sign +1, -1, +i or -i.  Returns sorted keys and int32 (re, im)."""
     rng = np.random.default_rng(seed)
     bits = 2 * n
-    keys = np.empty(0, dtype=np.uint64)
-    while keys.size < count:
-        need = int((count - keys.size) * 1.05) + 16
+
+    def draw(m):
         if bits >= 64:
-            cand = rng.integers(0, 2**63, size=need, dtype=np.uint64) * np.uint64(2) + \
-                rng.integers(0, 2, size=need, dtype=np.uint64)
-        else:
-            cand = rng.integers(0, 1 << bits, size=need, dtype=np.uint64)
-        keys = np.unique(np.concatenate([keys, cand]))
-    keys = rng.permutation(keys)[:count]
-    keys.sort()
+            return rng.integers(0, 2**63, size=m, dtype=np.uint64) * np.uint64(2) + \
+                rng.integers(0, 2, size=m, dtype=np.uint64)
+        return rng.integers(0, 1 << bits, size=m, dtype=np.uint64)
+
+    def distinct(a):
+        a = np.sort(a)
+        return a[np.concatenate([[True], a[1:] != a[:-1]])] if a.size else a
+
+    keys = distinct(draw(count))
+    while keys.size < count:   # duplicates drawn: add more, then keep a uniform subset
+        keys = distinct(np.concatenate([keys, draw(count - keys.size + 16)]))
+    if keys.size > count:
+        keys = np.sort(rng.choice(keys, size=count, replace=False))
     sel = rng.integers(0, 4, size=count)
     re = np.where(sel == 0, 1, np.where(sel == 1, -1, 0)).astype(np.int32)
     im = np.where(sel == 2, 1, np.where(sel == 3, -1, 0)).astype(np.int32)

@@ -307,3 +307,31 @@ def test_rejects_too_large_step():
     sim = O.OracleSim(prob, 1, seed=0, n_diag=100)
     sim.init(P.rho_pure({0: 1.0, 1: 1.0}))
     assert sim.step(0.02, 1) == O.ERR_DT_TOO_LARGE
+
+
+@pytest.mark.parametrize("integrator,proposal", [(O.AB2, 0), (O.EULER, 0), (O.AB2, 1)])
+def test_next_value_equals_the_step(integrator, proposal):
+    """The one-key form of the step (the value N(t + dt) takes at a key,
+    replayed from the parents that can reach it) equals the step itself at
+    every output key and at unoccupied neighbours, with the initiator rule
+    on; it is what the full-size GPU check samples."""
+    prob = P.ghz_circuit(5)
+    sim = O.OracleSim(prob, 3, seed=19, integrator=integrator, init_min=40, n_diag=3000)
+    sim.set_proposal(proposal)
+    sim.init(P.rho_pure({0: 1.0, 7: 0.5, 18: -0.4j}))
+    assert sim.step(0.01, 230) == O.OK
+    # every state a parent of N(t) or N(t - dt) can reach: parent key ^ destination mask
+    _, t, _, _, _ = sim.clock()
+    masks, _ = O.OracleProblem(prob).static(t, 0.01)
+    before = {}
+    for s in range(3):
+        parents = set(int(v) for v in sim.population(s)[0]) | set(int(v) for v in sim.population(s, 1)[0])
+        probe = parents | {p ^ int(m) for p in parents for m in masks}
+        before[s] = {key: sim.next_value(s, 0.01, key) for key in sorted(probe)}
+    assert sim.step(0.01, 1) == O.OK
+    for s in range(3):
+        k, r, i = sim.population(s)
+        after = {int(a): (int(b), int(c)) for a, b, c in zip(k, r, i)}
+        assert set(after) <= set(before[s])
+        for key, v in before[s].items():
+            assert v == after.get(key, (0, 0)), (s, key)
