@@ -439,6 +439,17 @@ int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, con
  * state is found by binary search in its vector.  Synchronises. */
 int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out);
 
+/* ||S - S^dagger||_F^2 of the sum S of the listed vectors' N(t) (host
+ * vectors[count], distinct, of equal qubit count), exactly, as host out[0]
+ * (low 64 bits) and out[1] (high): the anti-Hermiticity of a replica
+ * aggregate [End Matter on Hermiticity preservation; replica aggregation,
+ * Markovian circuit dynamics: rho_QMC = S / N^diag_eff, so epsilon =
+ * sqrt(value) / N^diag_eff].  Each record looks up its key and its transposed
+ * key in every listed vector (binary search).  Errors: INVALID_ARG (count
+ * outside 1..65535, an index out of range or repeated, mixed qubit counts),
+ * STATE (no population).  Synchronises. */
+int qmc_antihermiticity_sum(qmc_ctx* ctx, const int32_t* vectors, int32_t count, uint64_t* out);
+
 /* ---- checkpoint / resume ------------------------------------------------- */
 
 /* Write (clock, seed, configuration hash, N(t), N(t - dt)) to path; restore

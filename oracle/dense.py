@@ -131,3 +131,44 @@ def fidelity(rho: np.ndarray, psi: dict) -> float:
         vecpsi[x] = a
     vecpsi /= np.linalg.norm(vecpsi)
     return float(abs(vecpsi.conj() @ rho @ vecpsi))
+
+
+def evolve_operators(prob, rho0: np.ndarray, dt: float, nsteps: int, integrator: str = "ab2",
+                     t0: float = 0.0, record=None) -> np.ndarray:
+    """The same Euler / AB2 recursion as ``evolve`` with L(t) applied to rho
+    as operators, L(rho) = -i[H, rho] + sum_k gamma_k (L_k rho L_k^dag -
+    {L_k^dag L_k, rho} / 2) (Eq. (1)), without forming the D^2 x D^2 matrix:
+    for n up to about 10 qubits.  H and the L_k are rebuilt only when the set
+    of active pulse windows or the rates change."""
+    cache = {}
+
+    def ops(t):
+        key = (tuple(window_on(prob, w, t) for w in range(len(prob.windows))),
+               tuple(rate_value(prob, r, t) for r in range(len(prob.rates))))
+        if key not in cache:
+            H = hamiltonian(prob, t)
+            Ls = [(g, Lk, Lk.conj().T, Lk.conj().T @ Lk) for g, Lk in lindblad_ops(prob, t)]
+            cache.clear()
+            cache[key] = (H, Ls)
+        return cache[key]
+
+    def apply(t, rho):
+        H, Ls = ops(t)
+        out = -1j * (H @ rho - rho @ H)
+        for g, Lk, Ld, LdL in Ls:
+            out += g * (Lk @ rho @ Ld - 0.5 * (LdL @ rho + rho @ LdL))
+        return out
+
+    rho = rho0.astype(np.complex128)
+    prev_term = None
+    for k in range(nsteps):
+        t = t0 + k * dt
+        cur_term = apply(t, rho)
+        if integrator == "ab2" and prev_term is not None:
+            rho = rho + dt * (1.5 * cur_term - 0.5 * prev_term)
+        else:
+            rho = rho + dt * cur_term
+        prev_term = cur_term
+        if record is not None:
+            record(k, rho)
+    return rho

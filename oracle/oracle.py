@@ -82,6 +82,7 @@ def lib():
         L.orc_next_value.restype = C.c_int
         L.orc_next_value.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_void_p]
         L.orc_antiherm.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_antiherm_sum.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.orc_walker_T.restype = C.c_int64
         L.orc_walker_T.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_int64]
         L.orc_mlp_exp.restype = C.c_float
@@ -275,6 +276,13 @@ class OracleSim:
         """||N - N^dagger||_F^2 of one vector, an exact integer."""
         out = np.zeros(2, dtype=np.uint64)
         lib().orc_antiherm(self.handle, seg, out.ctypes.data)
+        return int(out[0]) + (int(out[1]) << 64)
+
+    def antiherm_sum(self, segs) -> int:
+        """||S - S^dagger||_F^2 of the sum S of the listed vectors, exact."""
+        sg = np.ascontiguousarray(segs, dtype=np.int32)
+        out = np.zeros(2, dtype=np.uint64)
+        lib().orc_antiherm_sum(self.handle, sg.ctypes.data, len(sg), out.ctypes.data)
         return int(out[0]) + (int(out[1]) << 64)
 
     def stats(self, seg: int):

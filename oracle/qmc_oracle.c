@@ -1189,6 +1189,54 @@ void orc_antiherm(void* sp, int seg, uint64_t out[2])
     out[1] = (uint64_t)(acc >> 64);
 }
 
+/* ||S - S^dagger||_F^2 of the sum S = sum over the listed vectors of their
+ * N(t), exactly (out[0] low, out[1] high 64 bits): the aggregated
+ * anti-Hermiticity of replicas [End Matter on Hermiticity preservation, with
+ * the replica aggregate of the Markovian circuit dynamics section].  Every
+ * entry (x, y) where some listed vector holds (x, y) or (y, x) contributes
+ * |S_xy - conj(S_yx)|^2. */
+void orc_antiherm_sum(void* sp, const int32_t* segs, int count, uint64_t out[2])
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    const uint64_t ymask = (((uint64_t)1) << n) - 1;
+    unsigned __int128 acc = 0;
+    for (int a = 0; a < count; ++a) {
+        const pop* p = &s->cur[segs[a]];
+        for (int64_t i = 0; i < p->len; ++i) {
+            const uint64_t key = p->r[i].key;
+            const uint64_t tkey = ((key & ymask) << n) | (key >> n);
+            /* visit each entry once: (x, y) from the first listed vector that holds it, and
+             * (y, x) from there too when no listed vector holds (y, x) */
+            int first = 1;
+            for (int b = 0; b < a && first; ++b) {
+                int64_t re, im;
+                value_at_key(&s->cur[segs[b]], key, &re, &im);
+                if (re != 0 || im != 0) first = 0;
+            }
+            if (!first) continue;
+            int64_t sre = 0, sim = 0, tre = 0, tim = 0;
+            int t_held = 0;
+            for (int b = 0; b < count; ++b) {
+                int64_t re, im;
+                value_at_key(&s->cur[segs[b]], key, &re, &im);
+                sre += re;
+                sim += im;
+                value_at_key(&s->cur[segs[b]], tkey, &re, &im);
+                tre += re;
+                tim += im;
+                if (re != 0 || im != 0) t_held = 1;
+            }
+            const int64_t dre = sre - tre, dim = sim + tim;
+            acc += (unsigned __int128)((__int128)dre * dre) + (unsigned __int128)((__int128)dim * dim);
+            if (tkey != key && !t_held)   /* the transposed entry -conj(S_xy) */
+                acc += (unsigned __int128)((__int128)sre * sre) + (unsigned __int128)((__int128)sim * sim);
+        }
+    }
+    out[0] = (uint64_t)acc;
+    out[1] = (uint64_t)(acc >> 64);
+}
+
 /* walker_T, exported for the tests of the draws' distribution. */
 int64_t orc_walker_T(const uint32_t kd[2], int64_t r, int phase, int comp, int64_t j, int64_t are)
 {

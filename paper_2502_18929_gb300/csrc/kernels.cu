@@ -369,8 +369,8 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st, uint32_t
     return false;
 }
 
-constexpr int kCandStage = 128;   // candidates staged per warp
-constexpr int kCandFlush = 96;    // a warp flushes once more than this are staged (at most 32 join at a time)
+constexpr int kCandStage = 256;   // candidates staged per warp
+constexpr int kCandFlush = 128;   // a warp flushes once more than this are staged
 constexpr uint32_t kJ20 = (1u << 20) - 1u;
 
 // Append a warp's staged candidates to the candidate list of the step.
@@ -387,22 +387,6 @@ __device__ __forceinline__ void cand_flush(const SpawnCand* stage, int n, const 
         if (pos < P.cand_cap) d4[pos] = s4[j];
     }
     __syncwarp();
-}
-
-// Stage the lanes' candidates (at most one per lane); flushes once the stage
-// holds more than kCandFlush.  Whole warp.
-__device__ __forceinline__ void cand_push(SpawnCand* stage, int* staged, bool c, const uint4& v, const StepParams& P,
-                                          int lane)
-{
-    const uint32_t b = __ballot_sync(kFull, c);
-    if (b == 0u) return;
-    if (c) ((uint4*)stage)[*staged + __popc(b & ((1u << lane) - 1u))] = v;
-    *staged += __popc(b);
-    __syncwarp();
-    if (*staged > kCandFlush) {
-        cand_flush(stage, *staged, P, lane);
-        *staged = 0;
-    }
 }
 
 // Candidate word w: the walker's index j in its component (20 bits), the
@@ -515,7 +499,63 @@ constexpr int kDrawGroups = 32;                 // rank groups per warp iteratio
 constexpr int kDrawRecs = 4 * kDrawGroups;      // records staged per iteration (2 KB)
 constexpr int kDrawStages = 3;                  // staged iterations per warp
 constexpr int kDrawWarps = kThreads / 32;
-constexpr int kDrawSmem = kDrawWarps * (kDrawStages * kDrawRecs * 16 + kCandStage * 16);
+constexpr int kXRing = 160;                     // queued single-call parents per warp
+constexpr int kDrawSmem = kDrawWarps * (kDrawStages * kDrawRecs * 16 + kCandStage * 16 + kXRing * 16);
+
+// Append up to four candidates per lane (those with bit i of `pass` set,
+// values v[i]) to the warp's stage in lane order; flushes the stage to the
+// step's candidate list as it fills.  Whole warp.
+__device__ __forceinline__ void cand_push4(SpawnCand* stage, int* staged, uint32_t pass, const uint4 (&v)[4],
+                                           const StepParams& P, int lane)
+{
+    const int n = __popc(pass);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int tot = __shfl_sync(kFull, incl, 31);
+    if (tot == 0) return;
+    if (*staged + tot > kCandStage) {
+        cand_flush(stage, *staged, P, lane);
+        *staged = 0;
+    }
+    uint4* s4 = (uint4*)stage + *staged + incl - n;
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if ((pass >> i) & 1u) s4[k++] = v[i];
+    *staged += tot;
+    __syncwarp();
+    if (*staged > kCandFlush) {
+        cand_flush(stage, *staged, P, lane);
+        *staged = 0;
+    }
+}
+
+// Candidates among the four walkers 1 + 4b .. 4 + 4b of one parent (its call
+// b); bit q of the result marks walker 1 + 4b + q.
+__device__ __forceinline__ uint32_t extra_cands(const SegDraw& d, uint32_t parent, uint32_t seg, uint32_t rank,
+                                                uint32_t b, int32_t re, int32_t im, int phase, bool act, uint4 (&v)[4])
+{
+    const uint32_t are = re < 0 ? 0u - (uint32_t)re : (uint32_t)re;
+    const uint32_t aim = im < 0 ? 0u - (uint32_t)im : (uint32_t)im;
+    const uint64_t m = (uint64_t)are + aim;
+    const uint4 xw = extra_words(rank, b, phase, d.kd);
+    const int noninit = (d.init_min > 0 && (int64_t)m < d.init_min) ? 1 : 0;
+    uint32_t pass = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint64_t w = 1ull + 4ull * (uint64_t)b + (uint64_t)q;
+        const uint32_t W = word_of(xw, q);
+        const int comp = w < are ? 0 : 1;
+        const uint32_t j = (uint32_t)(comp ? w - are : w);
+        v[q] = make_uint4(parent, seg, W, cand_meta(j, comp, phase, noninit, comp ? im : re));
+        if (act && w < m && passes(d, W)) pass |= 1u << q;
+    }
+    return pass;
+}
 
 // Walker draws of one population slot (phase 0: N(t), phase 1: N(t - dt)).
 // The slot's records form rank groups of four consecutive records of one
@@ -523,13 +563,15 @@ constexpr int kDrawSmem = kDrawWarps * (kDrawStages * kDrawRecs * 16 + kCandStag
 // [gb, ge) and takes them 32 at a time, lane l group G0 + l, their records
 // staged by one bulk copy per iteration (kDrawStages - 1 iterations ahead).
 // A lane draws its group call (one Philox call: the first walkers of its four
-// parents) and compares each word with the vector's prefilter bound;
-// further walkers of parents with two or more take their parents' calls
-// (four walkers each), spread evenly over the lanes.  Parents with more than
-// heavy_walkers walkers become heavy work items (all their walkers).
-__device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, Rec* buf, uint64_t* bar,
-                                          uint32_t* use_no, const Rec* src, const int64_t* off, const int64_t* gof,
-                                          int64_t gb, int64_t ge, int phase, const StepInfo& inf, int lane)
+// parents) and compares each word with the vector's prefilter bound.
+// Parents with 2 to 5 walkers (one further call) are queued per warp and
+// their calls drawn 32 at a time; parents with 6 to heavy_walkers walkers
+// take their calls at once, spread evenly over the lanes; heavier parents
+// become heavy work items (all their walkers).
+__device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint4* xring,
+                                          int* xhead, int* xcnt, Rec* buf, uint64_t* bar, uint32_t* use_no,
+                                          const Rec* src, const int64_t* off, const int64_t* gof, int64_t gb,
+                                          int64_t ge, int phase, const StepInfo& inf, int lane)
 {
     const int nseg = P.nseg;
     const int64_t Gt = gof[nseg];
@@ -569,6 +611,27 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         mbar_arrive_expect(b, bytes);
         bulk_load(buf + (u % kDrawStages) * kDrawRecs, src + r0, bytes, b);
     };
+    // the queued parents' calls, 32 at a time (n <= 32 entries from the head)
+    auto drain = [&](int n) {
+        const bool act = lane < n;
+        const uint4 e = act ? xring[(*xhead + lane) % kXRing] : make_uint4(0u, 0u, 0u, 0u);
+        const int sg = (int)e.y;
+        SegDraw d;
+        d.pre = 0u;
+        d.all = false;
+        d.init_min = 0;
+        d.kd = make_uint2(0u, 0u);
+        uint32_t rank = 0u;
+        if (act) {
+            d = seg_draw(P, inf, sg, phase);
+            rank = e.x - (uint32_t)__ldg(&off[sg]);
+        }
+        uint4 v[4];
+        const uint32_t pass = extra_cands(d, e.x, e.y, rank, 0u, (int32_t)e.z, (int32_t)e.w, phase, act, v);
+        cand_push4(stage, staged, pass, v, P, lane);
+        *xhead = (*xhead + n) % kXRing;
+        *xcnt -= n;
+    };
     if (lane == 0)
         for (int64_t k = 0; k < kDrawStages - 1 && k < nit; ++k) issue(k);
     // the lane's vector (cached while its groups stay inside it)
@@ -604,89 +667,126 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         const int64_t r0 = __shfl_sync(kFull, first, 0);
         const int pos = (int)(first - r0);
         const uint4 gw = group_words(g, phase, sd.kd);
-        int ne[4];         // extra calls of the lane's four parents
-        int total_ne = 0;
+        Rec r[4];
+        uint32_t pass = 0u, queue = 0u, multi = 0u;
+        bool any_heavy = false;
+        uint4 v[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            Rec r{0ull, 0, 0};
-            if (i < cnt) r = tb[pos + i];
-            const uint32_t are = r.re < 0 ? 0u - (uint32_t)r.re : (uint32_t)r.re;
-            const uint32_t aim = r.im < 0 ? 0u - (uint32_t)r.im : (uint32_t)r.im;
+            r[i] = Rec{0ull, 0, 0};
+            if (i < cnt) r[i] = tb[pos + i];
+            const uint32_t are = r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re;
+            const uint32_t aim = r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im;
             const uint64_t m = (uint64_t)are + aim;
-            const bool heavy = m > (uint64_t)P.heavy_walkers;
-            if (__any_sync(kFull, heavy) && heavy) emit_heavy(P, first + i, phase, seg, are, aim);
+            const bool heavy = i < cnt && m > (uint64_t)P.heavy_walkers;
+            any_heavy |= heavy;
             const int comp = are ? 0 : 1;
             const int noninit = (sd.init_min > 0 && (int64_t)m < sd.init_min) ? 1 : 0;
             const uint32_t W = word_of(gw, i);
-            const bool c = i < cnt && !heavy && passes(sd, W);
-            cand_push(stage, staged, c,
-                      make_uint4((uint32_t)(first + i), (uint32_t)seg, W,
-                                 cand_meta(0u, comp, phase, noninit, comp ? r.im : r.re)),
-                      P, lane);
-            ne[i] = (i < cnt && !heavy && m >= 2) ? (int)((m + 2) / 4) : 0;
-            total_ne += ne[i];
-        }
-        // further walkers: the warp's extra calls, 32 at a time
-        int incl = total_ne;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int tot = __shfl_sync(kFull, incl, 31);
-        for (int rr = 0; rr < tot; rr += 32) {
-            const int gi = rr + lane;
-            int lo = 0, hi = 31;   // owner: the first lane whose inclusive count exceeds gi
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (__shfl_sync(kFull, incl, mid) > gi) hi = mid; else lo = mid + 1;
+            v[i] = make_uint4((uint32_t)(first + i), (uint32_t)seg, W,
+                              cand_meta(0u, comp, phase, noninit, comp ? r[i].im : r[i].re));
+            if (i < cnt && !heavy) {
+                if (passes(sd, W)) pass |= 1u << i;
+                if (m >= 2 && m <= 5) queue |= 1u << i;
+                else if (m > 5) multi |= 1u << i;
             }
-            const int owner = lo;
-            const bool act = gi < tot;
-            int local = gi - (__shfl_sync(kFull, incl, owner) - __shfl_sync(kFull, total_ne, owner));
-            int o_ne[4];
+        }
+        if (__any_sync(kFull, any_heavy)) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o_ne[q] = __shfl_sync(kFull, ne[q], owner);
-            const int o_pos = __shfl_sync(kFull, pos, owner);
-            const uint32_t o_first = __shfl_sync(kFull, (uint32_t)first, owner);
-            const int o_seg = __shfl_sync(kFull, seg, owner);
-            const uint32_t o_g = __shfl_sync(kFull, g, owner);
-            const uint2 o_kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
-            SegDraw od;
-            od.kd = o_kd;
-            od.pre = __shfl_sync(kFull, sd.pre, owner);
-            od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
-            od.init_min = __shfl_sync(kFull, sd.init_min, owner);
-            int i = 0;   // the owner's parent holding call `local`, then the call's index in it
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t are = r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re;
+                const uint32_t aim = r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im;
+                if (i < cnt && (uint64_t)are + aim > (uint64_t)P.heavy_walkers)
+                    emit_heavy(P, first + i, phase, seg, are, aim);
+            }
+        }
+        cand_push4(stage, staged, pass, v, P, lane);
+        // queue the parents with one further call (their calls are drawn 32 at a time)
+        {
+            const int nq = __popc(queue);
+            int incl = nq;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (i == q && local >= o_ne[q]) {
-                    local -= o_ne[q];
-                    ++i;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(kFull, incl, 31);
+            if (tot) {
+                int at = *xhead + *xcnt + incl - nq;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if ((queue >> i) & 1u)
+                        xring[(at++) % kXRing] = make_uint4((uint32_t)(first + i), (uint32_t)seg,
+                                                            (uint32_t)r[i].re, (uint32_t)r[i].im);
+                *xcnt += tot;
+                __syncwarp();
+                while (*xcnt >= 32) {
+                    drain(32);
+                    __syncwarp();
                 }
             }
-            Rec r{0ull, 0, 0};
-            if (act) r = tb[o_pos + i];
-            const uint32_t are = r.re < 0 ? 0u - (uint32_t)r.re : (uint32_t)r.re;
-            const uint32_t aim = r.im < 0 ? 0u - (uint32_t)r.im : (uint32_t)r.im;
-            const uint64_t m = (uint64_t)are + aim;
-            const uint32_t rank = 4u * o_g + (uint32_t)i;
-            const uint4 xw = extra_words(rank, (uint32_t)local, phase, o_kd);
-            const int noninit = (od.init_min > 0 && (int64_t)m < od.init_min) ? 1 : 0;
+        }
+        // parents with 6 .. heavy_walkers walkers: their calls at once, spread evenly over the lanes
+        if (__any_sync(kFull, multi != 0u)) {
+            int ne[4];
+            int total_ne = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint64_t w = 1ull + 4ull * (uint64_t)local + (uint64_t)q;
-                const uint32_t W = word_of(xw, q);
-                const bool c = act && w < m && passes(od, W);
-                const int comp = w < are ? 0 : 1;
-                const uint32_t j = (uint32_t)(comp ? w - are : w);
-                cand_push(stage, staged, c,
-                          make_uint4(o_first + (uint32_t)i, (uint32_t)o_seg, W,
-                                     cand_meta(j, comp, phase, noninit, comp ? r.im : r.re)),
-                          P, lane);
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t m = (uint64_t)(r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re) +
+                                   (uint64_t)(r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im);
+                ne[i] = ((multi >> i) & 1u) ? (int)((m + 2) / 4) : 0;
+                total_ne += ne[i];
+            }
+            int incl = total_ne;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(kFull, incl, 31);
+            for (int rr = 0; rr < tot; rr += 32) {
+                const int gi = rr + lane;
+                int lo = 0, hi = 31;   // owner: the first lane whose inclusive count exceeds gi
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__shfl_sync(kFull, incl, mid) > gi) hi = mid; else lo = mid + 1;
+                }
+                const int owner = lo;
+                const bool act = gi < tot;
+                int local = gi - (__shfl_sync(kFull, incl, owner) - __shfl_sync(kFull, total_ne, owner));
+                int o_ne[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o_ne[q] = __shfl_sync(kFull, ne[q], owner);
+                const int o_pos = __shfl_sync(kFull, pos, owner);
+                const uint32_t o_first = __shfl_sync(kFull, (uint32_t)first, owner);
+                const int o_seg = __shfl_sync(kFull, seg, owner);
+                const uint32_t o_g = __shfl_sync(kFull, g, owner);
+                SegDraw od;
+                od.kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
+                od.pre = __shfl_sync(kFull, sd.pre, owner);
+                od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
+                od.init_min = __shfl_sync(kFull, sd.init_min, owner);
+                int i = 0;   // the owner's parent holding call `local`, then the call's index in it
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (i == q && local >= o_ne[q]) {
+                        local -= o_ne[q];
+                        ++i;
+                    }
+                }
+                Rec pr{0ull, 0, 0};
+                if (act) pr = tb[o_pos + i];
+                uint4 xv[4];
+                const uint32_t xp = extra_cands(od, o_first + (uint32_t)i, (uint32_t)o_seg, 4u * o_g + (uint32_t)i,
+                                                (uint32_t)local, pr.re, pr.im, phase, act, xv);
+                cand_push4(stage, staged, xp, xv, P, lane);
             }
         }
         __syncwarp();   // every read of the stage done before it is refilled
+    }
+    if (*xcnt > 0) {
+        drain(*xcnt);
+        __syncwarp();
     }
     if (gave_up) {
         // a copy may still be landing in the last stages: wait for them once more (bounded)
@@ -698,7 +798,7 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
     *use_no = u0 + (uint32_t)nit;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
+__global__ void __launch_bounds__(kThreads, 2) k_spawn_draw(StepParams P)
 {
     extern __shared__ __align__(128) uint4 dsm[];
     __shared__ __align__(8) uint64_t sbar[kDrawWarps][kDrawStages];
@@ -707,6 +807,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Rec* buf = (Rec*)(dsm + warp * (kDrawStages * kDrawRecs));
     SpawnCand* stage = (SpawnCand*)(dsm + kDrawWarps * kDrawStages * kDrawRecs + warp * kCandStage);
+    uint4* xring = dsm + kDrawWarps * (kDrawStages * kDrawRecs + kCandStage) + warp * kXRing;
+    int xhead = 0, xcnt = 0;
     if (P.sort_mode)   // bucket counters of this step's spawn sort
         for (int b = blockIdx.x * kThreads + threadIdx.x; b < (1 << P.bucket_bits); b += gridDim.x * kThreads)
             P.bucket[b] = 0u;
@@ -728,8 +830,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_spawn_draw(StepParams P)
         // each warp owns one contiguous range of the slot's rank groups, a multiple of 32
         const int64_t chunk = ((Gt + nwarps - 1) / nwarps + kDrawGroups - 1) / kDrawGroups * kDrawGroups;
         const int64_t gb = min(Gt, gw * chunk), ge = min(Gt, gb + chunk);
-        draw_slot(P, stage, &staged, buf, sbar[warp], &use_no, P.pop[slot], P.segoff[slot], gof, gb, ge, phase, inf,
-                  lane);
+        draw_slot(P, stage, &staged, xring, &xhead, &xcnt, buf, sbar[warp], &use_no, P.pop[slot], P.segoff[slot], gof,
+                  gb, ge, phase, inf, lane);
     }
     if (staged) cand_flush(stage, staged, P, lane);
 }
@@ -2635,6 +2737,72 @@ __global__ void k_antiherm(StepParams P, unsigned long long* __restrict__ out)
     if (cs >= 0 && acc) add_u128(out + 2 * cs, acc);
 }
 
+// Value of N(t) at key in vector seg (0 when unoccupied), by binary search.
+__device__ __forceinline__ void value_in(const Rec* pop, const int64_t* off, int seg, uint64_t key, long long* re,
+                                         long long* im)
+{
+    int64_t lo = off[seg], hi = off[seg + 1];
+    const int64_t end = hi;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pop[mid].key < key) lo = mid + 1; else hi = mid;
+    }
+    *re = 0;
+    *im = 0;
+    if (lo < end && pop[lo].key == key) {
+        *re = pop[lo].re;
+        *im = pop[lo].im;
+    }
+}
+
+// ||S - S^dagger||_F^2 of the sum S of the listed vectors of N(t), exactly
+// (the replica aggregate's anti-Hermiticity).  Grid (x: records, y: listed
+// vector a).  A record (x, y) of vector segs[a] accounts for the entry (x, y)
+// when no earlier listed vector holds (x, y), and then also for the entry
+// (y, x) when no listed vector holds (y, x).
+__global__ void k_antiherm_sum(StepParams P, const int32_t* __restrict__ segs, int count,
+                               unsigned long long* __restrict__ out)
+{
+    const DevState* st = P.st;
+    const int slot = st->cur;
+    const Rec* pop = P.pop[slot];
+    const int64_t* off = P.segoff[slot];
+    const int a = blockIdx.y;
+    const int sa = segs[a];
+    const int n = P.seginfo[sa].n;
+    const uint64_t ymask = n == 32 ? 0xFFFFFFFFull : ((1ull << n) - 1ull);
+    unsigned __int128 acc = 0;
+    for (int64_t i = off[sa] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < off[sa + 1];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = pop[i].key;
+        const uint64_t tkey = ((key & ymask) << n) | (key >> n);
+        bool first = true;
+        for (int b = 0; b < a && first; ++b) {
+            long long re, im;
+            value_in(pop, off, segs[b], key, &re, &im);
+            if (re != 0 || im != 0) first = false;
+        }
+        if (!first) continue;
+        long long sre = 0, sim = 0, tre = 0, tim = 0;
+        bool t_held = false;
+        for (int b = 0; b < count; ++b) {
+            long long re, im;
+            value_in(pop, off, segs[b], key, &re, &im);
+            sre += re;
+            sim += im;
+            value_in(pop, off, segs[b], tkey, &re, &im);
+            tre += re;
+            tim += im;
+            t_held |= re != 0 || im != 0;
+        }
+        const long long dre = sre - tre, dim = sim + tim;
+        acc += (unsigned __int128)((__int128)dre * dre) + (unsigned __int128)((__int128)dim * dim);
+        if (tkey != key && !t_held)
+            acc += (unsigned __int128)((__int128)sre * sre) + (unsigned __int128)((__int128)sim * sim);
+    }
+    if (acc) add_u128(out, acc);
+}
+
 // Pack host-uploaded (key, re, im) arrays into records of one slot and check
 // them: keys ascending within each vector, below 2^(2n), values nonzero and not
 // -2^31.  A violation sets *bad (the caller rejects the call).
@@ -2800,6 +2968,15 @@ void launch_antiherm(const StepParams& P, unsigned long long* out, int grid, cud
     if (g_grid_spawn == 0) configure_kernels();
     cudaMemsetAsync(out, 0, (size_t)P.nseg * 16, stream);
     k_antiherm<<<grid > 0 ? grid : g_grid_misc, kThreads, 0, stream>>>(P, out);
+}
+
+void launch_antiherm_sum(const StepParams& P, const int32_t* segs, int count, unsigned long long* out, int grid,
+                         cudaStream_t stream)
+{
+    if (g_grid_spawn == 0) configure_kernels();
+    cudaMemsetAsync(out, 0, 16, stream);
+    const int gx = grid > 0 ? grid : (g_grid_misc + count - 1) / count;
+    k_antiherm_sum<<<dim3(gx > 0 ? gx : 1, count), kThreads, 0, stream>>>(P, segs, count, out);
 }
 
 void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,

@@ -172,6 +172,9 @@ void launch_overlap_all(const StepParams& P, const uint64_t* idx, const double* 
                         cudaStream_t stream);
 // ||N - N^dagger||_F^2 of every vector of N(t), exactly (out: nseg x (low, high) 64-bit words, zeroed here).
 void launch_antiherm(const StepParams& P, unsigned long long* out, int grid, cudaStream_t stream);
+// ||S - S^dagger||_F^2 of the sum S of the listed vectors (device segs[count]); out: (low, high), zeroed here.
+void launch_antiherm_sum(const StepParams& P, const int32_t* segs, int count, unsigned long long* out, int grid,
+                         cudaStream_t stream);
 void launch_init(const StepParams& P, const uint64_t* x, const uint64_t* y, const double* re, const double* im,
                  int64_t nnz, int64_t* tmp_vals, cudaStream_t stream);
 

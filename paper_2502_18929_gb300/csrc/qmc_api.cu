@@ -1371,6 +1371,31 @@ int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out)
     return leave(ctx);
 }
 
+int qmc_antihermiticity_sum(qmc_ctx* ctx, const int32_t* vectors, int32_t count, uint64_t* out)
+{
+    if (!ctx || !vectors || !out || count < 1 || count > 65535) return QMC_ERR_INVALID_ARG;
+    if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "no population");
+    const int nseg = ctx->cfg.n_segments;
+    std::vector<int32_t> v(vectors, vectors + count), sorted = v;
+    std::sort(sorted.begin(), sorted.end());
+    for (int i = 0; i < count; ++i) {
+        if (sorted[i] < 0 || sorted[i] >= nseg) return fail(ctx, QMC_ERR_INVALID_ARG, "vector index out of range");
+        if (i && sorted[i] == sorted[i - 1]) return fail(ctx, QMC_ERR_INVALID_ARG, "a vector is listed twice");
+        if (instance_of(ctx, sorted[i]).n != instance_of(ctx, sorted[0]).n)
+            return fail(ctx, QMC_ERR_INVALID_ARG, "listed vectors differ in qubit count");
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if ((rc = aux_reserve(ctx, 16 + 4 * (int64_t)count)) != QMC_OK) return rc;
+    int32_t* d_segs = (int32_t*)(ctx->d_aux + 16);
+    CK(cudaMemcpyAsync(d_segs, v.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, ctx->work));
+    launch_antiherm_sum(params(ctx), d_segs, count, (unsigned long long*)ctx->d_aux, ctx->grid, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, ctx->d_aux, 16, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return leave(ctx);
+}
+
 int qmc_checkpoint(qmc_ctx* ctx, const char* path)
 {
     if (!ctx || !path) return QMC_ERR_INVALID_ARG;

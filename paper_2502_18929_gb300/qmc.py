@@ -39,7 +39,7 @@ EXPORTED = [
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
     "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
-    "qmc_overlap_all", "qmc_antihermiticity",
+    "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum",
 ]
 
 
@@ -136,6 +136,7 @@ def lib():
         L.qmc_z_history.argtypes = [vp, vp, C.c_int64, vp]
         L.qmc_overlap_all.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp]
         L.qmc_antihermiticity.argtypes = [vp, vp]
+        L.qmc_antihermiticity_sum.argtypes = [vp, vp, C.c_int32, vp]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_kernel_name.argtypes = [C.c_int32]
@@ -467,6 +468,15 @@ class QMC:
         out = np.zeros(2 * self.nseg, dtype=np.uint64)
         self._check(self.L.qmc_antihermiticity(self.h, out.ctypes.data), "qmc_antihermiticity")
         return [int(out[2 * s]) + (int(out[2 * s + 1]) << 64) for s in range(self.nseg)]
+
+    def antihermiticity_sum(self, vectors) -> int:
+        """Exact ||S - S^dagger||_F^2 of the sum S of the listed vectors (a
+        replica aggregate), a Python int."""
+        v = _arr(list(vectors), np.int32)
+        out = np.zeros(2, dtype=np.uint64)
+        self._check(self.L.qmc_antihermiticity_sum(self.h, _ptr(v), len(v), out.ctypes.data),
+                    "qmc_antihermiticity_sum")
+        return int(out[0]) + (int(out[1]) << 64)
 
     def export(self, seg: int, which: int = 0):
         cnt = C.c_int64()

@@ -132,3 +132,28 @@ def test_antihermiticity_after_steps():
     gpu.step(0.01, 250)
     assert orc.step(0.01, 250) == O.OK
     assert gpu.antihermiticity() == [orc.antiherm(s) for s in range(5)]
+
+
+def test_antihermiticity_of_replica_sums():
+    prob = P.ghz_circuit(32)
+    gpu, orc = _pair(prob, 5, 2, 10**6)
+    pops = [_spread_pairs(32, 2000 + 300 * s, 40 + s) for s in range(5)]
+    # shared keys across vectors (some cancel in the sum), transposed keys in other vectors
+    k0, r0, i0 = pops[0]
+    for s in (1, 3):
+        k, r, i = pops[s]
+        keys = np.concatenate([k, k0[:400], ((k0[400:700] & np.uint64(0xFFFFFFFF)) << np.uint64(32)) |
+                               (k0[400:700] >> np.uint64(32))])
+        re = np.concatenate([r, -r0[:400], r0[400:700]])
+        im = np.concatenate([i, i0[:400], i0[400:700]])
+        keys, first = np.unique(keys, return_index=True)
+        re, im = re[first], im[first]
+        keep = (re != 0) | (im != 0)
+        pops[s] = (keys[keep], re[keep], im[keep])
+    gpu.set_populations(pops)
+    for s, (k, r, i) in enumerate(pops):
+        orc.set_population(s, k, r, i)
+    for segs in ([0, 1, 2, 3, 4], [3, 0], [4], [1, 3]):
+        assert gpu.antihermiticity_sum(segs) == orc.antiherm_sum(segs), segs
+    with pytest.raises(qmc.QmcError):
+        gpu.antihermiticity_sum([1, 1])

@@ -77,3 +77,17 @@ def test_antiherm_exact_beyond_64_bits():
         expect += d[0] * d[0] + d[1] * d[1]
     assert expect > 2**64
     assert sim.antiherm(0) == expect
+
+
+def test_antiherm_sum_against_dense_norm_of_the_sum():
+    """Replica aggregate: the anti-Hermiticity of the summed populations of
+    several vectors (listed in any order, a vector listed once) against the
+    dense norm of the summed density matrices."""
+    from test_oracle_column import random_problem
+    prob = random_problem(3, 6)
+    sim = _evolved(prob, 5, 13, 80, dt=0.005)
+    for segs in ([0, 1, 2, 3, 4], [3, 1], [2]):
+        S = sum(sim.density(s) for s in segs)
+        dense = np.sum(np.abs(S - S.conj().T) ** 2)
+        assert sim.antiherm_sum(segs) == int(round(dense)), segs
+    assert sim.antiherm_sum([4]) == sim.antiherm(4)

@@ -335,3 +335,14 @@ def test_next_value_equals_the_step(integrator, proposal):
         assert set(after) <= set(before[s])
         for key, v in before[s].items():
             assert v == after.get(key, (0, 0)), (s, key)
+
+
+def test_operator_form_dense_recursion_matches_kronecker():
+    """The matrix-free dense recursion (operators applied to rho) equals the
+    Kronecker-matrix recursion of Eq. (2), through pulse-window changes."""
+    for prob, rho0, steps in ((P.ghz_circuit(3), P.rho_basis(0), 300),
+                              (P.dd_ring(4, seed=2, t_end=2.0, x_basis=False), P.rho_pure(P.w_state(4)), 250)):
+        r0 = Dn.rho_from_entries(prob.n, rho0)
+        a = Dn.evolve(prob, r0, 0.008, steps, "ab2")
+        b = Dn.evolve_operators(prob, r0, 0.008, steps, "ab2")
+        assert np.abs(a - b).max() < 1e-12
