@@ -436,10 +436,9 @@ __device__ __forceinline__ const uint8_t* prog_ptr(const StepParams& P, const St
 // needs W <= P >> 20; all: every walker is a candidate, the bound having
 // reached 2^52), and its instance's initiator threshold.
 struct SegDraw {
-    uint32_t pre;
-    int64_t init_min;
+    uint32_t pre;        // W <= pre: candidate (2^32 - 1 once the bound reaches 2^52: every walker)
+    uint32_t init_thr;   // parents with fewer walkers are non-initiators (0: none)
     uint2 kd;
-    bool all;
 };
 
 __device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo& inf, int seg, int phase)
@@ -447,15 +446,15 @@ __device__ __forceinline__ SegDraw seg_draw(const StepParams& P, const StepInfo&
     const SegInfo si = P.seginfo[seg];
     const ProgHeader* h = (const ProgHeader*)prog_ptr(P, inf, si.inst, phase);
     const int64_t pb = P.proposal ? h->p_att : h->p_bound;   // attempt bound of the choice rule
+    const int64_t im = P.inst[si.inst].init_min;
     SegDraw d;
-    d.all = pb >= (1ll << 52);
-    d.pre = d.all ? 0xFFFFFFFFu : (uint32_t)(pb >> 20);
-    d.init_min = P.inst[si.inst].init_min;
+    d.pre = pb >= (1ll << 52) ? 0xFFFFFFFFu : (uint32_t)(pb >> 20);
+    d.init_thr = im <= 0 ? 0u : (im >= 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)im);
     d.kd = P.kd[seg];
     return d;
 }
 
-__device__ __forceinline__ bool passes(const SegDraw& d, uint32_t W) { return d.all || W <= d.pre; }
+__device__ __forceinline__ bool passes(const SegDraw& d, uint32_t W) { return W <= d.pre; }
 
 // The walker draw's counters [reading R3]: for the parent at rank r of its
 // vector (index in the key-sorted population) in pass phase, walker w (real
@@ -499,34 +498,42 @@ constexpr int kDrawGroups = 32;                 // rank groups per warp iteratio
 constexpr int kDrawRecs = 4 * kDrawGroups;      // records staged per iteration (2 KB)
 constexpr int kDrawStages = 3;                  // staged iterations per warp
 constexpr int kDrawWarps = kThreads / 32;
-constexpr int kXRing = 160;                     // queued single-call parents per warp
+constexpr int kXRing = 256;                     // queued single-call parents per warp (a power of two)
 constexpr int kDrawSmem = kDrawWarps * (kDrawStages * kDrawRecs * 16 + kCandStage * 16 + kXRing * 16);
 
-// Append up to four candidates per lane (those with bit i of `pass` set,
-// values v[i]) to the warp's stage in lane order; flushes the stage to the
-// step's candidate list as it fills.  Whole warp.
-__device__ __forceinline__ void cand_push4(SpawnCand* stage, int* staged, uint32_t pass, const uint4 (&v)[4],
-                                           const StepParams& P, int lane)
+__device__ __forceinline__ uint32_t uabs32(int32_t v) { return v < 0 ? 0u - (uint32_t)v : (uint32_t)v; }
+
+// Warp-wide placement of up to four items per lane (bit i of `bits`): one
+// ballot per slot i; slot i's items follow slot i - 1's, lanes in order.
+// Returns the total; off[i] is the lane's position for its slot-i item.
+__device__ __forceinline__ int warp_place4(uint32_t bits, int (&off)[4], int lane)
 {
-    const int n = __popc(pass);
-    int incl = n;
+    const uint32_t lt = (1u << lane) - 1u;
+    int base = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t b = __ballot_sync(kFull, (bits >> i) & 1u);
+        off[i] = base + __popc(b & lt);
+        base += __popc(b);
     }
-    const int tot = __shfl_sync(kFull, incl, 31);
-    if (tot == 0) return;
+    return base;
+}
+
+// Make room for `tot` more candidates in the warp's stage (flushing it first
+// if needed); returns the stage position where they start.
+__device__ __forceinline__ int cand_reserve(SpawnCand* stage, int* staged, int tot, const StepParams& P, int lane)
+{
     if (*staged + tot > kCandStage) {
         cand_flush(stage, *staged, P, lane);
         *staged = 0;
     }
-    uint4* s4 = (uint4*)stage + *staged + incl - n;
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if ((pass >> i) & 1u) s4[k++] = v[i];
+    const int at = *staged;
     *staged += tot;
+    return at;
+}
+
+__device__ __forceinline__ void cand_done(SpawnCand* stage, int* staged, const StepParams& P, int lane)
+{
     __syncwarp();
     if (*staged > kCandFlush) {
         cand_flush(stage, *staged, P, lane);
@@ -534,27 +541,35 @@ __device__ __forceinline__ void cand_push4(SpawnCand* stage, int* staged, uint32
     }
 }
 
-// Candidates among the four walkers 1 + 4b .. 4 + 4b of one parent (its call
-// b); bit q of the result marks walker 1 + 4b + q.
-__device__ __forceinline__ uint32_t extra_cands(const SegDraw& d, uint32_t parent, uint32_t seg, uint32_t rank,
-                                                uint32_t b, int32_t re, int32_t im, int phase, bool act, uint4 (&v)[4])
+// Candidates among the walkers 1 + 4b .. 4 + 4b of one parent (its call b):
+// staged for the lanes that are active.  Whole warp.
+__device__ __forceinline__ void extra_draw(SpawnCand* stage, int* staged, const StepParams& P, const SegDraw& d,
+                                           uint32_t parent, uint32_t seg, uint32_t rank, uint32_t b, int32_t re,
+                                           int32_t im, int phase, bool act, int lane)
 {
-    const uint32_t are = re < 0 ? 0u - (uint32_t)re : (uint32_t)re;
-    const uint32_t aim = im < 0 ? 0u - (uint32_t)im : (uint32_t)im;
-    const uint64_t m = (uint64_t)are + aim;
+    const uint32_t are = uabs32(re), m = are + uabs32(im);
     const uint4 xw = extra_words(rank, b, phase, d.kd);
-    const int noninit = (d.init_min > 0 && (int64_t)m < d.init_min) ? 1 : 0;
-    uint32_t pass = 0u;
+    uint32_t bits = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint64_t w = 1ull + 4ull * (uint64_t)b + (uint64_t)q;
-        const uint32_t W = word_of(xw, q);
-        const int comp = w < are ? 0 : 1;
-        const uint32_t j = (uint32_t)(comp ? w - are : w);
-        v[q] = make_uint4(parent, seg, W, cand_meta(j, comp, phase, noninit, comp ? im : re));
-        if (act && w < m && passes(d, W)) pass |= 1u << q;
+    for (int q = 0; q < 4; ++q)
+        if (act && 1u + 4u * b + (uint32_t)q < m && passes(d, word_of(xw, q))) bits |= 1u << q;
+    int off[4];
+    const int tot = warp_place4(bits, off, lane);
+    if (tot == 0) return;
+    const int at = cand_reserve(stage, staged, tot, P, lane);
+    if (bits) {
+        const uint32_t noninit = m < d.init_thr ? 1u : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!((bits >> q) & 1u)) continue;
+            const uint32_t w = 1u + 4u * b + (uint32_t)q;
+            const int comp = w < are ? 0 : 1;
+            ((uint4*)stage)[at + off[q]] =
+                make_uint4(parent, seg, word_of(xw, q),
+                           cand_meta(comp ? w - are : w, comp, phase, (int)noninit, comp ? im : re));
+        }
     }
-    return pass;
+    cand_done(stage, staged, P, lane);
 }
 
 // Walker draws of one population slot (phase 0: N(t), phase 1: N(t - dt)).
@@ -567,7 +582,8 @@ __device__ __forceinline__ uint32_t extra_cands(const SegDraw& d, uint32_t paren
 // Parents with 2 to 5 walkers (one further call) are queued per warp and
 // their calls drawn 32 at a time; parents with 6 to heavy_walkers walkers
 // take their calls at once, spread evenly over the lanes; heavier parents
-// become heavy work items (all their walkers).
+// become heavy work items (all their walkers).  Record indices and walker
+// counts fit 32 bits (at most 2^31 - 1 records per slot, |re|, |im| < 2^31).
 __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint4* xring,
                                           int* xhead, int* xcnt, Rec* buf, uint64_t* bar, uint32_t* use_no,
                                           const Rec* src, const int64_t* off, const int64_t* gof, int64_t gb,
@@ -577,6 +593,7 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
     const int64_t Gt = gof[nseg];
     const int64_t nit = (ge - gb + kDrawGroups - 1) / kDrawGroups;
     const uint32_t u0 = *use_no;
+    const uint32_t heavy_w = (uint32_t)P.heavy_walkers;
     bool gave_up = false;
     // lane 0: a cursor over the slot's vectors for the copies issued ahead
     // (the iterations' record ranges follow one another)
@@ -614,34 +631,30 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
     // the queued parents' calls, 32 at a time (n <= 32 entries from the head)
     auto drain = [&](int n) {
         const bool act = lane < n;
-        const uint4 e = act ? xring[(*xhead + lane) % kXRing] : make_uint4(0u, 0u, 0u, 0u);
-        const int sg = (int)e.y;
+        const uint4 e = act ? xring[(*xhead + lane) & (kXRing - 1)] : make_uint4(0u, 0u, 0u, 0u);
         SegDraw d;
         d.pre = 0u;
-        d.all = false;
-        d.init_min = 0;
+        d.init_thr = 0u;
         d.kd = make_uint2(0u, 0u);
         uint32_t rank = 0u;
         if (act) {
-            d = seg_draw(P, inf, sg, phase);
-            rank = e.x - (uint32_t)__ldg(&off[sg]);
+            d = seg_draw(P, inf, (int)e.y, phase);
+            rank = e.x - (uint32_t)__ldg(&off[e.y]);
         }
-        uint4 v[4];
-        const uint32_t pass = extra_cands(d, e.x, e.y, rank, 0u, (int32_t)e.z, (int32_t)e.w, phase, act, v);
-        cand_push4(stage, staged, pass, v, P, lane);
-        *xhead = (*xhead + n) % kXRing;
+        extra_draw(stage, staged, P, d, e.x, e.y, rank, 0u, (int32_t)e.z, (int32_t)e.w, phase, act, lane);
+        *xhead = (*xhead + n) & (kXRing - 1);
         *xcnt -= n;
     };
     if (lane == 0)
         for (int64_t k = 0; k < kDrawStages - 1 && k < nit; ++k) issue(k);
     // the lane's vector (cached while its groups stay inside it)
     int seg = 0;
-    int64_t seg_gend = -1, seg_off = 0, seg_gof = 0, seg_K = 0;
+    int64_t seg_gend = -1;
+    uint32_t seg_off = 0u, seg_gof = 0u, seg_K = 0u;
     SegDraw sd;
     sd.pre = 0u;
-    sd.init_min = 0;
+    sd.init_thr = 0u;
     sd.kd = make_uint2(0u, 0u);
-    sd.all = false;
     for (int64_t k = 0; k < nit; ++k) {
         const uint32_t u = u0 + (uint32_t)k;
         const int64_t G0 = gb + k * kDrawGroups;
@@ -655,69 +668,78 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         if (valid && G >= seg_gend) {
             seg = group_seg(gof, nseg, G);
             seg_gend = __ldg(&gof[seg + 1]);
-            seg_off = __ldg(&off[seg]);
-            seg_gof = __ldg(&gof[seg]);
-            seg_K = __ldg(&off[seg + 1]) - seg_off;
+            seg_off = (uint32_t)__ldg(&off[seg]);
+            seg_gof = (uint32_t)__ldg(&gof[seg]);
+            seg_K = (uint32_t)__ldg(&off[seg + 1]) - seg_off;
             sd = seg_draw(P, inf, seg, phase);
         }
-        const uint32_t g = (uint32_t)(G - seg_gof);
-        const int64_t first = seg_off + 4 * (int64_t)g;
-        const int cnt = valid ? (int)min((int64_t)4, seg_K - 4 * (int64_t)g) : 0;
+        const uint32_t g = (uint32_t)G - seg_gof;
+        const uint32_t first = seg_off + 4u * g;
+        const uint32_t rem = seg_K - 4u * g;
+        const int cnt = valid ? (rem < 4u ? (int)rem : 4) : 0;
         // the stage starts at the first record of group G0, lane 0's
-        const int64_t r0 = __shfl_sync(kFull, first, 0);
+        const uint32_t r0 = __shfl_sync(kFull, first, 0);
         const int pos = (int)(first - r0);
         const uint4 gw = group_words(g, phase, sd.kd);
-        Rec r[4];
-        uint32_t pass = 0u, queue = 0u, multi = 0u;
-        bool any_heavy = false;
-        uint4 v[4];
+        int32_t re[4], im[4];
+        uint32_t pass = 0u, queue = 0u, multi = 0u, heavy = 0u;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            r[i] = Rec{0ull, 0, 0};
-            if (i < cnt) r[i] = tb[pos + i];
-            const uint32_t are = r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re;
-            const uint32_t aim = r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im;
-            const uint64_t m = (uint64_t)are + aim;
-            const bool heavy = i < cnt && m > (uint64_t)P.heavy_walkers;
-            any_heavy |= heavy;
-            const int comp = are ? 0 : 1;
-            const int noninit = (sd.init_min > 0 && (int64_t)m < sd.init_min) ? 1 : 0;
-            const uint32_t W = word_of(gw, i);
-            v[i] = make_uint4((uint32_t)(first + i), (uint32_t)seg, W,
-                              cand_meta(0u, comp, phase, noninit, comp ? r[i].im : r[i].re));
-            if (i < cnt && !heavy) {
-                if (passes(sd, W)) pass |= 1u << i;
-                if (m >= 2 && m <= 5) queue |= 1u << i;
-                else if (m > 5) multi |= 1u << i;
+            re[i] = 0;
+            im[i] = 0;
+            if (i < cnt) {
+                const uint4 w = ((const uint4*)tb)[pos + i];
+                re[i] = (int32_t)w.z;
+                im[i] = (int32_t)w.w;
+            }
+            const uint32_t m = uabs32(re[i]) + uabs32(im[i]);
+            if (i < cnt) {
+                if (m > heavy_w) heavy |= 1u << i;
+                else {
+                    if (passes(sd, word_of(gw, i))) pass |= 1u << i;
+                    if (m >= 2u) {
+                        if (m <= 5u) queue |= 1u << i;
+                        else multi |= 1u << i;
+                    }
+                }
             }
         }
-        if (__any_sync(kFull, any_heavy)) {
+        if (__any_sync(kFull, heavy != 0u)) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t are = r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re;
-                const uint32_t aim = r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im;
-                if (i < cnt && (uint64_t)are + aim > (uint64_t)P.heavy_walkers)
-                    emit_heavy(P, first + i, phase, seg, are, aim);
+            for (int i = 0; i < 4; ++i)
+                if ((heavy >> i) & 1u) emit_heavy(P, first + i, phase, seg, uabs32(re[i]), uabs32(im[i]));
+        }
+        // the first walkers that pass: staged
+        {
+            int offs[4];
+            const int tot = warp_place4(pass, offs, lane);
+            if (tot) {
+                const int at = cand_reserve(stage, staged, tot, P, lane);
+                if (pass) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (!((pass >> i) & 1u)) continue;
+                        const uint32_t m = uabs32(re[i]) + uabs32(im[i]);
+                        const int comp = re[i] ? 0 : 1;
+                        ((uint4*)stage)[at + offs[i]] =
+                            make_uint4(first + i, (uint32_t)seg, word_of(gw, i),
+                                       cand_meta(0u, comp, phase, m < sd.init_thr ? 1 : 0, comp ? im[i] : re[i]));
+                    }
+                }
+                cand_done(stage, staged, P, lane);
             }
         }
-        cand_push4(stage, staged, pass, v, P, lane);
         // queue the parents with one further call (their calls are drawn 32 at a time)
         {
-            const int nq = __popc(queue);
-            int incl = nq;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int tot = __shfl_sync(kFull, incl, 31);
+            int offs[4];
+            const int tot = warp_place4(queue, offs, lane);
             if (tot) {
-                int at = *xhead + *xcnt + incl - nq;
+                const int tail = *xhead + *xcnt;
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
                     if ((queue >> i) & 1u)
-                        xring[(at++) % kXRing] = make_uint4((uint32_t)(first + i), (uint32_t)seg,
-                                                            (uint32_t)r[i].re, (uint32_t)r[i].im);
+                        xring[(tail + offs[i]) & (kXRing - 1)] =
+                            make_uint4(first + i, (uint32_t)seg, (uint32_t)re[i], (uint32_t)im[i]);
                 *xcnt += tot;
                 __syncwarp();
                 while (*xcnt >= 32) {
@@ -732,9 +754,7 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
             int total_ne = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const uint64_t m = (uint64_t)(r[i].re < 0 ? 0u - (uint32_t)r[i].re : (uint32_t)r[i].re) +
-                                   (uint64_t)(r[i].im < 0 ? 0u - (uint32_t)r[i].im : (uint32_t)r[i].im);
-                ne[i] = ((multi >> i) & 1u) ? (int)((m + 2) / 4) : 0;
+                ne[i] = ((multi >> i) & 1u) ? (int)((uabs32(re[i]) + uabs32(im[i]) + 2u) / 4u) : 0;
                 total_ne += ne[i];
             }
             int incl = total_ne;
@@ -758,14 +778,13 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
 #pragma unroll
                 for (int q = 0; q < 4; ++q) o_ne[q] = __shfl_sync(kFull, ne[q], owner);
                 const int o_pos = __shfl_sync(kFull, pos, owner);
-                const uint32_t o_first = __shfl_sync(kFull, (uint32_t)first, owner);
+                const uint32_t o_first = __shfl_sync(kFull, first, owner);
                 const int o_seg = __shfl_sync(kFull, seg, owner);
                 const uint32_t o_g = __shfl_sync(kFull, g, owner);
                 SegDraw od;
                 od.kd = make_uint2(__shfl_sync(kFull, sd.kd.x, owner), __shfl_sync(kFull, sd.kd.y, owner));
                 od.pre = __shfl_sync(kFull, sd.pre, owner);
-                od.all = __shfl_sync(kFull, sd.all ? 1 : 0, owner) != 0;
-                od.init_min = __shfl_sync(kFull, sd.init_min, owner);
+                od.init_thr = __shfl_sync(kFull, sd.init_thr, owner);
                 int i = 0;   // the owner's parent holding call `local`, then the call's index in it
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
@@ -774,12 +793,14 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
                         ++i;
                     }
                 }
-                Rec pr{0ull, 0, 0};
-                if (act) pr = tb[o_pos + i];
-                uint4 xv[4];
-                const uint32_t xp = extra_cands(od, o_first + (uint32_t)i, (uint32_t)o_seg, 4u * o_g + (uint32_t)i,
-                                                (uint32_t)local, pr.re, pr.im, phase, act, xv);
-                cand_push4(stage, staged, xp, xv, P, lane);
+                int32_t pre_ = 0, pim = 0;
+                if (act) {
+                    const uint4 w = ((const uint4*)tb)[o_pos + i];
+                    pre_ = (int32_t)w.z;
+                    pim = (int32_t)w.w;
+                }
+                extra_draw(stage, staged, P, od, o_first + (uint32_t)i, (uint32_t)o_seg, 4u * o_g + (uint32_t)i,
+                           (uint32_t)local, pre_, pim, phase, act, lane);
             }
         }
         __syncwarp();   // every read of the stage done before it is refilled
