@@ -99,7 +99,7 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
 #define TAG_INIT 0x494E4954u /* per segment key for initial rounding */
 #define KIND_INIT 1u
 #define KIND_LEARNED 2u
-#define KIND_GROUP 3u   /* first walkers of four parents (one rank group) */
+#define KIND_GROUP 3u   /* walker 0 or 1 of four parents (one rank group) */
 #define KIND_EXTRA 4u   /* further walkers of one parent, four per call */
 #define KIND_LOW 5u     /* low 20 bits of one walker's draw */
 
@@ -771,25 +771,25 @@ static cint column_at(const column* c, uint64_t mask)
  * in pass phase (0: N(t), 1: N(t - dt)), with the step's key kd (reading R3;
  * the paper names no generator).  The parent's walkers are numbered
  * w = 0 .. m - 1, real walkers first.  T = W << 20 | L, where W is a 32-bit
- * word -- for w = 0 word r % 4 of the call keyed by the rank group r / 4 (one
- * call serves the first walkers of four parents), for w >= 1 word (w - 1) % 4
- * of the parent's call (w - 1) / 4 -- and L the top 20 bits of word 0 of the
- * walker's own call.  Every word comes from a distinct Philox counter, so the
- * T of all walkers are independent and uniform on [0, 2^52).
+ * word -- for w = 0 and w = 1 word r % 4 of the rank group's call of level w
+ * (one call serves walker w of four consecutive parents), for w >= 2 word
+ * (w - 2) % 4 of the parent's call (w - 2) / 4 -- and L the top 20 bits of
+ * word 0 of the walker's own call.  Every word comes from a distinct Philox
+ * counter, so the T of all walkers are independent and uniform on [0, 2^52).
  */
 static int64_t walker_T(const uint32_t kd[2], int64_t r, int phase, int comp, int64_t j, int64_t are)
 {
     const int64_t w = (comp ? are : 0) + j;
     uint32_t o[4];
     uint32_t W;
-    if (w == 0) {
-        const uint32_t ctr[4] = {(uint32_t)(r >> 2), 0u, (uint32_t)phase | (KIND_GROUP << 2), 0u};
+    if (w <= 1) {
+        const uint32_t ctr[4] = {(uint32_t)(r >> 2), (uint32_t)w, (uint32_t)phase | (KIND_GROUP << 2), 0u};
         orc_philox(ctr, kd, o);
         W = o[r & 3];
     } else {
-        const uint32_t ctr[4] = {(uint32_t)r, (uint32_t)((w - 1) >> 2), (uint32_t)phase | (KIND_EXTRA << 2), 0u};
+        const uint32_t ctr[4] = {(uint32_t)r, (uint32_t)((w - 2) >> 2), (uint32_t)phase | (KIND_EXTRA << 2), 0u};
         orc_philox(ctr, kd, o);
-        W = o[(w - 1) & 3];
+        W = o[(w - 2) & 3];
     }
     const uint32_t ctr2[4] = {(uint32_t)r, (uint32_t)j, (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_LOW << 2),
                               0u};
