@@ -157,14 +157,18 @@ def reduce_over_ranks(dist, values, device):
 
 def set_proposal(sim, prob, kind: str):
     """Choice rule of the spawn step: the paper's exact rule, the static-weight
-    proposal, or the learned proposal with an untrained network (32 hidden
-    units, static share 0.1)."""
+    proposal, the learned proposal with an untrained network (32 hidden units,
+    static share 0.1), or the same on the tensor cores (64 hidden units, bf16,
+    GELU)."""
     from paper_2502_18929_gb300 import qmc
     if kind == "static":
         sim.set_proposal(qmc.PROPOSAL_STATIC)
     elif kind == "learned":
         sim.set_mlp(P.random_network(prob, hidden=32, seed=0, eps=0.1))
         sim.set_proposal(qmc.PROPOSAL_LEARNED)
+    elif kind == "learned_tc":
+        sim.set_mlp(P.random_network(prob, hidden=64, seed=0, eps=0.1))
+        sim.set_proposal(qmc.PROPOSAL_LEARNED_TC)
 
 
 def piece_dt(pl, step: int) -> float:
@@ -723,7 +727,7 @@ def main():
     ap.add_argument("--workload", default="spread32")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--proposal", default="exact", choices=["exact", "static", "learned"],
+    ap.add_argument("--proposal", default="exact", choices=["exact", "static", "learned", "learned_tc"],
                     help="spawn choice rule (learned: an untrained network)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes after the warm-up (state kept) and use the fastest")

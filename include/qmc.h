@@ -181,6 +181,17 @@ const char* qmc_last_error(const qmc_ctx* ctx);
 #define QMC_PROPOSAL_EXACT 0
 #define QMC_PROPOSAL_STATIC 1
 #define QMC_PROPOSAL_LEARNED 2
+/* QMC_PROPOSAL_LEARNED_TC (no counterpart in the paper): the learned
+ * proposal with its network evaluated on the tensor cores -- bf16 weights
+ * and activations, fp32 accumulation (mma.sync m16n8k16), GELU (tanh form,
+ * the hardware tanh approximation) in place of ReLU, exp by CUDA's
+ * single-precision function -- 16 sources per
+ * warp.  The walker law is unbiased for any proposal, so this mode draws
+ * from the same expected spawns as the others; its integer weights Q follow
+ * the same construction as QMC_PROPOSAL_LEARNED's but are not reproducible
+ * bit for bit on a CPU.  Needs a network with 16, 32, 48 or 64 hidden units,
+ * at most 256 outputs and 80 inputs (INVALID_ARG otherwise). */
+#define QMC_PROPOSAL_LEARNED_TC 3
 int qmc_set_proposal(qmc_ctx* ctx, int32_t kind);
 
 /* Network of the learned proposal (no counterpart in the paper).  With
@@ -248,6 +259,18 @@ int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, f
  * (4 H + G + 1) above 2^28), STATE, OOM. */
 int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
                    int64_t ld, int64_t n_events, float* grad, double* loss);
+
+/* As qmc_learn_grad for the tensor-core proposal's network
+ * (QMC_PROPOSAL_LEARNED_TC): inputs -> GELU -> GELU -> logits with the
+ * weights and both hidden activations taken as bf16 and fp32 accumulation
+ * (mma.sync m16n8k16), the same masked weighted cross-entropy; the
+ * gradient flows through the bf16 roundings unchanged.  Weight gradients are
+ * bf16 products over chunks of 4096 events, summed chunk by chunk in a fixed
+ * order (deterministic).  Event arrays 16-byte aligned.  Errors: as
+ * qmc_learn_grad, and INVALID_ARG when the network does not fit the tensor
+ * cores (16, 32, 48 or 64 hidden units, at most 256 outputs, 80 inputs). */
+int qmc_learn_grad_tc(qmc_ctx* ctx, const float* params, const float* feat, const float* target,
+                      const float* weight, int64_t ld, int64_t n_events, float* grad, double* loss);
 
 /* One Adam step (Kingma & Ba, 2015) on params with first and second moments
  * m, v (device, n_params floats each; zero before step t = 1).  Asynchronous

@@ -126,3 +126,69 @@ def loss_grad(params: dict, feat, target, weight):
     g["w1"] = dh1 @ X.T
     g["b1"] = dh1.sum(axis=1)
     return loss, g
+
+
+# ---------------------------------------------------------------------------
+# The tensor-core proposal's network: bf16 weights and activations, GELU.
+# ---------------------------------------------------------------------------
+def bf16(x) -> np.ndarray:
+    """float32 values rounded to bfloat16 (nearest, ties to even), as float64."""
+    a = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + np.uint64(0x7FFF) + ((a >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gelu(x):
+    """GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))."""
+    return 0.5 * x * (1.0 + np.tanh(np.sqrt(2.0 / np.pi) * (x + 0.044715 * x ** 3)))
+
+
+def gelu_prime(x):
+    u = np.sqrt(2.0 / np.pi) * (x + 0.044715 * x ** 3)
+    th = np.tanh(u)
+    return 0.5 * (1.0 + th) + 0.5 * x * (1.0 - th * th) * np.sqrt(2.0 / np.pi) * (1.0 + 3 * 0.044715 * x * x)
+
+
+def loss_grad_tc(params: dict, feat, target, weight, round_bf16: bool = True):
+    """Loss and gradient of the tensor-core proposal's network in float64:
+    inputs -> GELU (tanh form) -> GELU -> logits, the weights, the input t and both hidden
+    activations rounded to bf16 where the tensor cores take them (the rounding
+    passes gradients through unchanged); the same masked weighted
+    cross-entropy as ``loss_grad``.  round_bf16=False gives the smooth
+    network (for finite differences)."""
+    q16 = bf16 if round_bf16 else (lambda v: np.asarray(v, dtype=np.float64))
+    X = np.asarray(feat, dtype=np.float64).copy()
+    X[-1] = q16(X[-1])                                # t enters as bf16
+    T = np.asarray(target, dtype=np.float64)
+    w = np.asarray(weight, dtype=np.float64)
+    W1, W2, W3 = (q16(params[k]) for k in ("w1", "w2", "w3"))
+    b1, b2, b3 = (np.asarray(params[k], dtype=np.float64) for k in ("b1", "b2", "b3"))
+    a1 = W1 @ X + b1[:, None]
+    h1 = q16(gelu(a1))
+    a2 = W2 @ h1 + b2[:, None]
+    h2 = q16(gelu(a2))
+    z = W3 @ h2 + b3[:, None]
+    present = T >= 0
+    p = np.where(present, T, 0.0)
+    zm = np.where(present, z, -np.inf)
+    m = zm.max(axis=0)
+    m = np.where(np.isfinite(m), m, 0.0)
+    ex = np.where(present, np.exp(zm - m), 0.0)
+    S = ex.sum(axis=0)
+    Ssafe = np.where(S > 0, S, 1.0)
+    q = ex / Ssafe
+    logq = np.where(present, z - m - np.log(Ssafe), 0.0)
+    ce = -(p * logq).sum(axis=0)
+    wsum = w.sum()
+    om = w / wsum if wsum > 0 else np.zeros_like(w)
+    loss = float((om * ce).sum())
+    sp = p.sum(axis=0)
+    dz = np.where(present, om * (sp * q - p), 0.0)
+    g = {"w3": dz @ h2.T, "b3": dz.sum(axis=1)}
+    da2 = (W3.T @ dz) * gelu_prime(a2)
+    g["w2"] = da2 @ h1.T
+    g["b2"] = da2.sum(axis=1)
+    da1 = (W2.T @ da2) * gelu_prime(a1)
+    g["w1"] = da1 @ X.T
+    g["b1"] = da1.sum(axis=1)
+    return loss, g

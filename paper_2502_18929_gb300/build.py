@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "qmc_api.cu", "noalloc.cu", "learn.cu"]
 CPP_SOURCES = ["term_compiler.cpp", "column_check.cpp"]
-HEADERS = ["kernels.h", "qmc_types.h", "term_compiler.h", "context.h", "column_eval.h"]
+HEADERS = ["kernels.h", "qmc_types.h", "term_compiler.h", "context.h", "column_eval.h", "tc_ops.h"]
 
 
 def _nvcc() -> str:

@@ -45,6 +45,7 @@ struct qmc_ctx {
     bool batch = false;
     int proposal = 0;   // spawn choice rule (qmc_set_proposal)
     float* d_mlp = nullptr;          // learned proposal network
+    uint8_t* d_mlp_tc = nullptr;     // the same network in the tensor-core layout (null if it does not fit)
     uint64_t* d_mlp_mask = nullptr;
     int32_t* d_mlp_idx = nullptr;
     int mlp_in = 0, mlp_hidden = 0, mlp_out = 0;
@@ -53,6 +54,8 @@ struct qmc_ctx {
     float* d_learn_scratch = nullptr;  // training: per-event activations and gradients
     int64_t learn_scratch_cap = 0;
     double* d_learn_small = nullptr;   // training: [0] event count (int64), [1] weight sum, [2] loss
+    uint8_t* d_learn_tc = nullptr;     // tensor-core training: bf16 weights and per-event rows, partial gradients
+    int64_t learn_tc_cap = 0;
     float mlp_eps = 0.f;
     bool has_pop = false;
     qmc::SegInfo* d_seginfo = nullptr;

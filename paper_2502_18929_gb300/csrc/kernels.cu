@@ -22,11 +22,13 @@
 // and the observables are bit-identical to any other exact evaluation.  The
 // learned proposal's network runs in single precision with each operation
 // rounded explicitly, reproducible by a CPU that takes the same steps.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "column_eval.h"
 #include "kernels.h"
+#include "tc_ops.h"
 
 namespace qmc {
 
@@ -458,12 +460,13 @@ __device__ __forceinline__ bool passes(const SegDraw& d, uint32_t W) { return W 
 
 // The walker draw's counters [reading R3]: for the parent at rank r of its
 // vector (index in the key-sorted population) in pass phase, walker w (real
-// walkers first) has T = W << 20 | L with W word r % 4 of the group call
-// (w = 0) or word (w - 1) % 4 of the parent's call (w - 1) / 4, and L the top
-// 20 bits of word 0 of the walker's own call (component comp, index j).
-__device__ __forceinline__ uint4 group_words(uint32_t g, int phase, uint2 kd)
+// walkers first) has T = W << 20 | L with W word r % 4 of the rank group's
+// call of level w (w = 0, 1) or word (w - 2) % 4 of the parent's call
+// (w - 2) / 4 (w >= 2), and L the top 20 bits of word 0 of the walker's own
+// call (component comp, index j).
+__device__ __forceinline__ uint4 group_words(uint32_t g, uint32_t level, int phase, uint2 kd)
 {
-    return philox10(make_uint4(g, 0u, (uint32_t)phase | (kKindGroup << 2), 0u), kd);
+    return philox10(make_uint4(g, level, (uint32_t)phase | (kKindGroup << 2), 0u), kd);
 }
 
 __device__ __forceinline__ uint4 extra_words(uint32_t rank, uint32_t b, int phase, uint2 kd)
@@ -541,7 +544,7 @@ __device__ __forceinline__ void cand_done(SpawnCand* stage, int* staged, const S
     }
 }
 
-// Candidates among the walkers 1 + 4b .. 4 + 4b of one parent (its call b):
+// Candidates among the walkers 2 + 4b .. 5 + 4b of one parent (its call b):
 // staged for the lanes that are active.  Whole warp.
 __device__ __forceinline__ void extra_draw(SpawnCand* stage, int* staged, const StepParams& P, const SegDraw& d,
                                            uint32_t parent, uint32_t seg, uint32_t rank, uint32_t b, int32_t re,
@@ -552,7 +555,7 @@ __device__ __forceinline__ void extra_draw(SpawnCand* stage, int* staged, const 
     uint32_t bits = 0u;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (act && 1u + 4u * b + (uint32_t)q < m && passes(d, word_of(xw, q))) bits |= 1u << q;
+        if (act && 2u + 4u * b + (uint32_t)q < m && passes(d, word_of(xw, q))) bits |= 1u << q;
     int off[4];
     const int tot = warp_place4(bits, off, lane);
     if (tot == 0) return;
@@ -562,7 +565,7 @@ __device__ __forceinline__ void extra_draw(SpawnCand* stage, int* staged, const 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (!((bits >> q) & 1u)) continue;
-            const uint32_t w = 1u + 4u * b + (uint32_t)q;
+            const uint32_t w = 2u + 4u * b + (uint32_t)q;
             const int comp = w < are ? 0 : 1;
             ((uint4*)stage)[at + off[q]] =
                 make_uint4(parent, seg, word_of(xw, q),
@@ -578,11 +581,12 @@ __device__ __forceinline__ void extra_draw(SpawnCand* stage, int* staged, const 
 // [gb, ge) and takes them 32 at a time, lane l group G0 + l, their records
 // staged by one bulk copy per iteration (kDrawStages - 1 iterations ahead).
 // A lane draws its group call (one Philox call: the first walkers of its four
-// parents) and compares each word with the vector's prefilter bound.
-// Parents with 2 to 5 walkers (one further call) are queued per warp and
-// their calls drawn 32 at a time; parents with 6 to heavy_walkers walkers
-// take their calls at once, spread evenly over the lanes; heavier parents
-// become heavy work items (all their walkers).  Record indices and walker
+// parents) and compares each word with the vector's prefilter bound; the
+// group's level-1 call gives the second walkers.  Parents with 3 to 6
+// walkers (one further call) are queued per warp and their calls drawn 32 at
+// a time; parents with 7 to heavy_walkers walkers take their calls at once,
+// spread evenly over the lanes; heavier parents become heavy work items (all
+// their walkers).  Record indices and walker
 // counts fit 32 bits (at most 2^31 - 1 records per slot, |re|, |im| < 2^31).
 __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage, int* staged, uint4* xring,
                                           int* xhead, int* xcnt, Rec* buf, uint64_t* bar, uint32_t* use_no,
@@ -680,9 +684,9 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
         // the stage starts at the first record of group G0, lane 0's
         const uint32_t r0 = __shfl_sync(kFull, first, 0);
         const int pos = (int)(first - r0);
-        const uint4 gw = group_words(g, phase, sd.kd);
+        const uint4 gw = group_words(g, 0u, phase, sd.kd);
         int32_t re[4], im[4];
-        uint32_t pass = 0u, queue = 0u, multi = 0u, heavy = 0u;
+        uint32_t pass = 0u, two = 0u, queue = 0u, multi = 0u, heavy = 0u;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             re[i] = 0;
@@ -697,8 +701,9 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
                 if (m > heavy_w) heavy |= 1u << i;
                 else {
                     if (passes(sd, word_of(gw, i))) pass |= 1u << i;
-                    if (m >= 2u) {
-                        if (m <= 5u) queue |= 1u << i;
+                    if (m >= 2u) two |= 1u << i;
+                    if (m >= 3u) {
+                        if (m <= 6u) queue |= 1u << i;
                         else multi |= 1u << i;
                     }
                 }
@@ -729,7 +734,33 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
                 cand_done(stage, staged, P, lane);
             }
         }
-        // queue the parents with one further call (their calls are drawn 32 at a time)
+        // the second walkers: the rank group's level-1 call
+        if (__any_sync(kFull, two != 0u)) {
+            const uint4 gw1 = group_words(g, 1u, phase, sd.kd);
+            uint32_t pass1 = 0u;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (((two >> i) & 1u) && passes(sd, word_of(gw1, i))) pass1 |= 1u << i;
+            int offs[4];
+            const int tot = warp_place4(pass1, offs, lane);
+            if (tot) {
+                const int at = cand_reserve(stage, staged, tot, P, lane);
+                if (pass1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (!((pass1 >> i) & 1u)) continue;
+                        const uint32_t are = uabs32(re[i]), m = are + uabs32(im[i]);
+                        const int comp = 1u < are ? 0 : 1;
+                        ((uint4*)stage)[at + offs[i]] =
+                            make_uint4(first + i, (uint32_t)seg, word_of(gw1, i),
+                                       cand_meta(comp ? 1u - are : 1u, comp, phase, m < sd.init_thr ? 1 : 0,
+                                                 comp ? im[i] : re[i]));
+                    }
+                }
+                cand_done(stage, staged, P, lane);
+            }
+        }
+        // queue the parents with 3 to 6 walkers: walkers 2 .. 5 in one call (drawn 32 calls at a time)
         {
             int offs[4];
             const int tot = warp_place4(queue, offs, lane);
@@ -748,13 +779,13 @@ __device__ __forceinline__ void draw_slot(const StepParams& P, SpawnCand* stage,
                 }
             }
         }
-        // parents with 6 .. heavy_walkers walkers: their calls at once, spread evenly over the lanes
+        // parents with 7 .. heavy_walkers walkers: their calls at once, spread evenly over the lanes
         if (__any_sync(kFull, multi != 0u)) {
             int ne[4];
             int total_ne = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                ne[i] = ((multi >> i) & 1u) ? (int)((uabs32(re[i]) + uabs32(im[i]) + 2u) / 4u) : 0;
+                ne[i] = ((multi >> i) & 1u) ? (int)((uabs32(re[i]) + uabs32(im[i]) + 1u) / 4u) : 0;
                 total_ne += ne[i];
             }
             int incl = total_ne;
@@ -1203,6 +1234,323 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
 }
 
 // ---------------------------------------------------------------------------
+// Learned proposal on the tensor cores (QMC_PROPOSAL_LEARNED_TC; the
+// library's extension, not in the paper).  The same proposal as above --
+// integer weights Q_k summing to 2^24 from the network's softmax (share
+// 1 - eps) and the static proposal (share eps), floor + Bernoulli walker
+// counts -- with the network evaluated as bf16 matrix products with fp32
+// accumulation (mma.sync m16n8k16) and GELU activations: one warp evaluates
+// 16 sources at once, hidden activations stay in registers between layers.
+// Unbiased for any Q (Q_k >= 1 wherever the column can be nonzero), so the
+// rounding of the products changes the variance only, never the mean; the
+// products of a source do not depend on the other rows of its tile, so a
+// parent gets the same Q on the light and the heavy path.
+// ---------------------------------------------------------------------------
+constexpr int kTcWarps = 4;                       // warps per CTA of the light kernel
+constexpr int kTcMaxH = 64, kTcMaxGp = 256, kTcMaxIp = 80;
+
+// Input c of a source: bit c of x, bit c - n of y, then t; 0 past the inputs.
+__device__ __forceinline__ float tc_feat(uint32_t x, uint32_t y, float t, int c, int n)
+{
+    return c < n ? (float)((x >> c) & 1u) : (c < 2 * n ? (float)((y >> (c - n)) & 1u) : (c == 2 * n ? t : 0.0f));
+}
+
+// Logits of 16 sources by one warp.  The lane's fragment rows are g = lane /
+// 4 (source a: xa, ya, ta) and g + 8 (source b); the weights are in shared
+// memory in the TcLayout; logits go to out[row * ldo + output] (fp32, all Gp
+// outputs).
+__device__ void tc_forward(const uint8_t* sw, const TcLayout& L, int n, uint32_t xa, uint32_t ya, float ta,
+                           uint32_t xb, uint32_t yb, float tb, float* out, int ldo, int lane)
+{
+    const int g = lane >> 2, tig = lane & 3;
+    const __nv_bfloat16* W1 = (const __nv_bfloat16*)(sw + L.o_w1);
+    const __nv_bfloat16* W2 = (const __nv_bfloat16*)(sw + L.o_w2);
+    const __nv_bfloat16* W3 = (const __nv_bfloat16*)(sw + L.o_w3);
+    const float* b1 = (const float*)(sw + L.o_b1);
+    const float* b2 = (const float*)(sw + L.o_b2);
+    const float* b3 = (const float*)(sw + L.o_b3);
+    const int nth = L.H / 8, kth = L.H / 16, kt1 = L.Ip / 16;
+    float acc[kTcMaxH / 8][4];
+    uint32_t a[kTcMaxH / 16][4];
+    // layer 1
+#pragma unroll
+    for (int nt = 0; nt < kTcMaxH / 8; ++nt) {
+        const int c = nt * 8 + 2 * tig;
+        acc[nt][0] = nt < nth ? b1[c] : 0.0f;
+        acc[nt][1] = nt < nth ? b1[c + 1] : 0.0f;
+        acc[nt][2] = acc[nt][0];
+        acc[nt][3] = acc[nt][1];
+    }
+#pragma unroll
+    for (int kt = 0; kt < kTcMaxIp / 16; ++kt) {
+        if (kt >= kt1) break;
+        const int c = kt * 16 + 2 * tig;
+        uint32_t f[4];
+        f[0] = bf16x2(tc_feat(xa, ya, ta, c, n), tc_feat(xa, ya, ta, c + 1, n));
+        f[1] = bf16x2(tc_feat(xb, yb, tb, c, n), tc_feat(xb, yb, tb, c + 1, n));
+        f[2] = bf16x2(tc_feat(xa, ya, ta, c + 8, n), tc_feat(xa, ya, ta, c + 9, n));
+        f[3] = bf16x2(tc_feat(xb, yb, tb, c + 8, n), tc_feat(xb, yb, tb, c + 9, n));
+#pragma unroll
+        for (int nt = 0; nt < kTcMaxH / 8; ++nt) {
+            if (nt >= nth) break;
+            const uint32_t* row = (const uint32_t*)(W1 + (nt * 8 + g) * L.ld1 + kt * 16 + 2 * tig);
+            mma_bf16(acc[nt], f, row[0], row[4]);
+        }
+    }
+    // GELU, repacked as the next layer's A fragments (two 8-column tiles per 16-column k tile)
+#pragma unroll
+    for (int kt = 0; kt < kTcMaxH / 16; ++kt) {
+        a[kt][0] = bf16x2(tc_gelu(acc[2 * kt][0]), tc_gelu(acc[2 * kt][1]));
+        a[kt][1] = bf16x2(tc_gelu(acc[2 * kt][2]), tc_gelu(acc[2 * kt][3]));
+        a[kt][2] = bf16x2(tc_gelu(acc[2 * kt + 1][0]), tc_gelu(acc[2 * kt + 1][1]));
+        a[kt][3] = bf16x2(tc_gelu(acc[2 * kt + 1][2]), tc_gelu(acc[2 * kt + 1][3]));
+    }
+    // layer 2
+#pragma unroll
+    for (int nt = 0; nt < kTcMaxH / 8; ++nt) {
+        const int c = nt * 8 + 2 * tig;
+        acc[nt][0] = nt < nth ? b2[c] : 0.0f;
+        acc[nt][1] = nt < nth ? b2[c + 1] : 0.0f;
+        acc[nt][2] = acc[nt][0];
+        acc[nt][3] = acc[nt][1];
+    }
+#pragma unroll
+    for (int kt = 0; kt < kTcMaxH / 16; ++kt) {
+        if (kt >= kth) break;
+#pragma unroll
+        for (int nt = 0; nt < kTcMaxH / 8; ++nt) {
+            if (nt >= nth) break;
+            const uint32_t* row = (const uint32_t*)(W2 + (nt * 8 + g) * L.ld2 + kt * 16 + 2 * tig);
+            mma_bf16(acc[nt], a[kt], row[0], row[4]);
+        }
+    }
+#pragma unroll
+    for (int kt = 0; kt < kTcMaxH / 16; ++kt) {
+        a[kt][0] = bf16x2(tc_gelu(acc[2 * kt][0]), tc_gelu(acc[2 * kt][1]));
+        a[kt][1] = bf16x2(tc_gelu(acc[2 * kt][2]), tc_gelu(acc[2 * kt][3]));
+        a[kt][2] = bf16x2(tc_gelu(acc[2 * kt + 1][0]), tc_gelu(acc[2 * kt + 1][1]));
+        a[kt][3] = bf16x2(tc_gelu(acc[2 * kt + 1][2]), tc_gelu(acc[2 * kt + 1][3]));
+    }
+    // layer 3: one 8-output tile at a time, straight to shared memory
+    for (int nt = 0; nt < L.Gp / 8; ++nt) {
+        const int c = nt * 8 + 2 * tig;
+        float d[4] = {b3[c], b3[c + 1], b3[c], b3[c + 1]};
+#pragma unroll
+        for (int kt = 0; kt < kTcMaxH / 16; ++kt) {
+            if (kt >= kth) break;
+            const uint32_t* row = (const uint32_t*)(W3 + (nt * 8 + g) * L.ld3 + kt * 16 + 2 * tig);
+            mma_bf16(d, a[kt], row[0], row[4]);
+        }
+        out[g * ldo + c] = d[0];
+        out[g * ldo + c + 1] = d[1];
+        out[(g + 8) * ldo + c] = d[2];
+        out[(g + 8) * ldo + c + 1] = d[3];
+    }
+}
+
+// Per program (pass): each static slot's network output (-1: none, or the
+// slot's width is 0), width and static part S_k = floor(eps s_k / p_att 2^24).
+struct TcSlots {
+    int16_t out[kMaxLearnedSlots];
+    int64_t width[kMaxLearnedSlots];
+    int64_t st[kMaxLearnedSlots];
+};
+
+__device__ void tc_slots_fill(const StepParams& P, const Prog& prog, TcSlots* s, int tid, int nthr)
+{
+    const int64_t p_att = prog.h->p_att;
+    for (int k = tid; k < prog.h->n_stat; k += nthr) {
+        const int64_t w = slot_width(prog, k);
+        s->width[k] = w;
+        s->out[k] = (int16_t)(w > 0 ? lp_output(P, prog.stat[k].mask) : -1);
+        s->st[k] = (w > 0 && p_att > 0 && p_att < (1ll << 52))
+                       ? (int64_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)P.mlp_eps, (double)w), (double)p_att),
+                                                  16777216.0))
+                       : 0;
+    }
+}
+
+// The weights Q_k of one source from its logits lg (by output; overwritten
+// with the exponentials by tc_row_prepare): m = max over the slots with an
+// output, e = exp(z - m), S = sum e in slot order, L_k = floor((1 - eps) e /
+// S 2^24), Q_k = max(1, L_k + S_k) on slots of positive width, the first
+// largest absorbing 2^24 - sum Q.  One thread per source; the light and the
+// heavy kernels share these two functions, so a parent's Q is the same on
+// either path.
+struct TcRow {
+    float S;
+    int arg;
+    int64_t rem;
+};
+
+__device__ __forceinline__ int64_t tc_q(const float* lg, const TcSlots* s, int k, float S, float eps)
+{
+    const int o = s->out[k];
+    int64_t L = 0;
+    if (o >= 0 && S > 0.0f)
+        L = (int64_t)floorf(__fmul_rn(__fmul_rn(__fsub_rn(1.0f, eps), __fdiv_rn(lg[o], S)), 16777216.0f));
+    const int64_t Q = L + s->st[k];
+    return Q < 1 ? 1 : Q;
+}
+
+__device__ TcRow tc_row_prepare(float* lg, const TcSlots* s, int ns, float eps)
+{
+    float m = -INFINITY;
+    for (int k = 0; k < ns; ++k)
+        if (s->out[k] >= 0) m = fmaxf(m, lg[s->out[k]]);
+    float S = 0.0f;
+    for (int k = 0; k < ns; ++k) {
+        const int o = s->out[k];
+        if (o < 0) continue;
+        const float e = expf(__fsub_rn(lg[o], m));
+        lg[o] = e;
+        S = __fadd_rn(S, e);
+    }
+    int64_t sum = 0, qa = -1;
+    int arg = -1;
+    for (int k = 0; k < ns; ++k) {
+        if (s->width[k] <= 0) continue;
+        const int64_t Q = tc_q(lg, s, k, S, eps);
+        sum += Q;
+        if (Q > qa) {
+            qa = Q;
+            arg = k;
+        }
+    }
+    TcRow r;
+    r.S = S;
+    r.arg = arg;
+    r.rem = (1ll << 24) - sum;
+    return r;
+}
+
+// The slot whose interval [cum_{k-1}, cum_k) of the weights holds V (ns when
+// none does) and its weight *Qk.
+__device__ int tc_row_choose(const float* lg, const TcSlots* s, int ns, float eps, const TcRow& r, uint32_t V,
+                             int64_t* Qk)
+{
+    int64_t cum = 0;
+    for (int k = 0; k < ns; ++k) {
+        if (s->width[k] <= 0) continue;
+        const int64_t Q = tc_q(lg, s, k, r.S, eps) + (k == r.arg ? r.rem : 0);
+        cum += Q;
+        if ((int64_t)V < cum) {
+            *Qk = Q;
+            return k;
+        }
+    }
+    *Qk = 0;
+    return ns;
+}
+
+// Light parents under the tensor-core proposal: each warp takes 16
+// candidates at a time.  Shared memory: the network (TcLayout), the slot
+// tables of both passes, one 16-row logit tile per warp.
+__global__ void __launch_bounds__(kTcWarps * 32) k_spawn_learned_tc(StepParams P)
+{
+    extern __shared__ __align__(16) uint8_t tsm[];
+    __shared__ __align__(16) SRec sstage[kTcWarps][kStage];
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const TcLayout L = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nthr = kTcWarps * 32;
+    for (int i = threadIdx.x; i < L.bytes / 16; i += nthr) ((uint4*)tsm)[i] = ((const uint4*)P.mlp_tc)[i];
+    TcSlots* slots = (TcSlots*)(tsm + L.bytes);
+    const int ldo = L.Gp + 4;
+    float* lgt = (float*)(tsm + L.bytes + 2 * sizeof(TcSlots)) + warp * 16 * ldo;
+    const StepInfo inf = P.info[st->call_index];
+    const int cur = st->cur, prv = (cur + 2) % 3;
+    const Prog prog[2] = {prog_at(prog_ptr(P, inf, 0, 0)), prog_at(prog_ptr(P, inf, 0, inf.ab2 ? 1 : 0))};
+    for (int ph = 0; ph < 2; ++ph) tc_slots_fill(P, prog[ph], slots + ph, threadIdx.x, nthr);
+    __syncthreads();
+    const int64_t total = min(st->cand_total, P.cand_cap);
+    SRec* stage = sstage[warp];
+    int staged = 0;
+    const int n = P.seginfo[0].n;
+    const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    const float tph[2] = {__double2float_rn(inf.t[0]), __double2float_rn(inf.t[1])};
+    const int64_t ntiles = (total + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kTcWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTcWarps) {
+        const int64_t i = tile * 16 + lane;
+        // lanes 0..15: one candidate each
+        bool att = false;
+        uint32_t x = 0u, y = 0u, j = 0u, seg = 0u;
+        int comp = 0, phase = 0, non = 0, sg = 1;
+        uint64_t key = 0ull;
+        if (lane < 16 && i < total) {
+            const uint4 cv = __ldcs((const uint4*)P.cand + i);
+            comp = (int)((cv.w >> 20) & 1u);
+            phase = (int)((cv.w >> 21) & 1u);
+            non = (int)((cv.w >> 22) & 1u);
+            sg = ((cv.w >> 23) & 1u) ? 1 : -1;
+            j = cv.w & kJ20;
+            seg = cv.y;
+            const uint32_t rank = cv.x - (uint32_t)__ldg(&P.segoff[phase ? prv : cur][cv.y]);
+            const int64_t T = walker_T(cv.z, rank, j, comp, phase, P.kd[cv.y]);
+            const int64_t p_att = prog[phase].h->p_att;
+            if (p_att >= (1ll << 52)) set_error(st, DERR_DT_TOO_LARGE);
+            att = p_att < (1ll << 52) && T < p_att;
+            key = __ldg(&(phase ? P.pop[prv] : P.pop[cur])[cv.x].key);
+            x = (uint32_t)(key >> n);
+            y = (uint32_t)(key & ymask);
+        }
+        const int ga = lane >> 2, gb = ga + 8;
+        const uint32_t xa = __shfl_sync(kFull, x, ga), ya = __shfl_sync(kFull, y, ga);
+        const uint32_t xb = __shfl_sync(kFull, x, gb), yb = __shfl_sync(kFull, y, gb);
+        const float ta = tph[__shfl_sync(kFull, phase, ga)], tb = tph[__shfl_sync(kFull, phase, gb)];
+        tc_forward(tsm, L, n, xa, ya, __bfloat162float(__float2bfloat16_rn(ta)), xb, yb,
+                   __bfloat162float(__float2bfloat16_rn(tb)), lgt, ldo, lane);
+        __syncwarp();
+        SRec rec[2];
+        bool ok[2] = {false, false};
+        if (att) {
+            const Prog& pg = prog[phase];
+            uint32_t V;
+            double u[2];
+            lp_draws(key, phase, comp, j, P.kd[seg], &V, &u[0], &u[1]);
+            int64_t Qk;
+            float* lg = lgt + lane * ldo;
+            const TcRow tr = tc_row_prepare(lg, slots + phase, pg.h->n_stat, P.mlp_eps);
+            const int k = tc_row_choose(lg, slots + phase, pg.h->n_stat, P.mlp_eps, tr, V, &Qk);
+            if (k < pg.h->n_stat) {
+                int64_t v[2];
+                value_at_mask(pg, pg.stat[k].mask, x, y, &v[0], &v[1]);
+                for (int c = 0; c < 2; ++c) {
+                    const int64_t cnt = lp_count(v[c], Qk, pg.h->p_att, u[c]);
+                    if (cnt == 0) continue;
+                    if (cnt > 0x7FFFFFFFll) {
+                        set_error(st, DERR_POP_OVERFLOW);
+                        continue;
+                    }
+                    ok[c] = true;
+                    rec[c] = make_spawn(key ^ pg.stat[k].mask, (int)seg, comp, c, v[c], sg, phase ? -1 : 1, non,
+                                        (int32_t)cnt);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t bal = __ballot_sync(kFull, ok[c]);
+            const int nrec = __popc(bal);
+            if (staged + nrec > kStage) {
+                warp_flush(stage, staged, P, lane);
+                staged = 0;
+            }
+            if (ok[c]) stage[staged + __popc(bal & ((1u << lane) - 1u))] = rec[c];
+            staged += nrec;
+            __syncwarp();
+        }
+    }
+    if (staged) warp_flush(stage, staged, P, lane);
+}
+
+__host__ __device__ __forceinline__ int tc_smem_bytes(const TcLayout& L, int warps)
+{
+    return L.bytes + 2 * (int)sizeof(TcSlots) + warps * 16 * (L.Gp + 4) * 4;
+}
+
+// ---------------------------------------------------------------------------
 // Spawning, heavy parents: one CTA per chunk of kHeavyChunk walkers of one
 // parent component.  The column is evaluated once into shared memory as a
 // cumulative weight table; each spawned walker finds its interval from a
@@ -1211,7 +1559,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spawn_learned(StepParams P)
 // counts are aggregated per (destination, channel) and emitted as one record
 // each.
 // ---------------------------------------------------------------------------
-template <bool kLearned>
+template <bool kLearned, bool kTc>
 __device__ __forceinline__ void spawn_heavy(const StepParams& P)
 {
     __shared__ int64_t cum[2 * kMaxEntries];
@@ -1235,6 +1583,16 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // learned proposal: 64-bit walker counts per (slot, channel) bin, over hist
     unsigned long long* lh = (unsigned long long*)hist;
+    // tensor-core proposal: the network, one program's slot table and a 16-row logit tile (dynamic)
+    extern __shared__ __align__(16) uint8_t hsm[];
+    const TcLayout TL = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
+    TcSlots* hslots = (TcSlots*)(hsm + TL.bytes);
+    const int hldo = TL.Gp + 4;
+    float* hlg = (float*)(hsm + TL.bytes + sizeof(TcSlots));
+    if (kTc) {
+        for (int i = tid; i < TL.bytes / 16; i += kThreads) ((uint4*)hsm)[i] = ((const uint4*)P.mlp_tc)[i];
+        __syncthreads();
+    }
 
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const HeavyItem it = P.heavy[item];
@@ -1293,7 +1651,32 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
                 vals[3 * k + 2] = width - iabs64(vr) - iabs64(vi);   // no-spawn remainder
             }
         const int ns = prog.h->n_stat;
-        if (learned) {
+        if (learned && kTc) {
+            // the source's weights Q (cum[k], then their inclusive prefix), the
+            // network on the tensor cores as on the light path (every row of the tile the parent)
+            for (int k = tid; k < ns; k += kThreads) {
+                int64_t vr, vi;
+                value_at_mask(prog, prog.stat[k].mask, x, y, &vr, &vi);
+                vals[2 * k] = vr;
+                vals[2 * k + 1] = vi;
+            }
+            for (int b = tid; b < nb; b += kThreads) lh[b] = 0ull;
+            tc_slots_fill(P, prog, hslots, tid, kThreads);
+            if (warp == 0) {
+                const float tb = __bfloat162float(__float2bfloat16_rn(__double2float_rn(inf.t[it.phase])));
+                tc_forward(hsm, TL, n, x, y, tb, x, y, tb, hlg, hldo, lane);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const TcRow r = tc_row_prepare(hlg, hslots, ns, P.mlp_eps);
+                int64_t run = 0;
+                for (int k = 0; k < ns; ++k) {
+                    if (hslots->width[k] > 0) run += tc_q(hlg, hslots, k, r.S, P.mlp_eps) + (k == r.arg ? r.rem : 0);
+                    cum[k] = run;
+                }
+            }
+            __syncthreads();
+        } else if (learned) {
             // the source's weights Q (cum[k], then their inclusive prefix)
             const LpNet net = lp_net(P);
             const float tf32 = __double2float_rn(inf.t[it.phase]);
@@ -1397,18 +1780,20 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
         const uint2 kd = P.kd[it.seg];
         const uint32_t rank = (uint32_t)(it.parent - P.segoff[it.phase ? prv : cur][it.seg]);
         const uint32_t pre = (uint32_t)(Pw >> 20);
-        // draw units: unit 0 is walker 0 (a word of the rank group's call),
-        // unit v >= 1 the parent's call v - 1 (walkers 4v - 3 .. 4v)
-        const int64_t v_lo = gw_lo == 0 ? 0 : 1 + ((gw_lo - 1) >> 2);
-        const int64_t v_hi = (gw_hi - 1 == 0 ? 0 : 1 + ((gw_hi - 2) >> 2)) + 1;
+        // draw units: units 0 and 1 are walkers 0 and 1 (words of the rank
+        // group's calls of levels 0 and 1), unit v >= 2 the parent's call
+        // v - 2 (walkers 4v - 6 .. 4v - 3)
+        auto unit_of = [](int64_t w) -> int64_t { return w <= 1 ? w : 2 + ((w - 2) >> 2); };
+        const int64_t v_lo = unit_of(gw_lo), v_hi = unit_of(gw_hi - 1) + 1;
         for (int64_t v = v_lo + tid; v < v_hi; v += kThreads) {
-            const uint4 o = v == 0 ? group_words(rank >> 2, it.phase, kd) : extra_words(rank, (uint32_t)(v - 1), it.phase, kd);
+            const uint4 o = v <= 1 ? group_words(rank >> 2, (uint32_t)v, it.phase, kd)
+                                   : extra_words(rank, (uint32_t)(v - 2), it.phase, kd);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (v == 0 && q > 0) break;
-                const int64_t w = v == 0 ? 0 : 4 * v - 3 + q;
+                if (v <= 1 && q > 0) break;
+                const int64_t w = v <= 1 ? v : 4 * v - 6 + q;
                 if (w < gw_lo || w >= gw_hi) continue;
-                const uint32_t W = v == 0 ? word_of(o, (int)(rank & 3u)) : word_of(o, q);
+                const uint32_t W = v <= 1 ? word_of(o, (int)(rank & 3u)) : word_of(o, q);
                 if (W > pre) continue;   // T >= (pre + 1) << 20 > P
                 const uint32_t j = (uint32_t)(w - wb);
                 const int64_t T = walker_T(W, rank, j, comp, it.phase, kd);
@@ -1475,8 +1860,9 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
 
 // The plain and static-proposal kernel carries none of the learned
 // proposal's state (fewer registers, more resident CTAs).
-__global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P) { spawn_heavy<false>(P); }
-__global__ void __launch_bounds__(kThreads) k_spawn_heavy_learned(StepParams P) { spawn_heavy<true>(P); }
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy(StepParams P) { spawn_heavy<false, false>(P); }
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy_learned(StepParams P) { spawn_heavy<true, false>(P); }
+__global__ void __launch_bounds__(kThreads) k_spawn_heavy_learned_tc(StepParams P) { spawn_heavy<true, true>(P); }
 
 // ---------------------------------------------------------------------------
 // LSD radix sort of spawn records by (segment, key).
@@ -2873,7 +3259,7 @@ const char* const kKernelNames[kNumTimedKernels] = {
 
 namespace {
 // persistent grids: resident CTAs per SM x SMs, per kernel
-int g_grid_spawn = 0, g_grid_choose = 0, g_grid_learned = 0, g_grid_heavy = 0, g_grid_heavy_learned = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0;
+int g_grid_spawn = 0, g_grid_choose = 0, g_grid_learned = 0, g_grid_heavy = 0, g_grid_heavy_learned = 0, g_grid_bsmall = 0, g_grid_bbig = 0, g_grid_sort = 0, g_grid_merge = 0, g_grid_learned_tc = 0;
 
 int resident(const void* fn, int smem, int sms, int threads = kThreads)
 {
@@ -2902,6 +3288,28 @@ void configure_kernels()
     g_grid_bsmall = resident((const void*)k_bucket_sort_small, kSmallSortSmem, sms);
     g_grid_bbig = resident((const void*)k_bucket_sort_big, kBigSortSmem, sms);
     g_grid_misc = 2 * sms;
+    // tensor-core proposal: sized for the largest network (64 hidden, 256 outputs, 80 inputs)
+    const TcLayout big = tc_layout(kTcMaxIp, kTcMaxH, kTcMaxGp);
+    const int tc_light = tc_smem_bytes(big, kTcWarps);
+    const int tc_heavy = big.bytes + (int)sizeof(TcSlots) + 16 * (big.Gp + 4) * 4;
+    cudaFuncSetAttribute(k_spawn_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_light);
+    cudaFuncSetAttribute(k_spawn_heavy_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_heavy);
+    g_grid_learned_tc = resident((const void*)k_spawn_learned_tc, tc_light, sms, kTcWarps * 32);
+}
+
+// Persistent grid of the tensor-core proposal's light kernel for its actual
+// shared memory (the network's size sets it).
+int tc_grid(int smem)
+{
+    static int cached_smem = -1, cached_grid = 0;
+    if (smem != cached_smem) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached_grid = resident((const void*)k_spawn_learned_tc, smem, sms, kTcWarps * 32);
+        cached_smem = smem;
+    }
+    return cached_grid;
 }
 
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev)
@@ -2916,13 +3324,20 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
     mark(1);
     k_spawn_draw<<<cap(g_grid_spawn), kThreads, kDrawSmem, stream>>>(P);
     mark(2);
+    const TcLayout TL = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
     if (P.proposal == 2)   // timed in the choose slot
         k_spawn_learned<<<cap(g_grid_learned), kThreads, 0, stream>>>(P);
+    else if (P.proposal == 3)
+        k_spawn_learned_tc<<<cap(tc_grid(tc_smem_bytes(TL, kTcWarps))), kTcWarps * 32, tc_smem_bytes(TL, kTcWarps),
+                             stream>>>(P);
     else
         k_spawn_choose<<<cap(g_grid_choose), kThreads, 0, stream>>>(P);
     mark(3);
     if (P.proposal == 2)
         k_spawn_heavy_learned<<<cap(g_grid_heavy_learned), kThreads, 0, stream>>>(P);
+    else if (P.proposal == 3)
+        k_spawn_heavy_learned_tc<<<cap(g_grid_heavy_learned), kThreads,
+                                   TL.bytes + (int)sizeof(TcSlots) + 16 * (TL.Gp + 4) * 4, stream>>>(P);
     else
         k_spawn_heavy<<<cap(g_grid_heavy), kThreads, 0, stream>>>(P);
     mark(4);
@@ -2989,6 +3404,44 @@ void launch_antiherm(const StepParams& P, unsigned long long* out, int grid, cud
     if (g_grid_spawn == 0) configure_kernels();
     cudaMemsetAsync(out, 0, (size_t)P.nseg * 16, stream);
     k_antiherm<<<grid > 0 ? grid : g_grid_misc, kThreads, 0, stream>>>(P, out);
+}
+
+// The packed fp32 parameters in the tensor-core layout: one thread per
+// element of the padded buffer (weights rounded to bf16, padding zero).
+__global__ void k_mlp_tc_pack(const float* __restrict__ prm, TcLayout L, uint8_t* __restrict__ out)
+{
+    const int I = L.I, H = L.H, G = L.G;
+    const float* w1 = prm;
+    const float* b1 = w1 + H * I;
+    const float* w2 = b1 + H;
+    const float* b2 = w2 + H * H;
+    const float* w3 = b2 + H;
+    const float* b3 = w3 + G * H;
+    const int n1 = H * L.ld1, n2 = H * L.ld2, n3 = L.Gp * L.ld3;
+    const int total = n1 + n2 + n3 + 2 * H + L.Gp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const int r = e / L.ld1, c = e % L.ld1;
+            ((__nv_bfloat16*)(out + L.o_w1))[e] = __float2bfloat16_rn(c < I ? w1[r * I + c] : 0.0f);
+        } else if (e < n1 + n2) {
+            const int f = e - n1, r = f / L.ld2, c = f % L.ld2;
+            ((__nv_bfloat16*)(out + L.o_w2))[f] = __float2bfloat16_rn(c < H ? w2[r * H + c] : 0.0f);
+        } else if (e < n1 + n2 + n3) {
+            const int f = e - n1 - n2, r = f / L.ld3, c = f % L.ld3;
+            ((__nv_bfloat16*)(out + L.o_w3))[f] = __float2bfloat16_rn(c < H && r < G ? w3[r * H + c] : 0.0f);
+        } else {
+            const int f = e - n1 - n2 - n3;
+            if (f < H) ((float*)(out + L.o_b1))[f] = b1[f];
+            else if (f < 2 * H) ((float*)(out + L.o_b2))[f - H] = b2[f - H];
+            else ((float*)(out + L.o_b3))[f - 2 * H] = (f - 2 * H) < G ? b3[f - 2 * H] : 0.0f;
+        }
+    }
+}
+
+void launch_mlp_tc_pack(const float* params, const TcLayout& L, uint8_t* out, cudaStream_t stream)
+{
+    cudaMemsetAsync(out, 0, (size_t)L.bytes, stream);
+    k_mlp_tc_pack<<<64, 256, 0, stream>>>(params, L, out);
 }
 
 void launch_antiherm_sum(const StepParams& P, const int32_t* segs, int count, unsigned long long* out, int grid,

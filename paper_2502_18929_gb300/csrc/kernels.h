@@ -119,7 +119,45 @@ struct StepParams {
     const int32_t* mlp_idx;     // output index of each sorted mask
     int mlp_in, mlp_hidden, mlp_out;
     float mlp_eps;
+    const uint8_t* mlp_tc;   // the network for the tensor-core proposal (bf16 weights, padded; see TcLayout)
+    int mlp_ip, mlp_gp;      // inputs padded to a multiple of 16, outputs to a multiple of 8
 };
+
+// The network in the tensor-core proposal's layout (bytes from the buffer's
+// start): W1 [H][Ip + 8], W2 [H][H + 8], W3 [Gp][H + 8] in bf16 (row = output
+// neuron, zero padding), then b1 [H], b2 [H], b3 [Gp] in fp32.  Rows are
+// padded by 8 elements so that the eight rows a warp's B fragment reads fall
+// in distinct shared-memory banks.
+struct TcLayout {
+    int I, H, G, Ip, Gp;
+    int ld1, ld2, ld3;                 // row lengths (elements)
+    int o_w1, o_w2, o_w3, o_b1, o_b2, o_b3, bytes;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int I, int H, int G)
+{
+    TcLayout L;
+    L.I = I;
+    L.H = H;
+    L.G = G;
+    L.Ip = (I + 15) / 16 * 16;
+    L.Gp = (G + 7) / 8 * 8;
+    L.ld1 = L.Ip + 8;
+    L.ld2 = H + 8;
+    L.ld3 = H + 8;
+    L.o_w1 = 0;
+    L.o_w2 = L.o_w1 + 2 * H * L.ld1;
+    L.o_w3 = L.o_w2 + 2 * H * L.ld2;
+    L.o_b1 = (L.o_w3 + 2 * L.Gp * L.ld3 + 15) / 16 * 16;
+    L.o_b2 = L.o_b1 + 4 * H;
+    L.o_b3 = L.o_b2 + 4 * H;
+    L.bytes = (L.o_b3 + 4 * L.Gp + 15) / 16 * 16;
+    return L;
+}
+
+// Pack the fp32 parameters (w1, b1, w2, b2, w3, b3) into the tensor-core
+// layout (bf16 weights rounded to nearest even).
+void launch_mlp_tc_pack(const float* params, const TcLayout& L, uint8_t* out, cudaStream_t stream);
 
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
 // launch sequence can be captured once in a CUDA graph and replayed.
@@ -156,6 +194,30 @@ struct LearnGrad {
     float *h1t, *h2t, *dzt, *d2t, *d1t, *lossv;   // scratch [rows][ld]
     double* wsum;
 };
+
+// Loss and gradient of the tensor-core proposal's network (bf16 operands,
+// fp32 accumulation, GELU): one warp per 16 events for the forward pass, the
+// masked softmax cross-entropy and the backpropagated signals (stored as bf16
+// rows over events), then the weight gradients as bf16 matrix products over
+// chunks of events, summed chunk by chunk in a fixed order.
+struct LearnTc {
+    const float* params;        // packed fp32 w1, b1, w2, b2, w3, b3 (master weights)
+    const float* feat;
+    const float* target;
+    const float* weight;
+    int64_t ld, E;              // the caller's event arrays: [rows][ld], E events
+    int I, H, G;
+    uint8_t* wts;               // training weights: TcLayout, then W2^T [H][H + 8], W3^T [H][Gp + 8] (bf16)
+    int64_t ldp;                // scratch row length (E rounded up to 16)
+    uint16_t *h1t, *h2t, *d1t, *d2t, *dzt;   // bf16 [rows][ldp]
+    float* lossv;               // [ldp]
+    float* partials;            // [chunks][params]
+    double* wsum;
+};
+constexpr int64_t kLearnTcChunk = 4096;   // events per partial weight gradient
+int64_t learn_tc_weights_bytes(int I, int H, int G);
+int64_t learn_tc_scratch_bytes(int I, int H, int G, int64_t E);   // bf16 rows, losses and partials
+void launch_learn_grad_tc(const LearnTc& A, float* grad, double* loss, cudaStream_t stream);
 
 void launch_learn_events(const LearnArgs& A, cudaStream_t stream);
 void launch_learn_grad(const LearnGrad& A, float* grad, double* loss, cudaStream_t stream);

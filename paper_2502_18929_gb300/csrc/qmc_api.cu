@@ -176,6 +176,12 @@ StepParams params(qmc_ctx* c)
     P.mlp_hidden = c->mlp_hidden;
     P.mlp_out = c->mlp_out;
     P.mlp_eps = c->mlp_eps;
+    P.mlp_tc = c->d_mlp_tc;
+    {
+        const TcLayout L = tc_layout(c->mlp_in, c->mlp_hidden, c->mlp_out);
+        P.mlp_ip = L.Ip;
+        P.mlp_gp = L.Gp;
+    }
     return P;
 }
 
@@ -495,8 +501,8 @@ void qmc_destroy(qmc_ctx* ctx)
                     ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_gofs[0], ctx->d_gofs[1], ctx->d_gofs[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
                     ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
                     ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_zacc, ctx->d_zhist, ctx->d_aux, ctx->d_info,
-                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_mask,
-                    ctx->d_mlp_idx, ctx->d_learn_prog, ctx->d_learn_scratch, ctx->d_learn_small};
+                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_tc, ctx->d_mlp_mask,
+                    ctx->d_mlp_idx, ctx->d_learn_prog, ctx->d_learn_scratch, ctx->d_learn_small, ctx->d_learn_tc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
@@ -532,13 +538,39 @@ int qmc_load_schedule(qmc_ctx* ctx, const qmc_ham_term* ham, int32_t n_ham, cons
     return QMC_OK;
 }
 
+namespace {
+// The network in the tensor-core proposal's layout (bf16 weights), rebuilt
+// from the fp32 parameters whenever they change; left null when the network
+// does not fit that path (hidden width a multiple of 16 up to 64, at most 256
+// outputs and 80 inputs).
+int repack_tc(qmc_ctx* ctx)
+{
+    const int I = ctx->mlp_in, H = ctx->mlp_hidden, G = ctx->mlp_out;
+    if (!ctx->d_mlp || H % 16 != 0 || H > 64 || G > 256 || I > 80) {
+        if (ctx->d_mlp_tc) cudaFree(ctx->d_mlp_tc);
+        ctx->d_mlp_tc = nullptr;
+        return QMC_OK;
+    }
+    const TcLayout L = tc_layout(I, H, G);
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->d_mlp_tc, (int64_t)L.bytes)) != QMC_OK) return rc;
+    launch_mlp_tc_pack(ctx->d_mlp, L, ctx->d_mlp_tc, ctx->work);
+    CK(cudaGetLastError());
+    return QMC_OK;
+}
+} // namespace
+
 int qmc_set_proposal(qmc_ctx* ctx, int32_t kind)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
-    if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC && kind != QMC_PROPOSAL_LEARNED)
+    if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC && kind != QMC_PROPOSAL_LEARNED &&
+        kind != QMC_PROPOSAL_LEARNED_TC)
         return fail(ctx, QMC_ERR_INVALID_ARG, "unknown proposal kind");
-    if (kind == QMC_PROPOSAL_LEARNED && !ctx->d_mlp)
+    if ((kind == QMC_PROPOSAL_LEARNED || kind == QMC_PROPOSAL_LEARNED_TC) && !ctx->d_mlp)
         return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    if (kind == QMC_PROPOSAL_LEARNED_TC && !ctx->d_mlp_tc)
+        return fail(ctx, QMC_ERR_INVALID_ARG,
+                    "the tensor-core proposal needs a hidden width of 16, 32, 48 or 64, at most 256 outputs and 80 inputs");
     if (ctx->proposal != kind) {
         ctx->proposal = kind;
         ctx->graph_dirty = true;
@@ -585,6 +617,8 @@ int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* m)
     ctx->mlp_hidden = H;
     ctx->mlp_out = G;
     ctx->mlp_eps = m->eps;
+    if ((rc = repack_tc(ctx)) != QMC_OK) return rc;
+    if (ctx->proposal == QMC_PROPOSAL_LEARNED_TC && !ctx->d_mlp_tc) ctx->proposal = QMC_PROPOSAL_EXACT;
     ctx->graph_dirty = true;
     return leave(ctx);
 }
@@ -596,6 +630,7 @@ int64_t mlp_param_count(const qmc_ctx* c)
     return H * I + H + H * H + H + G * H + G;
 }
 } // namespace
+
 
 int qmc_learn_param_count(qmc_ctx* ctx, int64_t* n_params)
 {
@@ -686,6 +721,61 @@ int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const f
     return leave(ctx);
 }
 
+int qmc_learn_grad_tc(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
+                      int64_t ld, int64_t n_events, float* grad, double* loss)
+{
+    if (!ctx || !params || !feat || !target || !weight || !grad || !loss) return QMC_ERR_INVALID_ARG;
+    if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
+    if (!ctx->d_mlp_tc)
+        return fail(ctx, QMC_ERR_INVALID_ARG,
+                    "the tensor-core network needs 16, 32, 48 or 64 hidden units, at most 256 outputs and 80 inputs");
+    if (n_events < 1 || ld < n_events) return fail(ctx, QMC_ERR_INVALID_ARG, "need 1 <= n_events <= ld");
+    if (((uintptr_t)feat & 15u) || ((uintptr_t)target & 15u) || ((uintptr_t)weight & 15u))
+        return fail(ctx, QMC_ERR_INVALID_ARG, "event arrays must be 16-byte aligned");
+    const int I = ctx->mlp_in, H = ctx->mlp_hidden, G = ctx->mlp_out;
+    const int64_t wb = learn_tc_weights_bytes(I, H, G);
+    const int64_t need = wb + learn_tc_scratch_bytes(I, H, G, n_events);
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if (need > ctx->learn_tc_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_learn_tc, need)) != QMC_OK) return rc;
+        ctx->learn_tc_cap = need;
+    }
+    if (!ctx->d_learn_small && (rc = dalloc(ctx, &ctx->d_learn_small, 4)) != QMC_OK) return rc;
+    const TcLayout L = tc_layout(I, H, G);
+    LearnTc A;
+    A.params = params;
+    A.feat = feat;
+    A.target = target;
+    A.weight = weight;
+    A.ld = ld;
+    A.E = n_events;
+    A.I = I;
+    A.H = H;
+    A.G = G;
+    A.wts = ctx->d_learn_tc;
+    A.ldp = (n_events + 15) / 16 * 16;
+    uint8_t* p = ctx->d_learn_tc + (wb + 255) / 256 * 256;
+    auto take = [&](int64_t bytes) {
+        uint8_t* r = p;
+        p += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    A.h1t = (uint16_t*)take(2 * A.ldp * H);
+    A.h2t = (uint16_t*)take(2 * A.ldp * H);
+    A.d1t = (uint16_t*)take(2 * A.ldp * H);
+    A.d2t = (uint16_t*)take(2 * A.ldp * H);
+    A.dzt = (uint16_t*)take(2 * A.ldp * L.Gp);
+    A.lossv = (float*)take(4 * A.ldp);
+    A.partials = (float*)p;
+    A.wsum = ctx->d_learn_small + 1;
+    launch_learn_grad_tc(A, grad, ctx->d_learn_small + 2, ctx->work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(loss, ctx->d_learn_small + 2, 8, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return leave(ctx);
+}
+
 int qmc_learn_adam(qmc_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t n_params, int64_t t,
                    float lr, float beta1, float beta2, float eps)
 {
@@ -708,6 +798,9 @@ int qmc_learn_load(qmc_ctx* ctx, const float* params)
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     CK(cudaMemcpyAsync(ctx->d_mlp, params, (size_t)mlp_param_count(ctx) * 4, cudaMemcpyDeviceToDevice, ctx->work));
+    if (ctx->d_mlp_tc) launch_mlp_tc_pack(ctx->d_mlp, tc_layout(ctx->mlp_in, ctx->mlp_hidden, ctx->mlp_out),
+                                          ctx->d_mlp_tc, ctx->work);
+    CK(cudaGetLastError());
     return leave(ctx);
 }
 
@@ -1045,7 +1138,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         const ProgHeader* h = (const ProgHeader*)tmp.data();
         if (h->n_entry > kMaxEntries)
             return fail(ctx, QMC_ERR_INVALID_ARG, "column has more destinations than the heavy path holds");
-        if (ctx->proposal == QMC_PROPOSAL_LEARNED && h->n_stat > kMaxLearnedSlots)
+        if ((ctx->proposal == QMC_PROPOSAL_LEARNED || ctx->proposal == QMC_PROPOSAL_LEARNED_TC) &&
+            h->n_stat > kMaxLearnedSlots)
             return fail(ctx, QMC_ERR_INVALID_ARG, "learned proposal: more than 256 destinations per column");
         const size_t slot = 2 * (size_t)k + pass;
         if (last_off[slot] >= 0 && last_blob[slot] == tmp) {

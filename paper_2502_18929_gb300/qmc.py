@@ -29,7 +29,7 @@ ERR_CHECKPOINT = -11
 
 EULER = 0
 AB2 = 1
-PROPOSAL_EXACT, PROPOSAL_STATIC, PROPOSAL_LEARNED = 0, 1, 2
+PROPOSAL_EXACT, PROPOSAL_STATIC, PROPOSAL_LEARNED, PROPOSAL_LEARNED_TC = 0, 1, 2, 3
 
 EXPORTED = [
     "qmc_create", "qmc_destroy", "qmc_last_error", "qmc_load_schedule", "qmc_init_populations",
@@ -39,7 +39,7 @@ EXPORTED = [
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
     "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
-    "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum",
+    "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum", "qmc_learn_grad_tc",
 ]
 
 
@@ -126,6 +126,7 @@ def lib():
         L.qmc_learn_param_count.argtypes = [vp, vp]
         L.qmc_learn_events.argtypes = [vp, C.c_double, C.c_int64, vp, vp, vp, vp]
         L.qmc_learn_grad.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, vp, vp]
+        L.qmc_learn_grad_tc.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, vp, vp]
         L.qmc_learn_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_float,
                                      C.c_float]
         L.qmc_learn_load.argtypes = [vp, vp]
@@ -328,6 +329,17 @@ class QMC:
         self._check(self.L.qmc_learn_grad(self.h, params.data_ptr(), feat.data_ptr(), target.data_ptr(),
                                           weight.data_ptr(), feat.shape[1], n_events, grad.data_ptr(),
                                           C.byref(loss)), "qmc_learn_grad")
+        return loss.value, grad
+
+    def learn_grad_tc(self, params, feat, target, weight, n_events: int):
+        """(loss, grad) of the tensor-core network (bf16, GELU) over the first
+        n_events events."""
+        import torch
+        grad = torch.empty_like(params)
+        loss = C.c_double()
+        self._check(self.L.qmc_learn_grad_tc(self.h, params.data_ptr(), feat.data_ptr(), target.data_ptr(),
+                                             weight.data_ptr(), feat.shape[1], n_events, grad.data_ptr(),
+                                             C.byref(loss)), "qmc_learn_grad_tc")
         return loss.value, grad
 
     def learn_adam(self, params, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,

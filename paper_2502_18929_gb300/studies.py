@@ -3,6 +3,7 @@ xi -> 0 extrapolation, and replica aggregation with the paper's scaling fits.
 
     python -m paper_2502_18929_gb300.studies initiator --out initiator.json
     python -m paper_2502_18929_gb300.studies replicas --out replicas.json
+    python -m paper_2502_18929_gb300.studies proposal --workload ghz24 --out proposal.json
 
 * Initiator study [End Matter, simulation methodology: spawns of parents
   below xi N^diag onto unoccupied states are discarded; the truncation error
@@ -161,9 +162,122 @@ def replica_study(sizes=(8, 10, 12, 14), state: str = "plus", replicas: int = 5,
     return {"rows": rows, "fits": fits}
 
 
+def _final_fidelity(sim, target, n_diag):
+    ov = sim.overlap_all(target)
+    norm = sum(abs(complex(v)) ** 2 for v in target.values())
+    return np.abs(ov / norm) / n_diag
+
+
+def proposal_study(name: str = "ghz24", nvec: int = 32, n_diag: int = 10**5, train_events: int = 10**7,
+                   train_steps: int = 300, hidden: int = 64, eps: float = 0.1, t_end: float | None = None,
+                   seed: int = 3):
+    """The learned proposal against the static and the exact rule [A9; the
+    library's extension].  Training: events logged from a run of the exact
+    rule (heat-bath shares of every present destination, weighted by the
+    parent's walkers) until train_events are collected, then full-batch Adam
+    on the tensor cores.  Comparison: nvec vectors of n_diag walkers per rule
+    from the same initial state; the final fidelity's spread over vectors s
+    gives the walkers needed for a standard error of 10^-3, n_diag (s /
+    10^-3)^2, and the time to reach it, time (s / 10^-3)^2 / nvec."""
+    import torch
+    from . import train as TR
+    if name.startswith("dd"):
+        n = int(name[2:].rstrip("i"))
+        prob = P.dd_ring(n, seed=0, t_end=t_end or 4.0, x_basis=True)
+        rho0, target, dt, xi = P.rho_basis(0), {0: 1.0}, 0.005, 1e-3
+        t_end = t_end or 4.0
+    else:
+        n = int(name[3:].rstrip("i"))
+        prob = P.ghz_circuit(n)
+        rho0, target, dt, xi = P.rho_basis(0), P.ghz_target(n), 0.01, 1e-3 if name.endswith("i") else 0.0
+        t_end = t_end or float(n)
+    net = P.random_network(prob, hidden=hidden, seed=seed, eps=eps)
+    pl = planner.plan(prob, t_end, dt)
+    init_min = int(math.ceil(xi * n_diag))
+    # events from the exact rule
+    sim = qmc.QMC(prob.n, nvec, seed, n_diag, integrator=qmc.AB2, initiator_min=init_min)
+    sim.load_schedule(prob)
+    sim.set_mlp(net)
+    sim.init_populations(rho0)
+    t0 = time.time()
+    feats, targets, weights, total = [], [], [], 0
+    steps_total = planner.total_steps(pl)
+    every = max(1, steps_total // 60)
+    idx = 0
+    for tp0, d, k in pl:
+        done = 0
+        step, _, tpp, dl, pv = sim.clock()
+        sim.set_clock(step, tp0, tpp, dl, pv)
+        while done < k:
+            if total < train_events:
+                f, tg, w, ne = sim.learn_events(d, min(1 << 20, train_events - total))
+                feats.append(f[:, :ne])
+                targets.append(tg[:, :ne])
+                weights.append(w[:ne])
+                total += ne
+            m = min(every, k - done)
+            sim.step(d, m)
+            done += m
+        idx += k
+    sim.close()
+    feat = torch.cat(feats, dim=1).contiguous()
+    target_t = torch.cat(targets, dim=1).contiguous()
+    weight = torch.cat(weights).contiguous()
+    E = feat.shape[1]
+    collect_s = time.time() - t0
+    # training on the tensor cores
+    trainer = qmc.QMC(prob.n, 1, seed, n_diag)
+    trainer.load_schedule(prob)
+    trainer.set_mlp(net)
+    params = torch.tensor(TR.pack(net), device="cuda")
+    mo, vo = torch.zeros_like(params), torch.zeros_like(params)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    losses = []
+    for t in range(1, train_steps + 1):
+        loss, grad = trainer.learn_grad_tc(params, feat, target_t, weight, E)
+        losses.append(loss)
+        trainer.learn_adam(params, grad, mo, vo, t, 3e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    trained = TR.unpack(params.cpu().numpy(), net)
+    trainer.close()
+    # comparison
+    rows = []
+    for rule, kind, netw in (("exact", qmc.PROPOSAL_EXACT, None), ("static", qmc.PROPOSAL_STATIC, None),
+                             ("learned_tc_untrained", qmc.PROPOSAL_LEARNED_TC, net),
+                             ("learned_tc_trained", qmc.PROPOSAL_LEARNED_TC, trained)):
+        sim = qmc.QMC(prob.n, nvec, seed + 1, n_diag, integrator=qmc.AB2, initiator_min=init_min,
+                      stream=torch.cuda.current_stream().cuda_stream)
+        sim.load_schedule(prob)
+        if netw is not None:
+            sim.set_mlp(netw)
+        sim.set_proposal(kind)
+        sim.init_populations(rho0)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        planner.run(sim, pl)
+        ev1.record()
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) * 1e-3
+        fid = _final_fidelity(sim, target, n_diag)
+        spread = float(fid.std(ddof=1))
+        rows.append({"rule": rule, "fidelity": float(fid.mean()), "spread": spread, "seconds": sec,
+                     "walkers_needed_1e-3": n_diag * (spread / 1e-3) ** 2,
+                     "time_to_1e-3_s": sec * (spread / 1e-3) ** 2 / nvec})
+        sim.close()
+    return {"workload": name, "n": prob.n, "G": len(net["out_masks"]), "hidden": hidden, "events": E,
+            "collect_s": collect_s, "train_steps": train_steps, "train_s": train_s,
+            "loss_first": losses[0], "loss_last": losses[-1], "nvec": nvec, "n_diag": n_diag, "xi": xi,
+            "t_end": t_end, "rules": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["initiator", "replicas"])
+    ap.add_argument("study", choices=["initiator", "replicas", "proposal"])
+    ap.add_argument("--workload", default="ghz24")
+    ap.add_argument("--events", type=int, default=10**7)
     ap.add_argument("--out", default=None)
     ap.add_argument("--sizes", default=None, help="comma-separated qubit counts")
     ap.add_argument("--state", default="plus", choices=["plus", "w"])
@@ -176,9 +290,11 @@ def main():
     if args.study == "initiator":
         sizes = tuple(int(v) for v in args.sizes.split(",")) if args.sizes else (8, 16, 24, 32)
         res = {"rows": initiator_study(sizes, nvec=args.nvec, n_diag=args.n_diag or 10**5)}
-    else:
+    elif args.study == "replicas":
         sizes = tuple(int(v) for v in args.sizes.split(",")) if args.sizes else (8, 10, 12, 14)
         res = replica_study(sizes, state=args.state, n_diag=args.n_diag or 2 * 10**5)
+    else:
+        res = proposal_study(args.workload, nvec=args.nvec, n_diag=args.n_diag or 10**5, train_events=args.events)
     res["wall_s"] = time.time() - t0
     txt = json.dumps(res, indent=1)
     if args.out:

@@ -100,3 +100,70 @@ def test_adam_lowers_loss_towards_entropy():
     sim.learn_load(params)
     sim.set_proposal(qmc.PROPOSAL_LEARNED)
     sim.step(0.01, 10)
+
+
+@pytest.mark.parametrize("hidden,scale", [(16, 1.0), (64, 1.5)])
+def test_tc_gradient_matches_fp64(hidden, scale):
+    """The tensor-core network's loss and gradient (bf16 operands, fp32
+    accumulation, GELU) against the FP64 reference with the same bf16
+    roundings of weights, t and hidden activations: the remaining difference
+    is the bf16 rounding of the backpropagated signals and of the weight
+    products, about 1 % of the gradient's norm."""
+    prob = P.ghz_circuit(6)
+    net = P.random_network(prob, hidden=hidden, seed=hidden + 1, scale=scale)
+    pops = _spread(6, 3, 3000, 7)
+    gpu, (f, tg, w, ne), _ = _events_pair(prob, net, pops, 2.5, 0.01, 6000)
+    params = torch.tensor(T.pack(net), device="cuda")
+    fd, td, wd = (torch.tensor(a, device="cuda").contiguous() for a in (f, tg, w))
+    loss, grad = gpu.learn_grad_tc(params, fd, td, wd, ne)
+    G = len(net["out_masks"])
+    ref_loss, ref_g = Lr.loss_grad_tc(Lr.split_params(T.pack(net).astype(np.float64), 13, hidden, G), f, tg, w)
+    gref = Lr.pack(ref_g)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss), (loss, ref_loss)
+    rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert rel < 2e-2, rel
+    o = 0
+    for name, size in (("w1", hidden * 13), ("b1", hidden), ("w2", hidden * hidden), ("b2", hidden),
+                       ("w3", G * hidden), ("b3", G)):
+        blk = slice(o, o + size)
+        o += size
+        nb = np.linalg.norm(gref[blk])
+        if nb > 0:
+            assert np.linalg.norm(g[blk] - gref[blk]) / nb < 5e-2, name
+    # deterministic: the same call gives the same bits
+    loss2, grad2 = gpu.learn_grad_tc(params, fd, td, wd, ne)
+    assert loss2 == loss and torch.equal(grad, grad2)
+
+
+def test_tc_training_on_a_million_events():
+    """Events logged over a GHZ-8 run (256 vectors, at least 10^6), full-batch Adam on the
+    tensor cores: the loss falls most of the way to the heat-bath entropy,
+    and the trained network runs in the tensor-core proposal."""
+    prob = P.ghz_circuit(8)
+    net = P.random_network(prob, hidden=64, seed=2, eps=0.1)
+    sim = qmc.QMC(8, 256, 5, 200000)
+    sim.load_schedule(prob)
+    sim.set_mlp(net)
+    sim.init_populations(P.rho_basis(0))
+    sim.step(0.01, 150)
+    feat, target, weight = T.collect_events(sim, 0.01, 600, 25, 1 << 20)
+    E = feat.shape[1]
+    assert E >= 10**6, E
+    params = torch.tensor(T.pack(net), device="cuda")
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    first = None
+    for t in range(1, 151):
+        loss, grad = sim.learn_grad_tc(params, feat, target, weight, E)
+        first = loss if first is None else first
+        sim.learn_adam(params, grad, m, v, t, 3e-3)
+    final, _ = sim.learn_grad_tc(params, feat, target, weight, E)
+    tg = target.cpu().numpy().astype(np.float64)
+    w = weight.cpu().numpy().astype(np.float64)
+    p = np.where(tg > 0, tg, 1.0)
+    ent = float((w * -(np.where(tg > 0, tg * np.log(p), 0.0)).sum(axis=0)).sum() / w.sum())
+    assert final - ent < 0.3 * (first - ent), (first, final, ent)
+    sim.learn_load(params)
+    sim.set_proposal(qmc.PROPOSAL_LEARNED_TC)
+    sim.step(0.01, 10)

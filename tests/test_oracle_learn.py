@@ -130,3 +130,41 @@ def test_events_match_dense_heat_bath(t):
             else:
                 assert target[g, e] == -1.0
         assert weight[e] == (walkers[e] if W > 0 else 0)
+
+
+def test_tc_network_gradient_finite_differences():
+    """The tensor-core network's reference gradient (GELU, smooth form)
+    against central differences of its own loss."""
+    from oracle import learn as Lr
+    rng = np.random.default_rng(3)
+    I, H, G, E = 9, 16, 6, 40
+    params = {"w1": rng.normal(size=(H, I)) * 0.5, "b1": rng.normal(size=H) * 0.1,
+              "w2": rng.normal(size=(H, H)) * 0.4, "b2": rng.normal(size=H) * 0.1,
+              "w3": rng.normal(size=(G, H)) * 0.4, "b3": rng.normal(size=G) * 0.2}
+    feat = np.vstack([rng.integers(0, 2, size=(I - 1, E)).astype(np.float64), rng.uniform(0, 3, size=(1, E))])
+    target = rng.dirichlet(np.ones(G), size=E).T
+    target[rng.random((G, E)) < 0.2] = -1.0
+    weight = rng.integers(1, 5, size=E).astype(np.float64)
+    loss, grad = Lr.loss_grad_tc(params, feat, target, weight, round_bf16=False)
+    h = 1e-6
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        flat = params[name].ravel()
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            up = {k: v.copy() for k, v in params.items()}
+            dn = {k: v.copy() for k, v in params.items()}
+            up[name].ravel()[idx] += h
+            dn[name].ravel()[idx] -= h
+            num = (Lr.loss_grad_tc(up, feat, target, weight, False)[0] -
+                   Lr.loss_grad_tc(dn, feat, target, weight, False)[0]) / (2 * h)
+            assert abs(num - grad[name].ravel()[idx]) < 1e-6 * max(1.0, abs(num)), (name, idx)
+
+
+def test_bf16_rounding():
+    from oracle import learn as Lr
+    # exactly representable values stay; halfway cases go to even
+    vals = np.array([1.0, -2.5, 1.0 + 2**-7, 1.0 + 2**-8, 1.0 + 3 * 2**-8, 3.14159265], dtype=np.float32)
+    got = Lr.bf16(vals)
+    assert got[0] == 1.0 and got[1] == -2.5 and got[2] == 1.0 + 2**-7
+    assert got[3] == 1.0            # halfway between 1 and 1 + 2^-7: even
+    assert got[4] == 1.0 + 2**-6    # halfway between 1 + 2^-7 and 1 + 2^-6: even
+    assert abs(got[5] - 3.140625) < 1e-12
