@@ -46,9 +46,10 @@ def lib():
         L.orc_problem_free.argtypes = [C.c_void_p]
         L.orc_column.restype = C.c_int
         L.orc_column.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
-                                 C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+                                 C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_static.restype = C.c_int
-        L.orc_static.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p]
+        L.orc_static.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]
         L.orc_state_new.restype = C.c_void_p
         L.orc_state_new.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
                                     C.c_int64]
@@ -56,6 +57,12 @@ def lib():
         L.orc_init.restype = C.c_int
         L.orc_init.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]
+        L.orc_set_population_xy.restype = C.c_int
+        L.orc_set_population_xy.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64] + [C.c_void_p] * 4
+        L.orc_export_xy.restype = C.c_int
+        L.orc_export_xy.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 4
+        L.orc_next_value_xy.restype = C.c_int
+        L.orc_next_value_xy.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_void_p]
         L.orc_set_population.restype = C.c_int
         L.orc_set_population.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p,
                                          C.c_void_p, C.c_void_p]
@@ -134,29 +141,37 @@ class OracleProblem:
         if not self.handle:
             raise ValueError("oracle rejected the problem")
 
+    def _masks(self, lo, hi, k):
+        """uint64 masks for n <= 32, else Python ints (dx << n | dy, 2n bits)."""
+        if self.n <= 32:
+            return lo[:k].copy()
+        return np.array([(int(b) << 64) | int(a) for a, b in zip(lo[:k], hi[:k])], dtype=object)
+
     def column(self, x: int, y: int, t: float, dt_eff: float):
         """Quantised column of dt_eff * L(t) at |x><y|: (mask, qre, qim) sorted by mask,
         in units of 2^-52."""
         cap = 4096
         mask = np.zeros(cap, dtype=np.uint64)
+        mask_hi = np.zeros(cap, dtype=np.uint64)
         qre = np.zeros(cap, dtype=np.int64)
         qim = np.zeros(cap, dtype=np.int64)
-        n = lib().orc_column(self.handle, x, y, t, dt_eff, cap, mask.ctypes.data,
+        n = lib().orc_column(self.handle, x, y, t, dt_eff, cap, mask.ctypes.data, mask_hi.ctypes.data,
                              qre.ctypes.data, qim.ctypes.data)
         if n < 0:
             raise RuntimeError(f"orc_column failed: {n}")
-        return mask[:n].copy(), qre[:n].copy(), qim[:n].copy()
+        return self._masks(mask, mask_hi, n), qre[:n].copy(), qim[:n].copy()
 
     def static(self, t: float, dt_eff: float):
         """Static weights of dt_eff * L(t): (mask, weight) sorted by mask, in
         units of 2^-52 (a bound on |Re L| + |Im L| of that destination)."""
         cap = 4096
         mask = np.zeros(cap, dtype=np.uint64)
+        mask_hi = np.zeros(cap, dtype=np.uint64)
         w = np.zeros(cap, dtype=np.int64)
-        n = lib().orc_static(self.handle, t, dt_eff, cap, mask.ctypes.data, w.ctypes.data)
+        n = lib().orc_static(self.handle, t, dt_eff, cap, mask.ctypes.data, mask_hi.ctypes.data, w.ctypes.data)
         if n < 0:
             raise RuntimeError(f"orc_static failed: {n}")
-        return mask[:n].copy(), w[:n].copy()
+        return self._masks(mask, mask_hi, n), w[:n].copy()
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -196,6 +211,17 @@ class OracleSim:
                                       re.ctypes.data, im.ctypes.data)
         if rc != OK:
             raise RuntimeError(f"orc_set_population failed: {rc}")
+
+    def set_population_xy(self, seg: int, x, y, re, im, which: int = 0):
+        """Population of one vector from records |x><y| (any n)."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        y = np.ascontiguousarray(y, dtype=np.uint64)
+        re = np.ascontiguousarray(re, dtype=np.int32)
+        im = np.ascontiguousarray(im, dtype=np.int32)
+        rc = lib().orc_set_population_xy(self.handle, seg, which, len(x), x.ctypes.data, y.ctypes.data,
+                                         re.ctypes.data, im.ctypes.data)
+        if rc != OK:
+            raise RuntimeError(f"orc_set_population_xy failed: {rc}")
 
     def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
                   prev_valid: bool = False):
@@ -256,6 +282,26 @@ class OracleSim:
             lib().orc_export(self.handle, seg, which, keys.ctypes.data, re.ctypes.data,
                              im.ctypes.data)
         return keys, re, im
+
+    def population_xy(self, seg: int, which: int = 0):
+        """One vector's population as (x, y, re, im) in key order (any n)."""
+        cnt = lib().orc_count(self.handle, seg, which)
+        x = np.zeros(cnt, dtype=np.uint64)
+        y = np.zeros(cnt, dtype=np.uint64)
+        re = np.zeros(cnt, dtype=np.int32)
+        im = np.zeros(cnt, dtype=np.int32)
+        if cnt:
+            lib().orc_export_xy(self.handle, seg, which, x.ctypes.data, y.ctypes.data, re.ctypes.data,
+                                im.ctypes.data)
+        return x, y, re, im
+
+    def next_value_xy(self, seg: int, dt: float, x: int, y: int):
+        """next_value at the state |x><y| (any n)."""
+        out = np.zeros(2, dtype=np.int64)
+        rc = lib().orc_next_value_xy(self.handle, seg, dt, x, y, out.ctypes.data)
+        if rc != OK:
+            raise RuntimeError(f"orc_next_value_xy failed: {rc}")
+        return int(out[0]), int(out[1])
 
     def next_value(self, seg: int, dt: float, key: int):
         """(re, im) that the next step of size dt leaves at `key` of vector

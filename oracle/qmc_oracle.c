@@ -34,6 +34,8 @@
  *     first after a change of dt) is Euler.
  *   - Initialisation N(0) = N^diag rho(0) [walker averaging, Eq. (3)]:
  *     stochastic rounding of each component.
+ *   - Keys: the state |x><y| of n qubits (n <= 60) is the 2n-bit integer
+ *     (x << n) | y, held in 128 bits; populations are sorted by it.
  *   - Proposal spawning (not in the paper; the library's optional
  *     alternative to the exact |L|-weighted choice): a walker attempts with
  *     p_att = the sum over destinations of their static weights (each
@@ -67,6 +69,9 @@
 #define ORC_ERR_COEF_RANGE (-9)
 
 #define ONE_52 4503599627370496.0 /* 2^52 */
+#define MAX_QUBITS 60
+
+typedef unsigned __int128 okey;   /* (x << n) | y */
 #define P_LIMIT (((int64_t)1) << 52)
 
 /* ------------------------------------------------------------------------ */
@@ -143,7 +148,7 @@ void* orc_problem_new(int n,
                       const double* rc,
                       int nw, const double* wt0, const double* wt1)
 {
-    if (n < 1 || n > 32) return NULL;
+    if (n < 1 || n > MAX_QUBITS) return NULL;
     problem* p = (problem*)calloc(1, sizeof(problem));
     if (!p) return NULL;
     p->n = n; p->nh = nh; p->nl = nl; p->nr = nr; p->nw = nw;
@@ -244,10 +249,10 @@ static int quantise(double re, double im, cint* out)
 
 /* Column entries of dt_eff * L(t) for the source |x><y|: a small list of     */
 /* destinations keyed by mask = (dx << n) | dy, kept sorted by that key.      */
-typedef struct { uint64_t mask; cint v; } col_entry;
+typedef struct { okey mask; cint v; } col_entry;
 typedef struct { col_entry* e; int len, cap; } column;
 
-static int column_add(column* c, uint64_t mask, cint v)
+static int column_add(column* c, okey mask, cint v)
 {
     int lo = 0, hi = c->len;
     while (lo < hi) {
@@ -303,9 +308,9 @@ static int build_column(const problem* p, uint64_t x, uint64_t y, double t, doub
         uint64_t x2, y2;
         int kx, ky;
         pauli_on_ket(n, ht->xm, ht->zm, x, &x2, &kx);
-        if ((rc = column_add(col, ((x ^ x2) << n), times_ik(qk, kx))) != ORC_OK) return rc;
+        if ((rc = column_add(col, (okey)(x ^ x2) << n, times_ik(qk, kx))) != ORC_OK) return rc;
         pauli_on_ket(n, ht->xm, ht->zm, y, &y2, &ky);
-        if ((rc = column_add(col, (y ^ y2), times_ik(qb, 4 - ky))) != ORC_OK) return rc;
+        if ((rc = column_add(col, (okey)(y ^ y2), times_ik(qb, 4 - ky))) != ORC_OK) return rc;
     }
     for (int i = 0; i < p->nl; ++i) {
         const lind_op* lo = &p->lind[i];
@@ -326,17 +331,17 @@ static int build_column(const problem* p, uint64_t x, uint64_t y, double t, doub
                 /* jump: P_a |x><y| P_b */
                 pauli_on_ket(n, la->xm, la->zm, x, &xa, &ka);
                 pauli_on_ket(n, lb->xm, lb->zm, y, &yb, &kb);
-                if ((rc = column_add(col, ((x ^ xa) << n) | (y ^ yb),
+                if ((rc = column_add(col, ((okey)(x ^ xa) << n) | (y ^ yb),
                                      times_ik(qj, ka + 4 - kb))) != ORC_OK) return rc;
                 /* ket side: P_a P_b |x> */
                 pauli_on_ket(n, lb->xm, lb->zm, x, &u1, &k1);
                 pauli_on_ket(n, la->xm, la->zm, u1, &u2, &k2);
-                if ((rc = column_add(col, ((x ^ u2) << n), times_ik(qa, k1 + k2))) != ORC_OK)
+                if ((rc = column_add(col, (okey)(x ^ u2) << n, times_ik(qa, k1 + k2))) != ORC_OK)
                     return rc;
                 /* bra side: <y| P_a P_b = conj(P_b P_a |y>) */
                 pauli_on_ket(n, la->xm, la->zm, y, &v1, &j1);
                 pauli_on_ket(n, lb->xm, lb->zm, v1, &v2, &j2);
-                if ((rc = column_add(col, (y ^ v2), times_ik(qa, 8 - j1 - j2))) != ORC_OK)
+                if ((rc = column_add(col, (okey)(y ^ v2), times_ik(qa, 8 - j1 - j2))) != ORC_OK)
                     return rc;
             }
         }
@@ -363,8 +368,8 @@ static int build_static(const problem* p, double t, double dt_eff, column* col)
         if ((rc = quantise(0.0, -v, &qk)) != ORC_OK) return rc;
         if ((rc = quantise(0.0, v, &qb)) != ORC_OK) return rc;
         cint a = {llabs(qk.re) + llabs(qk.im), 0}, b = {llabs(qb.re) + llabs(qb.im), 0};
-        if ((rc = column_add(col, ht->xm << n, a)) != ORC_OK) return rc;
-        if ((rc = column_add(col, ht->xm, b)) != ORC_OK) return rc;
+        if ((rc = column_add(col, (okey)ht->xm << n, a)) != ORC_OK) return rc;
+        if ((rc = column_add(col, (okey)ht->xm, b)) != ORC_OK) return rc;
     }
     for (int i = 0; i < p->nl; ++i) {
         const lind_op* lo = &p->lind[i];
@@ -381,26 +386,28 @@ static int build_static(const problem* p, double t, double dt_eff, column* col)
                 if ((rc = quantise(s * zre, s * zim, &qj)) != ORC_OK) return rc;
                 if ((rc = quantise(hs * zre, -(hs * zim), &qa)) != ORC_OK) return rc;
                 cint aj = {llabs(qj.re) + llabs(qj.im), 0}, aa = {llabs(qa.re) + llabs(qa.im), 0};
-                if ((rc = column_add(col, (la->xm << n) | lb->xm, aj)) != ORC_OK) return rc;
-                if ((rc = column_add(col, (la->xm ^ lb->xm) << n, aa)) != ORC_OK) return rc;
-                if ((rc = column_add(col, la->xm ^ lb->xm, aa)) != ORC_OK) return rc;
+                if ((rc = column_add(col, ((okey)la->xm << n) | lb->xm, aj)) != ORC_OK) return rc;
+                if ((rc = column_add(col, (okey)(la->xm ^ lb->xm) << n, aa)) != ORC_OK) return rc;
+                if ((rc = column_add(col, (okey)(la->xm ^ lb->xm), aa)) != ORC_OK) return rc;
             }
         }
     }
     return ORC_OK;
 }
 
-/* Exported for tests: the quantised column, sorted by mask.  Returns the
- * number of entries (which may exceed cap; only cap are written) or < 0. */
+/* Exported for tests: the quantised column, sorted by mask (low 64 bits in
+ * mask, high 64 in mask_hi unless null).  Returns the number of entries
+ * (which may exceed cap; only cap are written) or < 0. */
 int orc_column(const void* pp, uint64_t x, uint64_t y, double t, double dt_eff, int cap,
-               uint64_t* mask, int64_t* qre, int64_t* qim)
+               uint64_t* mask, uint64_t* mask_hi, int64_t* qre, int64_t* qim)
 {
     const problem* p = (const problem*)pp;
     column col = {0, 0, 0};
     int rc = build_column(p, x, y, t, dt_eff, &col);
     if (rc != ORC_OK) { free(col.e); return rc; }
     for (int i = 0; i < col.len && i < cap; ++i) {
-        mask[i] = col.e[i].mask;
+        mask[i] = (uint64_t)col.e[i].mask;
+        if (mask_hi) mask_hi[i] = (uint64_t)(col.e[i].mask >> 64);
         qre[i] = col.e[i].v.re;
         qim[i] = col.e[i].v.im;
     }
@@ -411,14 +418,16 @@ int orc_column(const void* pp, uint64_t x, uint64_t y, double t, double dt_eff, 
 
 /* Exported for tests: the static weights (see build_static), sorted by
  * mask.  Returns the number of entries (only cap are written) or < 0. */
-int orc_static(const void* pp, double t, double dt_eff, int cap, uint64_t* mask, int64_t* weight)
+int orc_static(const void* pp, double t, double dt_eff, int cap, uint64_t* mask, uint64_t* mask_hi,
+               int64_t* weight)
 {
     const problem* p = (const problem*)pp;
     column col = {0, 0, 0};
     int rc = build_static(p, t, dt_eff, &col);
     if (rc != ORC_OK) { free(col.e); return rc; }
     for (int i = 0; i < col.len && i < cap; ++i) {
-        mask[i] = col.e[i].mask;
+        mask[i] = (uint64_t)col.e[i].mask;
+        if (mask_hi) mask_hi[i] = (uint64_t)(col.e[i].mask >> 64);
         weight[i] = col.e[i].v.re;
     }
     int len = col.len;
@@ -429,10 +438,10 @@ int orc_static(const void* pp, double t, double dt_eff, int cap, uint64_t* mask,
 /* ------------------------------------------------------------------------ */
 /* Populations                                                             */
 /* ------------------------------------------------------------------------ */
-typedef struct { uint64_t key; int32_t re, im; } rec;
+typedef struct { okey key; int32_t re, im; } rec;
 typedef struct { rec* r; int64_t len, cap; } pop;
 
-typedef struct { uint64_t key; int64_t re, im; int noninit; } spawn_rec;
+typedef struct { okey key; int64_t re, im; int noninit; } spawn_rec;
 typedef struct { spawn_rec* s; int64_t len, cap; } spawn_list;
 
 typedef struct {
@@ -513,10 +522,10 @@ static float mlp_logit(const state* s, const float* h2, int g)
 }
 
 /* Output index of a destination mask, or -1. */
-static int mlp_output(const state* s, uint64_t mask)
+static int mlp_output(const state* s, okey mask)
 {
     for (int g = 0; g < s->mlp_out; ++g)
-        if (s->out_mask[g] == mask) return g;
+        if ((okey)s->out_mask[g] == mask) return g;
     return -1;
 }
 
@@ -562,11 +571,11 @@ static void learned_weights(const state* s, const column* st, int64_t p_att, uin
 }
 
 /* Per-walker randomness of the learned proposal: two Philox calls. */
-static void learned_draws(uint64_t key, int phase, int comp, int64_t j, const uint32_t kd[2], uint32_t* V,
+static void learned_draws(okey key, int phase, int comp, int64_t j, const uint32_t kd[2], uint32_t* V,
                           double* ure, double* uim)
 {
     uint32_t a[4], b[4];
-    uint32_t ctr[4] = {(uint32_t)key, (uint32_t)(key >> 32),
+    uint32_t ctr[4] = {(uint32_t)key, (uint32_t)(key >> 32),   /* n <= 32: key < 2^64 */
                        (uint32_t)phase | ((uint32_t)comp << 1) | (KIND_LEARNED << 2),
                        (uint32_t)(((j >> 1) << 2) | ((j & 1) << 1))};
     orc_philox(ctr, kd, a);
@@ -589,7 +598,7 @@ static int pop_reserve(pop* p, int64_t cap)
     return ORC_OK;
 }
 
-static int spawn_push(spawn_list* l, uint64_t key, int64_t re, int64_t im, int noninit)
+static int spawn_push(spawn_list* l, okey key, int64_t re, int64_t im, int noninit)
 {
     if (l->len == l->cap) {
         int64_t nc = l->cap ? 2 * l->cap : 256;
@@ -635,19 +644,22 @@ void orc_state_free(void* sp)
     free(s);
 }
 
-static int cmp_u64(uint64_t a, uint64_t b) { return a < b ? -1 : (a > b ? 1 : 0); }
+static int cmp_key(okey a, okey b) { return a < b ? -1 : (a > b ? 1 : 0); }
 
 static int rec_cmp(const void* a, const void* b)
 {
-    return cmp_u64(((const rec*)a)->key, ((const rec*)b)->key);
+    return cmp_key(((const rec*)a)->key, ((const rec*)b)->key);
 }
 
 static int spawn_cmp(const void* a, const void* b)
 {
-    return cmp_u64(((const spawn_rec*)a)->key, ((const spawn_rec*)b)->key);
+    return cmp_key(((const spawn_rec*)a)->key, ((const spawn_rec*)b)->key);
 }
 
-/* N(0) := N^diag rho(0), each component stochastically rounded (reading R4). */
+/* N(0) := N^diag rho(0), each component stochastically rounded (reading R4).
+ * The rounding draw of a component is keyed by the state's key: its bits
+ * 0-63 in the first two counter words, 64-95 in the fourth, 96-119 in the
+ * top 24 bits of the third (all zero for n <= 32). */
 int orc_init(void* sp, int ne, const uint64_t* x, const uint64_t* y, const double* re,
              const double* im)
 {
@@ -661,14 +673,15 @@ int orc_init(void* sp, int ne, const uint64_t* x, const uint64_t* y, const doubl
         s->prev[seg].len = 0;
         if (pop_reserve(c, ne > 0 ? ne : 1) != ORC_OK) return ORC_ERR_OOM;
         for (int i = 0; i < ne; ++i) {
-            uint64_t key = (x[i] << n) | y[i];
+            const okey key = ((okey)x[i] << n) | y[i];
             int64_t v[2];
             for (int comp = 0; comp < 2; ++comp) {
                 double val = (double)s->n_diag * (comp == 0 ? re[i] : im[i]);
                 double fl = floor(val);
                 double fr = val - fl;
                 uint32_t ctr[4] = {(uint32_t)key, (uint32_t)(key >> 32),
-                                   ((uint32_t)comp << 1) | (KIND_INIT << 2), 0u};
+                                   ((uint32_t)comp << 1) | (KIND_INIT << 2) | ((uint32_t)(key >> 96) << 8),
+                                   (uint32_t)(key >> 64)};
                 uint32_t w[4];
                 orc_philox(ctr, kd, w);
                 uint64_t r = ((uint64_t)w[1] << 32) | w[0];
@@ -694,17 +707,22 @@ int orc_init(void* sp, int ne, const uint64_t* x, const uint64_t* y, const doubl
     return ORC_OK;
 }
 
-int orc_set_population(void* sp, int seg, int which, int64_t cnt, const uint64_t* keys,
-                       const int32_t* re, const int32_t* im)
+/* Population of vector seg (which 0: N(t), 1: N(t - dt)) from cnt records
+ * |x[i]><y[i]| with values (re[i], im[i]); zero records are dropped. */
+int orc_set_population_xy(void* sp, int seg, int which, int64_t cnt, const uint64_t* x, const uint64_t* y,
+                          const int32_t* re, const int32_t* im)
 {
     state* s = (state*)sp;
     if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    const int n = s->prob->n;
+    const uint64_t lim = (((uint64_t)1) << n) - 1;
     pop* p = which ? &s->prev[seg] : &s->cur[seg];
     if (pop_reserve(p, cnt > 0 ? cnt : 1) != ORC_OK) return ORC_ERR_OOM;
     p->len = 0;
     for (int64_t i = 0; i < cnt; ++i) {
+        if ((x[i] & ~lim) || (y[i] & ~lim)) return ORC_ERR_INVALID_ARG;
         if (re[i] == 0 && im[i] == 0) continue;
-        p->r[p->len].key = keys[i];
+        p->r[p->len].key = ((okey)x[i] << n) | y[i];
         p->r[p->len].re = re[i];
         p->r[p->len].im = im[i];
         p->len++;
@@ -713,6 +731,26 @@ int orc_set_population(void* sp, int seg, int which, int64_t cnt, const uint64_t
     for (int64_t i = 1; i < p->len; ++i)
         if (p->r[i].key == p->r[i - 1].key) return ORC_ERR_INVALID_ARG;
     return ORC_OK;
+}
+
+/* The same with whole keys (x << n) | y (n <= 32). */
+int orc_set_population(void* sp, int seg, int which, int64_t cnt, const uint64_t* keys,
+                       const int32_t* re, const int32_t* im)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg || s->prob->n > 32) return ORC_ERR_INVALID_ARG;
+    const int n = s->prob->n;
+    uint64_t* x = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(cnt > 0 ? cnt : 1));
+    uint64_t* y = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(cnt > 0 ? cnt : 1));
+    if (!x || !y) { free(x); free(y); return ORC_ERR_OOM; }
+    for (int64_t i = 0; i < cnt; ++i) {
+        x[i] = keys[i] >> n;
+        y[i] = keys[i] & ((((uint64_t)1) << n) - 1);
+    }
+    const int rc = orc_set_population_xy(sp, seg, which, cnt, x, y, re, im);
+    free(x);
+    free(y);
+    return rc;
 }
 
 /* Restrict orc_step to a subset of the vectors (each vector is independent,
@@ -802,8 +840,8 @@ static int spawn_parent(const state* s, const rec* par, int64_t rank, int phase,
 {
     const problem* p = s->prob;
     const int n = p->n;
-    uint64_t x = par->key >> n;
-    uint64_t y = par->key & ((((uint64_t)1) << n) - 1);
+    const uint64_t x = (uint64_t)(par->key >> n);
+    const uint64_t y = (uint64_t)par->key & ((((uint64_t)1) << n) - 1);
     int rc = build_column(p, x, y, t, dt_eff, col);
     if (rc != ORC_OK) return rc;
 
@@ -935,7 +973,7 @@ static int annihilate(const pop* cur, spawn_list* sp, pop* next)
     next->len = 0;
     int64_t i = 0, j = 0;
     while (i < cur->len || j < sp->len) {
-        uint64_t key;
+        okey key;
         if (j >= sp->len || (i < cur->len && cur->r[i].key <= sp->s[j].key)) key = cur->r[i].key;
         else key = sp->s[j].key;
         int occupied = (i < cur->len && cur->r[i].key == key);
@@ -1019,7 +1057,7 @@ int orc_step(void* sp, double dt, int nsteps)
     return rc;
 }
 
-static void value_at_key(const pop* p, uint64_t key, int64_t* re, int64_t* im);
+static void value_at_key(const pop* p, okey key, int64_t* re, int64_t* im);
 
 /*
  * The value N(t + dt) of vector seg at one key after the next step of size dt
@@ -1031,10 +1069,11 @@ static void value_at_key(const pop* p, uint64_t key, int64_t* re, int64_t* im);
  * with N(t)'s value there under the initiator rule.  For checking sampled
  * outputs of a large step one key at a time.  out = (re, im).
  */
-int orc_next_value(void* sp, int seg, double dt, uint64_t key, int64_t out[2])
+int orc_next_value_xy(void* sp, int seg, double dt, uint64_t x, uint64_t y, int64_t out[2])
 {
     state* s = (state*)sp;
     if (seg < 0 || seg >= s->nseg || !(dt > 0.0)) return ORC_ERR_INVALID_ARG;
+    const okey key = ((okey)x << s->prob->n) | y;
     const double t = s->t;
     const int ab2 = (s->integrator == 1 && s->prev_valid && s->dt_last == dt);
     const double dt_cur = ab2 ? dt * 1.5 : dt;
@@ -1056,7 +1095,7 @@ int orc_next_value(void* sp, int seg, double dt, uint64_t key, int64_t out[2])
         const pop* src = phase ? &s->prev[seg] : cur;
         const column* masks = phase ? &m_prev : &m_cur;
         for (int e = 0; e < masks->len && rc == ORC_OK; ++e) {
-            const uint64_t pk = key ^ masks->e[e].mask;
+            const okey pk = key ^ masks->e[e].mask;
             /* the parent's rank: its index in the sorted population */
             int64_t lo = 0, hi = src->len;
             while (lo < hi) {
@@ -1086,12 +1125,21 @@ int orc_next_value(void* sp, int seg, double dt, uint64_t key, int64_t out[2])
     return rc;
 }
 
+/* orc_next_value_xy at the key (x << n) | y given whole (n <= 32). */
+int orc_next_value(void* sp, int seg, double dt, uint64_t key, int64_t out[2])
+{
+    state* s = (state*)sp;
+    const int n = s->prob->n;
+    if (n > 32) return ORC_ERR_INVALID_ARG;
+    return orc_next_value_xy(sp, seg, dt, key >> n, key & ((((uint64_t)1) << n) - 1), out);
+}
+
 /* Spawn choice of the following steps: 0 exact |L|-weighted (the paper's),
  * 1 static-weight proposal (see the header). */
 int orc_set_proposal(void* sp, int kind)
 {
     state* s = (state*)sp;
-    if (kind < 0 || kind > 2 || (kind == 2 && !s->w1)) return ORC_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 2 || (kind == 2 && (!s->w1 || s->prob->n > 32))) return ORC_ERR_INVALID_ARG;
     s->proposal = kind;
     return ORC_OK;
 }
@@ -1103,7 +1151,7 @@ int orc_set_mlp(void* sp, int n_in, int n_hidden, int n_out, const uint64_t* out
                 const float* b1, const float* w2, const float* b2, const float* w3, const float* b3, float eps)
 {
     state* s = (state*)sp;
-    if (n_in != 2 * s->prob->n + 1 || n_hidden < 1 || n_hidden > 64 || n_out < 1 || !(eps > 0.0f) || eps > 1.0f)
+    if (s->prob->n > 32 || n_in != 2 * s->prob->n + 1 || n_hidden < 1 || n_hidden > 64 || n_out < 1 || !(eps > 0.0f) || eps > 1.0f)
         return ORC_ERR_INVALID_ARG;
     s->mlp_in = n_in;
     s->mlp_hidden = n_hidden;
@@ -1138,14 +1186,14 @@ void orc_zsum(void* sp, int seg, int64_t* out)
     const uint64_t ymask = (((uint64_t)1) << n) - 1;
     for (int q = 0; q < n; ++q) out[q] = 0;
     for (int64_t i = 0; i < p->len; ++i) {
-        const uint64_t x = p->r[i].key >> n, y = p->r[i].key & ymask;
+        const uint64_t x = (uint64_t)(p->r[i].key >> n), y = (uint64_t)p->r[i].key & ymask;
         if (x != y) continue;
         for (int q = 0; q < n; ++q) out[q] += ((x >> q) & 1u) ? -(int64_t)p->r[i].re : (int64_t)p->r[i].re;
     }
 }
 
 /* Value of vector seg's N(t) at key (0 when unoccupied). */
-static void value_at_key(const pop* p, uint64_t key, int64_t* re, int64_t* im)
+static void value_at_key(const pop* p, okey key, int64_t* re, int64_t* im)
 {
     int64_t lo = 0, hi = p->len;
     while (lo < hi) {
@@ -1174,9 +1222,9 @@ void orc_antiherm(void* sp, int seg, uint64_t out[2])
     const uint64_t ymask = (((uint64_t)1) << n) - 1;
     unsigned __int128 acc = 0;
     for (int64_t i = 0; i < p->len; ++i) {
-        const uint64_t x = p->r[i].key >> n, y = p->r[i].key & ymask;
+        const uint64_t x = (uint64_t)(p->r[i].key >> n), y = (uint64_t)p->r[i].key & ymask;
         int64_t tre, tim;
-        value_at_key(p, (y << n) | x, &tre, &tim);
+        value_at_key(p, ((okey)y << n) | x, &tre, &tim);
         const int64_t dre = (int64_t)p->r[i].re - tre, dim = (int64_t)p->r[i].im + tim;
         acc += (unsigned __int128)((__int128)dre * dre) + (unsigned __int128)((__int128)dim * dim);
         if (tre == 0 && tim == 0) {
@@ -1204,8 +1252,8 @@ void orc_antiherm_sum(void* sp, const int32_t* segs, int count, uint64_t out[2])
     for (int a = 0; a < count; ++a) {
         const pop* p = &s->cur[segs[a]];
         for (int64_t i = 0; i < p->len; ++i) {
-            const uint64_t key = p->r[i].key;
-            const uint64_t tkey = ((key & ymask) << n) | (key >> n);
+            const okey key = p->r[i].key;
+            const okey tkey = ((key & ymask) << n) | (key >> n);
             /* visit each entry once: (x, y) from the first listed vector that holds it, and
              * (y, x) from there too when no listed vector holds (y, x) */
             int first = 1;
@@ -1255,7 +1303,7 @@ int orc_learned_q(void* sp, double t, double dt_eff, uint64_t x, uint64_t y, int
                   int64_t* Q, int64_t* p_att)
 {
     state* s = (state*)sp;
-    if (!s->w1) return ORC_ERR_INVALID_ARG;
+    if (!s->w1 || s->prob->n > 32) return ORC_ERR_INVALID_ARG;
     column st = {0, 0, 0};
     int rc = build_static(s->prob, t, dt_eff, &st);
     if (rc != ORC_OK) { free(st.e); return rc; }
@@ -1265,7 +1313,7 @@ int orc_learned_q(void* sp, double t, double dt_eff, uint64_t x, uint64_t y, int
     int64_t Qw[256];
     learned_weights(s, &st, P, x, y, t, Qw);
     for (int e = 0; e < st.len; ++e) {
-        mask[e] = st.e[e].mask;
+        mask[e] = (uint64_t)st.e[e].mask;
         Q[e] = Qw[e];
     }
     *p_att = P;
@@ -1284,10 +1332,26 @@ int64_t orc_count(void* sp, int seg, int which)
 int orc_export(void* sp, int seg, int which, uint64_t* keys, int32_t* re, int32_t* im)
 {
     state* s = (state*)sp;
-    if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    if (seg < 0 || seg >= s->nseg || s->prob->n > 32) return ORC_ERR_INVALID_ARG;
     const pop* p = which ? &s->prev[seg] : &s->cur[seg];
     for (int64_t i = 0; i < p->len; ++i) {
-        keys[i] = p->r[i].key;
+        keys[i] = (uint64_t)p->r[i].key;
+        re[i] = p->r[i].re;
+        im[i] = p->r[i].im;
+    }
+    return ORC_OK;
+}
+
+/* The population as bit strings: record i is |x[i]><y[i]| (any n). */
+int orc_export_xy(void* sp, int seg, int which, uint64_t* x, uint64_t* y, int32_t* re, int32_t* im)
+{
+    state* s = (state*)sp;
+    if (seg < 0 || seg >= s->nseg) return ORC_ERR_INVALID_ARG;
+    const int n = s->prob->n;
+    const pop* p = which ? &s->prev[seg] : &s->cur[seg];
+    for (int64_t i = 0; i < p->len; ++i) {
+        x[i] = (uint64_t)(p->r[i].key >> n);
+        y[i] = (uint64_t)p->r[i].key & ((((uint64_t)1) << n) - 1);
         re[i] = p->r[i].re;
         im[i] = p->r[i].im;
     }
@@ -1301,10 +1365,10 @@ void orc_stats(void* sp, int seg, int64_t out[4])
     const int n = s->prob->n;
     const pop* p = &s->cur[seg];
     int64_t ntot = 0, dre = 0, dim = 0;
-    uint64_t ymask = (((uint64_t)1) << n) - 1;
+    const uint64_t ymask = (((uint64_t)1) << n) - 1;
     for (int64_t i = 0; i < p->len; ++i) {
         ntot += llabs((int64_t)p->r[i].re) + llabs((int64_t)p->r[i].im);
-        if ((p->r[i].key >> n) == (p->r[i].key & ymask)) {
+        if ((uint64_t)(p->r[i].key >> n) == ((uint64_t)p->r[i].key & ymask)) {
             dre += p->r[i].re;
             dim += p->r[i].im;
         }
