@@ -18,9 +18,14 @@
  *     one context.
  *   - Pointers marked "host" are caller-owned host memory, borrowed for the
  *     duration of the call only.  Pointers marked "device" are device memory
- *     on the context's GPU.  The library owns all memory it allocates.
+ *     on the context's GPU.  The library owns all memory it allocates; it
+ *     takes it from qmc_config.alloc / free when given, else from a
+ *     stream-ordered memory pool of the context.
  *   - Keys: qubit q is bit q of a basis index; rho_xy lives at the packed key
- *     (x << n) | y, n = number of qubits (1 <= n <= 32).
+ *     (x << n) | y, n = number of qubits (1 <= n <= 60).  Up to 32 qubits a
+ *     key is one uint64_t and the calls that take or return keys use it; from
+ *     33 qubits on a key has 2n > 64 bits and a state is given as its bit
+ *     strings x and y (qmc_init_populations, qmc_export_xy, qmc_overlap_all).
  *   - Pauli strings are bit-mask pairs (xm, zm): I (0,0), X (1,0), Z (0,1),
  *     Hermitian Y (1,1) per qubit.
  *   - Work is issued on the stream given in qmc_config.cuda_stream (0 = the
@@ -51,6 +56,8 @@ extern "C" {
 #define QMC_ERR_IO (-10)            /* checkpoint file could not be read/written*/
 #define QMC_ERR_CHECKPOINT (-11)    /* checkpoint corrupt or from another setup */
 
+#define QMC_MAX_QUBITS 60
+
 #define QMC_EULER 0
 #define QMC_AB2 1
 
@@ -59,11 +66,20 @@ extern "C" {
 
 typedef struct qmc_ctx qmc_ctx;
 
+/* Device allocator supplied by the caller (e.g. a framework's caching
+ * allocator).  alloc returns bytes of device memory usable in stream order
+ * on cuda_stream (the context's own work stream), or null when out of
+ * memory; free returns such a block, in stream order on the same stream.
+ * user is passed through unchanged. */
+typedef void* (*qmc_alloc_fn)(uint64_t bytes, void* cuda_stream, void* user);
+typedef void (*qmc_free_fn)(void* ptr, void* cuda_stream, void* user);
+
 /* Run configuration.  n_segments independent population vectors ("samples",
  * Eq. (3)) share one problem; each draws its own counter-based random stream
  * keyed by (seed, step, segment, key, walker). */
 typedef struct {
-    int32_t n_qubits;      /* 1..32                                              */
+    int32_t n_qubits;      /* 1..QMC_MAX_QUBITS (above 32: 128-bit keys, exact
+                              spawn choice only, no batch)                     */
     int32_t n_segments;    /* number of independent vectors, >= 1                */
     int32_t integrator;    /* QMC_EULER or QMC_AB2 (AB2 starts with one Euler)   */
     int32_t max_ctas;      /* cap on the CTAs of each persistent or grid-stride
@@ -75,6 +91,12 @@ typedef struct {
     int64_t capacity_hint; /* initial records per population buffer (0 = auto)   */
     int64_t max_records;   /* hard cap for automatic growth (0 = no cap)         */
     void* cuda_stream;     /* cudaStream_t to issue work on                     */
+    qmc_alloc_fn alloc;    /* device memory: null (with free null) = a pool of
+                              the context's own, cudaMallocFromPoolAsync /
+                              cudaFreeAsync in stream order on its work stream,
+                              so growing a buffer never synchronises the device */
+    qmc_free_fn free;      /* set together with alloc                           */
+    void* alloc_user;      /* passed to alloc and free                          */
 } qmc_config;
 
 /* One term h * rate(t) * window(t) * P of H(t) [Eq. (1)]. */
@@ -114,8 +136,13 @@ typedef struct {
 /* ---- lifecycle --------------------------------------------------------- */
 
 /* Create a context on the current CUDA device.  *out is set only on success.
- * Errors: INVALID_ARG (n_qubits outside 1..32, n_segments < 1, n_diag < 1),
- * OOM, CUDA. */
+ * With n_qubits > 32 the context steps 128-bit keys (records of 24 bytes)
+ * with the same method and random stream; of the calls below it supports
+ * load_schedule, init_populations, step, observables, step_history,
+ * counters, memory, export_xy and overlap_all, and the exact spawn choice
+ * (the others return INVALID_ARG or STATE).
+ * Errors: INVALID_ARG (n_qubits outside 1..QMC_MAX_QUBITS, n_segments < 1,
+ * n_diag < 1), OOM, CUDA. */
 int qmc_create(qmc_ctx** out, const qmc_config* cfg);
 
 /* One problem instance of a batch: its own qubit count, population vectors,
@@ -149,7 +176,7 @@ typedef struct {
  * qmc_create with the same seed (its index inside the instance keys the
  * stream), so each instance's populations are bit-identical to such a run.
  * All instances share dt, the clock and integrator, capacity_hint,
- * max_records, max_ctas and cuda_stream from cfg (cfg's n_qubits,
+ * max_records, max_ctas, cuda_stream and the allocator from cfg (cfg's n_qubits,
  * n_segments, seed, n_diag and initiator_min are ignored).
  * qmc_init_populations gives every instance the same rho(0) (its (x, y)
  * must fit the smallest instance); qmc_load_schedule is refused (STATE).
@@ -399,11 +426,22 @@ int qmc_spawn_prob_bound(const qmc_ctx* ctx, double t, double dt, double* p_boun
  * copies keep their fixed limit.  Errors: INVALID_ARG (above 2^30). */
 int qmc_set_spin_limit(qmc_ctx* ctx, uint32_t polls);
 
+/* Device memory the context holds (host out[2]): out[0] bytes, out[1]
+ * blocks, whether from qmc_config.alloc or the context's pool. */
+int qmc_memory(const qmc_ctx* ctx, int64_t* out);
+
 /* ---- results --------------------------------------------------------------- */
 
 /* Per-vector observables of N(t) into obs[0 .. n_segments) (host).
  * Synchronises the stream. */
 int qmc_observables(qmc_ctx* ctx, qmc_obs* obs);
+
+/* Records of one vector (which 0: N(t), 1: N(t - dt)) as bit strings, in key
+ * order: record i is (re[i] + i im[i]) |x[i]><y[i]| (host arrays of cap
+ * entries; *count receives the vector's record count, of which min(cap,
+ * count) are written).  Any n.  Errors: INVALID_ARG. */
+int qmc_export_xy(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* x, uint64_t* y, int32_t* re, int32_t* im,
+                  int64_t cap, int64_t* count);
 
 /* Per-step observables of the last qmc_step call: host array of
  * nsteps * n_segments entries, step-major.  *count receives the number of
@@ -530,8 +568,8 @@ int qmc_observables_noalloc(const void* records, const int64_t* seg_offsets, int
 int qmc_column_eval(int32_t n_qubits, const qmc_ham_term* ham, int32_t n_ham, const qmc_lindblad* lind,
                     int32_t n_lind, const qmc_pauli_coef* coefs, int32_t n_coefs, const qmc_rate* rates,
                     int32_t n_rates, const qmc_window* windows, int32_t n_windows, double t, double dt_eff,
-                    uint64_t x, uint64_t y, int32_t cap, uint64_t* mask, int64_t* vre, int64_t* vim,
-                    int64_t* p_out);
+                    uint64_t x, uint64_t y, int32_t cap, uint64_t* mask, uint64_t* mask_hi, int64_t* vre,
+                    int64_t* vim, int64_t* p_out);
 
 #ifdef __cplusplus
 }

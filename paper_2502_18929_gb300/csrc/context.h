@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/qmc.h"
@@ -25,6 +26,9 @@ struct qmc_ctx {
     cudaStream_t user_stream = nullptr;
     cudaStream_t work = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaMemPool_t pool = nullptr;                   // stream-ordered device memory (no alloc callback)
+    std::unordered_map<void*, size_t> blocks;       // device blocks held, with their sizes
+    int64_t held_bytes = 0;
     int device = 0;
     int sm_count = 0;
     int grid = 0;
@@ -106,6 +110,24 @@ struct qmc_ctx {
     bool prev_valid = false;
     int64_t last_call_steps = 0;
     int64_t acc_redo = 0;   // step launches repeated after a buffer grew (qmc_counters out[10])
+
+    // 33..60 qubits: 128-bit keys; d_pop holds WRec records and the step is
+    // the wide kernels' (wide.cu)
+    bool wide = false;
+    qmc::WSpawn* d_wspawn = nullptr;
+    qmc::WSpawn* d_wspawn_alt = nullptr;
+    qmc::WRun* d_wrun = nullptr;
+    int32_t* d_wflag_u = nullptr;
+    int64_t* d_wscan_u = nullptr;
+    qmc::WAux* d_waux = nullptr;
+    int32_t* d_wflag_a = nullptr;
+    int64_t* d_wscan_a = nullptr;
+    int64_t* d_wpart = nullptr;
+    int64_t wpart_cap = 0;
+    uint32_t* d_whist = nullptr;
+    uint32_t* d_wtile = nullptr;
+    int64_t wtiles_cap = 0;
+    uint32_t* d_wplan = nullptr;
 
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;

@@ -162,6 +162,59 @@ void launch_mlp_tc_pack(const float* params, const TcLayout& L, uint8_t* out, cu
 // Launchers (kernels.cu).  All take their sizes from DevState, so the same
 // launch sequence can be captured once in a CUDA graph and replayed.
 constexpr int kNumTimedKernels = 15;
+// ---- the step for 33..60 qubits (128-bit keys, wide.cu) ----------------------
+constexpr int kWMaxPasses = 20;      // 8-bit digits of (vector, key): up to 2 * 60 + 28 bits
+constexpr int kWTile = 4096;         // records per tile of the radix sort's scatter
+constexpr int kWChunk = 1024;        // extra draw calls (four walkers each) per heavy work item
+constexpr int kWLight = 64;          // parents with more walkers take the heavy path
+constexpr int kWScanTile = 2048;     // flags per tile of the survivors' prefix sums
+
+// Run of equal (vector, key) in the sorted spawns, at its first record: the
+// position of the key in N(t) (posA, a global index), whether N(t) holds it,
+// and the sum of the spawns that survive the initiator rule (all of them
+// when N(t) holds the key, the initiators' alone otherwise).
+struct WRun {
+    int64_t posA;
+    int64_t re, im;
+    int32_t matched, pad;
+};
+
+// Per record of N(t): the first sorted spawn at or after its key (lbS) and
+// its value after annihilation.
+struct WAux {
+    int64_t lbS;
+    int32_t re, im;
+};
+
+struct WideParams {
+    WSpawn* spawn;          // unsorted spawns (sort ping-pong A)
+    WSpawn* spawn_alt;      // sort ping-pong B
+    WRun* run;              // [spawn_cap]
+    int32_t* flag_u;        // [spawn_cap]: run head whose key is new to N(t + dt)
+    int64_t* scan_u;        // [spawn_cap + 1]
+    WAux* aux;              // [pop_cap]
+    int32_t* flag_a;        // [pop_cap]: record of N(t) that survives
+    int64_t* scan_a;        // [pop_cap + 1]
+    int64_t* part;          // scan partials
+    int64_t part_cap;
+    uint32_t* hist;         // [kWMaxPasses][256] digit counts, then digit starts
+    uint32_t* tile_hist;    // [tiles][256]
+    int64_t tiles_cap;
+    uint32_t* plan;         // [kWMaxPasses + 1]: per pass bit 0 skip, bit 1 source is spawn_alt; last: final buffer
+    int passes;             // ceil((2n + vector bits) / 8)
+};
+
+void configure_wide_kernels();   // once per process, before the first capture of a wide step
+void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t stream);
+int wide_step_launch_count(const StepParams& P, const WideParams& W);
+void launch_wide_init(const StepParams& P, const uint64_t* xs, const uint64_t* ys, const double* re,
+                      const double* im, int64_t nnz, int64_t* vals, cudaStream_t stream);
+void launch_wide_obs(const StepParams& P, int which, SegStats* out, cudaStream_t stream);
+void launch_wide_lookup(const StepParams& P, int seg, const uint64_t* qx, const uint64_t* qy, int nq, int64_t* out,
+                        cudaStream_t stream);
+void launch_wide_export(const StepParams& P, int slot, int64_t first, int64_t count, uint64_t* x, uint64_t* y,
+                        int32_t* re, int32_t* im, cudaStream_t stream);
+
 void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);

@@ -45,22 +45,69 @@ int fail(qmc_ctx* c, int code, const std::string& why)
             return fail(ctx, QMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Device memory of the context: from the caller's allocator when one was
+// given, else from the context's pool, both in stream order on the work
+// stream (no device-wide synchronisation when a buffer grows).
+void* mem_alloc(qmc_ctx* ctx, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (ctx->cfg.alloc) {
+        p = ctx->cfg.alloc((uint64_t)bytes, (void*)ctx->work, ctx->cfg.alloc_user);
+    } else if (cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->work) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        ctx->blocks[p] = bytes;
+        ctx->held_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void mem_free(qmc_ctx* ctx, void* p)
+{
+    if (!p) return;
+    auto it = ctx->blocks.find(p);
+    if (it == ctx->blocks.end()) return;   // not ours
+    ctx->held_bytes -= (int64_t)it->second;
+    ctx->blocks.erase(it);
+    if (ctx->cfg.alloc)
+        ctx->cfg.free(p, (void*)ctx->work, ctx->cfg.alloc_user);
+    else
+        cudaFreeAsync(p, ctx->work);
+}
+
 template <typename T>
 int dalloc(qmc_ctx* ctx, T** p, int64_t count)
 {
-    if (*p) {
-        cudaFree(*p);
-        *p = nullptr;
-    }
+    mem_free(ctx, *p);
+    *p = nullptr;
     if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(ctx, QMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    }
+    *p = (T*)mem_alloc(ctx, (size_t)count * sizeof(T));
+    if (!*p) return fail(ctx, QMC_ERR_OOM, "device allocation of " + std::to_string((size_t)count * sizeof(T)) + " bytes failed");
     return QMC_OK;
 }
+
+// Temporary device buffers of one call, returned in stream order when the
+// call ends, on its error paths too.
+struct Scratch {
+    qmc_ctx* ctx;
+    std::vector<void*> held;
+    explicit Scratch(qmc_ctx* c) : ctx(c) {}
+    ~Scratch()
+    {
+        for (void* p : held) mem_free(ctx, p);
+    }
+    template <typename T>
+    int get(T** p, int64_t count)
+    {
+        *p = (T*)mem_alloc(ctx, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+        if (!*p) return fail(ctx, QMC_ERR_OOM, "no device memory for a temporary buffer");
+        held.push_back(*p);
+        return QMC_OK;
+    }
+};
 
 int seg_bits_of(int nseg)
 {
@@ -185,6 +232,28 @@ StepParams params(qmc_ctx* c)
     return P;
 }
 
+WideParams wparams(qmc_ctx* c)
+{
+    WideParams W;
+    std::memset(&W, 0, sizeof(W));
+    W.spawn = c->d_wspawn;
+    W.spawn_alt = c->d_wspawn_alt;
+    W.run = c->d_wrun;
+    W.flag_u = c->d_wflag_u;
+    W.scan_u = c->d_wscan_u;
+    W.aux = c->d_waux;
+    W.flag_a = c->d_wflag_a;
+    W.scan_a = c->d_wscan_a;
+    W.part = c->d_wpart;
+    W.part_cap = c->wpart_cap;
+    W.hist = c->d_whist;
+    W.tile_hist = c->d_wtile;
+    W.tiles_cap = c->wtiles_cap;
+    W.plan = c->d_wplan;
+    W.passes = (2 * c->cfg.n_qubits + seg_bits_of(c->cfg.n_segments) + 7) / 8;
+    return W;
+}
+
 // Make the work stream wait for the caller's stream (and vice versa at exit).
 int enter(qmc_ctx* ctx)
 {
@@ -218,12 +287,35 @@ int note_launches(qmc_ctx* ctx, int64_t n)
     return QMC_OK;
 }
 
+// Prefix-sum partials of the wide step: one per kWScanTile records or spawns.
+int grow_wpart(qmc_ctx* ctx)
+{
+    const int64_t cap = std::max(ctx->pop_cap, ctx->spawn_cap) / kWScanTile + 2;
+    if (cap <= ctx->wpart_cap) return QMC_OK;
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->d_wpart, cap)) != QMC_OK) return rc;
+    ctx->wpart_cap = cap;
+    ctx->graph_dirty = true;
+    return QMC_OK;
+}
+
 int grow_spawn(qmc_ctx* ctx, int64_t need)
 {
     int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
     if (cap > kLookbackValueLimit) cap = kLookbackValueLimit;
     if (need > cap) return fail(ctx, QMC_ERR_CAPACITY, "spawn records exceed 2^31 - 1 per step");
     int rc;
+    if (ctx->wide) {
+        if ((rc = dalloc(ctx, &ctx->d_wspawn, cap)) != QMC_OK || (rc = dalloc(ctx, &ctx->d_wspawn_alt, cap)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wrun, cap)) != QMC_OK || (rc = dalloc(ctx, &ctx->d_wflag_u, cap)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wscan_u, cap + 1)) != QMC_OK)
+            return rc;
+        ctx->wtiles_cap = (cap + kWTile - 1) / kWTile + 1;
+        if ((rc = dalloc(ctx, &ctx->d_wtile, ctx->wtiles_cap * 256)) != QMC_OK) return rc;
+        ctx->spawn_cap = cap;
+        ctx->graph_dirty = true;
+        return grow_wpart(ctx);
+    }
     if ((rc = dalloc(ctx, &ctx->d_spawn, cap)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn_alt, cap)) != QMC_OK) return rc;
     // sort windows: one per 224 spawn records (the bucket sort's window length)
@@ -239,6 +331,7 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
 
 int grow_cand(qmc_ctx* ctx, int64_t need)
 {
+    if (ctx->wide) return QMC_OK;   // the wide step has no candidate list
     const int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
     int rc;
     if ((rc = dalloc(ctx, &ctx->d_cand, cap)) != QMC_OK) return rc;
@@ -249,6 +342,7 @@ int grow_cand(qmc_ctx* ctx, int64_t need)
 
 int grow_merge_tiles(qmc_ctx* ctx)
 {
+    if (ctx->wide) return QMC_OK;   // nor merge tiles
     const int64_t cap = (ctx->pop_cap + ctx->spawn_cap) / kMergeTile + ctx->cfg.n_segments + 2;
     if (cap <= ctx->merge_tiles_cap) return QMC_OK;
     int rc;
@@ -272,22 +366,25 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
     DevState hs;
     CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
+    const size_t rec_bytes = ctx->wide ? sizeof(WRec) : sizeof(Rec);
     for (int i = 0; i < 3; ++i) {
-        Rec* np = nullptr;
-        cudaError_t e = cudaMalloc((void**)&np, (size_t)cap * sizeof(Rec));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, QMC_ERR_OOM, "population buffer allocation failed");
-        }
+        Rec* np = (Rec*)mem_alloc(ctx, (size_t)cap * rec_bytes);
+        if (!np) return fail(ctx, QMC_ERR_OOM, "population buffer allocation failed");
         const int64_t keep = std::min<int64_t>(hs.count[i], std::min(ctx->pop_cap, cap));
         if (ctx->d_pop[i] && keep > 0)
-            CK(cudaMemcpyAsync(np, ctx->d_pop[i], (size_t)keep * sizeof(Rec), cudaMemcpyDeviceToDevice, ctx->work));
-        CK(cudaStreamSynchronize(ctx->work));
-        if (ctx->d_pop[i]) cudaFree(ctx->d_pop[i]);
+            CK(cudaMemcpyAsync(np, ctx->d_pop[i], (size_t)keep * rec_bytes, cudaMemcpyDeviceToDevice, ctx->work));
+        mem_free(ctx, ctx->d_pop[i]);   // in stream order, after the copy
         ctx->d_pop[i] = np;
     }
     ctx->pop_cap = cap;
     ctx->graph_dirty = true;
+    if (ctx->wide) {
+        int rc;
+        if ((rc = dalloc(ctx, &ctx->d_waux, cap)) != QMC_OK || (rc = dalloc(ctx, &ctx->d_wflag_a, cap)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wscan_a, cap + 1)) != QMC_OK)
+            return rc;
+        return grow_wpart(ctx);
+    }
     return grow_merge_tiles(ctx);
 }
 
@@ -327,7 +424,10 @@ int capture_graph(qmc_ctx* ctx)
     StepParams P = params(ctx);
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
-    launch_step(P, ctx->grid, ctx->work);
+    if (ctx->wide)
+        launch_wide_step(P, wparams(ctx), ctx->work);
+    else
+        launch_step(P, ctx->grid, ctx->work);
     CK(cudaStreamEndCapture(ctx->work, &g));
     cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
@@ -373,6 +473,7 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     ctx->cfg = *cfg;
     ctx->inst = std::move(inst);
     ctx->batch = batch;
+    ctx->wide = cfg->n_qubits > 32;
     ctx->user_stream = (cudaStream_t)cfg->cuda_stream;
     int rc = QMC_OK;
     auto bail = [&](int code) { qmc_destroy(ctx); return code; };
@@ -380,15 +481,27 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     ctx->grid = cfg->max_ctas > 0 ? cfg->max_ctas : 0;   // 0: each kernel fills the GPU
     configure_kernels();
+    configure_wide_kernels();
     if (cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) != cudaSuccess) return bail(QMC_ERR_CUDA);
     if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return bail(QMC_ERR_INVALID_ARG);
+    if (!cfg->alloc) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) return bail(QMC_ERR_CUDA);
+        uint64_t keep_all = ~0ull;   // freed blocks stay in the pool for the next growth
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+    }
     const int nseg = cfg->n_segments;
     if ((rc = dalloc(ctx, &ctx->d_state, 1)) != QMC_OK) return bail(rc);
-    if (cudaMemset(ctx->d_state, 0, sizeof(DevState)) != cudaSuccess) return bail(QMC_ERR_CUDA);
+    if (cudaMemsetAsync(ctx->d_state, 0, sizeof(DevState), ctx->work) != cudaSuccess) return bail(QMC_ERR_CUDA);
     for (int i = 0; i < 3; ++i) {
         if ((rc = dalloc(ctx, &ctx->d_segoff[i], nseg + 1)) != QMC_OK) return bail(rc);
         if ((rc = dalloc(ctx, &ctx->d_gofs[i], nseg + 1)) != QMC_OK) return bail(rc);
-        if (cudaMemset(ctx->d_segoff[i], 0, (size_t)(nseg + 1) * 8) != cudaSuccess) return bail(QMC_ERR_CUDA);
+        if (cudaMemsetAsync(ctx->d_segoff[i], 0, (size_t)(nseg + 1) * 8, ctx->work) != cudaSuccess)
+            return bail(QMC_ERR_CUDA);
     }
     if ((rc = dalloc(ctx, &ctx->d_kd, nseg)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_bucket, (int64_t)1 << kBucketBits)) != QMC_OK) return bail(rc);
@@ -403,6 +516,9 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     if ((rc = dalloc(ctx, &ctx->d_obs, nseg)) != QMC_OK) return bail(rc);
     ctx->heavy_cap = 4096;
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
+    if (ctx->wide && ((rc = dalloc(ctx, &ctx->d_whist, kWMaxPasses * 256)) != QMC_OK ||
+                      (rc = dalloc(ctx, &ctx->d_wplan, kWMaxPasses + 1)) != QMC_OK))
+        return bail(rc);
     const int64_t hint = cfg->capacity_hint > 0 ? cfg->capacity_hint : (int64_t)1 << 16;
     if ((rc = grow_spawn(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
     if ((rc = grow_cand(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
@@ -418,8 +534,11 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
         }
         if ((rc = dalloc(ctx, &ctx->d_seginfo, nseg)) != QMC_OK) return bail(rc);
         if ((rc = dalloc(ctx, &ctx->d_inst, (int64_t)ii.size())) != QMC_OK) return bail(rc);
-        if (cudaMemcpy(ctx->d_seginfo, si.data(), si.size() * sizeof(SegInfo), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(ctx->d_inst, ii.data(), ii.size() * sizeof(InstInfo), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(ctx->d_seginfo, si.data(), si.size() * sizeof(SegInfo), cudaMemcpyHostToDevice,
+                            ctx->work) != cudaSuccess ||
+            cudaMemcpyAsync(ctx->d_inst, ii.data(), ii.size() * sizeof(InstInfo), cudaMemcpyHostToDevice,
+                            ctx->work) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->work) != cudaSuccess)
             return bail(QMC_ERR_CUDA);
     }
     if (cudaStreamSynchronize(ctx->work) != cudaSuccess) return bail(QMC_ERR_CUDA);
@@ -434,7 +553,7 @@ extern "C" {
 int qmc_create(qmc_ctx** out, const qmc_config* cfg)
 {
     if (!out || !cfg) return QMC_ERR_INVALID_ARG;
-    if (cfg->n_qubits < 1 || cfg->n_qubits > 32 || cfg->n_segments < 1 || cfg->n_diag < 1 ||
+    if (cfg->n_qubits < 1 || cfg->n_qubits > QMC_MAX_QUBITS || cfg->n_segments < 1 || cfg->n_diag < 1 ||
         cfg->n_segments > (1 << 28) || (cfg->integrator != QMC_EULER && cfg->integrator != QMC_AB2) ||
         cfg->initiator_min < 0)
         return QMC_ERR_INVALID_ARG;
@@ -497,17 +616,22 @@ void qmc_destroy(qmc_ctx* ctx)
     if (!ctx) return;
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-    void* ptrs[] = {ctx->d_state, ctx->d_pop[0], ctx->d_pop[1], ctx->d_pop[2], ctx->d_segoff[0],
-                    ctx->d_segoff[1], ctx->d_segoff[2], ctx->d_gofs[0], ctx->d_gofs[1], ctx->d_gofs[2], ctx->d_spawn, ctx->d_spawn_alt, ctx->d_cand, ctx->d_bucket, ctx->d_bscan_status, ctx->d_win, ctx->d_big_list, ctx->d_heavy,
-                    ctx->d_kd, ctx->d_sort_hist, ctx->d_sort_status, ctx->d_bseg, ctx->d_tile_start,
-                    ctx->d_mtiles, ctx->d_merge_status, ctx->d_segacc, ctx->d_history, ctx->d_zacc, ctx->d_zhist, ctx->d_aux, ctx->d_info,
-                    ctx->d_progs, ctx->d_obs, ctx->d_seginfo, ctx->d_inst, ctx->d_mlp, ctx->d_mlp_tc, ctx->d_mlp_mask,
-                    ctx->d_mlp_idx, ctx->d_learn_prog, ctx->d_learn_scratch, ctx->d_learn_small, ctx->d_learn_tc};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    std::vector<void*> held;
+    for (const auto& b : ctx->blocks) held.push_back(b.first);
+    for (void* p : held) mem_free(ctx, p);
+    if (ctx->work) cudaStreamSynchronize(ctx->work);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
     if (ctx->work) cudaStreamDestroy(ctx->work);
     delete ctx;
+}
+
+int qmc_memory(const qmc_ctx* ctx, int64_t* out)
+{
+    if (!ctx || !out) return QMC_ERR_INVALID_ARG;
+    out[0] = ctx->held_bytes;
+    out[1] = (int64_t)ctx->blocks.size();
+    return QMC_OK;
 }
 
 const char* qmc_last_error(const qmc_ctx* ctx)
@@ -547,7 +671,7 @@ int repack_tc(qmc_ctx* ctx)
 {
     const int I = ctx->mlp_in, H = ctx->mlp_hidden, G = ctx->mlp_out;
     if (!ctx->d_mlp || H % 16 != 0 || H > 64 || G > 256 || I > 80) {
-        if (ctx->d_mlp_tc) cudaFree(ctx->d_mlp_tc);
+        mem_free(ctx, ctx->d_mlp_tc);
         ctx->d_mlp_tc = nullptr;
         return QMC_OK;
     }
@@ -562,6 +686,8 @@ int repack_tc(qmc_ctx* ctx)
 
 int qmc_set_proposal(qmc_ctx* ctx, int32_t kind)
 {
+    if (ctx && ctx->wide && kind != QMC_PROPOSAL_EXACT)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "only the exact spawn choice above 32 qubits");
     if (!ctx) return QMC_ERR_INVALID_ARG;
     if (kind != QMC_PROPOSAL_EXACT && kind != QMC_PROPOSAL_STATIC && kind != QMC_PROPOSAL_LEARNED &&
         kind != QMC_PROPOSAL_LEARNED_TC)
@@ -580,6 +706,7 @@ int qmc_set_proposal(qmc_ctx* ctx, int32_t kind)
 
 int qmc_set_proposal_mlp(qmc_ctx* ctx, const qmc_mlp* m)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_set_proposal_mlp: not available above 32 qubits");
     if (!ctx || !m) return QMC_ERR_INVALID_ARG;
     if (ctx->batch) return fail(ctx, QMC_ERR_STATE, "the learned proposal takes a context of one instance");
     const int n = ctx->inst[0].n, I = m->n_in, H = m->n_hidden, G = m->n_out;
@@ -643,6 +770,7 @@ int qmc_learn_param_count(qmc_ctx* ctx, int64_t* n_params)
 int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, float* target, float* weight,
                      int64_t* n_events)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_learn_events: not available above 32 qubits");
     if (!ctx || !feat || !target || !weight || !n_events) return QMC_ERR_INVALID_ARG;
     if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
     if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
@@ -683,6 +811,7 @@ int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, f
 int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
                    int64_t ld, int64_t n_events, float* grad, double* loss)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_learn_grad: not available above 32 qubits");
     if (!ctx || !params || !feat || !target || !weight || !grad || !loss) return QMC_ERR_INVALID_ARG;
     if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
     if (n_events < 1 || ld < n_events) return fail(ctx, QMC_ERR_INVALID_ARG, "need 1 <= n_events <= ld");
@@ -724,6 +853,7 @@ int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const f
 int qmc_learn_grad_tc(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
                       int64_t ld, int64_t n_events, float* grad, double* loss)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_learn_grad_tc: not available above 32 qubits");
     if (!ctx || !params || !feat || !target || !weight || !grad || !loss) return QMC_ERR_INVALID_ARG;
     if (!ctx->d_mlp) return fail(ctx, QMC_ERR_STATE, "load the learned proposal's network first");
     if (!ctx->d_mlp_tc)
@@ -838,6 +968,7 @@ int qmc_get_tuning(const qmc_ctx* ctx, qmc_tuning* t)
 
 int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_autotune: not available above 32 qubits");
     if (!ctx) return QMC_ERR_INVALID_ARG;
     if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
     if (!(dt > 0.0) || nsteps < 1 || nsteps > 64) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0, 1 <= nsteps <= 64");
@@ -851,20 +982,11 @@ int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out)
     const int slot[2] = {hs0.cur, (hs0.cur + 2) % 3};
     Rec* keep[2] = {nullptr, nullptr};
     int64_t* keep_off[2] = {nullptr, nullptr};
-    auto release = [&]() {
-        for (int w = 0; w < 2; ++w) {
-            if (keep[w]) cudaFree(keep[w]);
-            if (keep_off[w]) cudaFree(keep_off[w]);
-        }
-    };
+    Scratch tmp(ctx);
     for (int w = 0; w < 2; ++w) {
         const int64_t cnt = hs0.count[slot[w]];
-        if (cudaMalloc((void**)&keep[w], (size_t)std::max<int64_t>(cnt, 1) * sizeof(Rec)) != cudaSuccess ||
-            cudaMalloc((void**)&keep_off[w], (size_t)(nseg + 1) * 8) != cudaSuccess) {
-            cudaGetLastError();
-            release();
+        if (tmp.get(&keep[w], cnt) != QMC_OK || tmp.get(&keep_off[w], nseg + 1) != QMC_OK)
             return fail(ctx, QMC_ERR_OOM, "autotune: no room for a copy of the populations");
-        }
         if (cnt) CK(cudaMemcpyAsync(keep[w], ctx->d_pop[slot[w]], cnt * sizeof(Rec), cudaMemcpyDeviceToDevice, ctx->work));
         CK(cudaMemcpyAsync(keep_off[w], ctx->d_segoff[slot[w]], (size_t)(nseg + 1) * 8, cudaMemcpyDeviceToDevice,
                            ctx->work));
@@ -916,10 +1038,7 @@ int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     double best_ms = 0.0;
     // the first trial also builds the step graph and warms the caches: time it twice
-    if ((rc = trial(best, &best_ms)) != QMC_OK || (rc = trial(best, &best_ms)) != QMC_OK) {
-        release();
-        return rc;
-    }
+    if ((rc = trial(best, &best_ms)) != QMC_OK || (rc = trial(best, &best_ms)) != QMC_OK) return rc;
     const int32_t ctas[3] = {0, 2 * sms, sms};
     const int32_t heavy[3] = {64, 256, 1024};
     const int32_t bucket[3] = {12, 24, 48};
@@ -940,7 +1059,6 @@ int qmc_autotune(qmc_ctx* ctx, double dt, int32_t nsteps, qmc_tuning* out)
     }
     if (rc == QMC_OK) rc = qmc_set_tuning(ctx, &best);
     if (rc == QMC_OK) rc = restore();
-    release();
     if (rc != QMC_OK) return rc;
     if (out) *out = best;
     return leave(ctx);
@@ -953,7 +1071,7 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
     if (!has_schedules(ctx)) return fail(ctx, QMC_ERR_STATE, "load a schedule first");
     if (nnz < 0 || (nnz > 0 && (!x || !y || !re || !im))) return fail(ctx, QMC_ERR_INVALID_ARG, "bad arrays");
     // every instance takes the same rho(0); (x, y) must fit the smallest one
-    int nmin = 32;
+    int nmin = QMC_MAX_QUBITS;
     for (const auto& I : ctx->inst) nmin = std::min(nmin, (int)I.n);
     const uint64_t lim = (1ull << nmin) - 1;
     std::vector<std::pair<std::pair<uint64_t, uint64_t>, int64_t>> order;
@@ -980,11 +1098,11 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
     uint64_t *d_x = nullptr, *d_y = nullptr;
     double *d_re = nullptr, *d_im = nullptr;
     int64_t* d_vals = nullptr;
-    if ((rc = dalloc(ctx, &d_x, nnz)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_y, nnz)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_re, nnz)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_im, nnz)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_vals, 2 * need)) != QMC_OK) return rc;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_x, nnz)) != QMC_OK || (rc = tmp.get(&d_y, nnz)) != QMC_OK ||
+        (rc = tmp.get(&d_re, nnz)) != QMC_OK || (rc = tmp.get(&d_im, nnz)) != QMC_OK ||
+        (rc = tmp.get(&d_vals, 2 * need)) != QMC_OK)
+        return rc;
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
@@ -995,16 +1113,14 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
         CK(cudaMemcpyAsync(d_im, him.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->work));
     }
     StepParams P = params(ctx);
-    launch_init(P, d_x, d_y, d_re, d_im, nnz, d_vals, ctx->work);
+    if (ctx->wide)
+        launch_wide_init(P, d_x, d_y, d_re, d_im, nnz, d_vals, ctx->work);
+    else
+        launch_init(P, d_x, d_y, d_re, d_im, nnz, d_vals, ctx->work);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(ctx->d_segoff[2], 0, (size_t)(ctx->cfg.n_segments + 1) * 8, ctx->work));
     CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
-    cudaFree(d_x);
-    cudaFree(d_y);
-    cudaFree(d_re);
-    cudaFree(d_im);
-    cudaFree(d_vals);
     if (hs.error) {
         clear_dev_error(ctx);
         return map_dev_error(ctx, hs.error, hs.error_aux);
@@ -1019,6 +1135,7 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y, con
 int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, const uint64_t* keys,
                         const int32_t* re, const int32_t* im)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_set_populations: not available above 32 qubits");
     if (!ctx || (which != 0 && which != 1) || !counts) return QMC_ERR_INVALID_ARG;
     const int nseg = ctx->cfg.n_segments;
     std::vector<int64_t> off(nseg + 1, 0);
@@ -1040,10 +1157,10 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
     uint64_t* d_keys = nullptr;
     int32_t *d_re = nullptr, *d_im = nullptr;
     int* d_bad = nullptr;
-    if ((rc = dalloc(ctx, &d_keys, total)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_re, total)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_im, total)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_bad, 1)) != QMC_OK) return rc;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_keys, total)) != QMC_OK || (rc = tmp.get(&d_re, total)) != QMC_OK ||
+        (rc = tmp.get(&d_im, total)) != QMC_OK || (rc = tmp.get(&d_bad, 1)) != QMC_OK)
+        return rc;
     CK(cudaMemsetAsync(d_bad, 0, sizeof(int), ctx->work));
     if (total) {
         CK(cudaMemcpyAsync(d_keys, keys, total * 8, cudaMemcpyHostToDevice, ctx->work));
@@ -1057,10 +1174,6 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
-    cudaFree(d_keys);
-    cudaFree(d_re);
-    cudaFree(d_im);
-    cudaFree(d_bad);
     if (bad) {
         // leave the slot empty rather than half-valid
         std::vector<int64_t> zero(nseg + 1, 0);
@@ -1289,6 +1402,7 @@ int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t
 {
     if (!ctx || !count || seg < 0 || seg >= ctx->cfg.n_segments || (which != 0 && which != 1))
         return QMC_ERR_INVALID_ARG;
+    if (ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "keys exceed 64 bits above 32 qubits: use qmc_export_xy");
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     DevState hs;
@@ -1310,6 +1424,53 @@ int qmc_export(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* keys, int32_t
             re[i] = r[i].re;
             im[i] = r[i].im;
         }
+    }
+    return leave(ctx);
+}
+
+int qmc_export_xy(qmc_ctx* ctx, int32_t seg, int32_t which, uint64_t* x, uint64_t* y, int32_t* re, int32_t* im,
+                  int64_t cap, int64_t* count)
+{
+    if (!ctx || !count || seg < 0 || seg >= ctx->cfg.n_segments || (which != 0 && which != 1))
+        return QMC_ERR_INVALID_ARG;
+    const int n = instance_of(ctx, seg).n;
+    if (!ctx->wide) {
+        std::vector<uint64_t> keys((size_t)std::max<int64_t>(cap, 1));
+        const int rc = qmc_export(ctx, seg, which, keys.data(), re, im, cap, count);
+        if (rc != QMC_OK) return rc;
+        const uint64_t ymask = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+        for (int64_t i = 0; i < *count && i < cap; ++i) {
+            x[i] = keys[i] >> n;
+            y[i] = keys[i] & ymask;
+        }
+        return QMC_OK;
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int slot = which == 0 ? hs.cur : (hs.cur + 2) % 3;
+    int64_t off[2];
+    CK(cudaMemcpyAsync(off, ctx->d_segoff[slot] + seg, 16, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int64_t cnt = off[1] - off[0];
+    *count = cnt;
+    if (cnt > cap) return fail(ctx, QMC_ERR_INVALID_ARG, "export capacity too small");
+    if (cnt > 0) {
+        uint64_t *d_x = nullptr, *d_y = nullptr;
+        int32_t *d_re = nullptr, *d_im = nullptr;
+        Scratch tmp(ctx);
+        if ((rc = tmp.get(&d_x, cnt)) != QMC_OK || (rc = tmp.get(&d_y, cnt)) != QMC_OK ||
+            (rc = tmp.get(&d_re, cnt)) != QMC_OK || (rc = tmp.get(&d_im, cnt)) != QMC_OK)
+            return rc;
+        launch_wide_export(params(ctx), slot, off[0], cnt, d_x, d_y, d_re, d_im, ctx->work);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(x, d_x, cnt * 8, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaMemcpyAsync(y, d_y, cnt * 8, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaMemcpyAsync(re, d_re, cnt * 4, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaMemcpyAsync(im, d_im, cnt * 4, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
     }
     return leave(ctx);
 }
@@ -1353,7 +1514,12 @@ int qmc_observables(qmc_ctx* ctx, qmc_obs* obs)
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     StepParams P = params(ctx);
-    launch_obs(P, 0, ctx->d_obs, ctx->grid, ctx->work);
+    if (ctx->wide) {
+        CK(cudaMemsetAsync(ctx->d_obs, 0, sizeof(SegStats) * (size_t)ctx->cfg.n_segments, ctx->work));
+        launch_wide_obs(P, 0, ctx->d_obs, ctx->work);
+    } else {
+        launch_obs(P, 0, ctx->d_obs, ctx->grid, ctx->work);
+    }
     CK(cudaGetLastError());
     std::vector<SegStats> h(ctx->cfg.n_segments);
     CK(cudaMemcpyAsync(h.data(), ctx->d_obs, h.size() * sizeof(SegStats), cudaMemcpyDeviceToHost, ctx->work));
@@ -1365,6 +1531,7 @@ int qmc_observables(qmc_ctx* ctx, qmc_obs* obs)
 int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* psi_re, const double* psi_im,
                 int32_t len, double* out_re, double* out_im)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_overlap: not available above 32 qubits");
     if (!ctx || seg < 0 || seg >= ctx->cfg.n_segments || len < 0 || !out_re || !out_im) return QMC_ERR_INVALID_ARG;
     const int n = instance_of(ctx, seg).n;
     const int nq = len * len;
@@ -1375,8 +1542,8 @@ int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* ps
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     uint64_t* d_q = nullptr;
     int64_t* d_v = nullptr;
-    if ((rc = dalloc(ctx, &d_q, nq)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &d_v, 2 * (int64_t)nq)) != QMC_OK) return rc;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_q, nq)) != QMC_OK || (rc = tmp.get(&d_v, 2 * (int64_t)nq)) != QMC_OK) return rc;
     std::vector<int64_t> v(2 * (size_t)(nq > 0 ? nq : 1));
     if (nq) {
         CK(cudaMemcpyAsync(d_q, q.data(), nq * 8, cudaMemcpyHostToDevice, ctx->work));
@@ -1385,8 +1552,6 @@ int qmc_overlap(qmc_ctx* ctx, int32_t seg, const uint64_t* idx, const double* ps
         CK(cudaMemcpyAsync(v.data(), d_v, 2 * (size_t)nq * 8, cudaMemcpyDeviceToHost, ctx->work));
     }
     CK(cudaStreamSynchronize(ctx->work));
-    cudaFree(d_q);
-    cudaFree(d_v);
     // sum_{a,b} conj(psi_a) N_ab psi_b in a fixed order
     double sr = 0.0, si = 0.0;
     for (int a = 0; a < len; ++a) {
@@ -1413,6 +1578,61 @@ int aux_reserve(qmc_ctx* ctx, int64_t bytes)
 }
 } // namespace
 
+} // extern "C"
+
+namespace {
+
+// qmc_overlap_all above 32 qubits: the len^2 values N_ab of every vector by
+// device lookups, summed on the host in qmc_overlap's order.
+int overlap_all_wide(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, const double* psi_im, int32_t len,
+                     double* out_re, double* out_im)
+{
+    const int nseg = ctx->cfg.n_segments;
+    const int nq = len * len;
+    std::vector<uint64_t> qx(nq), qy(nq);
+    for (int a = 0; a < len; ++a)
+        for (int b = 0; b < len; ++b) {
+            qx[a * len + b] = idx[a];
+            qy[a * len + b] = idx[b];
+        }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    uint64_t *d_qx = nullptr, *d_qy = nullptr;
+    int64_t* d_v = nullptr;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_qx, nq)) != QMC_OK || (rc = tmp.get(&d_qy, nq)) != QMC_OK ||
+        (rc = tmp.get(&d_v, 2 * (int64_t)nq * nseg)) != QMC_OK)
+        return rc;
+    CK(cudaMemcpyAsync(d_qx, qx.data(), 8 * (size_t)nq, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(d_qy, qy.data(), 8 * (size_t)nq, cudaMemcpyHostToDevice, ctx->work));
+    const StepParams P = params(ctx);
+    for (int s = 0; s < nseg; ++s) launch_wide_lookup(P, s, d_qx, d_qy, nq, d_v + 2 * (int64_t)nq * s, ctx->work);
+    CK(cudaGetLastError());
+    std::vector<int64_t> v(2 * (size_t)nq * nseg);
+    CK(cudaMemcpyAsync(v.data(), d_v, v.size() * 8, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (int s = 0; s < nseg; ++s) {
+        const int64_t* w = v.data() + 2 * (size_t)nq * s;
+        double sr = 0.0, si = 0.0;
+        for (int a = 0; a < len; ++a) {
+            for (int b = 0; b < len; ++b) {
+                const double nr = (double)w[2 * (a * len + b)], ni = (double)w[2 * (a * len + b) + 1];
+                const double car = psi_re[a], cai = -psi_im[a];
+                const double pr = car * nr - cai * ni, pi = car * ni + cai * nr;
+                sr += pr * psi_re[b] - pi * psi_im[b];
+                si += pr * psi_im[b] + pi * psi_re[b];
+            }
+        }
+        out_re[s] = sr;
+        out_im[s] = si;
+    }
+    return leave(ctx);
+}
+
+} // namespace
+
+extern "C" {
+
 int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, const double* psi_im, int32_t len,
                     double* out_re, double* out_im)
 {
@@ -1425,6 +1645,7 @@ int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, con
     for (int a = 0; a < len; ++a)
         if (nmin < 64 && (idx[a] >> nmin)) return fail(ctx, QMC_ERR_INVALID_ARG, "target index >= 2^n");
     int rc;
+    if (ctx->wide) return overlap_all_wide(ctx, idx, psi_re, psi_im, len, out_re, out_im);
     if ((rc = enter(ctx)) != QMC_OK) return rc;
     const int64_t bytes = 8 * (int64_t)len + 16 * (int64_t)len + 16 * (int64_t)nseg;
     if ((rc = aux_reserve(ctx, bytes)) != QMC_OK) return rc;
@@ -1452,6 +1673,7 @@ int qmc_overlap_all(qmc_ctx* ctx, const uint64_t* idx, const double* psi_re, con
 
 int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_antihermiticity: not available above 32 qubits");
     if (!ctx || !out) return QMC_ERR_INVALID_ARG;
     if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "no population");
     const int nseg = ctx->cfg.n_segments;
@@ -1467,6 +1689,7 @@ int qmc_antihermiticity(qmc_ctx* ctx, uint64_t* out)
 
 int qmc_antihermiticity_sum(qmc_ctx* ctx, const int32_t* vectors, int32_t count, uint64_t* out)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_antihermiticity_sum: not available above 32 qubits");
     if (!ctx || !vectors || !out || count < 1 || count > 65535) return QMC_ERR_INVALID_ARG;
     if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "no population");
     const int nseg = ctx->cfg.n_segments;
@@ -1492,6 +1715,7 @@ int qmc_antihermiticity_sum(qmc_ctx* ctx, const int32_t* vectors, int32_t count,
 
 int qmc_checkpoint(qmc_ctx* ctx, const char* path)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_checkpoint: not available above 32 qubits");
     if (!ctx || !path) return QMC_ERR_INVALID_ARG;
     if (!ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "nothing to checkpoint");
     int rc;
@@ -1548,6 +1772,7 @@ int qmc_checkpoint(qmc_ctx* ctx, const char* path)
 
 int qmc_restore(qmc_ctx* ctx, const char* path)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_restore: not available above 32 qubits");
     if (!ctx || !path) return QMC_ERR_INVALID_ARG;
     if (!has_schedules(ctx)) return fail(ctx, QMC_ERR_STATE, "load the same schedule before restoring");
     FILE* f = std::fopen(path, "rb");
@@ -1623,6 +1848,7 @@ extern "C" {
 
 int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap, int32_t* n_kernels)
 {
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_step_profile: not available above 32 qubits");
     if (!ctx || !kernel_ms || !n_kernels || cap < 0) return QMC_ERR_INVALID_ARG;
     if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
     if (!(dt > 0.0) || nsteps < 1) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 1");
@@ -1676,7 +1902,8 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
 int qmc_step_launches(const qmc_ctx* ctx, int32_t* launches)
 {
     if (!ctx || !launches) return QMC_ERR_INVALID_ARG;
-    *launches = step_launch_count(params(const_cast<qmc_ctx*>(ctx)));
+    qmc_ctx* c = const_cast<qmc_ctx*>(ctx);
+    *launches = c->wide ? wide_step_launch_count(params(c), wparams(c)) : step_launch_count(params(c));
     return QMC_OK;
 }
 

@@ -7,6 +7,11 @@
 //   receives val (0: re, 1: im) and noninit marks a spawn from a parent below
 //   the initiator threshold [End Matter, simulation methodology].
 //
+// Key widths: up to 32 qubits a key is a uint64_t and a qubit mask a
+// uint32_t; from 33 to 60 qubits a key is 128 bits (u128) and a mask a
+// uint64_t (the "wide" layouts, records WRec / WSpawn, programs with the
+// template arguments <uint64_t, u128>).
+//
 // Column program: the column of dt_eff * L(t) at |x><y| [Eq. (2)] for one step
 // and one pass, in the 2^-52 fixed-point units of the expanded terms.  Terms
 // are grouped by destination mask (dx << n | dy); a group's element is a sum
@@ -19,6 +24,8 @@
 #include <stdint.h>
 
 namespace qmc {
+
+typedef unsigned __int128 u128;
 
 struct Rec {
     uint64_t key;
@@ -33,6 +40,22 @@ struct SRec {
 
 static_assert(sizeof(Rec) == 16, "population record must be 16 bytes");
 static_assert(sizeof(SRec) == 16, "spawn record must be 16 bytes");
+
+// Wide records (33..60 qubits): the key (x << n) | y as two 64-bit words,
+// compared high word first.
+struct WRec {
+    uint64_t lo, hi;
+    int32_t re, im;
+};
+
+struct WSpawn {
+    uint64_t lo, hi;
+    uint32_t meta;   // segment << 2 | target << 1 | noninit, as in SRec
+    int32_t val;
+};
+
+static_assert(sizeof(WRec) == 24, "wide population record must be 24 bytes");
+static_assert(sizeof(WSpawn) == 24, "wide spawn record must be 24 bytes");
 
 // ---- column program --------------------------------------------------------
 struct ProgHeader {
@@ -52,28 +75,32 @@ struct ProgHeader {
 // Proposal spawning: every destination with a nonzero static weight (sum of
 // |Re| + |Im| over its expanded terms), in ascending mask order, with the
 // end of its interval in the cumulative static weights.
-struct StatSlot {
-    uint64_t mask;
+template <class K>
+struct StatSlotT {
+    K mask;
     int64_t end;
 };
 
 // Self-family parity term: Q' * (|M| - 2 popc(pat & M)), pat = x, y or x ^ y.
-struct SelfFam {
-    uint32_t members;
+template <class M>
+struct SelfFamT {
+    M members;
     uint32_t type; // 0: zl = e_q (pattern x); 1: zr = e_q (y); 2: both (x ^ y)
     int64_t qre, qim;
 };
 
 // Self generic parity term (multi-qubit Z parity on the diagonal element).
-struct SelfGen {
-    uint32_t zl, zr;
+template <class M>
+struct SelfGenT {
+    M zl, zr;
     int64_t qre, qim;
 };
 
 // Family of single-qubit groups: member q has destination mask
 // (alpha e_q) << n | (beta e_q) and element tab[pi], pi = 2 x_q + y_q.
-struct Fam {
-    uint32_t members;
+template <class M>
+struct FamT {
+    M members;
     uint32_t ab;   // bit 1: alpha (ket flips q), bit 0: beta (bra flips q)
     int64_t a[4];  // |Re tab| + |Im tab|
     int64_t tre[4], tim[4];
@@ -85,31 +112,35 @@ struct Fam {
 //   s0 + sa cx + sb cy + sc c11   (complex),
 // and the summed weight of the families with that mask,
 //   f0 + fx cx + fy cy + f11 c11  (= sum over members of |Re T| + |Im T|).
-struct AffGroup {
-    uint32_t members;
+template <class M>
+struct AffGroupT {
+    M members;
     uint32_t pad;
     int64_t s0re, s0im, sare, saim, sbre, sbim, scre, scim;
     int64_t f0, fx, fy, f11;
 };
 
 // Generic group: element = sum over terms [first, first + count) of +-Q'.
-struct Gen {
-    uint64_t mask_key;
+template <class K>
+struct GenT {
+    K mask_key;
     int32_t first, count;
     int32_t is_const, pad;
     int64_t cre, cim; // the element when is_const
 };
 
-struct GTerm {
-    uint32_t zl, zr;
+template <class M>
+struct GTermT {
+    M zl, zr;
     int64_t qre, qim;
 };
 
 // Destinations of the column in ascending mask order (the canonical order of
 // the multinomial choice).  kind 0: diagonal (mask 0); 1: family member
 // (idx = fam | q << 16); 2: generic group (idx = gen).
-struct Entry {
-    uint64_t mask_key;
+template <class K>
+struct EntryT {
+    K mask_key;
     uint32_t kind;
     uint32_t idx;
 };
@@ -118,12 +149,24 @@ struct Entry {
 // q, kind 1: idx = family, members = their q bits), or a single entry of
 // kind 0 or 2 (idx = its entry index).  The destination choice walks runs and
 // skips a family run by its summed weight.
-struct Run {
+template <class M>
+struct RunT {
     uint32_t kind;
     uint32_t idx;
-    uint32_t members;
+    M members;
     uint32_t shift;   // family runs: n (a member's ket bit is q + n)
 };
+
+// Narrow programs (up to 32 qubits).
+using StatSlot = StatSlotT<uint64_t>;
+using SelfFam = SelfFamT<uint32_t>;
+using SelfGen = SelfGenT<uint32_t>;
+using Fam = FamT<uint32_t>;
+using AffGroup = AffGroupT<uint32_t>;
+using Gen = GenT<uint64_t>;
+using GTerm = GTermT<uint32_t>;
+using Entry = EntryT<uint64_t>;
+using Run = RunT<uint32_t>;
 
 // ---- device-resident step state ---------------------------------------------
 enum DevError : uint32_t {

@@ -32,12 +32,18 @@ namespace {
 constexpr double kOne52 = 4503599627370496.0;       // 2^52
 constexpr double kLimit62 = 4611686018427387904.0;  // 2^62
 
-struct Raw {
-    uint32_t xl, zl, xr, zr;
+// One expanded term c P_L rho P_R: X and Z masks of both strings (M is the
+// qubit-mask type, uint32_t up to 32 qubits and uint64_t above).
+template <class M>
+struct RawT {
+    M xl, zl, xr, zr;
     int64_t qre, qim;
 };
 
 inline int popc(uint32_t v) { return __builtin_popcount(v); }
+inline int popc(uint64_t v) { return __builtin_popcountll(v); }
+inline int ctz(uint32_t v) { return __builtin_ctz(v); }
+inline int ctz(uint64_t v) { return __builtin_ctzll(v); }
 
 inline void rot(int64_t* re, int64_t* im, int k)
 {
@@ -73,7 +79,8 @@ bool window_on(const Schedule& s, int id, double t)
 }
 
 // letter index: 0 I, 1 X, 2 Y, 3 Z
-inline int letter(uint32_t x, uint32_t z, int q)
+template <class M>
+inline int letter(M x, M z, int q)
 {
     int xb = (x >> q) & 1, zb = (z >> q) & 1;
     if (xb && zb) return 2;
@@ -83,8 +90,8 @@ inline int letter(uint32_t x, uint32_t z, int q)
 }
 
 // P_a P_b = i^k P_c for Hermitian Pauli strings.
-void pauli_mul(int n, uint32_t xa, uint32_t za, uint32_t xb, uint32_t zb, uint32_t* xc,
-               uint32_t* zc, int* k)
+template <class M>
+void pauli_mul(int n, M xa, M za, M xb, M zb, M* xc, M* zc, int* k)
 {
     int kk = 0;
     for (int q = 0; q < n; ++q) {
@@ -97,7 +104,8 @@ void pauli_mul(int n, uint32_t xa, uint32_t za, uint32_t xb, uint32_t zb, uint32
     *k = kk & 3;
 }
 
-int expand(const Schedule& s, double t, double dt_eff, std::vector<Raw>* out)
+template <class M>
+int expand(const Schedule& s, double t, double dt_eff, std::vector<RawT<M>>* out)
 {
     out->clear();
     int rc;
@@ -105,9 +113,9 @@ int expand(const Schedule& s, double t, double dt_eff, std::vector<Raw>* out)
         if (!window_on(s, h.window_id, t)) continue;
         double sc = rate_value(s, h.rate_id, t) * dt_eff;
         double v = h.h * sc;
-        uint32_t xm = (uint32_t)h.xm, zm = (uint32_t)h.zm;
+        const M xm = (M)h.xm, zm = (M)h.zm;
         int ny = popc(xm & zm);
-        Raw a{xm, zm, 0, 0, 0, 0}, b{0, 0, xm, zm, 0, 0};
+        RawT<M> a{xm, zm, 0, 0, 0, 0}, b{0, 0, xm, zm, 0, 0};
         if ((rc = quantise(0.0, -v, &a.qre, &a.qim)) != QMC_OK) return rc;
         if ((rc = quantise(0.0, v, &b.qre, &b.qim)) != QMC_OK) return rc;
         rot(&a.qre, &a.qim, ny);
@@ -125,19 +133,19 @@ int expand(const Schedule& s, double t, double dt_eff, std::vector<Raw>* out)
                 const qmc_pauli_coef& lb = s.coefs[L.first + ib];
                 double zre = la.re * lb.re + la.im * lb.im;
                 double zim = la.im * lb.re - la.re * lb.im;
-                uint32_t xa = (uint32_t)la.xm, za = (uint32_t)la.zm;
-                uint32_t xb = (uint32_t)lb.xm, zb = (uint32_t)lb.zm;
-                Raw j{xa, za, xb, zb, 0, 0};
+                const M xa = (M)la.xm, za = (M)la.zm;
+                const M xb = (M)lb.xm, zb = (M)lb.zm;
+                RawT<M> j{xa, za, xb, zb, 0, 0};
                 if ((rc = quantise(sc * zre, sc * zim, &j.qre, &j.qim)) != QMC_OK) return rc;
                 rot(&j.qre, &j.qim, popc(xa & za) - popc(xb & zb) + 4);
                 out->push_back(j);
                 int64_t cre, cim;
                 if ((rc = quantise(hs * zre, -(hs * zim), &cre, &cim)) != QMC_OK) return rc;
-                uint32_t xc, zc;
+                M xc, zc;
                 int k;
                 pauli_mul(s.n, xa, za, xb, zb, &xc, &zc, &k);
                 int nyc = popc(xc & zc);
-                Raw l{xc, zc, 0, 0, cre, cim}, r{0, 0, xc, zc, cre, cim};
+                RawT<M> l{xc, zc, 0, 0, cre, cim}, r{0, 0, xc, zc, cre, cim};
                 rot(&l.qre, &l.qim, k + nyc);
                 rot(&r.qre, &r.qim, k - nyc + 4);
                 out->push_back(l);
@@ -154,7 +162,11 @@ void put(std::vector<uint8_t>* blob, size_t at, const T* src, size_t count)
     if (count) std::memcpy(blob->data() + at, src, count * sizeof(T));
 }
 
-size_t align8(size_t v) { return (v + 7) & ~(size_t)7; }
+template <size_t A>
+size_t align_up(size_t v) { return (v + (A - 1)) & ~(A - 1); }
+
+template <class M, class K, size_t A>
+int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint8_t>* blob);
 
 } // namespace
 
@@ -184,24 +196,44 @@ int validate_schedule(const Schedule& s, std::string* why)
 
 double spawn_prob_bound(const Schedule& s, double t, double dt_eff)
 {
-    std::vector<Raw> raw;
+    std::vector<RawT<uint64_t>> raw;
     if (expand(s, t, dt_eff, &raw) != QMC_OK) return INFINITY;
     double acc = 0.0;
-    for (const Raw& r : raw) acc += (std::fabs((double)r.qre) + std::fabs((double)r.qim)) / kOne52;
+    for (const RawT<uint64_t>& r : raw) acc += (std::fabs((double)r.qre) + std::fabs((double)r.qim)) / kOne52;
     return acc;
 }
 
 int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_t>* blob)
 {
+    if (s.n <= 32) return build_program_t<uint32_t, uint64_t, 8>(s, t, dt_eff, blob);
+    return build_program_t<uint64_t, u128, 16>(s, t, dt_eff, blob);
+}
+
+namespace {
+
+// The program of one step and pass with qubit masks M and keys K; sections
+// aligned to A bytes (16 for 128-bit keys).
+template <class M, class K, size_t A>
+int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint8_t>* blob)
+{
+    using SelfFam = SelfFamT<M>;
+    using SelfGen = SelfGenT<M>;
+    using Fam = FamT<M>;
+    using AffGroup = AffGroupT<M>;
+    using Gen = GenT<K>;
+    using GTerm = GTermT<M>;
+    using Entry = EntryT<K>;
+    using Run = RunT<M>;
+    using StatSlot = StatSlotT<K>;
     const int n = s.n;
-    std::vector<Raw> raw;
+    std::vector<RawT<M>> raw;
     int rc = expand(s, t, dt_eff, &raw);
     if (rc != QMC_OK) return rc;
 
     // group by destination mask, merge equal parity terms (exact sums)
-    std::map<uint64_t, std::map<std::pair<uint32_t, uint32_t>, std::pair<int64_t, int64_t>>> groups;
-    for (const Raw& r : raw) {
-        uint64_t mk = ((uint64_t)r.xl << n) | (uint64_t)r.xr;
+    std::map<K, std::map<std::pair<M, M>, std::pair<int64_t, int64_t>>> groups;
+    for (const RawT<M>& r : raw) {
+        const K mk = ((K)r.xl << n) | (K)r.xr;
         auto& g = groups[mk][{r.zl, r.zr}];
         g.first += r.qre;
         g.second += r.qim;
@@ -217,11 +249,11 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
 
     // diagonal (self) group
     {
-        std::map<std::tuple<uint32_t, int64_t, int64_t>, uint32_t> sf; // (type, q) -> members
-        auto it = groups.find(0);
+        std::map<std::tuple<uint32_t, int64_t, int64_t>, M> sf; // (type, q) -> members
+        auto it = groups.find((K)0);
         if (it != groups.end()) {
             for (const auto& kv : it->second) {
-                uint32_t zl = kv.first.first, zr = kv.first.second;
+                const M zl = kv.first.first, zr = kv.first.second;
                 int64_t qre = kv.second.first, qim = kv.second.second;
                 if (qre == 0 && qim == 0) continue;
                 if (zl == 0 && zr == 0) {
@@ -245,11 +277,11 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     }
 
     // off-diagonal groups: single-qubit families or generic groups
-    std::map<std::vector<int64_t>, uint32_t> famkeys; // (ab, tre[4], tim[4]) -> members
+    std::map<std::vector<int64_t>, M> famkeys; // (ab, tre[4], tim[4]) -> members
     for (const auto& gkv : groups) {
-        uint64_t mk = gkv.first;
-        uint32_t xl = (uint32_t)(mk >> n), xr = (uint32_t)(mk & ((n == 32) ? 0xFFFFFFFFull : ((1ull << n) - 1)));
-        uint32_t qm = xl | xr;
+        const K mk = gkv.first;
+        const M xl = (M)(mk >> n), xr = (M)(mk & (((K)1 << n) - 1));
+        const M qm = xl | xr;
         bool single = popc(qm) == 1;
         std::vector<GTerm> terms;
         for (const auto& kv : gkv.second) {
@@ -259,7 +291,7 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
         }
         if (terms.empty()) continue;
         if (single) {
-            int q = __builtin_ctz(qm);
+            int q = ctz(qm);
             int64_t tre[4] = {0, 0, 0, 0}, tim[4] = {0, 0, 0, 0};
             for (int pi = 0; pi < 4; ++pi) {
                 int xq = pi >> 1, yq = pi & 1;
@@ -306,13 +338,13 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     }
 
     // affine forms per member mask (self families and families)
-    std::map<uint32_t, AffGroup> aff;
-    auto group = [&](uint32_t M) -> AffGroup& {
-        auto it = aff.find(M);
+    std::map<M, AffGroup> aff;
+    auto group = [&](M mem) -> AffGroup& {
+        auto it = aff.find(mem);
         if (it == aff.end()) {
             AffGroup g{};
-            g.members = M;
-            it = aff.emplace(M, g).first;
+            g.members = mem;
+            it = aff.emplace(mem, g).first;
         }
         return it->second;
     };
@@ -383,13 +415,13 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
 
     // destinations in ascending mask order (the multinomial's canonical order)
     std::vector<Entry> entries;
-    entries.push_back(Entry{0ull, 0u, 0u});
+    entries.push_back(Entry{(K)0, 0u, 0u});
     for (size_t f = 0; f < fams.size(); ++f) {
-        uint32_t m = fams[f].members;
+        M m = fams[f].members;
         while (m) {
-            int q = __builtin_ctz(m);
+            int q = ctz(m);
             m &= m - 1;
-            uint64_t mk = (((fams[f].ab >> 1) & 1ull) << (q + n)) | ((uint64_t)(fams[f].ab & 1u) << q);
+            const K mk = ((K)((fams[f].ab >> 1) & 1u) << (q + n)) | ((K)(fams[f].ab & 1u) << q);
             entries.push_back(Entry{mk, 1u, (uint32_t)f | ((uint32_t)q << 16)});
         }
     }
@@ -401,9 +433,9 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     // any merging (the proposal spawning's destination law)
     std::vector<StatSlot> stat;
     {
-        std::map<uint64_t, int64_t> sw;
-        for (const Raw& r : raw) {
-            const uint64_t mk = ((uint64_t)r.xl << n) | (uint64_t)r.xr;
+        std::map<K, int64_t> sw;
+        for (const RawT<M>& r : raw) {
+            const K mk = ((K)r.xl << n) | (K)r.xr;
             const int64_t a = std::llabs(r.qre) + std::llabs(r.qim);
             int64_t& acc = sw[mk];
             acc = (acc >= (1ll << 52) || a >= (1ll << 52)) ? (1ll << 52) : std::min<int64_t>(acc + a, 1ll << 52);
@@ -424,12 +456,12 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
         if (E.kind == 1u) {
             const uint32_t f = E.idx & 0xFFFFu, q = E.idx >> 16;
             if (!runs.empty() && runs.back().kind == 1u && runs.back().idx == f) {
-                runs.back().members |= 1u << q;
+                runs.back().members |= (M)1 << q;
                 continue;
             }
-            runs.push_back(Run{1u, f, 1u << q, (uint32_t)n});
+            runs.push_back(Run{1u, f, (M)1 << q, (uint32_t)n});
         } else {
-            runs.push_back(Run{E.kind, (uint32_t)e, 0u, 0u});
+            runs.push_back(Run{E.kind, (uint32_t)e, (M)0, 0u});
         }
     }
 
@@ -440,18 +472,18 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     hdr.n_gterm = (int32_t)gterms.size();
     hdr.n_entry = (int32_t)entries.size();
 
-    size_t base = align8(blob->size());
-    size_t off = align8(sizeof(ProgHeader));
-    hdr.off_selffam = (int32_t)off; off = align8(off + selffam.size() * sizeof(SelfFam));
-    hdr.off_selfgen = (int32_t)off; off = align8(off + selfgen.size() * sizeof(SelfGen));
-    hdr.off_fam = (int32_t)off;     off = align8(off + fams.size() * sizeof(Fam));
-    hdr.off_gen = (int32_t)off;     off = align8(off + gens.size() * sizeof(Gen));
-    hdr.off_gterm = (int32_t)off;   off = align8(off + gterms.size() * sizeof(GTerm));
-    hdr.off_entry = (int32_t)off;   off = align8(off + entries.size() * sizeof(Entry));
-    hdr.off_aff = (int32_t)off;     off = align8(off + affs.size() * sizeof(AffGroup));
+    size_t base = align_up<A>(blob->size());
+    size_t off = align_up<A>(sizeof(ProgHeader));
+    hdr.off_selffam = (int32_t)off; off = align_up<A>(off + selffam.size() * sizeof(SelfFam));
+    hdr.off_selfgen = (int32_t)off; off = align_up<A>(off + selfgen.size() * sizeof(SelfGen));
+    hdr.off_fam = (int32_t)off;     off = align_up<A>(off + fams.size() * sizeof(Fam));
+    hdr.off_gen = (int32_t)off;     off = align_up<A>(off + gens.size() * sizeof(Gen));
+    hdr.off_gterm = (int32_t)off;   off = align_up<A>(off + gterms.size() * sizeof(GTerm));
+    hdr.off_entry = (int32_t)off;   off = align_up<A>(off + entries.size() * sizeof(Entry));
+    hdr.off_aff = (int32_t)off;     off = align_up<A>(off + affs.size() * sizeof(AffGroup));
     hdr.n_aff = (int32_t)affs.size();
-    hdr.off_run = (int32_t)off;     off = align8(off + runs.size() * sizeof(Run));
-    hdr.off_stat = (int32_t)off;    off = align8(off + stat.size() * sizeof(StatSlot));
+    hdr.off_run = (int32_t)off;     off = align_up<A>(off + runs.size() * sizeof(Run));
+    hdr.off_stat = (int32_t)off;    off = align_up<A>(off + stat.size() * sizeof(StatSlot));
     hdr.n_stat = (int32_t)stat.size();
     hdr.n_run = (int32_t)runs.size();
     hdr.bytes = (int32_t)off;
@@ -468,6 +500,8 @@ int build_program(const Schedule& s, double t, double dt_eff, std::vector<uint8_
     put(blob, base + hdr.off_stat, stat.data(), stat.size());
     return QMC_OK;
 }
+
+} // namespace
 
 uint64_t schedule_hash(const Schedule& s, uint64_t seed, int32_t nseg, int32_t integrator,
                        int64_t n_diag, int64_t init_min)

@@ -39,7 +39,8 @@ EXPORTED = [
     "qmc_step_launches", "qmc_batch_create", "qmc_set_proposal", "qmc_set_proposal_mlp",
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
     "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
-    "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum", "qmc_learn_grad_tc",
+    "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum", "qmc_learn_grad_tc", "qmc_memory",
+    "qmc_export_xy",
 ]
 
 
@@ -49,11 +50,46 @@ class QmcError(RuntimeError):
         self.code = code
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class Config(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_segments", C.c_int32), ("integrator", C.c_int32),
                 ("max_ctas", C.c_int32), ("seed", C.c_uint64), ("n_diag", C.c_int64),
                 ("initiator_min", C.c_int64), ("capacity_hint", C.c_int64), ("max_records", C.c_int64),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class TorchAllocator:
+    """Device memory of a context from torch's caching allocator (the
+    qmc_config.alloc / free callbacks): blocks are taken and returned in
+    stream order on the context's work stream.  ``calls`` counts
+    [allocations, frees]."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.calls = [0, 0]
+
+        def _alloc(nbytes, stream, user):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+                self.calls[0] += 1
+                return p
+            except Exception:   # out of memory: the library reports QMC_ERR_OOM
+                return None
+
+        def _free(ptr, stream, user):
+            self.calls[1] += 1
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+    def attach(self, cfg: Config):
+        cfg.alloc = self.alloc
+        cfg.free = self.free
 
 
 class HamTerm(C.Structure):
@@ -140,6 +176,8 @@ def lib():
         L.qmc_antihermiticity_sum.argtypes = [vp, vp, C.c_int32, vp]
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
+        L.qmc_memory.argtypes = [vp, vp]
+        L.qmc_export_xy.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, C.c_int64, C.POINTER(C.c_int64)]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
         for name in EXPORTED:
@@ -206,13 +244,16 @@ class QMC:
 
     def __init__(self, n_qubits: int, n_segments: int, seed: int, n_diag: int, integrator: int = AB2,
                  initiator_min: int = 0, capacity_hint: int = 0, max_records: int = 0, stream: int | None = None,
-                 max_ctas: int = 0):
+                 max_ctas: int = 0, allocator: "TorchAllocator | None" = None):
         self.L = lib()
         self.n = n_qubits
         self.nseg = n_segments
         self.n_diag = n_diag
         cfg = Config(n_qubits, n_segments, integrator, max_ctas, seed, n_diag, initiator_min, capacity_hint,
                      max_records, C.c_void_p(current_stream_handle() if stream is None else stream))
+        self._allocator = allocator   # its callbacks must outlive the context
+        if allocator is not None:
+            allocator.attach(cfg)
         h = C.c_void_p()
         rc = self.L.qmc_create(C.byref(h), C.byref(cfg))
         if rc != OK:
@@ -237,11 +278,13 @@ class QMC:
     # -- problem -------------------------------------------------------------
     @classmethod
     def batch(cls, problems, n_vectors, seeds, n_diags, integrator: int = AB2, initiator_mins=None,
-              capacity_hint: int = 0, max_records: int = 0, stream: int | None = None, max_ctas: int = 0):
+              capacity_hint: int = 0, max_records: int = 0, stream: int | None = None, max_ctas: int = 0,
+              allocator: "TorchAllocator | None" = None):
         """One context stepping several problem instances (qmc_batch_create):
         instance i's vectors are segments offsets[i] .. offsets[i + 1]."""
         self = cls.__new__(cls)
         self.L = lib()
+        self._allocator = allocator
         k = len(problems)
         mins = initiator_mins if initiator_mins is not None else [0] * k
         keep, arr = [], (Instance * k)()
@@ -254,6 +297,8 @@ class QMC:
                               nc, nr, C.cast(rates, C.c_void_p), C.cast(wins, C.c_void_p), nw, 0)
         cfg = Config(max(p.n for p in problems), int(sum(n_vectors)), integrator, max_ctas, 0, 1, 0, capacity_hint,
                      max_records, C.c_void_p(current_stream_handle() if stream is None else stream))
+        if allocator is not None:
+            allocator.attach(cfg)
         h = C.c_void_p()
         rc = self.L.qmc_batch_create(C.byref(h), arr, k, C.byref(cfg))
         if rc != OK:
@@ -412,6 +457,12 @@ class QMC:
                     "qmc_step_profile")
         return {self.L.qmc_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
 
+    def memory(self) -> dict:
+        """Device memory the context holds (qmc_memory)."""
+        out = np.zeros(2, dtype=np.int64)
+        self._check(self.L.qmc_memory(self.h, out.ctypes.data), "qmc_memory")
+        return {"bytes": int(out[0]), "blocks": int(out[1])}
+
     def counters(self, reset: bool = False) -> dict:
         """Cumulative device totals since the last reset (see qmc_counters)."""
         out = np.zeros(11, dtype=np.int64)
@@ -503,6 +554,21 @@ class QMC:
                     "qmc_export")
         return keys, re, im
 
+    def export_xy(self, seg: int, which: int = 0):
+        """One vector's records as (x, y, re, im) in key order (any n)."""
+        cnt = C.c_int64()
+        rc = self.L.qmc_export_xy(self.h, seg, which, None, None, None, None, 0, C.byref(cnt))
+        if rc not in (OK, ERR_INVALID_ARG):
+            self._check(rc, "qmc_export_xy")
+        n = cnt.value
+        x = np.zeros(n, dtype=np.uint64)
+        y = np.zeros(n, dtype=np.uint64)
+        re = np.zeros(n, dtype=np.int32)
+        im = np.zeros(n, dtype=np.int32)
+        self._check(self.L.qmc_export_xy(self.h, seg, which, _ptr(x), _ptr(y), _ptr(re), _ptr(im), n, C.byref(cnt)),
+                    "qmc_export_xy")
+        return x, y, re, im
+
     def overlap(self, seg: int, psi: dict) -> complex:
         idx = _arr(list(psi.keys()), np.uint64)
         vals = np.array([complex(v) for v in psi.values()])
@@ -535,17 +601,21 @@ def column_eval(prob, x: int, y: int, t: float, dt_eff: float, cap: int = 4096):
     rates = (Rate * max(1, len(prob.rates)))(*[Rate(k, 0, a, b, c) for k, a, b, c in prob.rates])
     wins = (Window * max(1, len(prob.windows)))(*[Window(a, b) for a, b in prob.windows])
     mask = np.zeros(cap, dtype=np.uint64)
+    mask_hi = np.zeros(cap, dtype=np.uint64)
     vre = np.zeros(cap, dtype=np.int64)
     vim = np.zeros(cap, dtype=np.int64)
     p = C.c_int64()
     vp = C.c_void_p
     L.qmc_column_eval.argtypes = [C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp,
                                   C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_int32, vp, vp, vp,
-                                  vp]
+                                  vp, vp]
     L.qmc_column_eval.restype = C.c_int
     ne = L.qmc_column_eval(prob.n, ham, len(prob.ham), lind, len(linds), cf, len(coefs), rates, len(prob.rates),
-                           wins, len(prob.windows), t, dt_eff, x, y, cap, mask.ctypes.data, vre.ctypes.data,
-                           vim.ctypes.data, C.byref(p))
+                           wins, len(prob.windows), t, dt_eff, x, y, cap, mask.ctypes.data, mask_hi.ctypes.data,
+                           vre.ctypes.data, vim.ctypes.data, C.byref(p))
     if ne < 0:
         raise QmcError(ne, "qmc_column_eval failed")
+    if prob.n > 32:   # masks (dx << n) | dy of 2n > 64 bits as Python ints
+        masks = np.array([(int(b) << 64) | int(a) for a, b in zip(mask[:ne], mask_hi[:ne])], dtype=object)
+        return masks, vre[:ne], vim[:ne], p.value
     return mask[:ne], vre[:ne], vim[:ne], p.value

@@ -118,10 +118,12 @@ def _union_records(sim, segs) -> int:
 
 
 def replica_study(sizes=(8, 10, 12, 14), state: str = "plus", replicas: int = 5, n_diag: int = 2 * 10**5,
-                  seed: int = 5, t_end: float = 4.0, dt: float = 0.005):
+                  seed: int = 5, t_end: float = 4.0, dt: float = 0.005, xi: float = 0.0):
     """Replica aggregation on the staggered-XX DD ring (|+>^n in the X basis
     or |W>_n): per size, r replicas of N^diag walkers; aggregates of 2 .. r
-    replicas give N^diag_eff = 2 .. r times N^diag."""
+    replicas give N^diag_eff = 2 .. r times N^diag.  xi > 0 runs with the
+    initiator (the W state in the computational basis has a sign problem at
+    these walker numbers without it)."""
     rows = []
     for n in sizes:
         if state == "plus":
@@ -130,13 +132,13 @@ def replica_study(sizes=(8, 10, 12, 14), state: str = "plus", replicas: int = 5,
         else:
             prob = P.dd_ring(n, seed=0, t_end=t_end, x_basis=False)
             rho0, target = P.rho_pure(P.w_state(n)), P.w_state(n)
-        r = run_vectors(prob, t_end, dt, replicas, n_diag, seed, rho0, target=target)
+        r = run_vectors(prob, t_end, dt, replicas, n_diag, seed, rho0, xi=xi, target=target)
         sim = r["sim"]
         ov = np.asarray(r["overlap_re"]) + 1j * np.asarray(r["overlap_im"])
         nd = np.asarray(r["n_diag_re"], dtype=np.float64)
         fid = np.abs(ov) / n_diag
         est, lo, hi = A.bootstrap_ci(fid)
-        row = {"n": n, "state": state, "replicas": replicas, "n_diag": n_diag,
+        row = {"n": n, "state": state, "replicas": replicas, "n_diag": n_diag, "xi": xi,
                "fidelity_per_replica": fid.tolist(), "fidelity_mean": float(est), "fidelity_ci95": [float(lo), float(hi)],
                "trace_per_replica": (nd / n_diag).tolist(),
                "ms": r["ms"], "walker_steps_per_s": r["walker_steps"] / (r["ms"] * 1e-3), "aggregates": []}
@@ -283,6 +285,10 @@ def main():
     ap.add_argument("--state", default="plus", choices=["plus", "w"])
     ap.add_argument("--nvec", type=int, default=16)
     ap.add_argument("--n-diag", type=int, default=0)
+    ap.add_argument("--xi", type=float, default=0.0)
+    ap.add_argument("--replicas", type=int, default=5)
+    ap.add_argument("--t-end", type=float, default=4.0,
+                    help="replicas: end time (4.5 completes the DD cycle on both sublattices)")
     args = ap.parse_args()
     import torch
     torch.cuda.init()
@@ -292,7 +298,8 @@ def main():
         res = {"rows": initiator_study(sizes, nvec=args.nvec, n_diag=args.n_diag or 10**5)}
     elif args.study == "replicas":
         sizes = tuple(int(v) for v in args.sizes.split(",")) if args.sizes else (8, 10, 12, 14)
-        res = replica_study(sizes, state=args.state, n_diag=args.n_diag or 2 * 10**5)
+        res = replica_study(sizes, state=args.state, n_diag=args.n_diag or 2 * 10**5, xi=args.xi,
+                            replicas=args.replicas, t_end=args.t_end)
     else:
         res = proposal_study(args.workload, nvec=args.nvec, n_diag=args.n_diag or 10**5, train_events=args.events)
     res["wall_s"] = time.time() - t0

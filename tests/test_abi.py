@@ -52,5 +52,8 @@ def test_invalid_config_rejected():
     import ctypes as C
     L = qmc.lib()
     h = C.c_void_p()
-    cfg = qmc.Config(40, 1, 1, 0, 1, 100, 0, 0, 0, None)   # 40 qubits: beyond the 32 supported
+    cfg = qmc.Config(61, 1, 1, 0, 1, 100, 0, 0, 0, None)   # 61 qubits: beyond the 60 supported
     assert L.qmc_create(C.byref(h), C.byref(cfg)) == qmc.ERR_INVALID_ARG
+    cfg = qmc.Config(8, 1, 1, 0, 1, 100, 0, 0, 0, None)
+    cfg.alloc = qmc.ALLOC_FN(lambda b, s, u: None)         # an allocator without its free
+    assert L.qmc_create(C.byref(h), C.byref(cfg)) in (qmc.ERR_INVALID_ARG, qmc.ERR_CUDA)

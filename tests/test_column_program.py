@@ -63,3 +63,41 @@ def test_time_dependent_negative_rates():
         for _ in range(20):
             x, y = int(rng.integers(0, 64)), int(rng.integers(0, 64))
             _compare(prob, x, y, t, 0.01)
+
+
+@pytest.mark.parametrize("n", [33, 40, 60])
+def test_wide_programs_match_oracle(n):
+    """Above 32 qubits (64-bit masks, 128-bit destination keys): the compiled
+    program against the oracle's column, at random states whose bits fill all
+    n qubits."""
+    from test_oracle_wide import embed_problem
+    rng = np.random.default_rng(n)
+    pos = sorted(int(v) for v in rng.choice(n, size=4, replace=False))
+    prob = embed_problem(random_problem(4, n), n, pos)
+    for _ in range(24):
+        x, y = int(rng.integers(0, 1 << n)), int(rng.integers(0, 1 << n))
+        op = O.OracleProblem(prob)
+        m_o, re_o, im_o = op.column(x, y, 0.3, 2.0**-7)
+        keep = (re_o != 0) | (im_o != 0)
+        m_l, re_l, im_l, P_l = qmc.column_eval(prob, x, y, 0.3, 2.0**-7)
+        keep_l = (re_l != 0) | (im_l != 0)
+        assert [int(v) for v in m_l[keep_l]] == [int(v) for v in m_o[keep]]
+        assert list(re_l[keep_l]) == list(re_o[keep]) and list(im_l[keep_l]) == list(im_o[keep])
+        assert [int(v) for v in m_l] == sorted(int(v) for v in m_l)
+        assert P_l == int(np.abs(re_o).sum() + np.abs(im_o).sum())
+    ghz = P.ghz_circuit(n)
+    for t in (0.5, 1.5, 2.5, float(n) - 0.5):
+        for _ in range(6):
+            x, y = int(rng.integers(0, 1 << n)), int(rng.integers(0, 1 << n))
+            _compare_wide(ghz, x, y, t, 0.01)
+
+
+def _compare_wide(prob, x, y, t, dte):
+    op = O.OracleProblem(prob)
+    m_o, re_o, im_o = op.column(x, y, t, dte)
+    keep = (re_o != 0) | (im_o != 0)
+    m_l, re_l, im_l, P_l = qmc.column_eval(prob, x, y, t, dte)
+    keep_l = (re_l != 0) | (im_l != 0)
+    assert [int(v) for v in m_l[keep_l]] == [int(v) for v in m_o[keep]], (x, y, t)
+    assert list(re_l[keep_l]) == list(re_o[keep]) and list(im_l[keep_l]) == list(im_o[keep])
+    assert P_l == int(np.abs(re_o).sum() + np.abs(im_o).sum())
