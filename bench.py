@@ -69,12 +69,18 @@ def workload(name: str):
     if name.startswith("ghz") and name[3:].isdigit():
         n = int(name[3:])
         prob = P.ghz_circuit(n)
-        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8}.get(n, 10**7)
+        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8, 40: 10**8}.get(n, 10**7)
         return dict(name=name, desc=f"GHZ-{n} preparation", prob=prob, nseg=16, n_diag=total // 16, dt=0.01,
                     t_end=float(n), rho0=P.rho_basis(0))
     if name == "spread32":
         prob = P.ghz_circuit(32)
         return dict(name="spread32", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "
+                    "1e8 distinct random states x 1 walker over 64 vectors",
+                    prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
+                    spread=10**8 // 64, default_steps=10)
+    if name == "spread40":
+        prob = P.ghz_circuit(40)
+        return dict(name="spread40", desc="GHZ-40 Liouvillian (CNOT 4->5 window + local noise), 128-bit keys, "
                     "1e8 distinct random states x 1 walker over 64 vectors",
                     prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
                     spread=10**8 // 64, default_steps=10)
@@ -87,7 +93,7 @@ def workload(name: str):
     if name.startswith("ghz") and name.endswith("i") and name[3:-1].isdigit():
         n = int(name[3:-1])
         prob = P.ghz_circuit(n)
-        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8}.get(n, 10**7)
+        total = {16: 10**7, 24: 5 * 10**7, 32: 10**8, 40: 10**8}.get(n, 10**7)
         return dict(name=name, desc=f"GHZ-{n} preparation, initiator xi = 1e-3", prob=prob, nseg=16,
                     n_diag=total // 16, dt=0.01, t_end=float(n), rho0=P.rho_basis(0), xi=1e-3)
     raise SystemExit(f"unknown workload {name}")
@@ -98,10 +104,11 @@ def capacity_hint(wl, nsteps: int) -> int:
     state: the records grow by about 1.3 % of the initial count per step in
     the CNOT window (new keys reached by spawns), so size for 2 % per step
     plus a quarter, and no buffer has to grow (and a step be redone) inside
-    the timed region.  0 (library default) for workloads that start from a
-    single state and grow as they go."""
+    the timed region.  Workloads that start from a single state get one
+    record per walker (a vector never holds more records than walkers, up to
+    the spawns of one step)."""
     if "spread" not in wl:
-        return 0
+        return int(wl["n_diag"] * wl["nseg"] * 1.2)
     base = wl["spread"] * wl["nseg"]
     return int(base * (1.0 + 0.02 * nsteps) * 1.25)
 
@@ -123,6 +130,12 @@ def host_inputs(wl, rank):
     import torch
     if "spread" not in wl:
         return None
+    if wl["prob"].n > 32:
+        pops = [P.spread_population_xy(wl["prob"].n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
+        counts = np.array([len(p[0]) for p in pops], dtype=np.int64)
+        cat = [torch.from_numpy(np.concatenate([p[k] for p in pops]).view(np.int64 if k < 2 else np.int32))
+               .pin_memory() for k in range(4)]
+        return ("xy", counts, *cat)
     pops = [P.spread_population(wl["prob"].n, wl["spread"], 10 * s + rank) for s in range(wl["nseg"])]
     counts = np.array([len(p[0]) for p in pops], dtype=np.int64)
     keys = torch.from_numpy(np.concatenate([p[0] for p in pops]).view(np.int64)).pin_memory()
@@ -136,6 +149,12 @@ def load_inputs(sim, wl, inputs):
     if inputs is None:
         sim.init_populations(wl["rho0"])
         return len(wl["rho0"]) * 32
+    if isinstance(inputs[0], str):   # ("xy", ...): more than 32 qubits, states as bit strings
+        _, counts, x, y, re, im = inputs
+        sim.set_populations_xy(counts, x.numpy().view(np.uint64), y.numpy().view(np.uint64), re.numpy(),
+                               im.numpy())
+        sim.set_clock(0, wl["t_start"])
+        return int(x.numel() * 16 + re.numel() * 8 + counts.nbytes)
     counts, keys, re, im = inputs
     sim.set_populations_packed(counts, keys.numpy().view(np.uint64), re.numpy(), im.numpy())
     sim.set_clock(0, wl["t_start"])
@@ -375,7 +394,8 @@ def run_gpu(args, rank: int, world: int):
     nkeys_start = int(sim.observables()[:, 0].sum())
 
     ck_path = None
-    if not args.no_profile:
+    wide = prob.n > 32
+    if not args.no_profile and not wide:
         import tempfile
         ck_path = os.path.join(tempfile.gettempdir(), f"qmc_bench_ck_{os.getpid()}_{rank}.bin")
         sim.checkpoint(ck_path)
@@ -444,6 +464,34 @@ def run_gpu(args, rank: int, world: int):
                 "units_per_launch": {k: round(v) for k, v in unit_counts.items()},
                 "kernel_share": {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}}
 
+    if wide:
+        # the whole step against the bytes it cannot avoid, 24-byte records
+        # read by the spawn pass (N(t), N(t - dt)) and the merge (N(t)), spawns
+        # written and read once, N(t + dt) written; the kernel groups' shares
+        # from three further steps replayed under events
+        peak, peak_kind = load_peaks()
+        if not args.no_profile and W + K + 3 <= total:
+            idx = 0
+            for t0, d, n in pl:
+                lo, hi = idx, idx + n
+                idx = hi
+                a, b = max(lo, W + K), min(hi, W + K + 3)
+                if a >= b:
+                    continue
+                if a == lo:
+                    step, _, tp, dl, pv = sim.clock()
+                    sim.set_clock(step, t0, tp, dl, pv)
+                for name, v in sim.step_profile(d, b - a).items():
+                    kernel_ms[name] = kernel_ms.get(name, 0.0) + v
+        steps = max(1, c["steps"])
+        bytes_step = 24.0 * (2 * c["k_cur"] + c["k_prev"] + 2 * c["spawns"] + c["k_next"]) / steps
+        achieved = bytes_step / (ms / K * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "whole step (128-bit keys)", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_step": round(bytes_step)}
+        if kernel_ms:
+            roof["kernel_share"] = {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}
+
     # end to end through the public API: a fresh context, inputs uploaded from
     # pinned host memory, every step, and a D2H read of each call's per-step
     # observables (the step's result), timed on the host clock
@@ -462,7 +510,7 @@ def run_gpu(args, rank: int, world: int):
     if rank != 0:
         return
     value = walkers_all / (ms_all * 1e-3)
-    ws = 3 * c["k_next"] / max(1, c["steps"]) * 16 * (world if world > 1 else 1)
+    ws = 3 * c["k_next"] / max(1, c["steps"]) * (24 if wide else 16) * (world if world > 1 else 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_all / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -638,8 +686,8 @@ def oracle_vector(name: str, vec: int, budget_s: float):
     prob = wl["prob"]
     sim = O.OracleSim(prob, 1, 1000 + vec, integrator=O.AB2, n_diag=wl["n_diag"])
     if "spread" in wl:
-        k, r, i = P.spread_population(prob.n, min(wl["spread"], CPU_SAMPLE_STATES), 10 * vec)
-        sim.set_population(0, k, r, i)
+        x, y, r, i = P.spread_population_xy(prob.n, min(wl["spread"], CPU_SAMPLE_STATES), 10 * vec)
+        sim.set_population_xy(0, x, y, r, i)
         sim.set_clock(0, wl["t_start"])
     else:
         sim.init(wl["rho0"])

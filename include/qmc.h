@@ -337,6 +337,12 @@ int qmc_init_populations(qmc_ctx* ctx, const uint64_t* x, const uint64_t* y,
 int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts,
                         const uint64_t* keys, const int32_t* re, const int32_t* im);
 
+/* qmc_set_populations with states given as bit strings (any n): record i of
+ * the concatenated host arrays is (re[i] + i im[i]) |x[i]><y[i]|, (x, y)
+ * ascending within each vector.  Errors as qmc_set_populations. */
+int qmc_set_populations_xy(qmc_ctx* ctx, int32_t which, const int64_t* counts, const uint64_t* x,
+                           const uint64_t* y, const int32_t* re, const int32_t* im);
+
 /* Set the clock: global step index (keys the random stream), t of N(t), and,
  * for AB2, the time and step size of the previous step.  prev_valid = 0 makes
  * the next step Euler. */
@@ -376,6 +382,10 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
  * a step still launch and are counted.  Errors: INVALID_ARG. */
 int qmc_step_launches(const qmc_ctx* ctx, int32_t* launches);
 const char* qmc_kernel_name(int32_t i);
+
+/* Name of entry i of qmc_step_profile's output for this context (above 32
+ * qubits the entries are groups of the wide step's kernels). */
+const char* qmc_step_kernel_name(const qmc_ctx* ctx, int32_t i);
 
 /* Launch shapes of the step (not in the paper; results never depend on
  * them: every draw is keyed by step, vector, key and walker, and the heavy

@@ -119,8 +119,9 @@ struct qmc_ctx {
     qmc::WRun* d_wrun = nullptr;
     int32_t* d_wflag_u = nullptr;
     int64_t* d_wscan_u = nullptr;
-    qmc::WAux* d_waux = nullptr;
-    int32_t* d_wflag_a = nullptr;
+    int2* d_wdelta = nullptr;
+    int32_t* d_wnewcnt = nullptr;
+    int64_t* d_wcnt_a = nullptr;
     int64_t* d_wscan_a = nullptr;
     int64_t* d_wpart = nullptr;
     int64_t wpart_cap = 0;

@@ -1271,12 +1271,12 @@ __device__ void tc_forward(const uint8_t* sw, const TcLayout& L, int n, uint32_t
     }
 }
 
-// Per program (pass): each static slot's network output (-1: none, or the
-// slot's width is 0), width and static part S_k = floor(eps s_k / p_att 2^24).
+// Per program (pass): each static slot's network output (-1: none; -2: the
+// slot has width 0 and is never chosen) and its static part S_k = floor(eps
+// s_k / p_att 2^24) (< 2^24).
 struct TcSlots {
     int16_t out[kMaxLearnedSlots];
-    int64_t width[kMaxLearnedSlots];
-    int64_t st[kMaxLearnedSlots];
+    int32_t st[kMaxLearnedSlots];
 };
 
 __device__ void tc_slots_fill(const StepParams& P, const Prog& prog, TcSlots* s, int tid, int nthr)
@@ -1284,10 +1284,9 @@ __device__ void tc_slots_fill(const StepParams& P, const Prog& prog, TcSlots* s,
     const int64_t p_att = prog.h->p_att;
     for (int k = tid; k < prog.h->n_stat; k += nthr) {
         const int64_t w = slot_width(prog, k);
-        s->width[k] = w;
-        s->out[k] = (int16_t)(w > 0 ? lp_output(P, prog.stat[k].mask) : -1);
+        s->out[k] = (int16_t)(w > 0 ? lp_output(P, prog.stat[k].mask) : -2);
         s->st[k] = (w > 0 && p_att > 0 && p_att < (1ll << 52))
-                       ? (int64_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)P.mlp_eps, (double)w), (double)p_att),
+                       ? (int32_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)P.mlp_eps, (double)w), (double)p_att),
                                                   16777216.0))
                        : 0;
     }
@@ -1295,23 +1294,22 @@ __device__ void tc_slots_fill(const StepParams& P, const Prog& prog, TcSlots* s,
 
 // The weights Q_k of one source from its logits lg (by output; overwritten
 // with the exponentials by tc_row_prepare): m = max over the slots with an
-// output, e = exp(z - m), S = sum e in slot order, L_k = floor((1 - eps) e /
-// S 2^24), Q_k = max(1, L_k + S_k) on slots of positive width, the first
-// largest absorbing 2^24 - sum Q.  One thread per source; the light and the
-// heavy kernels share these two functions, so a parent's Q is the same on
+// output, e = exp(z - m), S = (sum of e over the even slots, in order) + (the
+// same over the odd slots), c = (1 - eps) 2^24 / S,
+// L_k = floor(e_k c), Q_k = max(1, L_k + S_k) on slots of positive width, the
+// first largest absorbing 2^24 - sum Q.  One thread per source; the light and
+// the heavy kernels share these functions, so a parent's Q is the same on
 // either path.
 struct TcRow {
-    float S;
+    float c;
     int arg;
     int64_t rem;
 };
 
-__device__ __forceinline__ int64_t tc_q(const float* lg, const TcSlots* s, int k, float S, float eps)
+__device__ __forceinline__ int64_t tc_q(const float* lg, const TcSlots* s, int k, float c)
 {
     const int o = s->out[k];
-    int64_t L = 0;
-    if (o >= 0 && S > 0.0f)
-        L = (int64_t)floorf(__fmul_rn(__fmul_rn(__fsub_rn(1.0f, eps), __fdiv_rn(lg[o], S)), 16777216.0f));
+    const int64_t L = o >= 0 ? (int64_t)floorf(__fmul_rn(lg[o], c)) : 0;
     const int64_t Q = L + s->st[k];
     return Q < 1 ? 1 : Q;
 }
@@ -1321,27 +1319,28 @@ __device__ TcRow tc_row_prepare(float* lg, const TcSlots* s, int ns, float eps)
     float m = -INFINITY;
     for (int k = 0; k < ns; ++k)
         if (s->out[k] >= 0) m = fmaxf(m, lg[s->out[k]]);
-    float S = 0.0f;
+    float Sh[2] = {0.0f, 0.0f};
     for (int k = 0; k < ns; ++k) {
         const int o = s->out[k];
         if (o < 0) continue;
         const float e = expf(__fsub_rn(lg[o], m));
         lg[o] = e;
-        S = __fadd_rn(S, e);
+        Sh[k & 1] = __fadd_rn(Sh[k & 1], e);
     }
+    const float S = __fadd_rn(Sh[0], Sh[1]);
+    TcRow r;
+    r.c = S > 0.0f ? __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, eps), 16777216.0f), S) : 0.0f;
     int64_t sum = 0, qa = -1;
     int arg = -1;
     for (int k = 0; k < ns; ++k) {
-        if (s->width[k] <= 0) continue;
-        const int64_t Q = tc_q(lg, s, k, S, eps);
+        if (s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c);
         sum += Q;
         if (Q > qa) {
             qa = Q;
             arg = k;
         }
     }
-    TcRow r;
-    r.S = S;
     r.arg = arg;
     r.rem = (1ll << 24) - sum;
     return r;
@@ -1349,13 +1348,12 @@ __device__ TcRow tc_row_prepare(float* lg, const TcSlots* s, int ns, float eps)
 
 // The slot whose interval [cum_{k-1}, cum_k) of the weights holds V (ns when
 // none does) and its weight *Qk.
-__device__ int tc_row_choose(const float* lg, const TcSlots* s, int ns, float eps, const TcRow& r, uint32_t V,
-                             int64_t* Qk)
+__device__ int tc_row_choose(const float* lg, const TcSlots* s, int ns, const TcRow& r, uint32_t V, int64_t* Qk)
 {
     int64_t cum = 0;
     for (int k = 0; k < ns; ++k) {
-        if (s->width[k] <= 0) continue;
-        const int64_t Q = tc_q(lg, s, k, r.S, eps) + (k == r.arg ? r.rem : 0);
+        if (s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c) + (k == r.arg ? r.rem : 0);
         cum += Q;
         if ((int64_t)V < cum) {
             *Qk = Q;
@@ -1364,6 +1362,86 @@ __device__ int tc_row_choose(const float* lg, const TcSlots* s, int ns, float ep
     }
     *Qk = 0;
     return ns;
+}
+
+// The same weights and choice for the rows of a 16-row logit tile, two lanes
+// per row (lane r and lane r + 16 take the even and the odd slots of row
+// r = lane & 15): the max and the integer sums do not depend on the order,
+// and the float sum is the even slots' sum plus the odd slots', as in
+// tc_row_prepare.  Every lane runs the same number of iterations (nsmax, the
+// larger slot count of the two passes); act = the row is in use.
+__device__ TcRow tc_pair_prepare(float* lg, const TcSlots* s, int ns, int nsmax, float eps, bool act, int half)
+{
+    float m = -INFINITY;
+    for (int k = half; k < nsmax; k += 2)
+        if (act && k < ns && s->out[k] >= 0) m = fmaxf(m, lg[s->out[k]]);
+    m = fmaxf(m, __shfl_xor_sync(kFull, m, 16));
+    float S = 0.0f;
+    for (int k = half; k < nsmax; k += 2) {
+        if (!act || k >= ns) continue;
+        const int o = s->out[k];
+        if (o < 0) continue;
+        const float e = expf(__fsub_rn(lg[o], m));
+        lg[o] = e;
+        S = __fadd_rn(S, e);
+    }
+    const float So = __shfl_xor_sync(kFull, S, 16);
+    const float St = half ? __fadd_rn(So, S) : __fadd_rn(S, So);
+    TcRow r;
+    r.c = St > 0.0f ? __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, eps), 16777216.0f), St) : 0.0f;
+    int64_t sum = 0, qa = -1;
+    int arg = -1;
+    for (int k = half; k < nsmax; k += 2) {
+        if (!act || k >= ns || s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c);
+        sum += Q;
+        if (Q > qa) {
+            qa = Q;
+            arg = k;
+        }
+    }
+    sum += __shfl_xor_sync(kFull, sum, 16);
+    const int64_t qo = __shfl_xor_sync(kFull, qa, 16);
+    const int ao = __shfl_xor_sync(kFull, arg, 16);
+    if (qo > qa || (qo == qa && ao >= 0 && (arg < 0 || ao < arg))) {
+        qa = qo;
+        arg = ao;
+    }
+    r.arg = arg;
+    r.rem = (1ll << 24) - sum;
+    return r;
+}
+
+__device__ int tc_pair_choose(const float* lg, const TcSlots* s, int ns, int nsmax, const TcRow& r, uint32_t V,
+                              bool act, int half, int64_t* Qk)
+{
+    int64_t cum = 0, qf = 0;
+    int found = act ? -1 : ns;
+    for (int i = 0; 2 * i < nsmax; ++i) {
+        const int k = 2 * i + half;
+        int64_t q = 0;
+        if (found < 0 && k < ns && s->out[k] != -2) q = tc_q(lg, s, k, r.c) + (k == r.arg ? r.rem : 0);
+        const int64_t qp = __shfl_xor_sync(kFull, q, 16);
+        const int64_t qe = half ? qp : q, qd = half ? q : qp;
+        if (found < 0) {
+            if ((int64_t)V < cum + qe) {
+                found = 2 * i;
+                qf = qe;
+            } else if ((int64_t)V < cum + qe + qd) {
+                found = 2 * i + 1;
+                qf = qd;
+            } else {
+                cum += qe + qd;
+            }
+        }
+        if (__all_sync(kFull, found >= 0)) break;
+    }
+    if (found < 0 || found >= ns) {
+        *Qk = 0;
+        return ns;
+    }
+    *Qk = qf;
+    return found;
 }
 
 // Light parents under the tensor-core proposal: each warp takes 16
@@ -1427,15 +1505,22 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_spawn_learned_tc(StepParams P
         __syncwarp();
         SRec rec[2];
         bool ok[2] = {false, false};
+        // the rows' weights and choices, two lanes per row
+        uint32_t V = 0u;
+        double u[2] = {0.0, 0.0};
+        if (att) lp_draws(key, phase, comp, j, P.kd[seg], &V, &u[0], &u[1]);
+        const int r = lane & 15, half = lane >> 4;
+        const bool ract = __shfl_sync(kFull, att, r);
+        const int rph = __shfl_sync(kFull, phase, r);
+        const uint32_t rV = __shfl_sync(kFull, V, r);
+        const int rns = prog[rph].h->n_stat;
+        const int nsmax = max(prog[0].h->n_stat, prog[1].h->n_stat);
+        float* rlg = lgt + r * ldo;
+        const TcRow tr = tc_pair_prepare(rlg, slots + rph, rns, nsmax, P.mlp_eps, ract, half);
+        int64_t Qk;
+        const int k = tc_pair_choose(rlg, slots + rph, rns, nsmax, tr, rV, ract, half, &Qk);
         if (att) {
             const Prog& pg = prog[phase];
-            uint32_t V;
-            double u[2];
-            lp_draws(key, phase, comp, j, P.kd[seg], &V, &u[0], &u[1]);
-            int64_t Qk;
-            float* lg = lgt + lane * ldo;
-            const TcRow tr = tc_row_prepare(lg, slots + phase, pg.h->n_stat, P.mlp_eps);
-            const int k = tc_row_choose(lg, slots + phase, pg.h->n_stat, P.mlp_eps, tr, V, &Qk);
             if (k < pg.h->n_stat) {
                 int64_t v[2];
                 value_at_mask(pg, pg.stat[k].mask, x, y, &v[0], &v[1]);
@@ -1594,7 +1679,7 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
                 const TcRow r = tc_row_prepare(hlg, hslots, ns, P.mlp_eps);
                 int64_t run = 0;
                 for (int k = 0; k < ns; ++k) {
-                    if (hslots->width[k] > 0) run += tc_q(hlg, hslots, k, r.S, P.mlp_eps) + (k == r.arg ? r.rem : 0);
+                    if (hslots->out[k] != -2) run += tc_q(hlg, hslots, k, r.c) + (k == r.arg ? r.rem : 0);
                     cum[k] = run;
                 }
             }

@@ -165,7 +165,7 @@ constexpr int kNumTimedKernels = 15;
 // ---- the step for 33..60 qubits (128-bit keys, wide.cu) ----------------------
 constexpr int kWMaxPasses = 20;      // 8-bit digits of (vector, key): up to 2 * 60 + 28 bits
 constexpr int kWTile = 4096;         // records per tile of the radix sort's scatter
-constexpr int kWChunk = 1024;        // extra draw calls (four walkers each) per heavy work item
+constexpr int kWChunk = 4096;        // extra draw calls (four walkers each) per heavy work item
 constexpr int kWLight = 64;          // parents with more walkers take the heavy path
 constexpr int kWScanTile = 2048;     // flags per tile of the survivors' prefix sums
 
@@ -179,12 +179,6 @@ struct WRun {
     int32_t matched, pad;
 };
 
-// Per record of N(t): the first sorted spawn at or after its key (lbS) and
-// its value after annihilation.
-struct WAux {
-    int64_t lbS;
-    int32_t re, im;
-};
 
 struct WideParams {
     WSpawn* spawn;          // unsorted spawns (sort ping-pong A)
@@ -192,9 +186,11 @@ struct WideParams {
     WRun* run;              // [spawn_cap]
     int32_t* flag_u;        // [spawn_cap]: run head whose key is new to N(t + dt)
     int64_t* scan_u;        // [spawn_cap + 1]
-    WAux* aux;              // [pop_cap]
-    int32_t* flag_a;        // [pop_cap]: record of N(t) that survives
-    int64_t* scan_a;        // [pop_cap + 1]
+    int2* delta;            // [pop_cap + 1]: per record of N(t) the spawn sum of the run on its key
+                            //   (zero otherwise), then its value after annihilation; zero between steps
+    int32_t* newcnt;        // [pop_cap + 1]: new keys inserted just before record i; zero between steps
+    int64_t* cnt_a;         // [pop_cap + 1]: survives | newcnt << 32
+    int64_t* scan_a;        // [pop_cap + 2]: exclusive prefix sums of cnt_a (both halves), total last
     int64_t* part;          // scan partials
     int64_t part_cap;
     uint32_t* hist;         // [kWMaxPasses][256] digit counts, then digit starts
@@ -205,11 +201,16 @@ struct WideParams {
 };
 
 void configure_wide_kernels();   // once per process, before the first capture of a wide step
-void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t stream);
+// ev (optional): kNumWideGroups + 1 events; kernel group i runs between ev[i] and ev[i + 1].
+constexpr int kNumWideGroups = 9;
+extern const char* const kWideGroupNames[kNumWideGroups];
+void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int wide_step_launch_count(const StepParams& P, const WideParams& W);
 void launch_wide_init(const StepParams& P, const uint64_t* xs, const uint64_t* ys, const double* re,
                       const double* im, int64_t nnz, int64_t* vals, cudaStream_t stream);
 void launch_wide_obs(const StepParams& P, int which, SegStats* out, cudaStream_t stream);
+void launch_wide_pack(const uint64_t* xs, const uint64_t* ys, const int32_t* re, const int32_t* im,
+                      const int64_t* off, int nseg, const SegInfo* seginfo, WRec* dst, int* bad, cudaStream_t stream);
 void launch_wide_lookup(const StepParams& P, int seg, const uint64_t* qx, const uint64_t* qy, int nq, int64_t* out,
                         cudaStream_t stream);
 void launch_wide_export(const StepParams& P, int slot, int64_t first, int64_t count, uint64_t* x, uint64_t* y,

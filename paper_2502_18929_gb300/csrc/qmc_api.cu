@@ -241,8 +241,9 @@ WideParams wparams(qmc_ctx* c)
     W.run = c->d_wrun;
     W.flag_u = c->d_wflag_u;
     W.scan_u = c->d_wscan_u;
-    W.aux = c->d_waux;
-    W.flag_a = c->d_wflag_a;
+    W.delta = c->d_wdelta;
+    W.newcnt = c->d_wnewcnt;
+    W.cnt_a = c->d_wcnt_a;
     W.scan_a = c->d_wscan_a;
     W.part = c->d_wpart;
     W.part_cap = c->wpart_cap;
@@ -331,7 +332,6 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
 
 int grow_cand(qmc_ctx* ctx, int64_t need)
 {
-    if (ctx->wide) return QMC_OK;   // the wide step has no candidate list
     const int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
     int rc;
     if ((rc = dalloc(ctx, &ctx->d_cand, cap)) != QMC_OK) return rc;
@@ -380,9 +380,13 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
     ctx->graph_dirty = true;
     if (ctx->wide) {
         int rc;
-        if ((rc = dalloc(ctx, &ctx->d_waux, cap)) != QMC_OK || (rc = dalloc(ctx, &ctx->d_wflag_a, cap)) != QMC_OK ||
-            (rc = dalloc(ctx, &ctx->d_wscan_a, cap + 1)) != QMC_OK)
+        if ((rc = dalloc(ctx, &ctx->d_wdelta, cap + 1)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wnewcnt, cap + 1)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wcnt_a, cap + 1)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wscan_a, cap + 2)) != QMC_OK)
             return rc;
+        CK(cudaMemsetAsync(ctx->d_wdelta, 0, (size_t)(cap + 1) * sizeof(int2), ctx->work));
+        CK(cudaMemsetAsync(ctx->d_wnewcnt, 0, (size_t)(cap + 1) * sizeof(int32_t), ctx->work));
         return grow_wpart(ctx);
     }
     return grow_merge_tiles(ctx);
@@ -514,7 +518,8 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     if ((rc = dalloc(ctx, &ctx->d_segacc, nseg)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_zacc, 32 * (int64_t)nseg)) != QMC_OK) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_obs, nseg)) != QMC_OK) return bail(rc);
-    ctx->heavy_cap = 4096;
+    // heavy work items: at most one per 64 records of the hinted capacity to start with
+    ctx->heavy_cap = std::max<int64_t>(4096, cfg->capacity_hint / 64);
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
     if (ctx->wide && ((rc = dalloc(ctx, &ctx->d_whist, kWMaxPasses * 256)) != QMC_OK ||
                       (rc = dalloc(ctx, &ctx->d_wplan, kWMaxPasses + 1)) != QMC_OK))
@@ -1192,6 +1197,78 @@ int qmc_set_populations(qmc_ctx* ctx, int32_t which, const int64_t* counts, cons
     return leave(ctx);
 }
 
+int qmc_set_populations_xy(qmc_ctx* ctx, int32_t which, const int64_t* counts, const uint64_t* x,
+                           const uint64_t* y, const int32_t* re, const int32_t* im)
+{
+    if (!ctx || (which != 0 && which != 1) || !counts) return QMC_ERR_INVALID_ARG;
+    const int nseg = ctx->cfg.n_segments;
+    std::vector<int64_t> off(nseg + 1, 0);
+    for (int s = 0; s < nseg; ++s) {
+        if (counts[s] < 0) return fail(ctx, QMC_ERR_INVALID_ARG, "negative count");
+        off[s + 1] = off[s] + counts[s];
+    }
+    const int64_t total = off[nseg];
+    if (total > 0 && (!x || !y || !re || !im)) return fail(ctx, QMC_ERR_INVALID_ARG, "null arrays");
+    if (!ctx->wide) {
+        // 64-bit keys: (x << n) | y per vector, then the key-based call
+        std::vector<uint64_t> keys((size_t)std::max<int64_t>(total, 1));
+        for (int s = 0; s < nseg; ++s) {
+            const int n = instance_of(ctx, s).n;
+            const uint64_t lim = (1ull << n) - 1ull;
+            for (int64_t i = off[s]; i < off[s + 1]; ++i) {
+                if ((x[i] & ~lim) || (y[i] & ~lim)) return fail(ctx, QMC_ERR_INVALID_ARG, "x or y >= 2^n");
+                keys[i] = (x[i] << n) | y[i];
+            }
+        }
+        return qmc_set_populations(ctx, which, counts, keys.data(), re, im);
+    }
+    int rc;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    if (total > ctx->pop_cap && (rc = grow_pop(ctx, total)) != QMC_OK) return rc;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    const int slot = which == 0 ? hs.cur : (hs.cur + 2) % 3;
+    uint64_t *d_x = nullptr, *d_y = nullptr;
+    int32_t *d_re = nullptr, *d_im = nullptr;
+    int* d_bad = nullptr;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_x, total)) != QMC_OK || (rc = tmp.get(&d_y, total)) != QMC_OK ||
+        (rc = tmp.get(&d_re, total)) != QMC_OK || (rc = tmp.get(&d_im, total)) != QMC_OK ||
+        (rc = tmp.get(&d_bad, 1)) != QMC_OK)
+        return rc;
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), ctx->work));
+    if (total) {
+        CK(cudaMemcpyAsync(d_x, x, total * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_y, y, total * 8, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_re, re, total * 4, cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaMemcpyAsync(d_im, im, total * 4, cudaMemcpyHostToDevice, ctx->work));
+    }
+    CK(cudaMemcpyAsync(ctx->d_segoff[slot], off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+    if (total)
+        launch_wide_pack(d_x, d_y, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->d_seginfo, (WRec*)ctx->d_pop[slot],
+                         d_bad, ctx->work);
+    CK(cudaGetLastError());
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    if (bad) {
+        std::vector<int64_t> zero(nseg + 1, 0);
+        CK(cudaMemcpyAsync(ctx->d_segoff[slot], zero.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
+        hs.count[slot] = 0;
+        CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        return fail(ctx, QMC_ERR_INVALID_ARG,
+                    "records must be nonzero, x, y < 2^n and (x, y) strictly ascending within each vector");
+    }
+    hs.count[slot] = total;
+    hs.error = 0;
+    CK(cudaMemcpyAsync(ctx->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    if (which == 0) ctx->has_pop = true;
+    return leave(ctx);
+}
+
 int qmc_set_clock(qmc_ctx* ctx, uint64_t step, double t, double t_prev, double dt_last, int32_t prev_valid)
 {
     if (!ctx) return QMC_ERR_INVALID_ARG;
@@ -1311,6 +1388,11 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         if (!hs.error) break;
         const uint32_t code = hs.error;
         if ((rc = clear_dev_error(ctx)) != QMC_OK) return rc;
+        if (ctx->wide) {
+            // a failed wide step may have left merge scratch behind: zero it for the redo
+            CK(cudaMemsetAsync(ctx->d_wdelta, 0, (size_t)(ctx->pop_cap + 1) * sizeof(int2), ctx->work));
+            CK(cudaMemsetAsync(ctx->d_wnewcnt, 0, (size_t)(ctx->pop_cap + 1) * sizeof(int32_t), ctx->work));
+        }
         if (code == DERR_SPAWN_CAPACITY) {
             if ((rc = grow_spawn(ctx, hs.spawn_total)) != QMC_OK) return rc;
             if ((rc = grow_merge_tiles(ctx)) != QMC_OK) return rc;
@@ -1362,6 +1444,12 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     }
     if (hs.max_cand > ctx->cand_cap * 3 / 4)
         if ((rc = grow_cand(ctx, hs.max_cand * 2)) != QMC_OK) return rc;
+    if (hs.max_heavy > ctx->heavy_cap * 3 / 4) {
+        const int64_t cap = hs.max_heavy * 2;
+        if ((rc = dalloc(ctx, &ctx->d_heavy, cap)) != QMC_OK) return rc;
+        ctx->heavy_cap = cap;
+        ctx->graph_dirty = true;
+    }
     if (hs.max_next > ctx->pop_cap * 3 / 4 && (ctx->cfg.max_records == 0 || ctx->pop_cap < ctx->cfg.max_records))
         if ((rc = grow_pop(ctx, hs.max_next * 2)) != QMC_OK) return rc;
     return leave(ctx);
@@ -1848,14 +1936,14 @@ extern "C" {
 
 int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms, int32_t cap, int32_t* n_kernels)
 {
-    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_step_profile: not available above 32 qubits");
     if (!ctx || !kernel_ms || !n_kernels || cap < 0) return QMC_ERR_INVALID_ARG;
     if (!has_schedules(ctx) || !ctx->has_pop) return fail(ctx, QMC_ERR_STATE, "load a schedule and populations first");
     if (!(dt > 0.0) || nsteps < 1) return fail(ctx, QMC_ERR_INVALID_ARG, "dt must be > 0 and nsteps >= 1");
-    *n_kernels = kNumTimedKernels;
-    for (int i = 0; i < cap && i < kNumTimedKernels; ++i) kernel_ms[i] = 0.0;
-    cudaEvent_t ev[kNumTimedKernels + 1];
-    for (int i = 0; i <= kNumTimedKernels; ++i) CK(cudaEventCreate(&ev[i]));
+    const int nk = ctx->wide ? kNumWideGroups : kNumTimedKernels;
+    *n_kernels = nk;
+    for (int i = 0; i < cap && i < nk; ++i) kernel_ms[i] = 0.0;
+    cudaEvent_t ev[kNumTimedKernels + kNumWideGroups + 1];
+    for (int i = 0; i <= nk; ++i) CK(cudaEventCreate(&ev[i]));
     int rc = QMC_OK;
     for (int64_t s = 0; s < nsteps && rc == QMC_OK; ++s) {
         // one ordinary step first, so programs, capacities and the clock are handled as in qmc_step
@@ -1873,7 +1961,10 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
         CK(cudaMemcpyAsync(ctx->d_state, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->work));
         StepParams P = params(ctx);
         if ((rc = note_launches(ctx, 1)) != QMC_OK) break;
-        launch_step(P, ctx->grid, ctx->work, ev);
+        if (ctx->wide)
+            launch_wide_step(P, wparams(ctx), ctx->work, ev);
+        else
+            launch_step(P, ctx->grid, ctx->work, ev);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->work));
         DevState after;
@@ -1889,13 +1980,13 @@ int qmc_step_profile(qmc_ctx* ctx, double dt, int64_t nsteps, double* kernel_ms,
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + acc0, (const uint8_t*)&hs + acc0, acc1 - acc0,
                            cudaMemcpyHostToDevice, ctx->work));
         CK(cudaStreamSynchronize(ctx->work));
-        for (int i = 0; i < kNumTimedKernels && i < cap; ++i) {
+        for (int i = 0; i < nk && i < cap; ++i) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
             kernel_ms[i] += ms;
         }
     }
-    for (int i = 0; i <= kNumTimedKernels; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i <= nk; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 
@@ -1911,6 +2002,12 @@ const char* qmc_kernel_name(int32_t i)
 {
     if (i < 0 || i >= kNumTimedKernels) return "";
     return kKernelNames[i];
+}
+
+const char* qmc_step_kernel_name(const qmc_ctx* ctx, int32_t i)
+{
+    if (ctx && ctx->wide) return (i >= 0 && i < kNumWideGroups) ? kWideGroupNames[i] : "";
+    return qmc_kernel_name(i);
 }
 
 } // extern "C"

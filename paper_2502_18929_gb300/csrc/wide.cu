@@ -88,8 +88,20 @@ struct WParent {
     uint2 kd;
 };
 
-// Parent i of a slot: its state, column weight and initiator status.  Returns
-// false (after raising the error) when its spawn probability reaches 1.
+// The exact column weight P of a loaded parent (once); false (after raising
+// the error) when its spawn probability reaches 1.
+__device__ __forceinline__ bool weigh_parent(const StepParams& P, const WProg& pr, WParent* q)
+{
+    if (q->Pw < 0) q->Pw = column_weight(pr, q->x, q->y, &q->sre, &q->sim);
+    if (q->Pw >= (1ll << 52)) {
+        set_error(P.st, DERR_DT_TOO_LARGE);
+        return false;
+    }
+    return true;
+}
+
+// Parent i of a slot with its column weight evaluated.  Returns false (after
+// raising the error) when its spawn probability reaches 1.
 __device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WRec* pop, const int64_t* off, int64_t i,
                             int phase, WParent* q, WProg* pr)
 {
@@ -193,6 +205,37 @@ __global__ void k_wide_prologue(StepParams P)
         P.kd[s] = make_uint2(o.x, o.y);
         P.segacc[s] = SegStats{0ull, 0ll, 0ll, 0ll};
     }
+    // rank-group offsets of N(t) and N(t - dt) (the light spawn's work
+    // units): gof[s] = sum over the vectors before s of ceil(K / 4)
+    __shared__ long long wsum[kWThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int w = 0; w < 2; ++w) {
+        const int slot = w ? (st->cur + 2) % 3 : st->cur;
+        const int64_t* off = P.segoff[slot];
+        int64_t* gof = P.gofs[slot];
+        long long carry = 0;
+        for (int base = 0; base < P.nseg; base += kWThreads) {
+            const int s = base + threadIdx.x;
+            const long long c = s < P.nseg ? (long long)((off[s + 1] - off[s] + 3) / 4) : 0ll;
+            long long incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            long long wo = 0, blk = 0;
+            for (int q = 0; q < kWThreads / 32; ++q) {
+                if (q < warp) wo += wsum[q];
+                blk += wsum[q];
+            }
+            if (s < P.nseg) gof[s] = carry + wo + incl - c;
+            carry += blk;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) gof[P.nseg] = carry;
+    }
     if (threadIdx.x == 0) {
         st->spawn_total = 0;
         st->cand_total = 0;
@@ -203,11 +246,41 @@ __global__ void k_wide_prologue(StepParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Spawning of light parents: one thread per parent, the warp's lanes stepping
-// through their walkers together so that each round's spawns take one atomic.
-// A parent with more than kWLight walkers becomes heavy work items of
-// kWChunk walkers each.
+// Spawning of light parents: one thread per rank group of four consecutive
+// parents of a vector, so that one Philox call gives the 32-bit words of the
+// group's first walkers (a second call their second walkers); the warp's
+// lanes step through their walkers together so that each round's spawns take
+// one atomic.  A walker's exact draw and the parent's column weight are
+// evaluated only when its word passes the program's prefilter.  A parent with
+// more than kWLight walkers becomes heavy work items.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int wgroup_seg(const int64_t* gof, int nseg, int64_t g)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&gof[mid]) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Candidate record (SpawnCand as four words): parent index in its slot,
+// vector, the walker's 32-bit word W, walker index | phase << 31.
+__device__ __forceinline__ void warp_append_cand(const StepParams& P, bool on, const uint4& c, int lane)
+{
+    const uint32_t bal = __ballot_sync(kFull, on);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long*)&P.st->cand_total, (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, leader);
+    if (on) {
+        const int64_t pos = (int64_t)base + __popc(bal & lanemask_lt());
+        if (pos < P.cand_cap) ((uint4*)P.cand)[pos] = c;
+        else set_error(P.st, DERR_CAND_CAPACITY);
+    }
+}
+
 __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WideParams W, int phase)
 {
     DevState* st = P.st;
@@ -217,82 +290,189 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
     const int slot = phase ? (st->cur + 2) % 3 : st->cur;
     const WRec* pop = (const WRec*)P.pop[slot];
     const int64_t* off = P.segoff[slot];
-    const int64_t K = off[P.nseg];
+    const int64_t* gof = P.gofs[slot];
+    const int64_t G = gof[P.nseg];
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < K; base += stride) {
-        const int64_t i = base + lane;
-        WParent q;
-        WProg pr;
-        int64_t m = 0;
-        if (i < K) {
-            if (load_parent(P, inf, pop, off, i, phase, &q, &pr)) {
-                m = iabs64(q.re) + iabs64(q.im);
-                if (m > kWLight) {
-                    const int64_t nb = (m - 2 + 3) / 4;   // extra calls (m > kWLight >= 2)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < G; base += stride) {
+        const int64_t g = base + lane;
+        int64_t m[4] = {0, 0, 0, 0};
+        int seg = 0;
+        uint32_t grp = 0;
+        int64_t first = 0;
+        uint2 kd = make_uint2(0u, 0u);
+        int64_t pre = -1;
+        if (g < G) {
+            seg = wgroup_seg(gof, P.nseg, g);
+            grp = (uint32_t)(g - gof[seg]);
+            first = off[seg] + 4 * (int64_t)grp;
+            const int cnt = (int)min((int64_t)4, off[seg + 1] - first);
+            kd = P.kd[seg];
+            pre = wprog_at(prog_of(P, inf, P.seginfo[seg].inst, phase)).h->p_bound >> 20;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k >= cnt) break;
+                const int2 v = __ldg((const int2*)&pop[first + k].re);
+                m[k] = iabs64(v.x) + iabs64(v.y);
+                if (m[k] > kWLight) {
+                    const int64_t nb = (m[k] - 2 + 3) / 4;
                     const int64_t chunks = (nb + kWChunk - 1) / kWChunk;
                     const int64_t at =
                         (int64_t)atomicAdd((unsigned long long*)&st->heavy_total, (unsigned long long)chunks);
                     for (int64_t c = 0; c < chunks; ++c) {
                         if (at + c < P.heavy_cap)
-                            P.heavy[at + c] = HeavyItem{i, phase, 0, (int32_t)c, q.seg};
+                            P.heavy[at + c] = HeavyItem{first + k, phase, 0, (int32_t)c, seg};
                         else
                             set_error(st, DERR_HEAVY_CAPACITY);
                     }
-                    m = 0;
+                    m[k] = 0;
                 }
             }
         }
-        for (int64_t w = 0; __any_sync(kFull, w < m); ++w) {
-            WSpawn rec;
-            bool sp = false;
-            if (w < m) sp = wide_walker(pr, q, w, walker_word(q, w), &rec);
-            warp_append(P, W, sp, rec, lane);
+        // first walkers: one call for the group
+        const uint4 gw0 = g < G ? group_words(grp, 0u, phase, kd) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t Wd = word_of(gw0, k);
+            const bool on = m[k] > 0 && (int64_t)Wd <= pre;
+            warp_append_cand(P, on, make_uint4((uint32_t)(first + k), (uint32_t)seg, Wd, (uint32_t)phase << 31),
+                             lane);
+        }
+        // second walkers: one more call; further walkers: the parent's calls
+        const bool two = m[0] > 1 || m[1] > 1 || m[2] > 1 || m[3] > 1;
+        if (__any_sync(kFull, two)) {
+            const uint4 gw1 = two ? group_words(grp, 1u, phase, kd) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t rank = 4u * grp + (uint32_t)k;
+                const int64_t mk = m[k];
+                for (int64_t w = 1; __any_sync(kFull, w < mk); ++w) {
+                    uint32_t Wd = 0u;
+                    if (w < mk)
+                        Wd = w == 1 ? word_of(gw1, k)
+                                    : word_of(extra_words(rank, (uint32_t)((w - 2) >> 2), phase, kd), (int)((w - 2) & 3));
+                    const bool on = w < mk && (int64_t)Wd <= pre;
+                    warp_append_cand(P, on,
+                                     make_uint4((uint32_t)(first + k), (uint32_t)seg, Wd, (uint32_t)w | ((uint32_t)phase << 31)),
+                                     lane);
+                }
+            }
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// Heavy parents: one warp per work item.  Item c of a parent covers the
-// walkers 2 + 4 b + (0..3) of its extra calls b in [c kWChunk, (c + 1)
-// kWChunk), one call per lane and round; item 0 also the walkers 0 and 1.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWThreads) k_wide_heavy(StepParams P, WideParams W)
+// Candidates: the parent's exact column weight, the walker's full draw and,
+// if it spawns, its record.
+__global__ void __launch_bounds__(kWThreads, 1) k_wide_choose(StepParams P, WideParams W)
 {
     DevState* st = P.st;
     if (cta_error(st)) return;
     const StepInfo inf = P.info[st->call_index];
-    const int64_t items = min((int64_t)st->heavy_total, P.heavy_cap);
+    const int64_t total = min((int64_t)st->cand_total, P.cand_cap);
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += warps) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int64_t i = base + lane;
+        WSpawn sr;
+        bool sp = false;
+        if (i < total) {
+            const uint4 c = ((const uint4*)P.cand)[i];
+            const int phase = (int)(c.w >> 31);
+            const int slot = phase ? (st->cur + 2) % 3 : st->cur;
+            WParent q;
+            WProg pr;
+            if (load_parent(P, inf, (const WRec*)P.pop[slot], P.segoff[slot], (int64_t)c.x, phase, &q, &pr))
+                sp = wide_walker(pr, q, (int64_t)(c.w & 0x7FFFFFFFu), c.z, &sr);
+        }
+        warp_append(P, W, sp, sr, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Heavy parents: one CTA per work item.  Item c of a parent covers the
+// walkers 2 + 4 b + (0..3) of its extra calls b in [c kWChunk, (c + 1)
+// kWChunk), item 0 also the walkers 0 and 1; the spawned walkers are counted
+// per (destination, channel, walker component) in shared memory and leave as
+// one record each (the merge adds records, so the populations are those of
+// one record per walker).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWThreads) k_wide_heavy(StepParams P, WideParams W)
+{
+    __shared__ int hist[4 * kMaxEntries];
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const StepInfo inf = P.info[st->call_index];
+    const int64_t items = min((int64_t)st->heavy_total, P.heavy_cap);
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int e = tid; e < 4 * kMaxEntries; e += blockDim.x) hist[e] = 0;
+    __syncthreads();
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const HeavyItem h = P.heavy[it];
         const int slot = h.phase ? (st->cur + 2) % 3 : st->cur;
         WParent q;
         WProg pr;
-        if (!load_parent(P, inf, (const WRec*)P.pop[slot], P.segoff[slot], h.parent, h.phase, &q, &pr)) continue;
-        const int64_t m = iabs64(q.re) + iabs64(q.im);
-        if (h.chunk == 0) {
-            WSpawn rec;
-            bool sp = false;
-            if (lane < 2 && lane < m) sp = wide_walker(pr, q, lane, walker_word(q, lane), &rec);
-            warp_append(P, W, sp, rec, lane);
-        }
-        const int64_t nb = (m - 2 + 3) / 4;   // extra calls of the parent
-        const int64_t b0 = (int64_t)h.chunk * kWChunk, b1 = min(nb, b0 + kWChunk);
-        for (int64_t bb = b0; bb < b1; bb += 32) {
-            const int64_t b = bb + lane;
-            uint4 o = make_uint4(0u, 0u, 0u, 0u);
-            if (b < b1) o = extra_words(q.rank, (uint32_t)b, h.phase, q.kd);
+        const bool ok = load_parent(P, inf, (const WRec*)P.pop[slot], P.segoff[slot], h.parent, h.phase, &q, &pr);
+        const int ne = pr.h->n_entry;
+        if (ok && ne <= kMaxEntries) {
+            const int64_t m = iabs64(q.re) + iabs64(q.im);
+            const int64_t are = iabs64(q.re);
+            auto walker = [&](int64_t w, uint32_t Wd) {
+                if ((int64_t)Wd > ((q.Pw - 1) >> 20)) return;
+                const int comp = w < are ? 0 : 1;
+                const uint32_t j = (uint32_t)(comp ? w - are : w);
+                const int64_t T = walker_T(Wd, q.rank, j, comp, q.phase, q.kd);
+                if (T >= q.Pw) return;
+                u128 mask;
+                int chan;
+                int64_t v;
+                if (!choose_destination(pr, q.x, q.y, q.sre, q.sim, T, &mask, &chan, &v)) return;
+                const int e = find_entry(pr, mask);
+                if (e >= 0) atomicAdd(&hist[(2 * e + chan) * 2 + comp], 1);
+            };
+            if (h.chunk == 0 && tid < 2 && tid < m) walker(tid, walker_word(q, tid));
+            const int64_t nb = (m - 2 + 3) / 4;
+            const int64_t b0 = (int64_t)h.chunk * kWChunk, b1 = min(nb, b0 + kWChunk);
+            for (int64_t b = b0 + tid; b < b1; b += blockDim.x) {
+                const uint4 o = extra_words(q.rank, (uint32_t)b, h.phase, q.kd);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t w = 2 + 4 * b + k;
-                WSpawn rec;
-                bool sp = false;
-                if (b < b1 && w < m) sp = wide_walker(pr, q, w, word_of(o, k), &rec);
-                warp_append(P, W, sp, rec, lane);
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t w = 2 + 4 * b + k;
+                    if (w < m) walker(w, word_of(o, k));
+                }
             }
         }
+        __syncthreads();
+        // one record per nonzero count, in rounds of the block's threads
+        const int nslots = ok ? 4 * min(ne, kMaxEntries) : 0;
+        for (int base = 0; base < nslots; base += blockDim.x) {
+            const int idx = base + tid;
+            WSpawn sr;
+            bool sp = false;
+            if (idx < nslots) {
+                const int cnt = hist[idx];
+                if (cnt) {
+                    hist[idx] = 0;
+                    const int e = idx >> 2, chan = (idx >> 1) & 1, comp = idx & 1;
+                    int64_t vr, vi;
+                    entry_value(pr, pr.ent[e], q.x, q.y, q.sre, q.sim, &vr, &vi);
+                    const int64_t v = chan ? vi : vr;
+                    const int sg = comp == 0 ? (q.re > 0 ? 1 : -1) : (q.im > 0 ? 1 : -1);
+                    const int sgn = (q.phase ? -1 : 1) * sg * (v > 0 ? 1 : -1);
+                    int target, val;
+                    if (chan == 0) { target = comp; val = sgn; }
+                    else if (comp == 0) { target = 1; val = sgn; }
+                    else { target = 0; val = -sgn; }
+                    const u128 dest = q.key ^ pr.ent[e].mask_key;
+                    sr.lo = (uint64_t)dest;
+                    sr.hi = (uint64_t)(dest >> 64);
+                    sr.meta = ((uint32_t)q.seg << 2) | ((uint32_t)target << 1) | (uint32_t)q.noninit;
+                    sr.val = val * cnt;
+                    sp = true;
+                }
+            }
+            warp_append(P, W, sp, sr, lane);
+        }
+        __syncthreads();
     }
 }
 
@@ -586,45 +766,40 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
         run.matched = matched ? 1 : 0;
         run.pad = 0;
         W.run[i] = run;
+        if (iabs64(run.re) > 2147483647ll || iabs64(run.im) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
         const bool fresh = !matched && (ire != 0 || iim != 0);
-        if (fresh && (iabs64(ire) > 2147483647ll || iabs64(iim) > 2147483647ll)) set_error(st, DERR_POP_OVERFLOW);
+        if (matched) W.delta[pos] = make_int2((int32_t)are, (int32_t)aim);   // the one run on this key
+        if (fresh) atomicAdd(&W.newcnt[pos], 1);
         W.flag_u[i] = fresh ? 1 : 0;
     }
 }
 
-// Each record of N(t) with the spawn run on its key (if any).
+// Each record of N(t) with the spawns on its key (delta, left there by the
+// run) and the count of new keys just before it: its value after
+// annihilation, and survives | newcnt << 32 for the prefix sums.  Index K
+// (past the last record) carries the new keys after it.
 __global__ void __launch_bounds__(kWThreads) k_wide_match(StepParams P, WideParams W)
 {
     DevState* st = P.st;
     if (cta_error(st)) return;
-    const WSpawn* sp = sorted_spawns(W);
     const int cur = st->cur;
     const WRec* A = (const WRec*)P.pop[cur];
-    const int64_t* offA = P.segoff[cur];
-    const int64_t K = offA[P.nseg];
-    int seg = -1;
-    int64_t seg_end = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
-        if (seg < 0 || i >= seg_end || i < offA[seg]) {
-            seg = seg_of(offA, P.nseg, i);
-            seg_end = offA[seg + 1];
+    const int64_t K = P.segoff[cur][P.nseg];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t nc = W.newcnt[i];
+        if (i == K) {
+            W.cnt_a[i] = nc << 32;
+            continue;
         }
-        const WRec a = wload(A, i);
-        const u128 k = wkey(a);
-        const int64_t lo = P.bseg[seg], hi = P.bseg[seg + 1];
-        const int64_t lb = lower_bound_spawn(sp, lo, hi, k);
-        int64_t re = a.re, im = a.im;
-        if (lb < hi && wkey(sp[lb]) == k) {
-            const WRun run = W.run[lb];
-            re += run.re;
-            im += run.im;
-        }
+        const int2 d = W.delta[i];
+        const int2 v = __ldg((const int2*)&A[i].re);
+        int64_t re = (int64_t)v.x + d.x, im = (int64_t)v.y + d.y;
         if (iabs64(re) > 2147483647ll || iabs64(im) > 2147483647ll) {
             set_error(st, DERR_POP_OVERFLOW);
             re = im = 0;
         }
-        W.aux[i] = WAux{lb, (int32_t)re, (int32_t)im};
-        W.flag_a[i] = (re != 0 || im != 0) ? 1 : 0;
+        W.delta[i] = make_int2((int32_t)re, (int32_t)im);
+        W.cnt_a[i] = ((re != 0 || im != 0) ? 1ll : 0ll) | (nc << 32);
     }
 }
 
@@ -633,20 +808,25 @@ __global__ void __launch_bounds__(kWThreads) k_wide_match(StepParams P, WidePara
 // the total.  which 0: the records of N(t); 1: the spawns.
 __device__ __forceinline__ int64_t flag_count(const StepParams& P, int which)
 {
-    return which ? spawn_count(P) : P.segoff[P.st->cur][P.nseg];
+    return which ? spawn_count(P) : P.segoff[P.st->cur][P.nseg] + 1;
+}
+
+// Input e of scan `which`: the spawns' 0/1 flags, or the records' packed counts.
+__device__ __forceinline__ int64_t scan_in(const WideParams& W, int which, int64_t e)
+{
+    return which ? (int64_t)W.flag_u[e] : W.cnt_a[e];
 }
 
 __global__ void __launch_bounds__(kWThreads) k_wide_scan_part(StepParams P, WideParams W, int which)
 {
     __shared__ int64_t red[kWThreads / 32];
     if (cta_error(P.st)) return;
-    const int32_t* f = which ? W.flag_u : W.flag_a;
     const int64_t N = flag_count(P, which);
     const int64_t tiles = (N + kWScanTile - 1) / kWScanTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int64_t c = 0;
         const int64_t e1 = min(N, (t + 1) * kWScanTile);
-        for (int64_t e = t * kWScanTile + threadIdx.x; e < e1; e += blockDim.x) c += f[e];
+        for (int64_t e = t * kWScanTile + threadIdx.x; e < e1; e += blockDim.x) c += scan_in(W, which, e);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -699,25 +879,24 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scan_apply(StepParams P, Wid
     constexpr int kPer = kWScanTile / kWThreads;
     __shared__ int64_t wsum[kWThreads / 32];
     if (cta_error(P.st)) return;
-    const int32_t* f = which ? W.flag_u : W.flag_a;
     int64_t* out = which ? W.scan_u : W.scan_a;
     const int64_t N = flag_count(P, which);
     const int64_t tiles = (N + kWScanTile - 1) / kWScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        // each thread a run of kPer consecutive flags
+        // each thread a run of kPer consecutive inputs
         const int64_t e0 = t * kWScanTile + (int64_t)threadIdx.x * kPer;
-        int v[kPer];
-        int c = 0;
+        int64_t v[kPer];
+        int64_t c = 0;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            v[k] = e0 + k < N ? f[e0 + k] : 0;
+            v[k] = e0 + k < N ? scan_in(W, which, e0 + k) : 0;
             c += v[k];
         }
-        int incl = c;
+        int64_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(kFull, incl, o);
+            const int64_t x = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += x;
         }
         if (lane == 31) wsum[warp] = incl;
@@ -747,10 +926,11 @@ __global__ void k_wide_outoff(StepParams P, WideParams W)
     const int cur = st->cur, nxt = (cur + 1) % 3;
     const int64_t* offA = P.segoff[cur];
     int64_t* off = P.segoff[nxt];
+    // the low half of scan_a counts surviving records of N(t)
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.nseg; s += gridDim.x * blockDim.x)
-        off[s] = W.scan_a[offA[s]] + W.scan_u[P.bseg[s]];
+        off[s] = (W.scan_a[offA[s]] & 0xFFFFFFFFll) + W.scan_u[P.bseg[s]];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const int64_t total = W.scan_a[offA[P.nseg]] + W.scan_u[spawn_count(P)];
+        const int64_t total = (W.scan_a[offA[P.nseg] + 1] & 0xFFFFFFFFll) + W.scan_u[spawn_count(P)];
         st->next_total = total;
         if (total > st->max_next) st->max_next = total;
         if (total > P.pop_cap) set_error(st, DERR_POP_CAPACITY);
@@ -765,15 +945,21 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scatter_a(StepParams P, Wide
     const WRec* A = (const WRec*)P.pop[cur];
     WRec* out = (WRec*)P.pop[(cur + 1) % 3];
     const int64_t K = P.segoff[cur][P.nseg];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
-        if (!W.flag_a[i]) continue;
-        const WAux x = W.aux[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
+        W.newcnt[i] = 0;   // zero for the next step
+        if (i == K) continue;
+        const int64_t c = W.cnt_a[i];
+        const int2 v = W.delta[i];
+        W.delta[i] = make_int2(0, 0);
+        if (!(c & 1ll)) continue;
+        const int64_t e = W.scan_a[i];
         WRec r;
         r.lo = A[i].lo;
         r.hi = A[i].hi;
-        r.re = x.re;
-        r.im = x.im;
-        out[W.scan_a[i] + W.scan_u[x.lbS]] = r;
+        r.re = v.x;
+        r.im = v.y;
+        // survivors and new keys before it, then the new keys just before it
+        out[(e & 0xFFFFFFFFll) + (e >> 32) + (c >> 32)] = r;
     }
 }
 
@@ -793,7 +979,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scatter_u(StepParams P, Wide
         r.hi = sp[i].hi;
         r.re = (int32_t)run.re;
         r.im = (int32_t)run.im;
-        out[W.scan_u[i] + W.scan_a[run.posA]] = r;
+        out[W.scan_u[i] + (W.scan_a[run.posA] & 0xFFFFFFFFll)] = r;
     }
 }
 
@@ -873,7 +1059,9 @@ __global__ void k_wide_finalize(StepParams P)
         st->acc_spawn += st->spawn_total;
         st->acc_knext += next;
         st->acc_heavy += st->heavy_total;
+        st->acc_cand += st->cand_total;
         st->acc_sort_lsd += 1;
+        if (st->cand_total > st->max_cand) st->max_cand = st->cand_total;
         if (st->spawn_total > st->max_spawn) st->max_spawn = st->spawn_total;
         if (st->heavy_total > st->max_heavy) st->max_heavy = st->heavy_total;
         st->count[nxt] = next;
@@ -908,40 +1096,58 @@ void configure_wide_kernels() { (void)wide_grid(); }
 
 // The kernels of one step, in order, on one stream (captured into a graph by
 // the host).
-void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s)
+const char* const kWideGroupNames[kNumWideGroups] = {
+    "w_prologue", "w_spawn", "w_spawn_heavy", "w_sort_hist_plan", "w_sort_passes",
+    "w_merge_runs_match", "w_merge_scans", "w_merge_scatter", "w_obs_finalize"};
+
+void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, cudaEvent_t* ev)
 {
     const int g = wide_grid();
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], s);
+    };
+    mark(0);
     k_wide_prologue<<<1, kWThreads, 0, s>>>(P);
     k_wide_zero_hist<<<1, kWThreads, 0, s>>>(W);
+    mark(1);
     k_wide_spawn<<<g, kWThreads, 0, s>>>(P, W, 0);
     k_wide_spawn<<<g, kWThreads, 0, s>>>(P, W, 1);
+    k_wide_choose<<<g, kWThreads, 0, s>>>(P, W);
+    mark(2);
     k_wide_heavy<<<g, kWThreads, 0, s>>>(P, W);
+    mark(3);
     k_wide_hist<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_plan<<<1, kWThreads, 0, s>>>(P, W);
+    mark(4);
     for (int p = 0; p < W.passes; ++p) {
         k_wide_tile_hist<<<g, kWThreads, 0, s>>>(P, W, p);
         k_wide_tile_scan<<<256, kWThreads, 0, s>>>(P, W, p);
         k_wide_scatter<<<g, kWThreads, 0, s>>>(P, W, p);
     }
+    mark(5);
     k_wide_spawn_off<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_runs<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_match<<<g, kWThreads, 0, s>>>(P, W);
+    mark(6);
     for (int which = 0; which < 2; ++which) {
         k_wide_scan_part<<<g, kWThreads, 0, s>>>(P, W, which);
         k_wide_scan_top<<<1, kWThreads, 0, s>>>(P, W, which);
         k_wide_scan_apply<<<g, kWThreads, 0, s>>>(P, W, which);
     }
+    mark(7);
     k_wide_outoff<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_scatter_a<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_scatter_u<<<g, kWThreads, 0, s>>>(P, W);
+    mark(8);
     k_wide_obs<<<g, kWThreads, 0, s>>>(P, 1, P.segacc);
     k_wide_finalize<<<1, kWThreads, 0, s>>>(P);
+    mark(9);
 }
 
 int wide_step_launch_count(const StepParams& P, const WideParams& W)
 {
     (void)P;
-    return 7 + 3 * W.passes + 3 + 6 + 5;
+    return 8 + 3 * W.passes + 3 + 6 + 5;
 }
 
 namespace {
@@ -1091,6 +1297,50 @@ void launch_wide_export(const StepParams& P, int slot, int64_t first, int64_t co
                         int32_t* re, int32_t* im, cudaStream_t s)
 {
     if (count > 0) k_wide_export<<<wide_grid(), kWThreads, 0, s>>>(P, slot, first, count, x, y, re, im);
+}
+
+} // namespace qmc
+
+namespace qmc {
+
+namespace {
+
+// Records |x><y| of the caller into a population slot; bad is set for a state
+// beyond n qubits, a zero or INT32_MIN value, or keys not ascending inside a
+// vector.
+__global__ void k_wide_pack(const uint64_t* __restrict__ xs, const uint64_t* __restrict__ ys,
+                            const int32_t* __restrict__ re, const int32_t* __restrict__ im,
+                            const int64_t* __restrict__ off, int nseg, const SegInfo* __restrict__ seginfo,
+                            WRec* __restrict__ dst, int* bad)
+{
+    const int64_t K = off[nseg];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = seg_of(off, nseg, i);
+        const int n = seginfo[s].n;
+        const uint64_t lim = (1ull << n) - 1ull;
+        const int32_t a = re[i], b = im[i];
+        bool ok = (xs[i] & ~lim) == 0 && (ys[i] & ~lim) == 0 && (a != 0 || b != 0) && a != INT32_MIN && b != INT32_MIN;
+        const u128 k = ((u128)xs[i] << n) | (u128)ys[i];
+        if (ok && i > off[s]) {
+            const u128 kp = ((u128)xs[i - 1] << n) | (u128)ys[i - 1];
+            if (kp >= k) ok = false;
+        }
+        if (!ok) atomicExch(bad, 1);
+        WRec r;
+        r.lo = (uint64_t)k;
+        r.hi = (uint64_t)(k >> 64);
+        r.re = a;
+        r.im = b;
+        dst[i] = r;
+    }
+}
+
+} // namespace
+
+void launch_wide_pack(const uint64_t* xs, const uint64_t* ys, const int32_t* re, const int32_t* im,
+                      const int64_t* off, int nseg, const SegInfo* seginfo, WRec* dst, int* bad, cudaStream_t s)
+{
+    k_wide_pack<<<wide_grid(), kWThreads, 0, s>>>(xs, ys, re, im, off, nseg, seginfo, dst, bad);
 }
 
 } // namespace qmc

@@ -358,6 +358,37 @@ def spread_population(n: int, count: int, seed: int) -> tuple[np.ndarray, np.nda
     return keys, re, im
 
 
+def spread_population_xy(n: int, count: int, seed: int):
+    """``count`` distinct uniformly random states |x><y| of n qubits (any n
+    up to 64), each holding one walker of sign +1, -1, +i or -i, in key order
+    ((x, y) ascending).  Returns uint64 x, y and int32 (re, im)."""
+    rng = np.random.default_rng(seed)
+    hi = 1 << n
+
+    def draw(m):
+        if n == 64:
+            return rng.integers(0, 2**64 - 1, size=m, dtype=np.uint64, endpoint=True)
+        return rng.integers(0, hi, size=m, dtype=np.uint64)
+
+    def distinct(x, y):
+        o = np.lexsort((y, x))
+        x, y = x[o], y[o]
+        keep = np.concatenate([[True], (x[1:] != x[:-1]) | (y[1:] != y[:-1])]) if x.size else np.zeros(0, bool)
+        return x[keep], y[keep]
+
+    x, y = distinct(draw(count), draw(count))
+    while x.size < count:
+        m = count - x.size + 16
+        x, y = distinct(np.concatenate([x, draw(m)]), np.concatenate([y, draw(m)]))
+    if x.size > count:
+        pick = np.sort(rng.choice(x.size, size=count, replace=False))
+        x, y = x[pick], y[pick]
+    sel = rng.integers(0, 4, size=count)
+    re = np.where(sel == 0, 1, np.where(sel == 1, -1, 0)).astype(np.int32)
+    im = np.where(sel == 2, 1, np.where(sel == 3, -1, 0)).astype(np.int32)
+    return x, y, re, im
+
+
 def destination_masks(prob) -> np.ndarray:
     """Every destination mask (dx << n) | dy that a term of the problem can
     reach (a Pauli string flips the bits of its X part), sorted."""

@@ -40,7 +40,7 @@ EXPORTED = [
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
     "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
     "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum", "qmc_learn_grad_tc", "qmc_memory",
-    "qmc_export_xy",
+    "qmc_export_xy", "qmc_set_populations_xy", "qmc_step_kernel_name",
 ]
 
 
@@ -177,11 +177,15 @@ def lib():
         L.qmc_batch_create.argtypes = [C.POINTER(vp), vp, C.c_int32, C.POINTER(Config)]
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_memory.argtypes = [vp, vp]
+        L.qmc_set_populations_xy.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
         L.qmc_export_xy.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, C.c_int64, C.POINTER(C.c_int64)]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
+        L.qmc_step_kernel_name.argtypes = [vp, C.c_int32]
+        L.qmc_step_kernel_name.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("qmc_destroy", "qmc_last_error", "qmc_kernel_name", "qmc_column_eval"):
+            if name not in ("qmc_destroy", "qmc_last_error", "qmc_kernel_name", "qmc_step_kernel_name",
+                            "qmc_column_eval"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -426,6 +430,15 @@ class QMC:
         self._check(self.L.qmc_set_populations(self.h, which, _ptr(counts), _ptr(keys), _ptr(re), _ptr(im)),
                     "qmc_set_populations")
 
+    def set_populations_xy(self, counts, x, y, re, im, which: int = 0):
+        """Populations from concatenated per-vector records |x><y| (any n),
+        (x, y) ascending within each vector."""
+        counts = _arr(counts, np.int64)
+        x, y = _arr(x, np.uint64), _arr(y, np.uint64)
+        re, im = _arr(re, np.int32), _arr(im, np.int32)
+        self._check(self.L.qmc_set_populations_xy(self.h, which, counts.ctypes.data, _ptr(x), _ptr(y), _ptr(re),
+                                                  _ptr(im)), "qmc_set_populations_xy")
+
     def set_clock(self, step: int, t: float, t_prev: float = 0.0, dt_last: float = 0.0,
                   prev_valid: bool = False):
         self._check(self.L.qmc_set_clock(self.h, step, t, t_prev, dt_last, int(prev_valid)), "qmc_set_clock")
@@ -455,7 +468,7 @@ class QMC:
         nk = C.c_int32()
         self._check(self.L.qmc_step_profile(self.h, dt, nsteps, ms.ctypes.data, 32, C.byref(nk)),
                     "qmc_step_profile")
-        return {self.L.qmc_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+        return {self.L.qmc_step_kernel_name(self.h, i).decode(): float(ms[i]) for i in range(nk.value)}
 
     def memory(self) -> dict:
         """Device memory the context holds (qmc_memory)."""

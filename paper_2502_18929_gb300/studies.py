@@ -204,7 +204,7 @@ def proposal_study(name: str = "ghz24", nvec: int = 32, n_diag: int = 10**5, tra
     t0 = time.time()
     feats, targets, weights, total = [], [], [], 0
     steps_total = planner.total_steps(pl)
-    every = max(1, steps_total // 60)
+    every = max(1, steps_total // 400)   # about 400 logging points over the run
     idx = 0
     for tp0, d, k in pl:
         done = 0

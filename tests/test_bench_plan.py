@@ -39,7 +39,8 @@ def test_capacity_covers_growth():
     # measured growth is about 1.3 % of the initial records per step
     for steps in (13, 25, 60):
         assert bench.capacity_hint(wl, steps) >= base * (1.0 + 0.013 * steps) * 1.2
-    assert bench.capacity_hint(bench.workload("ghz4"), 25) == 0
+    g = bench.workload("ghz4")   # from one state: one record per walker
+    assert bench.capacity_hint(g, 25) >= g["n_diag"] * g["nseg"]
 
 
 def test_cpu_info_names_host():
