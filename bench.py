@@ -1,7 +1,7 @@
 """Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload spread32|spread32s|dd12|dd12i|ghz4|ghzN|ghzNi|batch256]
+                    [--workload spread32|spread32s|spread40|dd12|dd12i|ghz4|ghzN|ghzNi|batch256]
 
 One "step" is one dt step of every population vector through the whole hot
 path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
@@ -317,24 +317,26 @@ def source_sha() -> str:
 
 
 def measured_traffic(kernel: str, units_launch: float):
-    """DRAM bytes (read + write) of one launch of `kernel`, scaled from the ncu
-    capture summarised in profiles/ by the units processed (parents plus spawn
-    candidates for the draw kernel; merged items plus outputs for the merge).
-    None when no capture exists or the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_spread32s.md")
+    """DRAM bytes (read + write) of one launch of `kernel`, scaled by the units
+    processed (parents plus spawn candidates for the draw kernel; merged items
+    plus outputs for the merge) from the ncu counters kept as data in
+    profiles/<kernel>_spread32s.json.  None when no capture exists or the
+    kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_spread32s.json")
     if not os.path.exists(path):
         return None
-    txt = open(path).read()
-    import re
-    sha = re.search(r"sha256\[:16\] = ([0-9a-f]+)", txt)
-    units = re.search(r"Units of the captured launch: ([0-9]+)", txt)
-    rd = re.search(r"\| DRAM read \| ([0-9.]+) (\w+)", txt)
-    wr = re.search(r"\| DRAM write \| ([0-9.]+) (\w+)", txt)
-    if not (sha and units and rd and wr) or sha.group(1) != source_sha():
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_sources_sha256_16") != source_sha() or not d.get("units_of_launch"):
         return None
+    m = d["metrics"]
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    total = float(rd.group(1)) * scale.get(rd.group(2), 1.0) + float(wr.group(1)) * scale.get(wr.group(2), 1.0)
-    return total * units_launch / float(units.group(1))
+    total = 0.0
+    for key in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        if key not in m:
+            return None
+        total += float(m[key]["value"]) * scale.get(m[key]["unit"], 1.0)
+    return total * units_launch / float(d["units_of_launch"])
 
 
 def kernel_bytes(name: str, c: dict) -> float:
@@ -459,7 +461,11 @@ def run_gpu(args, rank: int, world: int):
         traffic = measured_traffic(top, units) if units else None
         roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None if traffic is None else round(traffic), "avg_launch_ms": round(avg_ms, 5),
+                "traffic": None if traffic is None else round(traffic),
+                "traffic_source": (None if traffic is None else
+                                   f"ncu DRAM read + write of {top} on spread32s (profiles/{top}_spread32s.json), "
+                                   "scaled to this launch by the units processed"),
+                "avg_launch_ms": round(avg_ms, 5),
                 "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "units_per_launch": {k: round(v) for k, v in unit_counts.items()},
                 "kernel_share": {k: round(v / sum(kernel_ms.values()), 4) for k, v in kernel_ms.items()}}
@@ -594,6 +600,9 @@ def run_batch(args, rank: int, world: int):
     clocks = sampler.stop()
     c = batch.counters(reset=True)
     launches = batch.step_launches()
+    prof = batch.step_profile(dt, 3)   # three further steps replayed under events
+    tot = sum(prof.values()) or 1.0
+    shares = {name: round(v / tot, 4) for name, v in sorted(prof.items(), key=lambda kv: -kv[1]) if v > 0}
     batch.close()
 
     alone_ms, alone_host, alone_walkers = 0.0, 0.0, 0
@@ -610,6 +619,36 @@ def run_batch(args, rank: int, world: int):
         sim.close()
     if alone_walkers != c["walker_steps"]:
         raise SystemExit("batched and per-instance runs disagree on the walker count")
+
+    # the strongest plain form: one context per instance, 16 host threads each
+    # stepping 16 contexts on its own stream, all at once (host wall time)
+    from concurrent.futures import ThreadPoolExecutor
+    nthreads = 16
+    streams = [torch.cuda.Stream() for _ in range(nthreads)]
+    sims = []
+    for i in range(k):
+        sm = qmc.QMC(probs[i].n, 1, seeds[i], ndiag[i], stream=streams[i % nthreads].cuda_stream)
+        sm.load_schedule(probs[i])
+        sm.init_populations(P.rho_basis(0))
+        sm.step(dt, pre + W)
+        sm.counters(reset=True)
+        sims.append(sm)
+    torch.cuda.synchronize()
+
+    def worker(tix):
+        for i in range(tix, k, nthreads):
+            sims[i].step(dt, K)
+
+    h0 = time.perf_counter()
+    with ThreadPoolExecutor(nthreads) as ex:
+        list(ex.map(worker, range(nthreads)))
+    torch.cuda.synchronize()
+    conc_s = time.perf_counter() - h0
+    conc_walkers = sum(sm.counters()["walker_steps"] for sm in sims)
+    for sm in sims:
+        sm.close()
+    if conc_walkers != c["walker_steps"]:
+        raise SystemExit("batched and concurrent per-instance runs disagree on the walker count")
     value = c["walker_steps"] / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -630,7 +669,12 @@ def run_batch(args, rank: int, world: int):
         "unbatched": {"value": alone_walkers / (alone_ms * 1e-3), "unit": UNIT,
                       "ms_per_step": alone_ms / K, "host_s": alone_host,
                       "note": "the same 256 instances, one context each, stepped one after the other"},
+        "unbatched_concurrent": {"value": conc_walkers / conc_s, "unit": UNIT, "host_s": conc_s,
+                                 "note": f"one context per instance, {nthreads} host threads and streams, "
+                                         "stepped concurrently (host wall time)"},
+        "kernel_share": shares,
         "batched_speedup": (alone_ms / ms) if ms > 0 else None,
+        "batched_speedup_vs_concurrent": (conc_s / host_s) if host_s > 0 else None,
         "gpu_launches": int(K * launches),
         "clocks": clocks,
     }

@@ -115,3 +115,68 @@ def test_wide_overlap_and_rejections():
         gpu.set_proposal(qmc.PROPOSAL_STATIC)
     with pytest.raises(qmc.QmcError):
         gpu.antihermiticity()
+
+
+def test_spread40_full_size_sampled_against_oracle():
+    """The 40-qubit benchmark step at full size (64 vectors of about 1.56e6
+    distinct random states, 1e8 records, 128-bit keys), one AB2 step inside the
+    CNOT 4 -> 5 pulse, checked on sampled outputs that the oracle computes one
+    state at a time from every parent that can reach it: occupied outputs, new
+    states, and states the step left empty; N(t - dt) after the step is the
+    input N(t)."""
+    import torch
+    torch.cuda.init()
+    n, nseg, per = 40, 64, 10**8 // 64
+    prob = P.ghz_circuit(n)
+    seed, dt, t = 1000, 0.01, 5.3
+    cur = [P.spread_population_xy(n, per, 10 * s) for s in range(nseg)]
+    prev = [P.spread_population_xy(n, per - 777, 5 + 10 * s) for s in range(nseg)]
+
+    def packed(pops):
+        return ([len(p[0]) for p in pops], *[np.concatenate([p[k] for p in pops]) for k in range(4)])
+
+    gpu = qmc.QMC(n, nseg, seed, per, integrator=qmc.AB2, stream=torch.cuda.current_stream().cuda_stream,
+                  capacity_hint=int(1.3 * nseg * per))
+    gpu.load_schedule(prob)
+    gpu.set_populations_xy(*packed(cur), which=0)
+    gpu.set_populations_xy(*packed(prev), which=1)
+    gpu.set_clock(530, t, t - dt, dt, True)
+    gpu.counters(reset=True)
+    gpu.step(dt, 1)
+    c = gpu.counters()
+    assert c["steps"] == 1 and c["k_cur"] == nseg * per and c["k_prev"] == nseg * (per - 777)
+    assert c["spawns"] > 10**6 and c["redo_launches"] == 0
+
+    orc = O.OracleSim(prob, nseg, seed, integrator=O.AB2, n_diag=per)
+    sampled = (0, 41)
+    for s in sampled:
+        orc.set_population_xy(s, *cur[s], which=0)
+        orc.set_population_xy(s, *prev[s], which=1)
+    orc.set_clock(530, t, t - dt, dt, True)
+    masks, _ = O.OracleProblem(prob).static(t, 1.5 * dt)
+    rng = np.random.default_rng(4)
+    ymask = (1 << n) - 1
+    for s in sampled:
+        px, py, pre_, pim = gpu.export_xy(s, which=1)
+        assert np.array_equal(px, cur[s][0]) and np.array_equal(py, cur[s][1])
+        assert np.array_equal(pre_, cur[s][2]) and np.array_equal(pim, cur[s][3])
+        x, y, re, im = gpu.export_xy(s)
+        out = {(int(a), int(b)): (int(r), int(i)) for a, b, r, i in zip(x, y, re, im)}
+        before = set(zip(cur[s][0].tolist(), cur[s][1].tolist()))
+        keys = list(out.keys())
+        for i in rng.choice(len(keys), size=1500, replace=False):
+            k = keys[i]
+            assert orc.next_value_xy(s, dt, k[0], k[1]) == out[k], (s, k)
+        new = [k for k in keys if k not in before]
+        for i in rng.choice(len(new), size=min(300, len(new)), replace=False):
+            k = new[i]
+            assert orc.next_value_xy(s, dt, k[0], k[1]) == out[k], (s, k)
+        gone = [k for k in before if k not in out]
+        probe = [gone[i] for i in rng.choice(len(gone), size=min(600, len(gone)), replace=False)]
+        for i in rng.choice(per, size=600, replace=False):
+            m = int(masks[rng.integers(len(masks))])
+            q = (int(cur[s][0][i]) ^ (m >> n), int(cur[s][1][i]) ^ (m & ymask))
+            if q not in out:
+                probe.append(q)
+        for k in probe:
+            assert orc.next_value_xy(s, dt, k[0], k[1]) == (0, 0), (s, k)
