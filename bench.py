@@ -1,7 +1,7 @@
 """Benchmark: walker-steps/s of the real-time population-dynamics QMC step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload spread32|spread32s|spread40|dd12|dd12i|ghz4|ghzN|ghzNi|batch256]
+                    [--workload spread32|spread32s|spread40|spread40s|dd12|dd12i|ghz4|ghzN|ghzNi|batch256]
 
 One "step" is one dt step of every population vector through the whole hot
 path: spawning (Hamiltonian and Lindblad terms, diagonal included), radix sort
@@ -84,6 +84,12 @@ def workload(name: str):
                     "1e8 distinct random states x 1 walker over 64 vectors",
                     prob=prob, nseg=64, n_diag=10**8 // 64, dt=0.01, t_end=6.0, t_start=5.0,
                     spread=10**8 // 64, default_steps=10)
+    if name == "spread40s":
+        prob = P.ghz_circuit(40)
+        return dict(name="spread40s", desc="GHZ-40 Liouvillian (CNOT 4->5 window + local noise), 128-bit keys, "
+                    "1.6e7 distinct random states x 1 walker over 64 vectors",
+                    prob=prob, nseg=64, n_diag=250000, dt=0.01, t_end=6.0, t_start=5.0,
+                    spread=250000, default_steps=10)
     if name == "spread32s":
         prob = P.ghz_circuit(32)
         return dict(name="spread32s", desc="GHZ-32 Liouvillian (CNOT 4->5 window + local noise), "

@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for log in logs:
             print(log)
     tmp = LIB + ".tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(dig)

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 #include <chrono>
 
@@ -1318,20 +1319,57 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     const int ni = (int)ctx->inst.size();
     std::vector<StepInfo> info(nsteps);
     std::vector<uint8_t> blob;
-    std::vector<uint8_t> tmp;
     std::vector<int64_t> last_off(2 * (size_t)ni, -1);
     std::vector<std::vector<uint8_t>> last_blob(2 * (size_t)ni);
-    auto add_prog = [&](int k, int pass, double tt, double dte, int64_t* off_out) -> int {
-        tmp.clear();
-        int rc = build_program(ctx->inst[k].sched, tt, dte, &tmp);
-        if (rc != QMC_OK) return rc;
+    // every (step, instance, pass) program, built by several host threads (the
+    // programs are independent; a batch of hundreds of instances builds
+    // hundreds per step)
+    struct Job {
+        int k, pass;
+        double t, dte;
+    };
+    std::vector<Job> jobs;
+    std::vector<int64_t> job0(nsteps + 1);
+    const double t0 = ctx->t;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const double ti = t0 + (double)i * dt;
+        const bool ab2 = ctx->cfg.integrator == QMC_AB2 && (i > 0 || (ctx->prev_valid && ctx->dt_last == dt));
+        const double tp = i > 0 ? t0 + (double)(i - 1) * dt : ctx->t_prev;
+        info[i].ab2 = ab2 ? 1 : 0;
+        info[i].t[0] = ti;
+        info[i].t[1] = ab2 ? tp : ti;
+        job0[i] = (int64_t)jobs.size();
+        for (int k = 0; k < ni; ++k) {
+            jobs.push_back(Job{k, 0, ti, ab2 ? dt * 1.5 : dt});
+            if (ab2) jobs.push_back(Job{k, 1, tp, dt * 0.5});
+        }
+    }
+    job0[nsteps] = (int64_t)jobs.size();
+    std::vector<std::vector<uint8_t>> built(jobs.size());
+    std::vector<int> built_rc(jobs.size(), QMC_OK);
+    {
+        const int64_t nj = (int64_t)jobs.size();
+        unsigned hw = std::thread::hardware_concurrency();
+        const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)16, nj / 8}));
+        auto work = [&](int w) {
+            for (int64_t j = w; j < nj; j += nthr)
+                built_rc[j] = build_program(ctx->inst[jobs[j].k].sched, jobs[j].t, jobs[j].dte, &built[j]);
+        };
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nthr; ++w) pool.emplace_back(work, w);
+        work(0);
+        for (auto& th : pool) th.join();
+    }
+    auto add_prog = [&](int64_t j, int64_t* off_out) -> int {
+        if (built_rc[j] != QMC_OK) return built_rc[j];
+        const std::vector<uint8_t>& tmp = built[j];
         const ProgHeader* h = (const ProgHeader*)tmp.data();
         if (h->n_entry > kMaxEntries)
             return fail(ctx, QMC_ERR_INVALID_ARG, "column has more destinations than the heavy path holds");
         if ((ctx->proposal == QMC_PROPOSAL_LEARNED || ctx->proposal == QMC_PROPOSAL_LEARNED_TC) &&
             h->n_stat > kMaxLearnedSlots)
             return fail(ctx, QMC_ERR_INVALID_ARG, "learned proposal: more than 256 destinations per column");
-        const size_t slot = 2 * (size_t)k + pass;
+        const size_t slot = 2 * (size_t)jobs[j].k + jobs[j].pass;
         if (last_off[slot] >= 0 && last_blob[slot] == tmp) {
             *off_out = last_off[slot];
             return QMC_OK;
@@ -1345,23 +1383,16 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         return QMC_OK;
     };
     std::vector<int64_t> tab(2 * (size_t)ni);
-    const double t0 = ctx->t;
     for (int64_t i = 0; i < nsteps; ++i) {
-        const double ti = t0 + (double)i * dt;
-        const bool ab2 = ctx->cfg.integrator == QMC_AB2 &&
-                         (i > 0 || (ctx->prev_valid && ctx->dt_last == dt));
-        const double tp = i > 0 ? t0 + (double)(i - 1) * dt : ctx->t_prev;
-        info[i].ab2 = ab2 ? 1 : 0;
-        info[i].t[0] = ti;
-        info[i].t[1] = ab2 ? tp : ti;
-        for (int k = 0; k < ni; ++k) {
-            int rc = add_prog(k, 0, ti, ab2 ? dt * 1.5 : dt, &tab[2 * k]);
-            tab[2 * k + 1] = tab[2 * k];
-            if (rc == QMC_OK && ab2) rc = add_prog(k, 1, tp, dt * 0.5, &tab[2 * k + 1]);
+        for (int64_t j = job0[i]; j < job0[i + 1]; ++j) {
+            int64_t off = 0;
+            const int rc = add_prog(j, &off);
             if (rc != QMC_OK) {
                 if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
                 return rc;
             }
+            tab[2 * jobs[j].k + jobs[j].pass] = off;
+            if (jobs[j].pass == 0) tab[2 * jobs[j].k + 1] = off;   // pass 1 repeats pass 0 when absent
         }
         const size_t at = (blob.size() + 15) & ~(size_t)15;
         blob.resize(at + tab.size() * sizeof(int64_t));
