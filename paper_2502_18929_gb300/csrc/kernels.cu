@@ -1273,65 +1273,33 @@ __device__ void tc_forward(const uint8_t* sw, const TcLayout& L, int n, uint32_t
 
 // Per program (pass): each static slot's network output (-1: none; -2: the
 // slot has width 0 and is never chosen) and its static part S_k = floor(eps
-// s_k / p_att 2^24) (< 2^24); by network output, the slot of the column that
-// it serves (-1: none) and that slot's S_k; over the slots of positive width
-// without an output, the sum of their weights max(1, S_k) and the largest
-// (first on ties).
+// s_k / p_att 2^24) (< 2^24).
 struct TcSlots {
     int16_t out[kMaxLearnedSlots];
     int32_t st[kMaxLearnedSlots];
-    int16_t slot_of[kTcMaxGp];
-    int32_t st_of[kTcMaxGp];
-    int64_t q_const;
-    int32_t best_q, best_k;
 };
 
-// All threads of the block call this (it synchronises the block).
 __device__ void tc_slots_fill(const StepParams& P, const Prog& prog, TcSlots* s, int tid, int nthr)
 {
     const int64_t p_att = prog.h->p_att;
-    const int ns = prog.h->n_stat;
-    for (int o = tid; o < kTcMaxGp; o += nthr) s->slot_of[o] = -1;
-    __syncthreads();
-    for (int k = tid; k < ns; k += nthr) {
+    for (int k = tid; k < prog.h->n_stat; k += nthr) {
         const int64_t w = slot_width(prog, k);
-        const int o = w > 0 ? lp_output(P, prog.stat[k].mask) : -2;
-        s->out[k] = (int16_t)o;
-        const int32_t stk = (w > 0 && p_att > 0 && p_att < (1ll << 52))
-                                ? (int32_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)P.mlp_eps, (double)w),
-                                                                     (double)p_att), 16777216.0))
-                                : 0;
-        s->st[k] = stk;
-        if (o >= 0) {
-            s->slot_of[o] = (int16_t)k;
-            s->st_of[o] = stk;
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int64_t sum = 0;
-        int32_t bq = -1, bk = -1;
-        for (int k = 0; k < ns; ++k) {
-            if (s->out[k] != -1) continue;
-            const int32_t q = s->st[k] < 1 ? 1 : s->st[k];
-            sum += q;
-            if (q > bq) {
-                bq = q;
-                bk = k;
-            }
-        }
-        s->q_const = sum;
-        s->best_q = bq;
-        s->best_k = bk;
+        s->out[k] = (int16_t)(w > 0 ? lp_output(P, prog.stat[k].mask) : -2);
+        s->st[k] = (w > 0 && p_att > 0 && p_att < (1ll << 52))
+                       ? (int32_t)floor(__dmul_rn(__ddiv_rn(__dmul_rn((double)P.mlp_eps, (double)w), (double)p_att),
+                                                  16777216.0))
+                       : 0;
     }
 }
 
 // The weights Q_k of one source from its logits lg (by output; overwritten
-// with the exponentials): m = max over the outputs the column serves, e =
-// exp(z - m), S = sum of e (in the order of tc_row_stats), c = (1 - eps) 2^24
-// / S, L_k = floor(e_k c), Q_k = max(1, L_k + S_k) on the slots of positive
-// width, the first largest absorbing 2^24 - sum Q.  The light and the heavy
-// kernels share these functions, so a parent's Q is the same on either path.
+// with the exponentials by tc_row_prepare): m = max over the slots with an
+// output, e = exp(z - m), S = (sum of e over the even slots, in order) + (the
+// same over the odd slots), c = (1 - eps) 2^24 / S,
+// L_k = floor(e_k c), Q_k = max(1, L_k + S_k) on slots of positive width, the
+// first largest absorbing 2^24 - sum Q.  One thread per source; the light and
+// the heavy kernels share these functions, so a parent's Q is the same on
+// either path.
 struct TcRow {
     float c;
     int arg;
@@ -1346,83 +1314,104 @@ __device__ __forceinline__ int64_t tc_q(const float* lg, const TcSlots* s, int k
     return Q < 1 ? 1 : Q;
 }
 
-__device__ __forceinline__ void tc_best(int64_t& q, int& k, int64_t q2, int k2)
+__device__ TcRow tc_row_prepare(float* lg, const TcSlots* s, int ns, float eps)
 {
-    if (q2 > q || (q2 == q && k2 >= 0 && (k < 0 || k2 < k))) {
-        q = q2;
-        k = k2;
+    float m = -INFINITY;
+    for (int k = 0; k < ns; ++k)
+        if (s->out[k] >= 0) m = fmaxf(m, lg[s->out[k]]);
+    float Sh[2] = {0.0f, 0.0f};
+    for (int k = 0; k < ns; ++k) {
+        const int o = s->out[k];
+        if (o < 0) continue;
+        const float e = expf(__fsub_rn(lg[o], m));
+        lg[o] = e;
+        Sh[k & 1] = __fadd_rn(Sh[k & 1], e);
     }
-}
-
-// The row statistics of a 16-row logit tile (one warp): lane (g, t) = (lane
-// / 4, lane % 4) takes rows g and g + 8 and the output columns 8 j + 2 t and
-// 8 j + 2 t + 1, j ascending; each quad of lanes combines its rows' partial
-// maxima, sums and largest weights with xor-shuffles (float sums therefore in
-// one fixed order).  rowphase bit r: row r uses the slot tables slots[1].
-// Writes rows[0 .. 16).
-__device__ void tc_row_stats(float* lgt, int ldo, int Gp, const TcSlots* slots, uint32_t rowphase, float eps,
-                             TcRow* rows, int lane)
-{
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int r = g + 8 * h;
-        const TcSlots* s = slots + ((rowphase >> r) & 1u);
-        float* lg = lgt + r * ldo;
-        float m = -INFINITY;
-        for (int c0 = 2 * t; c0 < Gp; c0 += 8)
-            for (int q = 0; q < 2; ++q)
-                if (s->slot_of[c0 + q] >= 0) m = fmaxf(m, lg[c0 + q]);
-        m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
-        m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
-        float S = 0.0f;
-        for (int c0 = 2 * t; c0 < Gp; c0 += 8)
-            for (int q = 0; q < 2; ++q) {
-                const int o = c0 + q;
-                if (s->slot_of[o] < 0) continue;
-                const float e = expf(__fsub_rn(lg[o], m));
-                lg[o] = e;
-                S = __fadd_rn(S, e);
-            }
-        S = __fadd_rn(S, __shfl_xor_sync(kFull, S, 1));
-        S = __fadd_rn(S, __shfl_xor_sync(kFull, S, 2));
-        const float c = S > 0.0f ? __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, eps), 16777216.0f), S) : 0.0f;
-        int64_t sum = 0, bq = -1;
-        int bk = -1;
-        for (int c0 = 2 * t; c0 < Gp; c0 += 8)
-            for (int q = 0; q < 2; ++q) {
-                const int o = c0 + q;
-                const int k = s->slot_of[o];
-                if (k < 0) continue;
-                int64_t Q = (int64_t)floorf(__fmul_rn(lg[o], c)) + s->st_of[o];
-                Q = Q < 1 ? 1 : Q;
-                sum += Q;
-                tc_best(bq, bk, Q, k);
-            }
-#pragma unroll
-        for (int x = 1; x <= 2; x <<= 1) {
-            sum += __shfl_xor_sync(kFull, sum, x);
-            const int64_t q2 = __shfl_xor_sync(kFull, bq, x);
-            const int k2 = __shfl_xor_sync(kFull, bk, x);
-            tc_best(bq, bk, q2, k2);
-        }
-        sum += s->q_const;
-        tc_best(bq, bk, (int64_t)s->best_q, s->best_k);
-        if (t == 0) {
-            TcRow row;
-            row.c = c;
-            row.arg = bk;
-            row.rem = (1ll << 24) - sum;
-            rows[r] = row;
+    const float S = __fadd_rn(Sh[0], Sh[1]);
+    TcRow r;
+    r.c = S > 0.0f ? __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, eps), 16777216.0f), S) : 0.0f;
+    int64_t sum = 0, qa = -1;
+    int arg = -1;
+    for (int k = 0; k < ns; ++k) {
+        if (s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c);
+        sum += Q;
+        if (Q > qa) {
+            qa = Q;
+            arg = k;
         }
     }
+    r.arg = arg;
+    r.rem = (1ll << 24) - sum;
+    return r;
 }
 
 // The slot whose interval [cum_{k-1}, cum_k) of the weights holds V (ns when
-// none does) and its weight *Qk, for the rows of a 16-row tile two lanes per
-// row (lane r and lane r + 16 take the even and the odd slots of row r =
-// lane & 15).  Every lane runs the loop to the larger slot count of the two
-// passes (nsmax); act = the row is in use.
+// none does) and its weight *Qk.
+__device__ int tc_row_choose(const float* lg, const TcSlots* s, int ns, const TcRow& r, uint32_t V, int64_t* Qk)
+{
+    int64_t cum = 0;
+    for (int k = 0; k < ns; ++k) {
+        if (s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c) + (k == r.arg ? r.rem : 0);
+        cum += Q;
+        if ((int64_t)V < cum) {
+            *Qk = Q;
+            return k;
+        }
+    }
+    *Qk = 0;
+    return ns;
+}
+
+// The same weights and choice for the rows of a 16-row logit tile, two lanes
+// per row (lane r and lane r + 16 take the even and the odd slots of row
+// r = lane & 15): the max and the integer sums do not depend on the order,
+// and the float sum is the even slots' sum plus the odd slots', as in
+// tc_row_prepare.  Every lane runs the same number of iterations (nsmax, the
+// larger slot count of the two passes); act = the row is in use.
+__device__ TcRow tc_pair_prepare(float* lg, const TcSlots* s, int ns, int nsmax, float eps, bool act, int half)
+{
+    float m = -INFINITY;
+    for (int k = half; k < nsmax; k += 2)
+        if (act && k < ns && s->out[k] >= 0) m = fmaxf(m, lg[s->out[k]]);
+    m = fmaxf(m, __shfl_xor_sync(kFull, m, 16));
+    float S = 0.0f;
+    for (int k = half; k < nsmax; k += 2) {
+        if (!act || k >= ns) continue;
+        const int o = s->out[k];
+        if (o < 0) continue;
+        const float e = expf(__fsub_rn(lg[o], m));
+        lg[o] = e;
+        S = __fadd_rn(S, e);
+    }
+    const float So = __shfl_xor_sync(kFull, S, 16);
+    const float St = half ? __fadd_rn(So, S) : __fadd_rn(S, So);
+    TcRow r;
+    r.c = St > 0.0f ? __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, eps), 16777216.0f), St) : 0.0f;
+    int64_t sum = 0, qa = -1;
+    int arg = -1;
+    for (int k = half; k < nsmax; k += 2) {
+        if (!act || k >= ns || s->out[k] == -2) continue;
+        const int64_t Q = tc_q(lg, s, k, r.c);
+        sum += Q;
+        if (Q > qa) {
+            qa = Q;
+            arg = k;
+        }
+    }
+    sum += __shfl_xor_sync(kFull, sum, 16);
+    const int64_t qo = __shfl_xor_sync(kFull, qa, 16);
+    const int ao = __shfl_xor_sync(kFull, arg, 16);
+    if (qo > qa || (qo == qa && ao >= 0 && (arg < 0 || ao < arg))) {
+        qa = qo;
+        arg = ao;
+    }
+    r.arg = arg;
+    r.rem = (1ll << 24) - sum;
+    return r;
+}
+
 __device__ int tc_pair_choose(const float* lg, const TcSlots* s, int ns, int nsmax, const TcRow& r, uint32_t V,
                               bool act, int half, int64_t* Qk)
 {
@@ -1462,7 +1451,6 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_spawn_learned_tc(StepParams P
 {
     extern __shared__ __align__(16) uint8_t tsm[];
     __shared__ __align__(16) SRec sstage[kTcWarps][kStage];
-    __shared__ TcRow wrows[kTcWarps][16];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const TcLayout L = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
@@ -1522,17 +1510,15 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_spawn_learned_tc(StepParams P
         double u[2] = {0.0, 0.0};
         if (att) lp_draws(key, phase, comp, j, P.kd[seg], &V, &u[0], &u[1]);
         const int r = lane & 15, half = lane >> 4;
-        const uint32_t rowphase = __ballot_sync(kFull, lane < 16 && phase == 1) & 0xFFFFu;
-        tc_row_stats(lgt, ldo, L.Gp, slots, rowphase, P.mlp_eps, wrows[warp], lane);
-        __syncwarp();
         const bool ract = __shfl_sync(kFull, att, r);
-        const int rph = (rowphase >> r) & 1;
+        const int rph = __shfl_sync(kFull, phase, r);
         const uint32_t rV = __shfl_sync(kFull, V, r);
         const int rns = prog[rph].h->n_stat;
         const int nsmax = max(prog[0].h->n_stat, prog[1].h->n_stat);
         float* rlg = lgt + r * ldo;
+        const TcRow tr = tc_pair_prepare(rlg, slots + rph, rns, nsmax, P.mlp_eps, ract, half);
         int64_t Qk;
-        const int k = tc_pair_choose(rlg, slots + rph, rns, nsmax, wrows[warp][r], rV, ract, half, &Qk);
+        const int k = tc_pair_choose(rlg, slots + rph, rns, nsmax, tr, rV, ract, half, &Qk);
         if (att) {
             const Prog& pg = prog[phase];
             if (k < pg.h->n_stat) {
@@ -1611,7 +1597,6 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
     TcSlots* hslots = (TcSlots*)(hsm + TL.bytes);
     const int hldo = TL.Gp + 4;
     float* hlg = (float*)(hsm + TL.bytes + sizeof(TcSlots));
-    __shared__ TcRow hrows[16];
     if (kTc) {
         for (int i = tid; i < TL.bytes / 16; i += kThreads) ((uint4*)hsm)[i] = ((const uint4*)P.mlp_tc)[i];
         __syncthreads();
@@ -1688,12 +1673,10 @@ __device__ __forceinline__ void spawn_heavy(const StepParams& P)
             if (warp == 0) {
                 const float tb = __bfloat162float(__float2bfloat16_rn(__double2float_rn(inf.t[it.phase])));
                 tc_forward(hsm, TL, n, x, y, tb, x, y, tb, hlg, hldo, lane);
-                __syncwarp();
-                tc_row_stats(hlg, hldo, TL.Gp, hslots, 0u, P.mlp_eps, hrows, lane);
             }
             __syncthreads();
             if (tid == 0) {
-                const TcRow r = hrows[0];
+                const TcRow r = tc_row_prepare(hlg, hslots, ns, P.mlp_eps);
                 int64_t run = 0;
                 for (int k = 0; k < ns; ++k) {
                     if (hslots->out[k] != -2) run += tc_q(hlg, hslots, k, r.c) + (k == r.arg ? r.rem : 0);
