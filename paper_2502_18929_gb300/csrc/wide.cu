@@ -302,8 +302,12 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
         int64_t first = 0;
         uint2 kd = make_uint2(0u, 0u);
         int64_t pre = -1;
+        // the vector of the warp's first group, then per lane only across a boundary
+        int seg0 = lane == 0 ? wgroup_seg(gof, P.nseg, base) : 0;
+        seg0 = __shfl_sync(kFull, seg0, 0);
+        const int64_t seg0_end = gof[seg0 + 1];
         if (g < G) {
-            seg = wgroup_seg(gof, P.nseg, g);
+            seg = g < seg0_end ? seg0 : wgroup_seg(gof, P.nseg, g);
             grp = (uint32_t)(g - gof[seg]);
             first = off[seg] + 4 * (int64_t)grp;
             const int cnt = (int)min((int64_t)4, off[seg + 1] - first);
@@ -329,14 +333,36 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
                 }
             }
         }
-        // first walkers: one call for the group
+        // first walkers: one call for the group; the warp's candidates of the
+        // round appended with one atomic
         const uint4 gw0 = g < G ? group_words(grp, 0u, phase, kd) : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t on = 0u;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t Wd = word_of(gw0, k);
-            const bool on = m[k] > 0 && (int64_t)Wd <= pre;
-            warp_append_cand(P, on, make_uint4((uint32_t)(first + k), (uint32_t)seg, Wd, (uint32_t)phase << 31),
-                             lane);
+        for (int k = 0; k < 4; ++k)
+            if (m[k] > 0 && (int64_t)word_of(gw0, k) <= pre) on |= 1u << k;
+        const int cnt = __popc(on);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int wtot = __shfl_sync(kFull, incl, 31);
+        if (wtot > 0) {
+            unsigned long long cb = 0;
+            if (lane == 31) cb = atomicAdd((unsigned long long*)&st->cand_total, (unsigned long long)wtot);
+            cb = __shfl_sync(kFull, cb, 31);
+            int64_t pos = (int64_t)cb + incl - cnt;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!((on >> k) & 1u)) continue;
+                if (pos < P.cand_cap)
+                    ((uint4*)P.cand)[pos] = make_uint4((uint32_t)(first + k), (uint32_t)seg, word_of(gw0, k),
+                                                       (uint32_t)phase << 31);
+                else
+                    set_error(st, DERR_CAND_CAPACITY);
+                ++pos;
+            }
         }
         // second walkers: one more call; further walkers: the parent's calls
         const bool two = m[0] > 1 || m[1] > 1 || m[2] > 1 || m[3] > 1;
