@@ -287,6 +287,18 @@ int qmc_learn_events(qmc_ctx* ctx, double dt, int64_t max_events, float* feat, f
 int qmc_learn_grad(qmc_ctx* ctx, const float* params, const float* feat, const float* target, const float* weight,
                    int64_t ld, int64_t n_events, float* grad, double* loss);
 
+/* The learned proposal's integer weights Q_k (summing to 2^24) for count
+ * sources |x[i]><y[i]| (host arrays, x, y < 2^n) under the static column of
+ * dt_eff L(t), by the current proposal mode: QMC_PROPOSAL_LEARNED the FP32
+ * network, the values the step uses bit for bit; QMC_PROPOSAL_LEARNED_TC the
+ * tensor-core network as the step evaluates it.  Q[i * cap_slots + k] for
+ * the column's static slot k (ascending destination mask; 0 where the slot
+ * has width 0); *n_slots receives the slot count.  Errors: INVALID_ARG
+ * (another mode, cap_slots too small, above 32 qubits), STATE (no schedule or
+ * network), COEF_RANGE. */
+int qmc_learned_weights(qmc_ctx* ctx, double t, double dt_eff, const uint64_t* x, const uint64_t* y, int32_t count,
+                        int64_t* Q, int32_t cap_slots, int32_t* n_slots);
+
 /* As qmc_learn_grad for the tensor-core proposal's network
  * (QMC_PROPOSAL_LEARNED_TC): inputs -> GELU -> GELU -> logits with the
  * weights and both hidden activations taken as bf16 and fp32 accumulation

@@ -3277,6 +3277,133 @@ int resident(const void* fn, int smem, int sms, int threads = kThreads)
 }
 } // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// The learned proposal's integer weights Q_k for given sources under one
+// program (a host query and the tests' handle on the forward pass): out[i *
+// cap + k] for slot k of source i, 0 on slots of width 0.  FP32 network: one
+// thread per source, the light kernel's arithmetic; tensor cores: one warp
+// per 16 sources, the light kernel's forward pass and row weights.
+// ---------------------------------------------------------------------------
+__global__ void k_learned_weights(StepParams P, const uint8_t* __restrict__ pb, double t,
+                                  const uint64_t* __restrict__ xs, const uint64_t* __restrict__ ys, int count,
+                                  int64_t* __restrict__ out, int cap)
+{
+    const Prog prog = prog_at(pb);
+    const LpNet net = lp_net(P);
+    const int ns = prog.h->n_stat;
+    const int64_t p_att = prog.h->p_att;
+    const int n = P.n;
+    const float tf32 = __double2float_rn(t);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)xs[i], y = (uint32_t)ys[i];
+        float h1[kMaxHidden], h2[kMaxHidden];
+        for (int q = 0; q < net.H; ++q) h1[q] = lp_h1(net, q, x, y, n, tf32);
+        for (int q = 0; q < net.H; ++q) h2[q] = lp_h2(net, q, h1);
+        float e[kMaxLearnedSlots];
+        int16_t g[kMaxLearnedSlots];
+        float m = -INFINITY;
+        for (int k = 0; k < ns; ++k) {
+            g[k] = (int16_t)(slot_width(prog, k) > 0 ? lp_output(P, prog.stat[k].mask) : -1);
+            if (g[k] >= 0) {
+                e[k] = lp_logit(net, g[k], h2);
+                if (e[k] > m) m = e[k];
+            }
+        }
+        float S = 0.0f;
+        for (int k = 0; k < ns; ++k)
+            if (g[k] >= 0) {
+                e[k] = lp_exp(__fsub_rn(e[k], m));
+                S = __fadd_rn(S, e[k]);
+            }
+        int64_t sum = 0, qa = -1;
+        int arg = -1;
+        for (int k = 0; k < ns; ++k) {
+            const int64_t w = slot_width(prog, k);
+            if (w <= 0) continue;
+            const int64_t Q = lp_q(e[k], g[k] >= 0, S, P.mlp_eps, w, p_att);
+            sum += Q;
+            if (arg < 0 || Q > qa) {
+                arg = k;
+                qa = Q;
+            }
+        }
+        for (int k = 0; k < ns; ++k) {
+            const int64_t w = slot_width(prog, k);
+            int64_t Q = w <= 0 ? 0 : lp_q(e[k], g[k] >= 0, S, P.mlp_eps, w, p_att);
+            if (k == arg) Q += (1ll << 24) - sum;
+            out[(int64_t)i * cap + k] = Q;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32) k_learned_weights_tc(StepParams P, const uint8_t* __restrict__ pb, double t,
+                                                           const uint64_t* __restrict__ xs,
+                                                           const uint64_t* __restrict__ ys, int count,
+                                                           int64_t* __restrict__ out, int cap)
+{
+    extern __shared__ __align__(16) uint8_t tsm[];
+    const TcLayout L = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < L.bytes / 16; i += 32) ((uint4*)tsm)[i] = ((const uint4*)P.mlp_tc)[i];
+    TcSlots* slots = (TcSlots*)(tsm + L.bytes);
+    const int ldo = L.Gp + 4;
+    float* lgt = (float*)(tsm + L.bytes + sizeof(TcSlots));
+    const Prog prog = prog_at(pb);
+    tc_slots_fill(P, prog, slots, lane, 32);
+    __syncthreads();
+    const int ns = prog.h->n_stat;
+    const int n = P.n;
+    const float tb = __bfloat162float(__float2bfloat16_rn(__double2float_rn(t)));
+    for (int tile = blockIdx.x; tile * 16 < count; tile += gridDim.x) {
+        const int i = tile * 16 + lane;
+        uint32_t x = 0u, y = 0u;
+        if (lane < 16 && i < count) {
+            x = (uint32_t)xs[i];
+            y = (uint32_t)ys[i];
+        }
+        const int ga = lane >> 2, gb = ga + 8;
+        const uint32_t xa = __shfl_sync(kFull, x, ga), ya = __shfl_sync(kFull, y, ga);
+        const uint32_t xb = __shfl_sync(kFull, x, gb), yb = __shfl_sync(kFull, y, gb);
+        tc_forward(tsm, L, n, xa, ya, tb, xb, yb, tb, lgt, ldo, lane);
+        __syncwarp();
+        const int r = lane & 15, half = lane >> 4;
+        const bool act = tile * 16 + r < count;
+        float* rlg = lgt + r * ldo;
+        const TcRow tr = tc_pair_prepare(rlg, slots, ns, ns, P.mlp_eps, act, half);
+        __syncwarp();
+        if (half == 0 && act)
+            for (int k = 0; k < ns; ++k) {
+                int64_t Q = 0;
+                if (slots->out[k] != -2) Q = tc_q(rlg, slots, k, tr.c) + (k == tr.arg ? tr.rem : 0);
+                out[(int64_t)(tile * 16 + r) * cap + k] = Q;
+            }
+        __syncwarp();
+    }
+}
+
+} // namespace
+
+int learned_weights_smem(const StepParams& P)
+{
+    const TcLayout L = tc_layout(P.mlp_in, P.mlp_hidden, P.mlp_out);
+    return L.bytes + (int)sizeof(TcSlots) + 16 * (L.Gp + 4) * 4;
+}
+
+void launch_learned_weights(const StepParams& P, bool tc, const uint8_t* prog, double t, const uint64_t* xs,
+                            const uint64_t* ys, int count, int64_t* out, int cap, cudaStream_t stream)
+{
+    if (count <= 0) return;
+    if (tc) {
+        const int smem = learned_weights_smem(P);
+        cudaFuncSetAttribute(k_learned_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_learned_weights_tc<<<(count + 15) / 16, 32, smem, stream>>>(P, prog, t, xs, ys, count, out, cap);
+    } else {
+        k_learned_weights<<<(count + 127) / 128, 128, 0, stream>>>(P, prog, t, xs, ys, count, out, cap);
+    }
+}
+
 void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);

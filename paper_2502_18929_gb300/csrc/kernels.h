@@ -216,6 +216,8 @@ void launch_wide_lookup(const StepParams& P, int seg, const uint64_t* qx, const 
 void launch_wide_export(const StepParams& P, int slot, int64_t first, int64_t count, uint64_t* x, uint64_t* y,
                         int32_t* re, int32_t* im, cudaStream_t stream);
 
+void launch_learned_weights(const StepParams& P, bool tc, const uint8_t* prog, double t, const uint64_t* xs,
+                            const uint64_t* ys, int count, int64_t* out, int cap, cudaStream_t stream);
 void configure_kernels();  // once per process, before the first launch
 extern const char* const kKernelNames[kNumTimedKernels];
 void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);

@@ -765,6 +765,50 @@ int64_t mlp_param_count(const qmc_ctx* c)
 } // namespace
 
 
+int qmc_learned_weights(qmc_ctx* ctx, double t, double dt_eff, const uint64_t* x, const uint64_t* y, int32_t count,
+                        int64_t* Q, int32_t cap_slots, int32_t* n_slots)
+{
+    if (ctx && ctx->wide) return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_learned_weights: not available above 32 qubits");
+    if (!ctx || !n_slots || count < 0 || cap_slots < 0 || (count > 0 && (!x || !y || !Q)) || !(dt_eff > 0.0))
+        return QMC_ERR_INVALID_ARG;
+    const bool tc = ctx->proposal == QMC_PROPOSAL_LEARNED_TC;
+    if (!tc && ctx->proposal != QMC_PROPOSAL_LEARNED)
+        return fail(ctx, QMC_ERR_INVALID_ARG, "qmc_learned_weights: set a learned proposal first");
+    if (!has_schedules(ctx) || !ctx->d_mlp || (tc && !ctx->d_mlp_tc))
+        return fail(ctx, QMC_ERR_STATE, "load a schedule and the network first");
+    const int n = ctx->inst[0].n;
+    const uint64_t lim = (1ull << n) - 1ull;
+    for (int32_t i = 0; i < count; ++i)
+        if ((x[i] & ~lim) || (y[i] & ~lim)) return fail(ctx, QMC_ERR_INVALID_ARG, "x or y >= 2^n");
+    std::vector<uint8_t> blob;
+    int rc = build_program(ctx->inst[0].sched, t, dt_eff, &blob);
+    if (rc != QMC_OK) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
+    const ProgHeader* h = (const ProgHeader*)blob.data();
+    *n_slots = h->n_stat;
+    if (h->n_stat > kMaxLearnedSlots) return fail(ctx, QMC_ERR_INVALID_ARG, "more than 256 destinations per column");
+    if (h->n_stat > cap_slots) return fail(ctx, QMC_ERR_INVALID_ARG, "cap_slots below the column's slot count");
+    if (count == 0) return QMC_OK;
+    if ((rc = enter(ctx)) != QMC_OK) return rc;
+    uint8_t* d_prog = nullptr;
+    uint64_t *d_x = nullptr, *d_y = nullptr;
+    int64_t* d_q = nullptr;
+    Scratch tmp(ctx);
+    if ((rc = tmp.get(&d_prog, (int64_t)blob.size())) != QMC_OK || (rc = tmp.get(&d_x, count)) != QMC_OK ||
+        (rc = tmp.get(&d_y, count)) != QMC_OK || (rc = tmp.get(&d_q, (int64_t)count * h->n_stat)) != QMC_OK)
+        return rc;
+    CK(cudaMemcpyAsync(d_prog, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(d_x, x, (size_t)count * 8, cudaMemcpyHostToDevice, ctx->work));
+    CK(cudaMemcpyAsync(d_y, y, (size_t)count * 8, cudaMemcpyHostToDevice, ctx->work));
+    launch_learned_weights(params(ctx), tc, d_prog, t, d_x, d_y, count, d_q, h->n_stat, ctx->work);
+    CK(cudaGetLastError());
+    std::vector<int64_t> hq((size_t)count * h->n_stat);
+    CK(cudaMemcpyAsync(hq.data(), d_q, hq.size() * 8, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    for (int32_t i = 0; i < count; ++i)
+        for (int k = 0; k < h->n_stat; ++k) Q[(int64_t)i * cap_slots + k] = hq[(size_t)i * h->n_stat + k];
+    return leave(ctx);
+}
+
 int qmc_learn_param_count(qmc_ctx* ctx, int64_t* n_params)
 {
     if (!ctx || !n_params) return QMC_ERR_INVALID_ARG;

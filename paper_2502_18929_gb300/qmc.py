@@ -40,7 +40,7 @@ EXPORTED = [
     "qmc_learn_param_count", "qmc_learn_events", "qmc_learn_grad", "qmc_learn_adam", "qmc_learn_load",
     "qmc_set_tuning", "qmc_get_tuning", "qmc_autotune", "qmc_set_spin_limit", "qmc_z_history",
     "qmc_overlap_all", "qmc_antihermiticity", "qmc_antihermiticity_sum", "qmc_learn_grad_tc", "qmc_memory",
-    "qmc_export_xy", "qmc_set_populations_xy", "qmc_step_kernel_name",
+    "qmc_export_xy", "qmc_set_populations_xy", "qmc_step_kernel_name", "qmc_learned_weights",
 ]
 
 
@@ -178,6 +178,8 @@ def lib():
         L.qmc_observables_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
         L.qmc_memory.argtypes = [vp, vp]
         L.qmc_set_populations_xy.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
+        L.qmc_learned_weights.argtypes = [vp, C.c_double, C.c_double, vp, vp, C.c_int32, vp, C.c_int32,
+                                          C.POINTER(C.c_int32)]
         L.qmc_export_xy.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, C.c_int64, C.POINTER(C.c_int64)]
         L.qmc_kernel_name.argtypes = [C.c_int32]
         L.qmc_kernel_name.restype = C.c_char_p
@@ -352,6 +354,16 @@ class QMC:
         return {"max_ctas": t.max_ctas, "heavy_walkers": t.heavy_walkers, "bucket_records": t.bucket_records}
 
     # -- training of the learned proposal (device tensors) ---------------------
+    def learned_weights(self, t: float, dt_eff: float, xs, ys, cap_slots: int = 256) -> np.ndarray:
+        """The learned proposal's integer weights (count, n_slots) for sources
+        |x><y| under the static column of dt_eff L(t) (qmc_learned_weights)."""
+        x, y = _arr(xs, np.uint64), _arr(ys, np.uint64)
+        Q = np.zeros((max(1, len(x)), cap_slots), dtype=np.int64)
+        ns = C.c_int32()
+        self._check(self.L.qmc_learned_weights(self.h, t, dt_eff, _ptr(x), _ptr(y), len(x), Q.ctypes.data, cap_slots,
+                                               C.byref(ns)), "qmc_learned_weights")
+        return Q[:len(x), :ns.value]
+
     def learn_param_count(self) -> int:
         n = C.c_int64()
         self._check(self.L.qmc_learn_param_count(self.h, C.byref(n)), "qmc_learn_param_count")
