@@ -110,11 +110,12 @@ def capacity_hint(wl, nsteps: int) -> int:
     state: the records grow by about 1.3 % of the initial count per step in
     the CNOT window (new keys reached by spawns), so size for 2 % per step
     plus a quarter, and no buffer has to grow (and a step be redone) inside
-    the timed region.  Workloads that start from a single state get one
-    record per walker (a vector never holds more records than walkers, up to
-    the spawns of one step)."""
+    the timed region.  Workloads that start from a single state get two
+    records per initial walker (a vector holds at most one record per walker,
+    and without the initiator the walker number grows), which also sizes the
+    spawn buffer (a quarter of the hint)."""
     if "spread" not in wl:
-        return int(wl["n_diag"] * wl["nseg"] * 1.2)
+        return int(wl["n_diag"] * wl["nseg"] * 2)
     base = wl["spread"] * wl["nseg"]
     return int(base * (1.0 + 0.02 * nsteps) * 1.25)
 
