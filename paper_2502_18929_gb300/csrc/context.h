@@ -111,8 +111,9 @@ struct qmc_ctx {
     int64_t last_call_steps = 0;
     int64_t acc_redo = 0;   // step launches repeated after a buffer grew (qmc_counters out[10])
 
-    // 33..60 qubits: 128-bit keys; d_pop holds WRec records and the step is
-    // the wide kernels' (wide.cu)
+    // 33..60 qubits: 128-bit keys; each d_pop slot holds pop_cap 16-byte keys
+    // followed by pop_cap 8-byte values (24 bytes a record, structure of
+    // arrays) and the step is the wide kernels' (wide.cu)
     bool wide = false;
     qmc::WSpawn* d_wspawn = nullptr;
     qmc::WSpawn* d_wspawn_alt = nullptr;
@@ -121,7 +122,9 @@ struct qmc_ctx {
     int64_t* d_wscan_u = nullptr;
     int2* d_wdelta = nullptr;
     int32_t* d_wnewcnt = nullptr;
-    int64_t* d_wcnt_a = nullptr;
+    unsigned long long* d_wmtile = nullptr;
+    longlong2* d_wmbase = nullptr;
+    int64_t wmtiles_cap = 0;
     int64_t* d_wscan_a = nullptr;
     int64_t* d_wpart = nullptr;
     int64_t wpart_cap = 0;

@@ -244,7 +244,9 @@ WideParams wparams(qmc_ctx* c)
     W.scan_u = c->d_wscan_u;
     W.delta = c->d_wdelta;
     W.newcnt = c->d_wnewcnt;
-    W.cnt_a = c->d_wcnt_a;
+    W.mtile = c->d_wmtile;
+    W.mbase = c->d_wmbase;
+    W.mtiles_cap = c->wmtiles_cap;
     W.scan_a = c->d_wscan_a;
     W.part = c->d_wpart;
     W.part_cap = c->wpart_cap;
@@ -372,8 +374,16 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
         Rec* np = (Rec*)mem_alloc(ctx, (size_t)cap * rec_bytes);
         if (!np) return fail(ctx, QMC_ERR_OOM, "population buffer allocation failed");
         const int64_t keep = std::min<int64_t>(hs.count[i], std::min(ctx->pop_cap, cap));
-        if (ctx->d_pop[i] && keep > 0)
+        if (ctx->d_pop[i] && keep > 0 && ctx->wide) {
+            // keys [0, cap) x 16 bytes, then values x 8 bytes: the value region moves with the capacity
+            uint8_t* dst = (uint8_t*)np;
+            const uint8_t* src = (const uint8_t*)ctx->d_pop[i];
+            CK(cudaMemcpyAsync(dst, src, (size_t)keep * 16, cudaMemcpyDeviceToDevice, ctx->work));
+            CK(cudaMemcpyAsync(dst + 16 * (size_t)cap, src + 16 * (size_t)ctx->pop_cap, (size_t)keep * 8,
+                               cudaMemcpyDeviceToDevice, ctx->work));
+        } else if (ctx->d_pop[i] && keep > 0) {
             CK(cudaMemcpyAsync(np, ctx->d_pop[i], (size_t)keep * rec_bytes, cudaMemcpyDeviceToDevice, ctx->work));
+        }
         mem_free(ctx, ctx->d_pop[i]);   // in stream order, after the copy
         ctx->d_pop[i] = np;
     }
@@ -383,11 +393,15 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
         int rc;
         if ((rc = dalloc(ctx, &ctx->d_wdelta, cap + 1)) != QMC_OK ||
             (rc = dalloc(ctx, &ctx->d_wnewcnt, cap + 1)) != QMC_OK ||
-            (rc = dalloc(ctx, &ctx->d_wcnt_a, cap + 1)) != QMC_OK ||
             (rc = dalloc(ctx, &ctx->d_wscan_a, cap + 2)) != QMC_OK)
+            return rc;
+        ctx->wmtiles_cap = cap / kWMTile + 2;
+        if ((rc = dalloc(ctx, &ctx->d_wmtile, ctx->wmtiles_cap)) != QMC_OK ||
+            (rc = dalloc(ctx, &ctx->d_wmbase, ctx->wmtiles_cap)) != QMC_OK)
             return rc;
         CK(cudaMemsetAsync(ctx->d_wdelta, 0, (size_t)(cap + 1) * sizeof(int2), ctx->work));
         CK(cudaMemsetAsync(ctx->d_wnewcnt, 0, (size_t)(cap + 1) * sizeof(int32_t), ctx->work));
+        CK(cudaMemsetAsync(ctx->d_wmtile, 0, (size_t)ctx->wmtiles_cap * 8, ctx->work));
         return grow_wpart(ctx);
     }
     return grow_merge_tiles(ctx);
@@ -449,6 +463,7 @@ int map_dev_error(qmc_ctx* ctx, uint32_t code, uint32_t aux = 0)
     case DERR_DT_TOO_LARGE: return fail(ctx, QMC_ERR_DT_TOO_LARGE, "spawn probability p >= 1: reduce dt");
     case DERR_POP_OVERFLOW: return fail(ctx, QMC_ERR_POP_OVERFLOW, "a population component exceeds 2^31 - 1");
     case DERR_TIMEOUT: return fail(ctx, QMC_ERR_DEVICE_TIMEOUT, std::string("a bounded device wait expired") + site);
+    case DERR_INTERNAL: return fail(ctx, QMC_ERR_STATE, "the step's self-check failed: merge counts disagree");
     default: return fail(ctx, QMC_ERR_CAPACITY, "capacity error");
     }
 }
@@ -1291,8 +1306,8 @@ int qmc_set_populations_xy(qmc_ctx* ctx, int32_t which, const int64_t* counts, c
     }
     CK(cudaMemcpyAsync(ctx->d_segoff[slot], off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, ctx->work));
     if (total)
-        launch_wide_pack(d_x, d_y, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->d_seginfo, (WRec*)ctx->d_pop[slot],
-                         d_bad, ctx->work);
+        launch_wide_pack(d_x, d_y, d_re, d_im, ctx->d_segoff[slot], nseg, ctx->d_seginfo, (uint8_t*)ctx->d_pop[slot],
+                         ctx->pop_cap, d_bad, ctx->work);
     CK(cudaGetLastError());
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
@@ -1467,6 +1482,7 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
             // a failed wide step may have left merge scratch behind: zero it for the redo
             CK(cudaMemsetAsync(ctx->d_wdelta, 0, (size_t)(ctx->pop_cap + 1) * sizeof(int2), ctx->work));
             CK(cudaMemsetAsync(ctx->d_wnewcnt, 0, (size_t)(ctx->pop_cap + 1) * sizeof(int32_t), ctx->work));
+            CK(cudaMemsetAsync(ctx->d_wmtile, 0, (size_t)ctx->wmtiles_cap * 8, ctx->work));
         }
         if (code == DERR_SPAWN_CAPACITY) {
             if ((rc = grow_spawn(ctx, hs.spawn_total)) != QMC_OK) return rc;

@@ -42,7 +42,8 @@ static_assert(sizeof(Rec) == 16, "population record must be 16 bytes");
 static_assert(sizeof(SRec) == 16, "spawn record must be 16 bytes");
 
 // Wide records (33..60 qubits): the key (x << n) | y as two 64-bit words,
-// compared high word first.
+// compared high word first.  WRec is a record in registers; in memory a
+// population slot stores its keys and its values as two arrays.
 struct WRec {
     uint64_t lo, hi;
     int32_t re, im;
@@ -179,6 +180,7 @@ enum DevError : uint32_t {
     DERR_HEAVY_CAPACITY = 6,
     DERR_TILE_CAPACITY = 7,
     DERR_CAND_CAPACITY = 8,
+    DERR_INTERNAL = 9,   // a step's self-check failed (counts of two kernels disagree)
 };
 
 constexpr int kMaxTileCounters = 32;

@@ -15,12 +15,15 @@
 //                       over tiles per digit, scatter with warp-match ranks
 //   k_wide_spawn_off    vector boundaries of the sorted spawns
 //   k_wide_runs         runs of equal keys: summed spawns under the initiator
-//                       rule, the key's position in N(t)
-//   k_wide_match        each record of N(t) with the spawns on its key
-//   k_wide_scan_*       exclusive prefix sums of the survivors
-//   k_wide_scatter_*    N(t + dt) = the survivors in key order [End Matter,
+//                       rule, the key's position in N(t), per merge tile the
+//                       records zeroed and the new keys
+//   k_wide_mtop         survivors and new keys before every merge tile
+//   k_wide_scan_*       exclusive prefix sums of the new keys
+//   k_wide_merge_a /
+//   k_wide_scatter_u    N(t + dt) = the survivors in key order [End Matter,
 //                       annihilation step], with the per-vector observables
-//   k_wide_finalize     vector offsets of N(t + dt), history, rotate the slots
+//   k_wide_outoff       vector offsets of N(t + dt)
+//   k_wide_finalize     history, counters, rotate the slots
 //
 // Integer-only, like the 64-bit step: results are bit-identical to the
 // oracle whatever the launch shape.
@@ -41,15 +44,38 @@ __device__ __forceinline__ u128 wkey(uint64_t lo, uint64_t hi) { return ((u128)h
 __device__ __forceinline__ u128 wkey(const WRec& r) { return wkey(r.lo, r.hi); }
 __device__ __forceinline__ u128 wkey(const WSpawn& r) { return wkey(r.lo, r.hi); }
 
-__device__ __forceinline__ WRec wload(const WRec* p, int64_t i)
+// A population slot in structure-of-arrays form: pop_cap 16-byte keys (low
+// word, high word), then pop_cap 8-byte values (re, im) -- 24 bytes a record,
+// keys and values each read with one vector access.
+struct WPop {
+    ulonglong2* key;
+    int2* val;
+};
+
+__device__ __forceinline__ WPop wpop(const StepParams& P, int slot)
 {
+    uint8_t* b = (uint8_t*)P.pop[slot];
+    return WPop{(ulonglong2*)b, (int2*)(b + 16 * P.pop_cap)};
+}
+
+__device__ __forceinline__ u128 wkey(const ulonglong2& k) { return ((u128)k.y << 64) | (u128)k.x; }
+
+__device__ __forceinline__ WRec wload(const WPop& p, int64_t i)
+{
+    const ulonglong2 k = __ldg(&p.key[i]);
+    const int2 v = __ldg(&p.val[i]);
     WRec r;
-    r.lo = __ldg(&p[i].lo);
-    r.hi = __ldg(&p[i].hi);
-    const int2 v = __ldg((const int2*)&p[i].re);
+    r.lo = k.x;
+    r.hi = k.y;
     r.re = v.x;
     r.im = v.y;
     return r;
+}
+
+__device__ __forceinline__ void wstore(const WPop& p, int64_t i, u128 key, int32_t re, int32_t im)
+{
+    p.key[i] = make_ulonglong2((unsigned long long)(uint64_t)key, (unsigned long long)(uint64_t)(key >> 64));
+    p.val[i] = make_int2(re, im);
 }
 
 __device__ __forceinline__ WSpawn wsload(const WSpawn* p, int64_t i)
@@ -102,7 +128,7 @@ __device__ __forceinline__ bool weigh_parent(const StepParams& P, const WProg& p
 
 // Parent i of a slot with its column weight evaluated.  Returns false (after
 // raising the error) when its spawn probability reaches 1.
-__device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WRec* pop, const int64_t* off, int64_t i,
+__device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WPop& pop, const int64_t* off, int64_t i,
                             int phase, WParent* q, WProg* pr)
 {
     const WRec r = wload(pop, i);
@@ -288,7 +314,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
     const StepInfo inf = P.info[st->call_index];
     if (phase == 1 && !inf.ab2) return;
     const int slot = phase ? (st->cur + 2) % 3 : st->cur;
-    const WRec* pop = (const WRec*)P.pop[slot];
+    const WPop pop = wpop(P, slot);
     const int64_t* off = P.segoff[slot];
     const int64_t* gof = P.gofs[slot];
     const int64_t G = gof[P.nseg];
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k >= cnt) break;
-                const int2 v = __ldg((const int2*)&pop[first + k].re);
+                const int2 v = __ldg(&pop.val[first + k]);
                 m[k] = iabs64(v.x) + iabs64(v.y);
                 if (m[k] > kWLight) {
                     const int64_t nb = (m[k] - 2 + 3) / 4;
@@ -407,7 +433,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_choose(StepParams P, Wide
             const int slot = phase ? (st->cur + 2) % 3 : st->cur;
             WParent q;
             WProg pr;
-            if (load_parent(P, inf, (const WRec*)P.pop[slot], P.segoff[slot], (int64_t)c.x, phase, &q, &pr))
+            if (load_parent(P, inf, wpop(P, slot), P.segoff[slot], (int64_t)c.x, phase, &q, &pr))
                 sp = wide_walker(pr, q, (int64_t)(c.w & 0x7FFFFFFFu), c.z, &sr);
         }
         warp_append(P, W, sp, sr, lane);
@@ -437,7 +463,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_heavy(StepParams P, WidePara
         const int slot = h.phase ? (st->cur + 2) % 3 : st->cur;
         WParent q;
         WProg pr;
-        const bool ok = load_parent(P, inf, (const WRec*)P.pop[slot], P.segoff[slot], h.parent, h.phase, &q, &pr);
+        const bool ok = load_parent(P, inf, wpop(P, slot), P.segoff[slot], h.parent, h.phase, &q, &pr);
         const int ne = pr.h->n_entry;
         if (ok && ne <= kMaxEntries) {
             const int64_t m = iabs64(q.re) + iabs64(q.im);
@@ -713,7 +739,7 @@ __device__ __forceinline__ const WSpawn* sorted_spawns(const WideParams& W)
 }
 
 // First index of [lo, hi) of a population slot whose key is >= k.
-__device__ __forceinline__ int64_t lower_bound_pop(const WRec* a, int64_t lo, int64_t hi, u128 k)
+__device__ __forceinline__ int64_t lower_bound_pop(const ulonglong2* a, int64_t lo, int64_t hi, u128 k)
 {
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -751,6 +777,9 @@ __global__ void k_wide_spawn_off(StepParams P, WideParams W)
 }
 
 // Runs of equal (vector, key) among the sorted spawns, at their first record.
+// A run on a key N(t) holds leaves its spawn sum in delta and, when that
+// zeroes the record, counts it in the record's merge tile; a run that brings
+// a new key counts it before its position in N(t) and in that tile.
 __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParams W)
 {
     DevState* st = P.st;
@@ -758,7 +787,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
     const WSpawn* sp = sorted_spawns(W);
     const int64_t S = spawn_count(P);
     const int cur = st->cur;
-    const WRec* A = (const WRec*)P.pop[cur];
+    const WPop A = wpop(P, cur);
     const int64_t* offA = P.segoff[cur];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
         const WSpawn r = wsload(sp, i);
@@ -783,8 +812,8 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
             }
         }
         const int64_t lo = offA[seg], hi = offA[seg + 1];
-        const int64_t pos = lower_bound_pop(A, lo, hi, k);
-        const bool matched = pos < hi && wkey(A[pos]) == k;
+        const int64_t pos = lower_bound_pop(A.key, lo, hi, k);
+        const bool matched = pos < hi && wkey(A.key[pos]) == k;
         WRun run;
         run.posA = pos;
         run.re = matched ? are : ire;
@@ -794,65 +823,97 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
         W.run[i] = run;
         if (iabs64(run.re) > 2147483647ll || iabs64(run.im) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
         const bool fresh = !matched && (ire != 0 || iim != 0);
-        if (matched) W.delta[pos] = make_int2((int32_t)are, (int32_t)aim);   // the one run on this key
-        if (fresh) atomicAdd(&W.newcnt[pos], 1);
+        if (matched) {
+            W.delta[pos] = make_int2((int32_t)are, (int32_t)aim);   // the one run on this key
+            const int2 a = __ldg(&A.val[pos]);
+            const int64_t vr = (int64_t)a.x + are, vi = (int64_t)a.y + aim;
+            if (iabs64(vr) > 2147483647ll || iabs64(vi) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
+            if (vr == 0 && vi == 0) atomicAdd(&W.mtile[pos / kWMTile], 1ull);
+        }
+        if (fresh) {
+            atomicAdd(&W.newcnt[pos], 1);
+            atomicAdd(&W.mtile[pos / kWMTile], 1ull << 32);
+        }
         W.flag_u[i] = fresh ? 1 : 0;
     }
 }
 
-// Each record of N(t) with the spawns on its key (delta, left there by the
-// run) and the count of new keys just before it: its value after
-// annihilation, and survives | newcnt << 32 for the prefix sums.  Index K
-// (past the last record) carries the new keys after it.
-__global__ void __launch_bounds__(kWThreads) k_wide_match(StepParams P, WideParams W)
+// Merge tiles over the indices 0 .. K of N(t) (index K carries the new keys
+// after the last record).
+__device__ __forceinline__ int64_t merge_tiles(int64_t K) { return K / kWMTile + 1; }
+
+// Per merge tile (one CTA): survivors and new keys before it, from the
+// counts of the runs kernel (the records of a tile less those its spawns
+// zero); clears the counts for the next step; N(t + dt)'s size, with
+// POP_CAPACITY when it does not fit.
+__global__ void __launch_bounds__(1024) k_wide_mtop(StepParams P, WideParams W)
 {
+    __shared__ long long ws[32], wn[32];
     DevState* st = P.st;
     if (cta_error(st)) return;
-    const int cur = st->cur;
-    const WRec* A = (const WRec*)P.pop[cur];
-    const int64_t K = P.segoff[cur][P.nseg];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t nc = W.newcnt[i];
-        if (i == K) {
-            W.cnt_a[i] = nc << 32;
-            continue;
+    const int64_t K = P.segoff[st->cur][P.nseg];
+    const int64_t T = merge_tiles(K);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long cs = 0, cn = 0;
+    for (int64_t base = 0; base < T; base += blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        long long s = 0, nn = 0;
+        if (t < T) {
+            const unsigned long long m = W.mtile[t];
+            W.mtile[t] = 0ull;
+            const int64_t lo = t * kWMTile, hi = min(K, lo + kWMTile);
+            s = (hi - lo) - (long long)(m & 0xFFFFFFFFull);
+            nn = (long long)(m >> 32);
         }
-        const int2 d = W.delta[i];
-        const int2 v = __ldg((const int2*)&A[i].re);
-        int64_t re = (int64_t)v.x + d.x, im = (int64_t)v.y + d.y;
-        if (iabs64(re) > 2147483647ll || iabs64(im) > 2147483647ll) {
-            set_error(st, DERR_POP_OVERFLOW);
-            re = im = 0;
+        long long is = s, in = nn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long a = __shfl_up_sync(kFull, is, o), b = __shfl_up_sync(kFull, in, o);
+            if (lane >= o) {
+                is += a;
+                in += b;
+            }
         }
-        W.delta[i] = make_int2((int32_t)re, (int32_t)im);
-        W.cnt_a[i] = ((re != 0 || im != 0) ? 1ll : 0ll) | (nc << 32);
+        if (lane == 31) {
+            ws[warp] = is;
+            wn[warp] = in;
+        }
+        __syncthreads();
+        long long os = 0, on = 0, bs = 0, bn = 0;
+        for (int q = 0; q < nw; ++q) {
+            if (q < warp) {
+                os += ws[q];
+                on += wn[q];
+            }
+            bs += ws[q];
+            bn += wn[q];
+        }
+        if (t < T) W.mbase[t] = make_longlong2(cs + os + is - s, cn + on + in - nn);
+        cs += bs;
+        cn += bn;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        W.mbase[T] = make_longlong2(cs, cn);
+        const int64_t total = cs + cn;
+        st->next_total = total;
+        if (total > st->max_next) st->max_next = total;
+        if (total > P.pop_cap) set_error(st, DERR_POP_CAPACITY);
     }
 }
 
-// Exclusive prefix sums of 0/1 flags (count n, read from the device):
-// per-tile sums, their prefix (one CTA), the tiles' own prefixes; out[n] is
-// the total.  which 0: the records of N(t); 1: the spawns.
-__device__ __forceinline__ int64_t flag_count(const StepParams& P, int which)
-{
-    return which ? spawn_count(P) : P.segoff[P.st->cur][P.nseg] + 1;
-}
-
-// Input e of scan `which`: the spawns' 0/1 flags, or the records' packed counts.
-__device__ __forceinline__ int64_t scan_in(const WideParams& W, int which, int64_t e)
-{
-    return which ? (int64_t)W.flag_u[e] : W.cnt_a[e];
-}
-
-__global__ void __launch_bounds__(kWThreads) k_wide_scan_part(StepParams P, WideParams W, int which)
+// Exclusive prefix sums of the spawns' new-key flags: per-tile sums, their
+// prefix (one CTA), the tiles' own prefixes; scan_u[S] is the total.
+__global__ void __launch_bounds__(kWThreads) k_wide_scan_part(StepParams P, WideParams W)
 {
     __shared__ int64_t red[kWThreads / 32];
     if (cta_error(P.st)) return;
-    const int64_t N = flag_count(P, which);
+    const int64_t N = spawn_count(P);
     const int64_t tiles = (N + kWScanTile - 1) / kWScanTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int64_t c = 0;
         const int64_t e1 = min(N, (t + 1) * kWScanTile);
-        for (int64_t e = t * kWScanTile + threadIdx.x; e < e1; e += blockDim.x) c += scan_in(W, which, e);
+        for (int64_t e = t * kWScanTile + threadIdx.x; e < e1; e += blockDim.x) c += W.flag_u[e];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -866,11 +927,11 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scan_part(StepParams P, Wide
     }
 }
 
-__global__ void __launch_bounds__(kWThreads) k_wide_scan_top(StepParams P, WideParams W, int which)
+__global__ void __launch_bounds__(kWThreads) k_wide_scan_top(StepParams P, WideParams W)
 {
     __shared__ int64_t wsum[kWThreads / 32];
     if (cta_error(P.st)) return;
-    const int64_t N = flag_count(P, which);
+    const int64_t N = spawn_count(P);
     const int64_t tiles = (N + kWScanTile - 1) / kWScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t carry = 0;
@@ -894,29 +955,25 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scan_top(StepParams P, WideP
         carry += blk;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        int64_t* out = which ? W.scan_u : W.scan_a;
-        out[N] = carry;
-    }
+    if (threadIdx.x == 0) W.scan_u[N] = carry;
 }
 
-__global__ void __launch_bounds__(kWThreads) k_wide_scan_apply(StepParams P, WideParams W, int which)
+__global__ void __launch_bounds__(kWThreads) k_wide_scan_apply(StepParams P, WideParams W)
 {
     constexpr int kPer = kWScanTile / kWThreads;
     __shared__ int64_t wsum[kWThreads / 32];
     if (cta_error(P.st)) return;
-    int64_t* out = which ? W.scan_u : W.scan_a;
-    const int64_t N = flag_count(P, which);
+    const int64_t N = spawn_count(P);
     const int64_t tiles = (N + kWScanTile - 1) / kWScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        // each thread a run of kPer consecutive inputs
+        // each thread a run of kPer consecutive flags
         const int64_t e0 = t * kWScanTile + (int64_t)threadIdx.x * kPer;
         int64_t v[kPer];
         int64_t c = 0;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            v[k] = e0 + k < N ? scan_in(W, which, e0 + k) : 0;
+            v[k] = e0 + k < N ? W.flag_u[e0 + k] : 0;
             c += v[k];
         }
         int64_t incl = c;
@@ -932,7 +989,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scan_apply(StepParams P, Wid
         run += incl - c;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            if (e0 + k < N) out[e0 + k] = run;
+            if (e0 + k < N) W.scan_u[e0 + k] = run;
             run += v[k];
         }
         __syncthreads();
@@ -943,8 +1000,199 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scan_apply(StepParams P, Wid
 
 namespace {
 
-// Output offsets of the vectors: survivors of N(t) before vector s plus new
-// keys before it.  Raises POP_CAPACITY when N(t + dt) does not fit.
+// Per-vector observables of N(t + dt) as the merge writes it: records,
+// N_tot = sum |re| + |im|, and the diagonal sums, accumulated per thread
+// while its vector stays the same.
+struct ObsAcc {
+    int seg = -1;
+    unsigned long long c = 0;
+    long long ntot = 0, dre = 0, dim = 0;
+
+    __device__ __forceinline__ void add(const ulonglong2& key, int2 v, int n)
+    {
+        ++c;
+        ntot += (v.x < 0 ? -(long long)v.x : v.x) + (v.y < 0 ? -(long long)v.y : v.y);
+        const u128 k = wkey(key);
+        if ((uint64_t)(k >> n) == ((uint64_t)k & ((1ull << n) - 1ull))) {
+            dre += v.x;
+            dim += v.y;
+        }
+    }
+
+    __device__ __forceinline__ void flush(SegStats* out)
+    {
+        if (seg >= 0 && c) {
+            atomicAdd(&out[seg].count, c);
+            atomicAdd((unsigned long long*)&out[seg].ntot, (unsigned long long)ntot);
+            atomicAdd((unsigned long long*)&out[seg].dre, (unsigned long long)dre);
+            atomicAdd((unsigned long long*)&out[seg].dim, (unsigned long long)dim);
+        }
+        c = 0;
+        ntot = dre = dim = 0;
+    }
+
+    // Last flush of a kernel (all lanes of the warp): one lane's atomics when
+    // the warp shares its vector.
+    __device__ __forceinline__ void flush_warp(SegStats* out)
+    {
+        const int s0 = __shfl_sync(kFull, seg, 0);
+        if (__all_sync(kFull, seg == s0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(kFull, c, o);
+                ntot += __shfl_xor_sync(kFull, ntot, o);
+                dre += __shfl_xor_sync(kFull, dre, o);
+                dim += __shfl_xor_sync(kFull, dim, o);
+            }
+            if ((threadIdx.x & 31) != 0) c = 0;
+        }
+        flush(out);
+    }
+};
+
+// N(t) into N(t + dt), one pass over every merge tile [End Matter,
+// annihilation step]: each record's value plus the spawn sum of its run
+// (delta); survivors (nonzero) go to their place in the key-ordered union,
+// after the survivors and new keys before them and the new keys just before
+// them.  The places come from the tile's bases and a prefix over the tile in
+// rounds of kWThreads indices.  Where new keys go just before a record, and at
+// the first record of every vector, the survivors before it are left in scan_a
+// for the new keys' scatter and the vector offsets.  delta and newcnt are
+// cleared where set.  Each CTA takes a contiguous range of tiles.
+__global__ void __launch_bounds__(kWThreads) k_wide_merge_a(StepParams P, WideParams W)
+{
+    constexpr int kWarps = kWThreads / 32;
+    __shared__ unsigned long long s_w[2][kWarps];
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const int cur = st->cur;
+    const WPop A = wpop(P, cur);
+    const WPop out = wpop(P, (cur + 1) % 3);
+    const int64_t* offA = P.segoff[cur];
+    const int64_t K = offA[P.nseg];
+    const int64_t T = merge_tiles(K);
+    const int64_t per = (T + gridDim.x - 1) / gridDim.x;
+    const int64_t tb = (int64_t)blockIdx.x * per, te = min(T, tb + per);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ObsAcc acc;
+    int n = 0;
+    int64_t seg_lo = 0, seg_hi = 0;
+    int par = 0;
+    for (int64_t t = tb; t < te; ++t) {
+        const longlong2 base = W.mbase[t];
+        unsigned long long carry = 0;   // survivors | new keys << 32 of the tile's earlier rounds
+        for (int r = 0; r < kWMTile / kWThreads; ++r) {
+            const int64_t r0 = t * kWMTile + (int64_t)r * kWThreads;
+            if (r0 > K) break;   // same for the whole CTA
+            const int64_t i = r0 + tid;
+            bool keep = false, start = false;
+            int nc = 0;
+            int2 v = make_int2(0, 0);
+            if (i <= K) {
+                nc = W.newcnt[i];
+                if (nc) W.newcnt[i] = 0;
+            }
+            if (i < K) {
+                const int2 d = W.delta[i];
+                if (d.x | d.y) W.delta[i] = make_int2(0, 0);
+                const int2 a = __ldg(&A.val[i]);
+                v = make_int2(a.x + d.x, a.y + d.y);   // range checked by the runs kernel
+                keep = (v.x | v.y) != 0;
+                if (acc.seg < 0 || i >= seg_hi) {
+                    acc.flush(P.segacc);
+                    acc.seg = seg_of(offA, P.nseg, i);
+                    seg_lo = offA[acc.seg];
+                    seg_hi = offA[acc.seg + 1];
+                    n = P.seginfo[acc.seg].n;
+                }
+                start = i == seg_lo;
+            } else if (i == K) {
+                start = true;
+            }
+            const unsigned long long x = (keep ? 1ull : 0ull) | ((unsigned long long)(uint32_t)nc << 32);
+            unsigned long long incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_w[par][warp] = incl;
+            __syncthreads();
+            unsigned long long wo = 0, blk = 0;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) {
+                const unsigned long long u = s_w[par][q];
+                if (q < warp) wo += u;
+                blk += u;
+            }
+            par ^= 1;
+            const unsigned long long ex = carry + wo + incl - x;
+            carry += blk;
+            const int64_t surv = base.x + (int64_t)(ex & 0xFFFFFFFFull);
+            const int64_t newb = base.y + (int64_t)(ex >> 32);
+            if (nc > 0 || start) W.scan_a[i] = surv;
+            if (keep) {
+                const int64_t o = surv + newb + nc;
+                if (o < P.pop_cap) {
+                    const ulonglong2 key = __ldg(&A.key[i]);
+                    out.key[o] = key;
+                    out.val[o] = v;
+                    acc.add(key, v, n);
+                } else {
+                    set_error(st, DERR_POP_CAPACITY);
+                }
+            }
+        }
+        // self-check: the tile's survivors and new keys as the runs counted them
+        if (tid == 0) {
+            const longlong2 nx = W.mbase[t + 1];
+            if (nx.x - base.x != (long long)(carry & 0xFFFFFFFFull) || nx.y - base.y != (long long)(carry >> 32))
+                set_error(st, DERR_INTERNAL);
+        }
+    }
+    acc.flush_warp(P.segacc);
+}
+
+// The new keys of N(t + dt): run j after the new keys before it and the
+// survivors of N(t) before its position there.  Each CTA a contiguous range.
+__global__ void __launch_bounds__(kWThreads) k_wide_scatter_u(StepParams P, WideParams W)
+{
+    DevState* st = P.st;
+    if (cta_error(st)) return;
+    const int cur = st->cur;
+    const WSpawn* sp = sorted_spawns(W);
+    const WPop out = wpop(P, (cur + 1) % 3);
+    const int64_t S = spawn_count(P);
+    const int64_t per = (S + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(S, b0 + per);
+    ObsAcc acc;
+    int n = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        if (!W.flag_u[i]) continue;
+        const WRun run = W.run[i];
+        const int64_t o = W.scan_u[i] + W.scan_a[run.posA];
+        const WSpawn r = wsload(sp, i);
+        const int seg = (int)(r.meta >> 2);
+        if (seg != acc.seg) {
+            acc.flush(P.segacc);
+            acc.seg = seg;
+            n = P.seginfo[seg].n;
+        }
+        const ulonglong2 key = make_ulonglong2(r.lo, r.hi);
+        const int2 v = make_int2((int32_t)run.re, (int32_t)run.im);
+        if (o < P.pop_cap) {
+            out.key[o] = key;
+            out.val[o] = v;
+            acc.add(key, v, n);
+        } else {
+            set_error(st, DERR_POP_CAPACITY);
+        }
+    }
+    acc.flush_warp(P.segacc);
+}
+
+// Vector offsets of N(t + dt): survivors of N(t) before vector s plus the new
+// keys before it.
 __global__ void k_wide_outoff(StepParams P, WideParams W)
 {
     DevState* st = P.st;
@@ -952,61 +1200,8 @@ __global__ void k_wide_outoff(StepParams P, WideParams W)
     const int cur = st->cur, nxt = (cur + 1) % 3;
     const int64_t* offA = P.segoff[cur];
     int64_t* off = P.segoff[nxt];
-    // the low half of scan_a counts surviving records of N(t)
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.nseg; s += gridDim.x * blockDim.x)
-        off[s] = (W.scan_a[offA[s]] & 0xFFFFFFFFll) + W.scan_u[P.bseg[s]];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const int64_t total = (W.scan_a[offA[P.nseg] + 1] & 0xFFFFFFFFll) + W.scan_u[spawn_count(P)];
-        st->next_total = total;
-        if (total > st->max_next) st->max_next = total;
-        if (total > P.pop_cap) set_error(st, DERR_POP_CAPACITY);
-    }
-}
-
-__global__ void __launch_bounds__(kWThreads) k_wide_scatter_a(StepParams P, WideParams W)
-{
-    DevState* st = P.st;
-    if (cta_error(st)) return;
-    const int cur = st->cur;
-    const WRec* A = (const WRec*)P.pop[cur];
-    WRec* out = (WRec*)P.pop[(cur + 1) % 3];
-    const int64_t K = P.segoff[cur][P.nseg];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
-        W.newcnt[i] = 0;   // zero for the next step
-        if (i == K) continue;
-        const int64_t c = W.cnt_a[i];
-        const int2 v = W.delta[i];
-        W.delta[i] = make_int2(0, 0);
-        if (!(c & 1ll)) continue;
-        const int64_t e = W.scan_a[i];
-        WRec r;
-        r.lo = A[i].lo;
-        r.hi = A[i].hi;
-        r.re = v.x;
-        r.im = v.y;
-        // survivors and new keys before it, then the new keys just before it
-        out[(e & 0xFFFFFFFFll) + (e >> 32) + (c >> 32)] = r;
-    }
-}
-
-__global__ void __launch_bounds__(kWThreads) k_wide_scatter_u(StepParams P, WideParams W)
-{
-    DevState* st = P.st;
-    if (cta_error(st)) return;
-    const int cur = st->cur;
-    const WSpawn* sp = sorted_spawns(W);
-    WRec* out = (WRec*)P.pop[(cur + 1) % 3];
-    const int64_t S = spawn_count(P);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
-        if (!W.flag_u[i]) continue;
-        const WRun run = W.run[i];
-        WRec r;
-        r.lo = sp[i].lo;
-        r.hi = sp[i].hi;
-        r.re = (int32_t)run.re;
-        r.im = (int32_t)run.im;
-        out[W.scan_u[i] + (W.scan_a[run.posA] & 0xFFFFFFFFll)] = r;
-    }
+        off[s] = W.scan_a[offA[s]] + W.scan_u[P.bseg[s]];
 }
 
 // Per-vector K, N_tot and N^diag of a slot: each CTA a contiguous range, a
@@ -1016,7 +1211,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_obs(StepParams P, int slot_r
     const DevState* st = P.st;
     if (read_error(st)) return;
     const int slot = (st->cur + slot_rel) % 3;
-    const WRec* pop = (const WRec*)P.pop[slot];
+    const WPop pop = wpop(P, slot);
     const int64_t* off = P.segoff[slot];
     const int64_t K = off[P.nseg];
     const int64_t per = (K + gridDim.x - 1) / gridDim.x;
@@ -1124,7 +1319,7 @@ void configure_wide_kernels() { (void)wide_grid(); }
 // the host).
 const char* const kWideGroupNames[kNumWideGroups] = {
     "w_prologue", "w_spawn", "w_spawn_heavy", "w_sort_hist_plan", "w_sort_passes",
-    "w_merge_runs_match", "w_merge_scans", "w_merge_scatter", "w_obs_finalize"};
+    "w_merge_runs", "w_merge_scans", "w_merge_scatter", "w_finalize"};
 
 void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, cudaEvent_t* ev)
 {
@@ -1153,19 +1348,16 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
     mark(5);
     k_wide_spawn_off<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_runs<<<g, kWThreads, 0, s>>>(P, W);
-    k_wide_match<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_mtop<<<1, 1024, 0, s>>>(P, W);
     mark(6);
-    for (int which = 0; which < 2; ++which) {
-        k_wide_scan_part<<<g, kWThreads, 0, s>>>(P, W, which);
-        k_wide_scan_top<<<1, kWThreads, 0, s>>>(P, W, which);
-        k_wide_scan_apply<<<g, kWThreads, 0, s>>>(P, W, which);
-    }
+    k_wide_scan_part<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_scan_top<<<1, kWThreads, 0, s>>>(P, W);
+    k_wide_scan_apply<<<g, kWThreads, 0, s>>>(P, W);
     mark(7);
-    k_wide_outoff<<<g, kWThreads, 0, s>>>(P, W);
-    k_wide_scatter_a<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_merge_a<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_scatter_u<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_outoff<<<1, kWThreads, 0, s>>>(P, W);
     mark(8);
-    k_wide_obs<<<g, kWThreads, 0, s>>>(P, 1, P.segacc);
     k_wide_finalize<<<1, kWThreads, 0, s>>>(P);
     mark(9);
 }
@@ -1173,7 +1365,7 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
 int wide_step_launch_count(const StepParams& P, const WideParams& W)
 {
     (void)P;
-    return 8 + 3 * W.passes + 3 + 6 + 5;
+    return 8 + 3 * W.passes + 3 + 3 + 3 + 1;
 }
 
 namespace {
@@ -1224,7 +1416,7 @@ __global__ void k_wide_init_compact(StepParams P, const uint64_t* __restrict__ x
     __shared__ int s_cnt[kWThreads];
     DevState* st = P.st;
     const int slot = st->cur;
-    WRec* dst = (WRec*)P.pop[slot];
+    const WPop dst = wpop(P, slot);
     int64_t* off = P.segoff[slot];
     int64_t pos = 0;
     const int tid = threadIdx.x;
@@ -1245,15 +1437,9 @@ __global__ void k_wide_init_compact(StepParams P, const uint64_t* __restrict__ x
             }
             const int excl = s_cnt[tid] - (keep ? 1 : 0);
             const int blk = s_cnt[kWThreads - 1];
-            if (keep && pos + excl < P.pop_cap) {
-                const u128 k = ((u128)xs[e] << n) | (u128)ys[e];
-                WRec r;
-                r.lo = (uint64_t)k;
-                r.hi = (uint64_t)(k >> 64);
-                r.re = (int32_t)vals[2 * i];
-                r.im = (int32_t)vals[2 * i + 1];
-                dst[pos + excl] = r;
-            }
+            if (keep && pos + excl < P.pop_cap)
+                wstore(dst, pos + excl, ((u128)xs[e] << n) | (u128)ys[e], (int32_t)vals[2 * i],
+                       (int32_t)vals[2 * i + 1]);
             pos += blk;
             __syncthreads();
         }
@@ -1270,24 +1456,25 @@ __global__ void k_wide_lookup(StepParams P, int seg, const uint64_t* __restrict_
                               int nq, int64_t* __restrict__ out)
 {
     const int cur = P.st->cur;
-    const WRec* A = (const WRec*)P.pop[cur];
+    const WPop A = wpop(P, cur);
     const int64_t lo = P.segoff[cur][seg], hi = P.segoff[cur][seg + 1];
     const int n = P.seginfo[seg].n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
         const u128 k = ((u128)qx[i] << n) | (u128)qy[i];
-        const int64_t p = lower_bound_pop(A, lo, hi, k);
-        const bool hit = p < hi && wkey(A[p]) == k;
-        out[2 * i] = hit ? A[p].re : 0;
-        out[2 * i + 1] = hit ? A[p].im : 0;
+        const int64_t p = lower_bound_pop(A.key, lo, hi, k);
+        const bool hit = p < hi && wkey(A.key[p]) == k;
+        const int2 v = hit ? A.val[p] : make_int2(0, 0);
+        out[2 * i] = v.x;
+        out[2 * i + 1] = v.y;
     }
 }
 
 __global__ void k_wide_export(StepParams P, int slot, int64_t first, int64_t count, uint64_t* __restrict__ x,
                               uint64_t* __restrict__ y, int32_t* __restrict__ re, int32_t* __restrict__ im)
 {
-    const WRec* A = (const WRec*)P.pop[slot];
+    const WPop A = wpop(P, slot);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const WRec r = A[first + i];
+        const WRec r = wload(A, first + i);
         const int seg = seg_of(P.segoff[slot], P.nseg, first + i);
         const int n = P.seginfo[seg].n;
         const u128 k = wkey(r);
@@ -1337,7 +1524,7 @@ namespace {
 __global__ void k_wide_pack(const uint64_t* __restrict__ xs, const uint64_t* __restrict__ ys,
                             const int32_t* __restrict__ re, const int32_t* __restrict__ im,
                             const int64_t* __restrict__ off, int nseg, const SegInfo* __restrict__ seginfo,
-                            WRec* __restrict__ dst, int* bad)
+                            uint8_t* __restrict__ dst_base, int64_t cap, int* bad)
 {
     const int64_t K = off[nseg];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1352,21 +1539,18 @@ __global__ void k_wide_pack(const uint64_t* __restrict__ xs, const uint64_t* __r
             if (kp >= k) ok = false;
         }
         if (!ok) atomicExch(bad, 1);
-        WRec r;
-        r.lo = (uint64_t)k;
-        r.hi = (uint64_t)(k >> 64);
-        r.re = a;
-        r.im = b;
-        dst[i] = r;
+        const WPop dst{(ulonglong2*)dst_base, (int2*)(dst_base + 16 * cap)};
+        wstore(dst, i, k, a, b);
     }
 }
 
 } // namespace
 
 void launch_wide_pack(const uint64_t* xs, const uint64_t* ys, const int32_t* re, const int32_t* im,
-                      const int64_t* off, int nseg, const SegInfo* seginfo, WRec* dst, int* bad, cudaStream_t s)
+                      const int64_t* off, int nseg, const SegInfo* seginfo, uint8_t* dst, int64_t cap, int* bad,
+                      cudaStream_t s)
 {
-    k_wide_pack<<<wide_grid(), kWThreads, 0, s>>>(xs, ys, re, im, off, nseg, seginfo, dst, bad);
+    k_wide_pack<<<wide_grid(), kWThreads, 0, s>>>(xs, ys, re, im, off, nseg, seginfo, dst, cap, bad);
 }
 
 } // namespace qmc
