@@ -316,6 +316,9 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
             return rc;
         ctx->wtiles_cap = (cap + kWTile - 1) / kWTile + 1;
         if ((rc = dalloc(ctx, &ctx->d_wtile, ctx->wtiles_cap * 256)) != QMC_OK) return rc;
+        // bucket sort windows: one per 224 spawn records
+        if ((rc = dalloc(ctx, &ctx->d_win, cap / 224 + 2)) != QMC_OK) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_big_list, cap / 224 + 2)) != QMC_OK) return rc;
         ctx->spawn_cap = cap;
         ctx->graph_dirty = true;
         return grow_wpart(ctx);

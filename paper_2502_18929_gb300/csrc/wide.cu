@@ -6,7 +6,12 @@
 //                       walkers, one thread per parent, a warp's spawns
 //                       appended together; heavy parents become work items
 //   k_wide_heavy        one warp per chunk of a heavy parent's walkers
-//   k_wide_hist         digit counts of every 8-bit radix pass of (vector, key)
+//   k_wide_bhist ..
+//   k_wide_bsort_big    bucket sort of the spawns by (vector, key): bucket
+//                       counts, their prefix, one counting pass, windows of
+//                       whole buckets sorted in shared memory
+//   k_wide_hist         (LSD fallback when a bucket is too large) digit counts
+//                       of every 8-bit radix pass of (vector, key)
 //   k_wide_plan         passes to skip (a digit shared by every record) and
 //                       the ping-pong buffer of each pass
 //   k_wide_tile_hist /
@@ -268,6 +273,8 @@ __global__ void k_wide_prologue(StepParams P)
         st->heavy_total = 0;
         st->next_total = 0;
         st->merge_tiles = 0;
+        st->sort_fallback = P.sort_mode == 0 ? 1u : 0u;
+        st->big_windows = 0u;
     }
 }
 
@@ -311,6 +318,9 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
 {
     DevState* st = P.st;
     if (cta_error(st)) return;
+    if (phase == 0 && P.sort_mode != 0)   // bucket counters of this step's spawn sort
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < (1 << P.bucket_bits); b += gridDim.x * blockDim.x)
+            P.bucket[b] = 0u;
     const StepInfo inf = P.info[st->call_index];
     if (phase == 1 && !inf.ab2) return;
     const int slot = phase ? (st->cur + 2) % 3 : st->cur;
@@ -564,7 +574,7 @@ __device__ __forceinline__ const WSpawn* pass_src(const WideParams& W, uint32_t 
 __global__ void __launch_bounds__(kWThreads) k_wide_hist(StepParams P, WideParams W)
 {
     __shared__ uint32_t h[kWMaxPasses * 256];
-    if (cta_error(P.st)) return;
+    if (cta_error(P.st) || !P.st->sort_fallback) return;
     const int64_t S = spawn_count(P);
     const int n2 = 2 * P.n;
     for (int i = threadIdx.x; i < W.passes * 256; i += blockDim.x) h[i] = 0u;
@@ -580,11 +590,17 @@ __global__ void __launch_bounds__(kWThreads) k_wide_hist(StepParams P, WideParam
 
 // Passes whose digit is the same for every spawn leave the order unchanged:
 // skip them.  The others alternate between the two buffers; their digit
-// counts become digit starts.
+// counts become digit starts.  After the bucket sort every pass is skipped
+// and the sorted spawns are in spawn_alt.
 __global__ void k_wide_plan(StepParams P, WideParams W)
 {
     __shared__ uint32_t s_skip;
     if (cta_error(P.st)) return;
+    if (!P.st->sort_fallback) {
+        for (int p = threadIdx.x; p < W.passes; p += blockDim.x) W.plan[p] = 1u;
+        if (threadIdx.x == 0) W.plan[W.passes] = 1u;
+        return;
+    }
     const uint32_t S = (uint32_t)spawn_count(P);
     uint32_t src = 0;
     for (int p = 0; p < W.passes; ++p) {
@@ -719,6 +735,269 @@ __global__ void __launch_bounds__(kWThreads) k_wide_scatter(StepParams P, WidePa
             for (int w = 0; w < kWarps; ++w) s_w[w][tid] = 0u;
             __syncthreads();
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spawn sort by buckets, the default.  The bucket digit holds every vector
+// bit and the top bucket_kb key bits, so buckets come in (vector, key) order:
+// one counting pass puts each record into its bucket (order inside a bucket
+// arbitrary), then the records are cut into windows of whole buckets --
+// window k starts at the bucket holding record k kWSortWin -- and every
+// window is sorted by (vector, key) in shared memory (a warp for up to
+// kWSmallWin records, a CTA for up to kWBigWin).  The order among equal keys
+// is irrelevant: a run's records are summed.  When the largest bucket could
+// overfill a window the step takes the LSD radix sort instead
+// (st->sort_fallback).
+// ---------------------------------------------------------------------------
+constexpr int kWSortWin = 224;
+constexpr int kWSmallWin = 256;
+constexpr int kWBigWin = 2048;
+constexpr int kWSortRec = 24 + 8 + 8 + 4;   // shared bytes per record: the record, key high, key low, tag
+constexpr int kWSmallSmem = (kWThreads / 32) * kWSmallWin * kWSortRec;
+constexpr int kWBigSmem = kWBigWin * kWSortRec;
+
+__device__ __forceinline__ uint32_t wbucket(const WSpawn& r, int kb, int n2)
+{
+    uint32_t d = (r.meta >> 2) << kb;
+    if (kb) d |= (uint32_t)(wkey(r) >> (n2 - kb));
+    return d;
+}
+
+// Bucket sizes of the step's spawns.
+__global__ void __launch_bounds__(kWThreads) k_wide_bhist(StepParams P, WideParams W)
+{
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int64_t S = spawn_count(P);
+    const int kb = P.bucket_kb, n2 = 2 * P.n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&P.bucket[wbucket(wsload(W.spawn, i), kb, n2)], 1u);
+}
+
+// Per 1024 buckets: their total and largest size, as total | largest << 32.
+__global__ void __launch_bounds__(kWThreads) k_wide_bpart(StepParams P)
+{
+    __shared__ uint32_t ssum[kWThreads / 32], smax[kWThreads / 32];
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int tiles = 1 << (P.bucket_bits - 10);
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        uint32_t c = 0, m = 0;
+        for (int b = threadIdx.x; b < 1024; b += blockDim.x) {
+            const uint32_t v = P.bucket[t * 1024 + b];
+            c += v;
+            m = max(m, v);
+        }
+        c = __reduce_add_sync(kFull, c);
+        m = __reduce_max_sync(kFull, m);
+        if ((threadIdx.x & 31) == 0) {
+            ssum[threadIdx.x >> 5] = c;
+            smax[threadIdx.x >> 5] = m;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = 0, x = 0;
+            for (int q = 0; q < kWThreads / 32; ++q) {
+                a += ssum[q];
+                x = max(x, smax[q]);
+            }
+            P.bscan_status[t] = (unsigned long long)a | ((unsigned long long)x << 32);
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive prefix of the bucket tiles' totals (one CTA of 1024 threads, at
+// most 2^(kBucketBits - 10) tiles); the LSD fallback when the largest bucket
+// could overfill a CTA's window.
+__global__ void __launch_bounds__(1024) k_wide_btop(StepParams P)
+{
+    __shared__ uint32_t wsum[32], wmax[32];
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int tiles = 1 << (P.bucket_bits - 10);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned long long v = t < tiles ? P.bscan_status[t] : 0ull;
+    const uint32_t c = (uint32_t)v, m = (uint32_t)(v >> 32);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t wm = __reduce_max_sync(kFull, m);
+    if (lane == 31) wsum[warp] = incl;
+    if (lane == 0) wmax[warp] = wm;
+    __syncthreads();
+    uint32_t off = 0, gm = 0;
+    for (int q = 0; q < 32; ++q) {
+        if (q < warp) off += wsum[q];
+        gm = max(gm, wmax[q]);
+    }
+    if (t < tiles) P.bscan_status[t] = off + incl - c;
+    if (t == 0 && gm > (uint32_t)(kWBigWin - kWSortWin)) st->sort_fallback = 1u;
+}
+
+// Bucket starts (exclusive prefix, in place) and the sort windows' starts.
+__global__ void __launch_bounds__(1024) k_wide_bapply(StepParams P)
+{
+    __shared__ uint32_t wsum[32];
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int tiles = 1 << (P.bucket_bits - 10);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int b = t * 1024 + threadIdx.x;
+        const uint32_t c = P.bucket[b];
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t off = (uint32_t)P.bscan_status[t];
+        for (int q = 0; q < warp; ++q) off += wsum[q];
+        const uint32_t start = off + incl - c;
+        P.bucket[b] = start;
+        for (uint32_t k = (start + kWSortWin - 1) / kWSortWin; k * kWSortWin < start + c; ++k) P.win[k] = start;
+        __syncthreads();
+    }
+}
+
+// Counting pass: spawn -> spawn_alt, each record into its bucket.
+__global__ void __launch_bounds__(kWThreads) k_wide_bscatter(StepParams P, WideParams W)
+{
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int64_t S = spawn_count(P);
+    const int kb = P.bucket_kb, n2 = 2 * P.n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
+        const WSpawn r = wsload(W.spawn, i);
+        const uint32_t pos = atomicAdd(&P.bucket[wbucket(r, kb, n2)], 1u);
+        if ((int64_t)pos < S) W.spawn_alt[pos] = r;
+    }
+}
+
+// Bitonic sort (N a power of two) by (G >> 12, H, L): G holds the record's
+// vector above its 12-bit index in the window, H and L its key's words.
+// Threads [t0, N/2) step nthr take the compare-exchanges; sync() orders the
+// stages.
+template <typename Sync>
+__device__ __forceinline__ void wbitonic(uint64_t* H, uint64_t* L, uint32_t* G, int N, int t0, int nthr, Sync sync)
+{
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = t0; t < (N >> 1); t += nthr) {
+                const int low = t & (j - 1);
+                const int i = ((t - low) << 1) + low;   // bit j of i is clear
+                const int l = i + j;
+                const bool asc = (i & k) == 0;
+                const uint32_t gi = G[i], gl = G[l];
+                const uint64_t hi = H[i], hl = H[l], li = L[i], ll = L[l];
+                const bool gt = (gi >> 12) != (gl >> 12) ? (gi >> 12) > (gl >> 12)
+                                : hi != hl ? hi > hl : li > ll;
+                if (gt == asc) {
+                    G[i] = gl;
+                    G[l] = gi;
+                    H[i] = hl;
+                    H[l] = hi;
+                    L[i] = ll;
+                    L[l] = li;
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// Window k's bounds [win[k], win[k + 1]), the last one ending at S.
+__device__ __forceinline__ void wwindow(const StepParams& P, int64_t k, int64_t nwin, uint32_t S, uint32_t* lo,
+                                        uint32_t* hi)
+{
+    *lo = P.win[k];
+    *hi = k + 1 < nwin ? P.win[k + 1] : S;
+}
+
+// Load a window of n records into shared memory (padded to N with keys
+// above every record), sort it, write it back in place.
+template <typename Sync>
+__device__ __forceinline__ void wsort_window(WSpawn* A, uint32_t start, int n, WSpawn* R, uint64_t* H, uint64_t* L,
+                                             uint32_t* G, int t0, int nthr, Sync sync)
+{
+    int N = 2;
+    while (N < n) N <<= 1;
+    for (int j = t0; j < N; j += nthr) {
+        if (j < n) {
+            const WSpawn r = wsload(A, start + j);
+            R[j] = r;
+            H[j] = r.hi;
+            L[j] = r.lo;
+            G[j] = ((r.meta >> 2) << 12) | (uint32_t)j;
+        } else {
+            H[j] = ~0ull;
+            L[j] = ~0ull;
+            G[j] = 0xFFFFF000u | (uint32_t)j;
+        }
+    }
+    sync();
+    wbitonic(H, L, G, N, t0, nthr, sync);
+    for (int j = t0; j < n; j += nthr) A[start + j] = R[G[j] & 0xFFFu];
+    sync();
+}
+
+// Windows of up to kWSmallWin records, one warp each; larger windows go to
+// the list of k_wide_bsort_big.
+__global__ void __launch_bounds__(kWThreads) k_wide_bsort_small(StepParams P, WideParams W)
+{
+    extern __shared__ __align__(16) uint8_t wsm[];
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kWThreads / 32;
+    WSpawn* R = (WSpawn*)wsm + warp * kWSmallWin;
+    uint64_t* H = (uint64_t*)(wsm + kW * kWSmallWin * 24) + warp * kWSmallWin;
+    uint64_t* L = (uint64_t*)(wsm + kW * kWSmallWin * 32) + warp * kWSmallWin;
+    uint32_t* G = (uint32_t*)(wsm + kW * kWSmallWin * 40) + warp * kWSmallWin;
+    const uint32_t S = (uint32_t)spawn_count(P);
+    const int64_t nwin = ((int64_t)S + kWSortWin - 1) / kWSortWin;
+    for (int64_t k = (int64_t)blockIdx.x * kW + warp; k < nwin; k += (int64_t)gridDim.x * kW) {
+        uint32_t start, end;
+        wwindow(P, k, nwin, S, &start, &end);
+        const int n = (int)(end - start);
+        if (n <= 1) continue;
+        if (n > kWSmallWin) {
+            if (lane == 0) P.big_list[atomicAdd(&st->big_windows, 1u)] = (uint32_t)k;
+            continue;
+        }
+        wsort_window(W.spawn_alt, start, n, R, H, L, G, lane, 32, [] { __syncwarp(); });
+    }
+}
+
+// Windows of kWSmallWin + 1 .. kWBigWin records, one CTA each.
+__global__ void __launch_bounds__(kWThreads) k_wide_bsort_big(StepParams P, WideParams W)
+{
+    extern __shared__ __align__(16) uint8_t wsm[];
+    WSpawn* R = (WSpawn*)wsm;
+    uint64_t* H = (uint64_t*)(wsm + kWBigWin * 24);
+    uint64_t* L = (uint64_t*)(wsm + kWBigWin * 32);
+    uint32_t* G = (uint32_t*)(wsm + kWBigWin * 40);
+    DevState* st = P.st;
+    if (cta_error(st) || st->sort_fallback) return;
+    const uint32_t S = (uint32_t)spawn_count(P);
+    const int64_t nwin = ((int64_t)S + kWSortWin - 1) / kWSortWin;
+    const uint32_t nbig = st->big_windows;
+    for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
+        uint32_t start, end;
+        wwindow(P, (int64_t)P.big_list[q], nwin, S, &start, &end);
+        const int n = (int)(end - start);
+        if (n > kWBigWin) {   // excluded by the fallback rule
+            if (threadIdx.x == 0) set_error(st, DERR_INTERNAL);
+            continue;
+        }
+        wsort_window(W.spawn_alt, start, n, R, H, L, G, threadIdx.x, kWThreads, [] { __syncthreads(); });
     }
 }
 
@@ -1281,7 +1560,7 @@ __global__ void k_wide_finalize(StepParams P)
         st->acc_knext += next;
         st->acc_heavy += st->heavy_total;
         st->acc_cand += st->cand_total;
-        st->acc_sort_lsd += 1;
+        if (st->sort_fallback) st->acc_sort_lsd += 1; else st->acc_sort_bucket += 1;
         if (st->cand_total > st->max_cand) st->max_cand = st->cand_total;
         if (st->spawn_total > st->max_spawn) st->max_spawn = st->spawn_total;
         if (st->heavy_total > st->max_heavy) st->max_heavy = st->heavy_total;
@@ -1313,7 +1592,12 @@ int wide_grid()
 
 } // namespace
 
-void configure_wide_kernels() { (void)wide_grid(); }
+void configure_wide_kernels()
+{
+    (void)wide_grid();
+    cudaFuncSetAttribute(k_wide_bsort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmallSmem);
+    cudaFuncSetAttribute(k_wide_bsort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, kWBigSmem);
+}
 
 // The kernels of one step, in order, on one stream (captured into a graph by
 // the host).
@@ -1337,6 +1621,13 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
     mark(2);
     k_wide_heavy<<<g, kWThreads, 0, s>>>(P, W);
     mark(3);
+    k_wide_bhist<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_bpart<<<g, kWThreads, 0, s>>>(P);
+    k_wide_btop<<<1, 1024, 0, s>>>(P);
+    k_wide_bapply<<<g, 1024, 0, s>>>(P);
+    k_wide_bscatter<<<g, kWThreads, 0, s>>>(P, W);
+    k_wide_bsort_small<<<g, kWThreads, kWSmallSmem, s>>>(P, W);
+    k_wide_bsort_big<<<g, kWThreads, kWBigSmem, s>>>(P, W);
     k_wide_hist<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_plan<<<1, kWThreads, 0, s>>>(P, W);
     mark(4);
@@ -1365,7 +1656,7 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
 int wide_step_launch_count(const StepParams& P, const WideParams& W)
 {
     (void)P;
-    return 8 + 3 * W.passes + 3 + 3 + 3 + 1;
+    return 15 + 3 * W.passes + 3 + 3 + 3 + 1;
 }
 
 namespace {

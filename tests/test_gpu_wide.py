@@ -7,6 +7,8 @@ the observables.
   initiator.
 * The 40-qubit GHZ circuit from spread states: thousands of distinct keys per
   vector whose bits fill all 80 key bits, several vectors.
+* Spawns crowded into few buckets: the LSD radix sort instead of the bucket
+  sort, bit for bit as well.
 * The counters show which paths ran; observables and target overlaps match
   the oracle's.
 """
@@ -93,6 +95,40 @@ def test_wide_spread_states_parity():
         assert orc.step(0.01, 2) == O.OK
         _same(gpu, orc, nseg, 0, f"chunk {chunk}")
         _same(gpu, orc, nseg, 1, f"chunk {chunk} N(t - dt)")
+    c = gpu.counters()
+    assert c["sort_bucket_steps"] == 6 and c["sort_lsd_steps"] == 0   # keys spread over all buckets
+
+
+def test_wide_lsd_fallback_parity():
+    """Spawns crowded into one bucket per vector (states that differ only in
+    the low 16 bits of x and y, 40 walkers each, inside the CNOT 4 -> 5
+    pulse): more than a sort window's worth of records share a bucket, so the
+    step takes the LSD radix sort; bit for bit with the oracle."""
+    n, nseg = 40, 2
+    prob = P.ghz_circuit(n)
+    rng = np.random.default_rng(11)
+    xs = rng.integers(0, 1 << 16, size=2500)
+    ys = rng.integers(0, 1 << 16, size=2500)
+    states = sorted({(int(a), int(b)) for a, b in zip(xs, ys)})
+    sign = rng.choice([-1, 1], size=len(states))
+    rho0 = [(a, b, float(40 * s), float(-20 * s)) for (a, b), s in zip(states, sign)]
+    gpu = qmc.QMC(n, nseg, 9, 1, integrator=qmc.AB2)
+    gpu.load_schedule(prob)
+    orc = O.OracleSim(prob, nseg, 9, integrator=O.AB2, n_diag=1)
+    gpu.init_populations(rho0)
+    orc.init(rho0)
+    gpu.set_clock(500, 5.0)
+    orc.set_clock(500, 5.0)
+    for chunk in range(3):
+        gpu.step(0.01, 2)
+        assert orc.step(0.01, 2) == O.OK
+        _same(gpu, orc, nseg, 0, f"chunk {chunk}")
+        _same(gpu, orc, nseg, 1, f"chunk {chunk} N(t - dt)")
+    c = gpu.counters()
+    assert c["sort_lsd_steps"] > 0 and c["spawns"] > 6 * 2 * 1824
+    obs = gpu.observables()
+    for s in range(nseg):
+        assert np.array_equal(obs[s], orc.stats(s)), s
 
 
 def test_wide_overlap_and_rejections():
