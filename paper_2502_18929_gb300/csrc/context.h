@@ -102,6 +102,12 @@ struct qmc_ctx {
     int64_t info_cap = 0;
     uint8_t* d_progs = nullptr;
     int64_t progs_cap = 0;
+    // pinned host staging of a qmc_step call's step table and programs: each
+    // chunk of steps is copied from a region no later chunk rewrites
+    qmc::StepInfo* h_info = nullptr;
+    int64_t h_info_cap = 0;
+    uint8_t* h_progs = nullptr;
+    int64_t h_progs_cap = 0;
     SegStats* d_obs = nullptr;
 
     // host mirror of the clock
@@ -124,6 +130,7 @@ struct qmc_ctx {
     int32_t* d_wnewcnt = nullptr;
     unsigned long long* d_wmtile = nullptr;
     longlong2* d_wmbase = nullptr;
+    int64_t* d_wabound = nullptr;
     int64_t wmtiles_cap = 0;
     int64_t* d_wscan_a = nullptr;
     int64_t* d_wpart = nullptr;

@@ -196,6 +196,7 @@ struct WideParams {
                                  //   zero between steps
     longlong2* mbase;       // [mtiles_cap]: per merge tile, survivors and new keys before it (last: totals)
     int64_t mtiles_cap;
+    int64_t* abound;        // [2^kBucketBits + 1]: first record of N(t) in each bucket of the spawn sort
     int64_t* part;          // scan partials
     int64_t part_cap;
     uint32_t* hist;         // [kWMaxPasses][256] digit counts, then digit starts

@@ -9,6 +9,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <atomic>
+#include <condition_variable>
+#include <memory>
+#include <mutex>
 #include <thread>
 #include <vector>
 #include <chrono>
@@ -247,6 +251,7 @@ WideParams wparams(qmc_ctx* c)
     W.mtile = c->d_wmtile;
     W.mbase = c->d_wmbase;
     W.mtiles_cap = c->wmtiles_cap;
+    W.abound = c->d_wabound;
     W.scan_a = c->d_wscan_a;
     W.part = c->d_wpart;
     W.part_cap = c->wpart_cap;
@@ -410,29 +415,53 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
     return grow_merge_tiles(ctx);
 }
 
-int upload_calls(qmc_ctx* ctx, const std::vector<StepInfo>& info, const std::vector<uint8_t>& blob)
+// Step table and history of a qmc_step call of nsteps steps: device and
+// pinned staging capacity (before any of its steps is launched).
+int ensure_call_capacity(qmc_ctx* ctx, int64_t nsteps)
 {
     int rc;
-    if ((int64_t)info.size() > ctx->info_cap) {
-        if ((rc = dalloc(ctx, &ctx->d_info, (int64_t)info.size())) != QMC_OK) return rc;
-        ctx->info_cap = (int64_t)info.size();
+    if (nsteps > ctx->info_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_info, nsteps)) != QMC_OK) return rc;
+        ctx->info_cap = nsteps;
         ctx->graph_dirty = true;
     }
-    if ((int64_t)blob.size() > ctx->progs_cap) {
-        if ((rc = dalloc(ctx, &ctx->d_progs, (int64_t)blob.size())) != QMC_OK) return rc;
-        ctx->progs_cap = (int64_t)blob.size();
+    if (nsteps > ctx->history_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_history, nsteps * ctx->cfg.n_segments)) != QMC_OK) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_zhist, nsteps * ctx->cfg.n_segments * ctx->cfg.n_qubits)) != QMC_OK) return rc;
+        ctx->history_cap = nsteps;
         ctx->graph_dirty = true;
     }
-    if ((int64_t)info.size() > ctx->history_cap) {
-        if ((rc = dalloc(ctx, &ctx->d_history, (int64_t)info.size() * ctx->cfg.n_segments)) != QMC_OK) return rc;
-        if ((rc = dalloc(ctx, &ctx->d_zhist, (int64_t)info.size() * ctx->cfg.n_segments * ctx->cfg.n_qubits)) !=
-            QMC_OK)
-            return rc;
-        ctx->history_cap = (int64_t)info.size();
+    if (nsteps > ctx->h_info_cap) {
+        CK(cudaStreamSynchronize(ctx->work));   // no copy from the old staging is pending
+        if (ctx->h_info) cudaFreeHost(ctx->h_info);
+        ctx->h_info = nullptr;
+        ctx->h_info_cap = 0;
+        if (cudaMallocHost((void**)&ctx->h_info, (size_t)nsteps * sizeof(StepInfo)) != cudaSuccess)
+            return fail(ctx, QMC_ERR_OOM, "pinned staging of the step table failed");
+        ctx->h_info_cap = nsteps;
+    }
+    return QMC_OK;
+}
+
+// Program space of a call (bytes), device and pinned staging.  A new device
+// buffer holds nothing: the caller uploads the programs again.
+int ensure_progs(qmc_ctx* ctx, int64_t bytes)
+{
+    int rc;
+    if (bytes > ctx->progs_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_progs, bytes)) != QMC_OK) return rc;
+        ctx->progs_cap = bytes;
         ctx->graph_dirty = true;
     }
-    CK(cudaMemcpyAsync(ctx->d_info, info.data(), info.size() * sizeof(StepInfo), cudaMemcpyHostToDevice, ctx->work));
-    CK(cudaMemcpyAsync(ctx->d_progs, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->work));
+    if (bytes > ctx->h_progs_cap) {
+        CK(cudaStreamSynchronize(ctx->work));   // no copy from the old staging is pending
+        if (ctx->h_progs) cudaFreeHost(ctx->h_progs);
+        ctx->h_progs = nullptr;
+        ctx->h_progs_cap = 0;
+        if (cudaMallocHost((void**)&ctx->h_progs, (size_t)bytes) != cudaSuccess)
+            return fail(ctx, QMC_ERR_OOM, "pinned staging of the column programs failed");
+        ctx->h_progs_cap = bytes;
+    }
     return QMC_OK;
 }
 
@@ -541,7 +570,8 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     ctx->heavy_cap = std::max<int64_t>(4096, cfg->capacity_hint / 64);
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
     if (ctx->wide && ((rc = dalloc(ctx, &ctx->d_whist, kWMaxPasses * 256)) != QMC_OK ||
-                      (rc = dalloc(ctx, &ctx->d_wplan, kWMaxPasses + 1)) != QMC_OK))
+                      (rc = dalloc(ctx, &ctx->d_wplan, kWMaxPasses + 1)) != QMC_OK ||
+                      (rc = dalloc(ctx, &ctx->d_wabound, ((int64_t)1 << kBucketBits) + 1)) != QMC_OK))
         return bail(rc);
     const int64_t hint = cfg->capacity_hint > 0 ? cfg->capacity_hint : (int64_t)1 << 16;
     if ((rc = grow_spawn(ctx, hint / 4 + 1024)) != QMC_OK) return bail(rc);
@@ -644,6 +674,8 @@ void qmc_destroy(qmc_ctx* ctx)
     for (const auto& b : ctx->blocks) held.push_back(b.first);
     for (void* p : held) mem_free(ctx, p);
     if (ctx->work) cudaStreamSynchronize(ctx->work);
+    if (ctx->h_info) cudaFreeHost(ctx->h_info);
+    if (ctx->h_progs) cudaFreeHost(ctx->h_progs);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
     if (ctx->work) cudaStreamDestroy(ctx->work);
@@ -1383,9 +1415,6 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     std::vector<uint8_t> blob;
     std::vector<int64_t> last_off(2 * (size_t)ni, -1);
     std::vector<std::vector<uint8_t>> last_blob(2 * (size_t)ni);
-    // every (step, instance, pass) program, built by several host threads (the
-    // programs are independent; a batch of hundreds of instances builds
-    // hundreds per step)
     struct Job {
         int k, pass;
         double t, dte;
@@ -1407,23 +1436,58 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         }
     }
     job0[nsteps] = (int64_t)jobs.size();
-    std::vector<std::vector<uint8_t>> built(jobs.size());
-    std::vector<int> built_rc(jobs.size(), QMC_OK);
+    // Every (step, instance, pass) program is built by host threads in step
+    // order while the GPU runs the steps already built: chunks of 1, 2, 4, ...
+    // steps are assembled, copied and launched as soon as their programs are
+    // ready, so that building overlaps the device's work.
+    const int64_t nj = (int64_t)jobs.size();
+    std::vector<std::vector<uint8_t>> built(nj);
+    std::vector<int> built_rc(nj, QMC_OK);
+    std::unique_ptr<std::atomic<int>[]> ready(new std::atomic<int>[nj]);
+    for (int64_t j = 0; j < nj; ++j) ready[j].store(0);
+    std::atomic<int64_t> next_job{0};
+    std::mutex mu;
+    std::condition_variable cv;
+    struct Pool {   // joins the builders on every exit path
+        std::vector<std::thread> th;
+        std::atomic<int64_t>* next;
+        int64_t nj;
+        ~Pool()
+        {
+            next->store(nj);
+            for (auto& t : th) t.join();
+        }
+    } pool{{}, &next_job, nj};
     {
-        const int64_t nj = (int64_t)jobs.size();
-        unsigned hw = std::thread::hardware_concurrency();
-        const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)16, nj / 8}));
-        auto work = [&](int w) {
-            for (int64_t j = w; j < nj; j += nthr)
-                built_rc[j] = build_program(ctx->inst[jobs[j].k].sched, jobs[j].t, jobs[j].dte, &built[j]);
-        };
-        std::vector<std::thread> pool;
-        for (int w = 1; w < nthr; ++w) pool.emplace_back(work, w);
-        work(0);
-        for (auto& th : pool) th.join();
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)16, nj}));
+        for (int w = 0; w < nthr; ++w)
+            pool.th.emplace_back([&]() {
+                for (;;) {
+                    const int64_t j = next_job.fetch_add(1);
+                    if (j >= nj) return;
+                    built_rc[j] = build_program(ctx->inst[jobs[j].k].sched, jobs[j].t, jobs[j].dte, &built[j]);
+                    {
+                        std::lock_guard<std::mutex> g(mu);
+                        ready[j].store(1);
+                    }
+                    cv.notify_all();
+                }
+            });
     }
+    int64_t jready = 0;
+    auto wait_built = [&](int64_t jend) {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] {
+            while (jready < jend && ready[jready].load()) ++jready;
+            return jready >= jend;
+        });
+    };
     auto add_prog = [&](int64_t j, int64_t* off_out) -> int {
-        if (built_rc[j] != QMC_OK) return built_rc[j];
+        if (built_rc[j] != QMC_OK) {
+            if (built_rc[j] == QMC_ERR_COEF_RANGE) return fail(ctx, built_rc[j], "coefficient * rate * dt >= 2^10");
+            return built_rc[j];
+        }
         const std::vector<uint8_t>& tmp = built[j];
         const ProgHeader* h = (const ProgHeader*)tmp.data();
         if (h->n_entry > kMaxEntries)
@@ -1444,35 +1508,72 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
         *off_out = (int64_t)at;
         return QMC_OK;
     };
-    std::vector<int64_t> tab(2 * (size_t)ni);
-    for (int64_t i = 0; i < nsteps; ++i) {
-        for (int64_t j = job0[i]; j < job0[i + 1]; ++j) {
-            int64_t off = 0;
-            const int rc = add_prog(j, &off);
-            if (rc != QMC_OK) {
-                if (rc == QMC_ERR_COEF_RANGE) return fail(ctx, rc, "coefficient * rate * dt >= 2^10");
-                return rc;
-            }
-            tab[2 * jobs[j].k + jobs[j].pass] = off;
-            if (jobs[j].pass == 0) tab[2 * jobs[j].k + 1] = off;   // pass 1 repeats pass 0 when absent
-        }
-        const size_t at = (blob.size() + 15) & ~(size_t)15;
-        blob.resize(at + tab.size() * sizeof(int64_t));
-        std::memcpy(blob.data() + at, tab.data(), tab.size() * sizeof(int64_t));
-        info[i].tab_off = (int64_t)at;
-    }
     int rc;
     if ((rc = enter(ctx)) != QMC_OK) return rc;
-    if ((rc = upload_calls(ctx, info, blob)) != QMC_OK) return rc;
+    if ((rc = ensure_call_capacity(ctx, nsteps)) != QMC_OK) return rc;
     int32_t zero = 0;
     CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &zero, 4, cudaMemcpyHostToDevice,
                        ctx->work));
-    int64_t done = 0;
-    for (int attempt = 0; attempt < 64; ++attempt) {
+    // A program that cannot be built stops the call before its step: the
+    // steps before it run to completion, then the call returns the error.
+    int build_err = QMC_OK;
+    int64_t nrun = 0;   // steps assembled and launched
+    int64_t uploaded = 0;
+    std::vector<int64_t> tab(2 * (size_t)ni);
+    for (int64_t chunk = 1; nrun < nsteps && build_err == QMC_OK; chunk *= 2) {
+        const int64_t end = std::min(nsteps, nrun + chunk);
+        wait_built(job0[end]);
+        int64_t i = nrun;
+        for (; i < end && build_err == QMC_OK; ++i) {
+            for (int64_t j = job0[i]; j < job0[i + 1]; ++j) {
+                int64_t off = 0;
+                if ((build_err = add_prog(j, &off)) != QMC_OK) break;
+                tab[2 * jobs[j].k + jobs[j].pass] = off;
+                if (jobs[j].pass == 0) tab[2 * jobs[j].k + 1] = off;   // pass 1 repeats pass 0 when absent
+            }
+            if (build_err != QMC_OK) break;
+            const size_t at = (blob.size() + 15) & ~(size_t)15;
+            blob.resize(at + tab.size() * sizeof(int64_t));
+            std::memcpy(blob.data() + at, tab.data(), tab.size() * sizeof(int64_t));
+            info[i].tab_off = (int64_t)at;
+        }
+        const int64_t stop = i;   // steps [nrun, stop) are complete
+        if (stop == nrun) break;
+        if ((int64_t)blob.size() > std::min(ctx->progs_cap, ctx->h_progs_cap)) {
+            // room for the whole call as the steps so far suggest
+            const int64_t per = (int64_t)blob.size() / stop;
+            const int64_t want = (int64_t)blob.size() + per * (nsteps - stop) * 5 / 4 + 65536;
+            if (uploaded > 0) CK(cudaStreamSynchronize(ctx->work));   // the staging is rewritten below
+            if ((rc = ensure_progs(ctx, want)) != QMC_OK) return rc;
+            uploaded = 0;   // a new device buffer: copy every program again
+        }
+        const int64_t nb = (int64_t)blob.size() - uploaded;
+        std::memcpy(ctx->h_progs + uploaded, blob.data() + uploaded, (size_t)nb);
+        CK(cudaMemcpyAsync(ctx->d_progs + uploaded, ctx->h_progs + uploaded, (size_t)nb, cudaMemcpyHostToDevice,
+                           ctx->work));
+        uploaded = (int64_t)blob.size();
+        std::memcpy(ctx->h_info + nrun, info.data() + nrun, (size_t)(stop - nrun) * sizeof(StepInfo));
+        CK(cudaMemcpyAsync(ctx->d_info + nrun, ctx->h_info + nrun, (size_t)(stop - nrun) * sizeof(StepInfo),
+                           cudaMemcpyHostToDevice, ctx->work));
         if ((rc = capture_graph(ctx)) != QMC_OK) return rc;
-        for (int64_t i = done; i < nsteps; ++i) {
+        for (int64_t s = nrun; s < stop; ++s) {
             if ((rc = note_launches(ctx, 1)) != QMC_OK) return rc;
             CK(cudaGraphLaunch(ctx->graph, ctx->work));
+        }
+        nrun = stop;
+    }
+    if (nrun == 0) {
+        leave(ctx);
+        return build_err;
+    }
+    int64_t done = 0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        if (attempt > 0) {   // the first attempt's steps were launched above
+            if ((rc = capture_graph(ctx)) != QMC_OK) return rc;
+            for (int64_t i = done; i < nrun; ++i) {
+                if ((rc = note_launches(ctx, 1)) != QMC_OK) return rc;
+                CK(cudaGraphLaunch(ctx->graph, ctx->work));
+            }
         }
         DevState hs;
         CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
@@ -1516,18 +1617,18 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
             return map_dev_error(ctx, code, hs.error_aux);
         }
         // redo from the failed step
-        ctx->acc_redo += nsteps - done;
+        ctx->acc_redo += nrun - done;
         CK(cudaMemcpyAsync((uint8_t*)ctx->d_state + offsetof(DevState, call_index), &done, 4,
                            cudaMemcpyHostToDevice, ctx->work));
         (void)zero;
     }
-    if (done != nsteps) return fail(ctx, QMC_ERR_CAPACITY, "could not complete the steps after growing buffers");
-    ctx->step += (uint64_t)nsteps;
-    ctx->t_prev = t0 + (double)(nsteps - 1) * dt;
-    ctx->t = t0 + (double)nsteps * dt;
+    if (done != nrun) return fail(ctx, QMC_ERR_CAPACITY, "could not complete the steps after growing buffers");
+    ctx->step += (uint64_t)nrun;
+    ctx->t_prev = t0 + (double)(nrun - 1) * dt;
+    ctx->t = t0 + (double)nrun * dt;
     ctx->dt_last = dt;
     ctx->prev_valid = true;
-    ctx->last_call_steps = nsteps;
+    ctx->last_call_steps = nrun;
     // grow ahead of need so the next call rarely retries
     DevState hs;
     CK(cudaMemcpyAsync(&hs, ctx->d_state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->work));
@@ -1546,7 +1647,8 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     }
     if (hs.max_next > ctx->pop_cap * 3 / 4 && (ctx->cfg.max_records == 0 || ctx->pop_cap < ctx->cfg.max_records))
         if ((rc = grow_pop(ctx, hs.max_next * 2)) != QMC_OK) return rc;
-    return leave(ctx);
+    if ((rc = leave(ctx)) != QMC_OK) return rc;
+    return build_err;   // QMC_OK unless a later step's program could not be built
 }
 
 int qmc_step_history(qmc_ctx* ctx, qmc_obs* obs, int64_t cap_steps, int64_t* count)

@@ -338,17 +338,28 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
         int64_t first = 0;
         uint2 kd = make_uint2(0u, 0u);
         int64_t pre = -1;
-        // the vector of the warp's first group, then per lane only across a boundary
-        int seg0 = lane == 0 ? wgroup_seg(gof, P.nseg, base) : 0;
+        // the vector of the warp's first group with its prefilter bound and
+        // key, then per lane only across a boundary
+        int seg0 = 0;
+        int64_t pre0 = 0;
+        uint2 kd0 = make_uint2(0u, 0u);
+        if (lane == 0) {
+            seg0 = wgroup_seg(gof, P.nseg, base);
+            pre0 = wprog_at(prog_of(P, inf, P.seginfo[seg0].inst, phase)).h->p_bound >> 20;
+            kd0 = P.kd[seg0];
+        }
         seg0 = __shfl_sync(kFull, seg0, 0);
+        pre0 = __shfl_sync(kFull, pre0, 0);
+        kd0.x = __shfl_sync(kFull, kd0.x, 0);
+        kd0.y = __shfl_sync(kFull, kd0.y, 0);
         const int64_t seg0_end = gof[seg0 + 1];
         if (g < G) {
             seg = g < seg0_end ? seg0 : wgroup_seg(gof, P.nseg, g);
             grp = (uint32_t)(g - gof[seg]);
             first = off[seg] + 4 * (int64_t)grp;
             const int cnt = (int)min((int64_t)4, off[seg + 1] - first);
-            kd = P.kd[seg];
-            pre = wprog_at(prog_of(P, inf, P.seginfo[seg].inst, phase)).h->p_bound >> 20;
+            kd = seg == seg0 ? kd0 : P.kd[seg];
+            pre = seg == seg0 ? pre0 : wprog_at(prog_of(P, inf, P.seginfo[seg].inst, phase)).h->p_bound >> 20;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k >= cnt) break;
@@ -425,7 +436,7 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
 
 // Candidates: the parent's exact column weight, the walker's full draw and,
 // if it spawns, its record.
-__global__ void __launch_bounds__(kWThreads, 1) k_wide_choose(StepParams P, WideParams W)
+__global__ void __launch_bounds__(kWThreads, 3) k_wide_choose(StepParams P, WideParams W)
 {
     DevState* st = P.st;
     if (cta_error(st)) return;
@@ -1055,10 +1066,36 @@ __global__ void k_wide_spawn_off(StepParams P, WideParams W)
     }
 }
 
+// Where each bucket of the spawn sort starts in N(t): abound[b] = first
+// record of b's vector whose key is at least the bucket's smallest key
+// (abound[2^bucket_bits] = K), so a spawn's key lies between abound[b] and
+// abound[b + 1] of its bucket b.
+__global__ void __launch_bounds__(kWThreads) k_wide_abound(StepParams P, WideParams W)
+{
+    DevState* st = P.st;
+    if (cta_error(st) || P.sort_mode == 0) return;
+    const int cur = st->cur;
+    const WPop A = wpop(P, cur);
+    const int64_t* offA = P.segoff[cur];
+    const int nb = 1 << P.bucket_bits, kb = P.bucket_kb, n2 = 2 * P.n;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+        const int seg = b >> kb;
+        int64_t p = offA[P.nseg];
+        if (b < nb && seg < P.nseg) {
+            const u128 lo = kb ? (u128)(uint32_t)(b & ((1 << kb) - 1)) << (n2 - kb) : (u128)0;
+            p = lower_bound_pop(A.key, offA[seg], offA[seg + 1], lo);
+        }
+        W.abound[b] = p;
+    }
+}
+
 // Runs of equal (vector, key) among the sorted spawns, at their first record.
 // A run on a key N(t) holds leaves its spawn sum in delta and, when that
 // zeroes the record, counts it in the record's merge tile; a run that brings
-// a new key counts it before its position in N(t) and in that tile.
+// a new key counts it before its position in N(t) and in that tile (one
+// atomic per warp when the warp's counts share a tile, as sorted spawns
+// mostly do).  The key is looked up in its bucket's stretch of N(t) (its
+// whole vector without the bucket digit).
 __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParams W)
 {
     DevState* st = P.st;
@@ -1068,52 +1105,80 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
     const int cur = st->cur;
     const WPop A = wpop(P, cur);
     const int64_t* offA = P.segoff[cur];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
-        const WSpawn r = wsload(sp, i);
-        const u128 k = wkey(r);
-        const uint32_t seg = r.meta >> 2;
-        if (i > 0) {
-            const WSpawn q = wsload(sp, i - 1);
-            if ((q.meta >> 2) == seg && wkey(q) == k) {
+    const int kb = P.bucket_kb, n2 = 2 * P.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < S; base += stride) {
+        const int64_t i = base + lane;
+        unsigned long long add = 0;   // records zeroed | new keys << 32, for tile `tile`
+        int64_t tile = -1;
+        if (i < S) {
+            const WSpawn r = wsload(sp, i);
+            const u128 k = wkey(r);
+            const uint32_t seg = r.meta >> 2;
+            bool head = true;
+            if (i > 0) {
+                const WSpawn q = wsload(sp, i - 1);
+                head = !((q.meta >> 2) == seg && wkey(q) == k);
+            }
+            if (!head) {
                 W.flag_u[i] = 0;
-                continue;
+            } else {
+                int64_t ire = 0, iim = 0, are = 0, aim = 0;
+                for (int64_t j = i; j < S; ++j) {
+                    const WSpawn q = wsload(sp, j);
+                    if ((q.meta >> 2) != seg || wkey(q) != k) break;
+                    const int64_t v = q.val;
+                    const bool to_im = (q.meta >> 1) & 1u;
+                    if (to_im) aim += v; else are += v;
+                    if (!(q.meta & 1u)) {
+                        if (to_im) iim += v; else ire += v;
+                    }
+                }
+                const int64_t hi = offA[seg + 1];
+                int64_t lo = offA[seg], top = hi;
+                if (P.sort_mode != 0) {
+                    const uint32_t bk = wbucket(r, kb, n2);
+                    lo = W.abound[bk];
+                    top = W.abound[bk + 1];
+                }
+                const int64_t pos = lower_bound_pop(A.key, lo, top, k);
+                const bool matched = pos < hi && wkey(A.key[pos]) == k;
+                WRun run;
+                run.posA = pos;
+                run.re = matched ? are : ire;
+                run.im = matched ? aim : iim;
+                run.matched = matched ? 1 : 0;
+                run.pad = 0;
+                W.run[i] = run;
+                if (iabs64(run.re) > 2147483647ll || iabs64(run.im) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
+                const bool fresh = !matched && (ire != 0 || iim != 0);
+                if (matched) {
+                    W.delta[pos] = make_int2((int32_t)are, (int32_t)aim);   // the one run on this key
+                    const int2 a = __ldg(&A.val[pos]);
+                    const int64_t vr = (int64_t)a.x + are, vi = (int64_t)a.y + aim;
+                    if (iabs64(vr) > 2147483647ll || iabs64(vi) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
+                    if (vr == 0 && vi == 0) add = 1ull;
+                }
+                if (fresh) {
+                    atomicAdd(&W.newcnt[pos], 1);
+                    add = 1ull << 32;
+                }
+                if (add) tile = pos / kWMTile;
+                W.flag_u[i] = fresh ? 1 : 0;
             }
         }
-        int64_t ire = 0, iim = 0, are = 0, aim = 0;
-        for (int64_t j = i; j < S; ++j) {
-            const WSpawn q = wsload(sp, j);
-            if ((q.meta >> 2) != seg || wkey(q) != k) break;
-            const int64_t v = q.val;
-            const bool to_im = (q.meta >> 1) & 1u;
-            if (to_im) aim += v; else are += v;
-            if (!(q.meta & 1u)) {
-                if (to_im) iim += v; else ire += v;
-            }
+        // the warp's tile counts: one atomic when they share a tile
+        const uint32_t act = __ballot_sync(kFull, add != 0);
+        if (!act) continue;
+        const int64_t t0 = __shfl_sync(kFull, tile, __ffs(act) - 1);
+        if (__all_sync(kFull, add == 0 || tile == t0)) {
+            const uint32_t kills = __reduce_add_sync(kFull, (uint32_t)add);
+            const uint32_t news = __reduce_add_sync(kFull, (uint32_t)(add >> 32));
+            if (lane == 0) atomicAdd(&W.mtile[t0], (unsigned long long)kills | ((unsigned long long)news << 32));
+        } else if (add) {
+            atomicAdd(&W.mtile[tile], add);
         }
-        const int64_t lo = offA[seg], hi = offA[seg + 1];
-        const int64_t pos = lower_bound_pop(A.key, lo, hi, k);
-        const bool matched = pos < hi && wkey(A.key[pos]) == k;
-        WRun run;
-        run.posA = pos;
-        run.re = matched ? are : ire;
-        run.im = matched ? aim : iim;
-        run.matched = matched ? 1 : 0;
-        run.pad = 0;
-        W.run[i] = run;
-        if (iabs64(run.re) > 2147483647ll || iabs64(run.im) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
-        const bool fresh = !matched && (ire != 0 || iim != 0);
-        if (matched) {
-            W.delta[pos] = make_int2((int32_t)are, (int32_t)aim);   // the one run on this key
-            const int2 a = __ldg(&A.val[pos]);
-            const int64_t vr = (int64_t)a.x + are, vi = (int64_t)a.y + aim;
-            if (iabs64(vr) > 2147483647ll || iabs64(vi) > 2147483647ll) set_error(st, DERR_POP_OVERFLOW);
-            if (vr == 0 && vi == 0) atomicAdd(&W.mtile[pos / kWMTile], 1ull);
-        }
-        if (fresh) {
-            atomicAdd(&W.newcnt[pos], 1);
-            atomicAdd(&W.mtile[pos / kWMTile], 1ull << 32);
-        }
-        W.flag_u[i] = fresh ? 1 : 0;
     }
 }
 
@@ -1124,7 +1189,16 @@ __device__ __forceinline__ int64_t merge_tiles(int64_t K) { return K / kWMTile +
 // Per merge tile (one CTA): survivors and new keys before it, from the
 // counts of the runs kernel (the records of a tile less those its spawns
 // zero); clears the counts for the next step; N(t + dt)'s size, with
-// POP_CAPACITY when it does not fit.
+// POP_CAPACITY when it does not fit.  Each thread sums a contiguous run of
+// tiles, one block scan places the runs, the thread writes its tiles' bases.
+__device__ __forceinline__ void mtile_counts(const WideParams& W, int64_t t, int64_t K, long long* s, long long* nn)
+{
+    const unsigned long long m = W.mtile[t];
+    const int64_t lo = t * kWMTile, hi = min(K, lo + kWMTile);
+    *s = (hi - lo) - (long long)(m & 0xFFFFFFFFull);
+    *nn = (long long)(m >> 32);
+}
+
 __global__ void __launch_bounds__(1024) k_wide_mtop(StepParams P, WideParams W)
 {
     __shared__ long long ws[32], wn[32];
@@ -1133,48 +1207,50 @@ __global__ void __launch_bounds__(1024) k_wide_mtop(StepParams P, WideParams W)
     const int64_t K = P.segoff[st->cur][P.nseg];
     const int64_t T = merge_tiles(K);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    long long cs = 0, cn = 0;
-    for (int64_t base = 0; base < T; base += blockDim.x) {
-        const int64_t t = base + threadIdx.x;
-        long long s = 0, nn = 0;
-        if (t < T) {
-            const unsigned long long m = W.mtile[t];
-            W.mtile[t] = 0ull;
-            const int64_t lo = t * kWMTile, hi = min(K, lo + kWMTile);
-            s = (hi - lo) - (long long)(m & 0xFFFFFFFFull);
-            nn = (long long)(m >> 32);
-        }
-        long long is = s, in = nn;
+    const int64_t per = (T + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = min(T, (int64_t)threadIdx.x * per), t1 = min(T, t0 + per);
+    long long s = 0, nn = 0;
+#pragma unroll 4
+    for (int64_t t = t0; t < t1; ++t) {
+        long long a, b;
+        mtile_counts(W, t, K, &a, &b);
+        s += a;
+        nn += b;
+    }
+    long long is = s, in = nn;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long a = __shfl_up_sync(kFull, is, o), b = __shfl_up_sync(kFull, in, o);
-            if (lane >= o) {
-                is += a;
-                in += b;
-            }
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(kFull, is, o), b = __shfl_up_sync(kFull, in, o);
+        if (lane >= o) {
+            is += a;
+            in += b;
         }
-        if (lane == 31) {
-            ws[warp] = is;
-            wn[warp] = in;
+    }
+    if (lane == 31) {
+        ws[warp] = is;
+        wn[warp] = in;
+    }
+    __syncthreads();
+    long long cs = is - s, cn = in - nn, ts = 0, tn = 0;
+    for (int q = 0; q < nw; ++q) {
+        if (q < warp) {
+            cs += ws[q];
+            cn += wn[q];
         }
-        __syncthreads();
-        long long os = 0, on = 0, bs = 0, bn = 0;
-        for (int q = 0; q < nw; ++q) {
-            if (q < warp) {
-                os += ws[q];
-                on += wn[q];
-            }
-            bs += ws[q];
-            bn += wn[q];
-        }
-        if (t < T) W.mbase[t] = make_longlong2(cs + os + is - s, cn + on + in - nn);
-        cs += bs;
-        cn += bn;
-        __syncthreads();
+        ts += ws[q];
+        tn += wn[q];
+    }
+    for (int64_t t = t0; t < t1; ++t) {
+        long long a, b;
+        mtile_counts(W, t, K, &a, &b);
+        W.mtile[t] = 0ull;
+        W.mbase[t] = make_longlong2(cs, cn);
+        cs += a;
+        cn += b;
     }
     if (threadIdx.x == 0) {
-        W.mbase[T] = make_longlong2(cs, cn);
-        const int64_t total = cs + cn;
+        W.mbase[T] = make_longlong2(ts, tn);
+        const int64_t total = ts + tn;
         st->next_total = total;
         if (total > st->max_next) st->max_next = total;
         if (total > P.pop_cap) set_error(st, DERR_POP_CAPACITY);
@@ -1333,15 +1409,19 @@ struct ObsAcc {
 // annihilation step]: each record's value plus the spawn sum of its run
 // (delta); survivors (nonzero) go to their place in the key-ordered union,
 // after the survivors and new keys before them and the new keys just before
-// them.  The places come from the tile's bases and a prefix over the tile in
-// rounds of kWThreads indices.  Where new keys go just before a record, and at
-// the first record of every vector, the survivors before it are left in scan_a
-// for the new keys' scatter and the vector offsets.  delta and newcnt are
-// cleared where set.  Each CTA takes a contiguous range of tiles.
-__global__ void __launch_bounds__(kWThreads) k_wide_merge_a(StepParams P, WideParams W)
+// them.  The places come from the tile's bases and a prefix over the tile,
+// kWMBatch rounds of kWThreads indices at a time (the batch's loads issued
+// together, one barrier per batch).  Where new keys go just before a record,
+// and at the first record of every vector, the survivors before it are left
+// in scan_a for the new keys' scatter and the vector offsets.  delta and
+// newcnt are cleared where set.  Each CTA takes a contiguous range of tiles.
+constexpr int kWMBatch = 4;
+
+__global__ void __launch_bounds__(kWThreads, 3) k_wide_merge_a(StepParams P, WideParams W)
 {
     constexpr int kWarps = kWThreads / 32;
-    __shared__ unsigned long long s_w[2][kWarps];
+    constexpr int kSpan = kWMBatch * kWThreads;
+    __shared__ unsigned long long s_w[2][kWMBatch][kWarps];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int cur = st->cur;
@@ -1359,68 +1439,83 @@ __global__ void __launch_bounds__(kWThreads) k_wide_merge_a(StepParams P, WidePa
     int par = 0;
     for (int64_t t = tb; t < te; ++t) {
         const longlong2 base = W.mbase[t];
-        unsigned long long carry = 0;   // survivors | new keys << 32 of the tile's earlier rounds
-        for (int r = 0; r < kWMTile / kWThreads; ++r) {
-            const int64_t r0 = t * kWMTile + (int64_t)r * kWThreads;
+        unsigned long long carry = 0;   // survivors | new keys << 32 of the tile's earlier indices
+        for (int r = 0; r < kWMTile / kSpan; ++r) {
+            const int64_t r0 = t * kWMTile + (int64_t)r * kSpan;
             if (r0 > K) break;   // same for the whole CTA
-            const int64_t i = r0 + tid;
-            bool keep = false, start = false;
-            int nc = 0;
-            int2 v = make_int2(0, 0);
-            if (i <= K) {
-                nc = W.newcnt[i];
-                if (nc) W.newcnt[i] = 0;
-            }
-            if (i < K) {
-                const int2 d = W.delta[i];
-                if (d.x | d.y) W.delta[i] = make_int2(0, 0);
-                const int2 a = __ldg(&A.val[i]);
-                v = make_int2(a.x + d.x, a.y + d.y);   // range checked by the runs kernel
-                keep = (v.x | v.y) != 0;
-                if (acc.seg < 0 || i >= seg_hi) {
-                    acc.flush(P.segacc);
-                    acc.seg = seg_of(offA, P.nseg, i);
-                    seg_lo = offA[acc.seg];
-                    seg_hi = offA[acc.seg + 1];
-                    n = P.seginfo[acc.seg].n;
+            int nc[kWMBatch];
+            int2 v[kWMBatch];
+            ulonglong2 key[kWMBatch];
+            unsigned long long x[kWMBatch], incl[kWMBatch];
+#pragma unroll
+            for (int b = 0; b < kWMBatch; ++b) {
+                const int64_t i = r0 + b * kWThreads + tid;
+                nc[b] = i <= K ? W.newcnt[i] : 0;
+                int2 d = make_int2(0, 0), a = make_int2(0, 0);
+                key[b] = make_ulonglong2(0ull, 0ull);
+                if (i < K) {
+                    d = W.delta[i];
+                    a = __ldg(&A.val[i]);
+                    key[b] = __ldg(&A.key[i]);
                 }
-                start = i == seg_lo;
-            } else if (i == K) {
-                start = true;
+                v[b] = make_int2(a.x + d.x, a.y + d.y);   // range checked by the runs kernel
+                if (d.x | d.y) W.delta[i] = make_int2(0, 0);
+                if (nc[b]) W.newcnt[i] = 0;
+                x[b] = ((v[b].x | v[b].y) != 0 ? 1ull : 0ull) | ((unsigned long long)(uint32_t)nc[b] << 32);
+                incl[b] = x[b];
             }
-            const unsigned long long x = (keep ? 1ull : 0ull) | ((unsigned long long)(uint32_t)nc << 32);
-            unsigned long long incl = x;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane == 31) s_w[par][warp] = incl;
-            __syncthreads();
-            unsigned long long wo = 0, blk = 0;
 #pragma unroll
-            for (int q = 0; q < kWarps; ++q) {
-                const unsigned long long u = s_w[par][q];
-                if (q < warp) wo += u;
-                blk += u;
-            }
-            par ^= 1;
-            const unsigned long long ex = carry + wo + incl - x;
-            carry += blk;
-            const int64_t surv = base.x + (int64_t)(ex & 0xFFFFFFFFull);
-            const int64_t newb = base.y + (int64_t)(ex >> 32);
-            if (nc > 0 || start) W.scan_a[i] = surv;
-            if (keep) {
-                const int64_t o = surv + newb + nc;
-                if (o < P.pop_cap) {
-                    const ulonglong2 key = __ldg(&A.key[i]);
-                    out.key[o] = key;
-                    out.val[o] = v;
-                    acc.add(key, v, n);
-                } else {
-                    set_error(st, DERR_POP_CAPACITY);
+                for (int b = 0; b < kWMBatch; ++b) {
+                    const unsigned long long y = __shfl_up_sync(kFull, incl[b], o);
+                    if (lane >= o) incl[b] += y;
                 }
             }
+            if (lane == 31) {
+#pragma unroll
+                for (int b = 0; b < kWMBatch; ++b) s_w[par][b][warp] = incl[b];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < kWMBatch; ++b) {
+                unsigned long long wo = 0, blk = 0;
+#pragma unroll
+                for (int q = 0; q < kWarps; ++q) {
+                    const unsigned long long u = s_w[par][b][q];
+                    if (q < warp) wo += u;
+                    blk += u;
+                }
+                const unsigned long long ex = carry + wo + incl[b] - x[b];
+                carry += blk;
+                const int64_t i = r0 + b * kWThreads + tid;
+                if (i > K) continue;
+                const int64_t surv = base.x + (int64_t)(ex & 0xFFFFFFFFull);
+                const int64_t newb = base.y + (int64_t)(ex >> 32);
+                bool start = i == K;
+                if (i < K) {
+                    if (acc.seg < 0 || i >= seg_hi) {
+                        acc.flush(P.segacc);
+                        acc.seg = seg_of(offA, P.nseg, i);
+                        seg_lo = offA[acc.seg];
+                        seg_hi = offA[acc.seg + 1];
+                        n = P.seginfo[acc.seg].n;
+                    }
+                    start = i == seg_lo;
+                }
+                if (nc[b] > 0 || start) W.scan_a[i] = surv;
+                if (x[b] & 1ull) {
+                    const int64_t o = surv + newb + nc[b];
+                    if (o < P.pop_cap) {
+                        out.key[o] = key[b];
+                        out.val[o] = v[b];
+                        acc.add(key[b], v[b], n);
+                    } else {
+                        set_error(st, DERR_POP_CAPACITY);
+                    }
+                }
+            }
+            par ^= 1;
         }
         // self-check: the tile's survivors and new keys as the runs counted them
         if (tid == 0) {
@@ -1614,6 +1709,7 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
     mark(0);
     k_wide_prologue<<<1, kWThreads, 0, s>>>(P);
     k_wide_zero_hist<<<1, kWThreads, 0, s>>>(W);
+    k_wide_abound<<<g, kWThreads, 0, s>>>(P, W);
     mark(1);
     k_wide_spawn<<<g, kWThreads, 0, s>>>(P, W, 0);
     k_wide_spawn<<<g, kWThreads, 0, s>>>(P, W, 1);
@@ -1656,7 +1752,7 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
 int wide_step_launch_count(const StepParams& P, const WideParams& W)
 {
     (void)P;
-    return 15 + 3 * W.passes + 3 + 3 + 3 + 1;
+    return 16 + 3 * W.passes + 3 + 3 + 3 + 1;
 }
 
 namespace {
