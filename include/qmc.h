@@ -369,12 +369,14 @@ int qmc_get_clock(const qmc_ctx* ctx, uint64_t* step, double* t, double* t_prev,
  * L(t0 + i dt), t0 = the clock at entry; AB2 steps also spawn from N(t - dt)
  * with L at the previous step's time [End Matter, simulation methodology].
  * Issued asynchronously on the context stream (captured once in a CUDA graph
- * and replayed); returns after checking the device status word.  On
- * CAPACITY the buffers grow and the failed step is redone (the result is
- * bit-identical: every draw is keyed by step, vector, key and walker).
- * Errors: STATE, DT_TOO_LARGE, POP_OVERFLOW, CAPACITY (past max_records),
- * DEVICE_TIMEOUT, CUDA.  After an error the state is that of the last
- * completed step. */
+ * and replayed); the column programs of the steps are built by host threads
+ * while the device runs the steps already built; returns after checking the
+ * device status word.  On CAPACITY the buffers grow and the failed step is
+ * redone (the result is bit-identical: every draw is keyed by step, vector,
+ * key and walker).  Errors: STATE, DT_TOO_LARGE, POP_OVERFLOW, CAPACITY (past
+ * max_records), DEVICE_TIMEOUT, CUDA, COEF_RANGE or INVALID_ARG (a step's
+ * column cannot be built: the steps before it complete), OOM.  After an
+ * error the state is that of the last completed step. */
 int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps);
 
 /* Take nsteps steps like qmc_step (dt, nsteps >= 1), and time each kernel of

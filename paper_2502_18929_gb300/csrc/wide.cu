@@ -119,18 +119,6 @@ struct WParent {
     uint2 kd;
 };
 
-// The exact column weight P of a loaded parent (once); false (after raising
-// the error) when its spawn probability reaches 1.
-__device__ __forceinline__ bool weigh_parent(const StepParams& P, const WProg& pr, WParent* q)
-{
-    if (q->Pw < 0) q->Pw = column_weight(pr, q->x, q->y, &q->sre, &q->sim);
-    if (q->Pw >= (1ll << 52)) {
-        set_error(P.st, DERR_DT_TOO_LARGE);
-        return false;
-    }
-    return true;
-}
-
 // Parent i of a slot with its column weight evaluated.  Returns false (after
 // raising the error) when its spawn probability reaches 1.
 __device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WPop& pop, const int64_t* off, int64_t i,
@@ -161,34 +149,25 @@ __device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WPop
     return true;
 }
 
-// Walker w of a parent (real walkers first) with its 32-bit word W: the
-// prefilter W <= (P - 1) >> 20, then the full draw T = W << 20 | L [reading
-// R3]; if T < P the spawn record of the destination whose cumulative-weight
-// interval holds T, with the paper's sign rule [End Matter, spawn step].
-__device__ __forceinline__ bool wide_walker(const WProg& pr, const WParent& q, int64_t w, uint32_t W, WSpawn* out)
+// The spawn record of a walker of component comp (0 real, 1 imaginary) whose
+// parent's value has sign sg there, onto dest through channel chan of an
+// element of sign v, with the paper's sign rule [End Matter, spawn step]: the
+// Re channel keeps the component, the Im channel multiplies by i; sigma = -1
+// for the N(t - dt) pass.
+__device__ __forceinline__ WSpawn wide_record(u128 dest, int seg, int comp, int chan, int64_t v, int sg, int phase,
+                                              int noninit)
 {
-    if ((int64_t)W > ((q.Pw - 1) >> 20)) return false;
-    const int64_t are = iabs64(q.re);
-    const int comp = w < are ? 0 : 1;
-    const uint32_t j = (uint32_t)(comp ? w - are : w);
-    const int64_t T = walker_T(W, q.rank, j, comp, q.phase, q.kd);
-    if (T >= q.Pw) return false;
-    u128 mask;
-    int chan;
-    int64_t v;
-    if (!choose_destination(pr, q.x, q.y, q.sre, q.sim, T, &mask, &chan, &v)) return false;
-    const int sg = comp == 0 ? (q.re > 0 ? 1 : -1) : (q.im > 0 ? 1 : -1);
-    const int s = (q.phase ? -1 : 1) * sg * (v > 0 ? 1 : -1);
+    const int s = (phase ? -1 : 1) * sg * (v > 0 ? 1 : -1);
     int target, val;
     if (chan == 0) { target = comp; val = s; }
     else if (comp == 0) { target = 1; val = s; }
     else { target = 0; val = -s; }
-    const u128 dest = q.key ^ mask;
-    out->lo = (uint64_t)dest;
-    out->hi = (uint64_t)(dest >> 64);
-    out->meta = ((uint32_t)q.seg << 2) | ((uint32_t)target << 1) | (uint32_t)q.noninit;
-    out->val = val;
-    return true;
+    WSpawn r;
+    r.lo = (uint64_t)dest;
+    r.hi = (uint64_t)(dest >> 64);
+    r.meta = ((uint32_t)seg << 2) | ((uint32_t)target << 1) | (uint32_t)noninit;
+    r.val = val;
+    return r;
 }
 
 // The 32-bit word of walker w (w = 0, 1: the rank group's call of level w;
@@ -198,6 +177,46 @@ __device__ __forceinline__ uint32_t walker_word(const WParent& q, int64_t w)
     if (w <= 1) return word_of(group_words(q.rank >> 2, (uint32_t)w, q.phase, q.kd), (int)(q.rank & 3u));
     return word_of(extra_words(q.rank, (uint32_t)((w - 2) >> 2), q.phase, q.kd), (int)((w - 2) & 3));
 }
+
+// Records a warp appends to a global array (dst, capacity cap, counter
+// total), gathered in kCap slots of shared memory: one atomic on the counter
+// and one contiguous copy per full stage instead of one atomic per round.
+// Every call is made by all 32 lanes; count is the same in every lane.
+template <typename T, int kCap>
+struct WarpStage {
+    T* buf;
+    int count;
+
+    __device__ __forceinline__ void flush(unsigned long long* total, T* dst, int64_t cap, DevState* st,
+                                          uint32_t err, int lane)
+    {
+        __syncwarp();
+        if (count == 0) return;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(total, (unsigned long long)count);
+        b = __shfl_sync(kFull, b, 0);
+        for (int j = lane; j < count; j += 32) {
+            const int64_t pos = (int64_t)b + j;
+            if (pos < cap) dst[pos] = buf[j];
+            else set_error(st, err);
+        }
+        __syncwarp();
+        count = 0;
+    }
+
+    __device__ __forceinline__ void push(bool on, const T& v, unsigned long long* total, T* dst, int64_t cap,
+                                         DevState* st, uint32_t err, int lane)
+    {
+        const uint32_t bal = __ballot_sync(kFull, on);
+        if (!bal) return;
+        const int n = __popc(bal);
+        if (count + n > kCap) flush(total, dst, cap, st, err, lane);
+        if (on) buf[count + __popc(bal & lanemask_lt())] = v;
+        count += n;
+    }
+};
+
+constexpr int kWStage = 128;   // staged records per warp
 
 // Append the spawns the lanes of a warp hold (sp) with one atomic.
 __device__ __forceinline__ void warp_append(const StepParams& P, const WideParams& W, bool sp, const WSpawn& rec,
@@ -297,25 +316,24 @@ __device__ __forceinline__ int wgroup_seg(const int64_t* gof, int nseg, int64_t 
     return lo;
 }
 
-// Candidate record (SpawnCand as four words): parent index in its slot,
-// vector, the walker's 32-bit word W, walker index | phase << 31.
-__device__ __forceinline__ void warp_append_cand(const StepParams& P, bool on, const uint4& c, int lane)
+// Candidate record (four words): parent index in its slot, vector, the
+// walker's 32-bit word W, and cand_word: the walker's index j in its
+// component (20 bits), the component, the pass, the initiator flag and the
+// sign of the parent's value in that component (bits 20 .. 23).
+constexpr uint32_t kWJ20 = (1u << 20) - 1u;
+
+__device__ __forceinline__ uint32_t cand_word(int64_t w, int32_t re, int32_t im, int phase, int non)
 {
-    const uint32_t bal = __ballot_sync(kFull, on);
-    if (!bal) return;
-    const int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd((unsigned long long*)&P.st->cand_total, (unsigned long long)__popc(bal));
-    base = __shfl_sync(kFull, base, leader);
-    if (on) {
-        const int64_t pos = (int64_t)base + __popc(bal & lanemask_lt());
-        if (pos < P.cand_cap) ((uint4*)P.cand)[pos] = c;
-        else set_error(P.st, DERR_CAND_CAPACITY);
-    }
+    const int64_t are = iabs64(re);
+    const int comp = w < are ? 0 : 1;
+    const uint32_t j = (uint32_t)(comp ? w - are : w);
+    const int pos = comp ? (im > 0) : (re > 0);
+    return j | ((uint32_t)comp << 20) | ((uint32_t)phase << 21) | ((uint32_t)non << 22) | ((uint32_t)pos << 23);
 }
 
 __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WideParams W, int phase)
 {
+    __shared__ uint4 s_cand[kWThreads / 32][kWStage];
     DevState* st = P.st;
     if (cta_error(st)) return;
     if (phase == 0 && P.sort_mode != 0)   // bucket counters of this step's spawn sort
@@ -329,10 +347,15 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
     const int64_t* gof = P.gofs[slot];
     const int64_t G = gof[P.nseg];
     const int lane = threadIdx.x & 31;
+    WarpStage<uint4, kWStage> cs{s_cand[threadIdx.x >> 5], 0};
+    unsigned long long* ctot = (unsigned long long*)&st->cand_total;
+    uint4* cdst = (uint4*)P.cand;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < G; base += stride) {
         const int64_t g = base + lane;
         int64_t m[4] = {0, 0, 0, 0};
+        int32_t vre[4] = {0, 0, 0, 0}, vim[4] = {0, 0, 0, 0};
+        int non[4] = {0, 0, 0, 0};
         int seg = 0;
         uint32_t grp = 0;
         int64_t first = 0;
@@ -341,15 +364,18 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
         // the vector of the warp's first group with its prefilter bound and
         // key, then per lane only across a boundary
         int seg0 = 0;
-        int64_t pre0 = 0;
+        int64_t pre0 = 0, imin0 = 0;
         uint2 kd0 = make_uint2(0u, 0u);
         if (lane == 0) {
             seg0 = wgroup_seg(gof, P.nseg, base);
-            pre0 = wprog_at(prog_of(P, inf, P.seginfo[seg0].inst, phase)).h->p_bound >> 20;
+            const int in0 = P.seginfo[seg0].inst;
+            pre0 = wprog_at(prog_of(P, inf, in0, phase)).h->p_bound >> 20;
+            imin0 = P.inst[in0].init_min;
             kd0 = P.kd[seg0];
         }
         seg0 = __shfl_sync(kFull, seg0, 0);
         pre0 = __shfl_sync(kFull, pre0, 0);
+        imin0 = __shfl_sync(kFull, imin0, 0);
         kd0.x = __shfl_sync(kFull, kd0.x, 0);
         kd0.y = __shfl_sync(kFull, kd0.y, 0);
         const int64_t seg0_end = gof[seg0 + 1];
@@ -360,11 +386,15 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
             const int cnt = (int)min((int64_t)4, off[seg + 1] - first);
             kd = seg == seg0 ? kd0 : P.kd[seg];
             pre = seg == seg0 ? pre0 : wprog_at(prog_of(P, inf, P.seginfo[seg].inst, phase)).h->p_bound >> 20;
+            const int64_t imin = seg == seg0 ? imin0 : P.inst[P.seginfo[seg].inst].init_min;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k >= cnt) break;
                 const int2 v = __ldg(&pop.val[first + k]);
                 m[k] = iabs64(v.x) + iabs64(v.y);
+                vre[k] = v.x;
+                vim[k] = v.y;
+                non[k] = (imin > 0 && m[k] < imin) ? 1 : 0;
                 if (m[k] > kWLight) {
                     const int64_t nb = (m[k] - 2 + 3) / 4;
                     const int64_t chunks = (nb + kWChunk - 1) / kWChunk;
@@ -380,37 +410,15 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
                 }
             }
         }
-        // first walkers: one call for the group; the warp's candidates of the
-        // round appended with one atomic
+        // first walkers: one call for the group; the candidates go through
+        // the warp's stage
         const uint4 gw0 = g < G ? group_words(grp, 0u, phase, kd) : make_uint4(0u, 0u, 0u, 0u);
-        uint32_t on = 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (m[k] > 0 && (int64_t)word_of(gw0, k) <= pre) on |= 1u << k;
-        const int cnt = __popc(on);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int wtot = __shfl_sync(kFull, incl, 31);
-        if (wtot > 0) {
-            unsigned long long cb = 0;
-            if (lane == 31) cb = atomicAdd((unsigned long long*)&st->cand_total, (unsigned long long)wtot);
-            cb = __shfl_sync(kFull, cb, 31);
-            int64_t pos = (int64_t)cb + incl - cnt;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (!((on >> k) & 1u)) continue;
-                if (pos < P.cand_cap)
-                    ((uint4*)P.cand)[pos] = make_uint4((uint32_t)(first + k), (uint32_t)seg, word_of(gw0, k),
-                                                       (uint32_t)phase << 31);
-                else
-                    set_error(st, DERR_CAND_CAPACITY);
-                ++pos;
-            }
-        }
+            cs.push(m[k] > 0 && (int64_t)word_of(gw0, k) <= pre,
+                    make_uint4((uint32_t)(first + k), (uint32_t)seg, word_of(gw0, k),
+                               cand_word(0, vre[k], vim[k], phase, non[k])),
+                    ctot, cdst, P.cand_cap, st, DERR_CAND_CAPACITY, lane);
         // second walkers: one more call; further walkers: the parent's calls
         const bool two = m[0] > 1 || m[1] > 1 || m[2] > 1 || m[3] > 1;
         if (__any_sync(kFull, two)) {
@@ -425,24 +433,29 @@ __global__ void __launch_bounds__(kWThreads) k_wide_spawn(StepParams P, WidePara
                         Wd = w == 1 ? word_of(gw1, k)
                                     : word_of(extra_words(rank, (uint32_t)((w - 2) >> 2), phase, kd), (int)((w - 2) & 3));
                     const bool on = w < mk && (int64_t)Wd <= pre;
-                    warp_append_cand(P, on,
-                                     make_uint4((uint32_t)(first + k), (uint32_t)seg, Wd, (uint32_t)w | ((uint32_t)phase << 31)),
-                                     lane);
+                    cs.push(on,
+                            make_uint4((uint32_t)(first + k), (uint32_t)seg, Wd,
+                                       cand_word(w, vre[k], vim[k], phase, non[k])),
+                            ctot, cdst, P.cand_cap, st, DERR_CAND_CAPACITY, lane);
                 }
             }
         }
     }
+    cs.flush(ctot, cdst, P.cand_cap, st, DERR_CAND_CAPACITY, lane);
 }
 
 // Candidates: the parent's exact column weight, the walker's full draw and,
 // if it spawns, its record.
 __global__ void __launch_bounds__(kWThreads, 3) k_wide_choose(StepParams P, WideParams W)
 {
+    __shared__ WSpawn s_sp[kWThreads / 32][kWStage];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const StepInfo inf = P.info[st->call_index];
     const int64_t total = min((int64_t)st->cand_total, P.cand_cap);
     const int lane = threadIdx.x & 31;
+    WarpStage<WSpawn, kWStage> ss{s_sp[threadIdx.x >> 5], 0};
+    unsigned long long* stot = (unsigned long long*)&st->spawn_total;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
         const int64_t i = base + lane;
@@ -450,15 +463,34 @@ __global__ void __launch_bounds__(kWThreads, 3) k_wide_choose(StepParams P, Wide
         bool sp = false;
         if (i < total) {
             const uint4 c = ((const uint4*)P.cand)[i];
-            const int phase = (int)(c.w >> 31);
+            const int comp = (int)((c.w >> 20) & 1u), phase = (int)((c.w >> 21) & 1u);
+            const int non = (int)((c.w >> 22) & 1u), sg = ((c.w >> 23) & 1u) ? 1 : -1;
             const int slot = phase ? (st->cur + 2) % 3 : st->cur;
-            WParent q;
-            WProg pr;
-            if (load_parent(P, inf, wpop(P, slot), P.segoff[slot], (int64_t)c.x, phase, &q, &pr))
-                sp = wide_walker(pr, q, (int64_t)(c.w & 0x7FFFFFFFu), c.z, &sr);
+            const int seg = (int)c.y;
+            const uint32_t rank = c.x - (uint32_t)__ldg(&P.segoff[slot][seg]);
+            const SegInfo si = P.seginfo[seg];
+            const u128 key = wkey(__ldg(&wpop(P, slot).key[c.x]));
+            const uint64_t x = (uint64_t)(key >> si.n), y = (uint64_t)key & ((1ull << si.n) - 1ull);
+            const WProg pr = wprog_at(prog_of(P, inf, si.inst, phase));
+            int64_t sre, sim;
+            const int64_t Pw = column_weight(pr, x, y, &sre, &sim);
+            if (Pw >= (1ll << 52)) {
+                set_error(st, DERR_DT_TOO_LARGE);
+            } else if ((int64_t)c.z <= ((Pw - 1) >> 20)) {
+                // the walker's full draw T = W << 20 | L [reading R3]
+                const int64_t T = walker_T(c.z, rank, c.w & kWJ20, comp, phase, P.kd[seg]);
+                u128 mask;
+                int chan;
+                int64_t v;
+                if (T < Pw && choose_destination(pr, x, y, sre, sim, T, &mask, &chan, &v)) {
+                    sp = true;
+                    sr = wide_record(key ^ mask, seg, comp, chan, v, sg, phase, non);
+                }
+            }
         }
-        warp_append(P, W, sp, sr, lane);
+        ss.push(sp, sr, stot, W.spawn, P.spawn_cap, st, DERR_SPAWN_CAPACITY, lane);
     }
+    ss.flush(stot, W.spawn, P.spawn_cap, st, DERR_SPAWN_CAPACITY, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1030,15 +1062,6 @@ __device__ __forceinline__ const WSpawn* sorted_spawns(const WideParams& W)
 
 // First index of [lo, hi) of a population slot whose key is >= k.
 __device__ __forceinline__ int64_t lower_bound_pop(const ulonglong2* a, int64_t lo, int64_t hi, u128 k)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (wkey(a[mid]) < k) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int64_t lower_bound_spawn(const WSpawn* a, int64_t lo, int64_t hi, u128 k)
 {
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
