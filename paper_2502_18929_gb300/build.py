@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "qmc_api.cu", "noalloc.cu", "learn.cu", "wide.cu"]
 CPP_SOURCES = ["term_compiler.cpp", "column_check.cpp"]
 HEADERS = ["kernels.h", "qmc_types.h", "term_compiler.h", "context.h", "column_eval.h", "tc_ops.h",
-           "device_common.h"]
+           "device_common.h", "wide.h"]
 
 
 def _nvcc() -> str:

@@ -19,6 +19,7 @@
 
 #include "../../include/qmc.h"
 #include "kernels.h"
+#include "wide.h"
 #include "qmc_types.h"
 #include "term_compiler.h"
 #include "context.h"

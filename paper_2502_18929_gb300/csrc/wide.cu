@@ -38,6 +38,7 @@
 #include "column_eval.h"
 #include "device_common.h"
 #include "kernels.h"
+#include "wide.h"
 
 namespace qmc {
 
