@@ -416,6 +416,23 @@ int grow_pop(qmc_ctx* ctx, int64_t need)
     return grow_merge_tiles(ctx);
 }
 
+// Host threads building column programs, over every context of the process:
+// concurrent step calls share the cores instead of taking up to 16 each.
+std::atomic<int> g_builders{0};
+
+// Builder threads for a call that wants `want`: what the process has left
+// (hardware threads less those building), at least one.
+int reserve_builders(int want)
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int cap = (int)(hw ? hw : 1);
+    int cur = g_builders.load();
+    for (;;) {
+        const int take = std::max(1, std::min(want, cap - cur));
+        if (g_builders.compare_exchange_weak(cur, cur + take)) return take;
+    }
+}
+
 // Step table and history of a qmc_step call of nsteps steps: device and
 // pinned staging capacity (before any of its steps is launched).
 int ensure_call_capacity(qmc_ctx* ctx, int64_t nsteps)
@@ -1449,19 +1466,21 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
     std::atomic<int64_t> next_job{0};
     std::mutex mu;
     std::condition_variable cv;
-    struct Pool {   // joins the builders on every exit path
+    struct Pool {   // joins the builders on every exit path and returns them to the process
         std::vector<std::thread> th;
         std::atomic<int64_t>* next;
         int64_t nj;
+        int reserved;
         ~Pool()
         {
             next->store(nj);
             for (auto& t : th) t.join();
+            g_builders -= reserved;
         }
-    } pool{{}, &next_job, nj};
+    } pool{{}, &next_job, nj, 0};
     {
-        const unsigned hw = std::thread::hardware_concurrency();
-        const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)16, nj}));
+        const int nthr = reserve_builders((int)std::min<int64_t>(16, nj));
+        pool.reserved = nthr;
         for (int w = 0; w < nthr; ++w)
             pool.th.emplace_back([&]() {
                 for (;;) {
