@@ -2,10 +2,13 @@
 // (arXiv:2502.18929: the method of the 64-bit step, same random stream).
 //
 //   k_wide_prologue     per-step Philox keys, counter resets
+//   k_wide_abound       where each bucket of the spawn sort starts in N(t)
 //   k_wide_spawn        spawning [End Matter, spawn step] of parents with few
-//                       walkers, one thread per parent, a warp's spawns
-//                       appended together; heavy parents become work items
-//   k_wide_heavy        one warp per chunk of a heavy parent's walkers
+//                       walkers: one thread per rank group of four parents,
+//                       walkers that pass the prefilter become candidates
+//   k_wide_choose       candidates: exact column weight, full draw, spawn record
+//   k_wide_heavy        one CTA per chunk of a heavy parent's walkers, the
+//                       column laid out once as bins of the draw
 //   k_wide_bhist ..
 //   k_wide_bsort_big    bucket sort of the spawns by (vector, key): bucket
 //                       counts, their prefix, one counting pass, windows of
@@ -108,48 +111,6 @@ __device__ __forceinline__ const uint8_t* prog_of(const StepParams& P, const Ste
     return P.progs + tab[2 * inst + phase];
 }
 
-// One parent as its walkers see it.
-struct WParent {
-    uint64_t x, y;
-    u128 key;
-    int32_t re, im;
-    uint32_t rank;
-    int seg, phase;
-    int64_t Pw, sre, sim;
-    int noninit;
-    uint2 kd;
-};
-
-// Parent i of a slot with its column weight evaluated.  Returns false (after
-// raising the error) when its spawn probability reaches 1.
-__device__ bool load_parent(const StepParams& P, const StepInfo& inf, const WPop& pop, const int64_t* off, int64_t i,
-                            int phase, WParent* q, WProg* pr)
-{
-    const WRec r = wload(pop, i);
-    const int seg = seg_of(off, P.nseg, i);
-    const SegInfo si = P.seginfo[seg];
-    const int n = si.n;
-    q->key = wkey(r);
-    q->x = (uint64_t)(q->key >> n);
-    q->y = (uint64_t)q->key & ((1ull << n) - 1ull);
-    q->re = r.re;
-    q->im = r.im;
-    q->rank = (uint32_t)(i - off[seg]);
-    q->seg = seg;
-    q->phase = phase;
-    q->kd = P.kd[seg];
-    *pr = wprog_at(prog_of(P, inf, si.inst, phase));
-    q->Pw = column_weight(*pr, q->x, q->y, &q->sre, &q->sim);
-    const int64_t m = iabs64(r.re) + iabs64(r.im);
-    const int64_t init_min = P.inst[si.inst].init_min;
-    q->noninit = (init_min > 0 && m < init_min) ? 1 : 0;
-    if (q->Pw >= (1ll << 52)) {
-        set_error(P.st, DERR_DT_TOO_LARGE);
-        return false;
-    }
-    return true;
-}
-
 // The spawn record of a walker of component comp (0 real, 1 imaginary) whose
 // parent's value has sign sg there, onto dest through channel chan of an
 // element of sign v, with the paper's sign rule [End Matter, spawn step]: the
@@ -169,14 +130,6 @@ __device__ __forceinline__ WSpawn wide_record(u128 dest, int seg, int comp, int 
     r.meta = ((uint32_t)seg << 2) | ((uint32_t)target << 1) | (uint32_t)noninit;
     r.val = val;
     return r;
-}
-
-// The 32-bit word of walker w (w = 0, 1: the rank group's call of level w;
-// w >= 2: the parent's call (w - 2) / 4).
-__device__ __forceinline__ uint32_t walker_word(const WParent& q, int64_t w)
-{
-    if (w <= 1) return word_of(group_words(q.rank >> 2, (uint32_t)w, q.phase, q.kd), (int)(q.rank & 3u));
-    return word_of(extra_words(q.rank, (uint32_t)((w - 2) >> 2), q.phase, q.kd), (int)((w - 2) & 3));
 }
 
 // Records a warp appends to a global array (dst, capacity cap, counter
@@ -497,59 +450,133 @@ __global__ void __launch_bounds__(kWThreads, 3) k_wide_choose(StepParams P, Wide
 // ---------------------------------------------------------------------------
 // Heavy parents: one CTA per work item.  Item c of a parent covers the
 // walkers 2 + 4 b + (0..3) of its extra calls b in [c kWChunk, (c + 1)
-// kWChunk), item 0 also the walkers 0 and 1; the spawned walkers are counted
-// per (destination, channel, walker component) in shared memory and leave as
-// one record each (the merge adds records, so the populations are those of
-// one record per walker).
+// kWChunk), item 0 also the walkers 0 and 1.  The parent's column is laid out
+// once per item in shared memory: one thread evaluates its weight P and
+// diagonal element, all threads the destination entries' elements, whose
+// |Re| and |Im| in the canonical order are the bins of the walkers' draw T
+// over [0, P) (the order choose_destination walks), with a table of the first
+// bin of each 2^s-wide slice of [0, P).  A spawned walker finds its bin with
+// one or two reads; the walkers are counted per (bin, walker component) and
+// leave as one record per nonzero count (the merge adds records, so the
+// populations are those of one record per walker).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWThreads) k_wide_heavy(StepParams P, WideParams W)
 {
-    __shared__ int hist[4 * kMaxEntries];
+    __shared__ int64_t cum[2 * kMaxEntries];   // bin widths, then their inclusive prefix
+    __shared__ int hist[4 * kMaxEntries];      // spawned walkers per (bin, component)
+    __shared__ int8_t sgnv[2 * kMaxEntries];   // sign of each bin's element
+    __shared__ uint16_t sidx[1025];            // first bin of each slice of [0, P)
+    __shared__ int64_t s_col[3];               // P and the diagonal element's Re, Im
+    __shared__ int64_t warp_tot[kWThreads / 32];
     DevState* st = P.st;
     if (cta_error(st)) return;
     const StepInfo inf = P.info[st->call_index];
     const int64_t items = min((int64_t)st->heavy_total, P.heavy_cap);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < 4 * kMaxEntries; e += blockDim.x) hist[e] = 0;
     __syncthreads();
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const HeavyItem h = P.heavy[it];
         const int slot = h.phase ? (st->cur + 2) % 3 : st->cur;
-        WParent q;
-        WProg pr;
-        const bool ok = load_parent(P, inf, wpop(P, slot), P.segoff[slot], h.parent, h.phase, &q, &pr);
-        const int ne = pr.h->n_entry;
-        if (ok && ne <= kMaxEntries) {
-            const int64_t m = iabs64(q.re) + iabs64(q.im);
-            const int64_t are = iabs64(q.re);
-            auto walker = [&](int64_t w, uint32_t Wd) {
-                if ((int64_t)Wd > ((q.Pw - 1) >> 20)) return;
-                const int comp = w < are ? 0 : 1;
-                const uint32_t j = (uint32_t)(comp ? w - are : w);
-                const int64_t T = walker_T(Wd, q.rank, j, comp, q.phase, q.kd);
-                if (T >= q.Pw) return;
-                u128 mask;
-                int chan;
-                int64_t v;
-                if (!choose_destination(pr, q.x, q.y, q.sre, q.sim, T, &mask, &chan, &v)) return;
-                const int e = find_entry(pr, mask);
-                if (e >= 0) atomicAdd(&hist[(2 * e + chan) * 2 + comp], 1);
-            };
-            if (h.chunk == 0 && tid < 2 && tid < m) walker(tid, walker_word(q, tid));
-            const int64_t nb = (m - 2 + 3) / 4;
-            const int64_t b0 = (int64_t)h.chunk * kWChunk, b1 = min(nb, b0 + kWChunk);
-            for (int64_t b = b0 + tid; b < b1; b += blockDim.x) {
-                const uint4 o = extra_words(q.rank, (uint32_t)b, h.phase, q.kd);
+        const int seg = h.seg;
+        const SegInfo si = P.seginfo[seg];
+        const WRec r = wload(wpop(P, slot), h.parent);
+        const u128 key = wkey(r);
+        const uint64_t x = (uint64_t)(key >> si.n), y = (uint64_t)key & ((1ull << si.n) - 1ull);
+        const WProg pr = wprog_at(prog_of(P, inf, si.inst, h.phase));
+        const int ne = pr.h->n_entry, nb = 2 * ne;
+        if (tid == 0) {
+            int64_t a, b;
+            s_col[0] = column_weight(pr, x, y, &a, &b);
+            s_col[1] = a;
+            s_col[2] = b;
+        }
+        __syncthreads();
+        const int64_t Pw = s_col[0];
+        if (Pw >= (1ll << 52) || ne > kMaxEntries) {   // the same in every thread
+            if (tid == 0) set_error(st, Pw >= (1ll << 52) ? DERR_DT_TOO_LARGE : DERR_TILE_CAPACITY);
+            return;
+        }
+        for (int e = tid; e < ne; e += blockDim.x) {
+            int64_t vr, vi;
+            entry_value(pr, pr.ent[e], x, y, s_col[1], s_col[2], &vr, &vi);
+            cum[2 * e] = iabs64(vr);
+            cum[2 * e + 1] = iabs64(vi);
+            sgnv[2 * e] = vr > 0 ? 1 : -1;
+            sgnv[2 * e + 1] = vi > 0 ? 1 : -1;
+        }
+        __syncthreads();
+        {   // inclusive prefix of the bin widths, in place (blocked per thread, then across threads)
+            const int per = (nb + kWThreads - 1) / kWThreads;
+            const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
+            int64_t acc = 0;
+            for (int b = b0; b < b1; ++b) acc += cum[b];
+            int64_t incl = acc;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int64_t w = 2 + 4 * b + k;
-                    if (w < m) walker(w, word_of(o, k));
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) warp_tot[warp] = incl;
+            __syncthreads();
+            int64_t run = incl - acc;
+            for (int q = 0; q < warp; ++q) run += warp_tot[q];
+            for (int b = b0; b < b1; ++b) {
+                run += cum[b];
+                cum[b] = run;
+            }
+        }
+        __syncthreads();
+        // first bin of each 2^ish-wide slice of [0, P): about eight slices per bin, at most 1024
+        int ish = 0;
+        if (nb > 0) {
+            const int64_t slices = nb < 128 ? 8 * nb : 1024;
+            while ((Pw >> ish) >= slices) ++ish;
+            const int nbk = (int)(Pw >> ish) + 1;
+            for (int k = tid; k < nbk; k += blockDim.x) {
+                const int64_t t0 = (int64_t)k << ish;
+                int lo = 0, hi = nb - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cum[mid] > t0) hi = mid; else lo = mid + 1;
                 }
+                sidx[k] = (uint16_t)lo;
+            }
+        }
+        __syncthreads();
+        const int64_t are = iabs64(r.re), m = are + iabs64(r.im);
+        const uint32_t rank = (uint32_t)(h.parent - P.segoff[slot][seg]);
+        const uint2 kd = P.kd[seg];
+        const int64_t pre = (Pw - 1) >> 20;
+        // walker w with its 32-bit word W [reading R3]: the prefilter, the full
+        // draw T = W << 20 | L, T < P, its bin
+        auto walker = [&](int64_t w, uint32_t Wd) {
+            if ((int64_t)Wd > pre) return;
+            const int comp = w < are ? 0 : 1;
+            const uint32_t j = (uint32_t)(comp ? w - are : w);
+            const int64_t T = walker_T(Wd, rank, j, comp, h.phase, kd);
+            if (T >= Pw) return;
+            int lo = sidx[T >> ish];   // first bin with cum > T
+            while (lo < nb - 1 && cum[lo] <= T) ++lo;
+            atomicAdd(&hist[2 * lo + comp], 1);
+        };
+        if (h.chunk == 0 && tid < 2 && tid < m)
+            walker(tid, word_of(group_words(rank >> 2, (uint32_t)tid, h.phase, kd), (int)(rank & 3u)));
+        const int64_t ncall = (m - 2 + 3) / 4;
+        const int64_t c0 = (int64_t)h.chunk * kWChunk, c1 = min(ncall, c0 + kWChunk);
+        for (int64_t b = c0 + tid; b < c1; b += blockDim.x) {
+            const uint4 o = extra_words(rank, (uint32_t)b, h.phase, kd);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t w = 2 + 4 * b + k;
+                if (w < m) walker(w, word_of(o, k));
             }
         }
         __syncthreads();
         // one record per nonzero count, in rounds of the block's threads
-        const int nslots = ok ? 4 * min(ne, kMaxEntries) : 0;
+        const int64_t init_min = P.inst[si.inst].init_min;
+        const int noninit = (init_min > 0 && m < init_min) ? 1 : 0;
+        const int nslots = 2 * nb;
         for (int base = 0; base < nslots; base += blockDim.x) {
             const int idx = base + tid;
             WSpawn sr;
@@ -558,21 +585,11 @@ __global__ void __launch_bounds__(kWThreads) k_wide_heavy(StepParams P, WidePara
                 const int cnt = hist[idx];
                 if (cnt) {
                     hist[idx] = 0;
-                    const int e = idx >> 2, chan = (idx >> 1) & 1, comp = idx & 1;
-                    int64_t vr, vi;
-                    entry_value(pr, pr.ent[e], q.x, q.y, q.sre, q.sim, &vr, &vi);
-                    const int64_t v = chan ? vi : vr;
-                    const int sg = comp == 0 ? (q.re > 0 ? 1 : -1) : (q.im > 0 ? 1 : -1);
-                    const int sgn = (q.phase ? -1 : 1) * sg * (v > 0 ? 1 : -1);
-                    int target, val;
-                    if (chan == 0) { target = comp; val = sgn; }
-                    else if (comp == 0) { target = 1; val = sgn; }
-                    else { target = 0; val = -sgn; }
-                    const u128 dest = q.key ^ pr.ent[e].mask_key;
-                    sr.lo = (uint64_t)dest;
-                    sr.hi = (uint64_t)(dest >> 64);
-                    sr.meta = ((uint32_t)q.seg << 2) | ((uint32_t)target << 1) | (uint32_t)q.noninit;
-                    sr.val = val * cnt;
+                    const int bin = idx >> 1, comp = idx & 1;
+                    const int sg = comp == 0 ? (r.re > 0 ? 1 : -1) : (r.im > 0 ? 1 : -1);
+                    sr = wide_record(key ^ pr.ent[bin >> 1].mask_key, seg, comp, bin & 1, sgnv[bin], sg, h.phase,
+                                     noninit);
+                    sr.val *= cnt;
                     sp = true;
                 }
             }
