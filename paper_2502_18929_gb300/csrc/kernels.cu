@@ -2519,6 +2519,7 @@ __device__ __forceinline__ int merge_walk(const uint4* buf, const MTileG& m, con
             *dre += vr;
             *dim += vi;
             // <Z_q> on the diagonal: Re N_xx of the states with bit q of x set
+            // (zrow: the tile's sums in shared memory)
             for (uint32_t xb = (uint32_t)(rkey >> n); xb; xb &= xb - 1u)
                 atomicAdd((unsigned long long*)&zrow[__ffs(xb) - 1], (unsigned long long)vr);
         }
@@ -2562,22 +2563,49 @@ __device__ __forceinline__ int merge_walk(const uint4* buf, const MTileG& m, con
         add_item(idx, takeA);
     }
     if (open) {
-        // finish the last run: later items of this tile, then spawns past the tile
-        for (;;) {
-            bool takeA;
-            if (ia >= na && ib >= nb) break;
-            if (ia >= na) takeA = false;
-            else if (ib >= nb) takeA = true;
-            else takeA = it_key(buf, ia) <= it_key(buf, na + ib);
-            const int idx = takeA ? ia : na + ib;
-            if (it_key(buf, idx) != rkey) break;
-            if (takeA) ++ia; else ++ib;
-            add_item(idx, takeA);
+        // finish the last run: later items of this tile, then spawns past the
+        // tile.  Every item before the run's next one has a key <= rkey, and
+        // N(t) sorts first on equal keys, so an N(t) record of key rkey would
+        // come first, then the tile's spawns of key rkey, a stretch from ib
+        // (they ascend from rkey): its end by a galloping search, then a sum
+        // over the stretch whose loads do not wait on one another (long runs
+        // come from concentrated spawns).
+        if (ia < na && it_key(buf, ia) == rkey) {
+            add_item(ia, true);
+            ++ia;
+        }
+        {
+            int lo = ib, hi = ib, step = 1;   // the tile's spawns [ib, lo) carry rkey
+            while (hi < nb && it_key(buf, na + hi) == rkey) {
+                lo = hi + 1;
+                hi = min(nb, ib + 2 * step - 1);
+                step *= 2;
+            }
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (it_key(buf, na + mid) == rkey) lo = mid + 1; else hi = mid;
+            }
+            for (int j = ib; j < lo; ++j) add_item(na + j, false);
+            ib = lo;
         }
         if (ia >= na && ib >= nb) {
-            for (int64_t jb = m.b_glob + nb; jb < m.b_seg_end; ++jb) {
+            // the run's spawns past the tile (their keys ascend from rkey): the
+            // run's end by a galloping search, then a sum over that range whose
+            // loads do not wait on one another (runs of thousands of records
+            // come from heavy parents' chunks)
+            const int64_t j0 = m.b_glob + nb, j1 = m.b_seg_end;
+            int64_t lo = j0, hi = j0, step = 1;   // every key in [j0, lo) is rkey
+            while (hi < j1 && sorted[hi].key == rkey) {
+                lo = hi + 1;
+                hi = min(j1, j0 + 2 * step - 1);
+                step *= 2;
+            }
+            while (lo < hi) {   // the first index in [lo, hi) whose key is above rkey
+                const int64_t mid = (lo + hi) >> 1;
+                if (sorted[mid].key == rkey) lo = mid + 1; else hi = mid;
+            }
+            for (int64_t jb = j0; jb < lo; ++jb) {
                 const SRec r = sorted[jb];
-                if (r.key != rkey) break;
                 const long long v = r.val;
                 if (r.meta & 1u) { if (r.meta & 2u) nim += v; else nre += v; }
                 else { if (r.meta & 2u) sim += v; else sre += v; }
@@ -2636,6 +2664,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
     __shared__ int s_wcount[2][kThreads / 32];
     __shared__ long long s_red[2][3][kThreads / 32];
     __shared__ int s_abort;
+    __shared__ long long s_z[32];   // the tile's <Z_q> sums, added to its vector's once per tile
     DevState* st = P.st;
     if (cta_error(st)) return;
     const int cur = st->cur, nxt = (cur + 1) % 3;
@@ -2747,6 +2776,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
     }
 
     // merging threads
+    if (tid < 32) s_z[tid] = 0ll;
+    merge_bar();
     for (int k = 0;; ++k) {
         const int s = k % kMergeStages, h = k & 1;
         const bool ok = mbar_wait(&full[s], (uint32_t)((k / kMergeStages) & 1), st, 5u, k);
@@ -2761,7 +2792,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
             const uint32_t n = (uint32_t)P.seginfo[seg].n;   // the tile's vector's qubit count
             const uint32_t ymask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
             nout = merge_walk(inbuf + s * kMergeTile, m, sorted, raw + tid * kMergeItems, st, n, ymask, &my_ntot,
-                              &my_dre, &my_dim, P.zacc + 32 * (int64_t)seg);
+                              &my_dre, &my_dim, s_z);
         }
         // block scan of run counts, block sums of the statistics
         int incl = nout;
@@ -2790,6 +2821,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(StepParams P)
             __syncwarp();
             if (lane == 0) mbar_arrive(&ready[s]);
             break;
+        }
+        if (tid < 32) {   // the tile's <Z_q> sums to its vector's (the walks are done)
+            const long long z = s_z[tid];
+            if (z) {
+                atomicAdd((unsigned long long*)&P.zacc[32 * (int64_t)seg + tid], (unsigned long long)z);
+                s_z[tid] = 0ll;
+            }
         }
         int woff = 0, tile_count = 0;
 #pragma unroll

@@ -1165,10 +1165,25 @@ __global__ void __launch_bounds__(kWThreads) k_wide_runs(StepParams P, WideParam
             if (!head) {
                 W.flag_u[i] = 0;
             } else {
-                int64_t ire = 0, iim = 0, are = 0, aim = 0;
-                for (int64_t j = i; j < S; ++j) {
+                // the run's end by a galloping search (the spawns after it hold
+                // larger (vector, key)), then a sum over that range
+                auto same = [&](int64_t j) {
                     const WSpawn q = wsload(sp, j);
-                    if ((q.meta >> 2) != seg || wkey(q) != k) break;
+                    return (q.meta >> 2) == seg && wkey(q) == k;
+                };
+                int64_t rend = i + 1, rhi = i + 1, step = 1;   // [i, rend) is the run so far
+                while (rhi < S && same(rhi)) {
+                    rend = rhi + 1;
+                    rhi = min(S, i + 1 + 2 * step - 1);
+                    step *= 2;
+                }
+                while (rend < rhi) {
+                    const int64_t mid = (rend + rhi) >> 1;
+                    if (same(mid)) rend = mid + 1; else rhi = mid;
+                }
+                int64_t ire = 0, iim = 0, are = 0, aim = 0;
+                for (int64_t j = i; j < rend; ++j) {
+                    const WSpawn q = wsload(sp, j);
                     const int64_t v = q.val;
                     const bool to_im = (q.meta >> 1) & 1u;
                     if (to_im) aim += v; else are += v;
