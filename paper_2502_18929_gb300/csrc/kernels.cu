@@ -2060,18 +2060,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_scatter(StepParams P, int 
 // Spawn sort by buckets.  The sort key is (vector, key); its top bucket_bits
 // bits (all vector bits and the top bucket_kb key bits) pick one of up to
 // 2^kBucketBits buckets.  One counting pass places every spawn record in its
-// bucket (order inside a bucket arbitrary).  Buckets come in sort-key order,
-// so any run of whole buckets sorted by key is in final order: the records
-// are cut into windows of whole buckets, window k starting at the bucket that
-// holds record k * kSortWin, and each window is sorted in shared memory (a
-// warp for up to kSmallBucket records, a CTA for up to kBigBucket).  When the
-// whole sort key fits the bucket digit the counting pass alone sorts.  A
-// bucket too large for a window sends the step to the LSD radix sort instead
-// (st->sort_fallback).
+// bucket (order inside a bucket arbitrary).  Buckets come in sort-key order
+// and each holds one vector, so sorting every bucket by key finishes the
+// sort: a lane for a bucket of up to kLaneBucket records (insertion sort in
+// place), a CTA for one of up to kBigBucket.  When the whole sort key fits
+// the bucket digit the counting pass alone sorts.  A bucket too large for a
+// CTA sends the step to the LSD radix sort instead (st->sort_fallback).
 // ---------------------------------------------------------------------------
-constexpr int kSmallBucket = 256;   // records a warp sorts
+constexpr int kLaneBucket = 32;     // records a lane sorts
 constexpr int kBigBucket = 4096;    // records a CTA sorts
-constexpr int kSortWin = 224;       // sort windows: whole buckets from every kSortWin-th record
 
 __device__ __forceinline__ uint32_t bucket_of(const SRec& r, const StepParams& P)
 {
@@ -2094,7 +2091,7 @@ __global__ void __launch_bounds__(kThreads) k_bucket_hist(StepParams P)
 
 // Exclusive scan of the bucket sizes into bucket cursors: 1024 buckets per
 // CTA, CTAs placed in ticket order by a decoupled look-back; decides between
-// the bucket sort and the LSD fallback.
+// the bucket sort and the LSD fallback (a bucket above kBigBucket records).
 __global__ void __launch_bounds__(1024) k_bucket_scan(StepParams P)
 {
     __shared__ uint32_t wsum[32];
@@ -2141,12 +2138,9 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(StepParams P)
     }
     __syncthreads();
     if (b < nb) {
-        const uint32_t start = (uint32_t)s_excl + base + incl - c;
-        P.bucket[b] = start;
-        // window k of the bucket sorts starts at the bucket holding position k * kSortWin
-        for (uint32_t k = (start + kSortWin - 1) / kSortWin; k * kSortWin < start + c; ++k) P.win[k] = start;
+        P.bucket[b] = (uint32_t)s_excl + base + incl - c;
     }
-    if (tid == 0 && P.sort_mode == 1 && gmax > (uint32_t)(kBigBucket - kSortWin)) {
+    if (tid == 0 && P.sort_mode == 1 && gmax > (uint32_t)kBigBucket) {
         // a bucket too large for the bucket sorts: LSD radix sort for this step
         st->sort_fallback = 1u;
         st->sort_final = (uint32_t)((P.key_passes + P.seg_passes) & 1);
@@ -2203,94 +2197,41 @@ __device__ __forceinline__ int pow2_at_least(int n)
     return N;
 }
 
-constexpr int kSmallSortSmem = (kThreads / 32) * kSmallBucket * (16 + 8 + 4);
-
-// Bounds of sort window k: [win[k], win[k + 1]), the last one ending at S.
-__device__ __forceinline__ void window_bounds(const StepParams& P, int64_t k, int64_t nwin, uint32_t S,
-                                              uint32_t* lo, uint32_t* hi)
-{
-    *lo = P.win[k];
-    *hi = k + 1 < nwin ? P.win[k + 1] : S;
-}
-
-// Sort windows of up to kSmallBucket records, one warp each, in place; larger
-// windows go to the list of k_bucket_sort_big.
+// Buckets of up to kLaneBucket records, one lane each: insertion sort by key
+// in place (a bucket holds one vector; its records sit in L1 after the first
+// read).  Larger buckets go to the list of k_bucket_sort_big.  After the
+// counting pass bucket[b] is the end of bucket b.
 __global__ void __launch_bounds__(kThreads) k_bucket_sort_small(StepParams P)
 {
-    extern __shared__ __align__(16) uint8_t ssm[];
     DevState* st = P.st;
     if (read_error(st) || st->sort_fallback || P.sort_mode != 1) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4* Rw = (uint4*)ssm + warp * kSmallBucket;
-    uint64_t* Kw = (uint64_t*)(ssm + (kThreads / 32) * kSmallBucket * 16) + warp * kSmallBucket;
-    uint32_t* Gw = (uint32_t*)(ssm + (kThreads / 32) * kSmallBucket * 24) + warp * kSmallBucket;
-    const uint32_t S = (uint32_t)min(st->spawn_total, P.spawn_cap);
-    const int64_t nwin = ((int64_t)S + kSortWin - 1) / kSortWin;
-    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
     uint4* A = (uint4*)P.spawn_alt;
-    for (int64_t k = (int64_t)blockIdx.x * (kThreads / 32) + warp; k < nwin; k += nwarps) {
-        uint32_t start, end;
-        window_bounds(P, k, nwin, S, &start, &end);
+    const int nb = 1 << P.bucket_bits;
+    for (int b = blockIdx.x * kThreads + threadIdx.x; b < nb; b += gridDim.x * kThreads) {
+        const uint32_t end = P.bucket[b], start = b ? P.bucket[b - 1] : 0u;
         const int n = (int)(end - start);
         if (n <= 1) continue;
-        if (n > kSmallBucket) {
-            if (lane == 0) {
-                const uint32_t q = atomicAdd(&st->big_windows, 1u);
-                P.big_list[q] = (uint32_t)k;
-            }
+        if (n > kLaneBucket) {
+            P.big_list[atomicAdd(&st->big_windows, 1u)] = (uint32_t)b;
             continue;
         }
-        if (n <= 32) {
-            // one record per lane, bitonic network over the lanes
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (lane < n) v = A[start + lane];
-            uint64_t key = lane < n ? (((uint64_t)v.y << 32) | v.x) : ~0ull;
-            uint32_t seg = lane < n ? (v.z >> 2) : 0xFFFFFFFFu;
-            int idx = lane;
-#pragma unroll
-            for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    const uint64_t ok = __shfl_xor_sync(kFull, key, j);
-                    const uint32_t os = __shfl_xor_sync(kFull, seg, j);
-                    const int oi = __shfl_xor_sync(kFull, idx, j);
-                    const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
-                    const bool lt = os != seg ? os < seg : ok < key;
-                    const bool gt = os != seg ? os > seg : ok > key;
-                    if (keep_min ? lt : gt) {
-                        key = ok;
-                        seg = os;
-                        idx = oi;
-                    }
-                }
+        for (int i = 1; i < n; ++i) {
+            const uint4 r = A[start + i];
+            const uint64_t k = ((uint64_t)r.y << 32) | r.x;
+            int j = i - 1;
+            for (; j >= 0; --j) {
+                const uint4 q = A[start + j];
+                if ((((uint64_t)q.y << 32) | q.x) <= k) break;
+                A[start + j + 1] = q;
             }
-            const uint4 r = make_uint4(__shfl_sync(kFull, v.x, idx), __shfl_sync(kFull, v.y, idx),
-                                       __shfl_sync(kFull, v.z, idx), __shfl_sync(kFull, v.w, idx));
-            if (lane < n) A[start + lane] = r;
-            continue;
+            A[start + j + 1] = r;
         }
-        const int N = pow2_at_least(n);
-        for (int j = lane; j < N; j += 32) {
-            if (j < n) {
-                const uint4 v = A[start + j];
-                Rw[j] = v;
-                Kw[j] = ((uint64_t)v.y << 32) | v.x;
-                Gw[j] = ((v.z >> 2) << 12) | (uint32_t)j;
-            } else {
-                Kw[j] = ~0ull;
-                Gw[j] = 0xFFFFF000u | (uint32_t)j;
-            }
-        }
-        __syncwarp();
-        bitonic_sort(Kw, Gw, N, lane, 32, [] { __syncwarp(); });
-        for (int j = lane; j < n; j += 32) A[start + j] = Rw[Gw[j] & 0xFFFu];
-        __syncwarp();
     }
 }
 
 constexpr int kBigSortSmem = kBigBucket * (16 + 8 + 4);
 
-// Windows of kSmallBucket + 1 .. kBigBucket records (listed by
+// Buckets of kLaneBucket + 1 .. kBigBucket records (listed by
 // k_bucket_sort_small), one CTA each.
 __global__ void __launch_bounds__(kThreads) k_bucket_sort_big(StepParams P)
 {
@@ -2301,13 +2242,11 @@ __global__ void __launch_bounds__(kThreads) k_bucket_sort_big(StepParams P)
     DevState* st = P.st;
     if (cta_error(st) || st->sort_fallback || P.sort_mode != 1) return;
     const int tid = threadIdx.x;
-    const uint32_t S = (uint32_t)min(st->spawn_total, P.spawn_cap);
-    const int64_t nwin = ((int64_t)S + kSortWin - 1) / kSortWin;
     const uint32_t nbig = st->big_windows;
     uint4* A = (uint4*)P.spawn_alt;
     for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
-        uint32_t start, end;
-        window_bounds(P, (int64_t)P.big_list[q], nwin, S, &start, &end);
+        const uint32_t bk = P.big_list[q];
+        const uint32_t end = P.bucket[bk], start = bk ? P.bucket[bk - 1] : 0u;
         const int n = (int)(end - start);
         if (n > kBigBucket) {   // excluded by the fallback rule
             if (tid == 0) set_error(st, DERR_TILE_CAPACITY);
@@ -3446,7 +3385,6 @@ void configure_kernels()
 {
     cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kMergeSmem);
     cudaFuncSetAttribute(k_spawn_draw, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrawSmem);
-    cudaFuncSetAttribute(k_bucket_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSortSmem);
     cudaFuncSetAttribute(k_bucket_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSortSmem);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -3458,7 +3396,7 @@ void configure_kernels()
     g_grid_heavy_learned = resident((const void*)k_spawn_heavy_learned, 0, sms);
     g_grid_sort = resident((const void*)k_sort_scatter, 0, sms);
     g_grid_merge = resident((const void*)k_merge, kMergeSmem, sms, kMergeThreads);
-    g_grid_bsmall = resident((const void*)k_bucket_sort_small, kSmallSortSmem, sms);
+    g_grid_bsmall = resident((const void*)k_bucket_sort_small, 0, sms);
     g_grid_bbig = resident((const void*)k_bucket_sort_big, kBigSortSmem, sms);
     g_grid_misc = 2 * sms;
     // tensor-core proposal: sized for the largest network (64 hidden, 256 outputs, 80 inputs)
@@ -3522,7 +3460,7 @@ void launch_step(const StepParams& P, int grid, cudaStream_t stream, cudaEvent_t
         k_bucket_scatter<<<cap(g_grid_misc), kThreads, 0, stream>>>(P);
         mark(7);
         if (P.sort_mode == 1) {
-            k_bucket_sort_small<<<cap(g_grid_bsmall), kThreads, kSmallSortSmem, stream>>>(P);
+            k_bucket_sort_small<<<cap(g_grid_bsmall), kThreads, 0, stream>>>(P);
             k_bucket_sort_big<<<cap(g_grid_bbig), kThreads, kBigSortSmem, stream>>>(P);
         }
         mark(8);

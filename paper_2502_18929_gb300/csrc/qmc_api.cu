@@ -331,9 +331,8 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
     }
     if ((rc = dalloc(ctx, &ctx->d_spawn, cap)) != QMC_OK) return rc;
     if ((rc = dalloc(ctx, &ctx->d_spawn_alt, cap)) != QMC_OK) return rc;
-    // sort windows: one per 224 spawn records (the bucket sort's window length)
-    if ((rc = dalloc(ctx, &ctx->d_win, cap / 224 + 2)) != QMC_OK) return rc;
-    if ((rc = dalloc(ctx, &ctx->d_big_list, cap / 224 + 2)) != QMC_OK) return rc;
+    // buckets of more than 32 records, sorted by a CTA each: at most one per 33 spawn records
+    if ((rc = dalloc(ctx, &ctx->d_big_list, cap / 32 + 2)) != QMC_OK) return rc;
     ctx->spawn_cap = cap;
     ctx->sort_tiles_cap = (cap + kSortTile - 1) / kSortTile + 1;
     if ((rc = dalloc(ctx, &ctx->d_sort_status, ctx->sort_tiles_cap * 256)) != QMC_OK) return rc;
