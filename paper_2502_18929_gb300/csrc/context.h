@@ -77,7 +77,6 @@ struct qmc_ctx {
     SpawnCand* d_cand = nullptr;
     uint32_t* d_bucket = nullptr;
     unsigned long long* d_bscan_status = nullptr;
-    uint32_t* d_win = nullptr;
     uint32_t* d_big_list = nullptr;
     int64_t cand_cap = 0;
     HeavyItem* d_heavy = nullptr;
@@ -132,6 +131,9 @@ struct qmc_ctx {
     unsigned long long* d_wmtile = nullptr;
     longlong2* d_wmbase = nullptr;
     int64_t* d_wabound = nullptr;
+    uint32_t* d_wwin = nullptr;
+    uint32_t* d_wbig = nullptr;
+    uint32_t* d_wnbig = nullptr;
     int64_t wmtiles_cap = 0;
     int64_t* d_wscan_a = nullptr;
     int64_t* d_wpart = nullptr;

@@ -107,8 +107,7 @@ struct StepParams {
     uint32_t spin_limit;  // polls of another CTA's look-back word before a wait gives up (0: none)
     uint32_t* bucket;     // 2^bucket_bits bucket counters / cursors
     unsigned long long* bscan_status; // look-back words of the bucket scan, 2^(kBucketBits - 10)
-    uint32_t* win;        // sort window starts of the wide step's bucket sort, one per 224 spawn records
-    uint32_t* big_list;   // buckets (64-bit step) or sort windows (wide step) too large for a lane or warp
+    uint32_t* big_list;   // buckets of the spawn sort too large for a lane
     const SegInfo* seginfo;   // per segment
     const InstInfo* inst;     // per instance
     int ninst;

@@ -213,7 +213,6 @@ StepParams params(qmc_ctx* c)
         P.sort_mode = (P.bucket_bits > kBucketBits || P.seg_bits > 19) ? 0 : (P.bucket_bits == total ? 2 : 1);
         P.bucket = c->d_bucket;
         P.bscan_status = c->d_bscan_status;
-        P.win = c->d_win;
         P.big_list = c->d_big_list;
     }
     P.seginfo = c->d_seginfo;
@@ -253,6 +252,9 @@ WideParams wparams(qmc_ctx* c)
     W.mbase = c->d_wmbase;
     W.mtiles_cap = c->wmtiles_cap;
     W.abound = c->d_wabound;
+    W.win = c->d_wwin;
+    W.big_list = c->d_wbig;
+    W.nbig = c->d_wnbig;
     W.scan_a = c->d_wscan_a;
     W.part = c->d_wpart;
     W.part_cap = c->wpart_cap;
@@ -322,9 +324,9 @@ int grow_spawn(qmc_ctx* ctx, int64_t need)
             return rc;
         ctx->wtiles_cap = (cap + kWTile - 1) / kWTile + 1;
         if ((rc = dalloc(ctx, &ctx->d_wtile, ctx->wtiles_cap * 256)) != QMC_OK) return rc;
-        // bucket sort windows: one per 224 spawn records
-        if ((rc = dalloc(ctx, &ctx->d_win, cap / 224 + 2)) != QMC_OK) return rc;
-        if ((rc = dalloc(ctx, &ctx->d_big_list, cap / 224 + 2)) != QMC_OK) return rc;
+        // sort windows of whole buckets: one per 224 spawn records, and those too large for a warp
+        if ((rc = dalloc(ctx, &ctx->d_wwin, cap / 224 + 2)) != QMC_OK) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_wbig, cap / 224 + 2)) != QMC_OK) return rc;
         ctx->spawn_cap = cap;
         ctx->graph_dirty = true;
         return grow_wpart(ctx);
@@ -587,6 +589,7 @@ int create_context(qmc_ctx** out, const qmc_config* cfg, std::vector<qmc_ctx::In
     ctx->heavy_cap = std::max<int64_t>(4096, cfg->capacity_hint / 64);
     if ((rc = dalloc(ctx, &ctx->d_heavy, ctx->heavy_cap)) != QMC_OK) return bail(rc);
     if (ctx->wide && ((rc = dalloc(ctx, &ctx->d_whist, kWMaxPasses * 256)) != QMC_OK ||
+                      (rc = dalloc(ctx, &ctx->d_wnbig, 1)) != QMC_OK ||
                       (rc = dalloc(ctx, &ctx->d_wplan, kWMaxPasses + 1)) != QMC_OK ||
                       (rc = dalloc(ctx, &ctx->d_wabound, ((int64_t)1 << kBucketBits) + 1)) != QMC_OK))
         return bail(rc);

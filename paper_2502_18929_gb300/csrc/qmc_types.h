@@ -216,7 +216,7 @@ struct DevState {
     uint32_t seq;         // look-back epoch base, advanced by 16 every step
     uint32_t sort_fallback;   // 1: this step's spawns take the LSD radix sort
     uint32_t sort_final;      // 1: the sorted spawns end in the second spawn buffer
-    uint32_t big_windows;     // buckets (64-bit step) or windows (wide step) listed for the CTA sort
+    uint32_t big_windows;     // buckets listed for the CTA sort
     uint32_t tile_ctr[kMaxTileCounters];
 };
 

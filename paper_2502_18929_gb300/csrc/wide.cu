@@ -247,7 +247,6 @@ __global__ void k_wide_prologue(StepParams P)
         st->next_total = 0;
         st->merge_tiles = 0;
         st->sort_fallback = P.sort_mode == 0 ? 1u : 0u;
-        st->big_windows = 0u;
     }
 }
 
@@ -901,7 +900,7 @@ __global__ void __launch_bounds__(1024) k_wide_btop(StepParams P)
 }
 
 // Bucket starts (exclusive prefix, in place) and the sort windows' starts.
-__global__ void __launch_bounds__(1024) k_wide_bapply(StepParams P)
+__global__ void __launch_bounds__(1024) k_wide_bapply(StepParams P, WideParams W)
 {
     __shared__ uint32_t wsum[32];
     DevState* st = P.st;
@@ -923,7 +922,7 @@ __global__ void __launch_bounds__(1024) k_wide_bapply(StepParams P)
         for (int q = 0; q < warp; ++q) off += wsum[q];
         const uint32_t start = off + incl - c;
         P.bucket[b] = start;
-        for (uint32_t k = (start + kWSortWin - 1) / kWSortWin; k * kWSortWin < start + c; ++k) P.win[k] = start;
+        for (uint32_t k = (start + kWSortWin - 1) / kWSortWin; k * kWSortWin < start + c; ++k) W.win[k] = start;
         __syncthreads();
     }
 }
@@ -975,11 +974,11 @@ __device__ __forceinline__ void wbitonic(uint64_t* H, uint64_t* L, uint32_t* G, 
 }
 
 // Window k's bounds [win[k], win[k + 1]), the last one ending at S.
-__device__ __forceinline__ void wwindow(const StepParams& P, int64_t k, int64_t nwin, uint32_t S, uint32_t* lo,
+__device__ __forceinline__ void wwindow(const WideParams& W, int64_t k, int64_t nwin, uint32_t S, uint32_t* lo,
                                         uint32_t* hi)
 {
-    *lo = P.win[k];
-    *hi = k + 1 < nwin ? P.win[k + 1] : S;
+    *lo = W.win[k];
+    *hi = k + 1 < nwin ? W.win[k + 1] : S;
 }
 
 // Load a window of n records into shared memory (padded to N with keys
@@ -1026,11 +1025,11 @@ __global__ void __launch_bounds__(kWThreads) k_wide_bsort_small(StepParams P, Wi
     const int64_t nwin = ((int64_t)S + kWSortWin - 1) / kWSortWin;
     for (int64_t k = (int64_t)blockIdx.x * kW + warp; k < nwin; k += (int64_t)gridDim.x * kW) {
         uint32_t start, end;
-        wwindow(P, k, nwin, S, &start, &end);
+        wwindow(W, k, nwin, S, &start, &end);
         const int n = (int)(end - start);
         if (n <= 1) continue;
         if (n > kWSmallWin) {
-            if (lane == 0) P.big_list[atomicAdd(&st->big_windows, 1u)] = (uint32_t)k;
+            if (lane == 0) W.big_list[atomicAdd(W.nbig, 1u)] = (uint32_t)k;
             continue;
         }
         wsort_window(W.spawn_alt, start, n, R, H, L, G, lane, 32, [] { __syncwarp(); });
@@ -1049,10 +1048,10 @@ __global__ void __launch_bounds__(kWThreads) k_wide_bsort_big(StepParams P, Wide
     if (cta_error(st) || st->sort_fallback) return;
     const uint32_t S = (uint32_t)spawn_count(P);
     const int64_t nwin = ((int64_t)S + kWSortWin - 1) / kWSortWin;
-    const uint32_t nbig = st->big_windows;
+    const uint32_t nbig = *W.nbig;
     for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
         uint32_t start, end;
-        wwindow(P, (int64_t)P.big_list[q], nwin, S, &start, &end);
+        wwindow(W, (int64_t)W.big_list[q], nwin, S, &start, &end);
         const int n = (int)(end - start);
         if (n > kWBigWin) {   // excluded by the fallback rule
             if (threadIdx.x == 0) set_error(st, DERR_INTERNAL);
@@ -1726,6 +1725,7 @@ __global__ void k_wide_finalize(StepParams P)
 __global__ void k_wide_zero_hist(WideParams W)
 {
     for (int i = threadIdx.x; i < kWMaxPasses * 256; i += blockDim.x) W.hist[i] = 0u;
+    if (threadIdx.x == 0) *W.nbig = 0u;
 }
 
 int g_wide_grid = 0;
@@ -1776,7 +1776,7 @@ void launch_wide_step(const StepParams& P, const WideParams& W, cudaStream_t s, 
     k_wide_bhist<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_bpart<<<g, kWThreads, 0, s>>>(P);
     k_wide_btop<<<1, 1024, 0, s>>>(P);
-    k_wide_bapply<<<g, 1024, 0, s>>>(P);
+    k_wide_bapply<<<g, 1024, 0, s>>>(P, W);
     k_wide_bscatter<<<g, kWThreads, 0, s>>>(P, W);
     k_wide_bsort_small<<<g, kWThreads, kWSmallSmem, s>>>(P, W);
     k_wide_bsort_big<<<g, kWThreads, kWBigSmem, s>>>(P, W);

@@ -42,6 +42,9 @@ struct WideParams {
     longlong2* mbase;       // [mtiles_cap]: per merge tile, survivors and new keys before it (last: totals)
     int64_t mtiles_cap;
     int64_t* abound;        // [2^kBucketBits + 1]: first record of N(t) in each bucket of the spawn sort
+    uint32_t* win;          // [spawn_cap / 224 + 2]: start of each sort window of whole buckets
+    uint32_t* big_list;     // [spawn_cap / 224 + 2]: windows too large for a warp
+    uint32_t* nbig;         // how many of them (zeroed every step)
     int64_t* part;          // scan partials
     int64_t part_cap;
     uint32_t* hist;         // [kWMaxPasses][256] digit counts, then digit starts
