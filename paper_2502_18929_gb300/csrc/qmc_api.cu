@@ -1552,6 +1552,7 @@ int qmc_step(qmc_ctx* ctx, double dt, int64_t nsteps)
                 if ((build_err = add_prog(j, &off)) != QMC_OK) break;
                 tab[2 * jobs[j].k + jobs[j].pass] = off;
                 if (jobs[j].pass == 0) tab[2 * jobs[j].k + 1] = off;   // pass 1 repeats pass 0 when absent
+                std::vector<uint8_t>().swap(built[j]);   // in the blob now (or shared with the step before)
             }
             if (build_err != QMC_OK) break;
             const size_t at = (blob.size() + 15) & ~(size_t)15;
