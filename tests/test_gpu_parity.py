@@ -220,6 +220,30 @@ def test_spawn_sort_paths():
     assert c["sort_lsd_steps"] == 1 and c["sort_bucket_steps"] == 0
 
 
+def test_spawn_sort_large_buckets():
+    """States whose keys take one of 64 values in their top 12 bits: the
+    step's spawns fall into a few dozen buckets of hundreds of records (the
+    bucket digit is the key's top 10 to 12 bits here), each sorted by a CTA
+    (buckets of more than 32 records), without overflowing into the LSD sort;
+    bit-exact against the oracle."""
+    prob = P.ghz_circuit(32)
+    gpu, orc = make_pair(prob, 1, 43, 10**6)
+    rng = np.random.default_rng(23)
+    low = np.uint64((1 << 52) - 1)
+    packed = []
+    for k, r, i in _spread_state(32, 1, 12000, 31) + _spread_state(32, 1, 11000, 32):
+        top = rng.integers(0, 64, size=k.size).astype(np.uint64) << np.uint64(52)
+        k2, idx = np.unique((k & low) | top, return_index=True)
+        packed.append((k2, r[idx], i[idx]))
+    _load_state(gpu, orc, [packed[0]], [packed[1]], 400, 5.1, 0.1)
+    gpu.counters(reset=True)
+    gpu.step(0.1, 1)
+    assert orc.step(0.1, 1) == O.OK
+    assert_same(gpu, orc, where="large buckets")
+    c = gpu.counters()
+    assert c["sort_bucket_steps"] == 1 and c["sort_lsd_steps"] == 0
+
+
 def test_heavy_and_light_parents():
     """A state with 1e5 walkers (four heavy chunks) next to light states."""
     prob = P.ghz_circuit(5)
