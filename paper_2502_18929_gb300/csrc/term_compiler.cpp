@@ -156,10 +156,17 @@ int expand(const Schedule& s, double t, double dt_eff, std::vector<RawT<M>>* out
     return QMC_OK;
 }
 
+// Copy count records into the blob with their padding bytes zeroed (with
+// 64-bit masks and 128-bit keys several records have padding), so a program's
+// bytes depend on its contents alone and equal programs compare equal.
 template <typename T>
 void put(std::vector<uint8_t>* blob, size_t at, const T* src, size_t count)
 {
-    if (count) std::memcpy(blob->data() + at, src, count * sizeof(T));
+    for (size_t i = 0; i < count; ++i) {
+        T rec = src[i];
+        __builtin_clear_padding(&rec);
+        std::memcpy(blob->data() + at + i * sizeof(T), &rec, sizeof(T));
+    }
 }
 
 template <size_t A>
@@ -376,16 +383,20 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
         int64_t b = std::llabs(hdr.self_const_re) + std::llabs(hdr.self_const_im);
         for (const Gen& g : gen_c) b += std::llabs(g.cre) + std::llabs(g.cim);
         for (const AffGroup& g : affs) {
+            // |er| + |ei| + f is convex in the counts (cx, cy, c11), whose
+            // feasible values are the integer points of the simplex spanned by
+            // the four ways all m members share one bit pattern (x_q, y_q):
+            // the maximum is at one of its corners.
             const int m = popc(g.members);
+            const int corner[4][3] = {{0, 0, 0}, {0, m, 0}, {m, 0, 0}, {m, m, m}};
             int64_t best = 0;
-            for (int cx = 0; cx <= m; ++cx)
-                for (int cy = 0; cy <= m; ++cy)
-                    for (int c11 = std::max(0, cx + cy - m); c11 <= std::min(cx, cy); ++c11) {
-                        const int64_t er = g.s0re + g.sare * cx + g.sbre * cy + g.scre * c11;
-                        const int64_t ei = g.s0im + g.saim * cx + g.sbim * cy + g.scim * c11;
-                        const int64_t f = g.f0 + g.fx * cx + g.fy * cy + g.f11 * c11;
-                        best = std::max<int64_t>(best, (int64_t)(std::llabs(er) + std::llabs(ei)) + f);
-                    }
+            for (const auto& c : corner) {
+                const int cx = c[0], cy = c[1], c11 = c[2];
+                const int64_t er = g.s0re + g.sare * cx + g.sbre * cy + g.scre * c11;
+                const int64_t ei = g.s0im + g.saim * cx + g.sbim * cy + g.scim * c11;
+                const int64_t f = g.f0 + g.fx * cx + g.fy * cy + g.f11 * c11;
+                best = std::max<int64_t>(best, (int64_t)(std::llabs(er) + std::llabs(ei)) + f);
+            }
             b += best;
         }
         for (const SelfGen& g : selfgen) b += std::llabs(g.qre) + std::llabs(g.qim);
