@@ -18,6 +18,7 @@
 #include "term_compiler.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -237,14 +238,34 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
     int rc = expand(s, t, dt_eff, &raw);
     if (rc != QMC_OK) return rc;
 
-    // group by destination mask, merge equal parity terms (exact sums)
-    std::map<K, std::map<std::pair<M, M>, std::pair<int64_t, int64_t>>> groups;
-    for (const RawT<M>& r : raw) {
-        const K mk = ((K)r.xl << n) | (K)r.xr;
-        auto& g = groups[mk][{r.zl, r.zr}];
-        g.first += r.qre;
-        g.second += r.qim;
+    // group by destination mask, merge equal parity terms (exact sums): the
+    // expanded terms sorted by (destination mask, zl, zr), equal keys summed;
+    // a group is a stretch of one mask, in ascending mask order
+    struct KeyedTerm {
+        K mk;
+        M zl, zr;
+        int64_t qre, qim;
+    };
+    std::vector<KeyedTerm> sorted;
+    sorted.reserve(raw.size());
+    for (const RawT<M>& r : raw) sorted.push_back(KeyedTerm{((K)r.xl << n) | (K)r.xr, r.zl, r.zr, r.qre, r.qim});
+    std::sort(sorted.begin(), sorted.end(), [](const KeyedTerm& a, const KeyedTerm& b) {
+        if (a.mk != b.mk) return a.mk < b.mk;
+        if (a.zl != b.zl) return a.zl < b.zl;
+        return a.zr < b.zr;
+    });
+    std::vector<KeyedTerm> merged;
+    merged.reserve(sorted.size());
+    for (const KeyedTerm& r : sorted) {
+        if (!merged.empty() && merged.back().mk == r.mk && merged.back().zl == r.zl && merged.back().zr == r.zr) {
+            merged.back().qre += r.qre;
+            merged.back().qim += r.qim;
+        } else {
+            merged.push_back(r);
+        }
     }
+    size_t g0 = 0;   // merged[0, g0): the diagonal group (mask 0)
+    while (g0 < merged.size() && merged[g0].mk == (K)0) ++g0;
 
     ProgHeader hdr;
     std::memset(&hdr, 0, sizeof(hdr));
@@ -257,11 +278,10 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
     // diagonal (self) group
     {
         std::map<std::tuple<uint32_t, int64_t, int64_t>, M> sf; // (type, q) -> members
-        auto it = groups.find((K)0);
-        if (it != groups.end()) {
-            for (const auto& kv : it->second) {
-                const M zl = kv.first.first, zr = kv.first.second;
-                int64_t qre = kv.second.first, qim = kv.second.second;
+        {
+            for (size_t i = 0; i < g0; ++i) {
+                const M zl = merged[i].zl, zr = merged[i].zr;
+                int64_t qre = merged[i].qre, qim = merged[i].qim;
                 if (qre == 0 && qim == 0) continue;
                 if (zl == 0 && zr == 0) {
                     hdr.self_const_re += qre;
@@ -276,7 +296,6 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
                     selfgen.push_back(SelfGen{zl, zr, qre, qim});
                 }
             }
-            groups.erase(it);
         }
         for (const auto& kv : sf)
             selffam.push_back(SelfFam{kv.second, std::get<0>(kv.first), std::get<1>(kv.first),
@@ -284,17 +303,19 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
     }
 
     // off-diagonal groups: single-qubit families or generic groups
-    std::map<std::vector<int64_t>, M> famkeys; // (ab, tre[4], tim[4]) -> members
-    for (const auto& gkv : groups) {
-        const K mk = gkv.first;
+    std::map<std::array<int64_t, 9>, M> famkeys; // (ab, tre[4], tim[4]) -> members
+    for (size_t ga = g0, gb = g0; ga < merged.size(); ga = gb) {
+        const K mk = merged[ga].mk;
+        while (gb < merged.size() && merged[gb].mk == mk) ++gb;
         const M xl = (M)(mk >> n), xr = (M)(mk & (((K)1 << n) - 1));
         const M qm = xl | xr;
         bool single = popc(qm) == 1;
         std::vector<GTerm> terms;
-        for (const auto& kv : gkv.second) {
-            if (kv.second.first == 0 && kv.second.second == 0) continue;
-            terms.push_back(GTerm{kv.first.first, kv.first.second, kv.second.first, kv.second.second});
-            if ((kv.first.first & ~qm) || (kv.first.second & ~qm)) single = false;
+        for (size_t i = ga; i < gb; ++i) {
+            const KeyedTerm& kt = merged[i];
+            if (kt.qre == 0 && kt.qim == 0) continue;
+            terms.push_back(GTerm{kt.zl, kt.zr, kt.qre, kt.qim});
+            if ((kt.zl & ~qm) || (kt.zr & ~qm)) single = false;
         }
         if (terms.empty()) continue;
         if (single) {
@@ -312,8 +333,8 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
             for (int pi = 0; pi < 4; ++pi) allzero = allzero && tre[pi] == 0 && tim[pi] == 0;
             if (allzero) continue;
             uint32_t ab = ((xl != 0) ? 2u : 0u) | ((xr != 0) ? 1u : 0u);
-            std::vector<int64_t> key = {(int64_t)ab, tre[0], tre[1], tre[2], tre[3],
-                                        tim[0], tim[1], tim[2], tim[3]};
+            const std::array<int64_t, 9> key = {(int64_t)ab, tre[0], tre[1], tre[2], tre[3],
+                                                tim[0], tim[1], tim[2], tim[3]};
             famkeys[key] |= qm;
             continue;
         }
@@ -444,18 +465,18 @@ int build_program_t(const Schedule& s, double t, double dt_eff, std::vector<uint
     // any merging (the proposal spawning's destination law)
     std::vector<StatSlot> stat;
     {
-        std::map<K, int64_t> sw;
-        for (const RawT<M>& r : raw) {
-            const K mk = ((K)r.xl << n) | (K)r.xr;
-            const int64_t a = std::llabs(r.qre) + std::llabs(r.qim);
-            int64_t& acc = sw[mk];
-            acc = (acc >= (1ll << 52) || a >= (1ll << 52)) ? (1ll << 52) : std::min<int64_t>(acc + a, 1ll << 52);
-        }
+        // per mask, a saturating sum (order-free) over the sorted expanded terms
         int64_t run = 0;
-        for (const auto& kv : sw) {
-            if (kv.second == 0) continue;
-            run = std::min<int64_t>(run + kv.second, 1ll << 52);
-            stat.push_back(StatSlot{kv.first, run});
+        for (size_t a = 0, b = 0; a < sorted.size(); a = b) {
+            const K mk = sorted[a].mk;
+            int64_t acc = 0;
+            for (b = a; b < sorted.size() && sorted[b].mk == mk; ++b) {
+                const int64_t w = std::llabs(sorted[b].qre) + std::llabs(sorted[b].qim);
+                acc = (acc >= (1ll << 52) || w >= (1ll << 52)) ? (1ll << 52) : std::min<int64_t>(acc + w, 1ll << 52);
+            }
+            if (acc == 0) continue;
+            run = std::min<int64_t>(run + acc, 1ll << 52);
+            stat.push_back(StatSlot{mk, run});
         }
         hdr.p_att = run;
     }
